@@ -1,0 +1,318 @@
+/*
+ * lof_ref.c -- ORACLE for the LOFAR Online Flagger hot path (test
+ * infrastructure only; see lof_ref.h).  Plain loops in the paper's order and
+ * notation, one binary64 operation per written step.
+ *
+ * Readings of points the paper leaves open (each is restated in the design
+ * notes of the repository):
+ *  - factor_I = startThreshold * p^(log2 I) / I, with startThreshold = 6, the
+ *    only reading that yields the printed 6 sigma (I=1) and 4.5 sigma (I=2)
+ *    of Section 2.1;
+ *  - a window of I samples is flagged when the sum of its samples, with every
+ *    already-flagged sample replaced by threshold_I, exceeds I*threshold_I
+ *    (upper side only, strict '>'), i.e. sum_unflagged > (I - n_flagged) *
+ *    threshold_I;
+ *  - all windows of one size are judged against the flags of the previous
+ *    sizes only (snapshot), windows lie fully inside the row;
+ *  - "stddev" is the robust 1.4826*MAD (population stddev when the MAD is 0);
+ *  - time-pass statistics pool every sample of the channels the frequency
+ *    pass left unflagged (Section 4: frequency flagging first "removes strong
+ *    narrow-band RFI that would otherwise decrease the quality of the
+ *    statistics");
+ *  - the history flagger keeps one ring of per-channel means, multiplier k,
+ *    ties flag (the listing's "if (currentValue < threshold)" keeps them).
+ */
+#include "lof_ref.h"
+
+#include <math.h>
+#include <stdlib.h>
+#include <string.h>
+
+/* 1/Phi^-1(3/4): scales the MAD of normal data to its standard deviation. */
+static const double MAD_TO_SIGMA = 1.482602218505602;
+
+/* Section 2.1: factor_I = startThreshold * p^(log2 I) / I, I = 2^k.
+ * p^k is formed by k successive multiplications. */
+double lof_ref_factor(const lof_ref_params *pr, int k) {
+  double pk = 1.0;
+  for (int i = 0; i < k; ++i) pk = pk * pr->p;
+  double f = pr->start_threshold * pk;
+  return f / (double)((int64_t)1 << k);
+}
+
+/* Section 2.1: threshold_I = median + stddev * factor_I * sensitivity. */
+double lof_ref_threshold(const lof_ref_params *pr, double median, double sigma, int k) {
+  double a = sigma * lof_ref_factor(pr, k);
+  double b = a * pr->sensitivity;
+  return median + b;
+}
+
+static int cmp_double(const void *a, const void *b) {
+  double x = *(const double *)a, y = *(const double *)b;
+  return (x > y) - (x < y);
+}
+
+/* Textbook median: middle order statistic, or the mean of the two middle
+ * ones for even n (Section 4.2 lists medians among the statistics). */
+double lof_ref_median(const double *x, int64_t n) {
+  if (n <= 0) return 0.0;
+  double *s = (double *)malloc((size_t)n * sizeof(double));
+  memcpy(s, x, (size_t)n * sizeof(double));
+  qsort(s, (size_t)n, sizeof(double), cmp_double);
+  double m = (n % 2) ? s[n / 2] : (s[n / 2 - 1] + s[n / 2]) * 0.5;
+  free(s);
+  return m;
+}
+
+/* Population standard deviation.  Integer data: exact moments,
+ * M = n*sum(x^2) - (sum x)^2 in 128-bit integers, sigma = sqrt(M / n^2).
+ * Float data: two sequential passes (mean, then squared deviations). */
+static double population_std(const double *x, int64_t n, int is_int) {
+  if (n <= 0) return 0.0;
+  if (is_int) {
+    unsigned __int128 s1 = 0, s2 = 0;
+    for (int64_t i = 0; i < n; ++i) {
+      unsigned __int128 v = (unsigned __int128)(uint64_t)x[i];
+      s1 += v;
+      s2 += v * v;
+    }
+    unsigned __int128 M = (unsigned __int128)(uint64_t)n * s2 - s1 * s1;
+    double nn = (double)n * (double)n;
+    return sqrt((double)M / nn);
+  }
+  double s = 0.0;
+  for (int64_t i = 0; i < n; ++i) s = s + x[i];
+  double mu = s / (double)n;
+  double q = 0.0;
+  for (int64_t i = 0; i < n; ++i) {
+    double d = x[i] - mu;
+    q = q + d * d;
+  }
+  return sqrt(q / (double)n);
+}
+
+/* Section 4.2 statistics: median and a robust stddev.  The MAD is the median
+ * of |x - median|. */
+double lof_ref_sigma(const lof_ref_params *pr, const double *x, int64_t n, int is_int,
+                     double *median) {
+  if (n <= 0) {
+    *median = 0.0;
+    return 0.0;
+  }
+  double m = lof_ref_median(x, n);
+  *median = m;
+  if (pr->sigma_estimator == LOF_REF_SIGMA_STD) return population_std(x, n, is_int);
+  double *d = (double *)malloc((size_t)n * sizeof(double));
+  for (int64_t i = 0; i < n; ++i) d[i] = fabs(x[i] - m);
+  double mad = lof_ref_median(d, n);
+  free(d);
+  if (mad > 0.0) return MAD_TO_SIGMA * mad;
+  return population_std(x, n, is_int);
+}
+
+/* Section 2.1 SumThreshold, one dimension.  For I = 1, 2, 4, ... up to
+ * min(max_window, L): every window [t, t+I) fully inside the row is judged
+ * against the flags left by the smaller windows; it is flagged when the sum
+ * of its unflagged samples exceeds (I - n_flagged) * threshold_I.  A sigma
+ * that is not positive flags nothing. */
+void lof_ref_sum_threshold(const lof_ref_params *pr, const double *v, int64_t L, double median,
+                           double sigma, uint8_t *flags) {
+  if (!(sigma > 0.0) || L <= 0) return;
+  uint8_t *next = (uint8_t *)malloc((size_t)L);
+  for (int k = 0;; ++k) {
+    int64_t I = (int64_t)1 << k;
+    if (I > pr->max_window || I > L) break;
+    double thr = lof_ref_threshold(pr, median, sigma, k);
+    memcpy(next, flags, (size_t)L);
+    for (int64_t t = 0; t + I <= L; ++t) {
+      int64_t nf = 0;
+      double su = 0.0;
+      for (int64_t j = t; j < t + I; ++j) {
+        if (flags[j])
+          nf++;
+        else
+          su = su + v[j];
+      }
+      double limit = (double)(I - nf) * thr;
+      if (su > limit)
+        for (int64_t j = t; j < t + I; ++j) next[j] = 1;
+    }
+    memcpy(flags, next, (size_t)L);
+  }
+  free(next);
+}
+
+/* Section 4: "we may have to compute amplitudes first" -- the power of one
+ * sample; non-finite Stokes I values are reported through *bad. */
+static double sample_power(int dtype, const void *in, int64_t idx, int *bad) {
+  *bad = 0;
+  if (dtype == LOF_REF_CI8) {
+    const int8_t *p = (const int8_t *)in + 2 * idx;
+    double re = (double)p[0], im = (double)p[1];
+    return re * re + im * im;
+  }
+  if (dtype == LOF_REF_CI16) {
+    const int16_t *p = (const int16_t *)in + 2 * idx;
+    double re = (double)p[0], im = (double)p[1];
+    return re * re + im * im;
+  }
+  float f = ((const float *)in)[idx];
+  if (!isfinite(f)) {
+    *bad = 1;
+    return 0.0;
+  }
+  return (double)f;
+}
+
+static void write_out(int dtype, const void *in, int64_t iidx, void *out, int64_t oidx,
+                      int flagged) {
+  if (dtype == LOF_REF_CI8) {
+    const int8_t *s = (const int8_t *)in + 2 * iidx;
+    int8_t *d = (int8_t *)out + 2 * oidx;
+    d[0] = flagged ? 0 : s[0];
+    d[1] = flagged ? 0 : s[1];
+  } else if (dtype == LOF_REF_CI16) {
+    const int16_t *s = (const int16_t *)in + 2 * iidx;
+    int16_t *d = (int16_t *)out + 2 * oidx;
+    d[0] = flagged ? 0 : s[0];
+    d[1] = flagged ? 0 : s[1];
+  } else {
+    float v = ((const float *)in)[iidx];
+    ((float *)out)[oidx] = flagged ? 0.0f : v;
+  }
+}
+
+/* Section 4.1: mean and population stddev of the stored per-channel means,
+ * summed oldest -> newest; threshold = mean + k * stddev. */
+static double history_threshold(const double *ring, int count, double k) {
+  double s = 0.0;
+  for (int i = 0; i < count; ++i) s = s + ring[i];
+  double mu = s / (double)count;
+  double q = 0.0;
+  for (int i = 0; i < count; ++i) {
+    double d = ring[i] - mu;
+    q = q + d * d;
+  }
+  double sd = sqrt(q / (double)count);
+  return mu + k * sd;
+}
+
+int lof_ref_flag_unit(const lof_ref_params *pr, int dtype, const void *in, int C, int T,
+                      int64_t in_stride, void *out, int64_t out_stride, uint8_t *mask,
+                      int64_t mask_stride, const double *ring, const int32_t *ring_count,
+                      double *pending, uint8_t *has_pending, lof_ref_stats *stats) {
+  if (!pr || !in || C < 0 || T < 0) return -1;
+  if (dtype != LOF_REF_CI8 && dtype != LOF_REF_CI16 && dtype != LOF_REF_F32) return -1;
+  const int is_int = dtype != LOF_REF_F32;
+  const int64_t N = (int64_t)C * T;
+  lof_ref_stats st;
+  memset(&st, 0, sizeof st);
+
+  /* power and entry flags */
+  double *P = (double *)malloc((size_t)(N > 0 ? N : 1) * sizeof(double));
+  uint8_t *F = (uint8_t *)calloc((size_t)(N > 0 ? N : 1), 1);
+  for (int c = 0; c < C; ++c)
+    for (int t = 0; t < T; ++t) {
+      int bad;
+      P[(int64_t)c * T + t] = sample_power(dtype, in, (int64_t)c * in_stride + t, &bad);
+      F[(int64_t)c * T + t] = (uint8_t)bad;
+    }
+
+  /* Section 4: integrate the time direction fully for frequency flagging. */
+  uint8_t *Fc = (uint8_t *)calloc((size_t)(C > 0 ? C : 1), 1);
+  double *S = (double *)malloc((size_t)(C > 0 ? C : 1) * sizeof(double));
+  for (int c = 0; c < C; ++c) {
+    double s = 0.0;
+    for (int t = 0; t < T; ++t)
+      if (!F[(int64_t)c * T + t]) s = s + P[(int64_t)c * T + t];
+    S[c] = s;
+  }
+  if (C > 0) st.sigma_f = lof_ref_sigma(pr, S, C, is_int, &st.median_f);
+  if (pr->enable_freq && C > 0) lof_ref_sum_threshold(pr, S, C, st.median_f, st.sigma_f, Fc);
+  for (int c = 0; c < C; ++c) st.n_chan_freq += Fc[c];
+
+  /* Section 4 / 4.2: statistics for the time pass pool the samples of the
+   * channels left unflagged by the frequency pass. */
+  int64_t nu = 0;
+  double *U = (double *)malloc((size_t)(N > 0 ? N : 1) * sizeof(double));
+  for (int c = 0; c < C; ++c) {
+    if (Fc[c]) continue;
+    for (int t = 0; t < T; ++t)
+      if (!F[(int64_t)c * T + t]) U[nu++] = P[(int64_t)c * T + t];
+  }
+  if (nu > 0) st.sigma_t = lof_ref_sigma(pr, U, nu, is_int, &st.median_t);
+  free(U);
+
+  /* Section 2.1 in the time direction, one channel at a time. */
+  uint8_t *entry = (uint8_t *)malloc((size_t)(T > 0 ? T : 1));
+  for (int c = 0; c < C; ++c) {
+    if (Fc[c] || !pr->enable_time || nu == 0) continue;
+    uint8_t *row = F + (int64_t)c * T;
+    memcpy(entry, row, (size_t)T);
+    lof_ref_sum_threshold(pr, P + (int64_t)c * T, T, st.median_t, st.sigma_t, row);
+    for (int t = 0; t < T; ++t) st.n_flag_time += (row[t] && !entry[t]);
+  }
+  free(entry);
+
+  /* Section 4.1: the history flagger, per channel. */
+  uint8_t *Fh = (uint8_t *)calloc((size_t)(C > 0 ? C : 1), 1);
+  for (int c = 0; c < C; ++c) {
+    if (has_pending) has_pending[c] = 0;
+    if (Fc[c]) continue;
+    double s = 0.0;
+    int64_t n = 0;
+    for (int t = 0; t < T; ++t)
+      if (!F[(int64_t)c * T + t]) {
+        s = s + P[(int64_t)c * T + t];
+        n++;
+      }
+    if (n == 0) continue;
+    double cur = s / (double)n;
+    double staged = cur;
+    if (pr->enable_history && ring && ring_count && ring_count[c] >= pr->history_min &&
+        ring_count[c] > 0) {
+      double thr = history_threshold(ring + (int64_t)c * pr->history_len, ring_count[c],
+                                     pr->history_k);
+      if (!(cur < thr)) {
+        staged = thr;
+        Fh[c] = 1;
+      }
+    }
+    if (pending) pending[c] = staged;
+    if (has_pending) has_pending[c] = 1;
+    st.n_chan_hist += Fh[c];
+  }
+
+  /* Apply: flagged data is removed (zeroed) and the mask is reported. */
+  for (int c = 0; c < C; ++c)
+    for (int t = 0; t < T; ++t) {
+      int f = Fc[c] || Fh[c] || F[(int64_t)c * T + t];
+      st.n_flag_total += f;
+      if (mask) mask[(int64_t)c * mask_stride + t] = (uint8_t)f;
+      if (out) write_out(dtype, in, (int64_t)c * in_stride + t, out, (int64_t)c * out_stride + t, f);
+    }
+
+  if (stats) *stats = st;
+  free(P);
+  free(F);
+  free(Fc);
+  free(S);
+  free(Fh);
+  return 0;
+}
+
+void lof_ref_history_commit(const lof_ref_params *pr, int C, double *ring, int32_t *ring_count,
+                            const double *pending, const uint8_t *has_pending) {
+  const int H = pr->history_len;
+  for (int c = 0; c < C; ++c) {
+    if (!has_pending[c]) continue;
+    double *r = ring + (int64_t)c * H;
+    if (ring_count[c] < H) {
+      r[ring_count[c]] = pending[c];
+      ring_count[c] += 1;
+    } else {
+      for (int i = 1; i < H; ++i) r[i - 1] = r[i];
+      r[H - 1] = pending[c];
+    }
+  }
+}
