@@ -1,0 +1,388 @@
+"""Benchmark: LOFAR Online Flagger hot path on GB300.
+
+Workload (one "step" = one block of the full LOFAR pre-beamformer
+configuration through the whole hot path): 48 stations x 2 polarisations x 8
+subbands = 768 units of 256 channels x 3072 samples of complex int16 voltages
+(sigma 32, seeded tones and broadband impulses), flagged by ONE persistent
+launch (lof_flag_block), followed by the history commit (lof_history_update)
+with rings pre-filled to 60 means.  Inputs (2.4 GB) stay resident in HBM and
+are larger than L2, so no flush is needed between steps.
+
+Reported: input Msamples/s (value), the same through the host-buffer entry
+point with PCIe/C2C copies inside the timed region (e2e), the HBM roofline
+fraction of the flag kernel, the oracle timed on the host cores
+(cpu_baseline), per-step p50/p99 latency of the batched launch against the
+plain form (one launch per station-subband), clocks during the timed region.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+N_STATION, N_POL, N_SUBBAND, C, T = 48, 2, 8, 256, 3072
+BYTES_PER_SAMPLE = 4 + 4 + 1          # ci16 in + ci16 out + uint8 mask
+METRIC = "input Msamples/s (full LOFAR pre-beamformer block, 768 units x 256 ch x 3072 t, ci16)"
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--no-plain", action="store_true")
+    ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    return ap.parse_args()
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+def measured_peak_hbm():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return float(json.load(f)["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled during the timed region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.Q}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except Exception:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self):
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            p = [x.strip() for x in ln.split(",")]
+            if len(p) < 9:
+                continue
+            try:
+                sm.append(float(p[1]))
+                mx.append(float(p[2]))
+            except ValueError:
+                continue
+            for n, v in zip(names, p[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(n)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def make_block(dev, seed=2, block=0):
+    """Config-2 block [station, pol, subband, C, T, 2] int16 on the device: tones in
+    ~2% of the channels of each station-subband, impulses covering ~1% of the
+    samples of each station (all its subbands and pols), independent stations."""
+    import torch
+    from paper_1701_08197_gb300 import synth
+    parts = []
+    for s in range(N_STATION):
+        spec = synth.VoltageSpec(n_station=1, n_pol=N_POL, n_subband=N_SUBBAND, C=C, T=T,
+                                 sigma=32.0, tone_frac=0.02, impulse_frac=0.01)
+        parts.append(synth.voltage_block(spec, seed=synth._mix(seed, s), block=block, device=dev))
+    return torch.cat(parts, dim=0).contiguous()
+
+
+def build_units(x, out, mask, stats, slot_base=0):
+    from paper_1701_08197_gb300 import lof
+    units = []
+    u = 0
+    for s in range(N_STATION):
+        for p in range(N_POL):
+            for b in range(N_SUBBAND):
+                units.append(lof.make_unit(x[s, p, b], out[s, p, b], mask[s, p, b],
+                                           slot_base + u * C, stats[u]))
+                u += 1
+    return units
+
+
+def run_gpu(args):
+    import numpy as np
+    import torch
+    import torch.distributed as dist
+    from paper_1701_08197_gb300 import lof
+
+    rank, world, local = dist_env()
+    dev = torch.device("cuda", local)
+    torch.cuda.set_device(dev)
+    if world > 1:
+        dist.init_process_group("nccl", device_id=dev)
+    n_units = N_STATION * N_POL * N_SUBBAND
+    samples = n_units * C * T
+    x = make_block(dev, seed=2 + 1000 * rank)
+    out = torch.empty_like(x)
+    mask = torch.empty(x.shape[:-1], dtype=torch.uint8, device=dev)
+    stats = lof.stats_tensor(n_units, dev)
+    fl = lof.Flagger(local, n_history_slots=n_units * C)
+    # rings pre-filled with 60 means per channel (steady state of the history flagger)
+    pw = (x.to(torch.float32) ** 2).sum(-1).mean(-1).reshape(-1).double().cpu().numpy()
+    rng = np.random.default_rng(7)
+    H = fl.params.history_len
+    ring = pw[:, None] * (1.0 + 0.01 * rng.standard_normal((pw.size, H)))
+    fl.history_import(0, ring, np.full(pw.size, H, np.int32))
+    units = build_units(x, out, mask, stats)
+    stream = torch.cuda.Stream(dev)
+
+    def step(seq):
+        fl.flag_block(lof.LOF_CI16, units, seq, stream)
+        fl.history_update(units, stream)
+
+    with torch.cuda.stream(stream):
+        for i in range(args.warmup):
+            step(i)
+        fl.status(stream)
+    torch.cuda.synchronize()
+    # timed region: K steps, events per step, and the flag kernel alone
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps + 1)]
+    kev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+           for _ in range(args.steps)]
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    with ClockSampler(local) as clk:
+        time.sleep(0.3)
+        ev[0].record(stream)
+        for i in range(args.steps):
+            kev[i][0].record(stream)
+            fl.flag_block(lof.LOF_CI16, units, 1000 + i, stream)
+            kev[i][1].record(stream)
+            fl.history_update(units, stream)
+            ev[i + 1].record(stream)
+        stream.synchronize()
+        time.sleep(0.2)
+    fl.status(stream)
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    step_ms = [ev[i].elapsed_time(ev[i + 1]) for i in range(args.steps)]
+    total_ms = ev[0].elapsed_time(ev[-1])
+    kern_ms = [a.elapsed_time(b) for a, b in kev]
+    t_max = total_ms
+    if world > 1:
+        tt = torch.tensor([total_ms], device=dev)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        t_max = float(tt.item())
+    value = samples * world * args.steps / (t_max * 1e-3) / 1e6
+    res = {"rank": rank, "value": value, "ms_per_step": t_max / args.steps, "step_ms": step_ms,
+           "kern_ms": kern_ms, "clocks": clk.summary(), "samples": samples}
+
+    # plain form: one launch per station-subband (its two polarisations)
+    if not args.no_plain and rank == 0:
+        groups = [[units[(s * N_POL + p) * N_SUBBAND + b] for p in range(N_POL)]
+                  for s in range(N_STATION) for b in range(N_SUBBAND)]
+        with torch.cuda.stream(stream):
+            for g in groups[:8]:
+                fl.flag_block(lof.LOF_CI16, g, 0, stream)
+        torch.cuda.synchronize()
+        pev = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
+        reps = []
+        for r in range(3):
+            a, b = pev[0], pev[1]
+            a.record(stream)
+            for g in groups:
+                fl.flag_block(lof.LOF_CI16, g, 0, stream)
+            b.record(stream)
+            stream.synchronize()
+            reps.append(a.elapsed_time(b))
+        fl.status(stream)
+        res["plain_ms"] = reps
+
+    # end to end through the host-buffer entry point
+    if not args.no_e2e and rank == 0:
+        hx = x.cpu().pin_memory()
+        hout = torch.empty_like(hx).pin_memory()
+        hmask = torch.empty(hx.shape[:-1], dtype=torch.uint8).pin_memory()
+        hst = torch.zeros_like(stats, device="cpu").pin_memory()
+        hunits = build_units(hx, hout, hmask, hst)
+        e2e_steps = max(2, min(5, args.steps))
+        fl.flag_block_host(lof.LOF_CI16, hunits, 0, stream)  # warm staging
+        stream.synchronize()
+        fl.status(stream)
+        t0 = time.perf_counter()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for i in range(e2e_steps):
+            fl.flag_block_host(lof.LOF_CI16, hunits, 2000 + i, stream)
+            fl.history_update(units, stream)
+        e1.record(stream)
+        stream.synchronize()
+        wall = time.perf_counter() - t0
+        fl.status(stream)
+        e2e_ms = e0.elapsed_time(e1) / e2e_steps
+        res["e2e"] = {"value": samples / (e2e_ms * 1e-3) / 1e6, "unit": "Msamples/s",
+                      "h2d_bytes_per_step": int(hx.numel() * hx.element_size()),
+                      "d2h_bytes_per_step": int(hout.numel() * hout.element_size() + hmask.numel()
+                                                + hst.numel() * 8),
+                      "ms_per_step": e2e_ms, "wall_ms_per_step": wall * 1e3 / e2e_steps}
+    fl.close()
+    if world > 1:
+        dist.destroy_process_group()
+    return res
+
+
+def oracle_sample(seconds: float, seed=2):
+    """The oracle (as it stands) on host cores: units of the same workload, one
+    per thread (the paper's thread-per-subband CPU layout), bounded in time."""
+    from concurrent.futures import ThreadPoolExecutor
+
+    import torch
+
+    import oracle
+    from paper_1701_08197_gb300 import synth
+    P = oracle.default_params()
+    cores = os.cpu_count() or 1
+    spec = synth.VoltageSpec(n_station=1, n_pol=N_POL, n_subband=N_SUBBAND, C=C, T=T,
+                             sigma=32.0, tone_frac=0.02, impulse_frac=0.01)
+    blk = synth.voltage_block(spec, seed=synth._mix(seed, 0), block=0, device="cpu")
+    units = [blk[0, p, b].numpy() for p in range(N_POL) for b in range(N_SUBBAND)]
+    oracle.lib()
+    done = [0]
+    lock = threading.Lock()
+    deadline = time.perf_counter() + seconds
+
+    def work(i):
+        if time.perf_counter() > deadline:
+            return 0
+        oracle.flag_unit(P, units[i % len(units)], want_out=True)
+        with lock:
+            done[0] += 1
+        return 1
+
+    t0 = time.perf_counter()
+    n_jobs = max(cores, 2 * cores)
+    with ThreadPoolExecutor(cores) as ex:
+        list(ex.map(work, range(n_jobs)))
+    wall = time.perf_counter() - t0
+    n = done[0]
+    value = n * C * T / wall / 1e6 if n else 0.0
+    return {"value": value, "unit": "Msamples/s", "cores": cores, "kind": "oracle",
+            "sample": f"{n} units of 256 x 3072 ci16 (one station's 16 units, repeated), "
+                      f"{cores} threads, one unit per thread, {wall:.1f} s wall"}
+
+
+def main():
+    args = parse()
+    rank, world, local = dist_env()
+    if args.impl == "reference":
+        if rank != 0:
+            return
+        steps = []
+        cb = None
+        for i in range(args.warmup + args.steps):
+            r = oracle_sample(max(2.0, args.cpu_seconds / max(1, args.steps)))
+            if i >= args.warmup:
+                steps.append(r)
+            cb = r
+        vals = [r["value"] for r in steps]
+        v = statistics.mean(vals) if vals else 0.0
+        line = {"impl": "reference", "metric": METRIC, "value": v, "unit": "Msamples/s",
+                "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+                "ms_per_step": (C * T * 1e-3 / v) if v else None, "higher_is_better": True,
+                "scaling": "weak", "vs_baseline": None, "dtype": "int64+f64",
+                "data": "synthetic (seeded)",
+                "config": {"workload": "full LOFAR pre-beamformer block, oracle on host cores",
+                           "units": "48 st x 2 pol x 8 sb", "n_chan": C, "n_time": T},
+                "cpu_baseline": {"value": v, "unit": "Msamples/s", "cores": cb["cores"],
+                                 "kind": "oracle", "sample": cb["sample"]},
+                "e2e": {"value": v, "unit": "Msamples/s", "h2d_bytes_per_step": 0,
+                        "d2h_bytes_per_step": 0}}
+        print(json.dumps(line))
+        return
+
+    res = run_gpu(args)
+    if rank != 0:
+        return
+    peak, peak_kind = measured_peak_hbm()
+    samples = res["samples"]
+    kern_avg = statistics.mean(res["kern_ms"])
+    alg_bytes = samples * BYTES_PER_SAMPLE
+    achieved = alg_bytes / (kern_avg * 1e-3) / 1e9
+    step_sorted = sorted(res["step_ms"])
+
+    def pct(a, q):
+        return a[min(len(a) - 1, int(math.ceil(q * len(a))) - 1)]
+
+    line = {
+        "metric": METRIC, "value": res["value"], "unit": "Msamples/s", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": res["ms_per_step"],
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int32/u64",
+        "data": "synthetic (seeded noise + tones + impulses)",
+        "config": {"workload": "full LOFAR pre-beamformer block: 48 st x 2 pol x 8 sb = 768 units "
+                               "x 256 ch x 3072 t, complex int16, history 60",
+                   "launch": "batched persistent (1 launch per block) + history commit",
+                   "l2": "inputs 2.4 GB > L2, no flush", "per_rank_units": 768},
+        "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                     "frac": achieved / peak, "traffic": None,
+                     "kernel": "lof_block_kernel<CI16>", "bytes_per_launch": alg_bytes,
+                     "kernel_ms": kern_avg, "peak_kind": peak_kind},
+        "latency_ms": {"batched_p50": pct(step_sorted, 0.5), "batched_p99": pct(step_sorted, 0.99),
+                       "deadline_ms": T * 1.31072},
+        "clocks": res["clocks"],
+        "gpu_launches": 2 * args.steps,
+    }
+    if "plain_ms" in res:
+        pm = sorted(res["plain_ms"])
+        line["latency_ms"]["plain_block_ms"] = pm[len(pm) // 2]
+        line["plain_vs_batched"] = pm[len(pm) // 2] / kern_avg
+    if "e2e" in res:
+        line["e2e"] = res["e2e"]
+    if not args.no_cpu:
+        line["cpu_baseline"] = oracle_sample(args.cpu_seconds)
+    print(json.dumps(line))
+
+
+if __name__ == "__main__":
+    main()

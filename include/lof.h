@@ -1,0 +1,192 @@
+/*
+ * lof.h -- C ABI of the GB300-native LOFAR Online Flagger (LOF) hot path.
+ *
+ * The operation is the real-time flagger of "Towards Exascale Real-Time RFI
+ * Mitigation" (van Nieuwpoort, 2017), applied independently to every "unit":
+ * one (station, polarisation, subband) block of n_chan channels x n_time
+ * samples (pre-correlation placement, Section 3), or one beam-formed Stokes I
+ * subband (post-beam-forming placement).  Per unit, in this order:
+ *   a1  power P[c,t] = re^2 + im^2 of the complex voltages (Section 4: "we may
+ *       have to compute amplitudes first"); Stokes I input is already power;
+ *   a2  time-integrated spectrum S[c] = sum_t P[c,t] (Section 4: "integrate the
+ *       time direction fully for frequency flagging");
+ *   a3  median and robust stddev of S (Section 4.2);
+ *   a4  SumThreshold over S (Section 2.1) -> whole channels flagged;
+ *   a5  median and robust stddev pooled over every sample of the channels the
+ *       frequency pass kept (Section 4: frequency flagging first protects the
+ *       statistics);
+ *   a6  SumThreshold along time in every kept channel, windows 1, 2, 4, ...,
+ *       max_window (Section 2.1);
+ *   a7  history flagger per channel (Section 4.1): the mean of the unflagged
+ *       samples against mean + k * stddev of the means of earlier blocks;
+ *   a8  mask = frequency | time | history flags; flagged samples of the output
+ *       are zeroed (flagged data is removed before the beam former, Section 3).
+ * SumThreshold (Section 2.1): threshold_I = median + stddev * factor_I *
+ * sensitivity with factor_I = start_threshold * p^(log2 I) / I.  A window of I
+ * samples is flagged when the sum of its samples, flagged ones counted as
+ * threshold_I, exceeds I * threshold_I; windows of one size see the flags of
+ * the smaller sizes only; windows lie inside the row.  "stddev" is
+ * 1.482602218505602 * MAD (population stddev when the MAD is 0).
+ *
+ * Integer voltages give bit-exact masks: powers and window sums are exact
+ * integers, and every threshold is the same binary64 formula, compared as an
+ * integer table floor((I - n_flagged) * threshold_I).
+ *
+ * Conventions
+ *  - Every call returns an int status (LOF_OK or a negative LOF_ERR_*) and
+ *    never aborts; lof_last_error() gives a message for the last failure.
+ *  - Calls are asynchronous on the caller's CUDA stream (a cudaStream_t passed
+ *    as void*, NULL = legacy default stream).  Device-side failures (a bounded
+ *    wait that timed out, an internal limit) set an error word in the context;
+ *    the next call, or lof_status(), returns them.
+ *  - The caller owns every data buffer (device memory, e.g. from PyTorch);
+ *    the context owns the history rings and its scratch memory.
+ *  - One context must not be used from two host threads at once, nor have two
+ *    lof_flag_block calls in flight on different streams at the same time
+ *    (they share scratch); calls on one stream are ordered.
+ */
+#ifndef LOF_H
+#define LOF_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct lof_ctx lof_ctx;
+
+enum {
+  LOF_OK = 0,
+  LOF_ERR_INVALID = -1,     /* bad argument, pointer, alignment or shape */
+  LOF_ERR_NOMEM = -2,       /* device or host allocation failed */
+  LOF_ERR_CUDA = -3,        /* a CUDA runtime call failed */
+  LOF_ERR_TIMEOUT = -4,     /* a bounded device-side wait gave up */
+  LOF_ERR_STATE = -5,       /* call out of order (e.g. history not sized) */
+  LOF_ERR_UNSUPPORTED = -6  /* valid request this build does not implement */
+};
+
+/* Sample types.  CI8 / CI16: complex voltages, interleaved (re, im) int8 or
+ * int16 pairs, one element = one complex sample.  F32: Stokes I power. */
+enum { LOF_CI8 = 1, LOF_CI16 = 2, LOF_F32 = 3 };
+
+enum { LOF_SIGMA_MAD = 0, LOF_SIGMA_STD = 1 };
+
+typedef struct {
+  double p;                /* Section 2.1, default 1.5 */
+  double sensitivity;      /* Section 2.1, default 1.0 */
+  double start_threshold;  /* Section 2.1, default 6 ("6 sigma" at I = 1) */
+  int32_t max_window;      /* largest SumThreshold window, power of two <= 64; default 64 */
+  int32_t history_len;     /* history ring capacity per channel, 1..1024; default 60 */
+  int32_t history_min;     /* stored means needed before the history test; default 8 */
+  double history_k;        /* history threshold = mean + k * stddev; default 6 */
+  int32_t sigma_estimator; /* LOF_SIGMA_MAD (default) or LOF_SIGMA_STD */
+  int32_t enable_freq;     /* frequency pass on (1) / off (0) */
+  int32_t enable_time;     /* time pass on / off */
+  int32_t enable_history;  /* history flagger on / off */
+} lof_params;
+
+/* Per-unit results, written by lof_flag_block when lof_unit.stats != NULL
+ * (device memory).  Medians and sigmas are the values the thresholds used. */
+typedef struct {
+  double median_f, sigma_f; /* spectrum statistics (a3) */
+  double median_t, sigma_t; /* pooled statistics of the time pass (a5) */
+  int64_t n_chan_freq;      /* channels flagged by the frequency pass */
+  int64_t n_flag_time;      /* samples flagged by the time pass */
+  int64_t n_chan_hist;      /* channels flagged by the history flagger */
+  int64_t n_flag_total;     /* ones in the mask */
+} lof_unit_stats;
+
+/* One unit.  All pointers are device pointers owned by the caller.
+ *  in    : n_chan rows of n_time samples; row c starts at in + c*in_row_stride
+ *          elements.  Must be aligned to the element size.
+ *  out   : same layout (out_row_stride); receives in with flagged samples set
+ *          to zero.  NULL = no data output.  out == in (same strides) flags in
+ *          place: only flagged samples are written.
+ *  mask  : uint8 0/1 per sample, row c at mask + c*mask_row_stride.  NULL = none.
+ *  history_slot: first of n_chan consecutive history slots of the context, or
+ *          -1 for no history (the history flagger is then skipped for the unit).
+ *  stats : optional device lof_unit_stats*, or NULL.
+ * Limits: 1 <= n_chan <= 4096, 1 <= n_time, and one row (n_time samples) must
+ * fit the kernel's shared-memory tile (n_time <= 12288 for CI16/F32, <= 24576
+ * for CI8); see lof_max_time(). */
+typedef struct {
+  const void *in;
+  void *out;
+  uint8_t *mask;
+  int32_t n_chan, n_time;
+  int64_t in_row_stride, out_row_stride, mask_row_stride;
+  int64_t history_slot;
+  lof_unit_stats *stats;
+} lof_unit;
+
+/* Fill *p with the defaults above. */
+void lof_default_params(lof_params *p);
+
+/* Create a context on CUDA device cuda_device with n_history_slots history
+ * channels (each a ring of history_len binary64 means, Section 4.1, sized as
+ * in the paper's storage estimate: slots x history_len x 8 bytes).  Allocates
+ * device memory; runs no kernel except memsets.  *out receives the context. */
+int lof_create(const lof_params *params, int cuda_device, int64_t n_history_slots,
+               lof_ctx **out);
+
+/* Flag one block of n_units units of sample type dtype (steps a1-a8 above) in
+ * ONE persistent kernel launch on cuda_stream.  units is a host array, read
+ * during the call.  History rings are read, not modified: the value each
+ * channel would add to its ring is staged and committed by
+ * lof_history_update (the paper processes seconds out of order, Section 4.1,
+ * so the commit is a separate step).  block_seq is an opaque sequence number
+ * recorded with the staged values.  Returns LOF_ERR_INVALID for bad
+ * descriptors (nothing launched), or a pending device error. */
+int lof_flag_block(lof_ctx *ctx, int dtype, const lof_unit *units, int n_units,
+                   uint64_t block_seq, void *cuda_stream);
+
+/* Same operation with HOST buffers: in/out/mask/stats of every unit are host
+ * pointers (pinned memory gives asynchronous copies).  Inputs are copied to
+ * context-owned device staging memory, flagged, and out/mask/stats copied
+ * back, all on cuda_stream; the call returns after enqueueing (synchronise the
+ * stream before reading the results).  Host buffers must stay valid until
+ * then. */
+int lof_flag_block_host(lof_ctx *ctx, int dtype, const lof_unit *units, int n_units,
+                        uint64_t block_seq, void *cuda_stream);
+
+/* Section 4.1 commit: for every channel of the given units (history_slot >= 0)
+ * append the value staged by the last lof_flag_block to its ring, dropping the
+ * oldest once history_len means are held, and refresh the cached
+ * mean + k*stddev threshold.  Channels with nothing staged are unchanged. */
+int lof_history_update(lof_ctx *ctx, const lof_unit *units, int n_units, void *cuda_stream);
+
+/* Copy n slots starting at slot0 of the history to / from host memory:
+ * values[n][history_len] oldest -> newest (unused tail zero) and counts[n].
+ * Synchronous (waits for the context's work).  For checkpointing and tests. */
+int lof_history_export(lof_ctx *ctx, int64_t slot0, int64_t n, double *values, int32_t *counts);
+int lof_history_import(lof_ctx *ctx, int64_t slot0, int64_t n, const double *values,
+                       const int32_t *counts);
+
+/* Wait for cuda_stream and return the first device-side error recorded by the
+ * context's kernels (LOF_ERR_TIMEOUT, ...) or LOF_OK; clears it. */
+int lof_status(lof_ctx *ctx, void *cuda_stream);
+
+/* Largest n_time a unit of dtype may have with the current tuning. */
+int lof_max_time(const lof_ctx *ctx, int dtype);
+
+/* Launch-shape knobs (an autotuner sweeps them; results do not depend on
+ * them).  0 keeps the current value. */
+typedef struct {
+  int32_t threads;         /* threads per CTA: 128, 256, 512 */
+  int32_t ctas_per_sm;     /* resident CTAs per SM: 1 or 2 */
+  int32_t tile_bytes;      /* shared-memory bytes for a tile of rows */
+  int32_t fine_bins;       /* counters per exact-selection refinement round */
+} lof_tuning;
+int lof_set_tuning(lof_ctx *ctx, const lof_tuning *t);
+int lof_get_tuning(const lof_ctx *ctx, lof_tuning *t);
+
+/* Message for the last failed call on ctx (or of lof_create when ctx is NULL). */
+const char *lof_last_error(const lof_ctx *ctx);
+
+int lof_destroy(lof_ctx *ctx);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

@@ -1,0 +1,806 @@
+// lof_api.cu -- host side of the C ABI declared in include/lof.h.
+//
+// A context owns the history rings (Section 4.1: one ring of binary64 means
+// per channel slot) and the scratch of the persistent kernel.  lof_flag_block
+// validates the unit descriptors, splits every unit into items (runs of whole
+// rows that fit one CTA's shared-memory tile), uploads the descriptor tables
+// and launches ONE cooperative kernel for the whole block.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "lof.h"
+#include "lof_internal.h"
+
+using lofk::DevUnit;
+using lofk::Item;
+using lofk::KParams;
+using lofk::Slot;
+using lofk::UnitCtl;
+
+namespace {
+
+thread_local std::string g_create_error;
+
+constexpr int kStageRing = 4;
+
+int esize_of(int dtype) {
+  switch (dtype) {
+    case LOF_CI8: return 2;
+    case LOF_CI16: return 4;
+    case LOF_F32: return 4;
+    default: return 0;
+  }
+}
+int vec_of(int dtype) { return 16 / esize_of(dtype); }
+int seg_of(int dtype) { return 64 * vec_of(dtype); }
+int64_t round_up64(int64_t x, int64_t m) { return (x + m - 1) / m * m; }
+
+}  // namespace
+
+struct lof_ctx {
+  int device = 0;
+  lof_params params{};
+  int n_sm = 0;
+  int smem_per_sm = 0, smem_optin = 0;
+  lof_tuning tuning{256, 2, 0, 512};
+  // history
+  int64_t n_slots = 0;
+  int H = 0;
+  lofk::HistoryDev hist{};
+  // scratch
+  DevUnit* d_units = nullptr;
+  size_t cap_units = 0;
+  Item* d_items = nullptr;
+  size_t cap_items = 0;
+  UnitCtl* d_ctl = nullptr;
+  size_t cap_ctl = 0;
+  unsigned long long* d_chanS = nullptr;
+  uint8_t* d_chanFc = nullptr;
+  size_t cap_chan = 0, cap_chanfc = 0;
+  Slot* d_slots = nullptr;
+  size_t cap_slots = 0;
+  int* d_ctrl = nullptr;  // [0] queue, [1] error, [2..3] error detail
+  int* h_err = nullptr;   // pinned copy of d_ctrl[1..3]
+  cudaEvent_t ev_err = nullptr;
+  bool err_copy_pending = false;
+  // descriptor staging (pinned, ring of buffers guarded by events)
+  void* h_stage[kStageRing] = {};
+  size_t cap_stage[kStageRing] = {};
+  cudaEvent_t ev_stage[kStageRing] = {};
+  int stage_next = 0;
+  // device staging for lof_flag_block_host
+  uint8_t* d_io = nullptr;
+  size_t cap_io = 0;
+  std::string last_error;
+};
+
+namespace {
+
+int fail(lof_ctx* c, int code, const char* fmt, ...) {
+  char buf[512];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof buf, fmt, ap);
+  va_end(ap);
+  if (c) c->last_error = buf;
+  else g_create_error = buf;
+  return code;
+}
+
+int cuda_fail(lof_ctx* c, cudaError_t e, const char* what) {
+  return fail(c, LOF_ERR_CUDA, "%s: %s", what, cudaGetErrorString(e));
+}
+
+struct DeviceGuard {
+  int prev = -1;
+  explicit DeviceGuard(int dev) {
+    if (cudaGetDevice(&prev) == cudaSuccess && prev != dev) cudaSetDevice(dev);
+    else prev = -1;
+  }
+  ~DeviceGuard() {
+    if (prev >= 0) cudaSetDevice(prev);
+  }
+};
+
+template <class T>
+int grow(lof_ctx* c, T** p, size_t* cap, size_t need, const char* what) {
+  if (need <= *cap && *p) return LOF_OK;
+  size_t n = std::max<size_t>(need, *cap ? *cap * 2 : 64);
+  if (*p) {
+    cudaError_t e = cudaDeviceSynchronize();  // scratch may still be in use
+    if (e != cudaSuccess) return cuda_fail(c, e, "cudaDeviceSynchronize");
+    cudaFree(*p);
+    *p = nullptr;
+    *cap = 0;
+  }
+  cudaError_t e = cudaMalloc(reinterpret_cast<void**>(p), n * sizeof(T));
+  if (e != cudaSuccess) return fail(c, LOF_ERR_NOMEM, "cudaMalloc(%s, %zu): %s", what, n * sizeof(T), cudaGetErrorString(e));
+  *cap = n;
+  return LOF_OK;
+}
+
+int pending_device_error(lof_ctx* c) {
+  if (!c->err_copy_pending) return LOF_OK;
+  if (cudaEventQuery(c->ev_err) != cudaSuccess) return LOF_OK;  // not known yet
+  c->err_copy_pending = false;
+  const int code = c->h_err[0];
+  if (code == lofk::kErrNone) return LOF_OK;
+  const int info0 = c->h_err[1], info1 = c->h_err[2];
+  c->h_err[0] = 0;
+  cudaMemset(c->d_ctrl + 1, 0, 3 * sizeof(int));
+  if (code == lofk::kErrTimeout)
+    return fail(c, LOF_ERR_TIMEOUT, "device wait timed out (round %d, block %d)", info0, info1);
+  return fail(c, LOF_ERR_STATE, "device error %d (detail %d, block %d)", code, info0, info1);
+}
+
+// Shared-memory plan for one launch.
+struct Plan {
+  int threads, ctas, grid;
+  int tile, pfx_words, mbits_words, fbits_words, smem;
+};
+
+int static_smem_bytes(int dtype, int threads) {
+  // conservative bound of the kernel's static shared memory (Fixed<NT> + locals)
+  (void)dtype;
+  return 7 * 1024 + (threads / 32) * 32;
+}
+
+int pfx_row_words(int dtype, int T) {
+  const int64_t PPw = round_up64(T, seg_of(dtype)) + lofk::kPadWords;
+  return static_cast<int>(PPw / 32 * 36);
+}
+
+int dpitch_of(int dtype, int T) {
+  return static_cast<int>(round_up64(static_cast<int64_t>(T) * esize_of(dtype), 128));
+}
+
+// Budget of dynamic shared memory per CTA.
+int dyn_budget(const lof_ctx* c, int dtype, int threads, int ctas) {
+  const int per = c->smem_per_sm / std::max(1, ctas) - 1024;
+  return std::min(per, c->smem_optin) - static_smem_bytes(dtype, threads);
+}
+
+// rows of one item for a unit with n_time T, given a tile size
+int rows_per_item(int dtype, int T, int tile) {
+  const int dp = dpitch_of(dtype, T);
+  int R = tile / dp;
+  R = std::min(R, lofk::kMaxRowsPerItem);
+  const int nseg = (T + seg_of(dtype) - 1) / seg_of(dtype);
+  R = std::min(R, 256 / std::max(1, nseg));
+  return R;
+}
+
+}  // namespace
+
+extern "C" void lof_default_params(lof_params* p) {
+  if (!p) return;
+  p->p = 1.5;
+  p->sensitivity = 1.0;
+  p->start_threshold = 6.0;
+  p->max_window = 64;
+  p->history_len = 60;
+  p->history_min = 8;
+  p->history_k = 6.0;
+  p->sigma_estimator = LOF_SIGMA_MAD;
+  p->enable_freq = 1;
+  p->enable_time = 1;
+  p->enable_history = 1;
+}
+
+extern "C" const char* lof_last_error(const lof_ctx* c) {
+  return c ? c->last_error.c_str() : g_create_error.c_str();
+}
+
+static int validate_params(const lof_params* p, std::string* why) {
+  char b[256];
+  if (!(p->p > 0.0) || !(p->sensitivity > 0.0) || !(p->start_threshold > 0.0)) {
+    *why = "p, sensitivity and start_threshold must be positive";
+    return 0;
+  }
+  if (p->max_window < 1 || p->max_window > 64 || (p->max_window & (p->max_window - 1))) {
+    snprintf(b, sizeof b, "max_window %d must be a power of two in [1, 64]", p->max_window);
+    *why = b;
+    return 0;
+  }
+  if (p->history_len < 1 || p->history_len > 1024 || p->history_min < 0 || !(p->history_k >= 0.0)) {
+    *why = "history_len in [1, 1024], history_min >= 0, history_k >= 0 required";
+    return 0;
+  }
+  if (p->sigma_estimator != LOF_SIGMA_MAD && p->sigma_estimator != LOF_SIGMA_STD) {
+    *why = "unknown sigma_estimator";
+    return 0;
+  }
+  return 1;
+}
+
+extern "C" int lof_create(const lof_params* params, int cuda_device, int64_t n_history_slots,
+                          lof_ctx** out) {
+  if (!out) return fail(nullptr, LOF_ERR_INVALID, "lof_create: out is NULL");
+  *out = nullptr;
+  lof_params p;
+  if (params) p = *params;
+  else lof_default_params(&p);
+  std::string why;
+  if (!validate_params(&p, &why)) return fail(nullptr, LOF_ERR_INVALID, "lof_create: %s", why.c_str());
+  if (n_history_slots < 0) return fail(nullptr, LOF_ERR_INVALID, "lof_create: negative history slots");
+  int ndev = 0;
+  cudaError_t e = cudaGetDeviceCount(&ndev);
+  if (e != cudaSuccess || ndev == 0)
+    return fail(nullptr, LOF_ERR_CUDA, "lof_create: no CUDA device (%s)", cudaGetErrorString(e));
+  if (cuda_device < 0 || cuda_device >= ndev)
+    return fail(nullptr, LOF_ERR_INVALID, "lof_create: device %d of %d", cuda_device, ndev);
+  DeviceGuard g(cuda_device);
+  e = cudaSetDevice(cuda_device);
+  if (e != cudaSuccess) return fail(nullptr, LOF_ERR_CUDA, "cudaSetDevice: %s", cudaGetErrorString(e));
+  lof_ctx* c = new lof_ctx();
+  c->device = cuda_device;
+  c->params = p;
+  cudaDeviceGetAttribute(&c->n_sm, cudaDevAttrMultiProcessorCount, cuda_device);
+  cudaDeviceGetAttribute(&c->smem_per_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, cuda_device);
+  cudaDeviceGetAttribute(&c->smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, cuda_device);
+  int rc = LOF_OK;
+  auto ck = [&](cudaError_t err, const char* what) {
+    if (err != cudaSuccess && rc == LOF_OK) rc = fail(nullptr, LOF_ERR_NOMEM, "%s: %s", what, cudaGetErrorString(err));
+  };
+  c->n_slots = n_history_slots;
+  c->H = p.history_len;
+  const size_t ns = static_cast<size_t>(std::max<int64_t>(1, n_history_slots));
+  ck(cudaMalloc(&c->hist.vals, ns * c->H * sizeof(double)), "history ring");
+  ck(cudaMalloc(&c->hist.count, ns * sizeof(int32_t)), "history count");
+  ck(cudaMalloc(&c->hist.head, ns * sizeof(int32_t)), "history head");
+  ck(cudaMalloc(&c->hist.thr, ns * sizeof(double)), "history threshold");
+  ck(cudaMalloc(&c->hist.pend, ns * sizeof(double)), "history pending");
+  ck(cudaMalloc(&c->hist.pend_flag, ns), "history pending flag");
+  ck(cudaMalloc(&c->hist.pend_seq, ns * sizeof(uint64_t)), "history pending seq");
+  ck(cudaMalloc(&c->d_ctrl, 4 * sizeof(int)), "control words");
+  ck(cudaHostAlloc(&c->h_err, 4 * sizeof(int), cudaHostAllocDefault), "pinned error word");
+  ck(cudaEventCreateWithFlags(&c->ev_err, cudaEventDisableTiming), "event");
+  for (int i = 0; i < kStageRing; ++i)
+    ck(cudaEventCreateWithFlags(&c->ev_stage[i], cudaEventDisableTiming), "event");
+  if (rc == LOF_OK) {
+    ck(cudaMemset(c->hist.vals, 0, ns * c->H * sizeof(double)), "memset");
+    ck(cudaMemset(c->hist.count, 0, ns * sizeof(int32_t)), "memset");
+    ck(cudaMemset(c->hist.head, 0, ns * sizeof(int32_t)), "memset");
+    ck(cudaMemset(c->hist.thr, 0, ns * sizeof(double)), "memset");
+    ck(cudaMemset(c->hist.pend_flag, 0, ns), "memset");
+    ck(cudaMemset(c->d_ctrl, 0, 4 * sizeof(int)), "memset");
+    ck(cudaDeviceSynchronize(), "cudaDeviceSynchronize");
+    memset(c->h_err, 0, 4 * sizeof(int));
+  }
+  c->hist.n_slots = n_history_slots;
+  c->hist.H = c->H;
+  if (rc != LOF_OK) {
+    lof_destroy(c);
+    return rc;
+  }
+  *out = c;
+  return LOF_OK;
+}
+
+extern "C" int lof_destroy(lof_ctx* c) {
+  if (!c) return LOF_OK;
+  DeviceGuard g(c->device);
+  cudaDeviceSynchronize();
+  cudaFree(c->hist.vals);
+  cudaFree(c->hist.count);
+  cudaFree(c->hist.head);
+  cudaFree(c->hist.thr);
+  cudaFree(c->hist.pend);
+  cudaFree(c->hist.pend_flag);
+  cudaFree(c->hist.pend_seq);
+  cudaFree(c->d_units);
+  cudaFree(c->d_items);
+  cudaFree(c->d_ctl);
+  cudaFree(c->d_chanS);
+  cudaFree(c->d_chanFc);
+  cudaFree(c->d_slots);
+  cudaFree(c->d_ctrl);
+  cudaFree(c->d_io);
+  if (c->h_err) cudaFreeHost(c->h_err);
+  for (int i = 0; i < kStageRing; ++i) {
+    if (c->h_stage[i]) cudaFreeHost(c->h_stage[i]);
+    if (c->ev_stage[i]) cudaEventDestroy(c->ev_stage[i]);
+  }
+  if (c->ev_err) cudaEventDestroy(c->ev_err);
+  delete c;
+  return LOF_OK;
+}
+
+extern "C" int lof_set_tuning(lof_ctx* c, const lof_tuning* t) {
+  if (!c || !t) return fail(c, LOF_ERR_INVALID, "lof_set_tuning: NULL argument");
+  lof_tuning n = c->tuning;
+  if (t->threads) {
+    if (t->threads != 256 && t->threads != 512)
+      return fail(c, LOF_ERR_INVALID, "threads must be 256 or 512");
+    n.threads = t->threads;
+  }
+  if (t->ctas_per_sm) {
+    if (t->ctas_per_sm < 1 || t->ctas_per_sm > 4) return fail(c, LOF_ERR_INVALID, "ctas_per_sm in [1, 4]");
+    n.ctas_per_sm = t->ctas_per_sm;
+  }
+  if (t->tile_bytes) {
+    if (t->tile_bytes < 4096 || (t->tile_bytes % 128)) return fail(c, LOF_ERR_INVALID, "tile_bytes >= 4096, multiple of 128");
+    n.tile_bytes = t->tile_bytes;
+  }
+  if (t->fine_bins) {
+    if (t->fine_bins < 64 || t->fine_bins > lofk::kMaxFine)
+      return fail(c, LOF_ERR_INVALID, "fine_bins in [64, %d]", lofk::kMaxFine);
+    n.fine_bins = t->fine_bins;
+  }
+  c->tuning = n;
+  return LOF_OK;
+}
+
+extern "C" int lof_get_tuning(const lof_ctx* c, lof_tuning* t) {
+  if (!c || !t) return LOF_ERR_INVALID;
+  *t = c->tuning;
+  return LOF_OK;
+}
+
+namespace {
+
+// Shared-memory plan: tile of rows, prefix/workspace, flag words.
+bool make_plan(const lof_ctx* c, int dtype, const int* Ts, int nT, Plan* pl, std::string* why) {
+  pl->threads = c->tuning.threads;
+  pl->ctas = c->tuning.ctas_per_sm;
+  const int budget = dyn_budget(c, dtype, pl->threads, pl->ctas);
+  int pfx = lofk::kWorkspaceBytes / 4;
+  int maxT = 0;
+  for (int i = 0; i < nT; ++i) {
+    pfx = std::max(pfx, pfx_row_words(dtype, Ts[i]));
+    maxT = std::max(maxT, Ts[i]);
+  }
+  // flag words: at most (tile / pitch) rows of (nch + 4) words; bound generously
+  int tile = c->tuning.tile_bytes ? c->tuning.tile_bytes : (budget - 4 * pfx) / 128 * 128;
+  for (int iter = 0; iter < 8; ++iter) {
+    int mb = 0, fb = 0;
+    for (int i = 0; i < nT; ++i) {
+      const int T = Ts[i];
+      const int R = rows_per_item(dtype, T, tile);
+      if (R < 1) {
+        char b[160];
+        snprintf(b, sizeof b, "n_time %d does not fit the shared-memory tile (%d bytes)", T, tile);
+        *why = b;
+        return false;
+      }
+      const int words = (T + 31) / 32 + 4;
+      const int nb = std::max(1, std::min(R, pfx / pfx_row_words(dtype, T)));
+      mb = std::max(mb, R * words);
+      fb = std::max(fb, nb * words);
+    }
+    const int total = tile + 4 * (pfx + mb + fb);
+    if (total <= budget || c->tuning.tile_bytes) {
+      pl->tile = tile;
+      pl->pfx_words = pfx;
+      pl->mbits_words = mb;
+      pl->fbits_words = fb;
+      pl->smem = total;
+      if (total > budget) {
+        *why = "tuned tile_bytes exceeds the shared-memory budget";
+        return false;
+      }
+      return true;
+    }
+    tile -= (total - budget + 127) / 128 * 128;
+    tile = tile / 128 * 128;
+    if (tile < 1024) break;
+  }
+  *why = "no shared-memory plan fits";
+  return false;
+}
+
+// Builds and launches one block for units already holding DEVICE pointers.
+int flag_block_device(lof_ctx* c, int dtype, const lof_unit* units, int n_units, uint64_t seq,
+                      void* stream) {
+  const int es = esize_of(dtype);
+  std::vector<int> Ts(n_units);
+  for (int i = 0; i < n_units; ++i) Ts[i] = units[i].n_time;
+  Plan pl;
+  std::string why;
+  if (!make_plan(c, dtype, Ts.data(), n_units, &pl, &why))
+    return fail(c, LOF_ERR_INVALID, "lof_flag_block: %s", why.c_str());
+  int occ = 0;
+  int krc = lofk_max_blocks_per_sm(dtype, pl.threads, pl.smem, &occ);
+  if (krc != 0 || occ < 1)
+    return fail(c, LOF_ERR_CUDA, "kernel does not fit (%d threads, %d B shared): rc %d occ %d",
+                pl.threads, pl.smem, krc, occ);
+  const int ctas = std::min(pl.ctas, occ);
+  // descriptors
+  std::vector<DevUnit> du(n_units);
+  std::vector<Item> items;
+  int64_t chan = 0;
+  int maxG = 0;
+  for (int i = 0; i < n_units; ++i) {
+    const lof_unit& u = units[i];
+    DevUnit& d = du[i];
+    d.in = u.in;
+    d.out = u.out;
+    d.mask = u.mask;
+    d.stats = u.stats;
+    d.in_stride = u.in_row_stride;
+    d.out_stride = u.out ? u.out_row_stride : 0;
+    d.mask_stride = u.mask ? u.mask_row_stride : 0;
+    d.hist_slot = u.history_slot;
+    d.C = u.n_chan;
+    d.T = u.n_time;
+    d.chan_off = static_cast<int32_t>(chan);
+    chan += u.n_chan;
+    int flags = 0;
+    const int64_t rowb = static_cast<int64_t>(u.n_time) * es;
+    if ((reinterpret_cast<uintptr_t>(u.in) % 16) == 0 && ((u.in_row_stride * es) % 16) == 0 &&
+        (rowb % 16) == 0)
+      flags |= lofk::kUnitInBulk;
+    if (u.out && u.out == u.in) flags |= lofk::kUnitInPlace;
+    else if (u.out && (reinterpret_cast<uintptr_t>(u.out) % 16) == 0 &&
+             ((u.out_row_stride * es) % 16) == 0 && (rowb % 16) == 0)
+      flags |= lofk::kUnitOutBulk;
+    if (u.mask && (reinterpret_cast<uintptr_t>(u.mask) % 16) == 0 && (u.mask_row_stride % 16) == 0)
+      flags |= lofk::kUnitMaskVec;
+    d.flags = flags;
+    const int Rmax = rows_per_item(dtype, u.n_time, pl.tile);
+    const int nit = (u.n_chan + Rmax - 1) / Rmax;
+    const int R = (u.n_chan + nit - 1) / nit;
+    d.first_item = static_cast<int32_t>(items.size());
+    d.n_items = nit;
+    maxG = std::max(maxG, nit);
+    for (int r0 = 0; r0 < u.n_chan; r0 += R)
+      items.push_back(Item{i, r0, std::min(R, u.n_chan - r0), 0});
+  }
+  const int n_items = static_cast<int>(items.size());
+  int grid = std::min(c->n_sm * ctas, n_items);
+  if (maxG > c->n_sm * ctas)
+    return fail(c, LOF_ERR_UNSUPPORTED,
+                "a unit needs %d co-resident CTAs, the device holds %d; use fewer channels per unit",
+                maxG, c->n_sm * ctas);
+  // scratch
+  int rc;
+  if ((rc = grow(c, &c->d_units, &c->cap_units, n_units, "units"))) return rc;
+  if ((rc = grow(c, &c->d_items, &c->cap_items, n_items, "items"))) return rc;
+  if ((rc = grow(c, &c->d_ctl, &c->cap_ctl, n_units, "unit control"))) return rc;
+  if ((rc = grow(c, &c->d_chanS, &c->cap_chan, static_cast<size_t>(chan), "spectrum"))) return rc;
+  if ((rc = grow(c, &c->d_chanFc, &c->cap_chanfc, static_cast<size_t>(chan), "channel flags"))) return rc;
+  if ((rc = grow(c, &c->d_slots, &c->cap_slots, static_cast<size_t>(grid), "slots"))) return rc;
+  // stage descriptors (pinned ring)
+  const size_t bytes_units = n_units * sizeof(DevUnit);
+  const size_t bytes_items = n_items * sizeof(Item);
+  const size_t bytes = bytes_units + bytes_items;
+  const int si = c->stage_next;
+  c->stage_next = (si + 1) % kStageRing;
+  cudaError_t e = cudaEventSynchronize(c->ev_stage[si]);
+  if (e != cudaSuccess) return cuda_fail(c, e, "cudaEventSynchronize");
+  if (c->cap_stage[si] < bytes) {
+    if (c->h_stage[si]) cudaFreeHost(c->h_stage[si]);
+    c->h_stage[si] = nullptr;
+    size_t n = std::max(bytes, 2 * c->cap_stage[si]);
+    e = cudaHostAlloc(&c->h_stage[si], n, cudaHostAllocDefault);
+    if (e != cudaSuccess) return fail(c, LOF_ERR_NOMEM, "pinned staging: %s", cudaGetErrorString(e));
+    c->cap_stage[si] = n;
+  }
+  uint8_t* hs = static_cast<uint8_t*>(c->h_stage[si]);
+  memcpy(hs, du.data(), bytes_units);
+  memcpy(hs + bytes_units, items.data(), bytes_items);
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  if ((e = cudaMemcpyAsync(c->d_units, hs, bytes_units, cudaMemcpyHostToDevice, st)) != cudaSuccess)
+    return cuda_fail(c, e, "descriptor upload");
+  if ((e = cudaMemcpyAsync(c->d_items, hs + bytes_units, bytes_items, cudaMemcpyHostToDevice, st)) !=
+      cudaSuccess)
+    return cuda_fail(c, e, "descriptor upload");
+  cudaEventRecord(c->ev_stage[si], st);
+  if ((e = cudaMemsetAsync(c->d_ctl, 0, n_units * sizeof(UnitCtl), st)) != cudaSuccess)
+    return cuda_fail(c, e, "memset");
+  if ((e = cudaMemsetAsync(c->d_ctrl, 0, sizeof(int), st)) != cudaSuccess) return cuda_fail(c, e, "memset");
+  KParams kp{};
+  kp.units = c->d_units;
+  kp.items = c->d_items;
+  kp.ctl = c->d_ctl;
+  kp.chan_S = c->d_chanS;
+  kp.chan_Fc = c->d_chanFc;
+  kp.slots = c->d_slots;
+  kp.queue = c->d_ctrl;
+  kp.err = c->d_ctrl + 1;
+  kp.err_info = c->d_ctrl + 2;
+  kp.hist = c->hist;
+  kp.n_units = n_units;
+  kp.n_items = n_items;
+  kp.tile_rows_bytes = pl.tile;
+  kp.pfx_words = pl.pfx_words;
+  kp.mbits_words = pl.mbits_words;
+  kp.fbits_words = pl.fbits_words;
+  kp.fine_bins = c->tuning.fine_bins;
+  const lof_params& P = c->params;
+  for (int k = 0; k <= lofk::kMaxLogWindow; ++k) {
+    // Section 2.1: factor_I = startThreshold * p^(log2 I) / I (p^k by k products)
+    volatile double pk = 1.0;
+    for (int i = 0; i < k; ++i) pk = pk * P.p;
+    volatile double fk = P.start_threshold * pk;
+    kp.factor[k] = fk / static_cast<double>(1 << k);
+  }
+  kp.sensitivity = P.sensitivity;
+  kp.history_k = P.history_k;
+  int mlw = 0;
+  while ((2 << mlw) <= P.max_window) ++mlw;
+  kp.max_log_window = mlw;
+  kp.history_min = P.history_min;
+  kp.sigma_std = P.sigma_estimator == LOF_SIGMA_STD;
+  kp.enable_freq = P.enable_freq;
+  kp.enable_time = P.enable_time;
+  kp.enable_history = P.enable_history;
+  kp.block_seq = seq;
+  kp.spin_limit = 2000000000ll;  // 2 s
+  krc = lofk_launch_block(dtype, &kp, grid, pl.threads, pl.smem, stream, 1);
+  if (krc != 0)
+    return fail(c, LOF_ERR_CUDA, "kernel launch failed: %s (grid %d, %d threads, %d B)",
+                cudaGetErrorString(static_cast<cudaError_t>(krc)), grid, pl.threads, pl.smem);
+  if ((e = cudaMemcpyAsync(c->h_err, c->d_ctrl + 1, 3 * sizeof(int), cudaMemcpyDeviceToHost, st)) !=
+      cudaSuccess)
+    return cuda_fail(c, e, "error word copy");
+  cudaEventRecord(c->ev_err, st);
+  c->err_copy_pending = true;
+  return LOF_OK;
+}
+
+int validate_units(lof_ctx* c, int dtype, const lof_unit* units, int n_units) {
+  if (esize_of(dtype) == 0) return fail(c, LOF_ERR_INVALID, "unknown dtype %d", dtype);
+  if (dtype == LOF_F32) return fail(c, LOF_ERR_UNSUPPORTED, "LOF_F32 is not implemented in this build");
+  if (n_units < 0 || (n_units > 0 && !units)) return fail(c, LOF_ERR_INVALID, "bad unit array");
+  const int es = esize_of(dtype);
+  for (int i = 0; i < n_units; ++i) {
+    const lof_unit& u = units[i];
+    if (!u.in) return fail(c, LOF_ERR_INVALID, "unit %d: in is NULL", i);
+    if (u.n_chan < 1 || u.n_chan > lofk::kMaxChan)
+      return fail(c, LOF_ERR_INVALID, "unit %d: n_chan %d outside [1, %d]", i, u.n_chan, lofk::kMaxChan);
+    if (u.n_time < 1) return fail(c, LOF_ERR_INVALID, "unit %d: n_time %d < 1", i, u.n_time);
+    if (u.in_row_stride < u.n_time && u.n_chan > 1)
+      return fail(c, LOF_ERR_INVALID, "unit %d: in_row_stride %lld < n_time", i, (long long)u.in_row_stride);
+    if (u.out && u.out_row_stride < u.n_time && u.n_chan > 1)
+      return fail(c, LOF_ERR_INVALID, "unit %d: out_row_stride < n_time", i);
+    if (u.mask && u.mask_row_stride < u.n_time && u.n_chan > 1)
+      return fail(c, LOF_ERR_INVALID, "unit %d: mask_row_stride < n_time", i);
+    if (u.out == u.in && u.out_row_stride != u.in_row_stride)
+      return fail(c, LOF_ERR_INVALID, "unit %d: in-place output needs equal strides", i);
+    if ((reinterpret_cast<uintptr_t>(u.in) % es) || (u.out && reinterpret_cast<uintptr_t>(u.out) % es))
+      return fail(c, LOF_ERR_INVALID, "unit %d: data pointers must be aligned to %d bytes", i, es);
+    if (u.history_slot < -1 || (u.history_slot >= 0 && u.history_slot + u.n_chan > c->n_slots))
+      return fail(c, LOF_ERR_INVALID, "unit %d: history slots [%lld, +%d) outside [0, %lld)", i,
+                  (long long)u.history_slot, u.n_chan, (long long)c->n_slots);
+  }
+  return LOF_OK;
+}
+
+}  // namespace
+
+extern "C" int lof_flag_block(lof_ctx* c, int dtype, const lof_unit* units, int n_units,
+                              uint64_t block_seq, void* cuda_stream) {
+  if (!c) return fail(nullptr, LOF_ERR_INVALID, "lof_flag_block: ctx is NULL");
+  DeviceGuard g(c->device);
+  int rc = pending_device_error(c);
+  if (rc) return rc;
+  if ((rc = validate_units(c, dtype, units, n_units))) return rc;
+  if (n_units == 0) return LOF_OK;
+  return flag_block_device(c, dtype, units, n_units, block_seq, cuda_stream);
+}
+
+extern "C" int lof_flag_block_host(lof_ctx* c, int dtype, const lof_unit* units, int n_units,
+                                   uint64_t block_seq, void* cuda_stream) {
+  if (!c) return fail(nullptr, LOF_ERR_INVALID, "lof_flag_block_host: ctx is NULL");
+  DeviceGuard g(c->device);
+  int rc = pending_device_error(c);
+  if (rc) return rc;
+  if ((rc = validate_units(c, dtype, units, n_units))) return rc;
+  if (n_units == 0) return LOF_OK;
+  const int es = esize_of(dtype);
+  // device staging: compact [C][T] input, output and mask, plus stats
+  size_t need = 0;
+  std::vector<size_t> off_in(n_units), off_out(n_units), off_mask(n_units), off_st(n_units);
+  for (int i = 0; i < n_units; ++i) {
+    const size_t n = static_cast<size_t>(units[i].n_chan) * units[i].n_time;
+    off_in[i] = need;
+    need += round_up64(n * es, 256);
+    off_out[i] = need;
+    if (units[i].out && units[i].out != units[i].in) need += round_up64(n * es, 256);
+    off_mask[i] = need;
+    if (units[i].mask) need += round_up64(n, 256);
+    off_st[i] = need;
+    if (units[i].stats) need += round_up64(sizeof(lof_unit_stats), 256);
+  }
+  if (need > c->cap_io) {
+    if (c->d_io) {
+      cudaError_t e = cudaDeviceSynchronize();
+      if (e != cudaSuccess) return cuda_fail(c, e, "cudaDeviceSynchronize");
+      cudaFree(c->d_io);
+      c->d_io = nullptr;
+      c->cap_io = 0;
+    }
+    cudaError_t e = cudaMalloc(&c->d_io, need);
+    if (e != cudaSuccess) return fail(c, LOF_ERR_NOMEM, "host-path staging %zu B: %s", need, cudaGetErrorString(e));
+    c->cap_io = need;
+  }
+  cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
+  std::vector<lof_unit> du(units, units + n_units);
+  for (int i = 0; i < n_units; ++i) {
+    const lof_unit& u = units[i];
+    const size_t rowb = static_cast<size_t>(u.n_time) * es;
+    uint8_t* din = c->d_io + off_in[i];
+    cudaError_t e = cudaMemcpy2DAsync(din, rowb, u.in, static_cast<size_t>(u.in_row_stride) * es, rowb,
+                                      u.n_chan, cudaMemcpyHostToDevice, st);
+    if (e != cudaSuccess) return cuda_fail(c, e, "host input copy");
+    du[i].in = din;
+    du[i].in_row_stride = u.n_time;
+    if (u.out) {
+      du[i].out = (u.out == u.in) ? din : c->d_io + off_out[i];
+      du[i].out_row_stride = u.n_time;
+    }
+    if (u.mask) {
+      du[i].mask = c->d_io + off_mask[i];
+      du[i].mask_row_stride = u.n_time;
+    }
+    if (u.stats) du[i].stats = reinterpret_cast<lof_unit_stats*>(c->d_io + off_st[i]);
+  }
+  rc = flag_block_device(c, dtype, du.data(), n_units, block_seq, cuda_stream);
+  if (rc) return rc;
+  for (int i = 0; i < n_units; ++i) {
+    const lof_unit& u = units[i];
+    const size_t rowb = static_cast<size_t>(u.n_time) * es;
+    cudaError_t e = cudaSuccess;
+    if (u.out)
+      e = cudaMemcpy2DAsync(u.out, static_cast<size_t>(u.out_row_stride) * es, du[i].out, rowb, rowb,
+                            u.n_chan, cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess && u.mask)
+      e = cudaMemcpy2DAsync(u.mask, static_cast<size_t>(u.mask_row_stride), du[i].mask, u.n_time,
+                            u.n_time, u.n_chan, cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess && u.stats)
+      e = cudaMemcpyAsync(u.stats, du[i].stats, sizeof(lof_unit_stats), cudaMemcpyDeviceToHost, st);
+    if (e != cudaSuccess) return cuda_fail(c, e, "host output copy");
+  }
+  return LOF_OK;
+}
+
+namespace {
+
+int commit_like(lof_ctx* c, const lof_unit* units, int n_units, void* stream, bool refresh) {
+  std::vector<DevUnit> du;
+  du.reserve(n_units);
+  int64_t chan = 0;
+  for (int i = 0; i < n_units; ++i) {
+    const lof_unit& u = units[i];
+    if (u.history_slot < 0) continue;
+    if (u.n_chan < 1 || u.history_slot + u.n_chan > c->n_slots)
+      return fail(c, LOF_ERR_INVALID, "unit %d: history slots out of range", i);
+    DevUnit d{};
+    d.C = u.n_chan;
+    d.T = u.n_time;
+    d.hist_slot = u.history_slot;
+    d.chan_off = static_cast<int32_t>(chan);
+    chan += u.n_chan;
+    du.push_back(d);
+  }
+  if (du.empty()) return LOF_OK;
+  int rc;
+  if ((rc = grow(c, &c->d_units, &c->cap_units, du.size(), "units"))) return rc;
+  const int si = c->stage_next;
+  c->stage_next = (si + 1) % kStageRing;
+  cudaError_t e = cudaEventSynchronize(c->ev_stage[si]);
+  if (e != cudaSuccess) return cuda_fail(c, e, "cudaEventSynchronize");
+  const size_t bytes = du.size() * sizeof(DevUnit);
+  if (c->cap_stage[si] < bytes) {
+    if (c->h_stage[si]) cudaFreeHost(c->h_stage[si]);
+    c->h_stage[si] = nullptr;
+    e = cudaHostAlloc(&c->h_stage[si], bytes, cudaHostAllocDefault);
+    if (e != cudaSuccess) return fail(c, LOF_ERR_NOMEM, "pinned staging: %s", cudaGetErrorString(e));
+    c->cap_stage[si] = bytes;
+  }
+  memcpy(c->h_stage[si], du.data(), bytes);
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  if ((e = cudaMemcpyAsync(c->d_units, c->h_stage[si], bytes, cudaMemcpyHostToDevice, st)) != cudaSuccess)
+    return cuda_fail(c, e, "descriptor upload");
+  cudaEventRecord(c->ev_stage[si], st);
+  lofk::CommitParams cp{};
+  cp.units = c->d_units;
+  cp.n_units = static_cast<int>(du.size());
+  cp.hist = c->hist;
+  cp.history_k = c->params.history_k;
+  cp.history_min = c->params.history_min;
+  const int krc = refresh ? lofk_launch_refresh(&cp, static_cast<int>(chan), stream)
+                          : lofk_launch_commit(&cp, static_cast<int>(chan), stream);
+  if (krc != 0)
+    return fail(c, LOF_ERR_CUDA, "history kernel: %s", cudaGetErrorString(static_cast<cudaError_t>(krc)));
+  return LOF_OK;
+}
+
+}  // namespace
+
+extern "C" int lof_history_update(lof_ctx* c, const lof_unit* units, int n_units, void* cuda_stream) {
+  if (!c) return fail(nullptr, LOF_ERR_INVALID, "lof_history_update: ctx is NULL");
+  if (n_units < 0 || (n_units > 0 && !units)) return fail(c, LOF_ERR_INVALID, "bad unit array");
+  DeviceGuard g(c->device);
+  int rc = pending_device_error(c);
+  if (rc) return rc;
+  return commit_like(c, units, n_units, cuda_stream, false);
+}
+
+extern "C" int lof_history_export(lof_ctx* c, int64_t slot0, int64_t n, double* values, int32_t* counts) {
+  if (!c || !values || !counts || slot0 < 0 || n < 0 || slot0 + n > c->n_slots)
+    return fail(c, LOF_ERR_INVALID, "lof_history_export: bad arguments");
+  DeviceGuard g(c->device);
+  cudaError_t e = cudaDeviceSynchronize();
+  if (e != cudaSuccess) return cuda_fail(c, e, "cudaDeviceSynchronize");
+  const int H = c->H;
+  std::vector<double> v(static_cast<size_t>(n) * H);
+  std::vector<int32_t> cnt(n), head(n);
+  if (n == 0) return LOF_OK;
+  if ((e = cudaMemcpy(v.data(), c->hist.vals + slot0 * H, v.size() * sizeof(double), cudaMemcpyDeviceToHost)) ||
+      (e = cudaMemcpy(cnt.data(), c->hist.count + slot0, n * sizeof(int32_t), cudaMemcpyDeviceToHost)) ||
+      (e = cudaMemcpy(head.data(), c->hist.head + slot0, n * sizeof(int32_t), cudaMemcpyDeviceToHost)))
+    return cuda_fail(c, e, "history export");
+  for (int64_t s = 0; s < n; ++s) {
+    const int k = cnt[s];
+    const int oldest = ((head[s] - k) % H + H) % H;
+    for (int i = 0; i < H; ++i) values[s * H + i] = i < k ? v[s * H + (oldest + i) % H] : 0.0;
+    counts[s] = k;
+  }
+  return LOF_OK;
+}
+
+extern "C" int lof_history_import(lof_ctx* c, int64_t slot0, int64_t n, const double* values,
+                                  const int32_t* counts) {
+  if (!c || !values || !counts || slot0 < 0 || n < 0 || slot0 + n > c->n_slots)
+    return fail(c, LOF_ERR_INVALID, "lof_history_import: bad arguments");
+  const int H = c->H;
+  for (int64_t s = 0; s < n; ++s)
+    if (counts[s] < 0 || counts[s] > H) return fail(c, LOF_ERR_INVALID, "history count out of range");
+  if (n == 0) return LOF_OK;
+  DeviceGuard g(c->device);
+  std::vector<int32_t> head(n);
+  for (int64_t s = 0; s < n; ++s) head[s] = counts[s] % H;
+  cudaError_t e;
+  if ((e = cudaDeviceSynchronize()) ||
+      (e = cudaMemcpy(c->hist.vals + slot0 * H, values, static_cast<size_t>(n) * H * sizeof(double), cudaMemcpyHostToDevice)) ||
+      (e = cudaMemcpy(c->hist.count + slot0, counts, n * sizeof(int32_t), cudaMemcpyHostToDevice)) ||
+      (e = cudaMemcpy(c->hist.head + slot0, head.data(), n * sizeof(int32_t), cudaMemcpyHostToDevice)) ||
+      (e = cudaMemset(c->hist.pend_flag + slot0, 0, n)))
+    return cuda_fail(c, e, "history import");
+  // refresh the cached thresholds with the device arithmetic
+  std::vector<lof_unit> us;
+  for (int64_t s = 0; s < n; s += lofk::kMaxChan) {
+    lof_unit u{};
+    u.n_chan = static_cast<int32_t>(std::min<int64_t>(lofk::kMaxChan, n - s));
+    u.n_time = 1;
+    u.history_slot = slot0 + s;
+    us.push_back(u);
+  }
+  int rc = commit_like(c, us.data(), static_cast<int>(us.size()), nullptr, true);
+  if (rc) return rc;
+  if ((e = cudaDeviceSynchronize())) return cuda_fail(c, e, "history refresh");
+  return LOF_OK;
+}
+
+extern "C" int lof_status(lof_ctx* c, void* cuda_stream) {
+  if (!c) return fail(nullptr, LOF_ERR_INVALID, "lof_status: ctx is NULL");
+  DeviceGuard g(c->device);
+  cudaError_t e = cudaStreamSynchronize(static_cast<cudaStream_t>(cuda_stream));
+  if (e != cudaSuccess) return cuda_fail(c, e, "cudaStreamSynchronize");
+  if (c->err_copy_pending) {
+    e = cudaEventSynchronize(c->ev_err);
+    if (e != cudaSuccess) return cuda_fail(c, e, "cudaEventSynchronize");
+  }
+  return pending_device_error(c);
+}
+
+extern "C" int lof_max_time(const lof_ctx* c, int dtype) {
+  if (!c || esize_of(dtype) == 0) return 0;
+  int lo = 0, hi = 1 << 20;
+  while (hi - lo > 1) {
+    const int mid = (lo + hi) / 2;
+    Plan pl;
+    std::string why;
+    if (make_plan(c, dtype, &mid, 1, &pl, &why)) lo = mid;
+    else hi = mid;
+  }
+  return lo;
+}

@@ -1,0 +1,161 @@
+// lof_internal.h -- definitions shared by the host side (lof_api.cu) and the
+// kernels (lof_kernels.cu) of the CUDA flagger library.  Not part of the ABI.
+#pragma once
+
+#include <cstdint>
+
+#include "lof.h"
+
+namespace lofk {
+
+// Coarse histogram of 32-bit keys: values < 32 get their own bin, larger
+// values 32 bins per octave (bin width at most 1/32 of the value).
+constexpr int kCoarseBins = 896;
+constexpr int kMaxLogWindow = 6;             // windows 1 .. 64
+constexpr int kKTable = 134;                 // sum_{k=0..6} (2^k + 1) threshold entries
+constexpr int kMaxChan = 2048;               // channels per unit
+constexpr int kMaxRowsPerItem = 64;          // rows of one unit staged by one CTA
+constexpr int kMaxTargets = 16;              // bins refined per selection round
+constexpr int kMaxFine = 2048;               // counters per refinement round (upper bound)
+constexpr int kSelCap = 2560;                // bin-list capacity for exact selection
+constexpr int kMaxRounds = 12;               // refinement rounds before giving up
+constexpr int kWorkspaceBytes = 36 * 1024;   // last-arriver workspace (overlays the prefix buffer)
+constexpr int kPadWords = 96;                // prefix-row slack beyond the row (window lookahead)
+constexpr uint32_t kFastMax = 1u << 26;      // 64 * max power < 2^32: 32-bit window sums exact
+
+// device error codes (written to the context's mapped error word)
+enum : int {
+  kErrNone = 0,
+  kErrTimeout = 1,     // a bounded wait on another CTA gave up
+  kErrSelect = 2,      // exact selection did not converge / bin list overflow
+  kErrInternal = 3,    // consistency check failed
+  kErrHistory = 4,     // history slot out of range
+};
+
+struct DevUnit {
+  const void* in;
+  void* out;
+  uint8_t* mask;
+  lof_unit_stats* stats;
+  int64_t in_stride, out_stride, mask_stride;  // elements
+  int64_t hist_slot;                           // first slot, or -1
+  int32_t C, T;
+  int32_t chan_off;                            // into per-channel scratch
+  int32_t first_item, n_items;
+  int32_t flags;                               // kUnit* bits
+};
+enum : int32_t {
+  kUnitInBulk = 1,      // every input row may be fetched with cp.async.bulk
+  kUnitOutBulk = 2,     // every output row may be written with cp.async.bulk
+  kUnitInPlace = 4,     // out == in: write flagged samples only
+  kUnitMaskVec = 8,     // mask rows 16-byte aligned
+};
+
+struct Item {
+  int32_t unit, row0, nrows, pad;
+};
+
+// Per-unit control words, zeroed before every launch.
+struct UnitCtl {
+  int arrive;    // arrivals, cumulative over rounds
+  int release;   // number of the last released round
+  int departed;  // CTAs done reading the unit's slot
+  int slot;      // slot (owning CTA) holding the unit's shared state
+};
+
+// Refinement target: bin [lo, hi] split into sub-bins of width 2^shift
+// starting at fine counter 'base'.
+struct alignas(16) Target {
+  uint32_t lo, hi, shift, base;
+};
+
+// Shared state of one unit while it is in flight (one per CTA of the grid;
+// the CTA that completes round 1 of a unit lends it its slot).
+struct Slot {
+  // round 1 (frequency pass)
+  double median_f, sigma_f;
+  long long n_pool;          // samples in the time-pass pool
+  int n_chan_freq;
+  int pad0;
+  // selection state
+  int state;                 // kState*
+  int n_bins;                // entries in the bin list
+  int n_targets, n_fine;
+  int round;
+  int mom_ready;             // moments accumulated
+  Target tgt[kMaxTargets];
+  int tgt_bin[kMaxTargets];  // bin-list index each target refines
+  unsigned long long mom[4]; // sum x (lo, hi), sum x^2 (lo, hi) -- 128-bit each
+  uint32_t coarse[kCoarseBins];
+  uint32_t fine[kMaxFine];
+  uint32_t blo[kSelCap], bhi[kSelCap], bcnt[kSelCap];
+  // final statistics of the time pass
+  double median_t, sigma_t;
+  long long K[kKTable];
+  int time_on;
+  int pad2;
+};
+enum : int {
+  kStateCoarse = 0,   // next: coarse histogram
+  kStateFine = 1,     // next: fine counts for the targets
+  kStateMoments = 2,  // next: exact moments (std estimator / MAD = 0)
+  kStateDone = 3,     // statistics ready
+};
+
+struct HistoryDev {
+  double* vals;        // [slots][H] ring storage
+  int32_t* count;      // entries held
+  int32_t* head;       // next write position
+  double* thr;         // cached mean + k*stddev (valid when count >= history_min)
+  double* pend;        // staged value
+  uint8_t* pend_flag;  // 1 = staged
+  uint64_t* pend_seq;  // block_seq of the staged value
+  int64_t n_slots;
+  int32_t H;
+};
+
+struct KParams {
+  const DevUnit* units;
+  const Item* items;
+  UnitCtl* ctl;
+  unsigned long long* chan_S;   // per channel spectrum sums
+  uint8_t* chan_Fc;             // per channel frequency flags
+  Slot* slots;
+  int* queue;                   // [0] next item
+  int* err;                     // first device-side error (0 = none)
+  int* err_info;                // detail words of that error
+  HistoryDev hist;
+  int n_units, n_items;
+  int tile_rows_bytes;          // shared bytes reserved for staged rows
+  int pfx_words;                // prefix buffer / workspace (32-bit words)
+  int mbits_words;              // flag bits of the staged rows
+  int fbits_words;              // fire bits of one batch of rows
+  int fine_bins;                // counters per refinement round
+  double factor[kMaxLogWindow + 1];
+  double sensitivity;
+  double history_k;
+  int max_log_window;
+  int history_min;
+  int sigma_std;
+  int enable_freq, enable_time, enable_history;
+  uint64_t block_seq;
+  long long spin_limit;         // bound of every device-side wait (ns)
+};
+
+struct CommitParams {
+  const DevUnit* units;
+  int n_units;
+  HistoryDev hist;
+  double history_k;
+  int history_min;
+};
+
+}  // namespace lofk
+
+// Kernel launchers (lof_kernels.cu)
+extern "C" int lofk_launch_block(int dtype, const lofk::KParams* kp, int grid, int threads,
+                                 int smem_bytes, void* stream, int cooperative);
+extern "C" int lofk_launch_commit(const lofk::CommitParams* cp, int total_channels, void* stream);
+extern "C" int lofk_launch_refresh(const lofk::CommitParams* cp, int total_channels, void* stream);
+extern "C" int lofk_max_blocks_per_sm(int dtype, int threads, int smem_bytes, int* out);
+extern "C" int lofk_set_smem_limit(int dtype, int smem_bytes);

@@ -1,0 +1,1713 @@
+// lof_kernels.cu -- sm_103a kernels of the LOFAR Online Flagger hot path.
+//
+// One persistent, cooperatively launched kernel flags every unit of a block
+// (one unit = one station/polarisation/subband: C channels x T samples).
+// Each CTA repeatedly takes an "item" (a run of whole rows of one unit) from a
+// device queue, stages the rows in shared memory with cp.async.bulk and keeps
+// them there for the whole pipeline, so every input byte crosses HBM once.
+// The unit-wide steps are resolved by the CTAs of a unit through bounded
+// group barriers; the last CTA to arrive at a round does the unit-wide work:
+//   round 1   row power sums -> spectrum S[c] -> median / MAD of S ->
+//             SumThreshold over S (Section 4: frequency flagging first)
+//   round 2   coarse histogram of the pooled powers of the kept channels
+//   round 3+  exact counts inside the few bins holding the median and the MAD
+//             end points, until both are exact (Section 4.2: O(N), no sort)
+// Then every CTA runs SumThreshold along time on its rows (Section 2.1, all
+// window sizes over a shared-memory prefix array), the history test
+// (Section 4.1), and writes the mask and the masked data.
+//
+// Integer inputs are exact end to end: powers and (window) sums are integers,
+// and each threshold is the binary64 formula of Section 2.1 turned into an
+// integer table K[n] = floor((I - n) * threshold_I) for n flagged samples.
+#include <cuda_runtime.h>
+
+#include <cstdint>
+
+#include "lof_internal.h"
+
+namespace lofk {
+namespace {
+
+constexpr int kWarp = 32;
+
+// ------------------------------------------------------------------ PTX helpers
+
+__device__ __forceinline__ uint32_t saddr(const void* p) {
+  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+__device__ __forceinline__ void mbar_init(uint64_t* b, uint32_t n) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(saddr(b)), "r"(n) : "memory");
+}
+__device__ __forceinline__ void fence_mbar_init() {
+  asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* b, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(saddr(b)),
+               "r"(bytes)
+               : "memory");
+}
+__device__ __forceinline__ bool mbar_try(uint64_t* b, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+      "selp.u32 %0, 1, 0, p;\n\t}"
+      : "=r"(ok)
+      : "r"(saddr(b)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+__device__ __forceinline__ void bulk_load(void* dst, const void* src, uint32_t bytes,
+                                          uint64_t* b) {
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::
+          "r"(saddr(dst)),
+      "l"(src), "r"(bytes), "r"(saddr(b))
+      : "memory");
+}
+__device__ __forceinline__ void bulk_store(void* dst, const void* src, uint32_t bytes) {
+  asm volatile("cp.async.bulk.global.shared::cta.bulk_group [%0], [%1], %2;" ::"l"(dst),
+               "r"(saddr(src)), "r"(bytes)
+               : "memory");
+}
+__device__ __forceinline__ void bulk_commit() {
+  asm volatile("cp.async.bulk.commit_group;" ::: "memory");
+}
+__device__ __forceinline__ void bulk_wait_read() {
+  asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory");
+}
+__device__ __forceinline__ void bulk_wait_all() {
+  asm volatile("cp.async.bulk.wait_group 0;" ::: "memory");
+}
+__device__ __forceinline__ void fence_async_smem() {
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+__device__ __forceinline__ int ld_acquire(const int* p) {
+  int v;
+  asm volatile("ld.acquire.gpu.global.b32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+__device__ __forceinline__ void st_release(int* p, int v) {
+  asm volatile("st.release.gpu.global.b32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+
+// ------------------------------------------------------------------ sample types
+// Power of one complex sample (Section 4: amplitudes first).  re^2 + im^2 of
+// int8/int16 components is exact in 32 bits (at most 2^31).
+
+template <int DT>
+struct Traits;
+
+template <>
+struct Traits<LOF_CI16> {
+  static constexpr int kBytes = 4;
+  static constexpr int kVec = 4;  // samples per 16-byte vector
+  __device__ static __forceinline__ uint32_t pw(uint32_t w) {
+    const int re = static_cast<int>(static_cast<int16_t>(w & 0xFFFFu));
+    const int im = static_cast<int>(static_cast<int16_t>(w >> 16));
+    return static_cast<uint32_t>(re * re) + static_cast<uint32_t>(im * im);
+  }
+  __device__ static __forceinline__ uint32_t at(const uint8_t* row, int t) {
+    return pw(reinterpret_cast<const uint32_t*>(row)[t]);
+  }
+  __device__ static __forceinline__ void vec(const uint8_t* row, int x, uint32_t (&v)[kVec]) {
+    const uint4 w = *reinterpret_cast<const uint4*>(row + static_cast<size_t>(x) * kBytes);
+    v[0] = pw(w.x);
+    v[1] = pw(w.y);
+    v[2] = pw(w.z);
+    v[3] = pw(w.w);
+  }
+  __device__ static __forceinline__ void zero(uint8_t* row, int t) {
+    reinterpret_cast<uint32_t*>(row)[t] = 0u;
+  }
+  __device__ static __forceinline__ void copy(uint8_t* dst, const uint8_t* src) {
+    *reinterpret_cast<uint32_t*>(dst) = *reinterpret_cast<const uint32_t*>(src);
+  }
+};
+
+template <>
+struct Traits<LOF_CI8> {
+  static constexpr int kBytes = 2;
+  static constexpr int kVec = 8;
+  __device__ static __forceinline__ uint32_t pw(uint32_t h) {
+    const int re = static_cast<int>(static_cast<int8_t>(h & 0xFFu));
+    const int im = static_cast<int>(static_cast<int8_t>((h >> 8) & 0xFFu));
+    return static_cast<uint32_t>(re * re + im * im);
+  }
+  __device__ static __forceinline__ uint32_t at(const uint8_t* row, int t) {
+    return pw(reinterpret_cast<const uint16_t*>(row)[t]);
+  }
+  __device__ static __forceinline__ void vec(const uint8_t* row, int x, uint32_t (&v)[kVec]) {
+    const uint4 w = *reinterpret_cast<const uint4*>(row + static_cast<size_t>(x) * kBytes);
+    v[0] = pw(w.x);
+    v[1] = pw(w.x >> 16);
+    v[2] = pw(w.y);
+    v[3] = pw(w.y >> 16);
+    v[4] = pw(w.z);
+    v[5] = pw(w.z >> 16);
+    v[6] = pw(w.w);
+    v[7] = pw(w.w >> 16);
+  }
+  __device__ static __forceinline__ void zero(uint8_t* row, int t) {
+    reinterpret_cast<uint16_t*>(row)[t] = 0;
+  }
+  __device__ static __forceinline__ void copy(uint8_t* dst, const uint8_t* src) {
+    *reinterpret_cast<uint16_t*>(dst) = *reinterpret_cast<const uint16_t*>(src);
+  }
+};
+
+// Powers of samples [x, x + kVec) of a staged row; zero at or beyond T.
+template <int DT>
+__device__ __forceinline__ void load_vec(const uint8_t* row, int x, int T,
+                                         uint32_t (&v)[Traits<DT>::kVec]) {
+  if (x + Traits<DT>::kVec <= T) {
+    Traits<DT>::vec(row, x, v);
+  } else {
+#pragma unroll
+    for (int j = 0; j < Traits<DT>::kVec; ++j)
+      v[j] = (x + j < T) ? Traits<DT>::at(row, x + j) : 0u;
+  }
+}
+
+// ------------------------------------------------------------------ small helpers
+
+// Coarse key of a 32-bit value: exact below 32, then 32 bins per octave.
+__device__ __forceinline__ uint32_t coarse_key(uint32_t v) {
+  if (v < 32u) return v;
+  const uint32_t e = 31u - __clz(v);
+  return ((e - 4u) << 5) | ((v >> (e - 5u)) & 31u);
+}
+__device__ __forceinline__ uint32_t coarse_lo(uint32_t k) {
+  if (k < 32u) return k;
+  const uint32_t e = (k >> 5) + 4u;
+  return (32u + (k & 31u)) << (e - 5u);
+}
+__device__ __forceinline__ uint32_t coarse_hi(uint32_t k) {
+  if (k < 32u) return k;
+  const uint32_t e = (k >> 5) + 4u;
+  return coarse_lo(k) + ((1u << (e - 5u)) - 1u);
+}
+
+// Index of prefix entry x in the padded prefix layout (4 spare words after
+// every 32): threads reading consecutive 32-word chunks hit distinct banks.
+__device__ __forceinline__ int pidx(int x) { return x + ((x >> 5) << 2); }
+
+__device__ __forceinline__ int round_up(int x, int m) { return (x + m - 1) / m * m; }
+
+__device__ __forceinline__ unsigned long long warp_sum64(unsigned long long v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xFFFFFFFFu, v, o);
+  return v;
+}
+__device__ __forceinline__ uint32_t warp_max32(uint32_t v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v = max(v, __shfl_xor_sync(0xFFFFFFFFu, v, o));
+  return v;
+}
+__device__ __forceinline__ uint32_t warp_sum32(uint32_t v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xFFFFFFFFu, v, o);
+  return v;
+}
+// exclusive warp scan (u32, wrapping); *total = sum over the warp
+__device__ __forceinline__ uint32_t warp_excl_scan(uint32_t v, int lane, uint32_t* total) {
+  uint32_t x = v;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const uint32_t y = __shfl_up_sync(0xFFFFFFFFu, x, o);
+    if (lane >= o) x += y;
+  }
+  *total = __shfl_sync(0xFFFFFFFFu, x, 31);
+  return x - v;
+}
+
+// u128 -> binary64, round to nearest even.
+__device__ __forceinline__ double u128_to_double(unsigned __int128 m) {
+  const unsigned long long hi = static_cast<unsigned long long>(m >> 64);
+  const unsigned long long lo = static_cast<unsigned long long>(m);
+  if (hi == 0) return __ull2double_rn(lo);
+  const int s = __clzll(static_cast<long long>(hi));
+  unsigned long long top = s ? ((hi << s) | (lo >> (64 - s))) : hi;
+  const unsigned long long rest = s ? (lo << s) : lo;
+  top |= (rest != 0ull) ? 1ull : 0ull;
+  return ldexp(__ull2double_rn(top), 64 - s);
+}
+
+// Population stddev from exact moments: sqrt((N*S2 - S1^2) / N^2).
+__device__ double moments_std(long long n, unsigned __int128 s1, unsigned __int128 s2) {
+  if (n <= 0) return 0.0;
+  const unsigned __int128 M = static_cast<unsigned __int128>(n) * s2 - s1 * s1;
+  const double nn = __dmul_rn(static_cast<double>(n), static_cast<double>(n));
+  return __dsqrt_rn(__ddiv_rn(u128_to_double(M), nn));
+}
+
+// Section 2.1: threshold_I = median + stddev * factor_I * sensitivity and the
+// integer table K[n] = floor((I - n) * threshold_I), n = 0..I, for I = 2^k.
+__device__ void fill_ktable(const KParams& kp, double median, double sigma, int kmax,
+                            long long* K) {
+  int off = 0;
+  for (int k = 0; k <= kmax; ++k) {
+    const int I = 1 << k;
+    const double thr =
+        __dadd_rn(median, __dmul_rn(__dmul_rn(sigma, kp.factor[k]), kp.sensitivity));
+    for (int n = 0; n <= I; ++n) {
+      const double lim = __dmul_rn(static_cast<double>(I - n), thr);
+      long long q;
+      if (!(lim == lim)) q = (1ll << 62);  // NaN threshold: never fires
+      else if (lim >= 4.0e18) q = (1ll << 62);
+      else if (lim <= -4.0e18) q = -(1ll << 62);
+      else q = __double2ll_rd(lim);
+      K[off + n] = q;
+    }
+    off += I + 1;
+  }
+}
+
+__device__ __forceinline__ int koffset(int k) { return (1 << k) + k - 1; }  // sum_{j<k}(2^j+1)
+
+__device__ void set_error(const KParams& kp, int code, int info) {
+  if (atomicCAS(kp.err, 0, code) == 0) {
+    kp.err_info[0] = info;
+    kp.err_info[1] = static_cast<int>(blockIdx.x);
+  }
+}
+
+__device__ __forceinline__ unsigned long long global_ns() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
+// Bounded wait until *p >= v (another CTA of this launch releases it).  Gives
+// up after kp.spin_limit nanoseconds, or as soon as another CTA reported an
+// error, and records a timeout.
+__device__ bool wait_geq(const KParams& kp, const int* p, int v, int code_info) {
+  const unsigned long long t0 = global_ns();
+  while (ld_acquire(p) < v) {
+    if (*reinterpret_cast<volatile int*>(kp.err) != 0) return false;
+    if (global_ns() - t0 > static_cast<unsigned long long>(kp.spin_limit)) {
+      set_error(kp, kErrTimeout, code_info);
+      return false;
+    }
+    __nanosleep(128);
+  }
+  return true;
+}
+
+// Bitonic sort of n (power of two) u64 values in shared memory, ascending.
+template <int NT>
+__device__ void block_sort64(unsigned long long* a, int n) {
+  for (int k = 2; k <= n; k <<= 1) {
+    for (int j = k >> 1; j > 0; j >>= 1) {
+      for (int i = threadIdx.x; i < n; i += NT) {
+        const int p = i ^ j;
+        if (p > i) {
+          const unsigned long long x = a[i], y = a[p];
+          const bool asc = (i & k) == 0;
+          if ((x > y) == asc) {
+            a[i] = y;
+            a[p] = x;
+          }
+        }
+      }
+      __syncthreads();
+    }
+  }
+}
+
+// 128-bit add into a pair of 64-bit words (lo, hi) in global memory.
+__device__ __forceinline__ void atomic_add_u128(unsigned long long* lohi, unsigned __int128 v) {
+  const unsigned long long vl = static_cast<unsigned long long>(v);
+  const unsigned long long vh = static_cast<unsigned long long>(v >> 64);
+  const unsigned long long old = atomicAdd(lohi, vl);
+  const unsigned long long carry = (old + vl < old) ? 1ull : 0ull;
+  if (vh + carry) atomicAdd(lohi + 1, vh + carry);
+}
+
+__device__ __forceinline__ Target ld_target(const Target* p) {
+  const uint4 v = __ldcg(reinterpret_cast<const uint4*>(p));
+  return Target{v.x, v.y, v.z, v.w};
+}
+
+// ------------------------------------------------------------------ shared state
+
+template <int NT>
+struct Fixed {
+  uint64_t mbar;
+  int item, ok, last, state, n_keep, n_tgt, owned_unit, slot;
+  unsigned int red_u32[NT / kWarp];
+  unsigned long long red_a[NT / kWarp], red_b[NT / kWarp], red_c[NT / kWarp];
+  unsigned long long cnt_time, cnt_total, cnt_hist;
+  unsigned long long rowS[kMaxRowsPerItem];
+  unsigned long long rowFlagSum[kMaxRowsPerItem];
+  uint32_t rowMax[kMaxRowsPerItem];
+  int rowNFlag[kMaxRowsPerItem];
+  uint8_t rowFc[kMaxRowsPerItem];
+  uint8_t rowFh[kMaxRowsPerItem];
+  int keep[kMaxRowsPerItem];
+  uint32_t segsum[256];
+  long long K[kKTable];
+  double median_t, sigma_t;
+  int time_on, kmax_t;
+  Target tgt[kMaxTargets];
+  // last-arriver scratch
+  long long m2lo, m2hi, da[2], db[2];
+  int mb[2], resolved, tb[kMaxTargets], nnz[kMaxTargets];
+  unsigned long long sd, md4;
+  double sig;
+  int kmax_f;
+};
+
+// ------------------------------------------------------------------ round 1
+// Frequency pass, run by the CTA that completes round 1 of a unit: median and
+// robust sigma of the spectrum and SumThreshold over it (Section 4).
+// Needs 36 KB of shared workspace.
+template <int NT>
+__device__ void frequency_pass(const KParams& kp, const DevUnit& u, Slot* slot, uint8_t* ws,
+                               Fixed<NT>& f) {
+  const int tid = threadIdx.x;
+  const int C = u.C;
+  int n2 = 1;
+  while (n2 < C) n2 <<= 1;
+  unsigned long long* srt = reinterpret_cast<unsigned long long*>(ws);  // kMaxChan
+  unsigned long long* Sv = srt + kMaxChan;                               // kMaxChan
+  uint8_t* Fc = reinterpret_cast<uint8_t*>(Sv + kMaxChan);               // kMaxChan
+  uint8_t* fire = Fc + kMaxChan;                                         // kMaxChan
+  const unsigned long long* gS = kp.chan_S + u.chan_off;
+  for (int i = tid; i < n2; i += NT) {
+    unsigned long long v = ~0ull;
+    if (i < C) {
+      v = __ldcg(gS + i);
+      Sv[i] = v;
+      Fc[i] = 0;
+    }
+    srt[i] = v;
+  }
+  __syncthreads();
+  block_sort64<NT>(srt, n2);
+  if (tid == 0) f.sd = (C & 1) ? 2ull * srt[C / 2] : srt[C / 2 - 1] + srt[C / 2];
+  __syncthreads();
+  const unsigned long long M2 = f.sd;  // twice the median of S
+  for (int i = tid; i < n2; i += NT) {
+    unsigned long long d = ~0ull;
+    if (i < C) {
+      const unsigned long long x2 = 2ull * Sv[i];
+      d = x2 > M2 ? x2 - M2 : M2 - x2;
+    }
+    srt[i] = d;
+  }
+  __syncthreads();
+  block_sort64<NT>(srt, n2);
+  if (tid == 0) {
+    // 4 x MAD: the median of |2S - M2| counted twice
+    f.md4 = (C & 1) ? 2ull * srt[C / 2] : srt[C / 2 - 1] + srt[C / 2];
+    const double med = __dmul_rn(__ull2double_rn(M2), 0.5);
+    const double mad = __dmul_rn(__ull2double_rn(f.md4), 0.25);
+    double sig;
+    if (!kp.sigma_std && mad > 0.0) {
+      sig = __dmul_rn(1.482602218505602, mad);
+    } else {
+      unsigned __int128 s1 = 0, s2 = 0;
+      for (int i = 0; i < C; ++i) {
+        s1 += Sv[i];
+        s2 += static_cast<unsigned __int128>(Sv[i]) * Sv[i];
+      }
+      sig = moments_std(C, s1, s2);
+    }
+    f.sig = sig;
+    slot->median_f = med;
+    slot->sigma_f = sig;
+    int kmax = 0;
+    while (kmax < kp.max_log_window && (2 << kmax) <= C) ++kmax;
+    f.kmax_f = kmax;
+    fill_ktable(kp, med, sig, kmax, f.K);
+  }
+  __syncthreads();
+  const double sig = f.sig;
+  const int kmax = f.kmax_f;
+  // Section 2.1 over the spectrum: direct window sums (C <= 2048 values)
+  if (kp.enable_freq && sig > 0.0) {
+    for (int k = 0; k <= kmax; ++k) {
+      const int I = 1 << k;
+      const long long* Kt = f.K + koffset(k);
+      for (int t = tid; t < C; t += NT) {
+        uint8_t fl = 0;
+        if (t + I <= C) {
+          unsigned long long su = 0;
+          int nf = 0;
+          for (int j = t; j < t + I; ++j) {
+            if (Fc[j]) ++nf;
+            else su += Sv[j];
+          }
+          fl = static_cast<long long>(su) > Kt[nf] ? 1 : 0;
+        }
+        fire[t] = fl;
+      }
+      __syncthreads();
+      for (int c = tid; c < C; c += NT) {
+        uint8_t any = Fc[c];
+        const int lo = c - I + 1 < 0 ? 0 : c - I + 1;
+        for (int t = lo; t <= c && !any; ++t) any = fire[t];
+        Fc[c] = any;
+      }
+      __syncthreads();
+    }
+  }
+  int nfc = 0;
+  for (int c = tid; c < C; c += NT) {
+    kp.chan_Fc[u.chan_off + c] = Fc[c];
+    nfc += Fc[c];
+  }
+  nfc = __reduce_add_sync(0xFFFFFFFFu, nfc);
+  if ((tid & 31) == 0) f.red_u32[tid >> 5] = static_cast<unsigned>(nfc);
+  for (int i = tid; i < kCoarseBins; i += NT) slot->coarse[i] = 0;
+  for (int i = tid; i < kMaxFine; i += NT) slot->fine[i] = 0;
+  __syncthreads();
+  if (tid == 0) {
+    int tot = 0;
+    for (int w = 0; w < NT / kWarp; ++w) tot += static_cast<int>(f.red_u32[w]);
+    slot->n_chan_freq = tot;
+    slot->n_pool = static_cast<long long>(C - tot) * u.T;
+    slot->mom[0] = slot->mom[1] = slot->mom[2] = slot->mom[3] = 0;
+    slot->mom_ready = 0;
+    slot->round = 1;
+    slot->n_bins = 0;
+    slot->n_targets = 0;
+    slot->n_fine = 0;
+    slot->median_t = 0.0;
+    slot->sigma_t = 0.0;
+    slot->time_on = 0;
+    slot->state = slot->n_pool > 0 ? kStateCoarse : kStateDone;
+    if (u.stats) {
+      u.stats->median_f = slot->median_f;
+      u.stats->sigma_f = slot->sigma_f;
+      u.stats->median_t = 0.0;
+      u.stats->sigma_t = 0.0;
+      u.stats->n_chan_freq = tot;
+      u.stats->n_flag_time = 0;
+      u.stats->n_chan_hist = 0;
+      u.stats->n_flag_total = 0;
+    }
+  }
+  __syncthreads();
+}
+
+// ------------------------------------------------------------------ exact selection
+// The pooled values are described by a sorted list of disjoint non-empty bins
+// [lo, hi] with counts.  An order statistic is exact once its bin has width 1.
+// The MAD is the r-th smallest |2x - M2| (M2 = twice the median); for a
+// distance d, c(d) = #{x : ceil((M2-d)/2) <= x <= floor((M2+d)/2)} is bounded
+// from both sides by the bins, which brackets d* = min{d : c(d) >= r+1}.
+
+struct BinList {
+  const uint32_t* lo;
+  const uint32_t* hi;
+  const uint32_t* cum;  // n + 1 entries, cum[0] = 0
+  int n;
+};
+
+// values in bins with lo <= y (an upper bound of #{x <= y})
+__device__ __forceinline__ long long cnt_upper(const BinList& B, long long y) {
+  if (y < 0) return 0;
+  int a = 0, b = B.n;
+  while (a < b) {
+    const int m = (a + b) >> 1;
+    if (static_cast<long long>(B.lo[m]) <= y) a = m + 1;
+    else b = m;
+  }
+  return B.cum[a];
+}
+// values in bins with hi <= y (a lower bound of #{x <= y})
+__device__ __forceinline__ long long cnt_lower(const BinList& B, long long y) {
+  if (y < 0) return 0;
+  int a = 0, b = B.n;
+  while (a < b) {
+    const int m = (a + b) >> 1;
+    if (static_cast<long long>(B.hi[m]) <= y) a = m + 1;
+    else b = m;
+  }
+  return B.cum[a];
+}
+__device__ __forceinline__ long long endA(long long M2, long long d) {
+  const long long t = M2 - d;
+  return t <= 0 ? 0 : (t + 1) >> 1;
+}
+__device__ __forceinline__ long long endB(long long M2, long long d) {
+  const long long t = (M2 + d) >> 1;
+  return t > 0xFFFFFFFFll ? 0xFFFFFFFFll : t;
+}
+__device__ __forceinline__ long long c_hi(const BinList& B, long long m2lo, long long m2hi,
+                                          long long d) {
+  return cnt_upper(B, endB(m2hi, d)) - cnt_lower(B, endA(m2lo, d) - 1);
+}
+__device__ __forceinline__ long long c_lo(const BinList& B, long long m2lo, long long m2hi,
+                                          long long d) {
+  const long long a = endA(m2hi, d), b = endB(m2lo, d);
+  if (a > b) return 0;
+  const long long v = cnt_lower(B, b) - cnt_upper(B, a - 1);
+  return v < 0 ? 0 : v;
+}
+// warp-wide 33-ary search: smallest d in [0, 2^34] with F(d) >= target (F monotone)
+template <bool HI>
+__device__ long long warp_search(const BinList& B, long long m2lo, long long m2hi,
+                                 long long target, int lane) {
+  long long lo = -1, hi = (1ll << 34);
+  while (hi - lo > 1) {
+    const long long span = hi - lo;
+    const long long d = lo + (span * (lane + 1)) / 33;
+    bool ok = false;
+    if (d > lo && d < hi) {
+      const long long cd = HI ? c_hi(B, m2lo, m2hi, d) : c_lo(B, m2lo, m2hi, d);
+      ok = cd >= target;
+    } else if (d >= hi) {
+      ok = true;
+    }
+    const unsigned bal = __ballot_sync(0xFFFFFFFFu, ok);
+    if (bal == 0u) {
+      lo = __shfl_sync(0xFFFFFFFFu, d, 31);
+    } else {
+      const int j = __ffs(bal) - 1;
+      const long long dj = __shfl_sync(0xFFFFFFFFu, d, j);
+      const long long dp = __shfl_sync(0xFFFFFFFFu, d, j > 0 ? j - 1 : 0);
+      if (dj < hi) hi = dj;
+      if (j > 0 && dp > lo) lo = dp;
+    }
+  }
+  return hi;
+}
+
+// Copies the slot's bin list to shared memory and forms cumulative counts.
+template <int NT>
+__device__ BinList load_bins(const Slot* slot, uint8_t* ws, int n) {
+  uint32_t* lo = reinterpret_cast<uint32_t*>(ws);
+  uint32_t* hi = lo + kSelCap;
+  uint32_t* cum = hi + kSelCap;
+  const int tid = threadIdx.x;
+  for (int i = tid; i < n; i += NT) {
+    lo[i] = __ldcg(slot->blo + i);
+    hi[i] = __ldcg(slot->bhi + i);
+    cum[i + 1] = __ldcg(slot->bcnt + i);
+  }
+  if (tid == 0) cum[0] = 0;
+  __syncthreads();
+  if (tid < kWarp) {
+    uint32_t carry = 0;
+    for (int base = 0; base < n; base += kWarp) {
+      const int i = base + tid;
+      const uint32_t v = i < n ? cum[i + 1] : 0u;
+      uint32_t tot;
+      const uint32_t ex = warp_excl_scan(v, tid, &tot);
+      if (i < n) cum[i + 1] = carry + ex + v;
+      carry += tot;
+    }
+  }
+  __syncthreads();
+  return BinList{lo, hi, cum, n};
+}
+
+__device__ __forceinline__ int bin_of_rank(const BinList& B, long long r) {
+  int a = 0, b = B.n;  // last index with cum[i] <= r
+  while (b - a > 1) {
+    const int m = (a + b) >> 1;
+    if (static_cast<long long>(B.cum[m]) <= r) a = m;
+    else b = m;
+  }
+  return a;
+}
+
+// Statistics are final: thresholds of the time pass (Section 2.1).
+template <int NT>
+__device__ void finalize_stats(const KParams& kp, const DevUnit& u, Slot* slot, double median,
+                               double sigma) {
+  if (threadIdx.x == 0) {
+    slot->median_t = median;
+    slot->sigma_t = sigma;
+    int kmax = 0;
+    while (kmax < kp.max_log_window && (2 << kmax) <= u.T) ++kmax;
+    long long K[kKTable];
+    fill_ktable(kp, median, sigma, kmax, K);
+    for (int i = 0; i < kKTable; ++i) slot->K[i] = K[i];
+    slot->time_on = (kp.enable_time && sigma > 0.0) ? 1 : 0;
+    slot->state = kStateDone;
+    if (u.stats) {
+      u.stats->median_t = median;
+      u.stats->sigma_t = sigma;
+    }
+  }
+  __syncthreads();
+}
+
+// Plan the next refinement round, or finish.  Whole CTA of the last arriver;
+// the bin list is in shared memory.
+template <int NT>
+__device__ void select_plan(const KParams& kp, const DevUnit& u, Slot* slot, const BinList& B,
+                            Fixed<NT>& f) {
+  const int tid = threadIdx.x, lane = tid & 31;
+  const long long N = B.cum[B.n];
+  if (tid == 0) {
+    if (N != slot->n_pool) set_error(kp, kErrInternal, 10);
+    const long long r1 = (N & 1) ? (N - 1) / 2 : N / 2 - 1;
+    const long long r2 = (N & 1) ? r1 : N / 2;
+    const int b1 = bin_of_rank(B, r1), b2 = bin_of_rank(B, r2);
+    f.mb[0] = b1;
+    f.mb[1] = b2;
+    if (N & 1) {
+      f.m2lo = 2ll * B.lo[b1];
+      f.m2hi = 2ll * B.hi[b1];
+    } else {
+      f.m2lo = static_cast<long long>(B.lo[b1]) + B.lo[b2];
+      f.m2hi = static_cast<long long>(B.hi[b1]) + B.hi[b2];
+    }
+  }
+  __syncthreads();
+  const long long m2lo = f.m2lo, m2hi = f.m2hi;
+  if (tid < kWarp) {
+    const int nr = (N & 1) ? 1 : 2;
+    for (int q = 0; q < nr; ++q) {
+      const long long r = (N & 1) ? (N - 1) / 2 : N / 2 - 1 + q;
+      const long long da = warp_search<true>(B, m2lo, m2hi, r + 1, lane);
+      const long long db = warp_search<false>(B, m2lo, m2hi, r + 1, lane);
+      if (lane == 0) {
+        f.da[q] = da;
+        f.db[q] = db;
+      }
+    }
+    if (nr == 1 && lane == 0) {
+      f.da[1] = f.da[0];
+      f.db[1] = f.db[0];
+    }
+  }
+  __syncthreads();
+  if (tid == 0) {
+    int nt = 0;
+    auto add = [&](int b) {
+      if (b < 0 || b >= B.n || B.hi[b] == B.lo[b]) return;
+      for (int i = 0; i < nt; ++i)
+        if (f.tb[i] == b) return;
+      if (nt < kMaxTargets) f.tb[nt++] = b;
+    };
+    auto add_range = [&](long long ylo, long long yhi) {
+      if (ylo < 0) ylo = 0;
+      if (yhi > 0xFFFFFFFFll) yhi = 0xFFFFFFFFll;
+      if (ylo > yhi) return;
+      int a = 0, b = B.n;  // first bin with hi >= ylo
+      while (a < b) {
+        const int m = (a + b) >> 1;
+        if (static_cast<long long>(B.hi[m]) < ylo) a = m + 1;
+        else b = m;
+      }
+      for (int i = a; i < B.n && static_cast<long long>(B.lo[i]) <= yhi; ++i) add(i);
+    };
+    add(f.mb[0]);
+    add(f.mb[1]);
+    const bool med_exact = (m2lo == m2hi);
+    bool mad_exact = med_exact;
+    for (int q = 0; q < 2; ++q) {
+      const long long da = f.da[q], db = f.db[q];
+      if (da != db || !med_exact) {
+        mad_exact = false;
+        add_range(endA(m2lo, db) - 1, endA(m2hi, da));
+        add_range(endB(m2lo, da) - 1, endB(m2hi, db) + 1);
+      }
+    }
+    f.resolved = (med_exact && mad_exact) ? 1 : 0;
+    for (int i = 1; i < nt; ++i)
+      for (int j = i; j > 0 && f.tb[j - 1] > f.tb[j]; --j) {
+        const int t = f.tb[j];
+        f.tb[j] = f.tb[j - 1];
+        f.tb[j - 1] = t;
+      }
+    if (!f.resolved && nt == 0) {
+      set_error(kp, kErrSelect, 1);
+      f.resolved = 2;
+    }
+    if (f.resolved == 0) {
+      int per = kp.fine_bins / nt;
+      int p2 = 1;
+      while (p2 * 2 <= per) p2 *= 2;
+      int base = 0;
+      for (int i = 0; i < nt; ++i) {
+        const uint32_t lo = B.lo[f.tb[i]], hi = B.hi[f.tb[i]];
+        const unsigned long long W = static_cast<unsigned long long>(hi - lo) + 1ull;
+        uint32_t sh = 0;
+        while (((W - 1ull) >> sh) + 1ull > static_cast<unsigned long long>(p2)) ++sh;
+        const int nsub = static_cast<int>(((W - 1ull) >> sh) + 1ull);
+        slot->tgt[i] = Target{lo, hi, sh, static_cast<uint32_t>(base)};
+        slot->tgt_bin[i] = f.tb[i];
+        base += nsub;
+      }
+      slot->n_targets = nt;
+      slot->n_fine = base;
+      slot->round += 1;
+      if (slot->round > kMaxRounds) {
+        set_error(kp, kErrSelect, 2);
+        f.resolved = 2;
+      } else {
+        slot->state = kStateFine;
+      }
+    }
+  }
+  __syncthreads();
+  if (f.resolved == 0) {
+    for (int i = tid; i < kMaxFine; i += NT) slot->fine[i] = 0;
+    __syncthreads();
+    return;
+  }
+  if (f.resolved == 2) {  // give up: no time pass for this unit
+    finalize_stats<NT>(kp, u, slot, 0.0, 0.0);
+    return;
+  }
+  const long long M2 = m2lo;
+  const long long mad4 = f.da[0] + f.da[1];  // odd N: 2 d*, even N: d*(a) + d*(b)
+  const double med = __dmul_rn(static_cast<double>(M2), 0.5);
+  const double mad = __dmul_rn(static_cast<double>(mad4), 0.25);
+  if (!kp.sigma_std && mad > 0.0) {
+    finalize_stats<NT>(kp, u, slot, med, __dmul_rn(1.482602218505602, mad));
+  } else if (kp.sigma_std) {
+    // moments were accumulated with the coarse histogram
+    const unsigned __int128 s1 =
+        (static_cast<unsigned __int128>(__ldcg(slot->mom + 1)) << 64) | __ldcg(slot->mom + 0);
+    const unsigned __int128 s2 =
+        (static_cast<unsigned __int128>(__ldcg(slot->mom + 3)) << 64) | __ldcg(slot->mom + 2);
+    finalize_stats<NT>(kp, u, slot, med, moments_std(N, s1, s2));
+  } else {
+    if (tid == 0) {
+      slot->median_t = med;
+      slot->mom[0] = slot->mom[1] = slot->mom[2] = slot->mom[3] = 0;
+      slot->state = kStateMoments;
+    }
+    __syncthreads();
+  }
+}
+
+// Builds the initial bin list from the coarse histogram (warp 0).
+template <int NT>
+__device__ void build_coarse_list(Slot* slot) {
+  const int tid = threadIdx.x;
+  if (tid < kWarp) {
+    int n = 0;
+    for (int base = 0; base < kCoarseBins; base += kWarp) {
+      const int k = base + tid;
+      const uint32_t c = __ldcg(slot->coarse + k);
+      const unsigned bal = __ballot_sync(0xFFFFFFFFu, c != 0u);
+      if (c) {
+        const int pos = n + __popc(bal & ((1u << tid) - 1u));
+        slot->blo[pos] = coarse_lo(k);
+        slot->bhi[pos] = coarse_hi(k);
+        slot->bcnt[pos] = c;
+      }
+      n += __popc(bal);
+    }
+    if (tid == 0) slot->n_bins = n;
+  }
+  __threadfence_block();
+  __syncthreads();
+}
+
+// Replaces every refined bin by its non-empty sub-bins.
+template <int NT>
+__device__ void merge_fine(const KParams& kp, Slot* slot, uint8_t* ws, Fixed<NT>& f) {
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int n = __ldcg(&slot->n_bins);
+  const int nt = __ldcg(&slot->n_targets);
+  uint32_t* lo = reinterpret_cast<uint32_t*>(ws);
+  uint32_t* hi = lo + kSelCap;
+  uint32_t* cnt = hi + kSelCap;
+  for (int i = tid; i < n; i += NT) {
+    lo[i] = __ldcg(slot->blo + i);
+    hi[i] = __ldcg(slot->bhi + i);
+    cnt[i] = __ldcg(slot->bcnt + i);
+  }
+  if (tid < kMaxTargets) {
+    if (tid < nt) {
+      f.tgt[tid] = ld_target(slot->tgt + tid);
+      f.tb[tid] = __ldcg(slot->tgt_bin + tid);
+    }
+  }
+  __syncthreads();
+  for (int t = warp; t < nt; t += NT / kWarp) {
+    const Target g = f.tgt[t];
+    const int nsub = static_cast<int>((static_cast<unsigned long long>(g.hi - g.lo) >> g.shift) + 1ull);
+    int nz = 0;
+    unsigned long long sum = 0;
+    for (int j = lane; j < nsub; j += kWarp) {
+      const uint32_t c = __ldcg(slot->fine + g.base + j);
+      nz += c != 0u;
+      sum += c;
+    }
+    nz = __reduce_add_sync(0xFFFFFFFFu, nz);
+    sum = warp_sum64(sum);
+    if (lane == 0) {
+      f.nnz[t] = nz;
+      if (sum != cnt[f.tb[t]]) set_error(kp, kErrInternal, 20);
+    }
+  }
+  __syncthreads();
+  int grow = 0;
+  for (int t = 0; t < nt; ++t) grow += f.nnz[t] - 1;
+  const int nn = n + grow;
+  if (nn > kSelCap) {
+    if (tid == 0) set_error(kp, kErrSelect, 3);
+    __syncthreads();
+    return;
+  }
+  for (int i = tid; i < n; i += NT) {
+    int shift = 0;
+    bool is_t = false;
+    for (int t = 0; t < nt; ++t) {
+      if (f.tb[t] < i) shift += f.nnz[t] - 1;
+      if (f.tb[t] == i) is_t = true;
+    }
+    if (!is_t) {
+      slot->blo[i + shift] = lo[i];
+      slot->bhi[i + shift] = hi[i];
+      slot->bcnt[i + shift] = cnt[i];
+    }
+  }
+  for (int t = warp; t < nt; t += NT / kWarp) {
+    const Target g = f.tgt[t];
+    int pos = f.tb[t];
+    for (int q = 0; q < t; ++q) pos += f.nnz[q] - 1;
+    const int nsub = static_cast<int>((static_cast<unsigned long long>(g.hi - g.lo) >> g.shift) + 1ull);
+    for (int base = 0; base < nsub; base += kWarp) {
+      const int j = base + lane;
+      const uint32_t c = j < nsub ? __ldcg(slot->fine + g.base + j) : 0u;
+      const unsigned bal = __ballot_sync(0xFFFFFFFFu, c != 0u);
+      if (c) {
+        const int p = pos + __popc(bal & ((1u << lane) - 1u));
+        const unsigned long long a = static_cast<unsigned long long>(g.lo) +
+                                     (static_cast<unsigned long long>(j) << g.shift);
+        unsigned long long b = a + (1ull << g.shift) - 1ull;
+        if (b > g.hi) b = g.hi;
+        slot->blo[p] = static_cast<uint32_t>(a);
+        slot->bhi[p] = static_cast<uint32_t>(b);
+        slot->bcnt[p] = c;
+      }
+      pos += __popc(bal);
+    }
+  }
+  __threadfence_block();
+  __syncthreads();
+  if (tid == 0) slot->n_bins = nn;
+  __syncthreads();
+}
+
+// ------------------------------------------------------------------ time pass helpers
+
+// Window sums of one 32-sample chunk from the prefix row E (fast path: no
+// flagged sample in reach, all window sums < 2^32).  Bit j: window at t0 + j
+// exceeds K0.
+template <int I>
+__device__ __forceinline__ uint32_t fast_fire(const uint32_t* E, int t0, uint32_t K0) {
+  uint32_t a[32], b[32];
+  const uint4* pa = reinterpret_cast<const uint4*>(E + pidx(t0));
+#pragma unroll
+  for (int q = 0; q < 8; ++q) {
+    const uint4 w = pa[q];
+    a[4 * q + 0] = w.x;
+    a[4 * q + 1] = w.y;
+    a[4 * q + 2] = w.z;
+    a[4 * q + 3] = w.w;
+  }
+  if constexpr (I >= 32) {
+    const uint4* pb = reinterpret_cast<const uint4*>(E + pidx(t0 + I));
+#pragma unroll
+    for (int q = 0; q < 8; ++q) {
+      const uint4 w = pb[q];
+      b[4 * q + 0] = w.x;
+      b[4 * q + 1] = w.y;
+      b[4 * q + 2] = w.z;
+      b[4 * q + 3] = w.w;
+    }
+  } else {
+#pragma unroll
+    for (int j = 0; j < 32 - I; ++j) b[j] = a[j + I];
+    const uint32_t* pn = E + pidx(t0 + 32);
+    if constexpr (I >= 4) {
+#pragma unroll
+      for (int q = 0; q < I / 4; ++q) {
+        const uint4 w = reinterpret_cast<const uint4*>(pn)[q];
+        b[32 - I + 4 * q + 0] = w.x;
+        b[32 - I + 4 * q + 1] = w.y;
+        b[32 - I + 4 * q + 2] = w.z;
+        b[32 - I + 4 * q + 3] = w.w;
+      }
+    } else if constexpr (I == 2) {
+      const uint2 w = *reinterpret_cast<const uint2*>(pn);
+      b[30] = w.x;
+      b[31] = w.y;
+    } else {
+      b[31] = pn[0];
+    }
+  }
+  uint32_t mx = 0;
+#pragma unroll
+  for (int j = 0; j < 32; ++j) mx = max(mx, b[j] - a[j]);
+  if (mx <= K0) return 0u;
+  uint32_t fire = 0;
+#pragma unroll
+  for (int j = 0; j < 32; ++j) fire |= ((b[j] - a[j]) > K0 ? 1u : 0u) << j;
+  return fire;
+}
+
+__device__ __forceinline__ uint32_t bit_at(const uint32_t* M, int j) {
+  return (M[j >> 5] >> (j & 31)) & 1u;
+}
+__device__ __forceinline__ uint32_t val_at(const uint32_t* E, int j) {
+  return E[pidx(j + 1)] - E[pidx(j)];  // single-sample difference: exact mod 2^32
+}
+
+// General path: exact 64-bit window sums with flagged samples substituted,
+// sliding across the chunk.  Compares sum_unflagged > K[n_flagged].
+__device__ uint32_t slow_fire(const uint32_t* E, const uint32_t* M, int t0, int I, int T,
+                              const long long* Kt) {
+  const int tl = min(t0 + 31, T - I);
+  unsigned long long su = 0;
+  int nf = 0;
+  for (int j = t0; j < t0 + I; ++j) {
+    if (bit_at(M, j)) ++nf;
+    else su += val_at(E, j);
+  }
+  uint32_t fire = 0;
+  for (int t = t0;; ++t) {
+    if (static_cast<long long>(su) > Kt[nf]) fire |= 1u << (t - t0);
+    if (t >= tl) break;
+    if (bit_at(M, t)) --nf;
+    else su -= val_at(E, t);
+    if (bit_at(M, t + I)) ++nf;
+    else su += val_at(E, t + I);
+  }
+  return fire;
+}
+
+// Flag bits covered by windows of I samples that start at a fired bit: bits
+// of word w from fire words w (hi) and w-1 (lo), for I <= 32.
+__device__ __forceinline__ uint32_t dilate32(uint32_t hi, uint32_t lo, int I) {
+  unsigned long long x = (static_cast<unsigned long long>(hi) << 32) | lo;
+  for (int s = 1; s < I; s <<= 1) x |= x << s;
+  return static_cast<uint32_t>(x >> 32);
+}
+
+template <int I>
+__device__ __forceinline__ uint32_t fire_chunk(bool fast, const uint32_t* E, const uint32_t* M,
+                                               int t0, int T, const long long* Kt, uint32_t K0) {
+  if (fast) return fast_fire<I>(E, t0, K0);
+  return slow_fire(E, M, t0, I, T, Kt);
+}
+
+// ------------------------------------------------------------------ the kernel
+
+template <int DT, int NT>
+__global__ void __launch_bounds__(NT, 512 / NT) lof_block_kernel(const KParams kp) {
+  using TR = Traits<DT>;
+  constexpr int VS = TR::kVec;
+  constexpr int SEG = 64 * VS;  // samples per segment task (two warp sweeps)
+  constexpr int NW = NT / kWarp;
+  extern __shared__ __align__(128) uint8_t smem[];
+  __shared__ Fixed<NT> f;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  uint8_t* const sdata = smem;
+  uint8_t* const swork = smem + kp.tile_rows_bytes;
+  uint32_t* const spfx = reinterpret_cast<uint32_t*>(swork);
+  uint32_t* const smbits = spfx + kp.pfx_words;
+  uint32_t* const sfbits = smbits + kp.mbits_words;
+
+  if (tid == 0) {
+    mbar_init(&f.mbar, 1);
+    fence_mbar_init();
+    f.owned_unit = -1;
+  }
+  __syncthreads();
+  uint32_t phase = 0;
+
+  for (;;) {
+    if (tid == 0) {
+      bulk_wait_read();  // previous item's bulk stores have read their rows
+      f.item = atomicAdd(kp.queue, 1);
+      f.ok = 1;
+      f.cnt_time = f.cnt_total = f.cnt_hist = 0;
+    }
+    __syncthreads();
+    const int item = f.item;
+    if (item >= kp.n_items) break;
+    const Item it = kp.items[item];
+    const DevUnit u = kp.units[it.unit];
+    UnitCtl* const ctl = kp.ctl + it.unit;
+    const int T = u.T, R = it.nrows, row0 = it.row0;
+    const int dpitch = round_up(T * TR::kBytes, 128);
+    const int G = u.n_items;
+    const int nch = (T + 31) >> 5;
+    const int MW = nch + 4;  // flag words per row, two zero words on each side
+    const int nseg = (T + SEG - 1) / SEG;
+    const bool bulk_in = (u.flags & kUnitInBulk) != 0;
+    const uint8_t* gin = static_cast<const uint8_t*>(u.in);
+
+    // ---- stage the rows
+    if (tid == 0 && bulk_in) {
+      mbar_expect_tx(&f.mbar, static_cast<uint32_t>(R * T * TR::kBytes));
+      for (int r = 0; r < R; ++r)
+        bulk_load(sdata + r * dpitch, gin + (row0 + r) * u.in_stride * TR::kBytes,
+                  static_cast<uint32_t>(T * TR::kBytes), &f.mbar);
+    }
+    if (!bulk_in) {
+      for (int r = 0; r < R; ++r)
+        for (int t = tid; t < T; t += NT)
+          TR::copy(sdata + r * dpitch + t * TR::kBytes,
+                   gin + ((row0 + r) * u.in_stride + t) * TR::kBytes);
+    }
+    for (int r = tid; r < R; r += NT) {
+      f.rowS[r] = 0;
+      f.rowMax[r] = 0;
+      f.rowFlagSum[r] = 0;
+      f.rowNFlag[r] = 0;
+      f.rowFh[r] = 0;
+      f.rowFc[r] = 0;
+    }
+    for (int i = tid; i < R * MW; i += NT) smbits[i] = 0u;
+    if (bulk_in) {
+      const unsigned long long t0 = global_ns();
+      while (!mbar_try(&f.mbar, phase)) {
+        if (global_ns() - t0 > static_cast<unsigned long long>(kp.spin_limit)) {
+          set_error(kp, kErrTimeout, 100);
+          break;
+        }
+      }
+      phase ^= 1u;
+    }
+    __syncthreads();
+
+    // ---- round 1 work: per-row power sums, maxima and segment sums
+    for (int task = warp; task < R * nseg; task += NW) {
+      const int r = task / nseg, s = task - r * nseg;
+      const uint8_t* row = sdata + r * dpitch;
+      const int x0 = s * SEG;
+      unsigned long long sum = 0;
+      uint32_t mx = 0;
+#pragma unroll
+      for (int q = 0; q < 2; ++q) {
+        const int x = x0 + q * 32 * VS + lane * VS;
+        if (x < T) {
+          uint32_t v[VS];
+          load_vec<DT>(row, x, T, v);
+#pragma unroll
+          for (int j = 0; j < VS; ++j) {
+            sum += v[j];
+            mx = max(mx, v[j]);
+          }
+        }
+      }
+      sum = warp_sum64(sum);
+      mx = warp_max32(mx);
+      if (lane == 0) {
+        atomicAdd(&f.rowS[r], sum);
+        atomicMax(&f.rowMax[r], mx);
+        f.segsum[r * nseg + s] = static_cast<uint32_t>(sum);
+      }
+    }
+    __syncthreads();
+    for (int r = tid; r < R; r += NT) kp.chan_S[u.chan_off + row0 + r] = f.rowS[r];
+    __syncthreads();
+    if (tid == 0) {
+      __threadfence();
+      const int old = atomicAdd(&ctl->arrive, 1);
+      f.last = (old + 1 == G) ? 1 : 0;
+    }
+    __syncthreads();
+    if (f.last) {
+      if (tid == 0) {
+        __threadfence();
+        // the slot this CTA lends must be free of the unit it served before
+        if (f.owned_unit >= 0) {
+          const int pu = f.owned_unit;
+          if (!wait_geq(kp, &kp.ctl[pu].departed, kp.units[pu].n_items, 200)) f.ok = 0;
+        }
+        f.owned_unit = it.unit;
+        ctl->slot = static_cast<int>(blockIdx.x);
+      }
+      __syncthreads();
+      if (f.ok) {
+        frequency_pass<NT>(kp, u, kp.slots + blockIdx.x, swork, f);
+        if (tid == 0) {
+          __threadfence();
+          st_release(&ctl->release, 1);
+        }
+      }
+    } else if (tid == 0) {
+      if (!wait_geq(kp, &ctl->release, 1, 1)) f.ok = 0;
+    }
+    __syncthreads();
+    if (!f.ok) break;
+    if (tid == 0) f.slot = __ldcg(&ctl->slot);
+    __syncthreads();
+    Slot* const slot = kp.slots + f.slot;
+    for (int r = tid; r < R; r += NT) f.rowFc[r] = __ldcg(kp.chan_Fc + u.chan_off + row0 + r);
+    __syncthreads();
+    if (tid == 0) {
+      int nk = 0;
+      for (int r = 0; r < R; ++r)
+        if (!f.rowFc[r]) f.keep[nk++] = r;
+      f.n_keep = nk;
+    }
+    __syncthreads();
+    const int nkeep = f.n_keep;
+
+    // ---- rounds 2+: exact pooled statistics of the kept rows
+    int round = 1;
+    for (;;) {
+      if (tid == 0) f.state = __ldcg(&slot->state);
+      __syncthreads();
+      const int state = f.state;
+      if (state == kStateDone) break;
+      ++round;
+      if (state == kStateCoarse) {
+        uint32_t* hist = spfx;
+        for (int i = tid; i < kCoarseBins; i += NT) hist[i] = 0u;
+        __syncthreads();
+        unsigned long long s1 = 0;
+        unsigned __int128 s2 = 0;
+        for (int task = warp; task < nkeep * nseg; task += NW) {
+          const int kr = task / nseg, s = task - kr * nseg;
+          const uint8_t* row = sdata + f.keep[kr] * dpitch;
+#pragma unroll
+          for (int q = 0; q < 2; ++q) {
+            const int x = s * SEG + q * 32 * VS + lane * VS;
+            if (x < T) {
+              uint32_t v[VS];
+              load_vec<DT>(row, x, T, v);
+#pragma unroll
+              for (int j = 0; j < VS; ++j) {
+                if (x + j < T) {
+                  atomicAdd(&hist[coarse_key(v[j])], 1u);
+                  if (kp.sigma_std) {
+                    s1 += v[j];
+                    s2 += static_cast<unsigned long long>(v[j]) * v[j];
+                  }
+                }
+              }
+            }
+          }
+        }
+        if (kp.sigma_std) {
+          s1 = warp_sum64(s1);
+          unsigned long long lo = static_cast<unsigned long long>(s2);
+          unsigned long long hi = static_cast<unsigned long long>(s2 >> 64);
+          // 128-bit warp sum through (lo, hi) pairs
+          for (int o = 16; o > 0; o >>= 1) {
+            const unsigned long long l2 = __shfl_xor_sync(0xFFFFFFFFu, lo, o);
+            const unsigned long long h2 = __shfl_xor_sync(0xFFFFFFFFu, hi, o);
+            const unsigned long long nl = lo + l2;
+            hi = hi + h2 + (nl < lo ? 1ull : 0ull);
+            lo = nl;
+          }
+          if (lane == 0) {
+            atomicAdd(slot->mom + 0, s1);  // s1 < 2^64 per warp; carry handled below
+            atomic_add_u128(slot->mom + 2, (static_cast<unsigned __int128>(hi) << 64) | lo);
+          }
+        }
+        __syncthreads();
+        for (int i = tid; i < kCoarseBins; i += NT) {
+          const uint32_t h = hist[i];
+          if (h) atomicAdd(slot->coarse + i, h);
+        }
+      } else if (state == kStateFine) {
+        uint32_t* fine = spfx;
+        uint8_t* map = reinterpret_cast<uint8_t*>(spfx + kMaxFine);
+        const int nt = __ldcg(&slot->n_targets);
+        const int nf = __ldcg(&slot->n_fine);
+        if (tid < nt) f.tgt[tid] = ld_target(slot->tgt + tid);
+        for (int i = tid; i < nf; i += NT) fine[i] = 0u;
+        __syncthreads();
+        for (int k = tid; k < kCoarseBins; k += NT) {
+          const uint32_t lo = coarse_lo(k), hi = coarse_hi(k);
+          int t = 0;
+          while (t < nt && f.tgt[t].hi < lo) ++t;
+          map[k] = (t < nt && f.tgt[t].lo <= hi) ? static_cast<uint8_t>(t) : 0xFFu;
+        }
+        __syncthreads();
+        for (int task = warp; task < nkeep * nseg; task += NW) {
+          const int kr = task / nseg, s = task - kr * nseg;
+          const uint8_t* row = sdata + f.keep[kr] * dpitch;
+#pragma unroll
+          for (int q = 0; q < 2; ++q) {
+            const int x = s * SEG + q * 32 * VS + lane * VS;
+            if (x < T) {
+              uint32_t v[VS];
+              load_vec<DT>(row, x, T, v);
+#pragma unroll
+              for (int j = 0; j < VS; ++j) {
+                if (x + j < T) {
+                  int t = map[coarse_key(v[j])];
+                  if (t != 0xFF) {
+                    for (; t < nt && v[j] >= f.tgt[t].lo; ++t) {
+                      if (v[j] <= f.tgt[t].hi) {
+                        atomicAdd(&fine[f.tgt[t].base + ((v[j] - f.tgt[t].lo) >> f.tgt[t].shift)],
+                                  1u);
+                        break;
+                      }
+                    }
+                  }
+                }
+              }
+            }
+          }
+        }
+        __syncthreads();
+        for (int i = tid; i < nf; i += NT) {
+          const uint32_t h = fine[i];
+          if (h) atomicAdd(slot->fine + i, h);
+        }
+      } else {  // kStateMoments
+        unsigned long long s1 = 0;
+        unsigned __int128 s2 = 0;
+        for (int task = warp; task < nkeep * nseg; task += NW) {
+          const int kr = task / nseg, s = task - kr * nseg;
+          const uint8_t* row = sdata + f.keep[kr] * dpitch;
+#pragma unroll
+          for (int q = 0; q < 2; ++q) {
+            const int x = s * SEG + q * 32 * VS + lane * VS;
+            if (x < T) {
+              uint32_t v[VS];
+              load_vec<DT>(row, x, T, v);
+#pragma unroll
+              for (int j = 0; j < VS; ++j) {
+                s1 += v[j];
+                s2 += static_cast<unsigned long long>(v[j]) * v[j];
+              }
+            }
+          }
+        }
+        s1 = warp_sum64(s1);
+        unsigned long long lo = static_cast<unsigned long long>(s2);
+        unsigned long long hi = static_cast<unsigned long long>(s2 >> 64);
+        for (int o = 16; o > 0; o >>= 1) {
+          const unsigned long long l2 = __shfl_xor_sync(0xFFFFFFFFu, lo, o);
+          const unsigned long long h2 = __shfl_xor_sync(0xFFFFFFFFu, hi, o);
+          const unsigned long long nl = lo + l2;
+          hi = hi + h2 + (nl < lo ? 1ull : 0ull);
+          lo = nl;
+        }
+        if (lane == 0) {
+          atomicAdd(slot->mom + 0, s1);
+          atomic_add_u128(slot->mom + 2, (static_cast<unsigned __int128>(hi) << 64) | lo);
+        }
+      }
+      __syncthreads();
+      if (tid == 0) {
+        __threadfence();
+        const int old = atomicAdd(&ctl->arrive, 1);
+        f.last = (old + 1 == round * G) ? 1 : 0;
+      }
+      __syncthreads();
+      if (f.last) {
+        if (tid == 0) __threadfence();
+        __syncthreads();
+        if (state == kStateCoarse) {
+          build_coarse_list<NT>(slot);
+          if (tid == 0 && kp.sigma_std) slot->mom_ready = 1;
+          const BinList B = load_bins<NT>(slot, swork, __ldcg(&slot->n_bins));
+          select_plan<NT>(kp, u, slot, B, f);
+        } else if (state == kStateFine) {
+          merge_fine<NT>(kp, slot, swork, f);
+          const BinList B = load_bins<NT>(slot, swork, __ldcg(&slot->n_bins));
+          select_plan<NT>(kp, u, slot, B, f);
+        } else {
+          const long long N = __ldcg(&slot->n_pool);
+          const unsigned __int128 s1 = __ldcg(slot->mom + 0);
+          const unsigned __int128 s2 =
+              (static_cast<unsigned __int128>(__ldcg(slot->mom + 3)) << 64) | __ldcg(slot->mom + 2);
+          finalize_stats<NT>(kp, u, slot, __ldcg(&slot->median_t), moments_std(N, s1, s2));
+        }
+        if (tid == 0) {
+          __threadfence();
+          st_release(&ctl->release, round);
+        }
+      } else if (tid == 0) {
+        if (!wait_geq(kp, &ctl->release, round, round)) f.ok = 0;
+      }
+      __syncthreads();
+      if (!f.ok) break;
+    }
+    if (!f.ok) break;
+    // the unit's statistics and thresholds
+    for (int i = tid; i < kKTable; i += NT) f.K[i] = __ldcg(slot->K + i);
+    if (tid == 0) {
+      f.median_t = __ldcg(&slot->median_t);
+      f.sigma_t = __ldcg(&slot->sigma_t);
+      f.time_on = __ldcg(&slot->time_on);
+      int kmax = 0;
+      while (kmax < kp.max_log_window && (2 << kmax) <= T) ++kmax;
+      f.kmax_t = kmax;
+    }
+    __syncthreads();
+    if (tid == 0) {
+      __threadfence();
+      atomicAdd(&ctl->departed, 1);
+    }
+
+    // ---- time pass: SumThreshold along t on the kept rows (Section 2.1)
+    if (f.time_on && nkeep > 0) {
+      const int PPw = round_up(T, SEG) + kPadWords;  // prefix entries per row (with slack)
+      const int PPp = PPw / 32 * 36;                  // padded words per row
+      const int nb = min(nkeep, kp.pfx_words / PPp);
+      if (nb < 1) {  // the host sizes the prefix buffer for every row length
+        if (tid == 0) set_error(kp, kErrInternal, 30);
+        break;
+      }
+      for (int b0 = 0; b0 < nkeep; b0 += nb) {
+        const int nbb = min(nb, nkeep - b0);
+        // prefix sums E[x] = sum_{t<x} P[t] (mod 2^32), padded layout
+        for (int task = warp; task < nbb * nseg; task += NW) {
+          const int rb = task / nseg, s = task - rb * nseg;
+          const int r = f.keep[b0 + rb];
+          const uint8_t* row = sdata + r * dpitch;
+          uint32_t* E = spfx + rb * PPp;
+          uint32_t off = 0;
+          for (int q = lane; q < s; q += kWarp) off += f.segsum[r * nseg + q];
+          uint32_t carry = warp_sum32(off);
+#pragma unroll
+          for (int q = 0; q < 2; ++q) {
+            const int x = s * SEG + q * 32 * VS + lane * VS;
+            uint32_t v[VS];
+            if (x < T) {
+              load_vec<DT>(row, x, T, v);
+            } else {
+#pragma unroll
+              for (int j = 0; j < VS; ++j) v[j] = 0u;
+            }
+            uint32_t e[VS];
+            uint32_t acc = 0;
+#pragma unroll
+            for (int j = 0; j < VS; ++j) {
+              e[j] = acc;
+              acc += v[j];
+            }
+            uint32_t tot;
+            const uint32_t ex = warp_excl_scan(acc, lane, &tot);
+            const uint32_t basev = carry + ex;
+#pragma unroll
+            for (int j = 0; j < VS; j += 4) {
+              uint4 w;
+              w.x = basev + e[j + 0];
+              w.y = basev + e[j + 1];
+              w.z = basev + e[j + 2];
+              w.w = basev + e[j + 3];
+              *reinterpret_cast<uint4*>(E + pidx(x + j)) = w;
+            }
+            carry += tot;
+          }
+          if (s == nseg - 1 && lane == 0) E[pidx(T)] = carry;
+        }
+        for (int i = tid; i < nbb * MW; i += NT) sfbits[i] = 0u;
+        __syncthreads();
+        for (int k = 0; k <= f.kmax_t; ++k) {
+          const int I = 1 << k;
+          const long long* Kt = f.K + koffset(k);
+          const long long K0l = Kt[0];
+          const uint32_t K0 = K0l >= 0xFFFFFFFFll ? 0xFFFFFFFFu : static_cast<uint32_t>(K0l);
+          const int rem = I - 1;
+          const uint32_t m1 = rem >= 32 ? 0xFFFFFFFFu : ((1u << rem) - 1u);
+          const uint32_t m2 = rem > 32 ? ((1u << (rem - 32)) - 1u) : 0u;
+          for (int c = tid; c < nbb * nch; c += NT) {
+            const int rb = c / nch, w = c - rb * nch, t0 = w << 5;
+            const int r = f.keep[b0 + rb];
+            const uint32_t* E = spfx + rb * PPp;
+            const uint32_t* M = smbits + r * MW + 2;
+            uint32_t* F = sfbits + rb * MW + 2;
+            const int nvalid = T - I + 1 - t0;
+            if (nvalid <= 0) {
+              F[w] = 0u;
+              continue;
+            }
+            const uint32_t vm = nvalid >= 32 ? 0xFFFFFFFFu : ((1u << nvalid) - 1u);
+            const uint32_t anyf = M[w] | (M[w + 1] & m1) | (M[w + 2] & m2);
+            const bool fast = (anyf == 0u) && (f.rowMax[r] < kFastMax);
+            uint32_t fire;
+            switch (k) {
+              case 0: fire = fire_chunk<1>(fast, E, M, t0, T, Kt, K0); break;
+              case 1: fire = fire_chunk<2>(fast, E, M, t0, T, Kt, K0); break;
+              case 2: fire = fire_chunk<4>(fast, E, M, t0, T, Kt, K0); break;
+              case 3: fire = fire_chunk<8>(fast, E, M, t0, T, Kt, K0); break;
+              case 4: fire = fire_chunk<16>(fast, E, M, t0, T, Kt, K0); break;
+              case 5: fire = fire_chunk<32>(fast, E, M, t0, T, Kt, K0); break;
+              default: fire = fire_chunk<64>(fast, E, M, t0, T, Kt, K0); break;
+            }
+            F[w] = fire & vm;
+          }
+          __syncthreads();
+          for (int c = tid; c < nbb * nch; c += NT) {
+            const int rb = c / nch, w = c - rb * nch;
+            const int r = f.keep[b0 + rb];
+            const uint32_t* F = sfbits + rb * MW + 2;
+            const uint32_t f0 = F[w], f1 = F[w - 1], f2 = F[w - 2];
+            if ((f0 | f1 | f2) == 0u) continue;
+            uint32_t D;
+            if (I <= 32) D = dilate32(f0, f1, I);
+            else D = dilate32(f0, f1, 32) | dilate32(f1, f2, 32);
+            smbits[r * MW + 2 + w] |= D;
+          }
+          __syncthreads();
+        }
+      }
+      // flagged counts and flagged power of every kept row
+      for (int c = tid; c < nkeep * nch; c += NT) {
+        const int kr = c / nch, w = c - kr * nch;
+        const int r = f.keep[kr];
+        uint32_t m = smbits[r * MW + 2 + w];
+        if (m) {
+          const uint8_t* row = sdata + r * dpitch;
+          unsigned long long fs = 0;
+          const int cnt = __popc(m);
+          while (m) {
+            const int j = __ffs(m) - 1;
+            m &= m - 1u;
+            fs += TR::at(row, (w << 5) + j);
+          }
+          atomicAdd(&f.rowNFlag[r], cnt);
+          atomicAdd(&f.rowFlagSum[r], fs);
+        }
+      }
+      __syncthreads();
+    }
+
+    // ---- history flagger (Section 4.1) and per-row counts
+    for (int r = tid; r < R; r += NT) {
+      const long long h = u.hist_slot >= 0 ? u.hist_slot + row0 + r : -1;
+      unsigned long long add_total;
+      if (f.rowFc[r]) {
+        if (h >= 0) kp.hist.pend_flag[h] = 0;
+        add_total = static_cast<unsigned long long>(T);
+      } else {
+        const int nfl = f.rowNFlag[r];
+        const int n = T - nfl;
+        uint8_t fh = 0;
+        if (n > 0) {
+          const unsigned long long su = f.rowS[r] - f.rowFlagSum[r];
+          const double cur = __ddiv_rn(__ull2double_rn(su), static_cast<double>(n));
+          double staged = cur;
+          if (kp.enable_history && h >= 0) {
+            const int cnt = kp.hist.count[h];
+            if (cnt >= kp.history_min && cnt > 0) {
+              const double thr = kp.hist.thr[h];
+              if (!(cur < thr)) {
+                fh = 1;
+                staged = thr;
+              }
+            }
+          }
+          if (h >= 0) {
+            kp.hist.pend[h] = staged;
+            kp.hist.pend_flag[h] = 1;
+            kp.hist.pend_seq[h] = kp.block_seq;
+          }
+        } else if (h >= 0) {
+          kp.hist.pend_flag[h] = 0;
+        }
+        f.rowFh[r] = fh;
+        atomicAdd(&f.cnt_time, static_cast<unsigned long long>(nfl));
+        if (fh) atomicAdd(&f.cnt_hist, 1ull);
+        add_total = fh ? static_cast<unsigned long long>(T) : static_cast<unsigned long long>(nfl);
+      }
+      atomicAdd(&f.cnt_total, add_total);
+    }
+    __syncthreads();
+
+    // ---- apply: mask bytes, zeroed data (Sections 3 and 4)
+    const bool inplace = (u.flags & kUnitInPlace) != 0;
+    const bool mask_vec = (u.flags & kUnitMaskVec) != 0;
+    for (int c = tid; c < R * nch; c += NT) {
+      const int r = c / nch, w = c - r * nch, t0 = w << 5;
+      const int nv = min(32, T - t0);
+      const uint32_t vm = nv >= 32 ? 0xFFFFFFFFu : ((1u << nv) - 1u);
+      const bool full = f.rowFc[r] || f.rowFh[r];
+      const uint32_t bits = full ? vm : (smbits[r * MW + 2 + w] & vm);
+      if (u.mask) {
+        uint8_t* mrow = u.mask + static_cast<int64_t>(row0 + r) * u.mask_stride;
+        if (mask_vec && nv == 32) {
+          uint32_t wd[8];
+#pragma unroll
+          for (int q = 0; q < 8; ++q) wd[q] = (((bits >> (4 * q)) & 0xFu) * 0x00204081u) & 0x01010101u;
+          uint4* dst = reinterpret_cast<uint4*>(mrow + t0);
+          dst[0] = make_uint4(wd[0], wd[1], wd[2], wd[3]);
+          dst[1] = make_uint4(wd[4], wd[5], wd[6], wd[7]);
+        } else {
+          for (int j = 0; j < nv; ++j) mrow[t0 + j] = static_cast<uint8_t>((bits >> j) & 1u);
+        }
+      }
+      if (u.out && bits) {
+        if (inplace) {
+          uint8_t* orow =
+              static_cast<uint8_t*>(u.out) + static_cast<int64_t>(row0 + r) * u.out_stride * TR::kBytes;
+          uint32_t m = bits;
+          while (m) {
+            const int j = __ffs(m) - 1;
+            m &= m - 1u;
+            TR::zero(orow, t0 + j);
+          }
+        } else {
+          uint8_t* srow = sdata + r * dpitch;
+          uint32_t m = bits;
+          while (m) {
+            const int j = __ffs(m) - 1;
+            m &= m - 1u;
+            TR::zero(srow, t0 + j);
+          }
+        }
+      }
+    }
+    __syncthreads();
+    if (u.out && !inplace) {
+      if (u.flags & kUnitOutBulk) {
+        fence_async_smem();
+        __syncthreads();
+        if (tid == 0) {
+          uint8_t* gout = static_cast<uint8_t*>(u.out);
+          for (int r = 0; r < R; ++r)
+            bulk_store(gout + (row0 + r) * u.out_stride * TR::kBytes, sdata + r * dpitch,
+                       static_cast<uint32_t>(T * TR::kBytes));
+          bulk_commit();
+        }
+      } else {
+        uint8_t* gout = static_cast<uint8_t*>(u.out);
+        for (int r = 0; r < R; ++r)
+          for (int t = tid; t < T; t += NT)
+            TR::copy(gout + ((row0 + r) * u.out_stride + t) * TR::kBytes,
+                     sdata + r * dpitch + t * TR::kBytes);
+      }
+    }
+    if (tid == 0 && u.stats) {
+      atomicAdd(reinterpret_cast<unsigned long long*>(&u.stats->n_flag_time), f.cnt_time);
+      atomicAdd(reinterpret_cast<unsigned long long*>(&u.stats->n_chan_hist), f.cnt_hist);
+      atomicAdd(reinterpret_cast<unsigned long long*>(&u.stats->n_flag_total), f.cnt_total);
+    }
+    __syncthreads();
+  }
+  if (tid == 0) bulk_wait_all();
+}
+
+// ------------------------------------------------------------------ history commit
+// Section 4.1: add each staged value to its channel's ring and refresh the
+// cached threshold mean + k * stddev (population, oldest -> newest, binary64
+// without contraction).
+__global__ void lof_commit_kernel(const CommitParams cp, int total, int refresh_only) {
+  const int g = blockIdx.x * blockDim.x + threadIdx.x;
+  if (g >= total) return;
+  int a = 0, b = cp.n_units;  // unit with chan_off <= g
+  while (b - a > 1) {
+    const int m = (a + b) >> 1;
+    if (cp.units[m].chan_off <= g) a = m;
+    else b = m;
+  }
+  const DevUnit& u = cp.units[a];
+  const int c = g - u.chan_off;
+  if (c < 0 || c >= u.C || u.hist_slot < 0) return;
+  const long long h = u.hist_slot + c;
+  const HistoryDev& H = cp.hist;
+  int cnt = H.count[h];
+  int head = H.head[h];
+  if (!refresh_only) {
+    if (!H.pend_flag[h]) return;
+    H.vals[h * H.H + head] = H.pend[h];
+    head = (head + 1) % H.H;
+    cnt = min(cnt + 1, H.H);
+    H.head[h] = head;
+    H.count[h] = cnt;
+    H.pend_flag[h] = 0;
+  }
+  if (cnt <= 0) {
+    H.thr[h] = 0.0;
+    return;
+  }
+  const int oldest = (head - cnt + H.H) % H.H;
+  double s = 0.0;
+  for (int i = 0; i < cnt; ++i) s = __dadd_rn(s, H.vals[h * H.H + (oldest + i) % H.H]);
+  const double mu = __ddiv_rn(s, static_cast<double>(cnt));
+  double q = 0.0;
+  for (int i = 0; i < cnt; ++i) {
+    const double d = __dsub_rn(H.vals[h * H.H + (oldest + i) % H.H], mu);
+    q = __dadd_rn(q, __dmul_rn(d, d));
+  }
+  const double sd = __dsqrt_rn(__ddiv_rn(q, static_cast<double>(cnt)));
+  H.thr[h] = __dadd_rn(mu, __dmul_rn(cp.history_k, sd));
+}
+
+template <int DT, int NT>
+void* kernel_ptr() {
+  return reinterpret_cast<void*>(&lof_block_kernel<DT, NT>);
+}
+
+void* pick_kernel(int dtype, int threads) {
+  if (dtype == LOF_CI16) {
+    if (threads == 256) return kernel_ptr<LOF_CI16, 256>();
+    if (threads == 512) return kernel_ptr<LOF_CI16, 512>();
+  } else if (dtype == LOF_CI8) {
+    if (threads == 256) return kernel_ptr<LOF_CI8, 256>();
+    if (threads == 512) return kernel_ptr<LOF_CI8, 512>();
+  }
+  return nullptr;
+}
+
+}  // namespace
+}  // namespace lofk
+
+using namespace lofk;
+
+extern "C" int lofk_set_smem_limit(int dtype, int smem_bytes) {
+  for (int t : {256, 512}) {
+    void* k = pick_kernel(dtype, t);
+    if (!k) return -1;
+    if (cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_bytes) !=
+        cudaSuccess)
+      return -2;
+  }
+  return 0;
+}
+
+extern "C" int lofk_max_blocks_per_sm(int dtype, int threads, int smem_bytes, int* out) {
+  void* k = pick_kernel(dtype, threads);
+  if (!k) return -1;
+  if (cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_bytes) !=
+      cudaSuccess)
+    return -2;
+  int n = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k, threads, smem_bytes) != cudaSuccess)
+    return -3;
+  *out = n;
+  return 0;
+}
+
+extern "C" int lofk_launch_block(int dtype, const KParams* kp, int grid, int threads,
+                                 int smem_bytes, void* stream, int cooperative) {
+  void* k = pick_kernel(dtype, threads);
+  if (!k) return -1;
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(static_cast<unsigned>(grid));
+  cfg.blockDim = dim3(static_cast<unsigned>(threads));
+  cfg.dynamicSmemBytes = static_cast<size_t>(smem_bytes);
+  cfg.stream = static_cast<cudaStream_t>(stream);
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeCooperative;
+  attr[0].val.cooperative = cooperative ? 1 : 0;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  void* args[] = {const_cast<KParams*>(kp)};
+  const cudaError_t e = cudaLaunchKernelExC(&cfg, k, args);
+  return e == cudaSuccess ? 0 : static_cast<int>(e);
+}
+
+extern "C" int lofk_launch_commit(const CommitParams* cp, int total_channels, void* stream) {
+  if (total_channels <= 0) return 0;
+  const int bs = 256;
+  const int grid = (total_channels + bs - 1) / bs;
+  lof_commit_kernel<<<grid, bs, 0, static_cast<cudaStream_t>(stream)>>>(*cp, total_channels, 0);
+  const cudaError_t e = cudaGetLastError();
+  return e == cudaSuccess ? 0 : static_cast<int>(e);
+}
+
+extern "C" int lofk_launch_refresh(const CommitParams* cp, int total_channels, void* stream) {
+  if (total_channels <= 0) return 0;
+  const int bs = 256;
+  const int grid = (total_channels + bs - 1) / bs;
+  lof_commit_kernel<<<grid, bs, 0, static_cast<cudaStream_t>(stream)>>>(*cp, total_channels, 1);
+  const cudaError_t e = cudaGetLastError();
+  return e == cudaSuccess ? 0 : static_cast<int>(e);
+}
