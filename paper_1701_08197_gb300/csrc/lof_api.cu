@@ -65,6 +65,12 @@ struct lof_ctx {
   size_t cap_chan = 0, cap_chanfc = 0;
   Slot* d_slots = nullptr;
   size_t cap_slots = 0;
+  uint32_t* d_pub = nullptr;
+  size_t cap_pub = 0;
+  unsigned long long* d_pubm = nullptr;
+  size_t cap_pubm = 0;
+  int* d_members = nullptr;
+  size_t cap_members = 0;
   int* d_ctrl = nullptr;  // [0] queue, [1] error, [2..3] error detail
   int* h_err = nullptr;   // pinned copy of d_ctrl[1..3]
   cudaEvent_t ev_err = nullptr;
@@ -151,9 +157,12 @@ int static_smem_bytes(int dtype, int threads) {
   return 7 * 1024 + (threads / 32) * 32;
 }
 
+// words of the time-pass buffer per row: padded chunk-local prefixes of
+// nch + 3 chunks (36 words each), chunk bases and chunk totals
 int pfx_row_words(int dtype, int T) {
-  const int64_t PPw = round_up64(T, seg_of(dtype)) + lofk::kPadWords;
-  return static_cast<int>(PPw / 32 * 36);
+  (void)dtype;
+  const int nch = (T + 31) / 32;
+  return ((nch + 3) * 36 + 2 * (nch + 4) + 3) & ~3;  // 16-byte aligned rows
 }
 
 int dpitch_of(int dtype, int T) {
@@ -171,8 +180,6 @@ int rows_per_item(int dtype, int T, int tile) {
   const int dp = dpitch_of(dtype, T);
   int R = tile / dp;
   R = std::min(R, lofk::kMaxRowsPerItem);
-  const int nseg = (T + seg_of(dtype) - 1) / seg_of(dtype);
-  R = std::min(R, 256 / std::max(1, nseg));
   return R;
 }
 
@@ -300,6 +307,9 @@ extern "C" int lof_destroy(lof_ctx* c) {
   cudaFree(c->d_chanS);
   cudaFree(c->d_chanFc);
   cudaFree(c->d_slots);
+  cudaFree(c->d_pub);
+  cudaFree(c->d_pubm);
+  cudaFree(c->d_members);
   cudaFree(c->d_ctrl);
   cudaFree(c->d_io);
   if (c->h_err) cudaFreeHost(c->h_err);
@@ -466,6 +476,10 @@ int flag_block_device(lof_ctx* c, int dtype, const lof_unit* units, int n_units,
   if ((rc = grow(c, &c->d_chanS, &c->cap_chan, static_cast<size_t>(chan), "spectrum"))) return rc;
   if ((rc = grow(c, &c->d_chanFc, &c->cap_chanfc, static_cast<size_t>(chan), "channel flags"))) return rc;
   if ((rc = grow(c, &c->d_slots, &c->cap_slots, static_cast<size_t>(grid), "slots"))) return rc;
+  if ((rc = grow(c, &c->d_pub, &c->cap_pub, static_cast<size_t>(grid) * lofk::kCoarseBins, "histograms")))
+    return rc;
+  if ((rc = grow(c, &c->d_pubm, &c->cap_pubm, static_cast<size_t>(grid) * 4, "moments"))) return rc;
+  if ((rc = grow(c, &c->d_members, &c->cap_members, static_cast<size_t>(n_items), "members"))) return rc;
   // stage descriptors (pinned ring)
   const size_t bytes_units = n_units * sizeof(DevUnit);
   const size_t bytes_items = n_items * sizeof(Item);
@@ -502,6 +516,9 @@ int flag_block_device(lof_ctx* c, int dtype, const lof_unit* units, int n_units,
   kp.chan_S = c->d_chanS;
   kp.chan_Fc = c->d_chanFc;
   kp.slots = c->d_slots;
+  kp.pub = c->d_pub;
+  kp.pubm = c->d_pubm;
+  kp.members = c->d_members;
   kp.queue = c->d_ctrl;
   kp.err = c->d_ctrl + 1;
   kp.err_info = c->d_ctrl + 2;

@@ -8,9 +8,9 @@
 
 namespace lofk {
 
-// Coarse histogram of 32-bit keys: values < 32 get their own bin, larger
-// values 32 bins per octave (bin width at most 1/32 of the value).
-constexpr int kCoarseBins = 896;
+// Coarse histogram of 32-bit keys: the exponent and 5 mantissa bits of the
+// value as binary32 (32 bins per octave, one per integer below 64).
+constexpr int kCoarseBins = 1056;
 constexpr int kMaxLogWindow = 6;             // windows 1 .. 64
 constexpr int kKTable = 134;                 // sum_{k=0..6} (2^k + 1) threshold entries
 constexpr int kMaxChan = 2048;               // channels per unit
@@ -20,8 +20,6 @@ constexpr int kMaxFine = 2048;               // counters per refinement round (u
 constexpr int kSelCap = 2560;                // bin-list capacity for exact selection
 constexpr int kMaxRounds = 12;               // refinement rounds before giving up
 constexpr int kWorkspaceBytes = 36 * 1024;   // last-arriver workspace (overlays the prefix buffer)
-constexpr int kPadWords = 96;                // prefix-row slack beyond the row (window lookahead)
-constexpr uint32_t kFastMax = 1u << 26;      // 64 * max power < 2^32: 32-bit window sums exact
 
 // device error codes (written to the context's mapped error word)
 enum : int {
@@ -121,6 +119,9 @@ struct KParams {
   unsigned long long* chan_S;   // per channel spectrum sums
   uint8_t* chan_Fc;             // per channel frequency flags
   Slot* slots;
+  uint32_t* pub;                // [grid][kCoarseBins] coarse histogram of each CTA's rows
+  unsigned long long* pubm;     // [grid][4] moments of each CTA's rows (128-bit s1, s2)
+  int* members;                 // [n_items] CTA that holds each item
   int* queue;                   // [0] next item
   int* err;                     // first device-side error (0 = none)
   int* err_info;                // detail words of that error

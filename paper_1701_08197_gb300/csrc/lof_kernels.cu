@@ -171,21 +171,28 @@ __device__ __forceinline__ void load_vec(const uint8_t* row, int x, int T,
 
 // ------------------------------------------------------------------ small helpers
 
-// Coarse key of a 32-bit value: exact below 32, then 32 bins per octave.
+// Coarse key of a 32-bit value: the top bits of its binary32 value rounded
+// toward zero (exponent and 5 mantissa bits), i.e. 32 bins per octave and
+// one bin per integer below 64.  Key 0 holds the value 0; keys 1..31 are
+// empty; the largest key is 1055.
+constexpr int kKeyBias = 4032;  // (127 - 1) << 5
 __device__ __forceinline__ uint32_t coarse_key(uint32_t v) {
-  if (v < 32u) return v;
-  const uint32_t e = 31u - __clz(v);
-  return ((e - 4u) << 5) | ((v >> (e - 5u)) & 31u);
+  const int k = static_cast<int>(__float_as_uint(__uint2float_rz(v)) >> 18) - kKeyBias;
+  return static_cast<uint32_t>(max(k, 0));
 }
-__device__ __forceinline__ uint32_t coarse_lo(uint32_t k) {
-  if (k < 32u) return k;
-  const uint32_t e = (k >> 5) + 4u;
-  return (32u + (k & 31u)) << (e - 5u);
+// Smallest integer v with coarse_key(v) >= k (k >= 1); 2^32 for k = 1056.
+__device__ __forceinline__ unsigned long long key_floor(uint32_t k) {
+  const float fv = __uint_as_float((k + static_cast<uint32_t>(kKeyBias)) << 18);
+  return static_cast<unsigned long long>(ceil(static_cast<double>(fv)));
 }
-__device__ __forceinline__ uint32_t coarse_hi(uint32_t k) {
-  if (k < 32u) return k;
-  const uint32_t e = (k >> 5) + 4u;
-  return coarse_lo(k) + ((1u << (e - 5u)) - 1u);
+// Integer range [lo, hi] of key k; false when the key holds no integer.
+__device__ __forceinline__ bool key_range(uint32_t k, uint32_t* lo, uint32_t* hi) {
+  const unsigned long long a = (k == 0) ? 0ull : key_floor(k);
+  const unsigned long long b = key_floor(k + 1);
+  if (a >= b) return false;
+  *lo = static_cast<uint32_t>(a);
+  *hi = static_cast<uint32_t>(b - 1ull);
+  return true;
 }
 
 // Index of prefix entry x in the padded prefix layout (4 spare words after
@@ -241,29 +248,31 @@ __device__ double moments_std(long long n, unsigned __int128 s1, unsigned __int1
   return __dsqrt_rn(__ddiv_rn(u128_to_double(M), nn));
 }
 
-// Section 2.1: threshold_I = median + stddev * factor_I * sensitivity and the
-// integer table K[n] = floor((I - n) * threshold_I), n = 0..I, for I = 2^k.
+__device__ __forceinline__ int koffset(int k) { return (1 << k) + k - 1; }  // sum_{j<k}(2^j+1)
+
+// Section 2.1: threshold_I = median + stddev * factor_I * sensitivity and its
+// integer table K[n] = floor((I - n) * threshold_I), n = 0..I, for I = 2^k,
+// k <= kmax; one entry per thread of the calling CTA (no barrier inside).
+template <int NT>
 __device__ void fill_ktable(const KParams& kp, double median, double sigma, int kmax,
                             long long* K) {
-  int off = 0;
-  for (int k = 0; k <= kmax; ++k) {
-    const int I = 1 << k;
+  const int total = koffset(kmax + 1);
+  for (int e = threadIdx.x; e < total; e += NT) {
+    int k = 0;
+    while (koffset(k + 1) <= e) ++k;
+    const int I = 1 << k, n = e - koffset(k);
     const double thr =
         __dadd_rn(median, __dmul_rn(__dmul_rn(sigma, kp.factor[k]), kp.sensitivity));
-    for (int n = 0; n <= I; ++n) {
-      const double lim = __dmul_rn(static_cast<double>(I - n), thr);
-      long long q;
-      if (!(lim == lim)) q = (1ll << 62);  // NaN threshold: never fires
-      else if (lim >= 4.0e18) q = (1ll << 62);
-      else if (lim <= -4.0e18) q = -(1ll << 62);
-      else q = __double2ll_rd(lim);
-      K[off + n] = q;
-    }
-    off += I + 1;
+    const double lim = __dmul_rn(static_cast<double>(I - n), thr);
+    long long q;
+    if (!(lim == lim)) q = (1ll << 62);  // NaN threshold: never fires
+    else if (lim >= 4.0e18) q = (1ll << 62);
+    else if (lim <= -4.0e18) q = -(1ll << 62);
+    else q = __double2ll_rd(lim);
+    K[e] = q;
   }
 }
 
-__device__ __forceinline__ int koffset(int k) { return (1 << k) + k - 1; }  // sum_{j<k}(2^j+1)
 
 __device__ void set_error(const KParams& kp, int code, int info) {
   if (atomicCAS(kp.err, 0, code) == 0) {
@@ -338,14 +347,13 @@ struct Fixed {
   unsigned int red_u32[NT / kWarp];
   unsigned long long red_a[NT / kWarp], red_b[NT / kWarp], red_c[NT / kWarp];
   unsigned long long cnt_time, cnt_total, cnt_hist;
+  unsigned long long mo1, mo2lo, mo2hi;  // moments of this CTA's rows
   unsigned long long rowS[kMaxRowsPerItem];
   unsigned long long rowFlagSum[kMaxRowsPerItem];
-  uint32_t rowMax[kMaxRowsPerItem];
   int rowNFlag[kMaxRowsPerItem];
   uint8_t rowFc[kMaxRowsPerItem];
   uint8_t rowFh[kMaxRowsPerItem];
   int keep[kMaxRowsPerItem];
-  uint32_t segsum[256];
   long long K[kKTable];
   double median_t, sigma_t;
   int time_on, kmax_t;
@@ -371,8 +379,8 @@ __device__ void frequency_pass(const KParams& kp, const DevUnit& u, Slot* slot, 
   while (n2 < C) n2 <<= 1;
   unsigned long long* srt = reinterpret_cast<unsigned long long*>(ws);  // kMaxChan
   unsigned long long* Sv = srt + kMaxChan;                               // kMaxChan
-  uint8_t* Fc = reinterpret_cast<uint8_t*>(Sv + kMaxChan);               // kMaxChan
-  uint8_t* fire = Fc + kMaxChan;                                         // kMaxChan
+  uint8_t* fire = reinterpret_cast<uint8_t*>(Sv + kMaxChan);             // kMaxChan
+  uint8_t* Fc = fire + kMaxChan;                                         // kMaxChan (kept after)
   const unsigned long long* gS = kp.chan_S + u.chan_off;
   for (int i = tid; i < n2; i += NT) {
     unsigned long long v = ~0ull;
@@ -420,8 +428,9 @@ __device__ void frequency_pass(const KParams& kp, const DevUnit& u, Slot* slot, 
     int kmax = 0;
     while (kmax < kp.max_log_window && (2 << kmax) <= C) ++kmax;
     f.kmax_f = kmax;
-    fill_ktable(kp, med, sig, kmax, f.K);
   }
+  __syncthreads();
+  fill_ktable<NT>(kp, __dmul_rn(__ull2double_rn(M2), 0.5), f.sig, f.kmax_f, f.K);
   __syncthreads();
   const double sig = f.sig;
   const int kmax = f.kmax_f;
@@ -619,14 +628,12 @@ __device__ __forceinline__ int bin_of_rank(const BinList& B, long long r) {
 template <int NT>
 __device__ void finalize_stats(const KParams& kp, const DevUnit& u, Slot* slot, double median,
                                double sigma) {
+  int kmax = 0;
+  while (kmax < kp.max_log_window && (2 << kmax) <= u.T) ++kmax;
+  fill_ktable<NT>(kp, median, sigma, kmax, slot->K);
   if (threadIdx.x == 0) {
     slot->median_t = median;
     slot->sigma_t = sigma;
-    int kmax = 0;
-    while (kmax < kp.max_log_window && (2 << kmax) <= u.T) ++kmax;
-    long long K[kKTable];
-    fill_ktable(kp, median, sigma, kmax, K);
-    for (int i = 0; i < kKTable; ++i) slot->K[i] = K[i];
     slot->time_on = (kp.enable_time && sigma > 0.0) ? 1 : 0;
     slot->state = kStateDone;
     if (u.stats) {
@@ -661,18 +668,22 @@ __device__ void select_plan(const KParams& kp, const DevUnit& u, Slot* slot, con
   }
   __syncthreads();
   const long long m2lo = f.m2lo, m2hi = f.m2hi;
-  if (tid < kWarp) {
+  {
+    // warps 0..3: lower / upper bracket of the MAD rank(s), one search each
+    const int warp = tid >> 5;
     const int nr = (N & 1) ? 1 : 2;
-    for (int q = 0; q < nr; ++q) {
+    if (warp < 2 * nr) {
+      const int q = warp >> 1;
       const long long r = (N & 1) ? (N - 1) / 2 : N / 2 - 1 + q;
-      const long long da = warp_search<true>(B, m2lo, m2hi, r + 1, lane);
-      const long long db = warp_search<false>(B, m2lo, m2hi, r + 1, lane);
+      const long long d = (warp & 1) ? warp_search<false>(B, m2lo, m2hi, r + 1, lane)
+                                     : warp_search<true>(B, m2lo, m2hi, r + 1, lane);
       if (lane == 0) {
-        f.da[q] = da;
-        f.db[q] = db;
+        if (warp & 1) f.db[q] = d;
+        else f.da[q] = d;
       }
     }
-    if (nr == 1 && lane == 0) {
+    __syncthreads();
+    if (tid == 0 && nr == 1) {
       f.da[1] = f.da[0];
       f.db[1] = f.db[0];
     }
@@ -780,28 +791,49 @@ __device__ void select_plan(const KParams& kp, const DevUnit& u, Slot* slot, con
   }
 }
 
-// Builds the initial bin list from the coarse histogram (warp 0).
+// Builds the initial bin list from a coarse histogram in shared memory (warp
+// 0): non-empty keys in order, straight into the shared-memory list (lo, hi,
+// cumulative counts) and into the slot for later refinement rounds.
 template <int NT>
-__device__ void build_coarse_list(Slot* slot) {
+__device__ BinList build_coarse_list(const KParams& kp, Slot* slot, const uint32_t* hist,
+                                     uint8_t* ws) {
+  uint32_t* lo = reinterpret_cast<uint32_t*>(ws);
+  uint32_t* hi = lo + kSelCap;
+  uint32_t* cum = hi + kSelCap;
   const int tid = threadIdx.x;
+  __shared__ int s_n;
   if (tid < kWarp) {
     int n = 0;
+    uint32_t carry = 0;
+    if (tid == 0) cum[0] = 0;
     for (int base = 0; base < kCoarseBins; base += kWarp) {
       const int k = base + tid;
-      const uint32_t c = __ldcg(slot->coarse + k);
-      const unsigned bal = __ballot_sync(0xFFFFFFFFu, c != 0u);
-      if (c) {
+      const uint32_t c = k < kCoarseBins ? hist[k] : 0u;
+      uint32_t a = 0, b = 0;
+      const bool ok = c != 0u && key_range(static_cast<uint32_t>(k), &a, &b);
+      if (c != 0u && !ok) set_error(kp, kErrInternal, 40);
+      const unsigned bal = __ballot_sync(0xFFFFFFFFu, ok);
+      uint32_t tot;
+      const uint32_t ex = warp_excl_scan(ok ? c : 0u, tid, &tot);
+      if (ok) {
         const int pos = n + __popc(bal & ((1u << tid) - 1u));
-        slot->blo[pos] = coarse_lo(k);
-        slot->bhi[pos] = coarse_hi(k);
+        lo[pos] = a;
+        hi[pos] = b;
+        cum[pos + 1] = carry + ex + c;
+        slot->blo[pos] = a;
+        slot->bhi[pos] = b;
         slot->bcnt[pos] = c;
       }
       n += __popc(bal);
+      carry += tot;
     }
-    if (tid == 0) slot->n_bins = n;
+    if (tid == 0) {
+      slot->n_bins = n;
+      s_n = n;
+    }
   }
-  __threadfence_block();
   __syncthreads();
+  return BinList{lo, hi, cum, s_n};
 }
 
 // Replaces every refined bin by its non-empty sub-bins.
@@ -893,89 +925,137 @@ __device__ void merge_fine(const KParams& kp, Slot* slot, uint8_t* ws, Fixed<NT>
 }
 
 // ------------------------------------------------------------------ time pass helpers
+//
+// Layout of one batch of rows in the prefix buffer (32-bit words per row):
+//   Pl: (nch + 3) chunks x 36 words -- exclusive prefix, inside each 32-sample
+//       chunk, of the values u (padded layout, see pidx); three zero chunks
+//       follow the row so windows may look ahead by up to 64 samples
+//   Pb: nch + 4 words -- exclusive prefix of the chunk totals (chunk bases)
+//   Tc: nch + 4 words -- chunk totals
+// so that the prefix of u at x is Pb[x >> 5] + Pl[pidx(x)] (mod 2^32).
+//
+// Packed path (integer units whose I = 1 threshold is below 2^20): after the
+// I = 1 pass every unflagged power is at most floor(threshold_1), so a window
+// of up to 64 unflagged values sums to less than Z = 2^26.  Flagged samples
+// are stored as u = Z: the difference of two prefix entries is then
+// S = n_flagged * Z + sum_unflagged with both parts recoverable.  Each window
+// is judged in three integer operations: Q = S + (S >> 26) * (tau - Z) =
+// sum_unflagged + n_flagged * tau, the Section 2.1 sum with flagged samples
+// counted as tau >= threshold_I + 2.  Q <= K[0] proves that the window does
+// not fire; only chunks holding a larger Q are judged exactly against
+// Kp[n] = n * Z + floor((I - n) * threshold_I).
 
-// Window sums of one 32-sample chunk from the prefix row E (fast path: no
-// flagged sample in reach, all window sums < 2^32).  Bit j: window at t0 + j
-// exceeds K0.
-template <int I>
-__device__ __forceinline__ uint32_t fast_fire(const uint32_t* E, int t0, uint32_t K0) {
-  uint32_t a[32], b[32];
-  const uint4* pa = reinterpret_cast<const uint4*>(E + pidx(t0));
+constexpr uint32_t kZ = 1u << 26;
+
+struct StLayout {
+  int PLW, PBW, per_row;
+};
+__device__ __forceinline__ StLayout st_layout(int nch) {
+  StLayout L;
+  L.PLW = (nch + 3) * 36;
+  L.PBW = nch + 4;
+  L.per_row = (L.PLW + 2 * L.PBW + 3) & ~3;  // rows start on 16-byte boundaries
+  return L;
+}
+
+__device__ __forceinline__ void load32(const uint32_t* p, uint32_t (&a)[32]) {
 #pragma unroll
   for (int q = 0; q < 8; ++q) {
-    const uint4 w = pa[q];
+    const uint4 w = reinterpret_cast<const uint4*>(p)[q];
     a[4 * q + 0] = w.x;
     a[4 * q + 1] = w.y;
     a[4 * q + 2] = w.z;
     a[4 * q + 3] = w.w;
   }
+}
+
+// Fire bits of the 32 windows of size I starting in chunk w (packed path).
+// S[j] = prefix(t0 + j + I) - prefix(t0 + j) is formed in place.
+template <int I>
+__device__ __forceinline__ uint32_t packed_fire(const uint32_t* pl, const uint32_t* pb, int w,
+                                                uint32_t K0, uint32_t cq, const uint32_t* Kp) {
+  uint32_t S[32];
+  const uint32_t base0 = pb[w];
   if constexpr (I >= 32) {
-    const uint4* pb = reinterpret_cast<const uint4*>(E + pidx(t0 + I));
+    const int w2 = w + I / 32;
+    load32(pl + pidx(w2 << 5), S);
+    const uint32_t dB = pb[w2] - base0;
+    const uint4* pa = reinterpret_cast<const uint4*>(pl + pidx(w << 5));
 #pragma unroll
     for (int q = 0; q < 8; ++q) {
-      const uint4 w = pb[q];
-      b[4 * q + 0] = w.x;
-      b[4 * q + 1] = w.y;
-      b[4 * q + 2] = w.z;
-      b[4 * q + 3] = w.w;
+      const uint4 v = pa[q];
+      S[4 * q + 0] += dB - v.x;
+      S[4 * q + 1] += dB - v.y;
+      S[4 * q + 2] += dB - v.z;
+      S[4 * q + 3] += dB - v.w;
     }
   } else {
-#pragma unroll
-    for (int j = 0; j < 32 - I; ++j) b[j] = a[j + I];
-    const uint32_t* pn = E + pidx(t0 + 32);
+    load32(pl + pidx(w << 5), S);
+    const uint32_t d1 = pb[w + 1] - base0;
+    const uint32_t* pn = pl + pidx((w + 1) << 5);
+    uint32_t t[I < 4 ? 4 : I];
     if constexpr (I >= 4) {
 #pragma unroll
       for (int q = 0; q < I / 4; ++q) {
-        const uint4 w = reinterpret_cast<const uint4*>(pn)[q];
-        b[32 - I + 4 * q + 0] = w.x;
-        b[32 - I + 4 * q + 1] = w.y;
-        b[32 - I + 4 * q + 2] = w.z;
-        b[32 - I + 4 * q + 3] = w.w;
+        const uint4 v = reinterpret_cast<const uint4*>(pn)[q];
+        t[4 * q + 0] = v.x;
+        t[4 * q + 1] = v.y;
+        t[4 * q + 2] = v.z;
+        t[4 * q + 3] = v.w;
       }
     } else if constexpr (I == 2) {
-      const uint2 w = *reinterpret_cast<const uint2*>(pn);
-      b[30] = w.x;
-      b[31] = w.y;
+      const uint2 v = *reinterpret_cast<const uint2*>(pn);
+      t[0] = v.x;
+      t[1] = v.y;
     } else {
-      b[31] = pn[0];
+      t[0] = pn[0];
     }
+#pragma unroll
+    for (int j = 0; j < 32 - I; ++j) S[j] = S[j + I] - S[j];
+#pragma unroll
+    for (int j = 32 - I; j < 32; ++j) S[j] = t[j + I - 32] + d1 - S[j];
   }
   uint32_t mx = 0;
 #pragma unroll
-  for (int j = 0; j < 32; ++j) mx = max(mx, b[j] - a[j]);
+  for (int j = 0; j < 32; ++j) mx = max(mx, S[j] + (S[j] >> 26) * cq);
   if (mx <= K0) return 0u;
   uint32_t fire = 0;
 #pragma unroll
-  for (int j = 0; j < 32; ++j) fire |= ((b[j] - a[j]) > K0 ? 1u : 0u) << j;
+  for (int j = 0; j < 32; ++j) fire |= (S[j] > Kp[S[j] >> 26] ? 1u : 0u) << j;
   return fire;
 }
 
 __device__ __forceinline__ uint32_t bit_at(const uint32_t* M, int j) {
   return (M[j >> 5] >> (j & 31)) & 1u;
 }
-__device__ __forceinline__ uint32_t val_at(const uint32_t* E, int j) {
-  return E[pidx(j + 1)] - E[pidx(j)];  // single-sample difference: exact mod 2^32
+__device__ __forceinline__ uint32_t pre_at(const uint32_t* pl, const uint32_t* pb, int x) {
+  return pb[x >> 5] + pl[pidx(x)];
 }
 
-// General path: exact 64-bit window sums with flagged samples substituted,
-// sliding across the chunk.  Compares sum_unflagged > K[n_flagged].
-__device__ uint32_t slow_fire(const uint32_t* E, const uint32_t* M, int t0, int I, int T,
-                              const long long* Kt) {
+// General path (any integer magnitudes): exact 64-bit sums of the unflagged
+// values of each window, sliding across the chunk; fires when
+// sum_unflagged > K[n_flagged].  Values are single prefix differences,
+// exact modulo 2^32.
+__device__ uint32_t general_fire(const uint32_t* pl, const uint32_t* pb, const uint32_t* M,
+                                 int t0, int I, int T, const long long* Kt) {
   const int tl = min(t0 + 31, T - I);
   unsigned long long su = 0;
   int nf = 0;
+  uint32_t prev = pre_at(pl, pb, t0);
   for (int j = t0; j < t0 + I; ++j) {
+    const uint32_t nx = pre_at(pl, pb, j + 1);
     if (bit_at(M, j)) ++nf;
-    else su += val_at(E, j);
+    else su += nx - prev;
+    prev = nx;
   }
   uint32_t fire = 0;
   for (int t = t0;; ++t) {
     if (static_cast<long long>(su) > Kt[nf]) fire |= 1u << (t - t0);
     if (t >= tl) break;
     if (bit_at(M, t)) --nf;
-    else su -= val_at(E, t);
+    else su -= pre_at(pl, pb, t + 1) - pre_at(pl, pb, t);
     if (bit_at(M, t + I)) ++nf;
-    else su += val_at(E, t + I);
+    else su += pre_at(pl, pb, t + I + 1) - pre_at(pl, pb, t + I);
   }
   return fire;
 }
@@ -988,11 +1068,102 @@ __device__ __forceinline__ uint32_t dilate32(uint32_t hi, uint32_t lo, int I) {
   return static_cast<uint32_t>(x >> 32);
 }
 
-template <int I>
-__device__ __forceinline__ uint32_t fire_chunk(bool fast, const uint32_t* E, const uint32_t* M,
-                                               int t0, int T, const long long* Kt, uint32_t K0) {
-  if (fast) return fast_fire<I>(E, t0, K0);
-  return slow_fire(E, M, t0, I, T, Kt);
+// Chunk-local prefixes of u for a batch of rows (strided warp tasks so that
+// every warp reads 512 contiguous bytes of the staged rows per load).  In
+// the packed path this is also the I = 1 pass: samples above K1 are flagged
+// and stored as Z.
+template <int DT, int NT>
+__device__ void st_build(const uint8_t* sdata, int dpitch, int T, int nch, const int* rows,
+                         int nbb, uint32_t* region, const StLayout& L, uint32_t* smbits, int MW,
+                         bool packed, uint32_t K1) {
+  using TR = Traits<DT>;
+  constexpr int VS = TR::kVec, LPC = 32 / VS, SEG = 64 * VS, NW = NT / kWarp;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, lp = lane & (LPC - 1);
+  const int nseg = (T + SEG - 1) / SEG;
+  for (int task = warp; task < nbb * nseg; task += NW) {
+    const int rb = task / nseg, s = task - rb * nseg;
+    const int r = rows[rb];
+    const uint8_t* row = sdata + r * dpitch;
+    uint32_t* pl = region + rb * L.per_row;
+    uint32_t* tc = pl + L.PLW + L.PBW;
+    uint32_t* mrow = smbits + r * MW + 2;
+#pragma unroll
+    for (int q = 0; q < 2; ++q) {
+      const int x = s * SEG + q * 32 * VS + lane * VS;
+      uint32_t v[VS];
+      if (x < T) {
+        load_vec<DT>(row, x, T, v);
+      } else {
+#pragma unroll
+        for (int j = 0; j < VS; ++j) v[j] = 0u;
+      }
+      uint32_t e[VS], acc = 0, fb = 0;
+#pragma unroll
+      for (int j = 0; j < VS; ++j) {
+        uint32_t uu = v[j];
+        if (packed && v[j] > K1) {
+          fb |= 1u << j;
+          uu = kZ;
+        }
+        e[j] = acc;
+        acc += uu;
+      }
+      uint32_t incl = acc;
+#pragma unroll
+      for (int o = 1; o < LPC; o <<= 1) {
+        const uint32_t y = __shfl_up_sync(0xFFFFFFFFu, incl, o);
+        if (lp >= o) incl += y;
+      }
+      const uint32_t off = incl - acc;
+      uint32_t fw = fb << (VS * lp);
+#pragma unroll
+      for (int o = 1; o < LPC; o <<= 1) fw |= __shfl_xor_sync(0xFFFFFFFFu, fw, o);
+      const int c = x >> 5;
+      if (c < nch + 3) {
+#pragma unroll
+        for (int j = 0; j < VS; j += 4) {
+          uint4 w4;
+          w4.x = off + e[j + 0];
+          w4.y = off + e[j + 1];
+          w4.z = off + e[j + 2];
+          w4.w = off + e[j + 3];
+          *reinterpret_cast<uint4*>(pl + pidx(x + j)) = w4;
+        }
+        if (lp == LPC - 1) tc[c] = incl;
+        if (lp == 0 && packed && c < nch) mrow[c] = fw;
+      }
+    }
+  }
+  // zero chunks after the row (look-ahead of the last windows)
+  for (int i = threadIdx.x; i < nbb * 3 * 32; i += NT) {
+    const int rb = i / 96, j = i - rb * 96;
+    const int x = nch * 32 + j;
+    uint32_t* pl = region + rb * L.per_row;
+    pl[pidx(x)] = 0u;
+    if ((j & 31) == 0) pl[L.PLW + L.PBW + (x >> 5)] = 0u;
+  }
+}
+
+// Chunk bases Pb = exclusive prefix of the chunk totals (warp per row);
+// only rows with dirty[rb] set (all rows when dirty == nullptr).
+template <int NT>
+__device__ void st_bases(uint32_t* region, const StLayout& L, int nch, int nbb, int* dirty) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  for (int rb = warp; rb < nbb; rb += NT / kWarp) {
+    if (dirty && !dirty[rb]) continue;
+    uint32_t* pb = region + rb * L.per_row + L.PLW;
+    const uint32_t* tc = pb + L.PBW;
+    uint32_t carry = 0;
+    for (int base = 0; base < L.PBW; base += kWarp) {
+      const int c = base + lane;
+      const uint32_t v = c < nch ? tc[c] : 0u;
+      uint32_t tot;
+      const uint32_t ex = warp_excl_scan(v, lane, &tot);
+      if (c < L.PBW) pb[c] = carry + ex;
+      carry += tot;
+    }
+    if (dirty && lane == 0) dirty[rb] = 0;
+  }
 }
 
 // ------------------------------------------------------------------ the kernel
@@ -1005,6 +1176,9 @@ __global__ void __launch_bounds__(NT, 512 / NT) lof_block_kernel(const KParams k
   constexpr int NW = NT / kWarp;
   extern __shared__ __align__(128) uint8_t smem[];
   __shared__ Fixed<NT> f;
+  __shared__ uint32_t s_K0[kMaxLogWindow + 1], s_cq[kMaxLogWindow + 1];
+  __shared__ uint32_t s_Kp[kKTable];
+  __shared__ int s_dirty[kMaxRowsPerItem];
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   uint8_t* const sdata = smem;
   uint8_t* const swork = smem + kp.tile_rows_bytes;
@@ -1022,10 +1196,11 @@ __global__ void __launch_bounds__(NT, 512 / NT) lof_block_kernel(const KParams k
 
   for (;;) {
     if (tid == 0) {
-      bulk_wait_read();  // previous item's bulk stores have read their rows
+      bulk_wait_read();  // the previous item's bulk stores have read their rows
       f.item = atomicAdd(kp.queue, 1);
       f.ok = 1;
       f.cnt_time = f.cnt_total = f.cnt_hist = 0;
+      f.mo1 = f.mo2lo = f.mo2hi = 0;
     }
     __syncthreads();
     const int item = f.item;
@@ -1041,6 +1216,7 @@ __global__ void __launch_bounds__(NT, 512 / NT) lof_block_kernel(const KParams k
     const int nseg = (T + SEG - 1) / SEG;
     const bool bulk_in = (u.flags & kUnitInBulk) != 0;
     const uint8_t* gin = static_cast<const uint8_t*>(u.in);
+    uint32_t* const hist = spfx;  // coarse histogram of this CTA's rows
 
     // ---- stage the rows
     if (tid == 0 && bulk_in) {
@@ -1057,13 +1233,13 @@ __global__ void __launch_bounds__(NT, 512 / NT) lof_block_kernel(const KParams k
     }
     for (int r = tid; r < R; r += NT) {
       f.rowS[r] = 0;
-      f.rowMax[r] = 0;
       f.rowFlagSum[r] = 0;
       f.rowNFlag[r] = 0;
       f.rowFh[r] = 0;
       f.rowFc[r] = 0;
     }
     for (int i = tid; i < R * MW; i += NT) smbits[i] = 0u;
+    for (int i = tid; i < kCoarseBins; i += NT) hist[i] = 0u;
     if (bulk_in) {
       const unsigned long long t0 = global_ns();
       while (!mbar_try(&f.mbar, phase)) {
@@ -1076,36 +1252,69 @@ __global__ void __launch_bounds__(NT, 512 / NT) lof_block_kernel(const KParams k
     }
     __syncthreads();
 
-    // ---- round 1 work: per-row power sums, maxima and segment sums
-    for (int task = warp; task < R * nseg; task += NW) {
-      const int r = task / nseg, s = task - r * nseg;
-      const uint8_t* row = sdata + r * dpitch;
-      const int x0 = s * SEG;
-      unsigned long long sum = 0;
-      uint32_t mx = 0;
+    // ---- pass 1: row power sums (spectrum) and coarse histogram of all rows
+    {
+      unsigned long long s1 = 0;
+      unsigned __int128 s2 = 0;
+      for (int task = warp; task < R * nseg; task += NW) {
+        const int r = task / nseg, s = task - r * nseg;
+        const uint8_t* row = sdata + r * dpitch;
+        unsigned long long sum = 0;
 #pragma unroll
-      for (int q = 0; q < 2; ++q) {
-        const int x = x0 + q * 32 * VS + lane * VS;
-        if (x < T) {
-          uint32_t v[VS];
-          load_vec<DT>(row, x, T, v);
+        for (int q = 0; q < 2; ++q) {
+          const int x = s * SEG + q * 32 * VS + lane * VS;
+          if (x < T) {
+            uint32_t v[VS];
+            load_vec<DT>(row, x, T, v);
 #pragma unroll
-          for (int j = 0; j < VS; ++j) {
-            sum += v[j];
-            mx = max(mx, v[j]);
+            for (int j = 0; j < VS; ++j) {
+              if (x + j < T) {
+                sum += v[j];
+                atomicAdd(&hist[coarse_key(v[j])], 1u);
+                if (kp.sigma_std) {
+                  s1 += v[j];
+                  s2 += static_cast<unsigned long long>(v[j]) * v[j];
+                }
+              }
+            }
           }
         }
+        sum = warp_sum64(sum);
+        if (lane == 0) atomicAdd(&f.rowS[r], sum);
       }
-      sum = warp_sum64(sum);
-      mx = warp_max32(mx);
-      if (lane == 0) {
-        atomicAdd(&f.rowS[r], sum);
-        atomicMax(&f.rowMax[r], mx);
-        f.segsum[r * nseg + s] = static_cast<uint32_t>(sum);
+      if (kp.sigma_std) {
+        s1 = warp_sum64(s1);
+        unsigned long long lo = static_cast<unsigned long long>(s2);
+        unsigned long long hi = static_cast<unsigned long long>(s2 >> 64);
+        for (int o = 16; o > 0; o >>= 1) {
+          const unsigned long long l2 = __shfl_xor_sync(0xFFFFFFFFu, lo, o);
+          const unsigned long long h2 = __shfl_xor_sync(0xFFFFFFFFu, hi, o);
+          const unsigned long long nl = lo + l2;
+          hi = hi + h2 + (nl < lo ? 1ull : 0ull);
+          lo = nl;
+        }
+        if (lane == 0) {
+          atomicAdd(&f.mo1, s1);
+          const unsigned long long old = atomicAdd(&f.mo2lo, lo);
+          atomicAdd(&f.mo2hi, hi + ((old + lo < old) ? 1ull : 0ull));
+        }
       }
     }
     __syncthreads();
+    // publish: spectrum, this CTA's histogram and moments, membership
     for (int r = tid; r < R; r += NT) kp.chan_S[u.chan_off + row0 + r] = f.rowS[r];
+    {
+      uint32_t* pub = kp.pub + static_cast<size_t>(blockIdx.x) * kCoarseBins;
+      for (int i = tid; i < kCoarseBins; i += NT) pub[i] = hist[i];
+      if (tid == 0) {
+        unsigned long long* pm = kp.pubm + static_cast<size_t>(blockIdx.x) * 4;
+        pm[0] = f.mo1;
+        pm[1] = 0;
+        pm[2] = f.mo2lo;
+        pm[3] = f.mo2hi;
+        kp.members[item] = static_cast<int>(blockIdx.x);
+      }
+    }
     __syncthreads();
     if (tid == 0) {
       __threadfence();
@@ -1126,7 +1335,85 @@ __global__ void __launch_bounds__(NT, 512 / NT) lof_block_kernel(const KParams k
       }
       __syncthreads();
       if (f.ok) {
-        frequency_pass<NT>(kp, u, kp.slots + blockIdx.x, swork, f);
+        Slot* const slot = kp.slots + blockIdx.x;
+        frequency_pass<NT>(kp, u, slot, swork, f);
+        if (__ldcg(&slot->state) != kStateDone) {
+          // pooled coarse histogram of the kept channels: all CTAs' histograms
+          // minus the rows the frequency pass flagged (re-read from the input).
+          // Workspace (bytes): the initial bin list lo [0, 4.2K), hi [10K, 14.2K),
+          // cum [20K, 24.2K); members [24K, 28K) (dead before the list is built);
+          // histogram [28K, 32.2K); Fc [34K, 36K).
+          const uint8_t* Fc = swork + 2 * kMaxChan * sizeof(unsigned long long) + kMaxChan;
+          uint32_t* uh = reinterpret_cast<uint32_t*>(swork + 28 * 1024);
+          int* mem = reinterpret_cast<int*>(swork + 24 * 1024);
+          for (int i = tid; i < G; i += NT) mem[i] = __ldcg(kp.members + u.first_item + i);
+          for (int k = tid; k < kCoarseBins; k += NT) uh[k] = 0u;
+          __syncthreads();
+          for (int i = warp; i < G; i += NW) {
+            const uint32_t* pb = kp.pub + static_cast<size_t>(mem[i]) * kCoarseBins;
+#pragma unroll 4
+            for (int k = lane; k < kCoarseBins; k += kWarp) {
+              const uint32_t h = __ldcg(pb + k);
+              if (h) atomicAdd(&uh[k], h);
+            }
+          }
+          unsigned long long s1 = 0;
+          unsigned __int128 s2 = 0;
+          for (int c = 0; c < u.C; ++c) {
+            if (!Fc[c]) continue;
+            const uint8_t* grow = gin + static_cast<int64_t>(c) * u.in_stride * TR::kBytes;
+            for (int t = tid; t < T; t += NT) {
+              const uint32_t v = TR::at(grow, t);
+              atomicSub(&uh[coarse_key(v)], 1u);
+              if (kp.sigma_std) {
+                s1 += v;
+                s2 += static_cast<unsigned long long>(v) * v;
+              }
+            }
+          }
+          if (kp.sigma_std) {
+            // moments of the kept channels: sum over CTAs minus flagged rows
+            s1 = warp_sum64(s1);
+            unsigned long long lo = static_cast<unsigned long long>(s2);
+            unsigned long long hi = static_cast<unsigned long long>(s2 >> 64);
+            for (int o = 16; o > 0; o >>= 1) {
+              const unsigned long long l2 = __shfl_xor_sync(0xFFFFFFFFu, lo, o);
+              const unsigned long long h2 = __shfl_xor_sync(0xFFFFFFFFu, hi, o);
+              const unsigned long long nl = lo + l2;
+              hi = hi + h2 + (nl < lo ? 1ull : 0ull);
+              lo = nl;
+            }
+            if (lane == 0) {
+              f.red_a[warp] = s1;
+              f.red_b[warp] = lo;
+              f.red_c[warp] = hi;
+            }
+          }
+          __syncthreads();
+          if (tid == 0 && kp.sigma_std) {
+            unsigned __int128 t1 = 0, t2 = 0, f1 = 0, f2 = 0;
+            for (int i = 0; i < G; ++i) {
+              const int m = __ldcg(kp.members + u.first_item + i);
+              const unsigned long long* pm = kp.pubm + static_cast<size_t>(m) * 4;
+              t1 += __ldcg(pm + 0);
+              t2 += (static_cast<unsigned __int128>(__ldcg(pm + 3)) << 64) | __ldcg(pm + 2);
+            }
+            for (int w = 0; w < NW; ++w) {
+              f1 += f.red_a[w];
+              f2 += (static_cast<unsigned __int128>(f.red_c[w]) << 64) | f.red_b[w];
+            }
+            t1 -= f1;
+            t2 -= f2;
+            slot->mom[0] = static_cast<unsigned long long>(t1);
+            slot->mom[1] = static_cast<unsigned long long>(t1 >> 64);
+            slot->mom[2] = static_cast<unsigned long long>(t2);
+            slot->mom[3] = static_cast<unsigned long long>(t2 >> 64);
+            slot->mom_ready = 1;
+          }
+          __syncthreads();
+          const BinList B = build_coarse_list<NT>(kp, slot, uh, swork);
+          select_plan<NT>(kp, u, slot, B, f);
+        }
         if (tid == 0) {
           __threadfence();
           st_release(&ctl->release, 1);
@@ -1151,7 +1438,7 @@ __global__ void __launch_bounds__(NT, 512 / NT) lof_block_kernel(const KParams k
     __syncthreads();
     const int nkeep = f.n_keep;
 
-    // ---- rounds 2+: exact pooled statistics of the kept rows
+    // ---- further rounds: exact counts in the refined bins, or moments
     int round = 1;
     for (;;) {
       if (tid == 0) f.state = __ldcg(&slot->state);
@@ -1159,57 +1446,7 @@ __global__ void __launch_bounds__(NT, 512 / NT) lof_block_kernel(const KParams k
       const int state = f.state;
       if (state == kStateDone) break;
       ++round;
-      if (state == kStateCoarse) {
-        uint32_t* hist = spfx;
-        for (int i = tid; i < kCoarseBins; i += NT) hist[i] = 0u;
-        __syncthreads();
-        unsigned long long s1 = 0;
-        unsigned __int128 s2 = 0;
-        for (int task = warp; task < nkeep * nseg; task += NW) {
-          const int kr = task / nseg, s = task - kr * nseg;
-          const uint8_t* row = sdata + f.keep[kr] * dpitch;
-#pragma unroll
-          for (int q = 0; q < 2; ++q) {
-            const int x = s * SEG + q * 32 * VS + lane * VS;
-            if (x < T) {
-              uint32_t v[VS];
-              load_vec<DT>(row, x, T, v);
-#pragma unroll
-              for (int j = 0; j < VS; ++j) {
-                if (x + j < T) {
-                  atomicAdd(&hist[coarse_key(v[j])], 1u);
-                  if (kp.sigma_std) {
-                    s1 += v[j];
-                    s2 += static_cast<unsigned long long>(v[j]) * v[j];
-                  }
-                }
-              }
-            }
-          }
-        }
-        if (kp.sigma_std) {
-          s1 = warp_sum64(s1);
-          unsigned long long lo = static_cast<unsigned long long>(s2);
-          unsigned long long hi = static_cast<unsigned long long>(s2 >> 64);
-          // 128-bit warp sum through (lo, hi) pairs
-          for (int o = 16; o > 0; o >>= 1) {
-            const unsigned long long l2 = __shfl_xor_sync(0xFFFFFFFFu, lo, o);
-            const unsigned long long h2 = __shfl_xor_sync(0xFFFFFFFFu, hi, o);
-            const unsigned long long nl = lo + l2;
-            hi = hi + h2 + (nl < lo ? 1ull : 0ull);
-            lo = nl;
-          }
-          if (lane == 0) {
-            atomicAdd(slot->mom + 0, s1);  // s1 < 2^64 per warp; carry handled below
-            atomic_add_u128(slot->mom + 2, (static_cast<unsigned __int128>(hi) << 64) | lo);
-          }
-        }
-        __syncthreads();
-        for (int i = tid; i < kCoarseBins; i += NT) {
-          const uint32_t h = hist[i];
-          if (h) atomicAdd(slot->coarse + i, h);
-        }
-      } else if (state == kStateFine) {
+      if (state == kStateFine) {
         uint32_t* fine = spfx;
         uint8_t* map = reinterpret_cast<uint8_t*>(spfx + kMaxFine);
         const int nt = __ldcg(&slot->n_targets);
@@ -1218,10 +1455,14 @@ __global__ void __launch_bounds__(NT, 512 / NT) lof_block_kernel(const KParams k
         for (int i = tid; i < nf; i += NT) fine[i] = 0u;
         __syncthreads();
         for (int k = tid; k < kCoarseBins; k += NT) {
-          const uint32_t lo = coarse_lo(k), hi = coarse_hi(k);
-          int t = 0;
-          while (t < nt && f.tgt[t].hi < lo) ++t;
-          map[k] = (t < nt && f.tgt[t].lo <= hi) ? static_cast<uint8_t>(t) : 0xFFu;
+          uint32_t lo, hi;
+          uint8_t mk = 0xFFu;
+          if (key_range(static_cast<uint32_t>(k), &lo, &hi)) {
+            int t = 0;
+            while (t < nt && f.tgt[t].hi < lo) ++t;
+            if (t < nt && f.tgt[t].lo <= hi) mk = static_cast<uint8_t>(t);
+          }
+          map[k] = mk;
         }
         __syncthreads();
         for (int task = warp; task < nkeep * nseg; task += NW) {
@@ -1301,12 +1542,7 @@ __global__ void __launch_bounds__(NT, 512 / NT) lof_block_kernel(const KParams k
       if (f.last) {
         if (tid == 0) __threadfence();
         __syncthreads();
-        if (state == kStateCoarse) {
-          build_coarse_list<NT>(slot);
-          if (tid == 0 && kp.sigma_std) slot->mom_ready = 1;
-          const BinList B = load_bins<NT>(slot, swork, __ldcg(&slot->n_bins));
-          select_plan<NT>(kp, u, slot, B, f);
-        } else if (state == kStateFine) {
+        if (state == kStateFine) {
           merge_fine<NT>(kp, slot, swork, f);
           const BinList B = load_bins<NT>(slot, swork, __ldcg(&slot->n_bins));
           select_plan<NT>(kp, u, slot, B, f);
@@ -1328,11 +1564,9 @@ __global__ void __launch_bounds__(NT, 512 / NT) lof_block_kernel(const KParams k
       if (!f.ok) break;
     }
     if (!f.ok) break;
-    // the unit's statistics and thresholds
+    // the unit's thresholds
     for (int i = tid; i < kKTable; i += NT) f.K[i] = __ldcg(slot->K + i);
     if (tid == 0) {
-      f.median_t = __ldcg(&slot->median_t);
-      f.sigma_t = __ldcg(&slot->sigma_t);
       f.time_on = __ldcg(&slot->time_on);
       int kmax = 0;
       while (kmax < kp.max_log_window && (2 << kmax) <= T) ++kmax;
@@ -1342,76 +1576,51 @@ __global__ void __launch_bounds__(NT, 512 / NT) lof_block_kernel(const KParams k
     if (tid == 0) {
       __threadfence();
       atomicAdd(&ctl->departed, 1);
+      // packed-path tables and guard (see the time pass helpers)
+      bool packed = f.K[0] >= 0 && f.K[0] < (1ll << 20);
+      for (int k = 0; k <= f.kmax_t && packed; ++k) {
+        const int I = 1 << k;
+        const long long* Kt = f.K + koffset(k);
+        for (int n = 0; n <= I; ++n)
+          if (Kt[n] < 0 || Kt[n] >= static_cast<long long>(kZ)) packed = false;
+        if (!packed) break;
+        s_K0[k] = static_cast<uint32_t>(Kt[0]);
+        // tau = floor(threshold_I) + 3 >= threshold_I + 2; floor(threshold_I) = K[I - 1]
+        const uint32_t tau = static_cast<uint32_t>(k == 0 ? Kt[0] : Kt[I - 1]) + 3u;
+        s_cq[k] = tau - kZ;
+        for (int n = 0; n <= I; ++n)
+          s_Kp[koffset(k) + n] = static_cast<uint32_t>(n) * kZ + static_cast<uint32_t>(Kt[n]);
+      }
+      f.state = packed ? 1 : 0;
     }
+    __syncthreads();
 
     // ---- time pass: SumThreshold along t on the kept rows (Section 2.1)
     if (f.time_on && nkeep > 0) {
-      const int PPw = round_up(T, SEG) + kPadWords;  // prefix entries per row (with slack)
-      const int PPp = PPw / 32 * 36;                  // padded words per row
-      const int nb = min(nkeep, kp.pfx_words / PPp);
+      const bool packed = f.state == 1;
+      const StLayout L = st_layout(nch);
+      const int nb = min(nkeep, kp.pfx_words / L.per_row);
       if (nb < 1) {  // the host sizes the prefix buffer for every row length
         if (tid == 0) set_error(kp, kErrInternal, 30);
         break;
       }
       for (int b0 = 0; b0 < nkeep; b0 += nb) {
         const int nbb = min(nb, nkeep - b0);
-        // prefix sums E[x] = sum_{t<x} P[t] (mod 2^32), padded layout
-        for (int task = warp; task < nbb * nseg; task += NW) {
-          const int rb = task / nseg, s = task - rb * nseg;
-          const int r = f.keep[b0 + rb];
-          const uint8_t* row = sdata + r * dpitch;
-          uint32_t* E = spfx + rb * PPp;
-          uint32_t off = 0;
-          for (int q = lane; q < s; q += kWarp) off += f.segsum[r * nseg + q];
-          uint32_t carry = warp_sum32(off);
-#pragma unroll
-          for (int q = 0; q < 2; ++q) {
-            const int x = s * SEG + q * 32 * VS + lane * VS;
-            uint32_t v[VS];
-            if (x < T) {
-              load_vec<DT>(row, x, T, v);
-            } else {
-#pragma unroll
-              for (int j = 0; j < VS; ++j) v[j] = 0u;
-            }
-            uint32_t e[VS];
-            uint32_t acc = 0;
-#pragma unroll
-            for (int j = 0; j < VS; ++j) {
-              e[j] = acc;
-              acc += v[j];
-            }
-            uint32_t tot;
-            const uint32_t ex = warp_excl_scan(acc, lane, &tot);
-            const uint32_t basev = carry + ex;
-#pragma unroll
-            for (int j = 0; j < VS; j += 4) {
-              uint4 w;
-              w.x = basev + e[j + 0];
-              w.y = basev + e[j + 1];
-              w.z = basev + e[j + 2];
-              w.w = basev + e[j + 3];
-              *reinterpret_cast<uint4*>(E + pidx(x + j)) = w;
-            }
-            carry += tot;
-          }
-          if (s == nseg - 1 && lane == 0) E[pidx(T)] = carry;
-        }
+        const int* rows = f.keep + b0;
+        st_build<DT, NT>(sdata, dpitch, T, nch, rows, nbb, spfx, L, smbits, MW, packed,
+                         packed ? s_K0[0] : 0u);
         for (int i = tid; i < nbb * MW; i += NT) sfbits[i] = 0u;
+        if (tid < nbb) s_dirty[tid] = 0;
         __syncthreads();
-        for (int k = 0; k <= f.kmax_t; ++k) {
+        st_bases<NT>(spfx, L, nch, nbb, nullptr);
+        __syncthreads();
+        for (int k = packed ? 1 : 0; k <= f.kmax_t; ++k) {
           const int I = 1 << k;
           const long long* Kt = f.K + koffset(k);
-          const long long K0l = Kt[0];
-          const uint32_t K0 = K0l >= 0xFFFFFFFFll ? 0xFFFFFFFFu : static_cast<uint32_t>(K0l);
-          const int rem = I - 1;
-          const uint32_t m1 = rem >= 32 ? 0xFFFFFFFFu : ((1u << rem) - 1u);
-          const uint32_t m2 = rem > 32 ? ((1u << (rem - 32)) - 1u) : 0u;
+          const uint32_t K0 = packed ? s_K0[k] : 0u, cq = packed ? s_cq[k] : 0u;
+          const uint32_t* Kp = s_Kp + koffset(k);
           for (int c = tid; c < nbb * nch; c += NT) {
             const int rb = c / nch, w = c - rb * nch, t0 = w << 5;
-            const int r = f.keep[b0 + rb];
-            const uint32_t* E = spfx + rb * PPp;
-            const uint32_t* M = smbits + r * MW + 2;
             uint32_t* F = sfbits + rb * MW + 2;
             const int nvalid = T - I + 1 - t0;
             if (nvalid <= 0) {
@@ -1419,33 +1628,58 @@ __global__ void __launch_bounds__(NT, 512 / NT) lof_block_kernel(const KParams k
               continue;
             }
             const uint32_t vm = nvalid >= 32 ? 0xFFFFFFFFu : ((1u << nvalid) - 1u);
-            const uint32_t anyf = M[w] | (M[w + 1] & m1) | (M[w + 2] & m2);
-            const bool fast = (anyf == 0u) && (f.rowMax[r] < kFastMax);
+            const uint32_t* pl = spfx + rb * L.per_row;
+            const uint32_t* pb = pl + L.PLW;
             uint32_t fire;
-            switch (k) {
-              case 0: fire = fire_chunk<1>(fast, E, M, t0, T, Kt, K0); break;
-              case 1: fire = fire_chunk<2>(fast, E, M, t0, T, Kt, K0); break;
-              case 2: fire = fire_chunk<4>(fast, E, M, t0, T, Kt, K0); break;
-              case 3: fire = fire_chunk<8>(fast, E, M, t0, T, Kt, K0); break;
-              case 4: fire = fire_chunk<16>(fast, E, M, t0, T, Kt, K0); break;
-              case 5: fire = fire_chunk<32>(fast, E, M, t0, T, Kt, K0); break;
-              default: fire = fire_chunk<64>(fast, E, M, t0, T, Kt, K0); break;
+            if (packed) {
+              switch (k) {
+                case 1: fire = packed_fire<2>(pl, pb, w, K0, cq, Kp); break;
+                case 2: fire = packed_fire<4>(pl, pb, w, K0, cq, Kp); break;
+                case 3: fire = packed_fire<8>(pl, pb, w, K0, cq, Kp); break;
+                case 4: fire = packed_fire<16>(pl, pb, w, K0, cq, Kp); break;
+                case 5: fire = packed_fire<32>(pl, pb, w, K0, cq, Kp); break;
+                default: fire = packed_fire<64>(pl, pb, w, K0, cq, Kp); break;
+              }
+            } else {
+              fire = general_fire(pl, pb, smbits + rows[rb] * MW + 2, t0, I, T, Kt);
             }
             F[w] = fire & vm;
           }
           __syncthreads();
+          // new flags: windows that fired flag all their samples (snapshot)
           for (int c = tid; c < nbb * nch; c += NT) {
             const int rb = c / nch, w = c - rb * nch;
-            const int r = f.keep[b0 + rb];
             const uint32_t* F = sfbits + rb * MW + 2;
             const uint32_t f0 = F[w], f1 = F[w - 1], f2 = F[w - 2];
             if ((f0 | f1 | f2) == 0u) continue;
-            uint32_t D;
-            if (I <= 32) D = dilate32(f0, f1, I);
-            else D = dilate32(f0, f1, 32) | dilate32(f1, f2, 32);
-            smbits[r * MW + 2 + w] |= D;
+            const uint32_t D = (I <= 32) ? dilate32(f0, f1, I)
+                                         : (dilate32(f0, f1, 32) | dilate32(f1, f2, 32));
+            uint32_t* Mw = smbits + rows[rb] * MW + 2 + w;
+            const uint32_t nw = D & ~*Mw;
+            if (nw == 0u) continue;
+            *Mw |= nw;
+            if (packed) {
+              // store the newly flagged samples of this chunk as Z
+              uint32_t* pl = spfx + rb * L.per_row + pidx(w << 5);
+              uint32_t* tcw = spfx + rb * L.per_row + L.PLW + L.PBW + w;
+              uint32_t cur = pl[0], acc = 0;
+              for (int j = 0; j < 32; ++j) {
+                const uint32_t nx = (j < 31) ? pl[j + 1] : *tcw;
+                uint32_t uu = nx - cur;
+                cur = nx;
+                if ((nw >> j) & 1u) uu = kZ;
+                pl[j] = acc;
+                acc += uu;
+              }
+              *tcw = acc;
+              s_dirty[rb] = 1;
+            }
           }
           __syncthreads();
+          if (packed && k < f.kmax_t) {
+            st_bases<NT>(spfx, L, nch, nbb, s_dirty);
+            __syncthreads();
+          }
         }
       }
       // flagged counts and flagged power of every kept row
