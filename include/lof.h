@@ -181,6 +181,30 @@ typedef struct {
 int lof_set_tuning(lof_ctx *ctx, const lof_tuning *t);
 int lof_get_tuning(const lof_ctx *ctx, lof_tuning *t);
 
+/* Flag one block of units like lof_flag_block, without allocating anything.
+ * The paper has no counterpart: this entry point exists for callers that may
+ * not allocate memory while they run -- real-time processing threads that
+ * cannot afford cudaMalloc/cudaFree (which block and synchronise the device),
+ * processes with a fixed allocation budget, or hosts without a memory pool.
+ * It needs no context: params may be NULL (defaults), and the history flagger
+ * is unavailable (every unit must have history_slot = -1).  Its scratch is
+ * one file-scope device array of 24 MiB that every GPU which loads the
+ * library holds until the process exits; host-side descriptors live in fixed
+ * static arrays (at most 1024 units and 65536 work items per call).  A block
+ * that does not fit is rejected with LOF_ERR_INVALID and a message
+ * (lof_last_error(NULL)); nothing is launched then.
+ * The first call on each device looks up the device address of the array
+ * (with that device current); make that first call before any stream
+ * capture.  All calls share the array and it keeps the last call's contents:
+ * each call clears what must start at zero, but calls whose work overlaps on
+ * the GPU (different streams, or different host threads without ordering)
+ * race on it -- serialise them.  status: optional DEVICE int that receives
+ * the device-side status of this call (0 = ok, else a device error code) when
+ * the stream reaches it; NULL = not reported.  Returns LOF_OK when the work
+ * was enqueued on cuda_stream. */
+int lof_flag_block_noalloc(const lof_params *params, int dtype, const lof_unit *units, int n_units,
+                           int *status, void *cuda_stream);
+
 /* Message for the last failed call on ctx (or of lof_create when ctx is NULL). */
 const char *lof_last_error(const lof_ctx *ctx);
 

@@ -19,7 +19,7 @@ CSRC = os.path.join(HERE, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(BUILD, "liblof.so")
-SOURCES = ["lof_kernels.cu", "lof_api.cu"]
+SOURCES = ["lof_kernels.cu", "lof_api.cu", "lof_noalloc.cu"]
 HEADERS = [os.path.join(CSRC, "lof_internal.h"), os.path.join(INCLUDE, "lof.h")]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 _lock = threading.Lock()

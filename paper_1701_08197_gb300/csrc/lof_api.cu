@@ -25,7 +25,7 @@ using lofk::UnitCtl;
 
 namespace {
 
-thread_local std::string g_create_error;
+thread_local char g_create_error[512];
 
 constexpr int kStageRing = 4;
 
@@ -37,8 +37,6 @@ int esize_of(int dtype) {
     default: return 0;
   }
 }
-int vec_of(int dtype) { return 16 / esize_of(dtype); }
-int seg_of(int dtype) { return 64 * vec_of(dtype); }
 int64_t round_up64(int64_t x, int64_t m) { return (x + m - 1) / m * m; }
 
 }  // namespace
@@ -95,7 +93,7 @@ int fail(lof_ctx* c, int code, const char* fmt, ...) {
   vsnprintf(buf, sizeof buf, fmt, ap);
   va_end(ap);
   if (c) c->last_error = buf;
-  else g_create_error = buf;
+  else snprintf(g_create_error, sizeof g_create_error, "%s", buf);
   return code;
 }
 
@@ -145,12 +143,6 @@ int pending_device_error(lof_ctx* c) {
   return fail(c, LOF_ERR_STATE, "device error %d (detail %d, block %d)", code, info0, info1);
 }
 
-// Shared-memory plan for one launch.
-struct Plan {
-  int threads, ctas, grid;
-  int tile, pfx_words, mbits_words, fbits_words, smem;
-};
-
 int static_smem_bytes(int dtype, int threads) {
   // conservative bound of the kernel's static shared memory (Fixed<NT> + locals)
   (void)dtype;
@@ -170,9 +162,9 @@ int dpitch_of(int dtype, int T) {
 }
 
 // Budget of dynamic shared memory per CTA.
-int dyn_budget(const lof_ctx* c, int dtype, int threads, int ctas) {
-  const int per = c->smem_per_sm / std::max(1, ctas) - 1024;
-  return std::min(per, c->smem_optin) - static_smem_bytes(dtype, threads);
+int dyn_budget(const lofk::HostCfg& h, int dtype, int threads, int ctas) {
+  const int per = h.smem_per_sm / std::max(1, ctas) - 1024;
+  return std::min(per, h.smem_optin) - static_smem_bytes(dtype, threads);
 }
 
 // rows of one item for a unit with n_time T, given a tile size
@@ -201,7 +193,7 @@ extern "C" void lof_default_params(lof_params* p) {
 }
 
 extern "C" const char* lof_last_error(const lof_ctx* c) {
-  return c ? c->last_error.c_str() : g_create_error.c_str();
+  return c ? c->last_error.c_str() : g_create_error;
 }
 
 static int validate_params(const lof_params* p, std::string* why) {
@@ -356,27 +348,21 @@ extern "C" int lof_get_tuning(const lof_ctx* c, lof_tuning* t) {
 namespace {
 
 // Shared-memory plan: tile of rows, prefix/workspace, flag words.
-bool make_plan(const lof_ctx* c, int dtype, const int* Ts, int nT, Plan* pl, std::string* why) {
-  pl->threads = c->tuning.threads;
-  pl->ctas = c->tuning.ctas_per_sm;
-  const int budget = dyn_budget(c, dtype, pl->threads, pl->ctas);
+bool make_plan(const lofk::HostCfg& h, int dtype, const int* Ts, int nT, lofk::Plan* pl,
+               char* why, int nwhy) {
+  pl->threads = h.tuning.threads;
+  pl->ctas = h.tuning.ctas_per_sm;
+  const int budget = dyn_budget(h, dtype, pl->threads, pl->ctas);
   int pfx = lofk::kWorkspaceBytes / 4;
-  int maxT = 0;
-  for (int i = 0; i < nT; ++i) {
-    pfx = std::max(pfx, pfx_row_words(dtype, Ts[i]));
-    maxT = std::max(maxT, Ts[i]);
-  }
-  // flag words: at most (tile / pitch) rows of (nch + 4) words; bound generously
-  int tile = c->tuning.tile_bytes ? c->tuning.tile_bytes : (budget - 4 * pfx) / 128 * 128;
+  for (int i = 0; i < nT; ++i) pfx = std::max(pfx, pfx_row_words(dtype, Ts[i]));
+  int tile = h.tuning.tile_bytes ? h.tuning.tile_bytes : (budget - 4 * pfx) / 128 * 128;
   for (int iter = 0; iter < 8; ++iter) {
     int mb = 0, fb = 0;
     for (int i = 0; i < nT; ++i) {
       const int T = Ts[i];
       const int R = rows_per_item(dtype, T, tile);
       if (R < 1) {
-        char b[160];
-        snprintf(b, sizeof b, "n_time %d does not fit the shared-memory tile (%d bytes)", T, tile);
-        *why = b;
+        snprintf(why, nwhy, "n_time %d does not fit the shared-memory tile (%d bytes)", T, tile);
         return false;
       }
       const int words = (T + 31) / 32 + 4;
@@ -385,14 +371,14 @@ bool make_plan(const lof_ctx* c, int dtype, const int* Ts, int nT, Plan* pl, std
       fb = std::max(fb, nb * words);
     }
     const int total = tile + 4 * (pfx + mb + fb);
-    if (total <= budget || c->tuning.tile_bytes) {
+    if (total <= budget || h.tuning.tile_bytes) {
       pl->tile = tile;
       pl->pfx_words = pfx;
       pl->mbits_words = mb;
       pl->fbits_words = fb;
       pl->smem = total;
       if (total > budget) {
-        *why = "tuned tile_bytes exceeds the shared-memory budget";
+        snprintf(why, nwhy, "tuned tile_bytes exceeds the shared-memory budget");
         return false;
       }
       return true;
@@ -401,31 +387,30 @@ bool make_plan(const lof_ctx* c, int dtype, const int* Ts, int nT, Plan* pl, std
     tile = tile / 128 * 128;
     if (tile < 1024) break;
   }
-  *why = "no shared-memory plan fits";
+  snprintf(why, nwhy, "no shared-memory plan fits");
   return false;
 }
 
-// Builds and launches one block for units already holding DEVICE pointers.
-int flag_block_device(lof_ctx* c, int dtype, const lof_unit* units, int n_units, uint64_t seq,
-                      void* stream) {
+}  // namespace
+
+namespace lofk {
+
+int host_prepare(const HostCfg& h, int dtype, const lof_unit* units, int n_units, DevUnit* du,
+                 Item* items, int max_items, int* Ts, Prep* out, char* why, int nwhy) {
   const int es = esize_of(dtype);
-  std::vector<int> Ts(n_units);
   for (int i = 0; i < n_units; ++i) Ts[i] = units[i].n_time;
-  Plan pl;
-  std::string why;
-  if (!make_plan(c, dtype, Ts.data(), n_units, &pl, &why))
-    return fail(c, LOF_ERR_INVALID, "lof_flag_block: %s", why.c_str());
+  if (!make_plan(h, dtype, Ts, n_units, &out->plan, why, nwhy)) return LOF_ERR_INVALID;
+  const Plan& pl = out->plan;
   int occ = 0;
-  int krc = lofk_max_blocks_per_sm(dtype, pl.threads, pl.smem, &occ);
-  if (krc != 0 || occ < 1)
-    return fail(c, LOF_ERR_CUDA, "kernel does not fit (%d threads, %d B shared): rc %d occ %d",
-                pl.threads, pl.smem, krc, occ);
+  const int krc = lofk_max_blocks_per_sm(dtype, pl.threads, pl.smem, &occ);
+  if (krc != 0 || occ < 1) {
+    snprintf(why, nwhy, "kernel does not fit (%d threads, %d B shared): rc %d occ %d", pl.threads,
+             pl.smem, krc, occ);
+    return LOF_ERR_CUDA;
+  }
   const int ctas = std::min(pl.ctas, occ);
-  // descriptors
-  std::vector<DevUnit> du(n_units);
-  std::vector<Item> items;
   int64_t chan = 0;
-  int maxG = 0;
+  int n_items = 0, maxG = 0;
   for (int i = 0; i < n_units; ++i) {
     const lof_unit& u = units[i];
     DevUnit& d = du[i];
@@ -445,93 +430,92 @@ int flag_block_device(lof_ctx* c, int dtype, const lof_unit* units, int n_units,
     const int64_t rowb = static_cast<int64_t>(u.n_time) * es;
     if ((reinterpret_cast<uintptr_t>(u.in) % 16) == 0 && ((u.in_row_stride * es) % 16) == 0 &&
         (rowb % 16) == 0)
-      flags |= lofk::kUnitInBulk;
-    if (u.out && u.out == u.in) flags |= lofk::kUnitInPlace;
+      flags |= kUnitInBulk;
+    if (u.out && u.out == u.in) flags |= kUnitInPlace;
     else if (u.out && (reinterpret_cast<uintptr_t>(u.out) % 16) == 0 &&
              ((u.out_row_stride * es) % 16) == 0 && (rowb % 16) == 0)
-      flags |= lofk::kUnitOutBulk;
+      flags |= kUnitOutBulk;
     if (u.mask && (reinterpret_cast<uintptr_t>(u.mask) % 16) == 0 && (u.mask_row_stride % 16) == 0)
-      flags |= lofk::kUnitMaskVec;
+      flags |= kUnitMaskVec;
     d.flags = flags;
     const int Rmax = rows_per_item(dtype, u.n_time, pl.tile);
     const int nit = (u.n_chan + Rmax - 1) / Rmax;
     const int R = (u.n_chan + nit - 1) / nit;
-    d.first_item = static_cast<int32_t>(items.size());
+    d.first_item = n_items;
     d.n_items = nit;
     maxG = std::max(maxG, nit);
-    for (int r0 = 0; r0 < u.n_chan; r0 += R)
-      items.push_back(Item{i, r0, std::min(R, u.n_chan - r0), 0});
+    for (int r0 = 0; r0 < u.n_chan; r0 += R) {
+      if (n_items >= max_items) {
+        snprintf(why, nwhy, "more than %d items in one block", max_items);
+        return LOF_ERR_INVALID;
+      }
+      items[n_items++] = Item{i, r0, std::min(R, u.n_chan - r0), 0};
+    }
   }
-  const int n_items = static_cast<int>(items.size());
-  int grid = std::min(c->n_sm * ctas, n_items);
-  if (maxG > c->n_sm * ctas)
-    return fail(c, LOF_ERR_UNSUPPORTED,
-                "a unit needs %d co-resident CTAs, the device holds %d; use fewer channels per unit",
-                maxG, c->n_sm * ctas);
-  // scratch
-  int rc;
-  if ((rc = grow(c, &c->d_units, &c->cap_units, n_units, "units"))) return rc;
-  if ((rc = grow(c, &c->d_items, &c->cap_items, n_items, "items"))) return rc;
-  if ((rc = grow(c, &c->d_ctl, &c->cap_ctl, n_units, "unit control"))) return rc;
-  if ((rc = grow(c, &c->d_chanS, &c->cap_chan, static_cast<size_t>(chan), "spectrum"))) return rc;
-  if ((rc = grow(c, &c->d_chanFc, &c->cap_chanfc, static_cast<size_t>(chan), "channel flags"))) return rc;
-  if ((rc = grow(c, &c->d_slots, &c->cap_slots, static_cast<size_t>(grid), "slots"))) return rc;
-  if ((rc = grow(c, &c->d_pub, &c->cap_pub, static_cast<size_t>(grid) * lofk::kCoarseBins, "histograms")))
-    return rc;
-  if ((rc = grow(c, &c->d_pubm, &c->cap_pubm, static_cast<size_t>(grid) * 4, "moments"))) return rc;
-  if ((rc = grow(c, &c->d_members, &c->cap_members, static_cast<size_t>(n_items), "members"))) return rc;
-  // stage descriptors (pinned ring)
-  const size_t bytes_units = n_units * sizeof(DevUnit);
-  const size_t bytes_items = n_items * sizeof(Item);
-  const size_t bytes = bytes_units + bytes_items;
-  const int si = c->stage_next;
-  c->stage_next = (si + 1) % kStageRing;
-  cudaError_t e = cudaEventSynchronize(c->ev_stage[si]);
-  if (e != cudaSuccess) return cuda_fail(c, e, "cudaEventSynchronize");
-  if (c->cap_stage[si] < bytes) {
-    if (c->h_stage[si]) cudaFreeHost(c->h_stage[si]);
-    c->h_stage[si] = nullptr;
-    size_t n = std::max(bytes, 2 * c->cap_stage[si]);
-    e = cudaHostAlloc(&c->h_stage[si], n, cudaHostAllocDefault);
-    if (e != cudaSuccess) return fail(c, LOF_ERR_NOMEM, "pinned staging: %s", cudaGetErrorString(e));
-    c->cap_stage[si] = n;
+  if (maxG > h.n_sm * ctas) {
+    snprintf(why, nwhy,
+             "a unit needs %d co-resident CTAs, the device holds %d; use fewer channels per unit",
+             maxG, h.n_sm * ctas);
+    return LOF_ERR_UNSUPPORTED;
   }
-  uint8_t* hs = static_cast<uint8_t*>(c->h_stage[si]);
-  memcpy(hs, du.data(), bytes_units);
-  memcpy(hs + bytes_units, items.data(), bytes_items);
+  out->n_items = n_items;
+  out->n_chan = chan;
+  out->grid = std::min(h.n_sm * ctas, n_items);
+  return LOF_OK;
+}
+
+// Count of items host_prepare will produce (for sizing host arrays).
+int host_count_items(const HostCfg& h, int dtype, const lof_unit* units, int n_units, int* Ts,
+                     int* n_items, char* why, int nwhy) {
+  Plan pl;
+  for (int i = 0; i < n_units; ++i) Ts[i] = units[i].n_time;
+  if (!make_plan(h, dtype, Ts, n_units, &pl, why, nwhy)) return LOF_ERR_INVALID;
+  int n = 0;
+  for (int i = 0; i < n_units; ++i) {
+    const int Rmax = rows_per_item(dtype, units[i].n_time, pl.tile);
+    const int nit = (units[i].n_chan + Rmax - 1) / Rmax;
+    n += nit;
+  }
+  *n_items = n;
+  return LOF_OK;
+}
+
+int host_launch(const lof_params& P, const HostCfg& h, int dtype, const Prep& pr,
+                const Scratch& sc, const DevUnit* du_host, int n_units, const Item* items_host,
+                uint64_t seq, void* stream, char* why, int nwhy) {
   cudaStream_t st = static_cast<cudaStream_t>(stream);
-  if ((e = cudaMemcpyAsync(c->d_units, hs, bytes_units, cudaMemcpyHostToDevice, st)) != cudaSuccess)
-    return cuda_fail(c, e, "descriptor upload");
-  if ((e = cudaMemcpyAsync(c->d_items, hs + bytes_units, bytes_items, cudaMemcpyHostToDevice, st)) !=
-      cudaSuccess)
-    return cuda_fail(c, e, "descriptor upload");
-  cudaEventRecord(c->ev_stage[si], st);
-  if ((e = cudaMemsetAsync(c->d_ctl, 0, n_units * sizeof(UnitCtl), st)) != cudaSuccess)
-    return cuda_fail(c, e, "memset");
-  if ((e = cudaMemsetAsync(c->d_ctrl, 0, sizeof(int), st)) != cudaSuccess) return cuda_fail(c, e, "memset");
+  cudaError_t e;
+  if ((e = cudaMemcpyAsync(sc.units, du_host, n_units * sizeof(DevUnit), cudaMemcpyHostToDevice, st)) !=
+          cudaSuccess ||
+      (e = cudaMemcpyAsync(sc.items, items_host, pr.n_items * sizeof(Item), cudaMemcpyHostToDevice,
+                           st)) != cudaSuccess ||
+      (e = cudaMemsetAsync(sc.ctl, 0, n_units * sizeof(UnitCtl), st)) != cudaSuccess ||
+      (e = cudaMemsetAsync(sc.ctrl, 0, sizeof(int), st)) != cudaSuccess) {
+    snprintf(why, nwhy, "descriptor upload: %s", cudaGetErrorString(e));
+    return LOF_ERR_CUDA;
+  }
   KParams kp{};
-  kp.units = c->d_units;
-  kp.items = c->d_items;
-  kp.ctl = c->d_ctl;
-  kp.chan_S = c->d_chanS;
-  kp.chan_Fc = c->d_chanFc;
-  kp.slots = c->d_slots;
-  kp.pub = c->d_pub;
-  kp.pubm = c->d_pubm;
-  kp.members = c->d_members;
-  kp.queue = c->d_ctrl;
-  kp.err = c->d_ctrl + 1;
-  kp.err_info = c->d_ctrl + 2;
-  kp.hist = c->hist;
+  kp.units = sc.units;
+  kp.items = sc.items;
+  kp.ctl = sc.ctl;
+  kp.chan_S = sc.chanS;
+  kp.chan_Fc = sc.chanFc;
+  kp.slots = sc.slots;
+  kp.pub = sc.pub;
+  kp.pubm = sc.pubm;
+  kp.members = sc.members;
+  kp.queue = sc.ctrl;
+  kp.err = sc.ctrl + 1;
+  kp.err_info = sc.ctrl + 2;
+  kp.hist = sc.hist;
   kp.n_units = n_units;
-  kp.n_items = n_items;
-  kp.tile_rows_bytes = pl.tile;
-  kp.pfx_words = pl.pfx_words;
-  kp.mbits_words = pl.mbits_words;
-  kp.fbits_words = pl.fbits_words;
-  kp.fine_bins = c->tuning.fine_bins;
-  const lof_params& P = c->params;
-  for (int k = 0; k <= lofk::kMaxLogWindow; ++k) {
+  kp.n_items = pr.n_items;
+  kp.tile_rows_bytes = pr.plan.tile;
+  kp.pfx_words = pr.plan.pfx_words;
+  kp.mbits_words = pr.plan.mbits_words;
+  kp.fbits_words = pr.plan.fbits_words;
+  kp.fine_bins = h.tuning.fine_bins;
+  for (int k = 0; k <= kMaxLogWindow; ++k) {
     // Section 2.1: factor_I = startThreshold * p^(log2 I) / I (p^k by k products)
     volatile double pk = 1.0;
     for (int i = 0; i < k; ++i) pk = pk * P.p;
@@ -550,10 +534,126 @@ int flag_block_device(lof_ctx* c, int dtype, const lof_unit* units, int n_units,
   kp.enable_history = P.enable_history;
   kp.block_seq = seq;
   kp.spin_limit = 2000000000ll;  // 2 s
-  krc = lofk_launch_block(dtype, &kp, grid, pl.threads, pl.smem, stream, 1);
-  if (krc != 0)
-    return fail(c, LOF_ERR_CUDA, "kernel launch failed: %s (grid %d, %d threads, %d B)",
-                cudaGetErrorString(static_cast<cudaError_t>(krc)), grid, pl.threads, pl.smem);
+  const int krc = lofk_launch_block(dtype, &kp, pr.grid, pr.plan.threads, pr.plan.smem, stream, 1);
+  if (krc != 0) {
+    snprintf(why, nwhy, "kernel launch failed: %s (grid %d, %d threads, %d B)",
+             cudaGetErrorString(static_cast<cudaError_t>(krc)), pr.grid, pr.plan.threads,
+             pr.plan.smem);
+    return LOF_ERR_CUDA;
+  }
+  return LOF_OK;
+}
+
+int host_validate_unit(int dtype, const lof_unit& u, int i, int64_t n_slots, char* why, int nwhy) {
+  const int es = esize_of(dtype);
+  if (!u.in) return snprintf(why, nwhy, "unit %d: in is NULL", i), LOF_ERR_INVALID;
+  if (u.n_chan < 1 || u.n_chan > kMaxChan)
+    return snprintf(why, nwhy, "unit %d: n_chan %d outside [1, %d]", i, u.n_chan, kMaxChan),
+           LOF_ERR_INVALID;
+  if (u.n_time < 1) return snprintf(why, nwhy, "unit %d: n_time %d < 1", i, u.n_time), LOF_ERR_INVALID;
+  if (u.in_row_stride < u.n_time && u.n_chan > 1)
+    return snprintf(why, nwhy, "unit %d: in_row_stride %lld < n_time", i,
+                    static_cast<long long>(u.in_row_stride)),
+           LOF_ERR_INVALID;
+  if (u.out && u.out_row_stride < u.n_time && u.n_chan > 1)
+    return snprintf(why, nwhy, "unit %d: out_row_stride < n_time", i), LOF_ERR_INVALID;
+  if (u.mask && u.mask_row_stride < u.n_time && u.n_chan > 1)
+    return snprintf(why, nwhy, "unit %d: mask_row_stride < n_time", i), LOF_ERR_INVALID;
+  if (u.out == u.in && u.out_row_stride != u.in_row_stride)
+    return snprintf(why, nwhy, "unit %d: in-place output needs equal strides", i), LOF_ERR_INVALID;
+  if ((reinterpret_cast<uintptr_t>(u.in) % es) || (u.out && reinterpret_cast<uintptr_t>(u.out) % es))
+    return snprintf(why, nwhy, "unit %d: data pointers must be aligned to %d bytes", i, es),
+           LOF_ERR_INVALID;
+  if (u.history_slot < -1 || (u.history_slot >= 0 && u.history_slot + u.n_chan > n_slots))
+    return snprintf(why, nwhy, "unit %d: history slots [%lld, +%d) outside [0, %lld)", i,
+                    static_cast<long long>(u.history_slot), u.n_chan,
+                    static_cast<long long>(n_slots)),
+           LOF_ERR_INVALID;
+  return LOF_OK;
+}
+
+void host_set_error(const char* msg) {
+  snprintf(g_create_error, sizeof g_create_error, "%s", msg);
+}
+
+int host_check_dtype(int dtype, char* why, int nwhy) {
+  if (esize_of(dtype) == 0) return snprintf(why, nwhy, "unknown dtype %d", dtype), LOF_ERR_INVALID;
+  if (dtype == LOF_F32)
+    return snprintf(why, nwhy, "LOF_F32 is not implemented in this build"), LOF_ERR_UNSUPPORTED;
+  return LOF_OK;
+}
+
+}  // namespace lofk
+
+namespace {
+
+lofk::HostCfg host_cfg(const lof_ctx* c) {
+  return lofk::HostCfg{c->n_sm, c->smem_per_sm, c->smem_optin, c->tuning};
+}
+
+// Builds and launches one block for units already holding DEVICE pointers.
+int flag_block_device(lof_ctx* c, int dtype, const lof_unit* units, int n_units, uint64_t seq,
+                      void* stream) {
+  char why[512];
+  const lofk::HostCfg h = host_cfg(c);
+  std::vector<int> Ts(n_units);
+  int n_items = 0;
+  int rc = lofk::host_count_items(h, dtype, units, n_units, Ts.data(), &n_items, why, sizeof why);
+  if (rc) return fail(c, rc, "lof_flag_block: %s", why);
+  std::vector<DevUnit> du(n_units);
+  std::vector<Item> items(n_items);
+  lofk::Prep pr{};
+  rc = lofk::host_prepare(h, dtype, units, n_units, du.data(), items.data(), n_items, Ts.data(), &pr,
+                          why, sizeof why);
+  if (rc) return fail(c, rc, "lof_flag_block: %s", why);
+  const int grid = pr.grid;
+  if ((rc = grow(c, &c->d_units, &c->cap_units, n_units, "units"))) return rc;
+  if ((rc = grow(c, &c->d_items, &c->cap_items, pr.n_items, "items"))) return rc;
+  if ((rc = grow(c, &c->d_ctl, &c->cap_ctl, n_units, "unit control"))) return rc;
+  if ((rc = grow(c, &c->d_chanS, &c->cap_chan, static_cast<size_t>(pr.n_chan), "spectrum"))) return rc;
+  if ((rc = grow(c, &c->d_chanFc, &c->cap_chanfc, static_cast<size_t>(pr.n_chan), "channel flags")))
+    return rc;
+  if ((rc = grow(c, &c->d_slots, &c->cap_slots, static_cast<size_t>(grid), "slots"))) return rc;
+  if ((rc = grow(c, &c->d_pub, &c->cap_pub, static_cast<size_t>(grid) * lofk::kCoarseBins, "histograms")))
+    return rc;
+  if ((rc = grow(c, &c->d_pubm, &c->cap_pubm, static_cast<size_t>(grid) * 4, "moments"))) return rc;
+  if ((rc = grow(c, &c->d_members, &c->cap_members, static_cast<size_t>(pr.n_items), "members"))) return rc;
+  // stage descriptors (pinned ring)
+  const size_t bytes_units = n_units * sizeof(DevUnit);
+  const size_t bytes_items = pr.n_items * sizeof(Item);
+  const size_t bytes = bytes_units + bytes_items;
+  const int si = c->stage_next;
+  c->stage_next = (si + 1) % kStageRing;
+  cudaError_t e = cudaEventSynchronize(c->ev_stage[si]);
+  if (e != cudaSuccess) return cuda_fail(c, e, "cudaEventSynchronize");
+  if (c->cap_stage[si] < bytes) {
+    if (c->h_stage[si]) cudaFreeHost(c->h_stage[si]);
+    c->h_stage[si] = nullptr;
+    size_t n = std::max(bytes, 2 * c->cap_stage[si]);
+    e = cudaHostAlloc(&c->h_stage[si], n, cudaHostAllocDefault);
+    if (e != cudaSuccess) return fail(c, LOF_ERR_NOMEM, "pinned staging: %s", cudaGetErrorString(e));
+    c->cap_stage[si] = n;
+  }
+  uint8_t* hs = static_cast<uint8_t*>(c->h_stage[si]);
+  memcpy(hs, du.data(), bytes_units);
+  memcpy(hs + bytes_units, items.data(), bytes_items);
+  lofk::Scratch sc{};
+  sc.units = c->d_units;
+  sc.items = c->d_items;
+  sc.ctl = c->d_ctl;
+  sc.chanS = c->d_chanS;
+  sc.chanFc = c->d_chanFc;
+  sc.slots = c->d_slots;
+  sc.pub = c->d_pub;
+  sc.pubm = c->d_pubm;
+  sc.members = c->d_members;
+  sc.ctrl = c->d_ctrl;
+  sc.hist = c->hist;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  rc = lofk::host_launch(c->params, h, dtype, pr, sc, reinterpret_cast<const DevUnit*>(hs), n_units,
+                         reinterpret_cast<const Item*>(hs + bytes_units), seq, stream, why, sizeof why);
+  cudaEventRecord(c->ev_stage[si], st);
+  if (rc) return fail(c, rc, "lof_flag_block: %s", why);
   if ((e = cudaMemcpyAsync(c->h_err, c->d_ctrl + 1, 3 * sizeof(int), cudaMemcpyDeviceToHost, st)) !=
       cudaSuccess)
     return cuda_fail(c, e, "error word copy");
@@ -563,29 +663,13 @@ int flag_block_device(lof_ctx* c, int dtype, const lof_unit* units, int n_units,
 }
 
 int validate_units(lof_ctx* c, int dtype, const lof_unit* units, int n_units) {
-  if (esize_of(dtype) == 0) return fail(c, LOF_ERR_INVALID, "unknown dtype %d", dtype);
-  if (dtype == LOF_F32) return fail(c, LOF_ERR_UNSUPPORTED, "LOF_F32 is not implemented in this build");
+  char why[512];
+  int rc = lofk::host_check_dtype(dtype, why, sizeof why);
+  if (rc) return fail(c, rc, "%s", why);
   if (n_units < 0 || (n_units > 0 && !units)) return fail(c, LOF_ERR_INVALID, "bad unit array");
-  const int es = esize_of(dtype);
   for (int i = 0; i < n_units; ++i) {
-    const lof_unit& u = units[i];
-    if (!u.in) return fail(c, LOF_ERR_INVALID, "unit %d: in is NULL", i);
-    if (u.n_chan < 1 || u.n_chan > lofk::kMaxChan)
-      return fail(c, LOF_ERR_INVALID, "unit %d: n_chan %d outside [1, %d]", i, u.n_chan, lofk::kMaxChan);
-    if (u.n_time < 1) return fail(c, LOF_ERR_INVALID, "unit %d: n_time %d < 1", i, u.n_time);
-    if (u.in_row_stride < u.n_time && u.n_chan > 1)
-      return fail(c, LOF_ERR_INVALID, "unit %d: in_row_stride %lld < n_time", i, (long long)u.in_row_stride);
-    if (u.out && u.out_row_stride < u.n_time && u.n_chan > 1)
-      return fail(c, LOF_ERR_INVALID, "unit %d: out_row_stride < n_time", i);
-    if (u.mask && u.mask_row_stride < u.n_time && u.n_chan > 1)
-      return fail(c, LOF_ERR_INVALID, "unit %d: mask_row_stride < n_time", i);
-    if (u.out == u.in && u.out_row_stride != u.in_row_stride)
-      return fail(c, LOF_ERR_INVALID, "unit %d: in-place output needs equal strides", i);
-    if ((reinterpret_cast<uintptr_t>(u.in) % es) || (u.out && reinterpret_cast<uintptr_t>(u.out) % es))
-      return fail(c, LOF_ERR_INVALID, "unit %d: data pointers must be aligned to %d bytes", i, es);
-    if (u.history_slot < -1 || (u.history_slot >= 0 && u.history_slot + u.n_chan > c->n_slots))
-      return fail(c, LOF_ERR_INVALID, "unit %d: history slots [%lld, +%d) outside [0, %lld)", i,
-                  (long long)u.history_slot, u.n_chan, (long long)c->n_slots);
+    rc = lofk::host_validate_unit(dtype, units[i], i, c->n_slots, why, sizeof why);
+    if (rc) return fail(c, rc, "%s", why);
   }
   return LOF_OK;
 }
@@ -814,9 +898,9 @@ extern "C" int lof_max_time(const lof_ctx* c, int dtype) {
   int lo = 0, hi = 1 << 20;
   while (hi - lo > 1) {
     const int mid = (lo + hi) / 2;
-    Plan pl;
-    std::string why;
-    if (make_plan(c, dtype, &mid, 1, &pl, &why)) lo = mid;
+    lofk::Plan pl;
+    char why[256];
+    if (make_plan(host_cfg(c), dtype, &mid, 1, &pl, why, sizeof why)) lo = mid;
     else hi = mid;
   }
   return lo;

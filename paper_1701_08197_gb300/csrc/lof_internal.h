@@ -151,6 +151,45 @@ struct CommitParams {
   int history_min;
 };
 
+// ---------------------------------------------------------------- host side
+struct HostCfg {
+  int n_sm, smem_per_sm, smem_optin;
+  lof_tuning tuning;
+};
+struct Plan {
+  int threads, ctas;
+  int tile, pfx_words, mbits_words, fbits_words, smem;
+};
+struct Prep {
+  Plan plan;
+  int n_items, grid;
+  int64_t n_chan;
+};
+// Device memory one launch works in.
+struct Scratch {
+  DevUnit* units;
+  Item* items;
+  UnitCtl* ctl;
+  unsigned long long* chanS;
+  uint8_t* chanFc;
+  Slot* slots;
+  uint32_t* pub;
+  unsigned long long* pubm;
+  int* members;
+  int* ctrl;  // [0] queue, [1] error, [2..3] detail
+  HistoryDev hist;
+};
+// lof_api.cu: heap-free steps shared by every entry point
+int host_check_dtype(int dtype, char* why, int nwhy);
+int host_validate_unit(int dtype, const lof_unit& u, int i, int64_t n_slots, char* why, int nwhy);
+int host_count_items(const HostCfg& h, int dtype, const lof_unit* units, int n_units, int* Ts,
+                     int* n_items, char* why, int nwhy);
+int host_prepare(const HostCfg& h, int dtype, const lof_unit* units, int n_units, DevUnit* du,
+                 Item* items, int max_items, int* Ts, Prep* out, char* why, int nwhy);
+int host_launch(const lof_params& P, const HostCfg& h, int dtype, const Prep& pr, const Scratch& sc,
+                const DevUnit* du_host, int n_units, const Item* items_host, uint64_t seq,
+                void* stream, char* why, int nwhy);
+
 }  // namespace lofk
 
 // Kernel launchers (lof_kernels.cu)

@@ -26,6 +26,7 @@ EXPORTED = [
     "lof_default_params", "lof_create", "lof_flag_block", "lof_flag_block_host",
     "lof_history_update", "lof_history_export", "lof_history_import", "lof_status",
     "lof_max_time", "lof_set_tuning", "lof_get_tuning", "lof_last_error", "lof_destroy",
+    "lof_flag_block_noalloc",
 ]
 
 
@@ -120,9 +121,10 @@ def library(build: bool = True):
     L.lof_last_error.argtypes = [V]
     L.lof_last_error.restype = ctypes.c_char_p
     L.lof_destroy.argtypes = [V]
+    L.lof_flag_block_noalloc.argtypes = [P(lof_params), ctypes.c_int, P(lof_unit), ctypes.c_int, V, V]
     for name in ("lof_create", "lof_flag_block", "lof_flag_block_host", "lof_history_update",
                  "lof_history_export", "lof_history_import", "lof_status", "lof_max_time",
-                 "lof_set_tuning", "lof_get_tuning", "lof_destroy"):
+                 "lof_set_tuning", "lof_get_tuning", "lof_destroy", "lof_flag_block_noalloc"):
         getattr(L, name).restype = ctypes.c_int
     _lib = L
     return L
@@ -168,6 +170,14 @@ def lof_flag_block(ctx, dtype: int, units, block_seq: int, stream: int) -> int:
 def lof_flag_block_host(ctx, dtype: int, units, block_seq: int, stream: int) -> int:
     arr, n = _units_array(units)
     return library().lof_flag_block_host(ctx, dtype, arr, n, block_seq, ctypes.c_void_p(stream))
+
+
+def lof_flag_block_noalloc(params, dtype: int, units, status_ptr: int, stream: int) -> int:
+    """Context-free, allocation-free flagging of one block (no history)."""
+    arr, n = _units_array(units)
+    return library().lof_flag_block_noalloc(ctypes.byref(params) if params is not None else None,
+                                            dtype, arr, n, ctypes.c_void_p(status_ptr or None),
+                                            ctypes.c_void_p(stream))
 
 
 def lof_history_update(ctx, units, stream: int) -> int:
