@@ -107,9 +107,9 @@ typedef struct {
  *  history_slot: first of n_chan consecutive history slots of the context, or
  *          -1 for no history (the history flagger is then skipped for the unit).
  *  stats : optional device lof_unit_stats*, or NULL.
- * Limits: 1 <= n_chan <= 4096, 1 <= n_time, and one row (n_time samples) must
- * fit the kernel's shared-memory tile (n_time <= 12288 for CI16/F32, <= 24576
- * for CI8); see lof_max_time(). */
+ * Limits: 1 <= n_chan <= 2048, 1 <= n_time, and one row must fit the
+ * kernel's shared-memory buffer for the time pass (about 4.6 bytes per sample:
+ * n_time up to ~20000 with the default tuning); see lof_max_time(). */
 typedef struct {
   const void *in;
   void *out;
@@ -188,9 +188,10 @@ int lof_get_tuning(const lof_ctx *ctx, lof_tuning *t);
  * processes with a fixed allocation budget, or hosts without a memory pool.
  * It needs no context: params may be NULL (defaults), and the history flagger
  * is unavailable (every unit must have history_slot = -1).  Its scratch is
- * one file-scope device array of 24 MiB that every GPU which loads the
- * library holds until the process exits; host-side descriptors live in fixed
- * static arrays (at most 1024 units and 65536 work items per call).  A block
+ * one file-scope device array of 64 MiB that every GPU which loads the
+ * library holds until the process exits (about 40 KB per unit plus 9 bytes
+ * per channel); host-side descriptors live in fixed static arrays (at most
+ * 1024 units and 262144 tasks per call).  A block
  * that does not fit is rejected with LOF_ERR_INVALID and a message
  * (lof_last_error(NULL)); nothing is launched then.
  * The first call on each device looks up the device address of the array

@@ -8,6 +8,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <cmath>
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
@@ -18,10 +19,9 @@
 #include "lof_internal.h"
 
 using lofk::DevUnit;
-using lofk::Item;
+using lofk::Task;
 using lofk::KParams;
-using lofk::Slot;
-using lofk::UnitCtl;
+using lofk::UnitState;
 
 namespace {
 
@@ -46,7 +46,7 @@ struct lof_ctx {
   lof_params params{};
   int n_sm = 0;
   int smem_per_sm = 0, smem_optin = 0;
-  lof_tuning tuning{256, 2, 0, 512};
+  lof_tuning tuning{256, 2, 0, 2048};
   // history
   int64_t n_slots = 0;
   int H = 0;
@@ -54,21 +54,13 @@ struct lof_ctx {
   // scratch
   DevUnit* d_units = nullptr;
   size_t cap_units = 0;
-  Item* d_items = nullptr;
-  size_t cap_items = 0;
-  UnitCtl* d_ctl = nullptr;
-  size_t cap_ctl = 0;
+  Task* d_tasks = nullptr;
+  size_t cap_tasks = 0;
+  UnitState* d_ustate = nullptr;
+  size_t cap_ustate = 0;
   unsigned long long* d_chanS = nullptr;
   uint8_t* d_chanFc = nullptr;
   size_t cap_chan = 0, cap_chanfc = 0;
-  Slot* d_slots = nullptr;
-  size_t cap_slots = 0;
-  uint32_t* d_pub = nullptr;
-  size_t cap_pub = 0;
-  unsigned long long* d_pubm = nullptr;
-  size_t cap_pubm = 0;
-  int* d_members = nullptr;
-  size_t cap_members = 0;
   int* d_ctrl = nullptr;  // [0] queue, [1] error, [2..3] error detail
   int* h_err = nullptr;   // pinned copy of d_ctrl[1..3]
   cudaEvent_t ev_err = nullptr;
@@ -157,9 +149,6 @@ int pfx_row_words(int dtype, int T) {
   return ((nch + 3) * 36 + 2 * (nch + 4) + 3) & ~3;  // 16-byte aligned rows
 }
 
-int dpitch_of(int dtype, int T) {
-  return static_cast<int>(round_up64(static_cast<int64_t>(T) * esize_of(dtype), 128));
-}
 
 // Budget of dynamic shared memory per CTA.
 int dyn_budget(const lofk::HostCfg& h, int dtype, int threads, int ctas) {
@@ -167,13 +156,6 @@ int dyn_budget(const lofk::HostCfg& h, int dtype, int threads, int ctas) {
   return std::min(per, h.smem_optin) - static_smem_bytes(dtype, threads);
 }
 
-// rows of one item for a unit with n_time T, given a tile size
-int rows_per_item(int dtype, int T, int tile) {
-  const int dp = dpitch_of(dtype, T);
-  int R = tile / dp;
-  R = std::min(R, lofk::kMaxRowsPerItem);
-  return R;
-}
 
 }  // namespace
 
@@ -257,6 +239,7 @@ extern "C" int lof_create(const lof_params* params, int cuda_device, int64_t n_h
   ck(cudaMalloc(&c->hist.pend, ns * sizeof(double)), "history pending");
   ck(cudaMalloc(&c->hist.pend_flag, ns), "history pending flag");
   ck(cudaMalloc(&c->hist.pend_seq, ns * sizeof(uint64_t)), "history pending seq");
+  ck(cudaMalloc(&c->hist.hint, ns * 2 * sizeof(unsigned long long)), "statistics hints");
   ck(cudaMalloc(&c->d_ctrl, 4 * sizeof(int)), "control words");
   ck(cudaHostAlloc(&c->h_err, 4 * sizeof(int), cudaHostAllocDefault), "pinned error word");
   ck(cudaEventCreateWithFlags(&c->ev_err, cudaEventDisableTiming), "event");
@@ -268,6 +251,7 @@ extern "C" int lof_create(const lof_params* params, int cuda_device, int64_t n_h
     ck(cudaMemset(c->hist.head, 0, ns * sizeof(int32_t)), "memset");
     ck(cudaMemset(c->hist.thr, 0, ns * sizeof(double)), "memset");
     ck(cudaMemset(c->hist.pend_flag, 0, ns), "memset");
+    ck(cudaMemset(c->hist.hint, 0xFF, ns * 2 * sizeof(unsigned long long)), "memset");
     ck(cudaMemset(c->d_ctrl, 0, 4 * sizeof(int)), "memset");
     ck(cudaDeviceSynchronize(), "cudaDeviceSynchronize");
     memset(c->h_err, 0, 4 * sizeof(int));
@@ -293,15 +277,12 @@ extern "C" int lof_destroy(lof_ctx* c) {
   cudaFree(c->hist.pend);
   cudaFree(c->hist.pend_flag);
   cudaFree(c->hist.pend_seq);
+  cudaFree(c->hist.hint);
   cudaFree(c->d_units);
-  cudaFree(c->d_items);
-  cudaFree(c->d_ctl);
+  cudaFree(c->d_tasks);
+  cudaFree(c->d_ustate);
   cudaFree(c->d_chanS);
   cudaFree(c->d_chanFc);
-  cudaFree(c->d_slots);
-  cudaFree(c->d_pub);
-  cudaFree(c->d_pubm);
-  cudaFree(c->d_members);
   cudaFree(c->d_ctrl);
   cudaFree(c->d_io);
   if (c->h_err) cudaFreeHost(c->h_err);
@@ -347,59 +328,87 @@ extern "C" int lof_get_tuning(const lof_ctx* c, lof_tuning* t) {
 
 namespace {
 
-// Shared-memory plan: tile of rows, prefix/workspace, flag words.
+// Rows of one flag task: as many as fit the shared-memory budget (prefix
+// buffer + flag words + fire words per row).
+int flag_rows(int dtype, int T, int budget_bytes) {
+  const int words = pfx_row_words(dtype, T) + 2 * ((T + 31) / 32 + 4);
+  return std::min(lofk::kMaxRowsPerTask, budget_bytes / (4 * words));
+}
+
+// Rows of one stats / fine task (streamed, ~64K samples per task).
+int stat_rows(int T) { return std::max(1, std::min(lofk::kMaxRowsPerTask, 65536 / std::max(1, T))); }
+
+// Shared-memory plan: the largest flag task of the launch or the unit-wide
+// workspace, whichever is larger.
 bool make_plan(const lofk::HostCfg& h, int dtype, const int* Ts, int nT, lofk::Plan* pl,
                char* why, int nwhy) {
   pl->threads = h.tuning.threads;
   pl->ctas = h.tuning.ctas_per_sm;
-  const int budget = dyn_budget(h, dtype, pl->threads, pl->ctas);
-  int pfx = lofk::kWorkspaceBytes / 4;
-  for (int i = 0; i < nT; ++i) pfx = std::max(pfx, pfx_row_words(dtype, Ts[i]));
-  int tile = h.tuning.tile_bytes ? h.tuning.tile_bytes : (budget - 4 * pfx) / 128 * 128;
-  for (int iter = 0; iter < 8; ++iter) {
-    int mb = 0, fb = 0;
-    for (int i = 0; i < nT; ++i) {
-      const int T = Ts[i];
-      const int R = rows_per_item(dtype, T, tile);
-      if (R < 1) {
-        snprintf(why, nwhy, "n_time %d does not fit the shared-memory tile (%d bytes)", T, tile);
-        return false;
-      }
-      const int words = (T + 31) / 32 + 4;
-      const int nb = std::max(1, std::min(R, pfx / pfx_row_words(dtype, T)));
-      mb = std::max(mb, R * words);
-      fb = std::max(fb, nb * words);
+  int budget = dyn_budget(h, dtype, pl->threads, pl->ctas);
+  if (h.tuning.tile_bytes) budget = std::min(budget, h.tuning.tile_bytes);
+  int need = lofk::kWorkspaceBytes;
+  for (int i = 0; i < nT; ++i) {
+    const int R = flag_rows(dtype, Ts[i], budget);
+    if (R < 1) {
+      snprintf(why, nwhy, "n_time %d does not fit the shared-memory budget (%d bytes)", Ts[i], budget);
+      return false;
     }
-    const int total = tile + 4 * (pfx + mb + fb);
-    if (total <= budget || h.tuning.tile_bytes) {
-      pl->tile = tile;
-      pl->pfx_words = pfx;
-      pl->mbits_words = mb;
-      pl->fbits_words = fb;
-      pl->smem = total;
-      if (total > budget) {
-        snprintf(why, nwhy, "tuned tile_bytes exceeds the shared-memory budget");
-        return false;
-      }
-      return true;
-    }
-    tile -= (total - budget + 127) / 128 * 128;
-    tile = tile / 128 * 128;
-    if (tile < 1024) break;
+    const int words = pfx_row_words(dtype, Ts[i]) + 2 * ((Ts[i] + 31) / 32 + 4);
+    need = std::max(need, R * words * 4);
   }
-  snprintf(why, nwhy, "no shared-memory plan fits");
-  return false;
+  if (need > budget) {
+    snprintf(why, nwhy, "the workspace (%d bytes) exceeds the shared-memory budget (%d)", need, budget);
+    return false;
+  }
+  pl->smem = need;
+  return true;
 }
 
 }  // namespace
 
 namespace lofk {
 
+int host_count_tasks(const HostCfg& h, int dtype, const lof_unit* units, int n_units,
+                     int* n_tasks, char* why, int nwhy) {
+  int budget = dyn_budget(h, dtype, h.tuning.threads, h.tuning.ctas_per_sm);
+  if (h.tuning.tile_bytes) budget = std::min(budget, h.tuning.tile_bytes);
+  int64_t n = 0;
+  for (int i = 0; i < n_units; ++i) {
+    const int T = units[i].n_time, C = units[i].n_chan;
+    const int Rc = flag_rows(dtype, T, budget);
+    if (Rc < 1) {
+      snprintf(why, nwhy, "n_time %d does not fit the shared-memory budget (%d bytes)", T, budget);
+      return LOF_ERR_INVALID;
+    }
+    const int Rs = stat_rows(T);
+    n += 2 * ((C + Rs - 1) / Rs) + (C + Rc - 1) / Rc;
+  }
+  if (n > (int64_t(1) << 30)) {
+    snprintf(why, nwhy, "too many tasks");
+    return LOF_ERR_INVALID;
+  }
+  *n_tasks = static_cast<int>(n);
+  return LOF_OK;
+}
+
 int host_prepare(const HostCfg& h, int dtype, const lof_unit* units, int n_units, DevUnit* du,
-                 Item* items, int max_items, int* Ts, Prep* out, char* why, int nwhy) {
+                 Task* tasks, int max_tasks, Prep* out, char* why, int nwhy) {
   const int es = esize_of(dtype);
-  for (int i = 0; i < n_units; ++i) Ts[i] = units[i].n_time;
-  if (!make_plan(h, dtype, Ts, n_units, &out->plan, why, nwhy)) return LOF_ERR_INVALID;
+  // plan over the distinct row lengths (bounded scan; units share few shapes)
+  int Ts[64];
+  int nT = 0;
+  for (int i = 0; i < n_units; ++i) {
+    bool seen = false;
+    for (int j = 0; j < nT; ++j) seen = seen || Ts[j] == units[i].n_time;
+    if (!seen) {
+      if (nT == 64) {
+        snprintf(why, nwhy, "more than 64 distinct n_time values in one block");
+        return LOF_ERR_INVALID;
+      }
+      Ts[nT++] = units[i].n_time;
+    }
+  }
+  if (!make_plan(h, dtype, Ts, nT, &out->plan, why, nwhy)) return LOF_ERR_INVALID;
   const Plan& pl = out->plan;
   int occ = 0;
   const int krc = lofk_max_blocks_per_sm(dtype, pl.threads, pl.smem, &occ);
@@ -409,8 +418,9 @@ int host_prepare(const HostCfg& h, int dtype, const lof_unit* units, int n_units
     return LOF_ERR_CUDA;
   }
   const int ctas = std::min(pl.ctas, occ);
-  int64_t chan = 0;
-  int n_items = 0, maxG = 0;
+  int budget = dyn_budget(h, dtype, pl.threads, pl.ctas);
+  if (h.tuning.tile_bytes) budget = std::min(budget, h.tuning.tile_bytes);
+  int64_t chan = 0, per_step = 0;
   for (int i = 0; i < n_units; ++i) {
     const lof_unit& u = units[i];
     DevUnit& d = du[i];
@@ -427,93 +437,91 @@ int host_prepare(const HostCfg& h, int dtype, const lof_unit* units, int n_units
     d.chan_off = static_cast<int32_t>(chan);
     chan += u.n_chan;
     int flags = 0;
-    const int64_t rowb = static_cast<int64_t>(u.n_time) * es;
-    if ((reinterpret_cast<uintptr_t>(u.in) % 16) == 0 && ((u.in_row_stride * es) % 16) == 0 &&
-        (rowb % 16) == 0)
-      flags |= kUnitInBulk;
+    if ((reinterpret_cast<uintptr_t>(u.in) % 16) == 0 && ((u.in_row_stride * es) % 16) == 0)
+      flags |= kUnitInVec;
     if (u.out && u.out == u.in) flags |= kUnitInPlace;
     else if (u.out && (reinterpret_cast<uintptr_t>(u.out) % 16) == 0 &&
-             ((u.out_row_stride * es) % 16) == 0 && (rowb % 16) == 0)
-      flags |= kUnitOutBulk;
+             ((u.out_row_stride * es) % 16) == 0)
+      flags |= kUnitOutVec;
     if (u.mask && (reinterpret_cast<uintptr_t>(u.mask) % 16) == 0 && (u.mask_row_stride % 16) == 0)
       flags |= kUnitMaskVec;
     d.flags = flags;
-    const int Rmax = rows_per_item(dtype, u.n_time, pl.tile);
-    const int nit = (u.n_chan + Rmax - 1) / Rmax;
-    const int R = (u.n_chan + nit - 1) / nit;
-    d.first_item = n_items;
-    d.n_items = nit;
-    maxG = std::max(maxG, nit);
-    for (int r0 = 0; r0 < u.n_chan; r0 += R) {
-      if (n_items >= max_items) {
-        snprintf(why, nwhy, "more than %d items in one block", max_items);
-        return LOF_ERR_INVALID;
-      }
-      items[n_items++] = Item{i, r0, std::min(R, u.n_chan - r0), 0};
+    const int Rs = stat_rows(u.n_time), Rc = flag_rows(dtype, u.n_time, budget);
+    d.nS = (u.n_chan + Rs - 1) / Rs;
+    d.nF = d.nS;
+    d.nC = (u.n_chan + Rc - 1) / Rc;
+    d.pad = 0;
+    per_step += d.nS + d.nC;
+  }
+  // Queue order, software-pipelined over units: step s holds the stats tasks
+  // of unit s, the fine tasks of unit s - dF and the flag tasks of unit s - dC,
+  // so that a unit's statistics are normally final before its flag tasks
+  // are taken, while its rows are still in L2.
+  const int grid = static_cast<int>(std::min<int64_t>(int64_t(h.n_sm) * ctas, std::max<int64_t>(1, per_step)));
+  const double avg = static_cast<double>(per_step) / std::max(1, n_units);
+  const int inflight = static_cast<int>(std::ceil(grid / std::max(1.0, avg)));
+  const int dF = inflight + 2, dC = dF + inflight + 2;
+  int n = 0;
+  auto emit = [&](int ui, int kind) -> bool {
+    const DevUnit& d = du[ui];
+    const int rows = kind == kTaskFlag ? (d.C + d.nC - 1) / d.nC : (d.C + d.nS - 1) / d.nS;
+    for (int r0 = 0; r0 < d.C; r0 += rows) {
+      if (n >= max_tasks) return false;
+      tasks[n++] = Task{ui, kind, r0, std::min(rows, d.C - r0)};
+    }
+    return true;
+  };
+  for (int step = 0; step < n_units + dC; ++step) {
+    bool ok = true;
+    if (step < n_units) ok = ok && emit(step, kTaskStats);
+    if (step - dF >= 0 && step - dF < n_units) ok = ok && emit(step - dF, kTaskFine);
+    if (step - dC >= 0 && step - dC < n_units) ok = ok && emit(step - dC, kTaskFlag);
+    if (!ok) {
+      snprintf(why, nwhy, "more than %d tasks in one block", max_tasks);
+      return LOF_ERR_INVALID;
     }
   }
-  if (maxG > h.n_sm * ctas) {
-    snprintf(why, nwhy,
-             "a unit needs %d co-resident CTAs, the device holds %d; use fewer channels per unit",
-             maxG, h.n_sm * ctas);
-    return LOF_ERR_UNSUPPORTED;
-  }
-  out->n_items = n_items;
-  out->n_chan = chan;
-  out->grid = std::min(h.n_sm * ctas, n_items);
-  return LOF_OK;
-}
-
-// Count of items host_prepare will produce (for sizing host arrays).
-int host_count_items(const HostCfg& h, int dtype, const lof_unit* units, int n_units, int* Ts,
-                     int* n_items, char* why, int nwhy) {
-  Plan pl;
-  for (int i = 0; i < n_units; ++i) Ts[i] = units[i].n_time;
-  if (!make_plan(h, dtype, Ts, n_units, &pl, why, nwhy)) return LOF_ERR_INVALID;
-  int n = 0;
+  // the row runs must match the task counts recorded per unit
   for (int i = 0; i < n_units; ++i) {
-    const int Rmax = rows_per_item(dtype, units[i].n_time, pl.tile);
-    const int nit = (units[i].n_chan + Rmax - 1) / Rmax;
-    n += nit;
+    DevUnit& d = du[i];
+    const int rs = (d.C + d.nS - 1) / d.nS, rc = (d.C + d.nC - 1) / d.nC;
+    d.nS = (d.C + rs - 1) / rs;
+    d.nF = d.nS;
+    d.nC = (d.C + rc - 1) / rc;
   }
-  *n_items = n;
+  out->n_tasks = n;
+  out->n_chan = chan;
+  out->grid = std::min(grid, n);
   return LOF_OK;
 }
 
 int host_launch(const lof_params& P, const HostCfg& h, int dtype, const Prep& pr,
-                const Scratch& sc, const DevUnit* du_host, int n_units, const Item* items_host,
+                const Scratch& sc, const DevUnit* du_host, int n_units, const Task* tasks_host,
                 uint64_t seq, void* stream, char* why, int nwhy) {
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   cudaError_t e;
   if ((e = cudaMemcpyAsync(sc.units, du_host, n_units * sizeof(DevUnit), cudaMemcpyHostToDevice, st)) !=
           cudaSuccess ||
-      (e = cudaMemcpyAsync(sc.items, items_host, pr.n_items * sizeof(Item), cudaMemcpyHostToDevice,
+      (e = cudaMemcpyAsync(sc.tasks, tasks_host, pr.n_tasks * sizeof(Task), cudaMemcpyHostToDevice,
                            st)) != cudaSuccess ||
-      (e = cudaMemsetAsync(sc.ctl, 0, n_units * sizeof(UnitCtl), st)) != cudaSuccess ||
+      (e = cudaMemset2DAsync(sc.ustate, sizeof(UnitState), 0, kUnitStateZeroBytes, n_units, st)) !=
+          cudaSuccess ||
       (e = cudaMemsetAsync(sc.ctrl, 0, sizeof(int), st)) != cudaSuccess) {
     snprintf(why, nwhy, "descriptor upload: %s", cudaGetErrorString(e));
     return LOF_ERR_CUDA;
   }
   KParams kp{};
   kp.units = sc.units;
-  kp.items = sc.items;
-  kp.ctl = sc.ctl;
+  kp.tasks = sc.tasks;
+  kp.ustate = sc.ustate;
   kp.chan_S = sc.chanS;
   kp.chan_Fc = sc.chanFc;
-  kp.slots = sc.slots;
-  kp.pub = sc.pub;
-  kp.pubm = sc.pubm;
-  kp.members = sc.members;
   kp.queue = sc.ctrl;
   kp.err = sc.ctrl + 1;
   kp.err_info = sc.ctrl + 2;
   kp.hist = sc.hist;
   kp.n_units = n_units;
-  kp.n_items = pr.n_items;
-  kp.tile_rows_bytes = pr.plan.tile;
-  kp.pfx_words = pr.plan.pfx_words;
-  kp.mbits_words = pr.plan.mbits_words;
-  kp.fbits_words = pr.plan.fbits_words;
+  kp.n_tasks = pr.n_tasks;
   kp.fine_bins = h.tuning.fine_bins;
   for (int k = 0; k <= kMaxLogWindow; ++k) {
     // Section 2.1: factor_I = startThreshold * p^(log2 I) / I (p^k by k products)
@@ -596,32 +604,12 @@ int flag_block_device(lof_ctx* c, int dtype, const lof_unit* units, int n_units,
                       void* stream) {
   char why[512];
   const lofk::HostCfg h = host_cfg(c);
-  std::vector<int> Ts(n_units);
-  int n_items = 0;
-  int rc = lofk::host_count_items(h, dtype, units, n_units, Ts.data(), &n_items, why, sizeof why);
+  int n_tasks = 0;
+  int rc = lofk::host_count_tasks(h, dtype, units, n_units, &n_tasks, why, sizeof why);
   if (rc) return fail(c, rc, "lof_flag_block: %s", why);
-  std::vector<DevUnit> du(n_units);
-  std::vector<Item> items(n_items);
-  lofk::Prep pr{};
-  rc = lofk::host_prepare(h, dtype, units, n_units, du.data(), items.data(), n_items, Ts.data(), &pr,
-                          why, sizeof why);
-  if (rc) return fail(c, rc, "lof_flag_block: %s", why);
-  const int grid = pr.grid;
-  if ((rc = grow(c, &c->d_units, &c->cap_units, n_units, "units"))) return rc;
-  if ((rc = grow(c, &c->d_items, &c->cap_items, pr.n_items, "items"))) return rc;
-  if ((rc = grow(c, &c->d_ctl, &c->cap_ctl, n_units, "unit control"))) return rc;
-  if ((rc = grow(c, &c->d_chanS, &c->cap_chan, static_cast<size_t>(pr.n_chan), "spectrum"))) return rc;
-  if ((rc = grow(c, &c->d_chanFc, &c->cap_chanfc, static_cast<size_t>(pr.n_chan), "channel flags")))
-    return rc;
-  if ((rc = grow(c, &c->d_slots, &c->cap_slots, static_cast<size_t>(grid), "slots"))) return rc;
-  if ((rc = grow(c, &c->d_pub, &c->cap_pub, static_cast<size_t>(grid) * lofk::kCoarseBins, "histograms")))
-    return rc;
-  if ((rc = grow(c, &c->d_pubm, &c->cap_pubm, static_cast<size_t>(grid) * 4, "moments"))) return rc;
-  if ((rc = grow(c, &c->d_members, &c->cap_members, static_cast<size_t>(pr.n_items), "members"))) return rc;
-  // stage descriptors (pinned ring)
+  // stage descriptors (pinned ring): units then tasks
   const size_t bytes_units = n_units * sizeof(DevUnit);
-  const size_t bytes_items = pr.n_items * sizeof(Item);
-  const size_t bytes = bytes_units + bytes_items;
+  const size_t bytes = bytes_units + static_cast<size_t>(n_tasks) * sizeof(Task);
   const int si = c->stage_next;
   c->stage_next = (si + 1) % kStageRing;
   cudaError_t e = cudaEventSynchronize(c->ev_stage[si]);
@@ -635,23 +623,27 @@ int flag_block_device(lof_ctx* c, int dtype, const lof_unit* units, int n_units,
     c->cap_stage[si] = n;
   }
   uint8_t* hs = static_cast<uint8_t*>(c->h_stage[si]);
-  memcpy(hs, du.data(), bytes_units);
-  memcpy(hs + bytes_units, items.data(), bytes_items);
+  DevUnit* du = reinterpret_cast<DevUnit*>(hs);
+  Task* tasks = reinterpret_cast<Task*>(hs + bytes_units);
+  lofk::Prep pr{};
+  rc = lofk::host_prepare(h, dtype, units, n_units, du, tasks, n_tasks, &pr, why, sizeof why);
+  if (rc) return fail(c, rc, "lof_flag_block: %s", why);
+  if ((rc = grow(c, &c->d_units, &c->cap_units, n_units, "units"))) return rc;
+  if ((rc = grow(c, &c->d_tasks, &c->cap_tasks, pr.n_tasks, "tasks"))) return rc;
+  if ((rc = grow(c, &c->d_ustate, &c->cap_ustate, n_units, "unit state"))) return rc;
+  if ((rc = grow(c, &c->d_chanS, &c->cap_chan, static_cast<size_t>(pr.n_chan), "spectrum"))) return rc;
+  if ((rc = grow(c, &c->d_chanFc, &c->cap_chanfc, static_cast<size_t>(pr.n_chan), "channel flags")))
+    return rc;
   lofk::Scratch sc{};
   sc.units = c->d_units;
-  sc.items = c->d_items;
-  sc.ctl = c->d_ctl;
+  sc.tasks = c->d_tasks;
+  sc.ustate = c->d_ustate;
   sc.chanS = c->d_chanS;
   sc.chanFc = c->d_chanFc;
-  sc.slots = c->d_slots;
-  sc.pub = c->d_pub;
-  sc.pubm = c->d_pubm;
-  sc.members = c->d_members;
   sc.ctrl = c->d_ctrl;
   sc.hist = c->hist;
   cudaStream_t st = static_cast<cudaStream_t>(stream);
-  rc = lofk::host_launch(c->params, h, dtype, pr, sc, reinterpret_cast<const DevUnit*>(hs), n_units,
-                         reinterpret_cast<const Item*>(hs + bytes_units), seq, stream, why, sizeof why);
+  rc = lofk::host_launch(c->params, h, dtype, pr, sc, du, n_units, tasks, seq, stream, why, sizeof why);
   cudaEventRecord(c->ev_stage[si], st);
   if (rc) return fail(c, rc, "lof_flag_block: %s", why);
   if ((e = cudaMemcpyAsync(c->h_err, c->d_ctrl + 1, 3 * sizeof(int), cudaMemcpyDeviceToHost, st)) !=

@@ -2,6 +2,7 @@
 // kernels (lof_kernels.cu) of the CUDA flagger library.  Not part of the ABI.
 #pragma once
 
+#include <cstddef>
 #include <cstdint>
 
 #include "lof.h"
@@ -14,10 +15,11 @@ constexpr int kCoarseBins = 1056;
 constexpr int kMaxLogWindow = 6;             // windows 1 .. 64
 constexpr int kKTable = 134;                 // sum_{k=0..6} (2^k + 1) threshold entries
 constexpr int kMaxChan = 2048;               // channels per unit
-constexpr int kMaxRowsPerItem = 64;          // rows of one unit staged by one CTA
-constexpr int kMaxTargets = 16;              // bins refined per selection round
+constexpr int kMaxRowsPerTask = 64;          // rows of one unit in one task
+constexpr int kMaxTargets = 32;              // bins refined per selection round
 constexpr int kMaxFine = 2048;               // counters per refinement round (upper bound)
-constexpr int kSelCap = 2560;                // bin-list capacity for exact selection
+constexpr int kMaxSpec = 1024;               // exact counters near the previous block's statistics
+constexpr int kSelCap = 2048;                // bin-list capacity for exact selection
 constexpr int kMaxRounds = 12;               // refinement rounds before giving up
 constexpr int kWorkspaceBytes = 36 * 1024;   // last-arriver workspace (overlays the prefix buffer)
 
@@ -39,26 +41,25 @@ struct DevUnit {
   int64_t hist_slot;                           // first slot, or -1
   int32_t C, T;
   int32_t chan_off;                            // into per-channel scratch
-  int32_t first_item, n_items;
+  int32_t nS, nF, nC;                          // stats / fine / flag tasks of the unit
   int32_t flags;                               // kUnit* bits
+  int32_t pad;
 };
 enum : int32_t {
-  kUnitInBulk = 1,      // every input row may be fetched with cp.async.bulk
-  kUnitOutBulk = 2,     // every output row may be written with cp.async.bulk
+  kUnitInVec = 1,       // input rows 16-byte aligned: vector loads
+  kUnitOutVec = 2,      // output rows 16-byte aligned: vector stores
   kUnitInPlace = 4,     // out == in: write flagged samples only
   kUnitMaskVec = 8,     // mask rows 16-byte aligned
 };
 
-struct Item {
-  int32_t unit, row0, nrows, pad;
+// One task of the persistent queue: a run of rows of one unit.
+enum : int32_t {
+  kTaskStats = 0,  // row sums + coarse histogram (reads the rows from HBM)
+  kTaskFine = 1,   // exact counts in refined bins (only when round 1 did not resolve)
+  kTaskFlag = 2,   // SumThreshold in time, history, mask and output
 };
-
-// Per-unit control words, zeroed before every launch.
-struct UnitCtl {
-  int arrive;    // arrivals, cumulative over rounds
-  int release;   // number of the last released round
-  int departed;  // CTAs done reading the unit's slot
-  int slot;      // slot (owning CTA) holding the unit's shared state
+struct Task {
+  int32_t unit, kind, row0, nrows;
 };
 
 // Refinement target: bin [lo, hi] split into sub-bins of width 2^shift
@@ -67,32 +68,36 @@ struct alignas(16) Target {
   uint32_t lo, hi, shift, base;
 };
 
-// Shared state of one unit while it is in flight (one per CTA of the grid;
-// the CTA that completes round 1 of a unit lends it its slot).
-struct Slot {
-  // round 1 (frequency pass)
+// Per-unit state of one launch.  The leading part (counters, moments, coarse
+// histogram) is zeroed by the host before every launch; the rest is written
+// before it is read.
+struct UnitState {
+  int done_S, done_F;        // completed stats / fine tasks
+  int ready;                 // 0: statistics pending, 1: fine counts needed, 2: final
+  int pad_ctl;
+  unsigned long long mom[4]; // sum x (lo, hi), sum x^2 (lo, hi) -- 128-bit each
+  uint32_t coarse[kCoarseBins];
+  uint32_t spec[kMaxSpec];   // exact counts in the bins around the previous block's statistics
+  // ---- end of the zeroed part
   double median_f, sigma_f;
   long long n_pool;          // samples in the time-pass pool
   int n_chan_freq;
-  int pad0;
-  // selection state
   int state;                 // kState*
   int n_bins;                // entries in the bin list
   int n_targets, n_fine;
   int round;
   int mom_ready;             // moments accumulated
+  int pad0;
   Target tgt[kMaxTargets];
   int tgt_bin[kMaxTargets];  // bin-list index each target refines
-  unsigned long long mom[4]; // sum x (lo, hi), sum x^2 (lo, hi) -- 128-bit each
-  uint32_t coarse[kCoarseBins];
   uint32_t fine[kMaxFine];
   uint32_t blo[kSelCap], bhi[kSelCap], bcnt[kSelCap];
-  // final statistics of the time pass
   double median_t, sigma_t;
   long long K[kKTable];
   int time_on;
   int pad2;
 };
+constexpr size_t kUnitStateZeroBytes = offsetof(UnitState, median_f);
 enum : int {
   kStateCoarse = 0,   // next: coarse histogram
   kStateFine = 1,     // next: fine counts for the targets
@@ -108,29 +113,22 @@ struct HistoryDev {
   double* pend;        // staged value
   uint8_t* pend_flag;  // 1 = staged
   uint64_t* pend_seq;  // block_seq of the staged value
+  unsigned long long* hint;  // [slots][2]: last exact 2*median and 4*MAD of the unit starting here
   int64_t n_slots;
   int32_t H;
 };
 
 struct KParams {
   const DevUnit* units;
-  const Item* items;
-  UnitCtl* ctl;
+  const Task* tasks;
+  UnitState* ustate;
   unsigned long long* chan_S;   // per channel spectrum sums
   uint8_t* chan_Fc;             // per channel frequency flags
-  Slot* slots;
-  uint32_t* pub;                // [grid][kCoarseBins] coarse histogram of each CTA's rows
-  unsigned long long* pubm;     // [grid][4] moments of each CTA's rows (128-bit s1, s2)
-  int* members;                 // [n_items] CTA that holds each item
-  int* queue;                   // [0] next item
+  int* queue;                   // [0] next task
   int* err;                     // first device-side error (0 = none)
   int* err_info;                // detail words of that error
   HistoryDev hist;
-  int n_units, n_items;
-  int tile_rows_bytes;          // shared bytes reserved for staged rows
-  int pfx_words;                // prefix buffer / workspace (32-bit words)
-  int mbits_words;              // flag bits of the staged rows
-  int fbits_words;              // fire bits of one batch of rows
+  int n_units, n_tasks;
   int fine_bins;                // counters per refinement round
   double factor[kMaxLogWindow + 1];
   double sensitivity;
@@ -158,36 +156,32 @@ struct HostCfg {
 };
 struct Plan {
   int threads, ctas;
-  int tile, pfx_words, mbits_words, fbits_words, smem;
+  int smem;                     // dynamic shared memory per CTA (bytes)
 };
 struct Prep {
   Plan plan;
-  int n_items, grid;
+  int n_tasks, grid;
   int64_t n_chan;
 };
 // Device memory one launch works in.
 struct Scratch {
   DevUnit* units;
-  Item* items;
-  UnitCtl* ctl;
+  Task* tasks;
+  UnitState* ustate;
   unsigned long long* chanS;
   uint8_t* chanFc;
-  Slot* slots;
-  uint32_t* pub;
-  unsigned long long* pubm;
-  int* members;
   int* ctrl;  // [0] queue, [1] error, [2..3] detail
   HistoryDev hist;
 };
 // lof_api.cu: heap-free steps shared by every entry point
 int host_check_dtype(int dtype, char* why, int nwhy);
 int host_validate_unit(int dtype, const lof_unit& u, int i, int64_t n_slots, char* why, int nwhy);
-int host_count_items(const HostCfg& h, int dtype, const lof_unit* units, int n_units, int* Ts,
-                     int* n_items, char* why, int nwhy);
+int host_count_tasks(const HostCfg& h, int dtype, const lof_unit* units, int n_units,
+                     int* n_tasks, char* why, int nwhy);
 int host_prepare(const HostCfg& h, int dtype, const lof_unit* units, int n_units, DevUnit* du,
-                 Item* items, int max_items, int* Ts, Prep* out, char* why, int nwhy);
+                 Task* tasks, int max_tasks, Prep* out, char* why, int nwhy);
 int host_launch(const lof_params& P, const HostCfg& h, int dtype, const Prep& pr, const Scratch& sc,
-                const DevUnit* du_host, int n_units, const Item* items_host, uint64_t seq,
+                const DevUnit* du_host, int n_units, const Task* tasks_host, uint64_t seq,
                 void* stream, char* why, int nwhy);
 
 }  // namespace lofk

@@ -338,22 +338,53 @@ __device__ __forceinline__ Target ld_target(const Target* p) {
   return Target{v.x, v.y, v.z, v.w};
 }
 
+// Coarse bins around the previous block's median and MAD end points (+-1/32
+// of each value), to be counted value by value while the stats tasks run.
+// Deterministic in (m2, mad4): every task of a unit derives the same list.
+// Returns the number of targets (bins, each refined to width 1).
+__device__ int spec_targets(unsigned long long m2, unsigned long long mad4, Target* tg) {
+  if (m2 == ~0ull) return 0;
+  const long long m = static_cast<long long>(m2 >> 1), d = static_cast<long long>(mad4 >> 2);
+  const long long P[3] = {m - d, m, m + d};
+  int nt = 0;
+  uint32_t base = 0;
+  for (int i = 0; i < 3; ++i) {
+    long long p = P[i] < 0 ? 0 : P[i];
+    if (p > 0xFFFFFFFFll) break;
+    const long long del = p / 32 > 2 ? p / 32 : 2;
+    const long long a = p - del < 0 ? 0 : p - del;
+    const long long b = p + del > 0xFFFFFFFFll ? 0xFFFFFFFFll : p + del;
+    const uint32_t k0 = coarse_key(static_cast<uint32_t>(a)), k1 = coarse_key(static_cast<uint32_t>(b));
+    for (uint32_t k = k0; k <= k1; ++k) {
+      uint32_t lo, hi;
+      if (!key_range(k, &lo, &hi)) continue;
+      if (nt > 0 && tg[nt - 1].lo >= lo) continue;
+      const uint32_t w = hi - lo + 1u;
+      if (base + w > static_cast<uint32_t>(kMaxSpec) || nt == kMaxTargets) return nt;
+      tg[nt++] = Target{lo, hi, 0u, base};
+      base += w;
+    }
+  }
+  return nt;
+}
+
 // ------------------------------------------------------------------ shared state
 
 template <int NT>
 struct Fixed {
   uint64_t mbar;
-  int item, ok, last, state, n_keep, n_tgt, owned_unit, slot;
+  int item, ok, last, state, n_keep, n_tgt, q_done, n_def;
+  int def[9];  // parked tasks whose unit was not ready
   unsigned int red_u32[NT / kWarp];
   unsigned long long red_a[NT / kWarp], red_b[NT / kWarp], red_c[NT / kWarp];
   unsigned long long cnt_time, cnt_total, cnt_hist;
   unsigned long long mo1, mo2lo, mo2hi;  // moments of this CTA's rows
-  unsigned long long rowS[kMaxRowsPerItem];
-  unsigned long long rowFlagSum[kMaxRowsPerItem];
-  int rowNFlag[kMaxRowsPerItem];
-  uint8_t rowFc[kMaxRowsPerItem];
-  uint8_t rowFh[kMaxRowsPerItem];
-  int keep[kMaxRowsPerItem];
+  unsigned long long rowS[kMaxRowsPerTask];
+  unsigned long long rowFlagSum[kMaxRowsPerTask];
+  int rowNFlag[kMaxRowsPerTask];
+  uint8_t rowFc[kMaxRowsPerTask];
+  uint8_t rowFh[kMaxRowsPerTask];
+  int keep[kMaxRowsPerTask];
   long long K[kKTable];
   double median_t, sigma_t;
   int time_on, kmax_t;
@@ -371,7 +402,7 @@ struct Fixed {
 // robust sigma of the spectrum and SumThreshold over it (Section 4).
 // Needs 36 KB of shared workspace.
 template <int NT>
-__device__ void frequency_pass(const KParams& kp, const DevUnit& u, Slot* slot, uint8_t* ws,
+__device__ void frequency_pass(const KParams& kp, const DevUnit& u, UnitState* slot, uint8_t* ws,
                                Fixed<NT>& f) {
   const int tid = threadIdx.x;
   const int C = u.C;
@@ -469,7 +500,6 @@ __device__ void frequency_pass(const KParams& kp, const DevUnit& u, Slot* slot, 
   }
   nfc = __reduce_add_sync(0xFFFFFFFFu, nfc);
   if ((tid & 31) == 0) f.red_u32[tid >> 5] = static_cast<unsigned>(nfc);
-  for (int i = tid; i < kCoarseBins; i += NT) slot->coarse[i] = 0;
   for (int i = tid; i < kMaxFine; i += NT) slot->fine[i] = 0;
   __syncthreads();
   if (tid == 0) {
@@ -477,7 +507,6 @@ __device__ void frequency_pass(const KParams& kp, const DevUnit& u, Slot* slot, 
     for (int w = 0; w < NT / kWarp; ++w) tot += static_cast<int>(f.red_u32[w]);
     slot->n_chan_freq = tot;
     slot->n_pool = static_cast<long long>(C - tot) * u.T;
-    slot->mom[0] = slot->mom[1] = slot->mom[2] = slot->mom[3] = 0;
     slot->mom_ready = 0;
     slot->round = 1;
     slot->n_bins = 0;
@@ -587,7 +616,7 @@ __device__ long long warp_search(const BinList& B, long long m2lo, long long m2h
 
 // Copies the slot's bin list to shared memory and forms cumulative counts.
 template <int NT>
-__device__ BinList load_bins(const Slot* slot, uint8_t* ws, int n) {
+__device__ BinList load_bins(const UnitState* slot, uint8_t* ws, int n) {
   uint32_t* lo = reinterpret_cast<uint32_t*>(ws);
   uint32_t* hi = lo + kSelCap;
   uint32_t* cum = hi + kSelCap;
@@ -626,7 +655,7 @@ __device__ __forceinline__ int bin_of_rank(const BinList& B, long long r) {
 
 // Statistics are final: thresholds of the time pass (Section 2.1).
 template <int NT>
-__device__ void finalize_stats(const KParams& kp, const DevUnit& u, Slot* slot, double median,
+__device__ void finalize_stats(const KParams& kp, const DevUnit& u, UnitState* slot, double median,
                                double sigma) {
   int kmax = 0;
   while (kmax < kp.max_log_window && (2 << kmax) <= u.T) ++kmax;
@@ -647,7 +676,7 @@ __device__ void finalize_stats(const KParams& kp, const DevUnit& u, Slot* slot, 
 // Plan the next refinement round, or finish.  Whole CTA of the last arriver;
 // the bin list is in shared memory.
 template <int NT>
-__device__ void select_plan(const KParams& kp, const DevUnit& u, Slot* slot, const BinList& B,
+__device__ void select_plan(const KParams& kp, const DevUnit& u, UnitState* slot, const BinList& B,
                             Fixed<NT>& f) {
   const int tid = threadIdx.x, lane = tid & 31;
   const long long N = B.cum[B.n];
@@ -770,6 +799,10 @@ __device__ void select_plan(const KParams& kp, const DevUnit& u, Slot* slot, con
   }
   const long long M2 = m2lo;
   const long long mad4 = f.da[0] + f.da[1];  // odd N: 2 d*, even N: d*(a) + d*(b)
+  if (tid == 0 && kp.hist.hint && u.hist_slot >= 0) {
+    kp.hist.hint[2 * u.hist_slot] = static_cast<unsigned long long>(M2);
+    kp.hist.hint[2 * u.hist_slot + 1] = static_cast<unsigned long long>(mad4);
+  }
   const double med = __dmul_rn(static_cast<double>(M2), 0.5);
   const double mad = __dmul_rn(static_cast<double>(mad4), 0.25);
   if (!kp.sigma_std && mad > 0.0) {
@@ -795,7 +828,7 @@ __device__ void select_plan(const KParams& kp, const DevUnit& u, Slot* slot, con
 // 0): non-empty keys in order, straight into the shared-memory list (lo, hi,
 // cumulative counts) and into the slot for later refinement rounds.
 template <int NT>
-__device__ BinList build_coarse_list(const KParams& kp, Slot* slot, const uint32_t* hist,
+__device__ BinList build_coarse_list(const KParams& kp, UnitState* slot, const uint32_t* hist,
                                      uint8_t* ws) {
   uint32_t* lo = reinterpret_cast<uint32_t*>(ws);
   uint32_t* hi = lo + kSelCap;
@@ -838,7 +871,7 @@ __device__ BinList build_coarse_list(const KParams& kp, Slot* slot, const uint32
 
 // Replaces every refined bin by its non-empty sub-bins.
 template <int NT>
-__device__ void merge_fine(const KParams& kp, Slot* slot, uint8_t* ws, Fixed<NT>& f) {
+__device__ void merge_fine(const KParams& kp, UnitState* slot, uint8_t* ws, Fixed<NT>& f) {
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int n = __ldcg(&slot->n_bins);
   const int nt = __ldcg(&slot->n_targets);
@@ -1068,40 +1101,108 @@ __device__ __forceinline__ uint32_t dilate32(uint32_t hi, uint32_t lo, int I) {
   return static_cast<uint32_t>(x >> 32);
 }
 
-// Chunk-local prefixes of u for a batch of rows (strided warp tasks so that
-// every warp reads 512 contiguous bytes of the staged rows per load).  In
+// Chunk bases Pb = exclusive prefix of the chunk totals (warp per row);
+// only rows with dirty[rb] set (all rows when dirty == nullptr).
+template <int NT>
+__device__ void st_bases(uint32_t* region, const StLayout& L, int nch, int nbb, int* dirty) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  for (int rb = warp; rb < nbb; rb += NT / kWarp) {
+    if (dirty && !dirty[rb]) continue;
+    uint32_t* pb = region + rb * L.per_row + L.PLW;
+    const uint32_t* tc = pb + L.PBW;
+    uint32_t carry = 0;
+    for (int base = 0; base < L.PBW; base += kWarp) {
+      const int c = base + lane;
+      const uint32_t v = c < nch ? tc[c] : 0u;
+      uint32_t tot;
+      const uint32_t ex = warp_excl_scan(v, lane, &tot);
+      if (c < L.PBW) pb[c] = carry + ex;
+      carry += tot;
+    }
+    if (dirty && lane == 0) dirty[rb] = 0;
+  }
+}
+
+// ------------------------------------------------------------------ global row access
+
+template <int DT>
+__device__ __forceinline__ void gload_vec(const uint8_t* grow, int x, int T, bool vec,
+                                          uint32_t (&v)[Traits<DT>::kVec]) {
+  using TR = Traits<DT>;
+  if (vec && x + TR::kVec <= T) {
+    const uint4 w = __ldg(reinterpret_cast<const uint4*>(grow + static_cast<size_t>(x) * TR::kBytes));
+    if constexpr (DT == LOF_CI16) {
+      v[0] = TR::pw(w.x);
+      v[1] = TR::pw(w.y);
+      v[2] = TR::pw(w.z);
+      v[3] = TR::pw(w.w);
+    } else {
+      v[0] = TR::pw(w.x);
+      v[1] = TR::pw(w.x >> 16);
+      v[2] = TR::pw(w.y);
+      v[3] = TR::pw(w.y >> 16);
+      v[4] = TR::pw(w.z);
+      v[5] = TR::pw(w.z >> 16);
+      v[6] = TR::pw(w.w);
+      v[7] = TR::pw(w.w >> 16);
+    }
+  } else {
+#pragma unroll
+    for (int j = 0; j < TR::kVec; ++j) v[j] = (x + j < T) ? TR::at(grow, x + j) : 0u;
+  }
+}
+
+__device__ __forceinline__ void warp_sum_u128(unsigned long long& lo, unsigned long long& hi) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    const unsigned long long l2 = __shfl_xor_sync(0xFFFFFFFFu, lo, o);
+    const unsigned long long h2 = __shfl_xor_sync(0xFFFFFFFFu, hi, o);
+    const unsigned long long nl = lo + l2;
+    hi = hi + h2 + (nl < lo ? 1ull : 0ull);
+    lo = nl;
+  }
+}
+
+// Chunk-local prefixes of u for the task's kept rows, read straight from the
+// input in global memory (each warp reads 512 contiguous bytes per load).  In
 // the packed path this is also the I = 1 pass: samples above K1 are flagged
 // and stored as Z.
 template <int DT, int NT>
-__device__ void st_build(const uint8_t* sdata, int dpitch, int T, int nch, const int* rows,
-                         int nbb, uint32_t* region, const StLayout& L, uint32_t* smbits, int MW,
+__device__ void st_build(const DevUnit& u, int row0, int T, int nch, const int* rows, int nbb,
+                         uint32_t* region, const StLayout& L, uint32_t* smbits, int MW,
                          bool packed, uint32_t K1) {
   using TR = Traits<DT>;
-  constexpr int VS = TR::kVec, LPC = 32 / VS, SEG = 64 * VS, NW = NT / kWarp;
+  constexpr int VS = TR::kVec, LPC = 32 / VS, NQ = 16 / VS, SEG = 32 * NQ * VS, NW = NT / kWarp;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, lp = lane & (LPC - 1);
   const int nseg = (T + SEG - 1) / SEG;
+  const bool vin = (u.flags & kUnitInVec) != 0;
+  const uint8_t* gin = static_cast<const uint8_t*>(u.in);
   for (int task = warp; task < nbb * nseg; task += NW) {
     const int rb = task / nseg, s = task - rb * nseg;
     const int r = rows[rb];
-    const uint8_t* row = sdata + r * dpitch;
+    const uint8_t* grow = gin + static_cast<int64_t>(row0 + r) * u.in_stride * TR::kBytes;
     uint32_t* pl = region + rb * L.per_row;
     uint32_t* tc = pl + L.PLW + L.PBW;
     uint32_t* mrow = smbits + r * MW + 2;
+    uint32_t v[NQ][VS];
 #pragma unroll
-    for (int q = 0; q < 2; ++q) {
+    for (int q = 0; q < NQ; ++q) {
       const int x = s * SEG + q * 32 * VS + lane * VS;
-      uint32_t v[VS];
       if (x < T) {
-        load_vec<DT>(row, x, T, v);
+        gload_vec<DT>(grow, x, T, vin, v[q]);
       } else {
 #pragma unroll
-        for (int j = 0; j < VS; ++j) v[j] = 0u;
+        for (int j = 0; j < VS; ++j) v[q][j] = 0u;
       }
+    }
+#pragma unroll
+    for (int q = 0; q < NQ; ++q) {
+      const int x = s * SEG + q * 32 * VS + lane * VS;
       uint32_t e[VS], acc = 0, fb = 0;
 #pragma unroll
       for (int j = 0; j < VS; ++j) {
-        uint32_t uu = v[j];
-        if (packed && v[j] > K1) {
+        uint32_t uu = v[q][j];
+        if (packed && uu > K1) {
           fb |= 1u << j;
           uu = kZ;
         }
@@ -1144,678 +1245,856 @@ __device__ void st_build(const uint8_t* sdata, int dpitch, int T, int nch, const
   }
 }
 
-// Chunk bases Pb = exclusive prefix of the chunk totals (warp per row);
-// only rows with dirty[rb] set (all rows when dirty == nullptr).
-template <int NT>
-__device__ void st_bases(uint32_t* region, const StLayout& L, int nch, int nbb, int* dirty) {
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  for (int rb = warp; rb < nbb; rb += NT / kWarp) {
-    if (dirty && !dirty[rb]) continue;
-    uint32_t* pb = region + rb * L.per_row + L.PLW;
-    const uint32_t* tc = pb + L.PBW;
-    uint32_t carry = 0;
-    for (int base = 0; base < L.PBW; base += kWarp) {
-      const int c = base + lane;
-      const uint32_t v = c < nch ? tc[c] : 0u;
-      uint32_t tot;
-      const uint32_t ex = warp_excl_scan(v, lane, &tot);
-      if (c < L.PBW) pb[c] = carry + ex;
-      carry += tot;
+// ------------------------------------------------------------------ fine counts
+
+// Exact counts of the pooled values inside the refinement targets, for rows
+// [ra, rb) of the unit whose frequency flag is clear; added to us->fine.
+template <int DT, int NT>
+__device__ void count_fine_rows(const KParams& kp, const DevUnit& u, UnitState* us, int ra,
+                                int rb_end, uint8_t* ws, Fixed<NT>& f) {
+  using TR = Traits<DT>;
+  constexpr int VS = TR::kVec, SEG = 64 * VS, NW = NT / kWarp;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int T = u.T, nseg = (T + SEG - 1) / SEG;
+  const bool vin = (u.flags & kUnitInVec) != 0;
+  const uint8_t* gin = static_cast<const uint8_t*>(u.in);
+  uint32_t* fine = reinterpret_cast<uint32_t*>(ws);
+  uint8_t* map = ws + 4 * kMaxFine;
+  uint8_t* fc = map + kCoarseBins;
+  const int nt = __ldcg(&us->n_targets);
+  const int nf = __ldcg(&us->n_fine);
+  if (tid < nt) f.tgt[tid] = ld_target(us->tgt + tid);
+  for (int i = tid; i < nf; i += NT) fine[i] = 0u;
+  for (int r = ra + tid; r < rb_end; r += NT) fc[r - ra] = __ldcg(kp.chan_Fc + u.chan_off + r);
+  __syncthreads();
+  for (int k = tid; k < kCoarseBins; k += NT) {
+    uint32_t lo, hi;
+    uint8_t mk = 0xFFu;
+    if (key_range(static_cast<uint32_t>(k), &lo, &hi)) {
+      int t = 0;
+      while (t < nt && f.tgt[t].hi < lo) ++t;
+      if (t < nt && f.tgt[t].lo <= hi) mk = static_cast<uint8_t>(t);
     }
-    if (dirty && lane == 0) dirty[rb] = 0;
+    map[k] = mk;
+  }
+  __syncthreads();
+  for (int task = warp; task < (rb_end - ra) * nseg; task += NW) {
+    const int rr = task / nseg, s = task - rr * nseg;
+    if (fc[rr]) continue;
+    const uint8_t* grow = gin + static_cast<int64_t>(ra + rr) * u.in_stride * TR::kBytes;
+    uint32_t v[2][VS];
+#pragma unroll
+    for (int q = 0; q < 2; ++q) {
+      const int x = s * SEG + q * 32 * VS + lane * VS;
+      if (x < T) gload_vec<DT>(grow, x, T, vin, v[q]);
+    }
+#pragma unroll
+    for (int q = 0; q < 2; ++q) {
+      const int x = s * SEG + q * 32 * VS + lane * VS;
+      if (x < T) {
+#pragma unroll
+        for (int j = 0; j < VS; ++j) {
+          if (x + j < T) {
+            const uint32_t val = v[q][j];
+            int t = map[coarse_key(val)];
+            if (t != 0xFF) {
+              for (; t < nt && val >= f.tgt[t].lo; ++t) {
+                if (val <= f.tgt[t].hi) {
+                  atomicAdd(&fine[f.tgt[t].base + ((val - f.tgt[t].lo) >> f.tgt[t].shift)], 1u);
+                  break;
+                }
+              }
+            }
+          }
+        }
+      }
+    }
+  }
+  __syncthreads();
+  for (int i = tid; i < nf; i += NT) {
+    const uint32_t h = fine[i];
+    if (h) atomicAdd(us->fine + i, h);
+  }
+  __syncthreads();
+}
+
+// Exact moments of every kept sample of the unit (std estimator fallback when
+// the MAD is zero), then the final statistics.
+template <int DT, int NT>
+__device__ void unit_moments(const KParams& kp, const DevUnit& u, UnitState* us, uint8_t* ws,
+                             Fixed<NT>& f) {
+  using TR = Traits<DT>;
+  constexpr int VS = TR::kVec, SEG = 64 * VS, NW = NT / kWarp;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int T = u.T, nseg = (T + SEG - 1) / SEG;
+  const bool vin = (u.flags & kUnitInVec) != 0;
+  const uint8_t* gin = static_cast<const uint8_t*>(u.in);
+  unsigned long long s1 = 0;
+  unsigned __int128 s2 = 0;
+  for (int task = warp; task < u.C * nseg; task += NW) {
+    const int r = task / nseg, s = task - r * nseg;
+    if (__ldcg(kp.chan_Fc + u.chan_off + r)) continue;
+    const uint8_t* grow = gin + static_cast<int64_t>(r) * u.in_stride * TR::kBytes;
+#pragma unroll
+    for (int q = 0; q < 2; ++q) {
+      const int x = s * SEG + q * 32 * VS + lane * VS;
+      if (x < T) {
+        uint32_t v[VS];
+        gload_vec<DT>(grow, x, T, vin, v);
+#pragma unroll
+        for (int j = 0; j < VS; ++j) {
+          s1 += v[j];
+          s2 += static_cast<unsigned long long>(v[j]) * v[j];
+        }
+      }
+    }
+  }
+  s1 = warp_sum64(s1);
+  unsigned long long lo = static_cast<unsigned long long>(s2);
+  unsigned long long hi = static_cast<unsigned long long>(s2 >> 64);
+  warp_sum_u128(lo, hi);
+  if (lane == 0) {
+    f.red_a[warp] = s1;
+    f.red_b[warp] = lo;
+    f.red_c[warp] = hi;
+  }
+  __syncthreads();
+  if (tid == 0) {
+    unsigned __int128 t1 = 0, t2 = 0;
+    for (int w = 0; w < NW; ++w) {
+      t1 += f.red_a[w];
+      t2 += (static_cast<unsigned __int128>(f.red_c[w]) << 64) | f.red_b[w];
+    }
+    f.sig = moments_std(__ldcg(&us->n_pool), t1, t2);
+  }
+  __syncthreads();
+  finalize_stats<NT>(kp, u, us, __ldcg(&us->median_t), f.sig);
+}
+
+// ------------------------------------------------------------------ unit-wide steps
+
+// After the last stats task of a unit: frequency pass, pooled coarse
+// histogram of the kept channels and the selection plan.  Releases the unit
+// with ready = 1 (fine counts needed) or 2 (statistics final).
+template <int DT, int NT>
+__device__ void unit_round1(const KParams& kp, const DevUnit& u, UnitState* us, uint8_t* ws,
+                            Fixed<NT>& f) {
+  using TR = Traits<DT>;
+  constexpr int NW = NT / kWarp;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int T = u.T;
+  frequency_pass<NT>(kp, u, us, ws, f);
+  if (__ldcg(&us->state) != kStateDone) {
+    // Workspace (bytes): the initial bin list lo [0, 4.2K), hi [8K, 12.2K),
+    // cum [16K, 20.2K); spec counts [24K, 28K); histogram [28K, 32.2K);
+    // Fc [34K, 36K).
+    const uint8_t* Fc = ws + 2 * kMaxChan * sizeof(unsigned long long) + kMaxChan;
+    uint32_t* uh = reinterpret_cast<uint32_t*>(ws + 28 * 1024);
+    uint32_t* sp = reinterpret_cast<uint32_t*>(ws + 24 * 1024);
+    if (tid == 0) {
+      f.n_tgt = 0;
+      if (kp.hist.hint && u.hist_slot >= 0)
+        f.n_tgt = spec_targets(__ldcg(kp.hist.hint + 2 * u.hist_slot),
+                               __ldcg(kp.hist.hint + 2 * u.hist_slot + 1), f.tgt);
+    }
+    for (int k = tid; k < kCoarseBins; k += NT) uh[k] = __ldcg(us->coarse + k);
+    for (int k = tid; k < kMaxSpec; k += NT) sp[k] = __ldcg(us->spec + k);
+    __syncthreads();
+    const int nspec_t = f.n_tgt;
+    // the stats tasks histogrammed every row: take out the flagged ones
+    constexpr int VS = TR::kVec, SEG = 64 * VS;
+    const int nseg = (T + SEG - 1) / SEG;
+    const bool vin = (u.flags & kUnitInVec) != 0;
+    const uint8_t* gin = static_cast<const uint8_t*>(u.in);
+    unsigned long long s1 = 0;
+    unsigned __int128 s2 = 0;
+    for (int c = 0; c < u.C; ++c) {
+      if (!Fc[c]) continue;
+      const uint8_t* grow = gin + static_cast<int64_t>(c) * u.in_stride * TR::kBytes;
+      for (int sg = warp; sg < nseg; sg += NW) {
+        uint32_t v[2][VS];
+#pragma unroll
+        for (int q = 0; q < 2; ++q) {
+          const int x = sg * SEG + q * 32 * VS + lane * VS;
+          if (x < T) gload_vec<DT>(grow, x, T, vin, v[q]);
+        }
+#pragma unroll
+        for (int q = 0; q < 2; ++q) {
+          const int x = sg * SEG + q * 32 * VS + lane * VS;
+          if (x >= T) continue;
+#pragma unroll
+          for (int j = 0; j < VS; ++j) {
+            if (x + j >= T) continue;
+            const uint32_t val = v[q][j];
+            const uint32_t key = coarse_key(val);
+            atomicSub(&uh[key], 1u);
+            for (int t = 0; t < nspec_t; ++t)
+              if (val >= f.tgt[t].lo && val <= f.tgt[t].hi)
+                atomicSub(&sp[f.tgt[t].base + (val - f.tgt[t].lo)], 1u);
+            if (kp.sigma_std) {
+              s1 += val;
+              s2 += static_cast<unsigned long long>(val) * val;
+            }
+          }
+        }
+      }
+    }
+    if (kp.sigma_std) {
+      s1 = warp_sum64(s1);
+      unsigned long long lo = static_cast<unsigned long long>(s2);
+      unsigned long long hi = static_cast<unsigned long long>(s2 >> 64);
+      warp_sum_u128(lo, hi);
+      if (lane == 0) {
+        f.red_a[warp] = s1;
+        f.red_b[warp] = lo;
+        f.red_c[warp] = hi;
+      }
+    }
+    __syncthreads();
+    if (tid == 0 && kp.sigma_std) {
+      unsigned __int128 t1 = (static_cast<unsigned __int128>(__ldcg(us->mom + 1)) << 64) |
+                             __ldcg(us->mom + 0);
+      unsigned __int128 t2 = (static_cast<unsigned __int128>(__ldcg(us->mom + 3)) << 64) |
+                             __ldcg(us->mom + 2);
+      for (int w = 0; w < NW; ++w) {
+        t1 -= f.red_a[w];
+        t2 -= (static_cast<unsigned __int128>(f.red_c[w]) << 64) | f.red_b[w];
+      }
+      us->mom[0] = static_cast<unsigned long long>(t1);
+      us->mom[1] = static_cast<unsigned long long>(t1 >> 64);
+      us->mom[2] = static_cast<unsigned long long>(t2);
+      us->mom[3] = static_cast<unsigned long long>(t2 >> 64);
+      us->mom_ready = 1;
+    }
+    __syncthreads();
+    const BinList B0 = build_coarse_list<NT>(kp, us, uh, ws);
+    // merge the value-by-value counts of the hinted bins (as a fine round)
+    if (tid == 0) {
+      int nt = 0, nsc = 0;
+      for (int t = 0; t < nspec_t; ++t) {
+        int a = 0, b = B0.n;  // bin with lo == target lo
+        while (a < b) {
+          const int mid = (a + b) >> 1;
+          if (B0.lo[mid] < f.tgt[t].lo) a = mid + 1;
+          else b = mid;
+        }
+        if (a < B0.n && B0.lo[a] == f.tgt[t].lo && B0.hi[a] == f.tgt[t].hi) {
+          us->tgt[nt] = f.tgt[t];
+          us->tgt_bin[nt] = a;
+          ++nt;
+        }
+        nsc = static_cast<int>(f.tgt[t].base + (f.tgt[t].hi - f.tgt[t].lo) + 1u);
+      }
+      us->n_targets = nt;
+      us->n_fine = nsc;
+      f.n_tgt = nt;
+      f.state = nsc;
+    }
+    __syncthreads();
+    if (f.n_tgt > 0) {
+      for (int i = tid; i < f.state; i += NT) us->fine[i] = sp[i];
+      __syncthreads();
+      merge_fine<NT>(kp, us, ws, f);
+      const BinList B = load_bins<NT>(us, ws, __ldcg(&us->n_bins));
+      select_plan<NT>(kp, u, us, B, f);
+    } else {
+      select_plan<NT>(kp, u, us, B0, f);
+    }
+    if (__ldcg(&us->state) == kStateMoments) unit_moments<DT, NT>(kp, u, us, ws, f);
+  }
+  __syncthreads();
+  if (tid == 0) {
+    __threadfence();
+    st_release(&us->ready, __ldcg(&us->state) == kStateFine ? 1 : 2);
   }
 }
 
-// ------------------------------------------------------------------ the kernel
-
+// After the last fine task of a unit: merge the counts, plan again; further
+// rounds (rare) are counted here over every kept row of the unit.
 template <int DT, int NT>
-__global__ void __launch_bounds__(NT, 512 / NT) lof_block_kernel(const KParams kp) {
-  using TR = Traits<DT>;
-  constexpr int VS = TR::kVec;
-  constexpr int SEG = 64 * VS;  // samples per segment task (two warp sweeps)
-  constexpr int NW = NT / kWarp;
-  extern __shared__ __align__(128) uint8_t smem[];
-  __shared__ Fixed<NT> f;
-  __shared__ uint32_t s_K0[kMaxLogWindow + 1], s_cq[kMaxLogWindow + 1];
-  __shared__ uint32_t s_Kp[kKTable];
-  __shared__ int s_dirty[kMaxRowsPerItem];
-  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  uint8_t* const sdata = smem;
-  uint8_t* const swork = smem + kp.tile_rows_bytes;
-  uint32_t* const spfx = reinterpret_cast<uint32_t*>(swork);
-  uint32_t* const smbits = spfx + kp.pfx_words;
-  uint32_t* const sfbits = smbits + kp.mbits_words;
-
-  if (tid == 0) {
-    mbar_init(&f.mbar, 1);
-    fence_mbar_init();
-    f.owned_unit = -1;
+__device__ void unit_round2(const KParams& kp, const DevUnit& u, UnitState* us, uint8_t* ws,
+                            Fixed<NT>& f) {
+  for (int guard = 0;; ++guard) {
+    merge_fine<NT>(kp, us, ws, f);
+    const BinList B = load_bins<NT>(us, ws, __ldcg(&us->n_bins));
+    select_plan<NT>(kp, u, us, B, f);
+    if (__ldcg(&us->state) != kStateFine || guard > kMaxRounds) break;
+    count_fine_rows<DT, NT>(kp, u, us, 0, u.C, ws, f);
+  }
+  if (__ldcg(&us->state) == kStateMoments) unit_moments<DT, NT>(kp, u, us, ws, f);
+  if (__ldcg(&us->state) != kStateDone) {  // did not converge: no time pass
+    finalize_stats<NT>(kp, u, us, 0.0, 0.0);
   }
   __syncthreads();
-  uint32_t phase = 0;
+  if (threadIdx.x == 0) {
+    __threadfence();
+    st_release(&us->ready, 2);
+  }
+}
 
-  for (;;) {
-    if (tid == 0) {
-      bulk_wait_read();  // the previous item's bulk stores have read their rows
-      f.item = atomicAdd(kp.queue, 1);
-      f.ok = 1;
-      f.cnt_time = f.cnt_total = f.cnt_hist = 0;
-      f.mo1 = f.mo2lo = f.mo2hi = 0;
-    }
-    __syncthreads();
-    const int item = f.item;
-    if (item >= kp.n_items) break;
-    const Item it = kp.items[item];
-    const DevUnit u = kp.units[it.unit];
-    UnitCtl* const ctl = kp.ctl + it.unit;
-    const int T = u.T, R = it.nrows, row0 = it.row0;
-    const int dpitch = round_up(T * TR::kBytes, 128);
-    const int G = u.n_items;
-    const int nch = (T + 31) >> 5;
-    const int MW = nch + 4;  // flag words per row, two zero words on each side
-    const int nseg = (T + SEG - 1) / SEG;
-    const bool bulk_in = (u.flags & kUnitInBulk) != 0;
-    const uint8_t* gin = static_cast<const uint8_t*>(u.in);
-    uint32_t* const hist = spfx;  // coarse histogram of this CTA's rows
+// ------------------------------------------------------------------ tasks
 
-    // ---- stage the rows
-    if (tid == 0 && bulk_in) {
-      mbar_expect_tx(&f.mbar, static_cast<uint32_t>(R * T * TR::kBytes));
-      for (int r = 0; r < R; ++r)
-        bulk_load(sdata + r * dpitch, gin + (row0 + r) * u.in_stride * TR::kBytes,
-                  static_cast<uint32_t>(T * TR::kBytes), &f.mbar);
+// Stats task: row power sums (spectrum) and the coarse histogram of its rows.
+template <int DT, int NT>
+__device__ void task_stats(const KParams& kp, const DevUnit& u, UnitState* us, const Task& tk,
+                           uint8_t* ws, Fixed<NT>& f) {
+  using TR = Traits<DT>;
+  constexpr int VS = TR::kVec, NQ = 32 / VS, SEG = 32 * NQ * VS, NW = NT / kWarp;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int T = u.T, R = tk.nrows, row0 = tk.row0, nseg = (T + SEG - 1) / SEG;
+  const bool vin = (u.flags & kUnitInVec) != 0;
+  const uint8_t* gin = static_cast<const uint8_t*>(u.in);
+  uint32_t* hist = reinterpret_cast<uint32_t*>(ws);
+  uint8_t* map = ws + 4 * kCoarseBins;                                   // [4224, 5280)
+  uint32_t* spec = reinterpret_cast<uint32_t*>(ws + 6 * 1024);           // [6K, 10K)
+  if (tid == 0) {
+    f.n_tgt = 0;
+    if (kp.hist.hint && u.hist_slot >= 0)
+      f.n_tgt = spec_targets(__ldcg(kp.hist.hint + 2 * u.hist_slot),
+                             __ldcg(kp.hist.hint + 2 * u.hist_slot + 1), f.tgt);
+  }
+  for (int i = tid; i < kCoarseBins; i += NT) {
+    hist[i] = 0u;
+    map[i] = 0xFFu;
+  }
+  for (int i = tid; i < kMaxSpec; i += NT) spec[i] = 0u;
+  for (int r = tid; r < R; r += NT) f.rowS[r] = 0;
+  __syncthreads();
+  const int nspec_t = f.n_tgt;
+  if (tid < nspec_t) map[coarse_key(f.tgt[tid].lo)] = static_cast<uint8_t>(tid);
+  __syncthreads();
+  for (int task = warp; task < R * nseg; task += NW) {
+    const int r = task / nseg, s = task - r * nseg;
+    const uint8_t* grow = gin + static_cast<int64_t>(row0 + r) * u.in_stride * TR::kBytes;
+    uint32_t v[NQ][VS];
+#pragma unroll
+    for (int q = 0; q < NQ; ++q) {
+      const int x = s * SEG + q * 32 * VS + lane * VS;
+      if (x < T) gload_vec<DT>(grow, x, T, vin, v[q]);
     }
-    if (!bulk_in) {
-      for (int r = 0; r < R; ++r)
-        for (int t = tid; t < T; t += NT)
-          TR::copy(sdata + r * dpitch + t * TR::kBytes,
-                   gin + ((row0 + r) * u.in_stride + t) * TR::kBytes);
-    }
-    for (int r = tid; r < R; r += NT) {
-      f.rowS[r] = 0;
-      f.rowFlagSum[r] = 0;
-      f.rowNFlag[r] = 0;
-      f.rowFh[r] = 0;
-      f.rowFc[r] = 0;
-    }
-    for (int i = tid; i < R * MW; i += NT) smbits[i] = 0u;
-    for (int i = tid; i < kCoarseBins; i += NT) hist[i] = 0u;
-    if (bulk_in) {
-      const unsigned long long t0 = global_ns();
-      while (!mbar_try(&f.mbar, phase)) {
-        if (global_ns() - t0 > static_cast<unsigned long long>(kp.spin_limit)) {
-          set_error(kp, kErrTimeout, 100);
-          break;
+    unsigned long long sum = 0;
+#pragma unroll
+    for (int q = 0; q < NQ; ++q) {
+      const int x = s * SEG + q * 32 * VS + lane * VS;
+      if (x < T) {
+#pragma unroll
+        for (int j = 0; j < VS; ++j) {
+          if (x + j < T) {
+            sum += v[q][j];
+            const uint32_t key = coarse_key(v[q][j]);
+            atomicAdd(&hist[key], 1u);
+            if (nspec_t) {
+              const int t = map[key];
+              if (t != 0xFF) atomicAdd(&spec[f.tgt[t].base + (v[q][j] - f.tgt[t].lo)], 1u);
+            }
+          }
         }
       }
-      phase ^= 1u;
     }
-    __syncthreads();
+    sum = warp_sum64(sum);
+    if (lane == 0) atomicAdd(&f.rowS[r], sum);
+  }
+  if (kp.sigma_std) {
+    // exact 128-bit moments for the std estimator, in a pass of their own
+    constexpr int SEG2 = 64 * VS;
+    const int nseg2 = (T + SEG2 - 1) / SEG2;
+    unsigned long long s1 = 0;
+    unsigned __int128 s2 = 0;
+    for (int task = warp; task < R * nseg2; task += NW) {
+      const int r = task / nseg2, s = task - r * nseg2;
+      const uint8_t* grow = gin + static_cast<int64_t>(row0 + r) * u.in_stride * TR::kBytes;
+#pragma unroll
+      for (int q = 0; q < 2; ++q) {
+        const int x = s * SEG2 + q * 32 * VS + lane * VS;
+        if (x < T) {
+          uint32_t v[VS];
+          gload_vec<DT>(grow, x, T, vin, v);
+#pragma unroll
+          for (int j = 0; j < VS; ++j) {
+            s1 += v[j];
+            s2 += static_cast<unsigned long long>(v[j]) * v[j];
+          }
+        }
+      }
+    }
+    s1 = warp_sum64(s1);
+    unsigned long long lo = static_cast<unsigned long long>(s2);
+    unsigned long long hi = static_cast<unsigned long long>(s2 >> 64);
+    warp_sum_u128(lo, hi);
+    if (lane == 0) {
+      f.red_a[warp] = s1;
+      f.red_b[warp] = lo;
+      f.red_c[warp] = hi;
+    }
+  }
+  __syncthreads();
+  for (int r = tid; r < R; r += NT) kp.chan_S[u.chan_off + row0 + r] = f.rowS[r];
+  for (int k = tid; k < kCoarseBins; k += NT) {
+    const uint32_t h = hist[k];
+    if (h) atomicAdd(us->coarse + k, h);
+  }
+  if (nspec_t) {
+    const int nsc = static_cast<int>(f.tgt[nspec_t - 1].base + (f.tgt[nspec_t - 1].hi - f.tgt[nspec_t - 1].lo) + 1u);
+    for (int i = tid; i < nsc; i += NT) {
+      const uint32_t h = spec[i];
+      if (h) atomicAdd(us->spec + i, h);
+    }
+  }
+  if (tid == 0 && kp.sigma_std) {
+    unsigned __int128 t1 = 0, t2 = 0;
+    for (int w = 0; w < NW; ++w) {
+      t1 += f.red_a[w];
+      t2 += (static_cast<unsigned __int128>(f.red_c[w]) << 64) | f.red_b[w];
+    }
+    atomic_add_u128(us->mom + 0, t1);
+    atomic_add_u128(us->mom + 2, t2);
+  }
+  __syncthreads();
+  if (tid == 0) {
+    __threadfence();
+    const int old = atomicAdd(&us->done_S, 1);
+    f.last = (old + 1 == u.nS) ? 1 : 0;
+    if (f.last) __threadfence();
+  }
+  __syncthreads();
+  if (f.last) unit_round1<DT, NT>(kp, u, us, ws, f);
+}
 
-    // ---- pass 1: row power sums (spectrum) and coarse histogram of all rows
-    {
-      unsigned long long s1 = 0;
-      unsigned __int128 s2 = 0;
-      for (int task = warp; task < R * nseg; task += NW) {
-        const int r = task / nseg, s = task - r * nseg;
-        const uint8_t* row = sdata + r * dpitch;
-        unsigned long long sum = 0;
-#pragma unroll
-        for (int q = 0; q < 2; ++q) {
-          const int x = s * SEG + q * 32 * VS + lane * VS;
-          if (x < T) {
-            uint32_t v[VS];
-            load_vec<DT>(row, x, T, v);
-#pragma unroll
-            for (int j = 0; j < VS; ++j) {
-              if (x + j < T) {
-                sum += v[j];
-                atomicAdd(&hist[coarse_key(v[j])], 1u);
-                if (kp.sigma_std) {
-                  s1 += v[j];
-                  s2 += static_cast<unsigned long long>(v[j]) * v[j];
-                }
-              }
-            }
-          }
-        }
-        sum = warp_sum64(sum);
-        if (lane == 0) atomicAdd(&f.rowS[r], sum);
-      }
-      if (kp.sigma_std) {
-        s1 = warp_sum64(s1);
-        unsigned long long lo = static_cast<unsigned long long>(s2);
-        unsigned long long hi = static_cast<unsigned long long>(s2 >> 64);
-        for (int o = 16; o > 0; o >>= 1) {
-          const unsigned long long l2 = __shfl_xor_sync(0xFFFFFFFFu, lo, o);
-          const unsigned long long h2 = __shfl_xor_sync(0xFFFFFFFFu, hi, o);
-          const unsigned long long nl = lo + l2;
-          hi = hi + h2 + (nl < lo ? 1ull : 0ull);
-          lo = nl;
-        }
-        if (lane == 0) {
-          atomicAdd(&f.mo1, s1);
-          const unsigned long long old = atomicAdd(&f.mo2lo, lo);
-          atomicAdd(&f.mo2hi, hi + ((old + lo < old) ? 1ull : 0ull));
-        }
-      }
-    }
-    __syncthreads();
-    // publish: spectrum, this CTA's histogram and moments, membership
-    for (int r = tid; r < R; r += NT) kp.chan_S[u.chan_off + row0 + r] = f.rowS[r];
-    {
-      uint32_t* pub = kp.pub + static_cast<size_t>(blockIdx.x) * kCoarseBins;
-      for (int i = tid; i < kCoarseBins; i += NT) pub[i] = hist[i];
-      if (tid == 0) {
-        unsigned long long* pm = kp.pubm + static_cast<size_t>(blockIdx.x) * 4;
-        pm[0] = f.mo1;
-        pm[1] = 0;
-        pm[2] = f.mo2lo;
-        pm[3] = f.mo2hi;
-        kp.members[item] = static_cast<int>(blockIdx.x);
-      }
-    }
-    __syncthreads();
-    if (tid == 0) {
-      __threadfence();
-      const int old = atomicAdd(&ctl->arrive, 1);
-      f.last = (old + 1 == G) ? 1 : 0;
-    }
-    __syncthreads();
-    if (f.last) {
-      if (tid == 0) {
-        __threadfence();
-        // the slot this CTA lends must be free of the unit it served before
-        if (f.owned_unit >= 0) {
-          const int pu = f.owned_unit;
-          if (!wait_geq(kp, &kp.ctl[pu].departed, kp.units[pu].n_items, 200)) f.ok = 0;
-        }
-        f.owned_unit = it.unit;
-        ctl->slot = static_cast<int>(blockIdx.x);
-      }
-      __syncthreads();
-      if (f.ok) {
-        Slot* const slot = kp.slots + blockIdx.x;
-        frequency_pass<NT>(kp, u, slot, swork, f);
-        if (__ldcg(&slot->state) != kStateDone) {
-          // pooled coarse histogram of the kept channels: all CTAs' histograms
-          // minus the rows the frequency pass flagged (re-read from the input).
-          // Workspace (bytes): the initial bin list lo [0, 4.2K), hi [10K, 14.2K),
-          // cum [20K, 24.2K); members [24K, 28K) (dead before the list is built);
-          // histogram [28K, 32.2K); Fc [34K, 36K).
-          const uint8_t* Fc = swork + 2 * kMaxChan * sizeof(unsigned long long) + kMaxChan;
-          uint32_t* uh = reinterpret_cast<uint32_t*>(swork + 28 * 1024);
-          int* mem = reinterpret_cast<int*>(swork + 24 * 1024);
-          for (int i = tid; i < G; i += NT) mem[i] = __ldcg(kp.members + u.first_item + i);
-          for (int k = tid; k < kCoarseBins; k += NT) uh[k] = 0u;
-          __syncthreads();
-          for (int i = warp; i < G; i += NW) {
-            const uint32_t* pb = kp.pub + static_cast<size_t>(mem[i]) * kCoarseBins;
-#pragma unroll 4
-            for (int k = lane; k < kCoarseBins; k += kWarp) {
-              const uint32_t h = __ldcg(pb + k);
-              if (h) atomicAdd(&uh[k], h);
-            }
-          }
-          unsigned long long s1 = 0;
-          unsigned __int128 s2 = 0;
-          for (int c = 0; c < u.C; ++c) {
-            if (!Fc[c]) continue;
-            const uint8_t* grow = gin + static_cast<int64_t>(c) * u.in_stride * TR::kBytes;
-            for (int t = tid; t < T; t += NT) {
-              const uint32_t v = TR::at(grow, t);
-              atomicSub(&uh[coarse_key(v)], 1u);
-              if (kp.sigma_std) {
-                s1 += v;
-                s2 += static_cast<unsigned long long>(v) * v;
-              }
-            }
-          }
-          if (kp.sigma_std) {
-            // moments of the kept channels: sum over CTAs minus flagged rows
-            s1 = warp_sum64(s1);
-            unsigned long long lo = static_cast<unsigned long long>(s2);
-            unsigned long long hi = static_cast<unsigned long long>(s2 >> 64);
-            for (int o = 16; o > 0; o >>= 1) {
-              const unsigned long long l2 = __shfl_xor_sync(0xFFFFFFFFu, lo, o);
-              const unsigned long long h2 = __shfl_xor_sync(0xFFFFFFFFu, hi, o);
-              const unsigned long long nl = lo + l2;
-              hi = hi + h2 + (nl < lo ? 1ull : 0ull);
-              lo = nl;
-            }
-            if (lane == 0) {
-              f.red_a[warp] = s1;
-              f.red_b[warp] = lo;
-              f.red_c[warp] = hi;
-            }
-          }
-          __syncthreads();
-          if (tid == 0 && kp.sigma_std) {
-            unsigned __int128 t1 = 0, t2 = 0, f1 = 0, f2 = 0;
-            for (int i = 0; i < G; ++i) {
-              const int m = __ldcg(kp.members + u.first_item + i);
-              const unsigned long long* pm = kp.pubm + static_cast<size_t>(m) * 4;
-              t1 += __ldcg(pm + 0);
-              t2 += (static_cast<unsigned __int128>(__ldcg(pm + 3)) << 64) | __ldcg(pm + 2);
-            }
-            for (int w = 0; w < NW; ++w) {
-              f1 += f.red_a[w];
-              f2 += (static_cast<unsigned __int128>(f.red_c[w]) << 64) | f.red_b[w];
-            }
-            t1 -= f1;
-            t2 -= f2;
-            slot->mom[0] = static_cast<unsigned long long>(t1);
-            slot->mom[1] = static_cast<unsigned long long>(t1 >> 64);
-            slot->mom[2] = static_cast<unsigned long long>(t2);
-            slot->mom[3] = static_cast<unsigned long long>(t2 >> 64);
-            slot->mom_ready = 1;
-          }
-          __syncthreads();
-          const BinList B = build_coarse_list<NT>(kp, slot, uh, swork);
-          select_plan<NT>(kp, u, slot, B, f);
-        }
-        if (tid == 0) {
-          __threadfence();
-          st_release(&ctl->release, 1);
-        }
-      }
-    } else if (tid == 0) {
-      if (!wait_geq(kp, &ctl->release, 1, 1)) f.ok = 0;
-    }
-    __syncthreads();
-    if (!f.ok) break;
-    if (tid == 0) f.slot = __ldcg(&ctl->slot);
-    __syncthreads();
-    Slot* const slot = kp.slots + f.slot;
-    for (int r = tid; r < R; r += NT) f.rowFc[r] = __ldcg(kp.chan_Fc + u.chan_off + row0 + r);
-    __syncthreads();
-    if (tid == 0) {
-      int nk = 0;
-      for (int r = 0; r < R; ++r)
-        if (!f.rowFc[r]) f.keep[nk++] = r;
-      f.n_keep = nk;
-    }
-    __syncthreads();
-    const int nkeep = f.n_keep;
+// Fine task: exact counts in the refined bins for its kept rows (skipped when
+// the first round already made the statistics exact).
+template <int DT, int NT>
+__device__ void task_fine(const KParams& kp, const DevUnit& u, UnitState* us, const Task& tk,
+                          uint8_t* ws, Fixed<NT>& f) {
+  const int tid = threadIdx.x;
+  if (tid == 0) {
+    if (!wait_geq(kp, &us->ready, 1, 300)) f.ok = 0;
+    f.state = f.ok ? __ldcg(&us->ready) : 0;
+  }
+  __syncthreads();
+  if (!f.ok || f.state == 2) return;
+  count_fine_rows<DT, NT>(kp, u, us, tk.row0, tk.row0 + tk.nrows, ws, f);
+  if (tid == 0) {
+    __threadfence();
+    const int old = atomicAdd(&us->done_F, 1);
+    f.last = (old + 1 == u.nF) ? 1 : 0;
+    if (f.last) __threadfence();
+  }
+  __syncthreads();
+  if (f.last) unit_round2<DT, NT>(kp, u, us, ws, f);
+}
 
-    // ---- further rounds: exact counts in the refined bins, or moments
-    int round = 1;
-    for (;;) {
-      if (tid == 0) f.state = __ldcg(&slot->state);
-      __syncthreads();
-      const int state = f.state;
-      if (state == kStateDone) break;
-      ++round;
-      if (state == kStateFine) {
-        uint32_t* fine = spfx;
-        uint8_t* map = reinterpret_cast<uint8_t*>(spfx + kMaxFine);
-        const int nt = __ldcg(&slot->n_targets);
-        const int nf = __ldcg(&slot->n_fine);
-        if (tid < nt) f.tgt[tid] = ld_target(slot->tgt + tid);
-        for (int i = tid; i < nf; i += NT) fine[i] = 0u;
-        __syncthreads();
-        for (int k = tid; k < kCoarseBins; k += NT) {
-          uint32_t lo, hi;
-          uint8_t mk = 0xFFu;
-          if (key_range(static_cast<uint32_t>(k), &lo, &hi)) {
-            int t = 0;
-            while (t < nt && f.tgt[t].hi < lo) ++t;
-            if (t < nt && f.tgt[t].lo <= hi) mk = static_cast<uint8_t>(t);
-          }
-          map[k] = mk;
-        }
-        __syncthreads();
-        for (int task = warp; task < nkeep * nseg; task += NW) {
-          const int kr = task / nseg, s = task - kr * nseg;
-          const uint8_t* row = sdata + f.keep[kr] * dpitch;
-#pragma unroll
-          for (int q = 0; q < 2; ++q) {
-            const int x = s * SEG + q * 32 * VS + lane * VS;
-            if (x < T) {
-              uint32_t v[VS];
-              load_vec<DT>(row, x, T, v);
-#pragma unroll
-              for (int j = 0; j < VS; ++j) {
-                if (x + j < T) {
-                  int t = map[coarse_key(v[j])];
-                  if (t != 0xFF) {
-                    for (; t < nt && v[j] >= f.tgt[t].lo; ++t) {
-                      if (v[j] <= f.tgt[t].hi) {
-                        atomicAdd(&fine[f.tgt[t].base + ((v[j] - f.tgt[t].lo) >> f.tgt[t].shift)],
-                                  1u);
-                        break;
-                      }
-                    }
-                  }
-                }
-              }
-            }
-          }
-        }
-        __syncthreads();
-        for (int i = tid; i < nf; i += NT) {
-          const uint32_t h = fine[i];
-          if (h) atomicAdd(slot->fine + i, h);
-        }
-      } else {  // kStateMoments
-        unsigned long long s1 = 0;
-        unsigned __int128 s2 = 0;
-        for (int task = warp; task < nkeep * nseg; task += NW) {
-          const int kr = task / nseg, s = task - kr * nseg;
-          const uint8_t* row = sdata + f.keep[kr] * dpitch;
-#pragma unroll
-          for (int q = 0; q < 2; ++q) {
-            const int x = s * SEG + q * 32 * VS + lane * VS;
-            if (x < T) {
-              uint32_t v[VS];
-              load_vec<DT>(row, x, T, v);
-#pragma unroll
-              for (int j = 0; j < VS; ++j) {
-                s1 += v[j];
-                s2 += static_cast<unsigned long long>(v[j]) * v[j];
-              }
-            }
-          }
-        }
-        s1 = warp_sum64(s1);
-        unsigned long long lo = static_cast<unsigned long long>(s2);
-        unsigned long long hi = static_cast<unsigned long long>(s2 >> 64);
-        for (int o = 16; o > 0; o >>= 1) {
-          const unsigned long long l2 = __shfl_xor_sync(0xFFFFFFFFu, lo, o);
-          const unsigned long long h2 = __shfl_xor_sync(0xFFFFFFFFu, hi, o);
-          const unsigned long long nl = lo + l2;
-          hi = hi + h2 + (nl < lo ? 1ull : 0ull);
-          lo = nl;
-        }
-        if (lane == 0) {
-          atomicAdd(slot->mom + 0, s1);
-          atomic_add_u128(slot->mom + 2, (static_cast<unsigned __int128>(hi) << 64) | lo);
-        }
-      }
-      __syncthreads();
-      if (tid == 0) {
-        __threadfence();
-        const int old = atomicAdd(&ctl->arrive, 1);
-        f.last = (old + 1 == round * G) ? 1 : 0;
-      }
-      __syncthreads();
-      if (f.last) {
-        if (tid == 0) __threadfence();
-        __syncthreads();
-        if (state == kStateFine) {
-          merge_fine<NT>(kp, slot, swork, f);
-          const BinList B = load_bins<NT>(slot, swork, __ldcg(&slot->n_bins));
-          select_plan<NT>(kp, u, slot, B, f);
-        } else {
-          const long long N = __ldcg(&slot->n_pool);
-          const unsigned __int128 s1 = __ldcg(slot->mom + 0);
-          const unsigned __int128 s2 =
-              (static_cast<unsigned __int128>(__ldcg(slot->mom + 3)) << 64) | __ldcg(slot->mom + 2);
-          finalize_stats<NT>(kp, u, slot, __ldcg(&slot->median_t), moments_std(N, s1, s2));
-        }
-        if (tid == 0) {
-          __threadfence();
-          st_release(&ctl->release, round);
-        }
-      } else if (tid == 0) {
-        if (!wait_geq(kp, &ctl->release, round, round)) f.ok = 0;
-      }
-      __syncthreads();
-      if (!f.ok) break;
-    }
-    if (!f.ok) break;
-    // the unit's thresholds
-    for (int i = tid; i < kKTable; i += NT) f.K[i] = __ldcg(slot->K + i);
-    if (tid == 0) {
-      f.time_on = __ldcg(&slot->time_on);
-      int kmax = 0;
-      while (kmax < kp.max_log_window && (2 << kmax) <= T) ++kmax;
-      f.kmax_t = kmax;
-    }
-    __syncthreads();
-    if (tid == 0) {
-      __threadfence();
-      atomicAdd(&ctl->departed, 1);
-      // packed-path tables and guard (see the time pass helpers)
-      bool packed = f.K[0] >= 0 && f.K[0] < (1ll << 20);
-      for (int k = 0; k <= f.kmax_t && packed; ++k) {
-        const int I = 1 << k;
-        const long long* Kt = f.K + koffset(k);
-        for (int n = 0; n <= I; ++n)
-          if (Kt[n] < 0 || Kt[n] >= static_cast<long long>(kZ)) packed = false;
-        if (!packed) break;
+// Flag task: SumThreshold in time on its kept rows (Section 2.1), the history
+// test (Section 4.1), the mask and the masked data.
+template <int DT, int NT>
+__device__ void task_flag(const KParams& kp, const DevUnit& u, UnitState* us, const Task& tk,
+                          uint8_t* ws, Fixed<NT>& f, uint32_t* s_K0, uint32_t* s_cq, uint32_t* s_Kp,
+                          int* s_dirty) {
+  using TR = Traits<DT>;
+  constexpr int VS = TR::kVec, SEG = 64 * VS, NW = NT / kWarp;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int T = u.T, R = tk.nrows, row0 = tk.row0;
+  const int nch = (T + 31) >> 5;
+  const int MW = nch + 4;  // flag words per row, two zero words on each side
+  const int nseg = (T + SEG - 1) / SEG;
+  const StLayout L = st_layout(nch);
+  uint32_t* const spfx = reinterpret_cast<uint32_t*>(ws);
+  uint32_t* const smbits = spfx + R * L.per_row;
+  uint32_t* const sfbits = smbits + R * MW;
+  const uint8_t* gin = static_cast<const uint8_t*>(u.in);
+  if (tid == 0) {
+    if (!wait_geq(kp, &us->ready, 2, 400)) f.ok = 0;
+  }
+  __syncthreads();
+  if (!f.ok) return;
+  for (int i = tid; i < kKTable; i += NT) f.K[i] = __ldcg(us->K + i);
+  for (int r = tid; r < R; r += NT) {
+    f.rowFc[r] = __ldcg(kp.chan_Fc + u.chan_off + row0 + r);
+    f.rowS[r] = __ldcg(kp.chan_S + u.chan_off + row0 + r);
+    f.rowFlagSum[r] = 0;
+    f.rowNFlag[r] = 0;
+    f.rowFh[r] = 0;
+  }
+  for (int i = tid; i < R * MW; i += NT) smbits[i] = 0u;
+  if (tid == 0) {
+    f.time_on = __ldcg(&us->time_on);
+    int kmax = 0;
+    while (kmax < kp.max_log_window && (2 << kmax) <= T) ++kmax;
+    f.kmax_t = kmax;
+  }
+  __syncthreads();
+  if (tid == 0) {
+    int nk = 0;
+    for (int r = 0; r < R; ++r)
+      if (!f.rowFc[r]) f.keep[nk++] = r;
+    f.n_keep = nk;
+  }
+  // packed-path tables and guard (see the time pass helpers), one entry per thread
+  bool bad = false;
+  {
+    const int total = koffset(f.kmax_t + 1);
+    if (f.K[0] < 0 || f.K[0] >= (1ll << 20)) bad = true;
+    for (int e = tid; e < total; e += NT) {
+      int k = 0;
+      while (koffset(k + 1) <= e) ++k;
+      const int I = 1 << k, n = e - koffset(k);
+      const long long* Kt = f.K + koffset(k);
+      if (Kt[n] < 0 || Kt[n] >= static_cast<long long>(kZ)) bad = true;
+      s_Kp[e] = static_cast<uint32_t>(n) * kZ + static_cast<uint32_t>(Kt[n]);
+      if (n == 0) {
         s_K0[k] = static_cast<uint32_t>(Kt[0]);
         // tau = floor(threshold_I) + 3 >= threshold_I + 2; floor(threshold_I) = K[I - 1]
         const uint32_t tau = static_cast<uint32_t>(k == 0 ? Kt[0] : Kt[I - 1]) + 3u;
         s_cq[k] = tau - kZ;
-        for (int n = 0; n <= I; ++n)
-          s_Kp[koffset(k) + n] = static_cast<uint32_t>(n) * kZ + static_cast<uint32_t>(Kt[n]);
       }
-      f.state = packed ? 1 : 0;
     }
-    __syncthreads();
+  }
+  bad = __syncthreads_or(bad);
+  if (tid == 0) f.state = bad ? 0 : 1;
+  __syncthreads();
+  const int nkeep = f.n_keep;
 
-    // ---- time pass: SumThreshold along t on the kept rows (Section 2.1)
-    if (f.time_on && nkeep > 0) {
-      const bool packed = f.state == 1;
-      const StLayout L = st_layout(nch);
-      const int nb = min(nkeep, kp.pfx_words / L.per_row);
-      if (nb < 1) {  // the host sizes the prefix buffer for every row length
-        if (tid == 0) set_error(kp, kErrInternal, 30);
-        break;
+  // ---- time pass over all kept rows of the task at once
+  if (f.time_on && nkeep > 0) {
+    const bool packed = f.state == 1;
+    const int* rows = f.keep;
+    const int nbb = nkeep;
+    st_build<DT, NT>(u, row0, T, nch, rows, nbb, spfx, L, smbits, MW, packed,
+                     packed ? s_K0[0] : 0u);
+    for (int i = tid; i < nbb * MW; i += NT) sfbits[i] = 0u;
+    if (tid < nbb) s_dirty[tid] = 0;
+    __syncthreads();
+    st_bases<NT>(spfx, L, nch, nbb, nullptr);
+    __syncthreads();
+    for (int k = packed ? 1 : 0; k <= f.kmax_t; ++k) {
+      const int I = 1 << k;
+      const long long* Kt = f.K + koffset(k);
+      const uint32_t K0 = packed ? s_K0[k] : 0u, cq = packed ? s_cq[k] : 0u;
+      const uint32_t* Kp = s_Kp + koffset(k);
+      for (int c = tid; c < nbb * nch; c += NT) {
+        const int rb = c / nch, w = c - rb * nch, t0 = w << 5;
+        uint32_t* F = sfbits + rb * MW + 2;
+        const int nvalid = T - I + 1 - t0;
+        if (nvalid <= 0) {
+          F[w] = 0u;
+          continue;
+        }
+        const uint32_t vm = nvalid >= 32 ? 0xFFFFFFFFu : ((1u << nvalid) - 1u);
+        const uint32_t* pl = spfx + rb * L.per_row;
+        const uint32_t* pb = pl + L.PLW;
+        uint32_t fire;
+        if (packed) {
+          switch (k) {
+            case 1: fire = packed_fire<2>(pl, pb, w, K0, cq, Kp); break;
+            case 2: fire = packed_fire<4>(pl, pb, w, K0, cq, Kp); break;
+            case 3: fire = packed_fire<8>(pl, pb, w, K0, cq, Kp); break;
+            case 4: fire = packed_fire<16>(pl, pb, w, K0, cq, Kp); break;
+            case 5: fire = packed_fire<32>(pl, pb, w, K0, cq, Kp); break;
+            default: fire = packed_fire<64>(pl, pb, w, K0, cq, Kp); break;
+          }
+        } else {
+          fire = general_fire(pl, pb, smbits + rows[rb] * MW + 2, t0, I, T, Kt);
+        }
+        F[w] = fire & vm;
       }
-      for (int b0 = 0; b0 < nkeep; b0 += nb) {
-        const int nbb = min(nb, nkeep - b0);
-        const int* rows = f.keep + b0;
-        st_build<DT, NT>(sdata, dpitch, T, nch, rows, nbb, spfx, L, smbits, MW, packed,
-                         packed ? s_K0[0] : 0u);
-        for (int i = tid; i < nbb * MW; i += NT) sfbits[i] = 0u;
-        if (tid < nbb) s_dirty[tid] = 0;
-        __syncthreads();
-        st_bases<NT>(spfx, L, nch, nbb, nullptr);
-        __syncthreads();
-        for (int k = packed ? 1 : 0; k <= f.kmax_t; ++k) {
-          const int I = 1 << k;
-          const long long* Kt = f.K + koffset(k);
-          const uint32_t K0 = packed ? s_K0[k] : 0u, cq = packed ? s_cq[k] : 0u;
-          const uint32_t* Kp = s_Kp + koffset(k);
-          for (int c = tid; c < nbb * nch; c += NT) {
-            const int rb = c / nch, w = c - rb * nch, t0 = w << 5;
-            uint32_t* F = sfbits + rb * MW + 2;
-            const int nvalid = T - I + 1 - t0;
-            if (nvalid <= 0) {
-              F[w] = 0u;
-              continue;
-            }
-            const uint32_t vm = nvalid >= 32 ? 0xFFFFFFFFu : ((1u << nvalid) - 1u);
-            const uint32_t* pl = spfx + rb * L.per_row;
-            const uint32_t* pb = pl + L.PLW;
-            uint32_t fire;
-            if (packed) {
-              switch (k) {
-                case 1: fire = packed_fire<2>(pl, pb, w, K0, cq, Kp); break;
-                case 2: fire = packed_fire<4>(pl, pb, w, K0, cq, Kp); break;
-                case 3: fire = packed_fire<8>(pl, pb, w, K0, cq, Kp); break;
-                case 4: fire = packed_fire<16>(pl, pb, w, K0, cq, Kp); break;
-                case 5: fire = packed_fire<32>(pl, pb, w, K0, cq, Kp); break;
-                default: fire = packed_fire<64>(pl, pb, w, K0, cq, Kp); break;
-              }
-            } else {
-              fire = general_fire(pl, pb, smbits + rows[rb] * MW + 2, t0, I, T, Kt);
-            }
-            F[w] = fire & vm;
+      __syncthreads();
+      // new flags: windows that fired flag all their samples (snapshot)
+      for (int c = tid; c < nbb * nch; c += NT) {
+        const int rb = c / nch, w = c - rb * nch;
+        const uint32_t* F = sfbits + rb * MW + 2;
+        const uint32_t f0 = F[w], f1 = F[w - 1], f2 = F[w - 2];
+        if ((f0 | f1 | f2) == 0u) continue;
+        const uint32_t D = (I <= 32) ? dilate32(f0, f1, I)
+                                     : (dilate32(f0, f1, 32) | dilate32(f1, f2, 32));
+        uint32_t* Mw = smbits + rows[rb] * MW + 2 + w;
+        const uint32_t nw = D & ~*Mw;
+        if (nw == 0u) continue;
+        *Mw |= nw;
+        if (packed) {
+          // store the newly flagged samples of this chunk as Z
+          uint32_t* pl = spfx + rb * L.per_row + pidx(w << 5);
+          uint32_t* tcw = spfx + rb * L.per_row + L.PLW + L.PBW + w;
+          uint32_t cur = pl[0], acc = 0;
+          for (int j = 0; j < 32; ++j) {
+            const uint32_t nx = (j < 31) ? pl[j + 1] : *tcw;
+            uint32_t uu = nx - cur;
+            cur = nx;
+            if ((nw >> j) & 1u) uu = kZ;
+            pl[j] = acc;
+            acc += uu;
           }
-          __syncthreads();
-          // new flags: windows that fired flag all their samples (snapshot)
-          for (int c = tid; c < nbb * nch; c += NT) {
-            const int rb = c / nch, w = c - rb * nch;
-            const uint32_t* F = sfbits + rb * MW + 2;
-            const uint32_t f0 = F[w], f1 = F[w - 1], f2 = F[w - 2];
-            if ((f0 | f1 | f2) == 0u) continue;
-            const uint32_t D = (I <= 32) ? dilate32(f0, f1, I)
-                                         : (dilate32(f0, f1, 32) | dilate32(f1, f2, 32));
-            uint32_t* Mw = smbits + rows[rb] * MW + 2 + w;
-            const uint32_t nw = D & ~*Mw;
-            if (nw == 0u) continue;
-            *Mw |= nw;
-            if (packed) {
-              // store the newly flagged samples of this chunk as Z
-              uint32_t* pl = spfx + rb * L.per_row + pidx(w << 5);
-              uint32_t* tcw = spfx + rb * L.per_row + L.PLW + L.PBW + w;
-              uint32_t cur = pl[0], acc = 0;
-              for (int j = 0; j < 32; ++j) {
-                const uint32_t nx = (j < 31) ? pl[j + 1] : *tcw;
-                uint32_t uu = nx - cur;
-                cur = nx;
-                if ((nw >> j) & 1u) uu = kZ;
-                pl[j] = acc;
-                acc += uu;
-              }
-              *tcw = acc;
-              s_dirty[rb] = 1;
-            }
-          }
-          __syncthreads();
-          if (packed && k < f.kmax_t) {
-            st_bases<NT>(spfx, L, nch, nbb, s_dirty);
-            __syncthreads();
-          }
+          *tcw = acc;
+          s_dirty[rb] = 1;
         }
       }
-      // flagged counts and flagged power of every kept row
-      for (int c = tid; c < nkeep * nch; c += NT) {
-        const int kr = c / nch, w = c - kr * nch;
-        const int r = f.keep[kr];
-        uint32_t m = smbits[r * MW + 2 + w];
-        if (m) {
-          const uint8_t* row = sdata + r * dpitch;
-          unsigned long long fs = 0;
-          const int cnt = __popc(m);
-          while (m) {
-            const int j = __ffs(m) - 1;
-            m &= m - 1u;
-            fs += TR::at(row, (w << 5) + j);
-          }
-          atomicAdd(&f.rowNFlag[r], cnt);
-          atomicAdd(&f.rowFlagSum[r], fs);
+      __syncthreads();
+      if (packed && k < f.kmax_t) {
+        st_bases<NT>(spfx, L, nch, nbb, s_dirty);
+        __syncthreads();
+      }
+    }
+    // flagged counts and flagged power of every kept row.  Packed rows: the
+    // chunk totals hold sum_unflagged + n_flagged * Z (mod 2^32), exact when
+    // T * floor(threshold_1) < 2^32; otherwise the flagged powers are re-read.
+    const bool from_prefix =
+        packed && static_cast<unsigned long long>(T) * s_K0[0] < (1ull << 32);
+    if (from_prefix) {
+      for (int rb = warp; rb < nbb; rb += NW) {
+        const int r = rows[rb];
+        const uint32_t* tc = spfx + rb * L.per_row + L.PLW + L.PBW;
+        const uint32_t* M = smbits + r * MW + 2;
+        uint32_t tot = 0;
+        int nfl = 0;
+        for (int c = lane; c < nch; c += kWarp) {
+          tot += tc[c];
+          nfl += __popc(M[c]);
+        }
+        tot = warp_sum32(tot);
+        nfl = __reduce_add_sync(0xFFFFFFFFu, nfl);
+        if (lane == 0) {
+          const uint32_t su = tot - static_cast<uint32_t>(nfl) * kZ;
+          f.rowNFlag[r] = nfl;
+          f.rowFlagSum[r] = f.rowS[r] - su;  // so that rowS - rowFlagSum = sum_unflagged
         }
       }
       __syncthreads();
     }
-
-    // ---- history flagger (Section 4.1) and per-row counts
-    for (int r = tid; r < R; r += NT) {
-      const long long h = u.hist_slot >= 0 ? u.hist_slot + row0 + r : -1;
-      unsigned long long add_total;
-      if (f.rowFc[r]) {
-        if (h >= 0) kp.hist.pend_flag[h] = 0;
-        add_total = static_cast<unsigned long long>(T);
-      } else {
-        const int nfl = f.rowNFlag[r];
-        const int n = T - nfl;
-        uint8_t fh = 0;
-        if (n > 0) {
-          const unsigned long long su = f.rowS[r] - f.rowFlagSum[r];
-          const double cur = __ddiv_rn(__ull2double_rn(su), static_cast<double>(n));
-          double staged = cur;
-          if (kp.enable_history && h >= 0) {
-            const int cnt = kp.hist.count[h];
-            if (cnt >= kp.history_min && cnt > 0) {
-              const double thr = kp.hist.thr[h];
-              if (!(cur < thr)) {
-                fh = 1;
-                staged = thr;
-              }
-            }
-          }
-          if (h >= 0) {
-            kp.hist.pend[h] = staged;
-            kp.hist.pend_flag[h] = 1;
-            kp.hist.pend_seq[h] = kp.block_seq;
-          }
-        } else if (h >= 0) {
-          kp.hist.pend_flag[h] = 0;
+    for (int c = tid; c < (from_prefix ? 0 : nkeep * nch); c += NT) {
+      const int kr = c / nch, w = c - kr * nch;
+      const int r = f.keep[kr];
+      uint32_t m = smbits[r * MW + 2 + w];
+      if (m) {
+        const uint8_t* grow = gin + static_cast<int64_t>(row0 + r) * u.in_stride * TR::kBytes;
+        unsigned long long fs = 0;
+        const int cnt = __popc(m);
+        while (m) {
+          const int j = __ffs(m) - 1;
+          m &= m - 1u;
+          fs += TR::at(grow, (w << 5) + j);
         }
-        f.rowFh[r] = fh;
-        atomicAdd(&f.cnt_time, static_cast<unsigned long long>(nfl));
-        if (fh) atomicAdd(&f.cnt_hist, 1ull);
-        add_total = fh ? static_cast<unsigned long long>(T) : static_cast<unsigned long long>(nfl);
+        atomicAdd(&f.rowNFlag[r], cnt);
+        atomicAdd(&f.rowFlagSum[r], fs);
       }
-      atomicAdd(&f.cnt_total, add_total);
-    }
-    __syncthreads();
-
-    // ---- apply: mask bytes, zeroed data (Sections 3 and 4)
-    const bool inplace = (u.flags & kUnitInPlace) != 0;
-    const bool mask_vec = (u.flags & kUnitMaskVec) != 0;
-    for (int c = tid; c < R * nch; c += NT) {
-      const int r = c / nch, w = c - r * nch, t0 = w << 5;
-      const int nv = min(32, T - t0);
-      const uint32_t vm = nv >= 32 ? 0xFFFFFFFFu : ((1u << nv) - 1u);
-      const bool full = f.rowFc[r] || f.rowFh[r];
-      const uint32_t bits = full ? vm : (smbits[r * MW + 2 + w] & vm);
-      if (u.mask) {
-        uint8_t* mrow = u.mask + static_cast<int64_t>(row0 + r) * u.mask_stride;
-        if (mask_vec && nv == 32) {
-          uint32_t wd[8];
-#pragma unroll
-          for (int q = 0; q < 8; ++q) wd[q] = (((bits >> (4 * q)) & 0xFu) * 0x00204081u) & 0x01010101u;
-          uint4* dst = reinterpret_cast<uint4*>(mrow + t0);
-          dst[0] = make_uint4(wd[0], wd[1], wd[2], wd[3]);
-          dst[1] = make_uint4(wd[4], wd[5], wd[6], wd[7]);
-        } else {
-          for (int j = 0; j < nv; ++j) mrow[t0 + j] = static_cast<uint8_t>((bits >> j) & 1u);
-        }
-      }
-      if (u.out && bits) {
-        if (inplace) {
-          uint8_t* orow =
-              static_cast<uint8_t*>(u.out) + static_cast<int64_t>(row0 + r) * u.out_stride * TR::kBytes;
-          uint32_t m = bits;
-          while (m) {
-            const int j = __ffs(m) - 1;
-            m &= m - 1u;
-            TR::zero(orow, t0 + j);
-          }
-        } else {
-          uint8_t* srow = sdata + r * dpitch;
-          uint32_t m = bits;
-          while (m) {
-            const int j = __ffs(m) - 1;
-            m &= m - 1u;
-            TR::zero(srow, t0 + j);
-          }
-        }
-      }
-    }
-    __syncthreads();
-    if (u.out && !inplace) {
-      if (u.flags & kUnitOutBulk) {
-        fence_async_smem();
-        __syncthreads();
-        if (tid == 0) {
-          uint8_t* gout = static_cast<uint8_t*>(u.out);
-          for (int r = 0; r < R; ++r)
-            bulk_store(gout + (row0 + r) * u.out_stride * TR::kBytes, sdata + r * dpitch,
-                       static_cast<uint32_t>(T * TR::kBytes));
-          bulk_commit();
-        }
-      } else {
-        uint8_t* gout = static_cast<uint8_t*>(u.out);
-        for (int r = 0; r < R; ++r)
-          for (int t = tid; t < T; t += NT)
-            TR::copy(gout + ((row0 + r) * u.out_stride + t) * TR::kBytes,
-                     sdata + r * dpitch + t * TR::kBytes);
-      }
-    }
-    if (tid == 0 && u.stats) {
-      atomicAdd(reinterpret_cast<unsigned long long*>(&u.stats->n_flag_time), f.cnt_time);
-      atomicAdd(reinterpret_cast<unsigned long long*>(&u.stats->n_chan_hist), f.cnt_hist);
-      atomicAdd(reinterpret_cast<unsigned long long*>(&u.stats->n_flag_total), f.cnt_total);
     }
     __syncthreads();
   }
-  if (tid == 0) bulk_wait_all();
+
+  // ---- history flagger (Section 4.1) and per-row counts
+  for (int r = tid; r < R; r += NT) {
+    const long long h = u.hist_slot >= 0 ? u.hist_slot + row0 + r : -1;
+    unsigned long long add_total;
+    if (f.rowFc[r]) {
+      if (h >= 0) kp.hist.pend_flag[h] = 0;
+      add_total = static_cast<unsigned long long>(T);
+    } else {
+      const int nfl = f.rowNFlag[r];
+      const int n = T - nfl;
+      uint8_t fh = 0;
+      if (n > 0) {
+        const unsigned long long su = f.rowS[r] - f.rowFlagSum[r];
+        const double cur = __ddiv_rn(__ull2double_rn(su), static_cast<double>(n));
+        double staged = cur;
+        if (kp.enable_history && h >= 0) {
+          const int cnt = kp.hist.count[h];
+          if (cnt >= kp.history_min && cnt > 0) {
+            const double thr = kp.hist.thr[h];
+            if (!(cur < thr)) {
+              fh = 1;
+              staged = thr;
+            }
+          }
+        }
+        if (h >= 0) {
+          kp.hist.pend[h] = staged;
+          kp.hist.pend_flag[h] = 1;
+          kp.hist.pend_seq[h] = kp.block_seq;
+        }
+      } else if (h >= 0) {
+        kp.hist.pend_flag[h] = 0;
+      }
+      f.rowFh[r] = fh;
+      atomicAdd(&f.cnt_time, static_cast<unsigned long long>(nfl));
+      if (fh) atomicAdd(&f.cnt_hist, 1ull);
+      add_total = fh ? static_cast<unsigned long long>(T) : static_cast<unsigned long long>(nfl);
+    }
+    atomicAdd(&f.cnt_total, add_total);
+  }
+  __syncthreads();
+
+  // ---- apply: mask bytes and masked data, streamed row by row (Sections 3, 4)
+  {
+    const bool inplace = (u.flags & kUnitInPlace) != 0;
+    const bool mask_vec = (u.flags & kUnitMaskVec) != 0;
+    const bool vin = (u.flags & kUnitInVec) != 0;
+    const bool vout = (u.flags & kUnitOutVec) != 0;
+    constexpr uint32_t kVm = (1u << VS) - 1u;
+    constexpr int NQO = 16 / VS, SEGO = 32 * NQO * VS;
+    const int nsego = (T + SEGO - 1) / SEGO;
+    for (int task = warp; task < R * nsego; task += NW) {
+      const int r = task / nsego, s = task - r * nsego;
+      const bool full = f.rowFc[r] || f.rowFh[r];
+      const uint32_t* M = smbits + r * MW + 2;
+      const int64_t grow_idx = static_cast<int64_t>(row0 + r);
+      uint4 win[NQO];
+      if (u.out && !inplace && vin && vout && !full) {
+#pragma unroll
+        for (int q = 0; q < NQO; ++q) {
+          const int x = s * SEGO + q * 32 * VS + lane * VS;
+          if (x + VS <= T)
+            win[q] = __ldg(reinterpret_cast<const uint4*>(gin + grow_idx * u.in_stride * TR::kBytes +
+                                                          static_cast<size_t>(x) * TR::kBytes));
+        }
+      }
+#pragma unroll
+      for (int q = 0; q < NQO; ++q) {
+        const int x = s * SEGO + q * 32 * VS + lane * VS;
+        if (x >= T) continue;
+        const int nv = min(VS, T - x);
+        const uint32_t valid = nv >= VS ? kVm : ((1u << nv) - 1u);
+        const uint32_t bits = full ? valid : ((M[x >> 5] >> (x & 31)) & valid);
+        if (u.mask) {
+          uint8_t* mrow = u.mask + grow_idx * u.mask_stride;
+          if (mask_vec && nv == VS) {
+            if constexpr (VS == 4) {
+              *reinterpret_cast<uint32_t*>(mrow + x) = (bits * 0x00204081u) & 0x01010101u;
+            } else {
+              const uint32_t lo = ((bits & 0xFu) * 0x00204081u) & 0x01010101u;
+              const uint32_t hi = (((bits >> 4) & 0xFu) * 0x00204081u) & 0x01010101u;
+              *reinterpret_cast<uint2*>(mrow + x) = make_uint2(lo, hi);
+            }
+          } else {
+            for (int j = 0; j < nv; ++j) mrow[x + j] = static_cast<uint8_t>((bits >> j) & 1u);
+          }
+        }
+        if (u.out) {
+          uint8_t* orow = static_cast<uint8_t*>(u.out) + grow_idx * u.out_stride * TR::kBytes;
+          if (inplace) {
+            uint32_t m = bits;
+            while (m) {
+              const int j = __ffs(m) - 1;
+              m &= m - 1u;
+              TR::zero(orow, x + j);
+            }
+          } else if (vin && vout && nv == VS) {
+            uint4 w = make_uint4(0u, 0u, 0u, 0u);
+            if (bits != kVm) {
+              w = win[q];
+              if (bits) {
+                uint32_t wd[4] = {w.x, w.y, w.z, w.w};
+#pragma unroll
+                for (int j = 0; j < VS; ++j) {
+                  if ((bits >> j) & 1u) {
+                    if constexpr (VS == 4) wd[j] = 0u;
+                    else wd[j >> 1] &= (j & 1) ? 0x0000FFFFu : 0xFFFF0000u;
+                  }
+                }
+                w = make_uint4(wd[0], wd[1], wd[2], wd[3]);
+              }
+            }
+            __stcs(reinterpret_cast<uint4*>(orow + static_cast<size_t>(x) * TR::kBytes), w);
+          } else {
+            const uint8_t* irow = gin + grow_idx * u.in_stride * TR::kBytes;
+            for (int j = 0; j < nv; ++j) {
+              if ((bits >> j) & 1u) TR::zero(orow, x + j);
+              else TR::copy(orow + static_cast<size_t>(x + j) * TR::kBytes,
+                            irow + static_cast<size_t>(x + j) * TR::kBytes);
+            }
+          }
+        }
+      }
+    }
+  }
+  if (tid == 0 && u.stats) {
+    atomicAdd(reinterpret_cast<unsigned long long*>(&u.stats->n_flag_time), f.cnt_time);
+    atomicAdd(reinterpret_cast<unsigned long long*>(&u.stats->n_chan_hist), f.cnt_hist);
+    atomicAdd(reinterpret_cast<unsigned long long*>(&u.stats->n_flag_total), f.cnt_total);
+  }
+}
+
+// ------------------------------------------------------------------ scheduling
+
+__device__ __forceinline__ bool task_ready(const KParams& kp, int t) {
+  const Task tk = kp.tasks[t];
+  if (tk.kind == kTaskStats) return true;
+  const int r = ld_acquire(&kp.ustate[tk.unit].ready);
+  return tk.kind == kTaskFine ? r >= 1 : r >= 2;
+}
+
+// Thread 0: the next task to run, or -1 when the queue is drained.  A task
+// whose unit is not ready yet (fine / flag tasks wait for the unit's
+// statistics) is parked in a small per-CTA list and the next task is taken
+// instead; parked tasks run as soon as they are ready.  Stats tasks never
+// wait, fine tasks wait only on stats tasks and flag tasks only on fine
+// tasks, and a CTA that polls always re-checks every task it holds, so the
+// waits cannot form a cycle.  Gives up after kp.spin_limit ns without
+// progress (error word set).
+template <int NT>
+__device__ int sched_next(const KParams& kp, Fixed<NT>& f) {
+  constexpr int kDefer = 8;
+  unsigned long long t0 = 0;
+  for (;;) {
+    for (int i = 0; i < f.n_def; ++i) {
+      const int t = f.def[i];
+      if (task_ready(kp, t)) {
+        f.def[i] = f.def[--f.n_def];
+        return t;
+      }
+    }
+    if (!f.q_done && f.n_def <= kDefer) {
+      const int t = atomicAdd(kp.queue, 1);
+      if (t >= kp.n_tasks) {
+        f.q_done = 1;
+        continue;
+      }
+      if (task_ready(kp, t)) return t;
+      f.def[f.n_def++] = t;
+      continue;
+    }
+    if (f.n_def == 0) return -1;
+    if (*reinterpret_cast<volatile int*>(kp.err) != 0) return -1;
+    if (t0 == 0) t0 = global_ns();
+    else if (global_ns() - t0 > static_cast<unsigned long long>(kp.spin_limit)) {
+      set_error(kp, kErrTimeout, 500);
+      return -1;
+    }
+    __nanosleep(256);
+  }
+}
+
+// ------------------------------------------------------------------ the kernel
+// Persistent loop over the task queue.  Tasks wait (bounded) only on tasks
+// that precede them in the queue, so no CTA ever waits on work that has not
+// been handed out.
+
+template <int DT, int NT>
+__global__ void __launch_bounds__(NT, 512 / NT) lof_block_kernel(const KParams kp) {
+  extern __shared__ __align__(128) uint8_t smem[];
+  __shared__ Fixed<NT> f;
+  __shared__ uint32_t s_K0[kMaxLogWindow + 1], s_cq[kMaxLogWindow + 1];
+  __shared__ uint32_t s_Kp[kKTable];
+  __shared__ int s_dirty[kMaxRowsPerTask];
+  const int tid = threadIdx.x;
+  if (tid == 0) {
+    f.q_done = 0;
+    f.n_def = 0;
+  }
+  for (;;) {
+    if (tid == 0) {
+      f.item = sched_next<NT>(kp, f);
+      f.ok = 1;
+      f.cnt_time = f.cnt_total = f.cnt_hist = 0;
+    }
+    __syncthreads();
+    const int ti = f.item;
+    if (ti < 0) break;
+    const Task tk = kp.tasks[ti];
+    const DevUnit u = kp.units[tk.unit];
+    UnitState* const us = kp.ustate + tk.unit;
+    if (tk.kind == kTaskStats) task_stats<DT, NT>(kp, u, us, tk, smem, f);
+    else if (tk.kind == kTaskFine) task_fine<DT, NT>(kp, u, us, tk, smem, f);
+    else task_flag<DT, NT>(kp, u, us, tk, smem, f, s_K0, s_cq, s_Kp, s_dirty);
+    __syncthreads();
+    if (!f.ok) break;
+  }
 }
 
 // ------------------------------------------------------------------ history commit

@@ -21,9 +21,9 @@
 
 namespace {
 
-constexpr size_t kScratchBytes = size_t(24) << 20;  // 24 MiB, held by every GPU that loads the library
+constexpr size_t kScratchBytes = size_t(64) << 20;  // 64 MiB, held by every GPU that loads the library
 constexpr int kMaxUnitsNA = 1024;
-constexpr int kMaxItemsNA = 65536;
+constexpr int kMaxTasksNA = 262144;
 constexpr int kMaxDevicesNA = 64;
 
 // The scratch.  In host code its name is only a host-side stand-in: the
@@ -33,8 +33,7 @@ static __device__ __align__(256) unsigned char g_scratch[kScratchBytes];
 std::mutex g_mu;                        // one caller at a time (the arrays below are shared)
 void* g_addr[kMaxDevicesNA] = {};       // device address of g_scratch, per device
 lofk::DevUnit g_du[kMaxUnitsNA];
-lofk::Item g_items[kMaxItemsNA];
-int g_Ts[kMaxUnitsNA];
+lofk::Task g_tasks[kMaxTasksNA];
 
 size_t up256(size_t x) { return (x + 255) & ~size_t(255); }
 
@@ -99,21 +98,21 @@ extern "C" int lof_flag_block_noalloc(const lof_params* params, int dtype, const
   cudaDeviceGetAttribute(&h.n_sm, cudaDevAttrMultiProcessorCount, dev);
   cudaDeviceGetAttribute(&h.smem_per_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev);
   cudaDeviceGetAttribute(&h.smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
-  h.tuning = lof_tuning{256, 2, 0, 512};
-  int n_items = 0;
-  rc = lofk::host_count_items(h, dtype, units, n_units, g_Ts, &n_items, why, sizeof why);
+  h.tuning = lof_tuning{256, 2, 0, 2048};
+  int n_tasks = 0;
+  rc = lofk::host_count_tasks(h, dtype, units, n_units, &n_tasks, why, sizeof why);
   if (rc) return fail(rc);
-  if (n_items > kMaxItemsNA) {
+  if (n_tasks > kMaxTasksNA) {
     snprintf(why, sizeof why,
-             "lof_flag_block_noalloc: the block needs %d work items, the maximum is %d", n_items,
-             kMaxItemsNA);
+             "lof_flag_block_noalloc: the block needs %d tasks, the maximum is %d", n_tasks,
+             kMaxTasksNA);
     return fail(LOF_ERR_INVALID);
   }
   lofk::Prep pr{};
-  rc = lofk::host_prepare(h, dtype, units, n_units, g_du, g_items, kMaxItemsNA, g_Ts, &pr, why,
+  rc = lofk::host_prepare(h, dtype, units, n_units, g_du, g_tasks, kMaxTasksNA, &pr, why,
                           sizeof why);
   if (rc) return fail(rc);
-  // carve the scratch: fixed part, then per-CTA slots and histograms
+  // carve the scratch
   unsigned char* base = static_cast<unsigned char*>(g_addr[dev]);
   size_t off = 0;
   lofk::Scratch sc{};
@@ -121,47 +120,31 @@ extern "C" int lof_flag_block_noalloc(const lof_params* params, int dtype, const
   off += 256;
   sc.units = reinterpret_cast<lofk::DevUnit*>(base + off);
   off += up256(n_units * sizeof(lofk::DevUnit));
-  sc.items = reinterpret_cast<lofk::Item*>(base + off);
-  off += up256(pr.n_items * sizeof(lofk::Item));
-  sc.ctl = reinterpret_cast<lofk::UnitCtl*>(base + off);
-  off += up256(n_units * sizeof(lofk::UnitCtl));
-  sc.members = reinterpret_cast<int*>(base + off);
-  off += up256(pr.n_items * sizeof(int));
+  sc.tasks = reinterpret_cast<lofk::Task*>(base + off);
+  off += up256(static_cast<size_t>(pr.n_tasks) * sizeof(lofk::Task));
   sc.chanS = reinterpret_cast<unsigned long long*>(base + off);
   off += up256(static_cast<size_t>(pr.n_chan) * 8);
   sc.chanFc = base + off;
   off += up256(static_cast<size_t>(pr.n_chan));
-  const size_t per_cta = up256(sizeof(lofk::Slot)) + up256(lofk::kCoarseBins * 4) + 32;
-  int maxG = 0;
-  for (int i = 0; i < n_units; ++i) maxG = std::max(maxG, g_du[i].n_items);
-  const int fit = off < kScratchBytes ? static_cast<int>((kScratchBytes - off) / per_cta) : 0;
-  if (fit < maxG) {
-    snprintf(why, sizeof why,
-             "lof_flag_block_noalloc: the block needs more than the %zu bytes of static scratch",
-             kScratchBytes);
-    return fail(LOF_ERR_INVALID);
-  }
-  pr.grid = std::min(pr.grid, fit);
-  sc.pubm = reinterpret_cast<unsigned long long*>(base + off);
-  off += up256(static_cast<size_t>(pr.grid) * 32);
-  sc.pub = reinterpret_cast<uint32_t*>(base + off);
-  off += up256(static_cast<size_t>(pr.grid) * lofk::kCoarseBins * 4);
-  sc.slots = reinterpret_cast<lofk::Slot*>(base + off);
-  off += static_cast<size_t>(pr.grid) * up256(sizeof(lofk::Slot));
+  sc.ustate = reinterpret_cast<lofk::UnitState*>(base + off);
+  off += static_cast<size_t>(n_units) * sizeof(lofk::UnitState);
   if (off > kScratchBytes) {
-    snprintf(why, sizeof why, "lof_flag_block_noalloc: scratch layout overflow");
+    snprintf(why, sizeof why,
+             "lof_flag_block_noalloc: the block needs %zu bytes of scratch, the static array holds %zu",
+             off, kScratchBytes);
     return fail(LOF_ERR_INVALID);
   }
   sc.hist = lofk::HistoryDev{};
   cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
-  // the error word and detail start at zero on every call (the queue is
-  // cleared by host_launch); every other part is written before it is read
+  // the error word and detail start at zero on every call (the queue and the
+  // per-unit counters, moments and histograms are cleared by host_launch);
+  // every other part is written before it is read
   e = cudaMemsetAsync(sc.ctrl, 0, 4 * sizeof(int), st);
   if (e != cudaSuccess) {
     snprintf(why, sizeof why, "lof_flag_block_noalloc: %s", cudaGetErrorString(e));
     return fail(LOF_ERR_CUDA);
   }
-  rc = lofk::host_launch(P, h, dtype, pr, sc, g_du, n_units, g_items, 0, cuda_stream, why,
+  rc = lofk::host_launch(P, h, dtype, pr, sc, g_du, n_units, g_tasks, 0, cuda_stream, why,
                          sizeof why);
   if (rc) return fail(rc);
   if (status) {
