@@ -173,9 +173,9 @@ int lof_max_time(const lof_ctx *ctx, int dtype);
 /* Launch-shape knobs (an autotuner sweeps them; results do not depend on
  * them).  0 keeps the current value. */
 typedef struct {
-  int32_t threads;         /* threads per CTA: 128, 256, 512 */
-  int32_t ctas_per_sm;     /* resident CTAs per SM: 1 or 2 */
-  int32_t tile_bytes;      /* shared-memory bytes for a tile of rows */
+  int32_t threads;         /* threads per CTA: 128 (default) or 256 */
+  int32_t ctas_per_sm;     /* resident CTAs per SM: 1 to 4 (default 4) */
+  int32_t tile_bytes;      /* cap on the shared-memory bytes of a CTA */
   int32_t fine_bins;       /* counters per exact-selection refinement round */
 } lof_tuning;
 int lof_set_tuning(lof_ctx *ctx, const lof_tuning *t);

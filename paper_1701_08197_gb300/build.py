@@ -1,8 +1,9 @@
 """Build step of the CUDA flagger library (liblof.so, sm_103a only).
 
-Compiles the two translation units of csrc/ in parallel with nvcc and links
-them into paper_1701_08197_gb300/_build/liblof.so (in-tree, git-ignored).
-Rebuilds only when a source or header is newer than the library.
+Compiles the translation units of csrc/ in parallel with nvcc (the kernel
+file once per input type) and links them into
+paper_1701_08197_gb300/_build/liblof.so (in-tree, git-ignored).  Rebuilds
+only when a source or header is newer than the library.
 """
 from __future__ import annotations
 
@@ -19,7 +20,14 @@ CSRC = os.path.join(HERE, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(BUILD, "liblof.so")
-SOURCES = ["lof_kernels.cu", "lof_api.cu", "lof_noalloc.cu"]
+# (source, object, extra nvcc flags)
+UNITS = [
+    ("lof_kernels.cu", "lof_kernels_ci16.o", ["-DLOF_KERNEL_DT=2"]),
+    ("lof_kernels.cu", "lof_kernels_ci8.o", ["-DLOF_KERNEL_DT=1"]),
+    ("lof_api.cu", "lof_api.o", []),
+    ("lof_noalloc.cu", "lof_noalloc.o", []),
+]
+SOURCES = sorted({u[0] for u in UNITS})
 HEADERS = [os.path.join(CSRC, "lof_internal.h"), os.path.join(INCLUDE, "lof.h")]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 _lock = threading.Lock()
@@ -49,9 +57,10 @@ def build(force: bool = False, verbose: bool = False) -> str:
         cc = nvcc()
         common = ["-std=c++17", "-O3", "-lineinfo", "-Xcompiler", "-fPIC", "-I" + INCLUDE] + ARCH
 
-        def compile_one(src):
-            obj = os.path.join(BUILD, os.path.splitext(src)[0] + ".o")
-            cmd = [cc] + common + ["-c", os.path.join(CSRC, src), "-o", obj]
+        def compile_one(unit):
+            src, oname, extra = unit
+            obj = os.path.join(BUILD, oname)
+            cmd = [cc] + common + extra + ["-c", os.path.join(CSRC, src), "-o", obj]
             if verbose:
                 print(" ".join(cmd), file=sys.stderr)
             r = subprocess.run(cmd, capture_output=True, text=True)
@@ -59,8 +68,8 @@ def build(force: bool = False, verbose: bool = False) -> str:
                 raise RuntimeError(f"nvcc failed for {src}:\n{r.stderr}")
             return obj
 
-        with ThreadPoolExecutor(len(SOURCES)) as ex:
-            objs = list(ex.map(compile_one, SOURCES))
+        with ThreadPoolExecutor(len(UNITS)) as ex:
+            objs = list(ex.map(compile_one, UNITS))
         tmp = LIB + f".{os.getpid()}.tmp"
         cmd = [cc, "-shared", "-o", tmp] + objs + ARCH + ["-lcudart"]
         r = subprocess.run(cmd, capture_output=True, text=True)

@@ -46,7 +46,7 @@ struct lof_ctx {
   lof_params params{};
   int n_sm = 0;
   int smem_per_sm = 0, smem_optin = 0;
-  lof_tuning tuning{256, 2, 0, 2048};
+  lof_tuning tuning{128, 4, 0, 2048};
   // history
   int64_t n_slots = 0;
   int H = 0;
@@ -299,8 +299,8 @@ extern "C" int lof_set_tuning(lof_ctx* c, const lof_tuning* t) {
   if (!c || !t) return fail(c, LOF_ERR_INVALID, "lof_set_tuning: NULL argument");
   lof_tuning n = c->tuning;
   if (t->threads) {
-    if (t->threads != 256 && t->threads != 512)
-      return fail(c, LOF_ERR_INVALID, "threads must be 256 or 512");
+    if (t->threads != 128 && t->threads != 256)
+      return fail(c, LOF_ERR_INVALID, "threads must be 128 or 256");
     n.threads = t->threads;
   }
   if (t->ctas_per_sm) {
@@ -328,39 +328,44 @@ extern "C" int lof_get_tuning(const lof_ctx* c, lof_tuning* t) {
 
 namespace {
 
-// Rows of one flag task: as many as fit the shared-memory budget (prefix
-// buffer + flag words + fire words per row).
-int flag_rows(int dtype, int T, int budget_bytes) {
-  const int words = pfx_row_words(dtype, T) + 2 * ((T + 31) / 32 + 4);
-  return std::min(lofk::kMaxRowsPerTask, budget_bytes / (4 * words));
+// Rows of one flag task: four per warp, fewer if the shared memory cannot
+// hold their flag words plus one row of the general (any-magnitude) path.
+int flag_words_row(int T) { return (T + 31) / 32 + 4; }
+int flag_rows(int dtype, int T, int budget_bytes, int threads) {
+  const int mw = flag_words_row(T), pr = pfx_row_words(dtype, T);
+  int R = std::min(lofk::kMaxRowsPerTask, 4 * (threads / 32));
+  while (R > 0 && 4 * (R * mw + pr + mw) > budget_bytes) --R;
+  return R;
 }
 
 // Rows of one stats / fine task (streamed, ~64K samples per task).
 int stat_rows(int T) { return std::max(1, std::min(lofk::kMaxRowsPerTask, 65536 / std::max(1, T))); }
 
-// Shared-memory plan: the largest flag task of the launch or the unit-wide
-// workspace, whichever is larger.
+// Shared-memory plan: the unit-wide workspace, the flag words of a flag
+// task and as many rows of the general path as the budget allows.
 bool make_plan(const lofk::HostCfg& h, int dtype, const int* Ts, int nT, lofk::Plan* pl,
                char* why, int nwhy) {
   pl->threads = h.tuning.threads;
   pl->ctas = h.tuning.ctas_per_sm;
   int budget = dyn_budget(h, dtype, pl->threads, pl->ctas);
   if (h.tuning.tile_bytes) budget = std::min(budget, h.tuning.tile_bytes);
-  int need = lofk::kWorkspaceBytes;
+  int need = lofk::kWorkspaceBytes, want = lofk::kWorkspaceBytes;
   for (int i = 0; i < nT; ++i) {
-    const int R = flag_rows(dtype, Ts[i], budget);
+    const int R = flag_rows(dtype, Ts[i], budget, pl->threads);
     if (R < 1) {
       snprintf(why, nwhy, "n_time %d does not fit the shared-memory budget (%d bytes)", Ts[i], budget);
       return false;
     }
-    const int words = pfx_row_words(dtype, Ts[i]) + 2 * ((Ts[i] + 31) / 32 + 4);
-    need = std::max(need, R * words * 4);
+    const int mw = flag_words_row(Ts[i]), pr = pfx_row_words(dtype, Ts[i]);
+    need = std::max(need, 4 * (R * mw + pr + mw));
+    want = std::max(want, 4 * (R * mw + R * (pr + mw)));
   }
   if (need > budget) {
     snprintf(why, nwhy, "the workspace (%d bytes) exceeds the shared-memory budget (%d)", need, budget);
     return false;
   }
-  pl->smem = need;
+  pl->smem = std::min(budget, want) & ~127;
+  if (pl->smem < need) pl->smem = need;
   return true;
 }
 
@@ -375,7 +380,7 @@ int host_count_tasks(const HostCfg& h, int dtype, const lof_unit* units, int n_u
   int64_t n = 0;
   for (int i = 0; i < n_units; ++i) {
     const int T = units[i].n_time, C = units[i].n_chan;
-    const int Rc = flag_rows(dtype, T, budget);
+    const int Rc = flag_rows(dtype, T, budget, h.tuning.threads);
     if (Rc < 1) {
       snprintf(why, nwhy, "n_time %d does not fit the shared-memory budget (%d bytes)", T, budget);
       return LOF_ERR_INVALID;
@@ -446,7 +451,7 @@ int host_prepare(const HostCfg& h, int dtype, const lof_unit* units, int n_units
     if (u.mask && (reinterpret_cast<uintptr_t>(u.mask) % 16) == 0 && (u.mask_row_stride % 16) == 0)
       flags |= kUnitMaskVec;
     d.flags = flags;
-    const int Rs = stat_rows(u.n_time), Rc = flag_rows(dtype, u.n_time, budget);
+    const int Rs = stat_rows(u.n_time), Rc = flag_rows(dtype, u.n_time, budget, pl.threads);
     d.nS = (u.n_chan + Rs - 1) / Rs;
     d.nF = d.nS;
     d.nC = (u.n_chan + Rc - 1) / Rc;
@@ -542,6 +547,7 @@ int host_launch(const lof_params& P, const HostCfg& h, int dtype, const Prep& pr
   kp.enable_history = P.enable_history;
   kp.block_seq = seq;
   kp.spin_limit = 2000000000ll;  // 2 s
+  kp.dyn_smem = pr.plan.smem;
   const int krc = lofk_launch_block(dtype, &kp, pr.grid, pr.plan.threads, pr.plan.smem, stream, 1);
   if (krc != 0) {
     snprintf(why, nwhy, "kernel launch failed: %s (grid %d, %d threads, %d B)",

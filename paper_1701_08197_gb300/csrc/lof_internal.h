@@ -139,6 +139,7 @@ struct KParams {
   int enable_freq, enable_time, enable_history;
   uint64_t block_seq;
   long long spin_limit;         // bound of every device-side wait (ns)
+  int dyn_smem;                 // dynamic shared memory of each CTA (bytes)
 };
 
 struct CommitParams {

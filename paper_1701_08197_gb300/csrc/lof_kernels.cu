@@ -333,6 +333,10 @@ __device__ __forceinline__ void atomic_add_u128(unsigned long long* lohi, unsign
   if (vh + carry) atomicAdd(lohi + 1, vh + carry);
 }
 
+// Offset-map entry of a coarse key that holds no target: val + kNoTarget >=
+// 2^31 - 1 for every power (at most 2^31), beyond any spec index.
+constexpr uint32_t kNoTarget = 0x7FFFFFFFu;
+
 __device__ __forceinline__ Target ld_target(const Target* p) {
   const uint4 v = __ldcg(reinterpret_cast<const uint4*>(p));
   return Target{v.x, v.y, v.z, v.w};
@@ -959,24 +963,23 @@ __device__ void merge_fine(const KParams& kp, UnitState* slot, uint8_t* ws, Fixe
 
 // ------------------------------------------------------------------ time pass helpers
 //
-// Layout of one batch of rows in the prefix buffer (32-bit words per row):
+// Packed values (integer units whose I = 1 threshold is below 2^20): after
+// the I = 1 pass every unflagged power is at most floor(threshold_1), so a
+// window of up to 64 unflagged values sums to less than Z = 2^26.  Flagged
+// samples are stored as u = Z: the difference of two prefix entries is then
+// S = n_flagged * Z + sum_unflagged with both parts recoverable, and the
+// window fires exactly when S > Kp[n] = n * Z + floor((I - n) * threshold_I).
+// These rows run one warp per row with the row in registers (wr_segment).
+//
+// Any other unit takes the general path: rows in a shared-memory prefix
+// buffer, exact 64-bit sums of the unflagged values.  Layout of one batch of
+// rows in that buffer (32-bit words per row):
 //   Pl: (nch + 3) chunks x 36 words -- exclusive prefix, inside each 32-sample
 //       chunk, of the values u (padded layout, see pidx); three zero chunks
 //       follow the row so windows may look ahead by up to 64 samples
 //   Pb: nch + 4 words -- exclusive prefix of the chunk totals (chunk bases)
 //   Tc: nch + 4 words -- chunk totals
 // so that the prefix of u at x is Pb[x >> 5] + Pl[pidx(x)] (mod 2^32).
-//
-// Packed path (integer units whose I = 1 threshold is below 2^20): after the
-// I = 1 pass every unflagged power is at most floor(threshold_1), so a window
-// of up to 64 unflagged values sums to less than Z = 2^26.  Flagged samples
-// are stored as u = Z: the difference of two prefix entries is then
-// S = n_flagged * Z + sum_unflagged with both parts recoverable.  Each window
-// is judged in three integer operations: Q = S + (S >> 26) * (tau - Z) =
-// sum_unflagged + n_flagged * tau, the Section 2.1 sum with flagged samples
-// counted as tau >= threshold_I + 2.  Q <= K[0] proves that the window does
-// not fire; only chunks holding a larger Q are judged exactly against
-// Kp[n] = n * Z + floor((I - n) * threshold_I).
 
 constexpr uint32_t kZ = 1u << 26;
 
@@ -989,73 +992,6 @@ __device__ __forceinline__ StLayout st_layout(int nch) {
   L.PBW = nch + 4;
   L.per_row = (L.PLW + 2 * L.PBW + 3) & ~3;  // rows start on 16-byte boundaries
   return L;
-}
-
-__device__ __forceinline__ void load32(const uint32_t* p, uint32_t (&a)[32]) {
-#pragma unroll
-  for (int q = 0; q < 8; ++q) {
-    const uint4 w = reinterpret_cast<const uint4*>(p)[q];
-    a[4 * q + 0] = w.x;
-    a[4 * q + 1] = w.y;
-    a[4 * q + 2] = w.z;
-    a[4 * q + 3] = w.w;
-  }
-}
-
-// Fire bits of the 32 windows of size I starting in chunk w (packed path).
-// S[j] = prefix(t0 + j + I) - prefix(t0 + j) is formed in place.
-template <int I>
-__device__ __forceinline__ uint32_t packed_fire(const uint32_t* pl, const uint32_t* pb, int w,
-                                                uint32_t K0, uint32_t cq, const uint32_t* Kp) {
-  uint32_t S[32];
-  const uint32_t base0 = pb[w];
-  if constexpr (I >= 32) {
-    const int w2 = w + I / 32;
-    load32(pl + pidx(w2 << 5), S);
-    const uint32_t dB = pb[w2] - base0;
-    const uint4* pa = reinterpret_cast<const uint4*>(pl + pidx(w << 5));
-#pragma unroll
-    for (int q = 0; q < 8; ++q) {
-      const uint4 v = pa[q];
-      S[4 * q + 0] += dB - v.x;
-      S[4 * q + 1] += dB - v.y;
-      S[4 * q + 2] += dB - v.z;
-      S[4 * q + 3] += dB - v.w;
-    }
-  } else {
-    load32(pl + pidx(w << 5), S);
-    const uint32_t d1 = pb[w + 1] - base0;
-    const uint32_t* pn = pl + pidx((w + 1) << 5);
-    uint32_t t[I < 4 ? 4 : I];
-    if constexpr (I >= 4) {
-#pragma unroll
-      for (int q = 0; q < I / 4; ++q) {
-        const uint4 v = reinterpret_cast<const uint4*>(pn)[q];
-        t[4 * q + 0] = v.x;
-        t[4 * q + 1] = v.y;
-        t[4 * q + 2] = v.z;
-        t[4 * q + 3] = v.w;
-      }
-    } else if constexpr (I == 2) {
-      const uint2 v = *reinterpret_cast<const uint2*>(pn);
-      t[0] = v.x;
-      t[1] = v.y;
-    } else {
-      t[0] = pn[0];
-    }
-#pragma unroll
-    for (int j = 0; j < 32 - I; ++j) S[j] = S[j + I] - S[j];
-#pragma unroll
-    for (int j = 32 - I; j < 32; ++j) S[j] = t[j + I - 32] + d1 - S[j];
-  }
-  uint32_t mx = 0;
-#pragma unroll
-  for (int j = 0; j < 32; ++j) mx = max(mx, S[j] + (S[j] >> 26) * cq);
-  if (mx <= K0) return 0u;
-  uint32_t fire = 0;
-#pragma unroll
-  for (int j = 0; j < 32; ++j) fire |= (S[j] > Kp[S[j] >> 26] ? 1u : 0u) << j;
-  return fire;
 }
 
 __device__ __forceinline__ uint32_t bit_at(const uint32_t* M, int j) {
@@ -1245,6 +1181,261 @@ __device__ void st_build(const DevUnit& u, int row0, int T, int nch, const int* 
   }
 }
 
+// Raw 16-byte vector of samples [x, x + kVec) of a row, zero at or past T.
+template <int DT>
+__device__ __forceinline__ uint4 gload_raw(const uint8_t* grow, int x, int T, bool vec) {
+  using TR = Traits<DT>;
+  if (vec && x + TR::kVec <= T)
+    return __ldg(reinterpret_cast<const uint4*>(grow + static_cast<size_t>(x) * TR::kBytes));
+  uint32_t w[4] = {0u, 0u, 0u, 0u};
+  for (int j = 0; j < TR::kVec && x + j < T; ++j) {
+    if constexpr (DT == LOF_CI16) {
+      w[j] = reinterpret_cast<const uint32_t*>(grow)[x + j];
+    } else {
+      const uint32_t h = reinterpret_cast<const uint16_t*>(grow)[x + j];
+      w[j >> 1] |= h << (16 * (j & 1));
+    }
+  }
+  return make_uint4(w[0], w[1], w[2], w[3]);
+}
+
+// Power of sample j (static) of a raw vector.
+template <int DT>
+__device__ __forceinline__ uint32_t raw_pw(const uint4& w, int j) {
+  if constexpr (DT == LOF_CI16) {
+    const uint32_t c = j == 0 ? w.x : j == 1 ? w.y : j == 2 ? w.z : w.w;
+    return Traits<DT>::pw(c);
+  } else {
+    const int k = j >> 1;
+    const uint32_t c = k == 0 ? w.x : k == 1 ? w.y : k == 2 ? w.z : w.w;
+    return Traits<DT>::pw((j & 1) ? (c >> 16) : c);
+  }
+}
+
+// ------------------------------------------------------------------ warp-row time pass
+// SumThreshold along time (Section 2.1) over one row segment by one warp,
+// every value in registers.  Lane L holds the NPL consecutive samples
+// s0 + L*NPL + [0, NPL) as packed values u[] (unflagged: the power, at most
+// K1 < 2^20 after the I = 1 pass; flagged: Z = 2^26) and their flag bits
+// M[].  The packed sum of a window is S = n * Z + sum_unflagged, and the
+// window fires exactly when S > Kp[n] = n * Z + floor((I - n) * threshold_I)
+// (n = S >> 26).  The sums slide along the lane, one three-input add per
+// window, taking the values past the lane's end from the next lanes by
+// shuffle; each decision is the sign bit of Kp[n] - S (|.| < 2^26), shifted
+// into the lane's fire words with a funnel shift.  New flags replace their
+// values by Z.
+//
+// Rows longer than 32 * NPL are cut into segments that overlap by a halo of
+// sum_I (I - 1) = 120 samples on each side: a flag decision at x depends
+// only on samples within I - 1 of x at each window size, so the flags of a
+// segment's interior equal those of the whole row.
+
+constexpr unsigned kFull = 0xFFFFFFFFu;
+constexpr int kWrHalo = 120;  // 0 + 1 + 3 + 7 + 15 + 31 + 63
+
+template <int NPL>
+struct WrRow {
+  static constexpr int NW = NPL / 32;
+  uint32_t u[NPL];  // packed values
+  uint32_t M[NW];   // flag bits of the lane's samples
+};
+
+// u at lane-relative position x >= 0 (x < 3 * NPL), from the next lanes by
+// shuffle; zero past lane 31 (past the segment).
+template <int NPL>
+__device__ __forceinline__ uint32_t wr_uat(const WrRow<NPL>& R, int lane, int x) {
+  if (x < NPL) return R.u[x];
+  const int q = x / NPL;
+  uint32_t v = __shfl_down_sync(kFull, R.u[x - q * NPL], q);
+  return lane + q < 32 ? v : 0u;
+}
+
+// Fire words F[w] (bit b: the window of size I at j = 32w + b fires), by a
+// descending slide of the packed window sums.
+template <int NPL, int I>
+__device__ __forceinline__ void wr_fire(const WrRow<NPL>& R, int lane, const uint32_t* Kp,
+                                        uint32_t (&F)[NPL / 32]) {
+  constexpr int NW = NPL / 32, m = I - 1;
+  // packed sum of the m values after the lane's last one
+  uint32_t hs;
+  {
+    constexpr int a = m < NPL ? m : NPL;
+    uint32_t A = 0u;
+#pragma unroll
+    for (int k = 0; k < a; ++k) A += R.u[k];
+    hs = __shfl_down_sync(kFull, A, 1);
+    if (lane + 1 >= 32) hs = 0u;
+    if constexpr (m > NPL) {
+      uint32_t B = 0u;
+#pragma unroll
+      for (int k = 0; k < m - NPL; ++k) B += R.u[k];
+      uint32_t hb = __shfl_down_sync(kFull, B, 2);
+      if (lane + 2 >= 32) hb = 0u;
+      hs += hb;
+    }
+  }
+  uint32_t S = R.u[NPL - 1] + hs;
+#pragma unroll
+  for (int w = NW - 1; w >= 0; --w) {
+    uint32_t f = 0u;
+#pragma unroll
+    for (int b = 31; b >= 0; --b) {
+      const int j = 32 * w + b;
+      if ((j & 15) == 15) __syncwarp();
+      f = __funnelshift_l(Kp[S >> 26] - S, f, 1);
+      if (j > 0) S = S + R.u[j - 1] - wr_uat<NPL>(R, lane, j - 1 + I);
+    }
+    F[w] = f;
+  }
+}
+
+// Dilate the fire bits (a fired window flags its I samples), add the new
+// flags to M and store them as Z.  I is a run-time value here so that one
+// copy of this code serves every window size.
+template <int NPL>
+__device__ __forceinline__ void wr_apply(WrRow<NPL>& R, int lane, int nvalid, int I,
+                                         uint32_t (&F)[NPL / 32]) {
+  constexpr int NW = NPL / 32;
+#pragma unroll
+  for (int w = 0; w < NW; ++w) {
+    const int nv = nvalid - 32 * w;
+    const uint32_t vm = nv >= 32 ? kFull : (nv <= 0 ? 0u : ((1u << nv) - 1u));
+    F[w] &= vm;
+  }
+  // the two fire words just before the lane's first word
+  uint32_t p1, p2;
+  if constexpr (NW == 1) {
+    p1 = __shfl_up_sync(kFull, F[0], 1);
+    p2 = __shfl_up_sync(kFull, F[0], 2);
+  } else {
+    p1 = __shfl_up_sync(kFull, F[NW - 1], 1);
+    p2 = __shfl_up_sync(kFull, F[NW - 2], 1);
+  }
+  if (lane < 1) p1 = 0u;
+  if (lane < (NW == 1 ? 2 : 1)) p2 = 0u;
+  uint32_t nw[NW];
+  uint32_t anyw = 0u;
+#pragma unroll
+  for (int w = 0; w < NW; ++w) {
+    const uint32_t f0 = F[w];
+    const uint32_t f1 = w >= 1 ? F[w - 1] : p1;
+    const uint32_t f2 = w >= 2 ? F[w - 2] : (w == 1 ? p1 : p2);
+    const uint32_t Dw = (I <= 32) ? dilate32(f0, f1, I) : (dilate32(f0, f1, 32) | dilate32(f1, f2, 32));
+    nw[w] = Dw & ~R.M[w];
+    anyw |= nw[w];
+  }
+#pragma unroll
+  for (int w = 0; w < NW; ++w) R.M[w] |= nw[w];
+  if (!__any_sync(kFull, anyw != 0u)) return;
+#pragma unroll
+  for (int j = 0; j < NPL; ++j)
+    if ((nw[j >> 5] >> (j & 31)) & 1u) R.u[j] = kZ;
+}
+
+// Loads the lane's samples (zero at or past T) as powers, flags those above
+// K1 (the I = 1 pass) and stores them as Z.
+template <int DT, int NPL>
+__device__ __forceinline__ void wr_build(WrRow<NPL>& R, const uint8_t* grow, int xl, int T,
+                                         bool vin, uint32_t K1) {
+  constexpr int VS = Traits<DT>::kVec, NV = NPL / VS;
+  uint4 v[NV];
+#pragma unroll
+  for (int q = 0; q < NV; ++q) {
+    const int x = xl + q * VS;
+    v[q] = x < T ? gload_raw<DT>(grow, x, T, vin) : make_uint4(0u, 0u, 0u, 0u);
+  }
+#pragma unroll
+  for (int w = 0; w < NPL / 32; ++w) R.M[w] = 0u;
+#pragma unroll
+  for (int j = 0; j < NPL; ++j) {
+    const uint32_t uu = raw_pw<DT>(v[j / VS], j % VS);
+    const bool fl = uu > K1;
+    R.u[j] = fl ? kZ : uu;
+    if (fl) R.M[j >> 5] |= 1u << (j & 31);
+  }
+}
+
+// Segments of a row: the first starts at 0, each later one at least
+// kWrHalo samples (rounded to whole 32-sample words) before the end of the
+// previous interior; a segment's interior ends kWrHalo samples (rounded down
+// to a word) before its span, except at the end of the row.
+template <int NPL>
+__device__ __forceinline__ void wr_seg_bounds(int T, int sg, int& s0, int& oa, int& ob) {
+  constexpr int SPAN = 32 * NPL;
+  oa = 0;
+  s0 = 0;
+  ob = SPAN >= T ? T : ((SPAN - kWrHalo) & ~31);
+  for (int i = 0; i < sg; ++i) {
+    oa = ob;
+    s0 = (oa - kWrHalo) & ~31;
+    ob = s0 + SPAN >= T ? T : ((s0 + SPAN - kWrHalo) & ~31);
+  }
+}
+template <int NPL>
+__device__ __forceinline__ int wr_seg_count(int T) {
+  constexpr int SPAN = 32 * NPL;
+  int n = 1, ob = SPAN >= T ? T : ((SPAN - kWrHalo) & ~31);
+  while (ob < T) {
+    const int s0 = (ob - kWrHalo) & ~31;
+    ob = s0 + SPAN >= T ? T : ((s0 + SPAN - kWrHalo) & ~31);
+    ++n;
+  }
+  return n;
+}
+
+// Time pass of segment sg of one row by one warp.  Writes the flag words of
+// the segment's interior to M_out (the row's words) and returns, in every
+// lane, the interior's number of flagged samples and sum of unflagged powers.
+template <int DT, int NPL>
+__device__ void wr_segment(const uint8_t* grow, int T, int sg, bool vin, int kmax,
+                           const uint32_t* s_Kp, uint32_t* M_out,
+                           int& n_flag, unsigned long long& sum_unflagged) {
+  constexpr int NW = NPL / 32, SPAN = 32 * NPL;
+  const int lane = threadIdx.x & 31;
+  int s0, oa, ob;
+  wr_seg_bounds<NPL>(T, sg, s0, oa, ob);
+  const int vend = min(T, s0 + SPAN);
+  const int xl = s0 + lane * NPL;
+  WrRow<NPL> R;
+  wr_build<DT, NPL>(R, grow, xl, T, vin, s_Kp[0]);
+#pragma unroll 1
+  for (int k = 1; k <= kmax; ++k) {
+    const int I = 1 << k;
+    const uint32_t* Kp = s_Kp + koffset(k);
+    uint32_t F[NW];
+    switch (k) {
+      case 1: wr_fire<NPL, 2>(R, lane, Kp, F); break;
+      case 2: wr_fire<NPL, 4>(R, lane, Kp, F); break;
+      case 3: wr_fire<NPL, 8>(R, lane, Kp, F); break;
+      case 4: wr_fire<NPL, 16>(R, lane, Kp, F); break;
+      case 5: wr_fire<NPL, 32>(R, lane, Kp, F); break;
+      default: wr_fire<NPL, 64>(R, lane, Kp, F); break;
+    }
+    wr_apply<NPL>(R, lane, vend - I + 1 - xl, I, F);
+  }
+  // interior words [oa, ob): flag words, counts and sums of unflagged powers
+  int nfl = 0;
+  unsigned long long su = 0;
+#pragma unroll
+  for (int w = 0; w < NW; ++w) {
+    const int x = xl + 32 * w;
+    if (x >= oa && x < ob) {
+      M_out[x >> 5] = R.M[w];
+      nfl += __popc(R.M[w]);
+      uint32_t s = 0u;  // packed: n * Z + sum_unflagged, n < 2^6
+#pragma unroll
+      for (int b = 0; b < 32; ++b) s += R.u[32 * w + b];
+      su += s - static_cast<uint32_t>(__popc(R.M[w])) * kZ;
+    }
+  }
+  n_flag = __reduce_add_sync(kFull, nfl);
+  sum_unflagged = warp_sum64(su);
+}
+
+// Samples per lane of the warp-row pass (rows longer than 32 * kWrNpl are
+// cut into overlapping segments).
+constexpr int kWrNpl = 32;
+
 // ------------------------------------------------------------------ fine counts
 
 // Exact counts of the pooled values inside the refinement targets, for rows
@@ -1402,41 +1593,75 @@ __device__ void unit_round1(const KParams& kp, const DevUnit& u, UnitState* us, 
     __syncthreads();
     const int nspec_t = f.n_tgt;
     // the stats tasks histogrammed every row: take out the flagged ones
-    constexpr int VS = TR::kVec, SEG = 64 * VS;
+    // (warps over (flagged row, segment) pairs, loads one segment ahead)
+    constexpr int VS = TR::kVec, NQ = 4, SEG = 32 * NQ * VS;
     const int nseg = (T + SEG - 1) / SEG;
     const bool vin = (u.flags & kUnitInVec) != 0;
     const uint8_t* gin = static_cast<const uint8_t*>(u.in);
+    int* frows = reinterpret_cast<int*>(ws + 32 * 1024 + 256);  // [32.25K, 34K): up to 448 rows
+    uint32_t* moff = reinterpret_cast<uint32_t*>(ws + 12 * 1024);  // [12K, 16.2K): key -> offset
+    for (int i = tid; i < kCoarseBins; i += NT) moff[i] = kNoTarget;
+    __syncthreads();
+    if (tid < nspec_t) moff[coarse_key(f.tgt[tid].lo)] = f.tgt[tid].base - f.tgt[tid].lo;
+    const uint32_t nsc = nspec_t ? f.tgt[nspec_t - 1].base + (f.tgt[nspec_t - 1].hi - f.tgt[nspec_t - 1].lo) + 1u : 0u;
+    if (tid == 0) {
+      int nf = 0;
+      for (int c = 0; c < u.C; ++c)
+        if (Fc[c]) {
+          if (nf < 448) frows[nf] = c;
+          ++nf;
+        }
+      f.n_keep = nf;
+    }
+    __syncthreads();
+    const int nfr = f.n_keep;
     unsigned long long s1 = 0;
     unsigned __int128 s2 = 0;
-    for (int c = 0; c < u.C; ++c) {
-      if (!Fc[c]) continue;
-      const uint8_t* grow = gin + static_cast<int64_t>(c) * u.in_stride * TR::kBytes;
-      for (int sg = warp; sg < nseg; sg += NW) {
-        uint32_t v[2][VS];
-#pragma unroll
-        for (int q = 0; q < 2; ++q) {
-          const int x = sg * SEG + q * 32 * VS + lane * VS;
-          if (x < T) gload_vec<DT>(grow, x, T, vin, v[q]);
+    for (int fb = 0; fb < nfr; fb += 448) {
+      if (fb > 0) {
+        __syncthreads();
+        if (tid == 0) {
+          int nf = 0, seen = 0;
+          for (int c = 0; c < u.C && nf < 448; ++c)
+            if (Fc[c] && seen++ >= fb) frows[nf++] = c;
         }
+        __syncthreads();
+      }
+      const int nfb = min(448, nfr - fb);
+      const int nsegs = nfb * nseg;
+      uint4 cur[NQ], nxt[NQ];
+      auto load_seg = [&](int task, uint4 (&v)[NQ]) {
+        const int i = task / nseg, s = task - i * nseg;
+        const uint8_t* grow = gin + static_cast<int64_t>(frows[min(i, nfb - 1)]) * u.in_stride * TR::kBytes;
 #pragma unroll
-        for (int q = 0; q < 2; ++q) {
-          const int x = sg * SEG + q * 32 * VS + lane * VS;
-          if (x >= T) continue;
+        for (int q = 0; q < NQ; ++q) {
+          const int x = s * SEG + q * 32 * VS + lane * VS;
+          v[q] = (task < nsegs && x < T) ? gload_raw<DT>(grow, x, T, vin) : make_uint4(0u, 0u, 0u, 0u);
+        }
+      };
+      load_seg(warp, cur);
+      for (int task = warp; task < nsegs; task += NW) {
+        load_seg(task + NW, nxt);
+        const int s = task % nseg;
+#pragma unroll
+        for (int q = 0; q < NQ; ++q) {
+          const int x = s * SEG + q * 32 * VS + lane * VS;
 #pragma unroll
           for (int j = 0; j < VS; ++j) {
             if (x + j >= T) continue;
-            const uint32_t val = v[q][j];
+            const uint32_t val = raw_pw<DT>(cur[q], j);
             const uint32_t key = coarse_key(val);
             atomicSub(&uh[key], 1u);
-            for (int t = 0; t < nspec_t; ++t)
-              if (val >= f.tgt[t].lo && val <= f.tgt[t].hi)
-                atomicSub(&sp[f.tgt[t].base + (val - f.tgt[t].lo)], 1u);
+            const uint32_t si = val + moff[key];
+            if (si < nsc) atomicSub(&sp[si], 1u);
             if (kp.sigma_std) {
               s1 += val;
               s2 += static_cast<unsigned long long>(val) * val;
             }
           }
         }
+#pragma unroll
+        for (int q = 0; q < NQ; ++q) cur[q] = nxt[q];
       }
     }
     if (kp.sigma_std) {
@@ -1539,13 +1764,13 @@ template <int DT, int NT>
 __device__ void task_stats(const KParams& kp, const DevUnit& u, UnitState* us, const Task& tk,
                            uint8_t* ws, Fixed<NT>& f) {
   using TR = Traits<DT>;
-  constexpr int VS = TR::kVec, NQ = 32 / VS, SEG = 32 * NQ * VS, NW = NT / kWarp;
+  constexpr int VS = TR::kVec, NQ = 8, SEG = 32 * NQ * VS, NW = NT / kWarp;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int T = u.T, R = tk.nrows, row0 = tk.row0, nseg = (T + SEG - 1) / SEG;
   const bool vin = (u.flags & kUnitInVec) != 0;
   const uint8_t* gin = static_cast<const uint8_t*>(u.in);
   uint32_t* hist = reinterpret_cast<uint32_t*>(ws);
-  uint8_t* map = ws + 4 * kCoarseBins;                                   // [4224, 5280)
+  uint32_t* moff = reinterpret_cast<uint32_t*>(ws + 10 * 1024);         // [10K, 14.2K)
   uint32_t* spec = reinterpret_cast<uint32_t*>(ws + 6 * 1024);           // [6K, 10K)
   if (tid == 0) {
     f.n_tgt = 0;
@@ -1555,44 +1780,52 @@ __device__ void task_stats(const KParams& kp, const DevUnit& u, UnitState* us, c
   }
   for (int i = tid; i < kCoarseBins; i += NT) {
     hist[i] = 0u;
-    map[i] = 0xFFu;
+    moff[i] = kNoTarget;
   }
   for (int i = tid; i < kMaxSpec; i += NT) spec[i] = 0u;
   for (int r = tid; r < R; r += NT) f.rowS[r] = 0;
   __syncthreads();
   const int nspec_t = f.n_tgt;
-  if (tid < nspec_t) map[coarse_key(f.tgt[tid].lo)] = static_cast<uint8_t>(tid);
+  if (tid < nspec_t) moff[coarse_key(f.tgt[tid].lo)] = f.tgt[tid].base - f.tgt[tid].lo;
+  const uint32_t nsc = nspec_t ? f.tgt[nspec_t - 1].base + (f.tgt[nspec_t - 1].hi - f.tgt[nspec_t - 1].lo) + 1u : 0u;
   __syncthreads();
-  for (int task = warp; task < R * nseg; task += NW) {
+  // software-pipelined: the loads of a warp's next segment are in flight
+  // while it histograms the current one
+  const int nsegs = R * nseg;
+  uint4 cur[NQ], nxt[NQ];
+  auto load_seg = [&](int task, uint4 (&v)[NQ]) {
     const int r = task / nseg, s = task - r * nseg;
-    const uint8_t* grow = gin + static_cast<int64_t>(row0 + r) * u.in_stride * TR::kBytes;
-    uint32_t v[NQ][VS];
+    const uint8_t* grow = gin + static_cast<int64_t>(row0 + min(r, R - 1)) * u.in_stride * TR::kBytes;
 #pragma unroll
     for (int q = 0; q < NQ; ++q) {
       const int x = s * SEG + q * 32 * VS + lane * VS;
-      if (x < T) gload_vec<DT>(grow, x, T, vin, v[q]);
+      v[q] = (task < nsegs && x < T) ? gload_raw<DT>(grow, x, T, vin) : make_uint4(0u, 0u, 0u, 0u);
     }
+  };
+  load_seg(warp, cur);
+  for (int task = warp; task < nsegs; task += NW) {
+    load_seg(task + NW, nxt);
+    const int r = task / nseg, s = task - r * nseg;
     unsigned long long sum = 0;
 #pragma unroll
     for (int q = 0; q < NQ; ++q) {
       const int x = s * SEG + q * 32 * VS + lane * VS;
-      if (x < T) {
 #pragma unroll
-        for (int j = 0; j < VS; ++j) {
-          if (x + j < T) {
-            sum += v[q][j];
-            const uint32_t key = coarse_key(v[q][j]);
-            atomicAdd(&hist[key], 1u);
-            if (nspec_t) {
-              const int t = map[key];
-              if (t != 0xFF) atomicAdd(&spec[f.tgt[t].base + (v[q][j] - f.tgt[t].lo)], 1u);
-            }
-          }
+      for (int j = 0; j < VS; ++j) {
+        if (x + j < T) {
+          const uint32_t val = raw_pw<DT>(cur[q], j);
+          sum += val;
+          const uint32_t key = coarse_key(val);
+          atomicAdd(&hist[key], 1u);
+          const uint32_t si = val + moff[key];  // spec index, or >= nsc off the targets
+          if (si < nsc) atomicAdd(&spec[si], 1u);
         }
       }
     }
     sum = warp_sum64(sum);
     if (lane == 0) atomicAdd(&f.rowS[r], sum);
+#pragma unroll
+    for (int q = 0; q < NQ; ++q) cur[q] = nxt[q];
   }
   if (kp.sigma_std) {
     // exact 128-bit moments for the std estimator, in a pass of their own
@@ -1687,8 +1920,7 @@ __device__ void task_fine(const KParams& kp, const DevUnit& u, UnitState* us, co
 // test (Section 4.1), the mask and the masked data.
 template <int DT, int NT>
 __device__ void task_flag(const KParams& kp, const DevUnit& u, UnitState* us, const Task& tk,
-                          uint8_t* ws, Fixed<NT>& f, uint32_t* s_K0, uint32_t* s_cq, uint32_t* s_Kp,
-                          int* s_dirty) {
+                          uint8_t* ws, Fixed<NT>& f, uint32_t* s_Kp) {
   using TR = Traits<DT>;
   constexpr int VS = TR::kVec, SEG = 64 * VS, NW = NT / kWarp;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
@@ -1697,8 +1929,11 @@ __device__ void task_flag(const KParams& kp, const DevUnit& u, UnitState* us, co
   const int MW = nch + 4;  // flag words per row, two zero words on each side
   const int nseg = (T + SEG - 1) / SEG;
   const StLayout L = st_layout(nch);
+  // shared workspace: Rb rows of prefix (general path), the flag words of
+  // the task's R rows, Rb rows of fire words
+  const int Rb = max(1, min(R, (kp.dyn_smem / 4 - R * MW) / (L.per_row + MW)));
   uint32_t* const spfx = reinterpret_cast<uint32_t*>(ws);
-  uint32_t* const smbits = spfx + R * L.per_row;
+  uint32_t* const smbits = spfx + Rb * L.per_row;
   uint32_t* const sfbits = smbits + R * MW;
   const uint8_t* gin = static_cast<const uint8_t*>(u.in);
   if (tid == 0) {
@@ -1736,16 +1971,10 @@ __device__ void task_flag(const KParams& kp, const DevUnit& u, UnitState* us, co
     for (int e = tid; e < total; e += NT) {
       int k = 0;
       while (koffset(k + 1) <= e) ++k;
-      const int I = 1 << k, n = e - koffset(k);
+      const int n = e - koffset(k);
       const long long* Kt = f.K + koffset(k);
       if (Kt[n] < 0 || Kt[n] >= static_cast<long long>(kZ)) bad = true;
       s_Kp[e] = static_cast<uint32_t>(n) * kZ + static_cast<uint32_t>(Kt[n]);
-      if (n == 0) {
-        s_K0[k] = static_cast<uint32_t>(Kt[0]);
-        // tau = floor(threshold_I) + 3 >= threshold_I + 2; floor(threshold_I) = K[I - 1]
-        const uint32_t tau = static_cast<uint32_t>(k == 0 ? Kt[0] : Kt[I - 1]) + 3u;
-        s_cq[k] = tau - kZ;
-      }
     }
   }
   bad = __syncthreads_or(bad);
@@ -1753,131 +1982,91 @@ __device__ void task_flag(const KParams& kp, const DevUnit& u, UnitState* us, co
   __syncthreads();
   const int nkeep = f.n_keep;
 
-  // ---- time pass over all kept rows of the task at once
+  // ---- time pass over the kept rows of the task
   if (f.time_on && nkeep > 0) {
-    const bool packed = f.state == 1;
-    const int* rows = f.keep;
-    const int nbb = nkeep;
-    st_build<DT, NT>(u, row0, T, nch, rows, nbb, spfx, L, smbits, MW, packed,
-                     packed ? s_K0[0] : 0u);
-    for (int i = tid; i < nbb * MW; i += NT) sfbits[i] = 0u;
-    if (tid < nbb) s_dirty[tid] = 0;
-    __syncthreads();
-    st_bases<NT>(spfx, L, nch, nbb, nullptr);
-    __syncthreads();
-    for (int k = packed ? 1 : 0; k <= f.kmax_t; ++k) {
-      const int I = 1 << k;
-      const long long* Kt = f.K + koffset(k);
-      const uint32_t K0 = packed ? s_K0[k] : 0u, cq = packed ? s_cq[k] : 0u;
-      const uint32_t* Kp = s_Kp + koffset(k);
-      for (int c = tid; c < nbb * nch; c += NT) {
-        const int rb = c / nch, w = c - rb * nch, t0 = w << 5;
-        uint32_t* F = sfbits + rb * MW + 2;
-        const int nvalid = T - I + 1 - t0;
-        if (nvalid <= 0) {
-          F[w] = 0u;
-          continue;
-        }
-        const uint32_t vm = nvalid >= 32 ? 0xFFFFFFFFu : ((1u << nvalid) - 1u);
-        const uint32_t* pl = spfx + rb * L.per_row;
-        const uint32_t* pb = pl + L.PLW;
-        uint32_t fire;
-        if (packed) {
-          switch (k) {
-            case 1: fire = packed_fire<2>(pl, pb, w, K0, cq, Kp); break;
-            case 2: fire = packed_fire<4>(pl, pb, w, K0, cq, Kp); break;
-            case 3: fire = packed_fire<8>(pl, pb, w, K0, cq, Kp); break;
-            case 4: fire = packed_fire<16>(pl, pb, w, K0, cq, Kp); break;
-            case 5: fire = packed_fire<32>(pl, pb, w, K0, cq, Kp); break;
-            default: fire = packed_fire<64>(pl, pb, w, K0, cq, Kp); break;
-          }
-        } else {
-          fire = general_fire(pl, pb, smbits + rows[rb] * MW + 2, t0, I, T, Kt);
-        }
-        F[w] = fire & vm;
-      }
-      __syncthreads();
-      // new flags: windows that fired flag all their samples (snapshot)
-      for (int c = tid; c < nbb * nch; c += NT) {
-        const int rb = c / nch, w = c - rb * nch;
-        const uint32_t* F = sfbits + rb * MW + 2;
-        const uint32_t f0 = F[w], f1 = F[w - 1], f2 = F[w - 2];
-        if ((f0 | f1 | f2) == 0u) continue;
-        const uint32_t D = (I <= 32) ? dilate32(f0, f1, I)
-                                     : (dilate32(f0, f1, 32) | dilate32(f1, f2, 32));
-        uint32_t* Mw = smbits + rows[rb] * MW + 2 + w;
-        const uint32_t nw = D & ~*Mw;
-        if (nw == 0u) continue;
-        *Mw |= nw;
-        if (packed) {
-          // store the newly flagged samples of this chunk as Z
-          uint32_t* pl = spfx + rb * L.per_row + pidx(w << 5);
-          uint32_t* tcw = spfx + rb * L.per_row + L.PLW + L.PBW + w;
-          uint32_t cur = pl[0], acc = 0;
-          for (int j = 0; j < 32; ++j) {
-            const uint32_t nx = (j < 31) ? pl[j + 1] : *tcw;
-            uint32_t uu = nx - cur;
-            cur = nx;
-            if ((nw >> j) & 1u) uu = kZ;
-            pl[j] = acc;
-            acc += uu;
-          }
-          *tcw = acc;
-          s_dirty[rb] = 1;
+    if (f.state == 1) {
+      // packed values: one warp per row segment, the segment in registers
+      const bool vin = (u.flags & kUnitInVec) != 0;
+      const int nsg = wr_seg_count<kWrNpl>(T);
+      for (int item = warp; item < nkeep * nsg; item += NW) {
+        const int kr = item / nsg, sg = item - kr * nsg;
+        const int r = f.keep[kr];
+        const uint8_t* grow = gin + static_cast<int64_t>(row0 + r) * u.in_stride * TR::kBytes;
+        int nfl = 0;
+        unsigned long long su = 0;
+        wr_segment<DT, kWrNpl>(grow, T, sg, vin, f.kmax_t, s_Kp, smbits + r * MW + 2, nfl,
+                               su);
+        if (lane == 0) {
+          atomicAdd(&f.rowNFlag[r], nfl);
+          atomicAdd(&f.rowFlagSum[r], 0ull - su);
         }
       }
       __syncthreads();
-      if (packed && k < f.kmax_t) {
-        st_bases<NT>(spfx, L, nch, nbb, s_dirty);
+      // rowS - rowFlagSum = sum_unflagged
+      for (int kr = tid; kr < nkeep; kr += NT) f.rowFlagSum[f.keep[kr]] += f.rowS[f.keep[kr]];
+      __syncthreads();
+    } else {
+      // any magnitudes: exact 64-bit window sums over a shared-memory prefix,
+      // Rb rows at a time
+      for (int kb = 0; kb < nkeep; kb += Rb) {
+        const int* rows = f.keep + kb;
+        const int nbb = min(Rb, nkeep - kb);
+        st_build<DT, NT>(u, row0, T, nch, rows, nbb, spfx, L, smbits, MW, false, 0u);
+        for (int i = tid; i < nbb * MW; i += NT) sfbits[i] = 0u;
+        __syncthreads();
+        st_bases<NT>(spfx, L, nch, nbb, nullptr);
+        __syncthreads();
+        for (int k = 0; k <= f.kmax_t; ++k) {
+          const int I = 1 << k;
+          const long long* Kt = f.K + koffset(k);
+          for (int c = tid; c < nbb * nch; c += NT) {
+            const int rb = c / nch, w = c - rb * nch, t0 = w << 5;
+            uint32_t* F = sfbits + rb * MW + 2;
+            const int nvalid = T - I + 1 - t0;
+            if (nvalid <= 0) {
+              F[w] = 0u;
+              continue;
+            }
+            const uint32_t vm = nvalid >= 32 ? 0xFFFFFFFFu : ((1u << nvalid) - 1u);
+            const uint32_t* pl = spfx + rb * L.per_row;
+            const uint32_t* pb = pl + L.PLW;
+            F[w] = general_fire(pl, pb, smbits + rows[rb] * MW + 2, t0, I, T, Kt) & vm;
+          }
+          __syncthreads();
+          // new flags: windows that fired flag all their samples (snapshot)
+          for (int c = tid; c < nbb * nch; c += NT) {
+            const int rb = c / nch, w = c - rb * nch;
+            const uint32_t* F = sfbits + rb * MW + 2;
+            const uint32_t f0 = F[w], f1 = F[w - 1], f2 = F[w - 2];
+            if ((f0 | f1 | f2) == 0u) continue;
+            const uint32_t D = (I <= 32) ? dilate32(f0, f1, I)
+                                         : (dilate32(f0, f1, 32) | dilate32(f1, f2, 32));
+            smbits[rows[rb] * MW + 2 + w] |= D;
+          }
+          __syncthreads();
+        }
+        // flagged counts and flagged powers of the batch's rows (re-read)
+        for (int c = tid; c < nbb * nch; c += NT) {
+          const int kr = c / nch, w = c - kr * nch;
+          const int r = rows[kr];
+          uint32_t m = smbits[r * MW + 2 + w];
+          if (m) {
+            const uint8_t* grow = gin + static_cast<int64_t>(row0 + r) * u.in_stride * TR::kBytes;
+            unsigned long long fs = 0;
+            const int cnt = __popc(m);
+            while (m) {
+              const int j = __ffs(m) - 1;
+              m &= m - 1u;
+              fs += TR::at(grow, (w << 5) + j);
+            }
+            atomicAdd(&f.rowNFlag[r], cnt);
+            atomicAdd(&f.rowFlagSum[r], fs);
+          }
+        }
         __syncthreads();
       }
     }
-    // flagged counts and flagged power of every kept row.  Packed rows: the
-    // chunk totals hold sum_unflagged + n_flagged * Z (mod 2^32), exact when
-    // T * floor(threshold_1) < 2^32; otherwise the flagged powers are re-read.
-    const bool from_prefix =
-        packed && static_cast<unsigned long long>(T) * s_K0[0] < (1ull << 32);
-    if (from_prefix) {
-      for (int rb = warp; rb < nbb; rb += NW) {
-        const int r = rows[rb];
-        const uint32_t* tc = spfx + rb * L.per_row + L.PLW + L.PBW;
-        const uint32_t* M = smbits + r * MW + 2;
-        uint32_t tot = 0;
-        int nfl = 0;
-        for (int c = lane; c < nch; c += kWarp) {
-          tot += tc[c];
-          nfl += __popc(M[c]);
-        }
-        tot = warp_sum32(tot);
-        nfl = __reduce_add_sync(0xFFFFFFFFu, nfl);
-        if (lane == 0) {
-          const uint32_t su = tot - static_cast<uint32_t>(nfl) * kZ;
-          f.rowNFlag[r] = nfl;
-          f.rowFlagSum[r] = f.rowS[r] - su;  // so that rowS - rowFlagSum = sum_unflagged
-        }
-      }
-      __syncthreads();
-    }
-    for (int c = tid; c < (from_prefix ? 0 : nkeep * nch); c += NT) {
-      const int kr = c / nch, w = c - kr * nch;
-      const int r = f.keep[kr];
-      uint32_t m = smbits[r * MW + 2 + w];
-      if (m) {
-        const uint8_t* grow = gin + static_cast<int64_t>(row0 + r) * u.in_stride * TR::kBytes;
-        unsigned long long fs = 0;
-        const int cnt = __popc(m);
-        while (m) {
-          const int j = __ffs(m) - 1;
-          m &= m - 1u;
-          fs += TR::at(grow, (w << 5) + j);
-        }
-        atomicAdd(&f.rowNFlag[r], cnt);
-        atomicAdd(&f.rowFlagSum[r], fs);
-      }
-    }
-    __syncthreads();
   }
-
   // ---- history flagger (Section 4.1) and per-row counts
   for (int r = tid; r < R; r += NT) {
     const long long h = u.hist_slot >= 0 ? u.hist_slot + row0 + r : -1;
@@ -2066,12 +2255,10 @@ __device__ int sched_next(const KParams& kp, Fixed<NT>& f) {
 // been handed out.
 
 template <int DT, int NT>
-__global__ void __launch_bounds__(NT, 512 / NT) lof_block_kernel(const KParams kp) {
+__global__ void __launch_bounds__(NT, NT == 128 ? 4 : 2) lof_block_kernel(const KParams kp) {
   extern __shared__ __align__(128) uint8_t smem[];
   __shared__ Fixed<NT> f;
-  __shared__ uint32_t s_K0[kMaxLogWindow + 1], s_cq[kMaxLogWindow + 1];
   __shared__ uint32_t s_Kp[kKTable];
-  __shared__ int s_dirty[kMaxRowsPerTask];
   const int tid = threadIdx.x;
   if (tid == 0) {
     f.q_done = 0;
@@ -2091,11 +2278,46 @@ __global__ void __launch_bounds__(NT, 512 / NT) lof_block_kernel(const KParams k
     UnitState* const us = kp.ustate + tk.unit;
     if (tk.kind == kTaskStats) task_stats<DT, NT>(kp, u, us, tk, smem, f);
     else if (tk.kind == kTaskFine) task_fine<DT, NT>(kp, u, us, tk, smem, f);
-    else task_flag<DT, NT>(kp, u, us, tk, smem, f, s_K0, s_cq, s_Kp, s_dirty);
+    else task_flag<DT, NT>(kp, u, us, tk, smem, f, s_Kp);
     __syncthreads();
     if (!f.ok) break;
   }
 }
+
+template <int DT, int NT>
+void* kernel_ptr() {
+  return reinterpret_cast<void*>(&lof_block_kernel<DT, NT>);
+}
+
+}  // namespace
+}  // namespace lofk
+
+// This file is compiled once per input type (LOF_KERNEL_DT = LOF_CI16 or
+// LOF_CI8) so that the two instantiations build in parallel; the CI16 object
+// also holds the history commit kernel and the launchers.
+#if !defined(LOF_KERNEL_DT) || (LOF_KERNEL_DT != 1 && LOF_KERNEL_DT != 2)
+#error "compile with -DLOF_KERNEL_DT=2 (ci16) or -DLOF_KERNEL_DT=1 (ci8)"
+#endif
+
+#if LOF_KERNEL_DT == 2  // LOF_CI16
+extern "C" void* lofk_block_kernel_ci16(int threads) {
+  if (threads == 128) return lofk::kernel_ptr<LOF_CI16, 128>();
+  if (threads == 256) return lofk::kernel_ptr<LOF_CI16, 256>();
+  return nullptr;
+}
+#else  // LOF_CI8
+extern "C" void* lofk_block_kernel_ci8(int threads) {
+  if (threads == 128) return lofk::kernel_ptr<LOF_CI8, 128>();
+  if (threads == 256) return lofk::kernel_ptr<LOF_CI8, 256>();
+  return nullptr;
+}
+#endif
+
+#if LOF_KERNEL_DT == 2
+extern "C" void* lofk_block_kernel_ci8(int threads);
+
+namespace lofk {
+namespace {
 
 // ------------------------------------------------------------------ history commit
 // Section 4.1: add each staged value to its channel's ring and refresh the
@@ -2143,19 +2365,9 @@ __global__ void lof_commit_kernel(const CommitParams cp, int total, int refresh_
   H.thr[h] = __dadd_rn(mu, __dmul_rn(cp.history_k, sd));
 }
 
-template <int DT, int NT>
-void* kernel_ptr() {
-  return reinterpret_cast<void*>(&lof_block_kernel<DT, NT>);
-}
-
 void* pick_kernel(int dtype, int threads) {
-  if (dtype == LOF_CI16) {
-    if (threads == 256) return kernel_ptr<LOF_CI16, 256>();
-    if (threads == 512) return kernel_ptr<LOF_CI16, 512>();
-  } else if (dtype == LOF_CI8) {
-    if (threads == 256) return kernel_ptr<LOF_CI8, 256>();
-    if (threads == 512) return kernel_ptr<LOF_CI8, 512>();
-  }
+  if (dtype == LOF_CI16) return lofk_block_kernel_ci16(threads);
+  if (dtype == LOF_CI8) return lofk_block_kernel_ci8(threads);
   return nullptr;
 }
 
@@ -2165,7 +2377,7 @@ void* pick_kernel(int dtype, int threads) {
 using namespace lofk;
 
 extern "C" int lofk_set_smem_limit(int dtype, int smem_bytes) {
-  for (int t : {256, 512}) {
+  for (int t : {128, 256}) {
     void* k = pick_kernel(dtype, t);
     if (!k) return -1;
     if (cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_bytes) !=
@@ -2224,3 +2436,4 @@ extern "C" int lofk_launch_refresh(const CommitParams* cp, int total_channels, v
   const cudaError_t e = cudaGetLastError();
   return e == cudaSuccess ? 0 : static_cast<int>(e);
 }
+#endif  // LOF_KERNEL_DT == 2
