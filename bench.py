@@ -36,6 +36,40 @@ BYTES_PER_SAMPLE = 4 + 4 + 1          # ci16 in + ci16 out + uint8 mask
 METRIC = "input Msamples/s (full LOFAR pre-beamformer block, 768 units x 256 ch x 3072 t, ci16)"
 
 
+PROFILE = os.path.join(ROOT, "profiles", "lof_block_kernel_ci16_full_station.md")
+
+
+def measured_traffic(n_units):
+    """DRAM bytes per launch of the block kernel from the committed ncu summary
+    (read + write bytes per unit x units), or None when the kernel sources have
+    changed since the counters were taken."""
+    import hashlib
+    try:
+        text = open(PROFILE).read()
+    except OSError:
+        return None
+    kv = {}
+    inside = False
+    for line in text.splitlines():
+        if line.startswith("```counters"):
+            inside = True
+        elif line.startswith("```"):
+            inside = False
+        elif inside and ":" in line:
+            k, v = line.split(":", 1)
+            kv[k.strip()] = v.strip()
+    csrc = os.path.join(ROOT, "paper_1701_08197_gb300", "csrc")
+    for f, key in (("lof_kernels.cu", "kernel_sha256_lof_kernels_cu"),
+                   ("lof_internal.h", "kernel_sha256_lof_internal_h")):
+        h = hashlib.sha256(open(os.path.join(csrc, f), "rb").read()).hexdigest()
+        if kv.get(key) != h:
+            return None
+    try:
+        return int(kv["traffic_bytes_per_unit"]) * n_units
+    except (KeyError, ValueError):
+        return None
+
+
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -370,7 +404,7 @@ def main():
                    "l2": "inputs > L2 (2.4 GB at 48 stations), no flush",
                    "per_rank_units": args.stations * 16},
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                     "frac": achieved / peak, "traffic": None,
+                     "frac": achieved / peak, "traffic": measured_traffic(args.stations * 16),
                      "kernel": "lof_block_kernel<CI16>", "bytes_per_launch": alg_bytes,
                      "kernel_ms": kern_avg, "peak_kind": peak_kind},
         "latency_ms": {"batched_p50": pct(step_sorted, 0.5), "batched_p99": pct(step_sorted, 0.99),

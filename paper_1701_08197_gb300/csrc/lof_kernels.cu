@@ -1181,12 +1181,41 @@ __device__ void st_build(const DevUnit& u, int row0, int T, int nch, const int* 
   }
 }
 
+// L2 eviction policies: the input of a unit is read by its statistics
+// tasks and again by its flag tasks shortly after, so those reads mark it
+// evict_last; the last read (the output copy) marks it evict_first.
+__device__ __forceinline__ uint64_t l2_policy_keep() {
+  uint64_t p;
+  asm volatile("createpolicy.fractional.L2::evict_last.b64 %0, 1.0;" : "=l"(p));
+  return p;
+}
+__device__ __forceinline__ uint64_t l2_policy_drop() {
+  uint64_t p;
+  asm volatile("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(p));
+  return p;
+}
+__device__ __forceinline__ uint4 ldg_policy(const void* ptr, uint64_t pol) {
+  uint4 v;
+  asm("ld.global.nc.L2::cache_hint.v4.u32 {%0, %1, %2, %3}, [%4], %5;"
+      : "=r"(v.x), "=r"(v.y), "=r"(v.z), "=r"(v.w)
+      : "l"(ptr), "l"(pol));
+  return v;
+}
+// Streaming (evict-first) stores of the mask bytes.
+__device__ __forceinline__ void st_stream_u32(void* p, uint32_t v) {
+  asm volatile("st.global.cs.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+__device__ __forceinline__ void st_stream_u64(void* p, uint32_t lo, uint32_t hi) {
+  asm volatile("st.global.cs.v2.u32 [%0], {%1, %2};" ::"l"(p), "r"(lo), "r"(hi) : "memory");
+}
+
 // Raw 16-byte vector of samples [x, x + kVec) of a row, zero at or past T.
 template <int DT>
-__device__ __forceinline__ uint4 gload_raw(const uint8_t* grow, int x, int T, bool vec) {
+__device__ __forceinline__ uint4 gload_raw(const uint8_t* grow, int x, int T, bool vec,
+                                           uint64_t pol) {
   using TR = Traits<DT>;
   if (vec && x + TR::kVec <= T)
-    return __ldg(reinterpret_cast<const uint4*>(grow + static_cast<size_t>(x) * TR::kBytes));
+    return ldg_policy(grow + static_cast<size_t>(x) * TR::kBytes, pol);
   uint32_t w[4] = {0u, 0u, 0u, 0u};
   for (int j = 0; j < TR::kVec && x + j < T; ++j) {
     if constexpr (DT == LOF_CI16) {
@@ -1337,12 +1366,13 @@ __device__ __forceinline__ void wr_apply(WrRow<NPL>& R, int lane, int nvalid, in
 template <int DT, int NPL>
 __device__ __forceinline__ void wr_build(WrRow<NPL>& R, const uint8_t* grow, int xl, int T,
                                          bool vin, uint32_t K1) {
+  const uint64_t pol = l2_policy_keep();
   constexpr int VS = Traits<DT>::kVec, NV = NPL / VS;
   uint4 v[NV];
 #pragma unroll
   for (int q = 0; q < NV; ++q) {
     const int x = xl + q * VS;
-    v[q] = x < T ? gload_raw<DT>(grow, x, T, vin) : make_uint4(0u, 0u, 0u, 0u);
+    v[q] = x < T ? gload_raw<DT>(grow, x, T, vin, pol) : make_uint4(0u, 0u, 0u, 0u);
   }
 #pragma unroll
   for (int w = 0; w < NPL / 32; ++w) R.M[w] = 0u;
@@ -1629,6 +1659,7 @@ __device__ void unit_round1(const KParams& kp, const DevUnit& u, UnitState* us, 
       }
       const int nfb = min(448, nfr - fb);
       const int nsegs = nfb * nseg;
+      const uint64_t pol = l2_policy_drop();
       uint4 cur[NQ], nxt[NQ];
       auto load_seg = [&](int task, uint4 (&v)[NQ]) {
         const int i = task / nseg, s = task - i * nseg;
@@ -1636,7 +1667,7 @@ __device__ void unit_round1(const KParams& kp, const DevUnit& u, UnitState* us, 
 #pragma unroll
         for (int q = 0; q < NQ; ++q) {
           const int x = s * SEG + q * 32 * VS + lane * VS;
-          v[q] = (task < nsegs && x < T) ? gload_raw<DT>(grow, x, T, vin) : make_uint4(0u, 0u, 0u, 0u);
+          v[q] = (task < nsegs && x < T) ? gload_raw<DT>(grow, x, T, vin, pol) : make_uint4(0u, 0u, 0u, 0u);
         }
       };
       load_seg(warp, cur);
@@ -1792,6 +1823,7 @@ __device__ void task_stats(const KParams& kp, const DevUnit& u, UnitState* us, c
   // software-pipelined: the loads of a warp's next segment are in flight
   // while it histograms the current one
   const int nsegs = R * nseg;
+  const uint64_t pol = l2_policy_keep();
   uint4 cur[NQ], nxt[NQ];
   auto load_seg = [&](int task, uint4 (&v)[NQ]) {
     const int r = task / nseg, s = task - r * nseg;
@@ -1799,7 +1831,7 @@ __device__ void task_stats(const KParams& kp, const DevUnit& u, UnitState* us, c
 #pragma unroll
     for (int q = 0; q < NQ; ++q) {
       const int x = s * SEG + q * 32 * VS + lane * VS;
-      v[q] = (task < nsegs && x < T) ? gload_raw<DT>(grow, x, T, vin) : make_uint4(0u, 0u, 0u, 0u);
+      v[q] = (task < nsegs && x < T) ? gload_raw<DT>(grow, x, T, vin, pol) : make_uint4(0u, 0u, 0u, 0u);
     }
   };
   load_seg(warp, cur);
@@ -2118,6 +2150,7 @@ __device__ void task_flag(const KParams& kp, const DevUnit& u, UnitState* us, co
     constexpr uint32_t kVm = (1u << VS) - 1u;
     constexpr int NQO = 16 / VS, SEGO = 32 * NQO * VS;
     const int nsego = (T + SEGO - 1) / SEGO;
+    const uint64_t pol_drop = l2_policy_drop();
     for (int task = warp; task < R * nsego; task += NW) {
       const int r = task / nsego, s = task - r * nsego;
       const bool full = f.rowFc[r] || f.rowFh[r];
@@ -2129,8 +2162,8 @@ __device__ void task_flag(const KParams& kp, const DevUnit& u, UnitState* us, co
         for (int q = 0; q < NQO; ++q) {
           const int x = s * SEGO + q * 32 * VS + lane * VS;
           if (x + VS <= T)
-            win[q] = __ldg(reinterpret_cast<const uint4*>(gin + grow_idx * u.in_stride * TR::kBytes +
-                                                          static_cast<size_t>(x) * TR::kBytes));
+            win[q] = ldg_policy(gin + grow_idx * u.in_stride * TR::kBytes +
+                                    static_cast<size_t>(x) * TR::kBytes, pol_drop);
         }
       }
 #pragma unroll
@@ -2144,11 +2177,11 @@ __device__ void task_flag(const KParams& kp, const DevUnit& u, UnitState* us, co
           uint8_t* mrow = u.mask + grow_idx * u.mask_stride;
           if (mask_vec && nv == VS) {
             if constexpr (VS == 4) {
-              *reinterpret_cast<uint32_t*>(mrow + x) = (bits * 0x00204081u) & 0x01010101u;
+              st_stream_u32(mrow + x, (bits * 0x00204081u) & 0x01010101u);
             } else {
               const uint32_t lo = ((bits & 0xFu) * 0x00204081u) & 0x01010101u;
               const uint32_t hi = (((bits >> 4) & 0xFu) * 0x00204081u) & 0x01010101u;
-              *reinterpret_cast<uint2*>(mrow + x) = make_uint2(lo, hi);
+              st_stream_u64(mrow + x, lo, hi);
             }
           } else {
             for (int j = 0; j < nv; ++j) mrow[x + j] = static_cast<uint8_t>((bits >> j) & 1u);
