@@ -67,7 +67,12 @@ enum {
 };
 
 /* Sample types.  CI8 / CI16: complex voltages, interleaved (re, im) int8 or
- * int16 pairs, one element = one complex sample.  F32: Stokes I power. */
+ * int16 pairs, one element = one complex sample; results are exact (integer
+ * window sums against an integer threshold table).  F32: Stokes I power
+ * (Section 4: the power is given); non-finite samples are flagged on entry.
+ * F32 statistics agree with binary64 within 1e-6 relative and window sums
+ * are float32 trees of at most 64 terms, so a flag can differ from binary64
+ * arithmetic only where a window sum lies within ~1e-6 of its threshold. */
 enum { LOF_CI8 = 1, LOF_CI16 = 2, LOF_F32 = 3 };
 
 enum { LOF_SIGMA_MAD = 0, LOF_SIGMA_STD = 1 };

@@ -375,6 +375,15 @@ namespace lofk {
 
 int host_count_tasks(const HostCfg& h, int dtype, const lof_unit* units, int n_units,
                      int* n_tasks, char* why, int nwhy) {
+  if (dtype == LOF_F32) {  // one CTA per unit, no task queue
+    for (int i = 0; i < n_units; ++i)
+      if (lofk_f32_smem(units[i].n_time) > h.smem_optin) {
+        snprintf(why, nwhy, "n_time %d does not fit the shared-memory budget", units[i].n_time);
+        return LOF_ERR_INVALID;
+      }
+    *n_tasks = 0;
+    return LOF_OK;
+  }
   int budget = dyn_budget(h, dtype, h.tuning.threads, h.tuning.ctas_per_sm);
   if (h.tuning.tile_bytes) budget = std::min(budget, h.tuning.tile_bytes);
   int64_t n = 0;
@@ -396,8 +405,47 @@ int host_count_tasks(const HostCfg& h, int dtype, const lof_unit* units, int n_u
   return LOF_OK;
 }
 
+// Unit descriptors of a float32 block (one CTA per unit, no tasks).
+int host_prepare_f32(const HostCfg& h, const lof_unit* units, int n_units, DevUnit* du, Prep* out) {
+  int maxT = 1;
+  int64_t chan = 0;
+  for (int i = 0; i < n_units; ++i) {
+    const lof_unit& u = units[i];
+    DevUnit& d = du[i];
+    d = DevUnit{};
+    d.in = u.in;
+    d.out = u.out;
+    d.mask = u.mask;
+    d.stats = u.stats;
+    d.in_stride = u.in_row_stride;
+    d.out_stride = u.out ? u.out_row_stride : 0;
+    d.mask_stride = u.mask ? u.mask_row_stride : 0;
+    d.hist_slot = u.history_slot;
+    d.C = u.n_chan;
+    d.T = u.n_time;
+    d.chan_off = static_cast<int32_t>(chan);
+    chan += u.n_chan;
+    int flags = 0;
+    if ((reinterpret_cast<uintptr_t>(u.in) % 16) == 0 && ((u.in_row_stride * 4) % 16) == 0)
+      flags |= kUnitInVec;
+    if (u.out && u.out == u.in) flags |= kUnitInPlace;
+    else if (u.out && (reinterpret_cast<uintptr_t>(u.out) % 16) == 0 && ((u.out_row_stride * 4) % 16) == 0)
+      flags |= kUnitOutVec;
+    if (u.mask && (reinterpret_cast<uintptr_t>(u.mask) % 16) == 0 && (u.mask_row_stride % 16) == 0)
+      flags |= kUnitMaskVec;
+    d.flags = flags;
+    maxT = std::max(maxT, u.n_time);
+  }
+  out->plan = Plan{256, 1, lofk_f32_smem(maxT)};
+  out->n_tasks = 0;
+  out->n_chan = chan;
+  out->grid = std::min(n_units, h.n_sm * 4);
+  return LOF_OK;
+}
+
 int host_prepare(const HostCfg& h, int dtype, const lof_unit* units, int n_units, DevUnit* du,
                  Task* tasks, int max_tasks, Prep* out, char* why, int nwhy) {
+  if (dtype == LOF_F32) return host_prepare_f32(h, units, n_units, du, out);
   const int es = esize_of(dtype);
   // plan over the distinct row lengths (bounded scan; units share few shapes)
   int Ts[64];
@@ -505,7 +553,13 @@ int host_launch(const lof_params& P, const HostCfg& h, int dtype, const Prep& pr
                 uint64_t seq, void* stream, char* why, int nwhy) {
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   cudaError_t e;
-  if ((e = cudaMemcpyAsync(sc.units, du_host, n_units * sizeof(DevUnit), cudaMemcpyHostToDevice, st)) !=
+  if (dtype == LOF_F32) {
+    if ((e = cudaMemcpyAsync(sc.units, du_host, n_units * sizeof(DevUnit), cudaMemcpyHostToDevice,
+                             st)) != cudaSuccess) {
+      snprintf(why, nwhy, "descriptor upload: %s", cudaGetErrorString(e));
+      return LOF_ERR_CUDA;
+    }
+  } else if ((e = cudaMemcpyAsync(sc.units, du_host, n_units * sizeof(DevUnit), cudaMemcpyHostToDevice, st)) !=
           cudaSuccess ||
       (e = cudaMemcpyAsync(sc.tasks, tasks_host, pr.n_tasks * sizeof(Task), cudaMemcpyHostToDevice,
                            st)) != cudaSuccess ||
@@ -548,7 +602,9 @@ int host_launch(const lof_params& P, const HostCfg& h, int dtype, const Prep& pr
   kp.block_seq = seq;
   kp.spin_limit = 2000000000ll;  // 2 s
   kp.dyn_smem = pr.plan.smem;
-  const int krc = lofk_launch_block(dtype, &kp, pr.grid, pr.plan.threads, pr.plan.smem, stream, 1);
+  const int krc = dtype == LOF_F32
+                      ? lofk_launch_f32(&kp, n_units, h.n_sm, pr.plan.smem, stream)
+                      : lofk_launch_block(dtype, &kp, pr.grid, pr.plan.threads, pr.plan.smem, stream, 1);
   if (krc != 0) {
     snprintf(why, nwhy, "kernel launch failed: %s (grid %d, %d threads, %d B)",
              cudaGetErrorString(static_cast<cudaError_t>(krc)), pr.grid, pr.plan.threads,
@@ -592,8 +648,6 @@ void host_set_error(const char* msg) {
 
 int host_check_dtype(int dtype, char* why, int nwhy) {
   if (esize_of(dtype) == 0) return snprintf(why, nwhy, "unknown dtype %d", dtype), LOF_ERR_INVALID;
-  if (dtype == LOF_F32)
-    return snprintf(why, nwhy, "LOF_F32 is not implemented in this build"), LOF_ERR_UNSUPPORTED;
   return LOF_OK;
 }
 
@@ -636,7 +690,8 @@ int flag_block_device(lof_ctx* c, int dtype, const lof_unit* units, int n_units,
   if (rc) return fail(c, rc, "lof_flag_block: %s", why);
   if ((rc = grow(c, &c->d_units, &c->cap_units, n_units, "units"))) return rc;
   if ((rc = grow(c, &c->d_tasks, &c->cap_tasks, pr.n_tasks, "tasks"))) return rc;
-  if ((rc = grow(c, &c->d_ustate, &c->cap_ustate, n_units, "unit state"))) return rc;
+  if ((rc = grow(c, &c->d_ustate, &c->cap_ustate, dtype == LOF_F32 ? 1 : n_units, "unit state")))
+    return rc;
   if ((rc = grow(c, &c->d_chanS, &c->cap_chan, static_cast<size_t>(pr.n_chan), "spectrum"))) return rc;
   if ((rc = grow(c, &c->d_chanFc, &c->cap_chanfc, static_cast<size_t>(pr.n_chan), "channel flags")))
     return rc;

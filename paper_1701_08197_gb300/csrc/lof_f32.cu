@@ -1,0 +1,707 @@
+// lof_f32.cu -- the flagger for float32 Stokes I units (power given).
+//
+// One CTA flags one unit at a time (units are independent; a launch takes a
+// whole block of units, grid-strided).  Steps, in the order of the paper's
+// Section 4 pipeline:
+//   a1  P = the input (non-finite samples count as flagged and are excluded)
+//   a2  row sums S[c] over the finite samples, binary64
+//   a3  median and 1.4826*MAD of S (bitonic sort in shared memory)
+//   a4  SumThreshold over S (Section 2.1), binary64 window sums in the order
+//       of the definition
+//   a5  median and MAD of the finite samples of the kept channels: exact
+//       order statistics by three radix-select passes over monotone 32-bit
+//       keys of the floats (two ranks at once for an even count); the MAD is
+//       taken over float32 keys of |x - median| (relative error <= 2^-24)
+//   a6  SumThreshold along time, one warp per 1024-sample row segment (rows
+//       longer than 1024 overlap by a 120-sample halo, as in the integer
+//       path): flagged samples are replaced by threshold_I and the window
+//       sums are built by doubling (S_2I(j) = S_I(j) + S_I(j + I)) in
+//       float32, so each sum is a balanced tree of at most 64 terms
+//       (relative error <= 6 * 2^-24); a window fires when its sum exceeds
+//       I * threshold_I
+//   a7  history test per channel (binary64 mean of the unflagged samples)
+//   a8  mask bytes and the masked data
+// Float results match the binary64 oracle except for samples whose deciding
+// window sum lies within a relative 1e-5 of its threshold (and the windows a
+// changed flag touches later).
+#include <cuda_runtime.h>
+
+#include <cstdint>
+
+#include "lof_internal.h"
+
+namespace lofk {
+namespace {
+
+constexpr unsigned kFullF = 0xFFFFFFFFu;
+constexpr int kHaloF = 120;   // sum over window sizes of (I - 1)
+constexpr int kNplF = 32;     // samples per lane in the time pass
+constexpr int kNtF = 256;     // threads per CTA
+constexpr int kNwF = kNtF / 32;
+
+// shared-memory layout of one CTA (bytes)
+constexpr int kOffS = 0;                                  // double S[2048]
+constexpr int kOffSrt = kOffS + 8 * kMaxChan;             // u64 sort keys [2048]
+constexpr int kOffFin = kOffSrt + 8 * kMaxChan;           // int finite count [2048]
+constexpr int kOffFc = kOffFin + 4 * kMaxChan;            // uint8 Fc [2048]
+constexpr int kOffFire = kOffFc + kMaxChan;               // uint8 fire [2048]
+constexpr int kOffHist = kOffFire + kMaxChan;             // u32 hist[2][2048]
+constexpr int kOffRows = kOffHist + 2 * 2048 * 4;         // per-warp flag words of one row
+constexpr int kFixedBytesF = kOffRows;
+
+struct F32Shared {
+  double median_f, sigma_f, median_t, sigma_t;
+  double tI[kMaxLogWindow + 1];   // threshold_I (time pass)
+  float limI[kMaxLogWindow + 1];  // I * threshold_I as float32
+  float tIf[kMaxLogWindow + 1];   // threshold_I as float32
+  long long n_pool;
+  unsigned long long cnt_time, cnt_total, cnt_hist;
+  uint32_t prefix[2];
+  long long rank[2];
+  int n_rank, kmax_t, time_on, nfc, ok;
+  double red[kNwF];
+};
+
+__device__ __forceinline__ double warp_sum_d(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(kFullF, v, o);
+  return v;
+}
+__device__ __forceinline__ long long warp_sum_ll(long long v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(kFullF, v, o);
+  return v;
+}
+__device__ __forceinline__ uint32_t fkey(float x) {  // monotone in x
+  const uint32_t u = __float_as_uint(x);
+  return (u & 0x80000000u) ? ~u : (u | 0x80000000u);
+}
+__device__ __forceinline__ float fkey_val(uint32_t k) {
+  return __uint_as_float((k & 0x80000000u) ? (k & 0x7FFFFFFFu) : ~k);
+}
+__device__ __forceinline__ unsigned long long dkey(double x) {  // monotone in x
+  const unsigned long long u = static_cast<unsigned long long>(__double_as_longlong(x));
+  return (u >> 63) ? ~u : (u | (1ull << 63));
+}
+__device__ __forceinline__ double dkey_val(unsigned long long k) {
+  return __longlong_as_double(static_cast<long long>((k >> 63) ? (k & ~(1ull << 63)) : ~k));
+}
+__device__ __forceinline__ uint32_t dilate32f(uint32_t hi, uint32_t lo, int I) {
+  unsigned long long x = (static_cast<unsigned long long>(hi) << 32) | lo;
+  for (int s = 1; s < I; s <<= 1) x |= x << s;
+  return static_cast<uint32_t>(x >> 32);
+}
+__device__ void set_error_f(const KParams& kp, int code, int info) {
+  if (atomicCAS(kp.err, 0, code) == 0) {
+    kp.err_info[0] = info;
+    kp.err_info[1] = static_cast<int>(kp.block_seq);
+  }
+}
+
+// threshold_I = median + sigma * factor_I * sensitivity (Section 2.1), binary64
+// in the order of the definition
+__device__ __forceinline__ double thr_of(const KParams& kp, double m, double s, int k) {
+  return __dadd_rn(m, __dmul_rn(__dmul_rn(s, kp.factor[k]), kp.sensitivity));
+}
+
+// 4 float samples of row r at x (x a multiple of 4); non-finite and past-T
+// samples come back as NaN.
+__device__ __forceinline__ float4 ld4(const float* row, int x, int T, bool vec) {
+  if (vec && x + 4 <= T) return __ldg(reinterpret_cast<const float4*>(row + x));
+  float a[4];
+#pragma unroll
+  for (int j = 0; j < 4; ++j) a[j] = x + j < T ? row[x + j] : __int_as_float(0x7FC00000);
+  return make_float4(a[0], a[1], a[2], a[3]);
+}
+__device__ __forceinline__ float f4at(const float4& v, int j) {
+  return j == 0 ? v.x : j == 1 ? v.y : j == 2 ? v.z : v.w;
+}
+
+// Bitonic sort of n (power of two) u64 keys, ascending.
+__device__ void sort64(unsigned long long* a, int n) {
+  for (int k = 2; k <= n; k <<= 1) {
+    for (int j = k >> 1; j > 0; j >>= 1) {
+      for (int i = threadIdx.x; i < n; i += kNtF) {
+        const int p = i ^ j;
+        if (p > i) {
+          const unsigned long long x = a[i], y = a[p];
+          if ((x > y) == ((i & k) == 0)) {
+            a[i] = y;
+            a[p] = x;
+          }
+        }
+      }
+      __syncthreads();
+    }
+  }
+}
+
+// Median and sigma of the C doubles in S (Section 4.2 statistics).
+__device__ void spectrum_stats(const KParams& kp, const double* S, int C, unsigned long long* srt,
+                               F32Shared& f) {
+  const int tid = threadIdx.x;
+  int n2 = 1;
+  while (n2 < C) n2 <<= 1;
+  for (int i = tid; i < n2; i += kNtF) srt[i] = i < C ? dkey(S[i]) : ~0ull;
+  __syncthreads();
+  sort64(srt, n2);
+  if (tid == 0) {
+    f.median_f = (C & 1) ? dkey_val(srt[C / 2])
+                         : __dmul_rn(__dadd_rn(dkey_val(srt[C / 2 - 1]), dkey_val(srt[C / 2])), 0.5);
+  }
+  __syncthreads();
+  const double m = f.median_f;
+  for (int i = tid; i < n2; i += kNtF) srt[i] = i < C ? dkey(fabs(__dsub_rn(S[i], m))) : ~0ull;
+  __syncthreads();
+  sort64(srt, n2);
+  if (tid == 0) {
+    const double mad = (C & 1) ? dkey_val(srt[C / 2])
+                               : __dmul_rn(__dadd_rn(dkey_val(srt[C / 2 - 1]), dkey_val(srt[C / 2])), 0.5);
+    double sig;
+    if (!kp.sigma_std && mad > 0.0) {
+      sig = __dmul_rn(1.482602218505602, mad);
+    } else {  // population stddev, two sequential passes
+      double s = 0.0;
+      for (int i = 0; i < C; ++i) s = __dadd_rn(s, S[i]);
+      const double mu = __ddiv_rn(s, static_cast<double>(C));
+      double q = 0.0;
+      for (int i = 0; i < C; ++i) {
+        const double d = __dsub_rn(S[i], mu);
+        q = __dadd_rn(q, __dmul_rn(d, d));
+      }
+      sig = __dsqrt_rn(__ddiv_rn(q, static_cast<double>(C)));
+    }
+    f.sigma_f = sig;
+  }
+  __syncthreads();
+}
+
+// Section 2.1 over the spectrum: binary64 window sums in index order.
+__device__ void spectrum_sum_threshold(const KParams& kp, const double* S, int C, uint8_t* Fc,
+                                       uint8_t* fire, const F32Shared& f) {
+  const int tid = threadIdx.x;
+  const double m = f.median_f, sig = f.sigma_f;
+  if (!kp.enable_freq || !(sig > 0.0)) return;
+  for (int k = 0; k <= kp.max_log_window; ++k) {
+    const int I = 1 << k;
+    if (I > C) break;
+    const double thr = thr_of(kp, m, sig, k);
+    for (int t = tid; t < C; t += kNtF) {
+      uint8_t fl = 0;
+      if (t + I <= C) {
+        double su = 0.0;
+        int nf = 0;
+        for (int j = t; j < t + I; ++j) {
+          if (Fc[j]) ++nf;
+          else su = __dadd_rn(su, S[j]);
+        }
+        fl = su > __dmul_rn(static_cast<double>(I - nf), thr) ? 1 : 0;
+      }
+      fire[t] = fl;
+    }
+    __syncthreads();
+    for (int c = tid; c < C; c += kNtF) {
+      uint8_t any = Fc[c];
+      for (int t = max(0, c - I + 1); t <= c && !any; ++t) any = fire[t];
+      Fc[c] = any;
+    }
+    __syncthreads();
+  }
+}
+
+// One radix-select pass over the finite samples of the kept rows: histogram
+// of the 11 (or 10) key bits below those already fixed, for each open rank.
+// MODE 0: keys of x; MODE 1: keys of float(|x - median_t|).
+template <int MODE>
+__device__ void select_pass(const DevUnit& u, const uint8_t* Fc, uint32_t* hist, int shift,
+                            int nbits, F32Shared& f) {
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int T = u.T, nb = 1 << nbits;
+  for (int i = tid; i < 2 * 2048; i += kNtF) hist[i] = 0u;
+  __syncthreads();
+  const uint32_t p0 = f.prefix[0], p1 = f.prefix[1];
+  const int hs = shift + nbits;  // bits above this digit are fixed
+  const bool two = f.n_rank == 2;
+  const double med = f.median_t;
+  const bool vin = (u.flags & kUnitInVec) != 0;
+  const float* gin = static_cast<const float*>(u.in);
+  const int nchunk = (T + 127) / 128;  // 32 lanes x 4 samples
+  for (int item = warp; item < u.C * nchunk; item += kNwF) {
+    const int c = item / nchunk, s = item - c * nchunk;
+    if (Fc[c]) continue;
+    const float* row = gin + static_cast<int64_t>(c) * u.in_stride;
+    const int x = s * 128 + lane * 4;
+    if (x >= T) continue;
+    const float4 v = ld4(row, x, T, vin);
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      const float xv = f4at(v, j);
+      if (!isfinite(xv)) continue;
+      const float kv = MODE == 0 ? xv : __double2float_rn(fabs(__dsub_rn(static_cast<double>(xv), med)));
+      const uint32_t key = fkey(kv);
+      const uint32_t hi = hs >= 32 ? 0u : (key >> hs);
+      const uint32_t dig = (key >> shift) & static_cast<uint32_t>(nb - 1);
+      if (hi == p0) atomicAdd(&hist[dig], 1u);
+      if (two && hi == p1) atomicAdd(&hist[2048 + dig], 1u);
+    }
+  }
+  __syncthreads();
+  // pick the digit of each open rank (one warp per rank)
+  if (warp < f.n_rank) {
+    const uint32_t* h = hist + 2048 * warp;
+    long long rk = f.rank[warp];
+    long long base = 0;
+    uint32_t digit = 0;
+    bool found = false;
+    for (int b0 = 0; b0 < nb && !found; b0 += 32) {
+      const uint32_t cnt = h[b0 + lane];
+      uint32_t incl = cnt;
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t y = __shfl_up_sync(kFullF, incl, o);
+        if (lane >= o) incl += y;
+      }
+      const uint32_t tot = __shfl_sync(kFullF, incl, 31);
+      if (rk < base + tot) {
+        const unsigned hit = __ballot_sync(kFullF, rk < base + static_cast<long long>(incl));
+        const int l = __ffs(hit) - 1;
+        const uint32_t excl = __shfl_sync(kFullF, incl - cnt, l);
+        digit = static_cast<uint32_t>(b0 + l);
+        rk -= base + excl;
+        found = true;
+      } else {
+        base += tot;
+      }
+    }
+    if (lane == 0) {
+      if (!found) f.ok = 0;
+      f.prefix[warp] = (f.prefix[warp] << nbits) | digit;
+      f.rank[warp] = rk;
+    }
+  }
+  __syncthreads();
+  if (tid == 0 && f.n_rank == 1) {
+    f.prefix[1] = f.prefix[0];
+    f.rank[1] = f.rank[0];
+  }
+  __syncthreads();
+}
+
+template <int MODE>
+__device__ double select_median(const DevUnit& u, const uint8_t* Fc, uint32_t* hist, F32Shared& f) {
+  const long long N = f.n_pool;
+  if (threadIdx.x == 0) {
+    f.prefix[0] = f.prefix[1] = 0u;
+    f.rank[0] = (N & 1) ? N / 2 : N / 2 - 1;
+    f.rank[1] = N / 2;
+    f.n_rank = (N & 1) ? 1 : 2;
+  }
+  __syncthreads();
+  select_pass<MODE>(u, Fc, hist, 21, 11, f);
+  select_pass<MODE>(u, Fc, hist, 10, 11, f);
+  select_pass<MODE>(u, Fc, hist, 0, 10, f);
+  const double a = static_cast<double>(fkey_val(f.prefix[0]));
+  const double b = static_cast<double>(fkey_val(f.prefix[1]));
+  return (N & 1) ? a : __dmul_rn(__dadd_rn(a, b), 0.5);
+}
+
+// population stddev of the pooled finite samples (binary64, two passes)
+__device__ double pooled_std(const DevUnit& u, const uint8_t* Fc, F32Shared& f) {
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const float* gin = static_cast<const float*>(u.in);
+  const int T = u.T;
+  double acc[2] = {0.0, 0.0};
+  double mu = 0.0;
+  for (int pass = 0; pass < 2; ++pass) {
+    double s = 0.0;
+    for (int c = warp; c < u.C; c += kNwF) {
+      if (Fc[c]) continue;
+      const float* row = gin + static_cast<int64_t>(c) * u.in_stride;
+      for (int t = lane; t < T; t += 32) {
+        const float xv = row[t];
+        if (!isfinite(xv)) continue;
+        const double d = pass == 0 ? static_cast<double>(xv) : __dsub_rn(static_cast<double>(xv), mu);
+        s = pass == 0 ? __dadd_rn(s, d) : __dadd_rn(s, __dmul_rn(d, d));
+      }
+    }
+    s = warp_sum_d(s);
+    if (lane == 0) f.red[warp] = s;
+    __syncthreads();
+    if (tid == 0) {
+      double t = 0.0;
+      for (int w = 0; w < kNwF; ++w) t = __dadd_rn(t, f.red[w]);
+      f.red[0] = t;
+    }
+    __syncthreads();
+    acc[pass] = f.red[0];
+    __syncthreads();
+    if (pass == 0) mu = __ddiv_rn(acc[0], static_cast<double>(f.n_pool));
+  }
+  return __dsqrt_rn(__ddiv_rn(acc[1], static_cast<double>(f.n_pool)));
+}
+
+// ---- time pass of one row segment by one warp (float32 window sums)
+struct WfRow {
+  float v[kNplF];  // the sample (0 where non-finite)
+  uint32_t M;      // flag bits
+};
+
+template <int I>
+__device__ __forceinline__ uint32_t wf_fire(const WfRow& R, int lane, float tI, float lim) {
+  float W[kNplF];
+#pragma unroll
+  for (int j = 0; j < kNplF; ++j) W[j] = ((R.M >> j) & 1u) ? tI : R.v[j];
+#pragma unroll
+  for (int s = 1; s < I; s <<= 1) {
+    float nx[kNplF];
+#pragma unroll
+    for (int j = 0; j < kNplF; ++j) {
+      if (j + s >= kNplF) {
+        const int q = (j + s) / kNplF;
+        float y = __shfl_down_sync(kFullF, W[j + s - q * kNplF], q);
+        nx[j] = lane + q < 32 ? y : 0.0f;
+      }
+    }
+#pragma unroll
+    for (int j = 0; j < kNplF; ++j) W[j] = __fadd_rn(W[j], j + s < kNplF ? W[j + s] : nx[j]);
+  }
+  uint32_t f = 0u;
+#pragma unroll
+  for (int j = kNplF - 1; j >= 0; --j) f = __funnelshift_l(__float_as_uint(__fsub_rn(lim, W[j])), f, 1);
+  return f;
+}
+
+// Flags of segment sg of one row (rows past 1024 samples overlap by a halo of
+// 120 samples); interior flag words go to Mrow, returns the interior's number
+// of flagged samples, entry-flagged samples and unflagged sum.
+__device__ void wf_segment(const float* row, int T, int sg, bool vin, const F32Shared& f,
+                           uint32_t* Mrow, int& nflag, int& nentry, double& su) {
+  constexpr int SPAN = 32 * kNplF;
+  const int lane = threadIdx.x & 31;
+  int oa = 0, s0 = 0, ob = SPAN >= T ? T : ((SPAN - kHaloF) & ~31);
+  for (int i = 0; i < sg; ++i) {
+    oa = ob;
+    s0 = (oa - kHaloF) & ~31;
+    ob = s0 + SPAN >= T ? T : ((s0 + SPAN - kHaloF) & ~31);
+  }
+  const int vend = min(T, s0 + SPAN);
+  const int xl = s0 + lane * kNplF;
+  WfRow R;
+  R.M = 0u;
+#pragma unroll
+  for (int q = 0; q < kNplF / 4; ++q) {
+    const int x = xl + 4 * q;
+    const float4 v = x < T ? ld4(row, x, T, vin) : make_float4(0.f, 0.f, 0.f, 0.f);
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      const float xv = f4at(v, j);
+      const bool bad = x + j < T && !isfinite(xv);
+      R.v[4 * q + j] = (x + j < T && !bad) ? xv : 0.0f;
+      if (bad) R.M |= 1u << (4 * q + j);
+    }
+  }
+  const uint32_t entry = R.M;
+#pragma unroll 1
+  for (int k = 0; k <= f.kmax_t; ++k) {
+    const int I = 1 << k;
+    const float tI = f.tIf[k], lim = f.limI[k];
+    uint32_t F;
+    switch (k) {
+      case 0: F = wf_fire<1>(R, lane, tI, lim); break;
+      case 1: F = wf_fire<2>(R, lane, tI, lim); break;
+      case 2: F = wf_fire<4>(R, lane, tI, lim); break;
+      case 3: F = wf_fire<8>(R, lane, tI, lim); break;
+      case 4: F = wf_fire<16>(R, lane, tI, lim); break;
+      case 5: F = wf_fire<32>(R, lane, tI, lim); break;
+      default: F = wf_fire<64>(R, lane, tI, lim); break;
+    }
+    const int nv = vend - I + 1 - xl;
+    F &= nv >= 32 ? kFullF : (nv <= 0 ? 0u : ((1u << nv) - 1u));
+    uint32_t p1 = __shfl_up_sync(kFullF, F, 1), p2 = __shfl_up_sync(kFullF, F, 2);
+    if (lane < 1) p1 = 0u;
+    if (lane < 2) p2 = 0u;
+    const uint32_t D = I <= 32 ? dilate32f(F, p1, I) : (dilate32f(F, p1, 32) | dilate32f(p1, p2, 32));
+    R.M |= D;
+  }
+  int nf = 0, ne = 0;
+  double s = 0.0;
+  if (xl >= oa && xl < ob) {
+    Mrow[xl >> 5] = R.M;
+    nf = __popc(R.M);
+    ne = __popc(entry);
+#pragma unroll
+    for (int j = 0; j < kNplF; ++j)
+      if (!((R.M >> j) & 1u)) s = __dadd_rn(s, static_cast<double>(R.v[j]));
+  }
+  nflag = __reduce_add_sync(kFullF, nf);
+  nentry = __reduce_add_sync(kFullF, ne);
+  su = warp_sum_d(s);
+}
+
+// Entry flags (non-finite samples) of a row without a time pass.
+__device__ void wf_entry_only(const float* row, int T, uint32_t* Mrow, int& nflag, double& su) {
+  const int lane = threadIdx.x & 31;
+  int nf = 0;
+  double s = 0.0;
+  for (int w = lane; w < (T + 31) / 32; w += 32) {
+    uint32_t m = 0u;
+    for (int j = 0; j < 32 && 32 * w + j < T; ++j) {
+      const float xv = row[32 * w + j];
+      if (!isfinite(xv)) m |= 1u << j;
+      else s = __dadd_rn(s, static_cast<double>(xv));
+    }
+    Mrow[w] = m;
+    nf += __popc(m);
+  }
+  nflag = __reduce_add_sync(kFullF, nf);
+  su = warp_sum_d(s);
+}
+
+// ---- one unit
+__device__ void f32_unit(const KParams& kp, const DevUnit& u, uint8_t* smem, F32Shared& f) {
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int C = u.C, T = u.T;
+  double* S = reinterpret_cast<double*>(smem + kOffS);
+  unsigned long long* srt = reinterpret_cast<unsigned long long*>(smem + kOffSrt);
+  int* fin = reinterpret_cast<int*>(smem + kOffFin);
+  uint8_t* Fc = smem + kOffFc;
+  uint8_t* fire = smem + kOffFire;
+  uint32_t* hist = reinterpret_cast<uint32_t*>(smem + kOffHist);
+  const int nwr = (T + 31) / 32;
+  uint32_t* Mrow = reinterpret_cast<uint32_t*>(smem + kOffRows) + warp * nwr;
+  const bool vin = (u.flags & kUnitInVec) != 0;
+  const float* gin = static_cast<const float*>(u.in);
+  if (tid == 0) {
+    f.cnt_time = f.cnt_total = f.cnt_hist = 0;
+    f.ok = 1;
+  }
+  // a2: row sums of the finite samples (binary64)
+  for (int c = warp; c < C; c += kNwF) {
+    const float* row = gin + static_cast<int64_t>(c) * u.in_stride;
+    double s = 0.0;
+    int nfin = 0;
+    for (int x = lane * 4; x < T; x += 128) {
+      const float4 v = ld4(row, x, T, vin);
+#pragma unroll
+      for (int j = 0; j < 4; ++j) {
+        const float xv = f4at(v, j);
+        if (x + j < T && isfinite(xv)) {
+          s = __dadd_rn(s, static_cast<double>(xv));
+          ++nfin;
+        }
+      }
+    }
+    s = warp_sum_d(s);
+    nfin = __reduce_add_sync(kFullF, nfin);
+    if (lane == 0) {
+      S[c] = s;
+      fin[c] = nfin;
+      Fc[c] = 0;
+    }
+  }
+  __syncthreads();
+  // a3, a4
+  spectrum_stats(kp, S, C, srt, f);
+  spectrum_sum_threshold(kp, S, C, Fc, fire, f);
+  // a5
+  long long np = 0;
+  int nfc = 0;
+  for (int c = tid; c < C; c += kNtF) {
+    if (!Fc[c]) np += fin[c];
+    nfc += Fc[c];
+  }
+  np = warp_sum_ll(np);
+  nfc = __reduce_add_sync(kFullF, nfc);
+  if (lane == 0) {
+    srt[warp] = static_cast<unsigned long long>(np);
+    fire[warp] = 0;
+    reinterpret_cast<int*>(hist)[warp] = nfc;
+  }
+  __syncthreads();
+  if (tid == 0) {
+    long long t = 0;
+    int tc = 0;
+    for (int w = 0; w < kNwF; ++w) {
+      t += static_cast<long long>(srt[w]);
+      tc += reinterpret_cast<int*>(hist)[w];
+    }
+    f.n_pool = t;
+    f.nfc = tc;
+  }
+  __syncthreads();
+  double med = 0.0, sig = 0.0;
+  if (f.n_pool > 0) {
+    med = select_median<0>(u, Fc, hist, f);
+    if (tid == 0) f.median_t = med;
+    __syncthreads();
+    double mad = 0.0;
+    if (!kp.sigma_std) mad = select_median<1>(u, Fc, hist, f);
+    if (!kp.sigma_std && mad > 0.0) sig = __dmul_rn(1.482602218505602, mad);
+    else sig = pooled_std(u, Fc, f);
+  }
+  if (tid == 0) {
+    if (!f.ok) set_error_f(kp, kErrSelect, 700);
+    f.median_t = med;
+    f.sigma_t = sig;
+    int kmax = 0;
+    while (kmax < kp.max_log_window && (2 << kmax) <= T) ++kmax;
+    f.kmax_t = kmax;
+    f.time_on = (kp.enable_time && f.n_pool > 0 && sig > 0.0) ? 1 : 0;
+    for (int k = 0; k <= kmax; ++k) {
+      const double t = thr_of(kp, med, sig, k);
+      f.tI[k] = t;
+      f.tIf[k] = __double2float_rn(t);
+      f.limI[k] = __double2float_rn(__dmul_rn(static_cast<double>(1 << k), t));
+    }
+  }
+  __syncthreads();
+  // a6 - a8, one warp per row
+  const int nsg = T <= 32 * kNplF ? 1 : [&] {
+    int n = 1, ob = (32 * kNplF - kHaloF) & ~31;
+    while (ob < T) {
+      const int s0 = (ob - kHaloF) & ~31;
+      ob = s0 + 32 * kNplF >= T ? T : ((s0 + 32 * kNplF - kHaloF) & ~31);
+      ++n;
+    }
+    return n;
+  }();
+  const bool mask_vec = (u.flags & kUnitMaskVec) != 0;
+  const bool vout = (u.flags & kUnitOutVec) != 0;
+  const bool inplace = (u.flags & kUnitInPlace) != 0;
+  for (int c = warp; c < C; c += kNwF) {
+    const float* row = gin + static_cast<int64_t>(c) * u.in_stride;
+    const long long h = u.hist_slot >= 0 ? u.hist_slot + c : -1;
+    bool full = Fc[c] != 0;
+    int nflag = 0;
+    if (!full) {
+      int nentry = 0;
+      double su = 0.0;
+      if (f.time_on) {
+        for (int sg = 0; sg < nsg; ++sg) {
+          int a, b;
+          double s;
+          wf_segment(row, T, sg, vin, f, Mrow, a, b, s);
+          nflag += a;
+          nentry += b;
+          su = __dadd_rn(su, s);
+        }
+      } else {
+        wf_entry_only(row, T, Mrow, nflag, su);
+        nentry = nflag;
+      }
+      __syncwarp();
+      // a7: history (Section 4.1)
+      const int n = T - nflag;
+      bool fh = false;
+      if (lane == 0) {
+        if (n > 0) {
+          const double cur = __ddiv_rn(su, static_cast<double>(n));
+          double staged = cur;
+          if (kp.enable_history && h >= 0) {
+            const int cnt = kp.hist.count[h];
+            if (cnt >= kp.history_min && cnt > 0) {
+              const double thr = kp.hist.thr[h];
+              if (!(cur < thr)) {
+                fh = true;
+                staged = thr;
+              }
+            }
+          }
+          if (h >= 0) {
+            kp.hist.pend[h] = staged;
+            kp.hist.pend_flag[h] = 1;
+            kp.hist.pend_seq[h] = kp.block_seq;
+          }
+        } else if (h >= 0) {
+          kp.hist.pend_flag[h] = 0;
+        }
+        atomicAdd(&f.cnt_time, static_cast<unsigned long long>(nflag - nentry));
+        if (fh) atomicAdd(&f.cnt_hist, 1ull);
+        atomicAdd(&f.cnt_total, fh ? static_cast<unsigned long long>(T)
+                                   : static_cast<unsigned long long>(nflag));
+      }
+      full = __shfl_sync(kFullF, fh ? 1 : 0, 0) != 0;
+    } else {
+      if (lane == 0) {
+        if (h >= 0) kp.hist.pend_flag[h] = 0;
+        atomicAdd(&f.cnt_total, static_cast<unsigned long long>(T));
+      }
+    }
+    // a8: mask and masked data
+    const int64_t gi = c;
+    for (int x = lane * 4; x < T; x += 128) {
+      const int nv = min(4, T - x);
+      const uint32_t valid = nv >= 4 ? 0xFu : ((1u << nv) - 1u);
+      const uint32_t bits = full ? valid : ((Mrow[x >> 5] >> (x & 31)) & valid);
+      if (u.mask) {
+        uint8_t* mr = u.mask + gi * u.mask_stride;
+        if (mask_vec && nv == 4) *reinterpret_cast<uint32_t*>(mr + x) = (bits * 0x00204081u) & 0x01010101u;
+        else for (int j = 0; j < nv; ++j) mr[x + j] = static_cast<uint8_t>((bits >> j) & 1u);
+      }
+      if (u.out) {
+        float* orow = static_cast<float*>(u.out) + gi * u.out_stride;
+        if (inplace) {
+          for (int j = 0; j < nv; ++j)
+            if ((bits >> j) & 1u) orow[x + j] = 0.0f;
+        } else if (vin && vout && nv == 4) {
+          float4 w = __ldg(reinterpret_cast<const float4*>(row + x));
+          if (bits & 1u) w.x = 0.0f;
+          if (bits & 2u) w.y = 0.0f;
+          if (bits & 4u) w.z = 0.0f;
+          if (bits & 8u) w.w = 0.0f;
+          __stcs(reinterpret_cast<float4*>(orow + x), w);
+        } else {
+          for (int j = 0; j < nv; ++j) orow[x + j] = ((bits >> j) & 1u) ? 0.0f : row[x + j];
+        }
+      }
+    }
+    __syncwarp();
+  }
+  __syncthreads();
+  if (tid == 0 && u.stats) {
+    u.stats->median_f = f.median_f;
+    u.stats->sigma_f = f.sigma_f;
+    u.stats->median_t = f.median_t;
+    u.stats->sigma_t = f.sigma_t;
+    u.stats->n_chan_freq = f.nfc;
+    u.stats->n_flag_time = static_cast<long long>(f.cnt_time);
+    u.stats->n_chan_hist = static_cast<long long>(f.cnt_hist);
+    u.stats->n_flag_total = static_cast<long long>(f.cnt_total);
+  }
+  __syncthreads();
+}
+
+__global__ void __launch_bounds__(kNtF, 2) lof_f32_kernel(const KParams kp) {
+  extern __shared__ __align__(16) uint8_t smem[];
+  __shared__ F32Shared f;
+  for (int ui = blockIdx.x; ui < kp.n_units; ui += gridDim.x) {
+    const DevUnit u = kp.units[ui];
+    f32_unit(kp, u, smem, f);
+  }
+}
+
+}  // namespace
+}  // namespace lofk
+
+// Shared-memory bytes for units of up to n_time samples per row.
+extern "C" int lofk_f32_smem(int max_T) {
+  return lofk::kFixedBytesF + lofk::kNwF * ((max_T + 31) / 32) * 4;
+}
+
+extern "C" int lofk_launch_f32(const lofk::KParams* kp, int n_units, int n_sm, int smem_bytes,
+                               void* stream) {
+  using namespace lofk;
+  if (n_units <= 0) return 0;
+  if (cudaFuncSetAttribute(reinterpret_cast<const void*>(&lof_f32_kernel),
+                           cudaFuncAttributeMaxDynamicSharedMemorySize, smem_bytes) != cudaSuccess)
+    return -2;
+  int occ = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, lof_f32_kernel, kNtF, smem_bytes) !=
+          cudaSuccess ||
+      occ < 1)
+    return -3;
+  const int grid = n_units < n_sm * occ ? n_units : n_sm * occ;
+  lof_f32_kernel<<<grid, kNtF, smem_bytes, static_cast<cudaStream_t>(stream)>>>(*kp);
+  const cudaError_t e = cudaGetLastError();
+  return e == cudaSuccess ? 0 : static_cast<int>(e);
+}

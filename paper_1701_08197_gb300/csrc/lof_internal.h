@@ -194,3 +194,6 @@ extern "C" int lofk_launch_commit(const lofk::CommitParams* cp, int total_channe
 extern "C" int lofk_launch_refresh(const lofk::CommitParams* cp, int total_channels, void* stream);
 extern "C" int lofk_max_blocks_per_sm(int dtype, int threads, int smem_bytes, int* out);
 extern "C" int lofk_set_smem_limit(int dtype, int smem_bytes);
+extern "C" int lofk_f32_smem(int max_T);
+extern "C" int lofk_launch_f32(const lofk::KParams* kp, int n_units, int n_sm, int smem_bytes,
+                               void* stream);

@@ -127,7 +127,7 @@ extern "C" int lof_flag_block_noalloc(const lof_params* params, int dtype, const
   sc.chanFc = base + off;
   off += up256(static_cast<size_t>(pr.n_chan));
   sc.ustate = reinterpret_cast<lofk::UnitState*>(base + off);
-  off += static_cast<size_t>(n_units) * sizeof(lofk::UnitState);
+  off += static_cast<size_t>(dtype == LOF_F32 ? 0 : n_units) * sizeof(lofk::UnitState);
   if (off > kScratchBytes) {
     snprintf(why, sizeof why,
              "lof_flag_block_noalloc: the block needs %zu bytes of scratch, the static array holds %zu",
