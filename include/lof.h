@@ -112,9 +112,10 @@ typedef struct {
  *  history_slot: first of n_chan consecutive history slots of the context, or
  *          -1 for no history (the history flagger is then skipped for the unit).
  *  stats : optional device lof_unit_stats*, or NULL.
- * Limits: 1 <= n_chan <= 2048, 1 <= n_time, and one row must fit the
- * kernel's shared-memory buffer for the time pass (about 4.6 bytes per sample:
- * n_time up to ~20000 with the default tuning); see lof_max_time(). */
+ * Limits: 1 <= n_chan <= 2048, 1 <= n_time; the flag words of one row (one
+ * bit per sample) must fit a CTA's shared memory, and a float32 row's flag
+ * words times 8 as well (n_time up to ~400000 with the default tuning; see
+ * lof_max_time()). */
 typedef struct {
   const void *in;
   void *out;
@@ -182,9 +183,40 @@ typedef struct {
   int32_t ctas_per_sm;     /* resident CTAs per SM: 1 to 4 (default 4) */
   int32_t tile_bytes;      /* cap on the shared-memory bytes of a CTA */
   int32_t fine_bins;       /* counters per exact-selection refinement round */
+  int32_t flag_rows;       /* rows per time-pass task (tile height), 1..64; 0 = 4 per warp */
+  int32_t stat_samples;    /* samples per statistics task, >= 1024; 0 = 65536 */
 } lof_tuning;
 int lof_set_tuning(lof_ctx *ctx, const lof_tuning *t);
 int lof_get_tuning(const lof_ctx *ctx, lof_tuning *t);
+
+/* Autotuner: times lof_flag_block on these units (reps timed launches after
+ * one warm-up, median) for every candidate launch shape -- threads per CTA,
+ * CTAs per SM, rows per time-pass task, samples per statistics task -- and
+ * keeps the fastest in the context (*best, *best_ms if not NULL).  Results
+ * never depend on the tuning.  Synchronous; stages history values like any
+ * lof_flag_block call (do not commit them).  F32 units have a single shape. */
+int lof_autotune(lof_ctx *ctx, int dtype, const lof_unit *units, int n_units, int reps,
+                 void *cuda_stream, lof_tuning *best, float *best_ms);
+
+/* Graph form of a block (the batching pattern for fixed buffers: every
+ * station x polarisation x subband of a real-time pipeline, re-flagged each
+ * block in the same device buffers).  lof_graph_create builds and uploads the
+ * descriptors of n_units units once (pointers, shapes and strides are fixed
+ * from then on; the data in the buffers changes freely) and captures the
+ * device-side steps of lof_flag_block -- state reset, the one persistent
+ * launch, the error-word copy -- in a CUDA graph, with the context's current
+ * tuning and parameters.  lof_graph_launch replays it on cuda_stream with the
+ * given block sequence number; history values are staged in the context's
+ * slots exactly as by lof_flag_block (commit them with lof_history_update).
+ * Replays of one graph must be ordered on one stream.  lof_graph_launch
+ * returns a device-side error of the previous replay once it has finished;
+ * lof_graph_status waits for cuda_stream and returns it. */
+typedef struct lof_graph lof_graph;
+int lof_graph_create(lof_ctx *ctx, int dtype, const lof_unit *units, int n_units,
+                     lof_graph **out);
+int lof_graph_launch(lof_graph *graph, uint64_t block_seq, void *cuda_stream);
+int lof_graph_status(lof_graph *graph, void *cuda_stream);
+int lof_graph_destroy(lof_graph *graph);
 
 /* Flag one block of units like lof_flag_block, without allocating anything.
  * The paper has no counterpart: this entry point exists for callers that may

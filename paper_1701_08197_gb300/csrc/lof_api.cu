@@ -46,7 +46,7 @@ struct lof_ctx {
   lof_params params{};
   int n_sm = 0;
   int smem_per_sm = 0, smem_optin = 0;
-  lof_tuning tuning{128, 4, 0, 2048};
+  lof_tuning tuning{128, 4, 0, 2048, 0, 0};
   // history
   int64_t n_slots = 0;
   int H = 0;
@@ -61,6 +61,8 @@ struct lof_ctx {
   unsigned long long* d_chanS = nullptr;
   uint8_t* d_chanFc = nullptr;
   size_t cap_chan = 0, cap_chanfc = 0;
+  uint32_t* d_gen = nullptr;  // general time-pass rows (per CTA)
+  size_t cap_gen = 0;
   int* d_ctrl = nullptr;  // [0] queue, [1] error, [2..3] error detail
   int* h_err = nullptr;   // pinned copy of d_ctrl[1..3]
   cudaEvent_t ev_err = nullptr;
@@ -283,6 +285,7 @@ extern "C" int lof_destroy(lof_ctx* c) {
   cudaFree(c->d_ustate);
   cudaFree(c->d_chanS);
   cudaFree(c->d_chanFc);
+  cudaFree(c->d_gen);
   cudaFree(c->d_ctrl);
   cudaFree(c->d_io);
   if (c->h_err) cudaFreeHost(c->h_err);
@@ -311,6 +314,15 @@ extern "C" int lof_set_tuning(lof_ctx* c, const lof_tuning* t) {
     if (t->tile_bytes < 4096 || (t->tile_bytes % 128)) return fail(c, LOF_ERR_INVALID, "tile_bytes >= 4096, multiple of 128");
     n.tile_bytes = t->tile_bytes;
   }
+  if (t->flag_rows) {
+    if (t->flag_rows < 1 || t->flag_rows > lofk::kMaxRowsPerTask)
+      return fail(c, LOF_ERR_INVALID, "flag_rows in [1, %d]", lofk::kMaxRowsPerTask);
+    n.flag_rows = t->flag_rows;
+  }
+  if (t->stat_samples) {
+    if (t->stat_samples < 1024) return fail(c, LOF_ERR_INVALID, "stat_samples >= 1024");
+    n.stat_samples = t->stat_samples;
+  }
   if (t->fine_bins) {
     if (t->fine_bins < 64 || t->fine_bins > lofk::kMaxFine)
       return fail(c, LOF_ERR_INVALID, "fine_bins in [64, %d]", lofk::kMaxFine);
@@ -329,17 +341,20 @@ extern "C" int lof_get_tuning(const lof_ctx* c, lof_tuning* t) {
 namespace {
 
 // Rows of one flag task: four per warp, fewer if the shared memory cannot
-// hold their flag words plus one row of the general (any-magnitude) path.
+// hold their flag words.
 int flag_words_row(int T) { return (T + 31) / 32 + 4; }
-int flag_rows(int dtype, int T, int budget_bytes, int threads) {
+int flag_rows(int dtype, int T, int budget_bytes, int threads, int cap = 0) {
   const int mw = flag_words_row(T), pr = pfx_row_words(dtype, T);
-  int R = std::min(lofk::kMaxRowsPerTask, 4 * (threads / 32));
-  while (R > 0 && 4 * (R * mw + pr + mw) > budget_bytes) --R;
+  (void)pr;
+  int R = std::min(lofk::kMaxRowsPerTask, cap > 0 ? cap : 4 * (threads / 32));
+  while (R > 0 && 4 * R * mw > budget_bytes) --R;
   return R;
 }
 
 // Rows of one stats / fine task (streamed, ~64K samples per task).
-int stat_rows(int T) { return std::max(1, std::min(lofk::kMaxRowsPerTask, 65536 / std::max(1, T))); }
+int stat_rows(int T, int samples = 0) {
+  return std::max(1, std::min(lofk::kMaxRowsPerTask, (samples > 0 ? samples : 65536) / std::max(1, T)));
+}
 
 // Shared-memory plan: the unit-wide workspace, the flag words of a flag
 // task and as many rows of the general path as the budget allows.
@@ -351,14 +366,14 @@ bool make_plan(const lofk::HostCfg& h, int dtype, const int* Ts, int nT, lofk::P
   if (h.tuning.tile_bytes) budget = std::min(budget, h.tuning.tile_bytes);
   int need = lofk::kWorkspaceBytes, want = lofk::kWorkspaceBytes;
   for (int i = 0; i < nT; ++i) {
-    const int R = flag_rows(dtype, Ts[i], budget, pl->threads);
+    const int R = flag_rows(dtype, Ts[i], budget, pl->threads, h.tuning.flag_rows);
     if (R < 1) {
       snprintf(why, nwhy, "n_time %d does not fit the shared-memory budget (%d bytes)", Ts[i], budget);
       return false;
     }
-    const int mw = flag_words_row(Ts[i]), pr = pfx_row_words(dtype, Ts[i]);
-    need = std::max(need, 4 * (R * mw + pr + mw));
-    want = std::max(want, 4 * (R * mw + R * (pr + mw)));
+    const int mw = flag_words_row(Ts[i]);
+    need = std::max(need, 4 * R * mw);
+    want = std::max(want, 4 * R * mw);
   }
   if (need > budget) {
     snprintf(why, nwhy, "the workspace (%d bytes) exceeds the shared-memory budget (%d)", need, budget);
@@ -389,12 +404,12 @@ int host_count_tasks(const HostCfg& h, int dtype, const lof_unit* units, int n_u
   int64_t n = 0;
   for (int i = 0; i < n_units; ++i) {
     const int T = units[i].n_time, C = units[i].n_chan;
-    const int Rc = flag_rows(dtype, T, budget, h.tuning.threads);
+    const int Rc = flag_rows(dtype, T, budget, h.tuning.threads, h.tuning.flag_rows);
     if (Rc < 1) {
       snprintf(why, nwhy, "n_time %d does not fit the shared-memory budget (%d bytes)", T, budget);
       return LOF_ERR_INVALID;
     }
-    const int Rs = stat_rows(T);
+    const int Rs = stat_rows(T, h.tuning.stat_samples);
     n += 2 * ((C + Rs - 1) / Rs) + (C + Rc - 1) / Rc;
   }
   if (n > (int64_t(1) << 30)) {
@@ -499,7 +514,8 @@ int host_prepare(const HostCfg& h, int dtype, const lof_unit* units, int n_units
     if (u.mask && (reinterpret_cast<uintptr_t>(u.mask) % 16) == 0 && (u.mask_row_stride % 16) == 0)
       flags |= kUnitMaskVec;
     d.flags = flags;
-    const int Rs = stat_rows(u.n_time), Rc = flag_rows(dtype, u.n_time, budget, pl.threads);
+    const int Rs = stat_rows(u.n_time, h.tuning.stat_samples),
+              Rc = flag_rows(dtype, u.n_time, budget, pl.threads, h.tuning.flag_rows);
     d.nS = (u.n_chan + Rs - 1) / Rs;
     d.nF = d.nS;
     d.nC = (u.n_chan + Rc - 1) / Rc;
@@ -545,28 +561,25 @@ int host_prepare(const HostCfg& h, int dtype, const lof_unit* units, int n_units
   out->n_tasks = n;
   out->n_chan = chan;
   out->grid = std::min(grid, n);
+  // one row of the general (any-magnitude) time pass per CTA, in global scratch
+  int gw = 0;
+  for (int i = 0; i < nT; ++i) gw = std::max(gw, pfx_row_words(dtype, Ts[i]) + flag_words_row(Ts[i]));
+  out->gen_words = (gw + 31) & ~31;
   return LOF_OK;
 }
 
-int host_launch(const lof_params& P, const HostCfg& h, int dtype, const Prep& pr,
-                const Scratch& sc, const DevUnit* du_host, int n_units, const Task* tasks_host,
-                uint64_t seq, void* stream, char* why, int nwhy) {
+// Device-side steps of one block (no host memory touched): per-unit state
+// and queue reset, the kernel launch.  Stream-capturable.
+int host_launch_kernel(const lof_params& P, const HostCfg& h, int dtype, const Prep& pr,
+                       const Scratch& sc, int n_units, uint64_t seq, void* stream, int cooperative,
+                       char* why, int nwhy) {
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   cudaError_t e;
-  if (dtype == LOF_F32) {
-    if ((e = cudaMemcpyAsync(sc.units, du_host, n_units * sizeof(DevUnit), cudaMemcpyHostToDevice,
-                             st)) != cudaSuccess) {
-      snprintf(why, nwhy, "descriptor upload: %s", cudaGetErrorString(e));
-      return LOF_ERR_CUDA;
-    }
-  } else if ((e = cudaMemcpyAsync(sc.units, du_host, n_units * sizeof(DevUnit), cudaMemcpyHostToDevice, st)) !=
-          cudaSuccess ||
-      (e = cudaMemcpyAsync(sc.tasks, tasks_host, pr.n_tasks * sizeof(Task), cudaMemcpyHostToDevice,
-                           st)) != cudaSuccess ||
-      (e = cudaMemset2DAsync(sc.ustate, sizeof(UnitState), 0, kUnitStateZeroBytes, n_units, st)) !=
-          cudaSuccess ||
-      (e = cudaMemsetAsync(sc.ctrl, 0, sizeof(int), st)) != cudaSuccess) {
-    snprintf(why, nwhy, "descriptor upload: %s", cudaGetErrorString(e));
+  if (dtype != LOF_F32 &&
+      ((e = cudaMemset2DAsync(sc.ustate, sizeof(UnitState), 0, kUnitStateZeroBytes, n_units, st)) !=
+           cudaSuccess ||
+       (e = cudaMemsetAsync(sc.ctrl, 0, sizeof(int), st)) != cudaSuccess)) {
+    snprintf(why, nwhy, "state reset: %s", cudaGetErrorString(e));
     return LOF_ERR_CUDA;
   }
   KParams kp{};
@@ -602,9 +615,12 @@ int host_launch(const lof_params& P, const HostCfg& h, int dtype, const Prep& pr
   kp.block_seq = seq;
   kp.spin_limit = 2000000000ll;  // 2 s
   kp.dyn_smem = pr.plan.smem;
+  kp.gen_scratch = sc.gen;
+  kp.gen_words = pr.gen_words;
   const int krc = dtype == LOF_F32
                       ? lofk_launch_f32(&kp, n_units, h.n_sm, pr.plan.smem, stream)
-                      : lofk_launch_block(dtype, &kp, pr.grid, pr.plan.threads, pr.plan.smem, stream, 1);
+                      : lofk_launch_block(dtype, &kp, pr.grid, pr.plan.threads, pr.plan.smem, stream,
+                                          cooperative);
   if (krc != 0) {
     snprintf(why, nwhy, "kernel launch failed: %s (grid %d, %d threads, %d B)",
              cudaGetErrorString(static_cast<cudaError_t>(krc)), pr.grid, pr.plan.threads,
@@ -612,6 +628,21 @@ int host_launch(const lof_params& P, const HostCfg& h, int dtype, const Prep& pr
     return LOF_ERR_CUDA;
   }
   return LOF_OK;
+}
+
+int host_launch(const lof_params& P, const HostCfg& h, int dtype, const Prep& pr,
+                const Scratch& sc, const DevUnit* du_host, int n_units, const Task* tasks_host,
+                uint64_t seq, void* stream, char* why, int nwhy) {
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  cudaError_t e;
+  if ((e = cudaMemcpyAsync(sc.units, du_host, n_units * sizeof(DevUnit), cudaMemcpyHostToDevice,
+                           st)) != cudaSuccess ||
+      (pr.n_tasks > 0 && (e = cudaMemcpyAsync(sc.tasks, tasks_host, pr.n_tasks * sizeof(Task),
+                                              cudaMemcpyHostToDevice, st)) != cudaSuccess)) {
+    snprintf(why, nwhy, "descriptor upload: %s", cudaGetErrorString(e));
+    return LOF_ERR_CUDA;
+  }
+  return host_launch_kernel(P, h, dtype, pr, sc, n_units, seq, stream, 1, why, nwhy);
 }
 
 int host_validate_unit(int dtype, const lof_unit& u, int i, int64_t n_slots, char* why, int nwhy) {
@@ -695,6 +726,9 @@ int flag_block_device(lof_ctx* c, int dtype, const lof_unit* units, int n_units,
   if ((rc = grow(c, &c->d_chanS, &c->cap_chan, static_cast<size_t>(pr.n_chan), "spectrum"))) return rc;
   if ((rc = grow(c, &c->d_chanFc, &c->cap_chanfc, static_cast<size_t>(pr.n_chan), "channel flags")))
     return rc;
+  if ((rc = grow(c, &c->d_gen, &c->cap_gen,
+                 static_cast<size_t>(std::max(1, pr.grid)) * std::max(1, pr.gen_words), "general rows")))
+    return rc;
   lofk::Scratch sc{};
   sc.units = c->d_units;
   sc.tasks = c->d_tasks;
@@ -703,6 +737,7 @@ int flag_block_device(lof_ctx* c, int dtype, const lof_unit* units, int n_units,
   sc.chanFc = c->d_chanFc;
   sc.ctrl = c->d_ctrl;
   sc.hist = c->hist;
+  sc.gen = c->d_gen;
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   rc = lofk::host_launch(c->params, h, dtype, pr, sc, du, n_units, tasks, seq, stream, why, sizeof why);
   cudaEventRecord(c->ev_stage[si], st);
@@ -957,4 +992,275 @@ extern "C" int lof_max_time(const lof_ctx* c, int dtype) {
     else hi = mid;
   }
   return lo;
+}
+
+// ------------------------------------------------------------------ graph form
+
+struct lof_graph {
+  lof_ctx* ctx = nullptr;
+  int dtype = 0, n_units = 0;
+  DevUnit* d_units = nullptr;
+  Task* d_tasks = nullptr;
+  UnitState* d_ustate = nullptr;
+  unsigned long long* d_chanS = nullptr;
+  uint8_t* d_chanFc = nullptr;
+  uint32_t* d_gen = nullptr;
+  int* d_ctrl = nullptr;  // [0] queue, [1] error, [2..3] detail
+  int* h_err = nullptr;   // pinned copy of d_ctrl[1..3], written by the graph
+  cudaEvent_t ev_err = nullptr;
+  bool launched = false;
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t exec = nullptr;
+  cudaGraphNode_t knode = nullptr;
+  cudaKernelNodeParams kparams{};
+  lofk::KParams kp{};  // argument storage for parameter updates
+  void* kargs[1] = {nullptr};
+};
+
+namespace {
+
+void graph_free(lof_graph* g) {
+  if (!g) return;
+  if (g->exec) cudaGraphExecDestroy(g->exec);
+  if (g->graph) cudaGraphDestroy(g->graph);
+  cudaFree(g->d_units);
+  cudaFree(g->d_tasks);
+  cudaFree(g->d_ustate);
+  cudaFree(g->d_chanS);
+  cudaFree(g->d_chanFc);
+  cudaFree(g->d_gen);
+  cudaFree(g->d_ctrl);
+  if (g->h_err) cudaFreeHost(g->h_err);
+  if (g->ev_err) cudaEventDestroy(g->ev_err);
+  delete g;
+}
+
+// Capture the device-side steps of a block into g->graph / g->exec.
+int graph_capture(lof_graph* g, const lofk::HostCfg& h, const lofk::Prep& pr, int cooperative,
+                  char* why, int nwhy) {
+  cudaStream_t s = nullptr;
+  cudaError_t e = cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking);
+  if (e != cudaSuccess) return snprintf(why, nwhy, "stream: %s", cudaGetErrorString(e)), LOF_ERR_CUDA;
+  lofk::Scratch sc{};
+  sc.units = g->d_units;
+  sc.tasks = g->d_tasks;
+  sc.ustate = g->d_ustate;
+  sc.chanS = g->d_chanS;
+  sc.chanFc = g->d_chanFc;
+  sc.ctrl = g->d_ctrl;
+  sc.hist = g->ctx->hist;
+  sc.gen = g->d_gen;
+  int rc = LOF_OK;
+  e = cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal);
+  if (e == cudaSuccess) {
+    rc = lofk::host_launch_kernel(g->ctx->params, h, g->dtype, pr, sc, g->n_units, 0, s, cooperative,
+                                  why, nwhy);
+    if (rc == LOF_OK) {
+      e = cudaMemcpyAsync(g->h_err, g->d_ctrl + 1, 3 * sizeof(int), cudaMemcpyDeviceToHost, s);
+      if (e != cudaSuccess) rc = LOF_ERR_CUDA, snprintf(why, nwhy, "error copy: %s", cudaGetErrorString(e));
+    }
+    cudaGraph_t gr = nullptr;
+    const cudaError_t ee = cudaStreamEndCapture(s, &gr);
+    if (rc == LOF_OK && ee != cudaSuccess)
+      rc = LOF_ERR_CUDA, snprintf(why, nwhy, "capture: %s", cudaGetErrorString(ee));
+    if (rc == LOF_OK) g->graph = gr;
+    else if (gr) cudaGraphDestroy(gr);
+  } else {
+    rc = LOF_ERR_CUDA;
+    snprintf(why, nwhy, "begin capture: %s", cudaGetErrorString(e));
+  }
+  cudaGetLastError();  // a refused launch inside the capture leaves no sticky error
+  cudaStreamDestroy(s);
+  if (rc) return rc;
+  size_t n = 0;
+  cudaGraphGetNodes(g->graph, nullptr, &n);
+  std::vector<cudaGraphNode_t> nodes(n);
+  cudaGraphGetNodes(g->graph, nodes.data(), &n);
+  for (size_t i = 0; i < n; ++i) {
+    cudaGraphNodeType t;
+    if (cudaGraphNodeGetType(nodes[i], &t) == cudaSuccess && t == cudaGraphNodeTypeKernel) {
+      g->knode = nodes[i];
+      cudaGraphKernelNodeGetParams(nodes[i], &g->kparams);
+      std::memcpy(&g->kp, g->kparams.kernelParams[0], sizeof(lofk::KParams));
+    }
+  }
+  if (!g->knode) return snprintf(why, nwhy, "no kernel node in the captured graph"), LOF_ERR_CUDA;
+  e = cudaGraphInstantiate(&g->exec, g->graph, 0);
+  if (e != cudaSuccess) return snprintf(why, nwhy, "instantiate: %s", cudaGetErrorString(e)), LOF_ERR_CUDA;
+  return LOF_OK;
+}
+
+}  // namespace
+
+extern "C" int lof_graph_create(lof_ctx* c, int dtype, const lof_unit* units, int n_units,
+                                lof_graph** out) {
+  if (!c || !out) return fail(c, LOF_ERR_INVALID, "lof_graph_create: NULL argument");
+  *out = nullptr;
+  DeviceGuard dg(c->device);
+  int rc = validate_units(c, dtype, units, n_units);
+  if (rc) return rc;
+  if (n_units == 0) return fail(c, LOF_ERR_INVALID, "lof_graph_create: no units");
+  char why[512];
+  const lofk::HostCfg h = host_cfg(c);
+  int n_tasks = 0;
+  rc = lofk::host_count_tasks(h, dtype, units, n_units, &n_tasks, why, sizeof why);
+  if (rc) return fail(c, rc, "lof_graph_create: %s", why);
+  std::vector<DevUnit> du(n_units);
+  std::vector<Task> tasks(std::max(1, n_tasks));
+  lofk::Prep pr{};
+  rc = lofk::host_prepare(h, dtype, units, n_units, du.data(), tasks.data(), n_tasks, &pr, why,
+                          sizeof why);
+  if (rc) return fail(c, rc, "lof_graph_create: %s", why);
+  lof_graph* g = new lof_graph();
+  g->ctx = c;
+  g->dtype = dtype;
+  g->n_units = n_units;
+  cudaError_t e;
+  const size_t nus = dtype == LOF_F32 ? 1 : static_cast<size_t>(n_units);
+  if ((e = cudaMalloc(&g->d_units, n_units * sizeof(DevUnit))) != cudaSuccess ||
+      (e = cudaMalloc(&g->d_tasks, std::max(1, pr.n_tasks) * sizeof(Task))) != cudaSuccess ||
+      (e = cudaMalloc(&g->d_ustate, nus * sizeof(UnitState))) != cudaSuccess ||
+      (e = cudaMalloc(&g->d_chanS, std::max<int64_t>(1, pr.n_chan) * 8)) != cudaSuccess ||
+      (e = cudaMalloc(&g->d_chanFc, std::max<int64_t>(1, pr.n_chan))) != cudaSuccess ||
+      (e = cudaMalloc(&g->d_gen, static_cast<size_t>(std::max(1, pr.grid)) * std::max(1, pr.gen_words) * 4)) !=
+          cudaSuccess ||
+      (e = cudaMalloc(&g->d_ctrl, 4 * sizeof(int))) != cudaSuccess ||
+      (e = cudaHostAlloc(&g->h_err, 3 * sizeof(int), cudaHostAllocDefault)) != cudaSuccess ||
+      (e = cudaEventCreateWithFlags(&g->ev_err, cudaEventDisableTiming)) != cudaSuccess) {
+    graph_free(g);
+    return fail(c, LOF_ERR_NOMEM, "lof_graph_create: %s", cudaGetErrorString(e));
+  }
+  if ((e = cudaMemcpy(g->d_units, du.data(), n_units * sizeof(DevUnit), cudaMemcpyHostToDevice)) !=
+          cudaSuccess ||
+      (pr.n_tasks > 0 && (e = cudaMemcpy(g->d_tasks, tasks.data(), pr.n_tasks * sizeof(Task),
+                                         cudaMemcpyHostToDevice)) != cudaSuccess) ||
+      (e = cudaMemset(g->d_ctrl, 0, 4 * sizeof(int))) != cudaSuccess) {
+    graph_free(g);
+    return cuda_fail(c, e, "lof_graph_create: upload");
+  }
+  std::memset(g->h_err, 0, 3 * sizeof(int));
+  // the persistent kernel is launched cooperatively (every CTA resident);
+  // where capture refuses that attribute, the grid is the resident capacity
+  rc = graph_capture(g, h, pr, 1, why, sizeof why);
+  if (rc) {
+    if (g->graph) cudaGraphDestroy(g->graph), g->graph = nullptr;
+    g->knode = nullptr;
+    rc = graph_capture(g, h, pr, 0, why, sizeof why);
+  }
+  if (rc) {
+    graph_free(g);
+    return fail(c, rc, "lof_graph_create: %s", why);
+  }
+  *out = g;
+  return LOF_OK;
+}
+
+extern "C" int lof_graph_launch(lof_graph* g, uint64_t block_seq, void* cuda_stream) {
+  if (!g) return fail(nullptr, LOF_ERR_INVALID, "lof_graph_launch: graph is NULL");
+  lof_ctx* c = g->ctx;
+  DeviceGuard dg(c->device);
+  cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
+  if (g->launched) {  // error of the previous replay, once it has finished
+    const cudaError_t q = cudaEventQuery(g->ev_err);
+    if (q == cudaSuccess && g->h_err[0] != lofk::kErrNone) {
+      const int code = g->h_err[0], i0 = g->h_err[1], i1 = g->h_err[2];
+      g->h_err[0] = 0;
+      cudaMemset(g->d_ctrl + 1, 0, 3 * sizeof(int));
+      if (code == lofk::kErrTimeout)
+        return fail(c, LOF_ERR_TIMEOUT, "device wait timed out (round %d, block %d)", i0, i1);
+      return fail(c, LOF_ERR_STATE, "device error %d (detail %d, block %d)", code, i0, i1);
+    }
+  }
+  g->kp.block_seq = block_seq;
+  cudaKernelNodeParams p = g->kparams;
+  g->kargs[0] = &g->kp;
+  p.kernelParams = g->kargs;
+  cudaError_t e = cudaGraphExecKernelNodeSetParams(g->exec, g->knode, &p);
+  if (e != cudaSuccess) return cuda_fail(c, e, "lof_graph_launch: parameter update");
+  e = cudaGraphLaunch(g->exec, st);
+  if (e != cudaSuccess) return cuda_fail(c, e, "lof_graph_launch");
+  cudaEventRecord(g->ev_err, st);
+  g->launched = true;
+  return LOF_OK;
+}
+
+extern "C" int lof_graph_status(lof_graph* g, void* cuda_stream) {
+  if (!g) return fail(nullptr, LOF_ERR_INVALID, "lof_graph_status: graph is NULL");
+  DeviceGuard dg(g->ctx->device);
+  cudaError_t e = cudaStreamSynchronize(static_cast<cudaStream_t>(cuda_stream));
+  if (e != cudaSuccess) return cuda_fail(g->ctx, e, "lof_graph_status");
+  if (g->launched && cudaEventSynchronize(g->ev_err) == cudaSuccess && g->h_err[0] != lofk::kErrNone) {
+    const int code = g->h_err[0], i0 = g->h_err[1], i1 = g->h_err[2];
+    g->h_err[0] = 0;
+    cudaMemset(g->d_ctrl + 1, 0, 3 * sizeof(int));
+    if (code == lofk::kErrTimeout)
+      return fail(g->ctx, LOF_ERR_TIMEOUT, "device wait timed out (round %d, block %d)", i0, i1);
+    return fail(g->ctx, LOF_ERR_STATE, "device error %d (detail %d, block %d)", code, i0, i1);
+  }
+  return LOF_OK;
+}
+
+extern "C" int lof_graph_destroy(lof_graph* g) {
+  if (!g) return LOF_OK;
+  DeviceGuard dg(g->ctx->device);
+  cudaDeviceSynchronize();
+  graph_free(g);
+  return LOF_OK;
+}
+
+// ------------------------------------------------------------------ autotuner
+
+extern "C" int lof_autotune(lof_ctx* c, int dtype, const lof_unit* units, int n_units, int reps,
+                            void* cuda_stream, lof_tuning* best, float* best_ms) {
+  if (!c) return fail(nullptr, LOF_ERR_INVALID, "lof_autotune: ctx is NULL");
+  DeviceGuard dg(c->device);
+  int rc = validate_units(c, dtype, units, n_units);
+  if (rc) return rc;
+  if (n_units == 0) return fail(c, LOF_ERR_INVALID, "lof_autotune: no units");
+  if (reps < 1) reps = 3;
+  cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
+  const lof_tuning saved = c->tuning;
+  std::vector<lof_tuning> cands;
+  if (dtype == LOF_F32) {
+    cands.push_back(saved);  // one CTA per unit: no launch shape to choose
+  } else {
+    for (int threads : {128, 256})
+      for (int ctas : {1, 2, 3, 4})
+        for (int rows : {8, 16, 32})
+          for (int samples : {32768, 65536, 131072})
+            cands.push_back(lof_tuning{threads, ctas, saved.tile_bytes, saved.fine_bins, rows, samples});
+  }
+  cudaEvent_t e0, e1;
+  cudaEventCreate(&e0);
+  cudaEventCreate(&e1);
+  float best_t = 1e30f;
+  lof_tuning best_c = saved;
+  std::vector<float> ts(reps);
+  for (const lof_tuning& t : cands) {
+    c->tuning = t;
+    if (lof_flag_block(c, dtype, units, n_units, 0, st) != LOF_OK) continue;  // warm-up
+    bool ok = true;
+    for (int r = 0; r < reps && ok; ++r) {
+      cudaEventRecord(e0, st);
+      ok = lof_flag_block(c, dtype, units, n_units, 0, st) == LOF_OK;
+      cudaEventRecord(e1, st);
+      cudaEventSynchronize(e1);
+      cudaEventElapsedTime(&ts[r], e0, e1);
+    }
+    if (!ok || lof_status(c, st) != LOF_OK) continue;
+    std::vector<float> srt(ts);
+    std::sort(srt.begin(), srt.end());
+    const float med = srt[reps / 2];
+    if (med < best_t) {
+      best_t = med;
+      best_c = t;
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  c->tuning = best_c;
+  c->last_error.clear();
+  if (best) *best = best_c;
+  if (best_ms) *best_ms = best_t;
+  return best_t < 1e30f ? LOF_OK : fail(c, LOF_ERR_CUDA, "lof_autotune: no candidate ran");
 }

@@ -140,6 +140,8 @@ struct KParams {
   uint64_t block_seq;
   long long spin_limit;         // bound of every device-side wait (ns)
   int dyn_smem;                 // dynamic shared memory of each CTA (bytes)
+  uint32_t* gen_scratch;        // general time-pass rows, gen_words per CTA
+  int gen_words;
 };
 
 struct CommitParams {
@@ -163,6 +165,7 @@ struct Prep {
   Plan plan;
   int n_tasks, grid;
   int64_t n_chan;
+  int gen_words;                 // per CTA, general time-pass rows
 };
 // Device memory one launch works in.
 struct Scratch {
@@ -173,6 +176,7 @@ struct Scratch {
   uint8_t* chanFc;
   int* ctrl;  // [0] queue, [1] error, [2..3] detail
   HistoryDev hist;
+  uint32_t* gen;  // general time-pass rows: grid x gen_words words
 };
 // lof_api.cu: heap-free steps shared by every entry point
 int host_check_dtype(int dtype, char* why, int nwhy);
@@ -184,6 +188,9 @@ int host_prepare(const HostCfg& h, int dtype, const lof_unit* units, int n_units
 int host_launch(const lof_params& P, const HostCfg& h, int dtype, const Prep& pr, const Scratch& sc,
                 const DevUnit* du_host, int n_units, const Task* tasks_host, uint64_t seq,
                 void* stream, char* why, int nwhy);
+int host_launch_kernel(const lof_params& P, const HostCfg& h, int dtype, const Prep& pr,
+                       const Scratch& sc, int n_units, uint64_t seq, void* stream, int cooperative,
+                       char* why, int nwhy);
 
 }  // namespace lofk
 

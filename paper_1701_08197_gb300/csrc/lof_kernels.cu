@@ -1961,12 +1961,13 @@ __device__ void task_flag(const KParams& kp, const DevUnit& u, UnitState* us, co
   const int MW = nch + 4;  // flag words per row, two zero words on each side
   const int nseg = (T + SEG - 1) / SEG;
   const StLayout L = st_layout(nch);
-  // shared workspace: Rb rows of prefix (general path), the flag words of
-  // the task's R rows, Rb rows of fire words
-  const int Rb = max(1, min(R, (kp.dyn_smem / 4 - R * MW) / (L.per_row + MW)));
-  uint32_t* const spfx = reinterpret_cast<uint32_t*>(ws);
-  uint32_t* const smbits = spfx + Rb * L.per_row;
-  uint32_t* const sfbits = smbits + R * MW;
+  // shared memory: the flag words of the task's R rows.  The general
+  // (any-magnitude) path keeps Rb rows of prefix and of fire words in this
+  // CTA's region of a global scratch (L2-resident; the path is rare).
+  uint32_t* const smbits = reinterpret_cast<uint32_t*>(ws);
+  uint32_t* const spfx = kp.gen_scratch + static_cast<int64_t>(blockIdx.x) * kp.gen_words;
+  const int Rb = max(1, min(R, kp.gen_words / (L.per_row + MW)));
+  uint32_t* const sfbits = spfx + Rb * L.per_row;
   const uint8_t* gin = static_cast<const uint8_t*>(u.in);
   if (tid == 0) {
     if (!wait_geq(kp, &us->ready, 2, 400)) f.ok = 0;

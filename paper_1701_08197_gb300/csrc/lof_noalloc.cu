@@ -98,7 +98,7 @@ extern "C" int lof_flag_block_noalloc(const lof_params* params, int dtype, const
   cudaDeviceGetAttribute(&h.n_sm, cudaDevAttrMultiProcessorCount, dev);
   cudaDeviceGetAttribute(&h.smem_per_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev);
   cudaDeviceGetAttribute(&h.smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
-  h.tuning = lof_tuning{128, 4, 0, 2048};
+  h.tuning = lof_tuning{128, 4, 0, 2048, 0, 0};
   int n_tasks = 0;
   rc = lofk::host_count_tasks(h, dtype, units, n_units, &n_tasks, why, sizeof why);
   if (rc) return fail(rc);
@@ -127,7 +127,9 @@ extern "C" int lof_flag_block_noalloc(const lof_params* params, int dtype, const
   sc.chanFc = base + off;
   off += up256(static_cast<size_t>(pr.n_chan));
   sc.ustate = reinterpret_cast<lofk::UnitState*>(base + off);
-  off += static_cast<size_t>(dtype == LOF_F32 ? 0 : n_units) * sizeof(lofk::UnitState);
+  off += up256(static_cast<size_t>(dtype == LOF_F32 ? 0 : n_units) * sizeof(lofk::UnitState));
+  sc.gen = reinterpret_cast<uint32_t*>(base + off);
+  off += static_cast<size_t>(std::max(1, pr.grid)) * std::max(1, pr.gen_words) * 4;
   if (off > kScratchBytes) {
     snprintf(why, sizeof why,
              "lof_flag_block_noalloc: the block needs %zu bytes of scratch, the static array holds %zu",

@@ -26,7 +26,8 @@ EXPORTED = [
     "lof_default_params", "lof_create", "lof_flag_block", "lof_flag_block_host",
     "lof_history_update", "lof_history_export", "lof_history_import", "lof_status",
     "lof_max_time", "lof_set_tuning", "lof_get_tuning", "lof_last_error", "lof_destroy",
-    "lof_flag_block_noalloc",
+    "lof_flag_block_noalloc", "lof_autotune", "lof_graph_create", "lof_graph_launch",
+    "lof_graph_status", "lof_graph_destroy",
 ]
 
 
@@ -84,6 +85,8 @@ class lof_tuning(ctypes.Structure):
         ("ctas_per_sm", ctypes.c_int32),
         ("tile_bytes", ctypes.c_int32),
         ("fine_bins", ctypes.c_int32),
+        ("flag_rows", ctypes.c_int32),
+        ("stat_samples", ctypes.c_int32),
     ]
 
 
@@ -122,9 +125,17 @@ def library(build: bool = True):
     L.lof_last_error.restype = ctypes.c_char_p
     L.lof_destroy.argtypes = [V]
     L.lof_flag_block_noalloc.argtypes = [P(lof_params), ctypes.c_int, P(lof_unit), ctypes.c_int, V, V]
+    L.lof_autotune.argtypes = [V, ctypes.c_int, P(lof_unit), ctypes.c_int, ctypes.c_int, V,
+                               P(lof_tuning), P(ctypes.c_float)]
+    L.lof_graph_create.argtypes = [V, ctypes.c_int, P(lof_unit), ctypes.c_int, P(V)]
+    L.lof_graph_launch.argtypes = [V, ctypes.c_uint64, V]
+    L.lof_graph_status.argtypes = [V, V]
+    L.lof_graph_destroy.argtypes = [V]
     for name in ("lof_create", "lof_flag_block", "lof_flag_block_host", "lof_history_update",
                  "lof_history_export", "lof_history_import", "lof_status", "lof_max_time",
-                 "lof_set_tuning", "lof_get_tuning", "lof_destroy", "lof_flag_block_noalloc"):
+                 "lof_set_tuning", "lof_get_tuning", "lof_destroy", "lof_flag_block_noalloc",
+                 "lof_autotune", "lof_graph_create", "lof_graph_launch", "lof_graph_status",
+                 "lof_graph_destroy"):
         getattr(L, name).restype = ctypes.c_int
     _lib = L
     return L
@@ -203,8 +214,9 @@ def lof_max_time(ctx, dtype: int) -> int:
     return library().lof_max_time(ctx, dtype)
 
 
-def lof_set_tuning(ctx, threads=0, ctas_per_sm=0, tile_bytes=0, fine_bins=0) -> int:
-    t = lof_tuning(threads, ctas_per_sm, tile_bytes, fine_bins)
+def lof_set_tuning(ctx, threads=0, ctas_per_sm=0, tile_bytes=0, fine_bins=0, flag_rows=0,
+                   stat_samples=0) -> int:
+    t = lof_tuning(threads, ctas_per_sm, tile_bytes, fine_bins, flag_rows, stat_samples)
     return library().lof_set_tuning(ctx, ctypes.byref(t))
 
 
@@ -333,6 +345,19 @@ class Flagger:
     def tuning(self) -> dict:
         return lof_get_tuning(self.ctx)
 
+    def autotune(self, dtype: int, units, reps: int = 3, stream=None):
+        """Pick the fastest launch shape for these units; returns (tuning dict, ms)."""
+        arr = (lof_unit * len(units))(*units)
+        best = lof_tuning()
+        ms = ctypes.c_float()
+        _check(library().lof_autotune(self.ctx, dtype, arr, len(units), reps, self._stream(stream),
+                                      ctypes.byref(best), ctypes.byref(ms)), self.ctx)
+        return {k: getattr(best, k) for k, _ in lof_tuning._fields_}, ms.value
+
+    def graph(self, dtype: int, units):
+        """Capture the block of these units (fixed buffers) as a replayable graph."""
+        return Graph(self, dtype, units)
+
     def max_time(self, dtype: int) -> int:
         return lof_max_time(self.ctx, dtype)
 
@@ -349,3 +374,39 @@ class Flagger:
         cnt = np.ascontiguousarray(counts, np.int32)
         _check(lof_history_import(self.ctx, slot0, cnt.size, vals.ctypes.data, cnt.ctypes.data),
                self.ctx)
+
+
+class Graph:
+    """A captured block (lof_graph_*): replay with launch(block_seq)."""
+
+    def __init__(self, flagger: "Flagger", dtype: int, units):
+        self.fl = flagger
+        self.units = list(units)
+        arr = (lof_unit * len(self.units))(*self.units)
+        h = ctypes.c_void_p()
+        _check(library().lof_graph_create(flagger.ctx, dtype, arr, len(self.units), ctypes.byref(h)),
+               flagger.ctx)
+        self.h = h
+
+    def launch(self, block_seq: int = 0, stream=None):
+        _check(library().lof_graph_launch(self.h, block_seq, Flagger._stream(stream)), self.fl.ctx)
+
+    def status(self, stream=None):
+        _check(library().lof_graph_status(self.h, Flagger._stream(stream)), self.fl.ctx)
+
+    def close(self):
+        if self.h:
+            library().lof_graph_destroy(self.h)
+            self.h = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
