@@ -95,6 +95,32 @@ def evaluate(n_subband=64, n_block=4, seed=4, n_bin=256, device="cuda:0", flagge
     return {k: {"snr": folders[k].snr(spec.duty), "flagged_fraction": frac[k]} for k in folders}
 
 
+def time_block(n_subband=488, seed=4, reps=5, device="cuda:0"):
+    """Flag-kernel time of one full Stokes I block (CUDA events, median)."""
+    dev = torch.device(device)
+    spec = synth.PulsarSpec(n_subband=n_subband)
+    x = synth.stokes_block(spec, seed=seed, block=0, device=dev).contiguous()
+    out = torch.empty_like(x)
+    mask = torch.empty(x.shape, dtype=torch.uint8, device=dev)
+    with lof.Flagger(dev.index or 0) as fl:
+        units = [lof.make_unit(x[s], out[s], mask[s]) for s in range(n_subband)]
+        st = torch.cuda.current_stream()
+        fl.flag_block(lof.LOF_F32, units, 0)
+        fl.status()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        ts = []
+        for _ in range(reps):
+            e0.record(st)
+            fl.flag_block(lof.LOF_F32, units, 0)
+            e1.record(st)
+            e1.synchronize()
+            ts.append(e0.elapsed_time(e1))
+        fl.status()
+    ms = sorted(ts)[reps // 2]
+    n = x.numel()
+    return {"ms": ms, "Msamples_s": n / ms / 1e3, "GBs_9B_per_sample": 9 * n / ms / 1e6}
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--subbands", type=int, default=488)
@@ -104,7 +130,7 @@ def main():
     res = evaluate(args.subbands, args.blocks, args.seed)
     print(json.dumps({"workload": f"Stokes I {args.subbands} sb x 16 ch x 12288 t, {args.blocks} "
                                   f"blocks, chi2(4) noise, pulsar P=0.714 s DM=26.8, seed {args.seed}",
-                      "folded_snr": res}))
+                      "folded_snr": res, "flag_block": time_block(args.subbands, args.seed)}))
 
 
 if __name__ == "__main__":
