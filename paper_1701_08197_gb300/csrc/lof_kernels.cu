@@ -25,6 +25,15 @@
 
 #include "lof_internal.h"
 
+// The task bodies of the complex-int8 kernel are separate functions: its
+// wider unpacking of 16-byte vectors otherwise exhausts the register budget
+// of the inlined whole (spills); the int16 kernel inlines them.
+#if defined(LOF_KERNEL_DT) && LOF_KERNEL_DT == 1
+#define LOFK_TASK_FN __noinline__
+#else
+#define LOFK_TASK_FN __forceinline__
+#endif
+
 namespace lofk {
 namespace {
 
@@ -1413,12 +1422,77 @@ __device__ __forceinline__ int wr_seg_count(int T) {
   return n;
 }
 
+// Output of one row for the fused writer of the warp-row pass.
+struct WrOut {
+  uint8_t* out;   // masked data row (NULL: none)
+  uint8_t* mask;  // mask row (NULL: none)
+  bool enabled, inplace, vout, mask_vec, vin;
+};
+
+// Mask bytes and masked data of the 32 samples [x, x + 32) of one row, from
+// their flag word m (one lane; bits past T are zero).
+template <int DT>
+__device__ __forceinline__ void wr_write_word(const WrOut& o, const uint8_t* grow, int x, int T,
+                                              uint32_t m) {
+  using TR = Traits<DT>;
+  constexpr int VS = TR::kVec;
+  const int nv = min(32, T - x);
+  if (o.mask) {
+    if (o.mask_vec && nv == 32) {
+      uint32_t w[8];
+#pragma unroll
+      for (int q = 0; q < 8; ++q) w[q] = (((m >> (4 * q)) & 0xFu) * 0x00204081u) & 0x01010101u;
+      st_stream_u64(o.mask + x, w[0], w[1]);
+      st_stream_u64(o.mask + x + 8, w[2], w[3]);
+      st_stream_u64(o.mask + x + 16, w[4], w[5]);
+      st_stream_u64(o.mask + x + 24, w[6], w[7]);
+    } else {
+      for (int j = 0; j < nv; ++j) o.mask[x + j] = static_cast<uint8_t>((m >> j) & 1u);
+    }
+  }
+  if (!o.out) return;
+  if (o.inplace) {
+    uint32_t mm = m;
+    while (mm) {
+      const int j = __ffs(mm) - 1;
+      mm &= mm - 1u;
+      TR::zero(o.out, x + j);
+    }
+    return;
+  }
+  if (o.vin && o.vout && nv == 32) {
+    const uint64_t pol = l2_policy_drop();
+#pragma unroll
+    for (int q = 0; q < 32 / VS; ++q) {
+      uint4 v = ldg_policy(grow + static_cast<size_t>(x + q * VS) * TR::kBytes, pol);
+      const uint32_t bits = (m >> (q * VS)) & ((1u << VS) - 1u);
+      if (bits) {
+        uint32_t wd[4] = {v.x, v.y, v.z, v.w};
+#pragma unroll
+        for (int j = 0; j < VS; ++j) {
+          if ((bits >> j) & 1u) {
+            if constexpr (VS == 4) wd[j] = 0u;
+            else wd[j >> 1] &= (j & 1) ? 0x0000FFFFu : 0xFFFF0000u;
+          }
+        }
+        v = make_uint4(wd[0], wd[1], wd[2], wd[3]);
+      }
+      __stcs(reinterpret_cast<uint4*>(o.out + static_cast<size_t>(x + q * VS) * TR::kBytes), v);
+    }
+    return;
+  }
+  for (int j = 0; j < nv; ++j) {
+    if ((m >> j) & 1u) TR::zero(o.out, x + j);
+    else TR::copy(o.out + static_cast<size_t>(x + j) * TR::kBytes, grow + static_cast<size_t>(x + j) * TR::kBytes);
+  }
+}
+
 // Time pass of segment sg of one row by one warp.  Writes the flag words of
 // the segment's interior to M_out (the row's words) and returns, in every
 // lane, the interior's number of flagged samples and sum of unflagged powers.
 template <int DT, int NPL>
 __device__ void wr_segment(const uint8_t* grow, int T, int sg, bool vin, int kmax,
-                           const uint32_t* s_Kp, uint32_t* M_out,
+                           const uint32_t* s_Kp, uint32_t* M_out, const WrOut& o,
                            int& n_flag, unsigned long long& sum_unflagged) {
   constexpr int NW = NPL / 32, SPAN = 32 * NPL;
   const int lane = threadIdx.x & 31;
@@ -1443,7 +1517,10 @@ __device__ void wr_segment(const uint8_t* grow, int T, int sg, bool vin, int kma
     }
     wr_apply<NPL>(R, lane, vend - I + 1 - xl, I, F);
   }
-  // interior words [oa, ob): flag words, counts and sums of unflagged powers
+  // interior words [oa, ob): flag words, counts and sums of unflagged powers,
+  // and (when an output is given) the mask bytes and the masked data of the
+  // interior, written while the rows are hot in L1 (a row that the history
+  // test flags whole is rewritten afterwards)
   int nfl = 0;
   unsigned long long su = 0;
 #pragma unroll
@@ -1456,6 +1533,7 @@ __device__ void wr_segment(const uint8_t* grow, int T, int sg, bool vin, int kma
 #pragma unroll
       for (int b = 0; b < 32; ++b) s += R.u[32 * w + b];
       su += s - static_cast<uint32_t>(__popc(R.M[w])) * kZ;
+      if (o.enabled) wr_write_word<DT>(o, grow, x, T, R.M[w]);
     }
   }
   n_flag = __reduce_add_sync(kFull, nfl);
@@ -1598,7 +1676,7 @@ __device__ void unit_moments(const KParams& kp, const DevUnit& u, UnitState* us,
 // histogram of the kept channels and the selection plan.  Releases the unit
 // with ready = 1 (fine counts needed) or 2 (statistics final).
 template <int DT, int NT>
-__device__ void unit_round1(const KParams& kp, const DevUnit& u, UnitState* us, uint8_t* ws,
+__device__ LOFK_TASK_FN void unit_round1(const KParams& kp, const DevUnit& u, UnitState* us, uint8_t* ws,
                             Fixed<NT>& f) {
   using TR = Traits<DT>;
   constexpr int NW = NT / kWarp;
@@ -1768,7 +1846,7 @@ __device__ void unit_round1(const KParams& kp, const DevUnit& u, UnitState* us, 
 // After the last fine task of a unit: merge the counts, plan again; further
 // rounds (rare) are counted here over every kept row of the unit.
 template <int DT, int NT>
-__device__ void unit_round2(const KParams& kp, const DevUnit& u, UnitState* us, uint8_t* ws,
+__device__ LOFK_TASK_FN void unit_round2(const KParams& kp, const DevUnit& u, UnitState* us, uint8_t* ws,
                             Fixed<NT>& f) {
   for (int guard = 0;; ++guard) {
     merge_fine<NT>(kp, us, ws, f);
@@ -1792,10 +1870,10 @@ __device__ void unit_round2(const KParams& kp, const DevUnit& u, UnitState* us, 
 
 // Stats task: row power sums (spectrum) and the coarse histogram of its rows.
 template <int DT, int NT>
-__device__ void task_stats(const KParams& kp, const DevUnit& u, UnitState* us, const Task& tk,
+__device__ LOFK_TASK_FN void task_stats(const KParams& kp, const DevUnit& u, UnitState* us, const Task& tk,
                            uint8_t* ws, Fixed<NT>& f) {
   using TR = Traits<DT>;
-  constexpr int VS = TR::kVec, NQ = 8, SEG = 32 * NQ * VS, NW = NT / kWarp;
+  constexpr int VS = TR::kVec, NQ = 32 / VS, SEG = 32 * NQ * VS, NW = NT / kWarp;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int T = u.T, R = tk.nrows, row0 = tk.row0, nseg = (T + SEG - 1) / SEG;
   const bool vin = (u.flags & kUnitInVec) != 0;
@@ -1928,7 +2006,7 @@ __device__ void task_stats(const KParams& kp, const DevUnit& u, UnitState* us, c
 // Fine task: exact counts in the refined bins for its kept rows (skipped when
 // the first round already made the statistics exact).
 template <int DT, int NT>
-__device__ void task_fine(const KParams& kp, const DevUnit& u, UnitState* us, const Task& tk,
+__device__ LOFK_TASK_FN void task_fine(const KParams& kp, const DevUnit& u, UnitState* us, const Task& tk,
                           uint8_t* ws, Fixed<NT>& f) {
   const int tid = threadIdx.x;
   if (tid == 0) {
@@ -1951,7 +2029,7 @@ __device__ void task_fine(const KParams& kp, const DevUnit& u, UnitState* us, co
 // Flag task: SumThreshold in time on its kept rows (Section 2.1), the history
 // test (Section 4.1), the mask and the masked data.
 template <int DT, int NT>
-__device__ void task_flag(const KParams& kp, const DevUnit& u, UnitState* us, const Task& tk,
+__device__ LOFK_TASK_FN void task_flag(const KParams& kp, const DevUnit& u, UnitState* us, const Task& tk,
                           uint8_t* ws, Fixed<NT>& f, uint32_t* s_Kp) {
   using TR = Traits<DT>;
   constexpr int VS = TR::kVec, SEG = 64 * VS, NW = NT / kWarp;
@@ -2027,7 +2105,16 @@ __device__ void task_flag(const KParams& kp, const DevUnit& u, UnitState* us, co
         const uint8_t* grow = gin + static_cast<int64_t>(row0 + r) * u.in_stride * TR::kBytes;
         int nfl = 0;
         unsigned long long su = 0;
-        wr_segment<DT, kWrNpl>(grow, T, sg, vin, f.kmax_t, s_Kp, smbits + r * MW + 2, nfl,
+        WrOut o;
+        o.out = u.out ? static_cast<uint8_t*>(u.out) + static_cast<int64_t>(row0 + r) * u.out_stride * TR::kBytes
+                      : nullptr;
+        o.mask = u.mask ? u.mask + static_cast<int64_t>(row0 + r) * u.mask_stride : nullptr;
+        o.enabled = o.out != nullptr || o.mask != nullptr;
+        o.inplace = (u.flags & kUnitInPlace) != 0;
+        o.vout = (u.flags & kUnitOutVec) != 0;
+        o.mask_vec = (u.flags & kUnitMaskVec) != 0;
+        o.vin = vin;
+        wr_segment<DT, kWrNpl>(grow, T, sg, vin, f.kmax_t, s_Kp, smbits + r * MW + 2, o, nfl,
                                su);
         if (lane == 0) {
           atomicAdd(&f.rowNFlag[r], nfl);
@@ -2152,9 +2239,13 @@ __device__ void task_flag(const KParams& kp, const DevUnit& u, UnitState* us, co
     constexpr int NQO = 16 / VS, SEGO = 32 * NQO * VS;
     const int nsego = (T + SEGO - 1) / SEGO;
     const uint64_t pol_drop = l2_policy_drop();
+    // rows of the packed time pass were written by the warps that flagged
+    // them; only rows flagged whole (frequency pass, history test) remain
+    const bool fused = f.time_on && f.state == 1;
     for (int task = warp; task < R * nsego; task += NW) {
       const int r = task / nsego, s = task - r * nsego;
       const bool full = f.rowFc[r] || f.rowFh[r];
+      if (fused && !full) continue;
       const uint32_t* M = smbits + r * MW + 2;
       const int64_t grow_idx = static_cast<int64_t>(row0 + r);
       uint4 win[NQO];
