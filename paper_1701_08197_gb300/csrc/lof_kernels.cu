@@ -386,7 +386,7 @@ __device__ int spec_targets(unsigned long long m2, unsigned long long mad4, Targ
 template <int NT>
 struct Fixed {
   uint64_t mbar;
-  int item, ok, last, state, n_keep, n_tgt, q_done, n_def;
+  int item, ok, last, state, n_keep, n_tgt, q_done, n_def, rows_done;
   int def[9];  // parked tasks whose unit was not ready
   unsigned int red_u32[NT / kWarp];
   unsigned long long red_a[NT / kWarp], red_b[NT / kWarp], red_c[NT / kWarp];
@@ -2026,6 +2026,58 @@ __device__ LOFK_TASK_FN void task_fine(const KParams& kp, const DevUnit& u, Unit
   if (f.last) unit_round2<DT, NT>(kp, u, us, ws, f);
 }
 
+// History test of one row (Section 4.1): the mean of its unflagged powers
+// against the cached threshold of its ring; stages the value for the commit
+// and adds the row to the task's counts.  One thread; returns whether the
+// whole row is flagged.
+template <int NT>
+__device__ __forceinline__ int history_row(const KParams& kp, const DevUnit& u, int c, int T,
+                                           int nfl, unsigned long long su, Fixed<NT>& f) {
+  const long long h = u.hist_slot >= 0 ? u.hist_slot + c : -1;
+  const int n = T - nfl;
+  int fh = 0;
+  if (n > 0) {
+    const double cur = __ddiv_rn(__ull2double_rn(su), static_cast<double>(n));
+    double staged = cur;
+    if (kp.enable_history && h >= 0) {
+      const int cnt = kp.hist.count[h];
+      if (cnt >= kp.history_min && cnt > 0) {
+        const double thr = kp.hist.thr[h];
+        if (!(cur < thr)) {
+          fh = 1;
+          staged = thr;
+        }
+      }
+    }
+    if (h >= 0) {
+      kp.hist.pend[h] = staged;
+      kp.hist.pend_flag[h] = 1;
+      kp.hist.pend_seq[h] = kp.block_seq;
+    }
+  } else if (h >= 0) {
+    kp.hist.pend_flag[h] = 0;
+  }
+  atomicAdd(&f.cnt_time, static_cast<unsigned long long>(nfl));
+  if (fh) atomicAdd(&f.cnt_hist, 1ull);
+  atomicAdd(&f.cnt_total, fh ? static_cast<unsigned long long>(T) : static_cast<unsigned long long>(nfl));
+  return fh;
+}
+
+// A row flagged whole: mask all ones, data all zero.  One warp.
+template <int DT>
+__device__ void write_row_flagged(const DevUnit& u, int c, int T) {
+  using TR = Traits<DT>;
+  const int lane = threadIdx.x & 31;
+  if (u.mask) {
+    uint8_t* mr = u.mask + static_cast<int64_t>(c) * u.mask_stride;
+    for (int x = lane; x < T; x += 32) mr[x] = 1;
+  }
+  if (u.out) {
+    uint8_t* orow = static_cast<uint8_t*>(u.out) + static_cast<int64_t>(c) * u.out_stride * TR::kBytes;
+    for (int x = lane; x < T; x += 32) TR::zero(orow, x);
+  }
+}
+
 // Flag task: SumThreshold in time on its kept rows (Section 2.1), the history
 // test (Section 4.1), the mask and the masked data.
 template <int DT, int NT>
@@ -2062,6 +2114,7 @@ __device__ LOFK_TASK_FN void task_flag(const KParams& kp, const DevUnit& u, Unit
   }
   for (int i = tid; i < R * MW; i += NT) smbits[i] = 0u;
   if (tid == 0) {
+    f.rows_done = 0;
     f.time_on = __ldcg(&us->time_on);
     int kmax = 0;
     while (kmax < kp.max_log_window && (2 << kmax) <= T) ++kmax;
@@ -2096,15 +2149,14 @@ __device__ LOFK_TASK_FN void task_flag(const KParams& kp, const DevUnit& u, Unit
   // ---- time pass over the kept rows of the task
   if (f.time_on && nkeep > 0) {
     if (f.state == 1) {
-      // packed values: one warp per row segment, the segment in registers
+      // packed values: one warp per row (its segments one after the other,
+      // each in registers, mask and data written as soon as they are final),
+      // then the row's history test and, when it fires, the whole row flagged
       const bool vin = (u.flags & kUnitInVec) != 0;
       const int nsg = wr_seg_count<kWrNpl>(T);
-      for (int item = warp; item < nkeep * nsg; item += NW) {
-        const int kr = item / nsg, sg = item - kr * nsg;
+      for (int kr = warp; kr < nkeep; kr += NW) {
         const int r = f.keep[kr];
         const uint8_t* grow = gin + static_cast<int64_t>(row0 + r) * u.in_stride * TR::kBytes;
-        int nfl = 0;
-        unsigned long long su = 0;
         WrOut o;
         o.out = u.out ? static_cast<uint8_t*>(u.out) + static_cast<int64_t>(row0 + r) * u.out_stride * TR::kBytes
                       : nullptr;
@@ -2114,16 +2166,24 @@ __device__ LOFK_TASK_FN void task_flag(const KParams& kp, const DevUnit& u, Unit
         o.vout = (u.flags & kUnitOutVec) != 0;
         o.mask_vec = (u.flags & kUnitMaskVec) != 0;
         o.vin = vin;
-        wr_segment<DT, kWrNpl>(grow, T, sg, vin, f.kmax_t, s_Kp, smbits + r * MW + 2, o, nfl,
-                               su);
-        if (lane == 0) {
-          atomicAdd(&f.rowNFlag[r], nfl);
-          atomicAdd(&f.rowFlagSum[r], 0ull - su);
+        int nfl_row = 0;
+        unsigned long long su_row = 0;
+        for (int sg = 0; sg < nsg; ++sg) {
+          int nfl = 0;
+          unsigned long long su = 0;
+          wr_segment<DT, kWrNpl>(grow, T, sg, vin, f.kmax_t, s_Kp, smbits + r * MW + 2, o, nfl, su);
+          nfl_row += nfl;
+          su_row += su;
+        }
+        int fh = 0;
+        if (lane == 0) fh = history_row<NT>(kp, u, row0 + r, T, nfl_row, su_row, f);
+        fh = __shfl_sync(kFull, fh, 0);
+        if (fh) {
+          __syncwarp();
+          write_row_flagged<DT>(u, row0 + r, T);
         }
       }
-      __syncthreads();
-      // rowS - rowFlagSum = sum_unflagged
-      for (int kr = tid; kr < nkeep; kr += NT) f.rowFlagSum[f.keep[kr]] += f.rowS[f.keep[kr]];
+      if (tid == 0) f.rows_done = 1;
       __syncthreads();
     } else {
       // any magnitudes: exact 64-bit window sums over a shared-memory prefix,
@@ -2187,8 +2247,11 @@ __device__ LOFK_TASK_FN void task_flag(const KParams& kp, const DevUnit& u, Unit
       }
     }
   }
-  // ---- history flagger (Section 4.1) and per-row counts
+  // ---- history flagger (Section 4.1) and per-row counts (rows the packed
+  // time pass has not finished)
+  const bool rows_done = f.rows_done != 0;
   for (int r = tid; r < R; r += NT) {
+    if (rows_done && !f.rowFc[r]) continue;
     const long long h = u.hist_slot >= 0 ? u.hist_slot + row0 + r : -1;
     unsigned long long add_total;
     if (f.rowFc[r]) {
@@ -2241,7 +2304,7 @@ __device__ LOFK_TASK_FN void task_flag(const KParams& kp, const DevUnit& u, Unit
     const uint64_t pol_drop = l2_policy_drop();
     // rows of the packed time pass were written by the warps that flagged
     // them; only rows flagged whole (frequency pass, history test) remain
-    const bool fused = f.time_on && f.state == 1;
+    const bool fused = rows_done;
     for (int task = warp; task < R * nsego; task += NW) {
       const int r = task / nsego, s = task - r * nsego;
       const bool full = f.rowFc[r] || f.rowFh[r];
