@@ -39,10 +39,10 @@ METRIC = "input Msamples/s (full LOFAR pre-beamformer block, 768 units x 256 ch 
 PROFILE = os.path.join(ROOT, "profiles", "lof_block_kernel_ci16_full_station.md")
 
 
-def measured_traffic(n_units):
+def measured_traffic(n_units, tuning):
     """DRAM bytes per launch of the block kernel from the committed ncu summary
-    (read + write bytes per unit x units), or None when the kernel sources have
-    changed since the counters were taken."""
+    (read + write bytes per unit x units), or None when the kernel sources or
+    the launch shape differ from the ones the counters were taken with."""
     import hashlib
     try:
         text = open(PROFILE).read()
@@ -64,7 +64,15 @@ def measured_traffic(n_units):
         h = hashlib.sha256(open(os.path.join(csrc, f), "rb").read()).hexdigest()
         if kv.get(key) != h:
             return None
+    def shape(t):
+        # resident CTAs per SM are capped by the kernel's launch bounds
+        cap = 4 if int(t["threads"]) == 128 else 2
+        return (int(t["threads"]), min(int(t["ctas_per_sm"]), cap), int(t["tile_bytes"]),
+                int(t["fine_bins"]), int(t["flag_rows"]), int(t["stat_samples"]))
     try:
+        taken = dict(f.split("=") for f in kv["tuning"].split())
+        if shape(taken) != shape(tuning):
+            return None
         return int(kv["traffic_bytes_per_unit"]) * n_units
     except (KeyError, ValueError):
         return None
@@ -79,6 +87,7 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-plain", action="store_true")
+    ap.add_argument("--no-autotune", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--stations", type=int, default=48,
                     help="stations per block (48 = the full configuration; fewer for profiling)")
@@ -240,6 +249,11 @@ def run_gpu(args):
         fl.flag_block(lof.LOF_CI16, units, seq, stream)
         fl.history_update(units, stream)
 
+    # launch shape from the autotuner (untimed; results do not depend on it)
+    tuning = None
+    if not args.no_autotune:
+        tuning, _ = fl.autotune(lof.LOF_CI16, units, reps=2, stream=stream)
+        torch.cuda.synchronize()
     with torch.cuda.stream(stream):
         for i in range(args.warmup):
             step(i)
@@ -273,7 +287,8 @@ def run_gpu(args):
     t_max = max_over_ranks(total_ms, world, dev)
     value = job_msamples_per_s(samples, world, args.steps, t_max)
     res = {"rank": rank, "value": value, "ms_per_step": t_max / args.steps, "step_ms": step_ms,
-           "kern_ms": kern_ms, "clocks": clk.summary(), "samples": samples}
+           "kern_ms": kern_ms, "clocks": clk.summary(), "samples": samples,
+           "tuning": tuning or fl.tuning()}
 
     # plain form: one launch per station-subband (its two polarisations)
     if not args.no_plain and rank == 0:
@@ -417,9 +432,9 @@ def main():
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": res["ms_per_step"],
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int32/u64",
         "data": "synthetic (seeded noise + tones + impulses)",
-        "config": workload_config(args.stations),
+        "config": dict(workload_config(args.stations), tuning=res["tuning"]),
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                     "frac": achieved / peak, "traffic": measured_traffic(args.stations * 16),
+                     "frac": achieved / peak, "traffic": measured_traffic(args.stations * 16, res["tuning"]),
                      "kernel": "lof_block_kernel<CI16>", "bytes_per_launch": alg_bytes,
                      "kernel_ms": kern_avg, "peak_kind": peak_kind},
         "latency_ms": {"batched_p50": pct(step_sorted, 0.5), "batched_p99": pct(step_sorted, 0.99),

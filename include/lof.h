@@ -179,12 +179,12 @@ int lof_max_time(const lof_ctx *ctx, int dtype);
 /* Launch-shape knobs (an autotuner sweeps them; results do not depend on
  * them).  0 keeps the current value. */
 typedef struct {
-  int32_t threads;         /* threads per CTA: 128 (default) or 256 */
-  int32_t ctas_per_sm;     /* resident CTAs per SM: 1 to 4 (default 4) */
+  int32_t threads;         /* threads per CTA: 128 or 256 (default) */
+  int32_t ctas_per_sm;     /* resident CTAs per SM: 1 to 4 (default 2) */
   int32_t tile_bytes;      /* cap on the shared-memory bytes of a CTA */
   int32_t fine_bins;       /* counters per exact-selection refinement round */
-  int32_t flag_rows;       /* rows per time-pass task (tile height), 1..64; 0 = 4 per warp */
-  int32_t stat_samples;    /* samples per statistics task, >= 1024; 0 = 65536 */
+  int32_t flag_rows;       /* rows per time-pass task (tile height), 1..64 (default 32) */
+  int32_t stat_samples;    /* samples per statistics task, >= 1024 (default 131072) */
 } lof_tuning;
 int lof_set_tuning(lof_ctx *ctx, const lof_tuning *t);
 int lof_get_tuning(const lof_ctx *ctx, lof_tuning *t);

@@ -46,7 +46,7 @@ struct lof_ctx {
   lof_params params{};
   int n_sm = 0;
   int smem_per_sm = 0, smem_optin = 0;
-  lof_tuning tuning{128, 4, 0, 2048, 0, 0};
+  lof_tuning tuning{256, 2, 0, 2048, 32, 131072};
   // history
   int64_t n_slots = 0;
   int H = 0;
