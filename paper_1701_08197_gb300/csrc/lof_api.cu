@@ -152,8 +152,10 @@ int pfx_row_words(int dtype, int T) {
 }
 
 
-// Budget of dynamic shared memory per CTA.
+// Budget of dynamic shared memory per CTA (at most as many resident CTAs as
+// the kernel's launch bounds allow: 4 of 128 threads, 2 of 256).
 int dyn_budget(const lofk::HostCfg& h, int dtype, int threads, int ctas) {
+  ctas = std::min(ctas, threads >= 256 ? 2 : 4);
   const int per = h.smem_per_sm / std::max(1, ctas) - 1024;
   return std::min(per, h.smem_optin) - static_smem_bytes(dtype, threads);
 }
@@ -341,13 +343,19 @@ extern "C" int lof_get_tuning(const lof_ctx* c, lof_tuning* t) {
 namespace {
 
 // Rows of one flag task: four per warp, fewer if the shared memory cannot
-// hold their flag words.
+// hold their flag words and the warps' staging buffers of the time pass (two
+// per warp, 32 rows of 32 samples + 16 bytes).
 int flag_words_row(int T) { return (T + 31) / 32 + 4; }
+int stage_bytes(int dtype, int threads) {
+  const int es = dtype == LOF_CI8 ? 2 : 4;
+  return (threads / 32) * 2 * 32 * (32 * es + 16);
+}
+int flag_bytes(int dtype, int T, int R, int threads) {
+  return ((4 * R * flag_words_row(T) + 15) & ~15) + stage_bytes(dtype, threads);
+}
 int flag_rows(int dtype, int T, int budget_bytes, int threads, int cap = 0) {
-  const int mw = flag_words_row(T), pr = pfx_row_words(dtype, T);
-  (void)pr;
   int R = std::min(lofk::kMaxRowsPerTask, cap > 0 ? cap : 4 * (threads / 32));
-  while (R > 0 && 4 * R * mw > budget_bytes) --R;
+  while (R > 0 && flag_bytes(dtype, T, R, threads) > budget_bytes) --R;
   return R;
 }
 
@@ -371,9 +379,8 @@ bool make_plan(const lofk::HostCfg& h, int dtype, const int* Ts, int nT, lofk::P
       snprintf(why, nwhy, "n_time %d does not fit the shared-memory budget (%d bytes)", Ts[i], budget);
       return false;
     }
-    const int mw = flag_words_row(Ts[i]);
-    need = std::max(need, 4 * R * mw);
-    want = std::max(want, 4 * R * mw);
+    need = std::max(need, flag_bytes(dtype, Ts[i], R, pl->threads));
+    want = std::max(want, flag_bytes(dtype, Ts[i], R, pl->threads));
   }
   if (need > budget) {
     snprintf(why, nwhy, "the workspace (%d bytes) exceeds the shared-memory budget (%d)", need, budget);

@@ -978,7 +978,7 @@ __device__ void merge_fine(const KParams& kp, UnitState* slot, uint8_t* ws, Fixe
 // samples are stored as u = Z: the difference of two prefix entries is then
 // S = n_flagged * Z + sum_unflagged with both parts recoverable, and the
 // window fires exactly when S > Kp[n] = n * Z + floor((I - n) * threshold_I).
-// These rows run one warp per row with the row in registers (wr_segment).
+// These rows run one warp per row with the row in registers (wr_passes).
 //
 // Any other unit takes the general path: rows in a shared-memory prefix
 // buffer, exact 64-bit sums of the unflagged values.  Layout of one batch of
@@ -991,6 +991,9 @@ __device__ void merge_fine(const KParams& kp, UnitState* slot, uint8_t* ws, Fixe
 // so that the prefix of u at x is Pb[x >> 5] + Pl[pidx(x)] (mod 2^32).
 
 constexpr uint32_t kZ = 1u << 26;
+// s_Kp holds the kKTable packed thresholds, then (c, Cb - 1) of each window
+// size 2^k at kKbOff + 2k (k >= 3, the prefiltered sizes).
+constexpr int kKbOff = kKTable;
 
 struct StLayout {
   int PLW, PBW, per_row;
@@ -1327,6 +1330,86 @@ __device__ __forceinline__ void wr_fire(const WrRow<NPL>& R, int lane, const uin
   }
 }
 
+// Q of block b (lane-relative), blocks past the lane's last from the next
+// lanes by shuffle (past lane 31: another valid packed sum; only windows that
+// the caller masks off read those).
+template <int NB>
+__device__ __forceinline__ uint32_t wr_qat(const uint32_t (&Q)[NB], int b) {
+  if (b < NB) return Q[b];
+  const int q = b / NB;
+  return __shfl_down_sync(kFull, Q[b - q * NB], q);
+}
+
+// Fire words for windows of I >= 8 samples, with an exact prefilter.  The
+// lane's samples form blocks of four; the windows that start in block b lie
+// in its union [4b, 4b + I + 4), whose n_U flagged samples and unflagged sum
+// s_U bound every such window (n <= n_U, s <= s_U).  With
+// c = Kt[I - 1] + 1 >= threshold_I and Cb = min_n (Kt[n] + 1 + n * c), a window
+// can fire (s > Kt[n]) only if s_U + n_U * c >= Cb, so blocks whose union
+// stays below Cb hold no firing window.  Only the block slots where some lane
+// has a candidate run the exact test (warp-uniform, so shuffles stay valid);
+// every other fire bit is zero, as the exact test would give.  Cb1 = Cb - 1.
+template <int NPL, int I>
+__device__ __forceinline__ void wr_fire_pf(const WrRow<NPL>& R, int lane, const uint32_t* Kp,
+                                           uint32_t c, uint32_t Cb1, uint32_t (&F)[NPL / 32]) {
+  static_assert(NPL == 32 && I >= 8 && I <= 64, "one flag word per lane, blocks of four");
+  constexpr int NB = NPL / 4, D = I / 4;
+  uint32_t Q[NB], X[NB];
+#pragma unroll
+  for (int b = 0; b < NB; ++b) {
+    Q[b] = R.u[4 * b] + R.u[4 * b + 1] + R.u[4 * b + 2] + R.u[4 * b + 3];
+    X[b] = Q[b] + (Q[b] >> 26) * (c - kZ);  // s + n * c (mod 2^32; < 2^28)
+  }
+  // V = sum of X over blocks b .. b + D, descending from b = NB - 1
+  uint32_t hs;
+  {
+    constexpr int a = D < NB ? D : NB;
+    uint32_t A = 0u;
+#pragma unroll
+    for (int k = 0; k < a; ++k) A += X[k];
+    hs = __shfl_down_sync(kFull, A, 1);
+    if constexpr (D > NB) hs += __shfl_down_sync(kFull, A, 2);
+  }
+  uint32_t V = X[NB - 1] + hs, cand = 0u;
+#pragma unroll
+  for (int b = NB - 1; b >= 0; --b) {
+    cand = __funnelshift_l(Cb1 - V, cand, 1);
+    if (b > 0) V = V + X[b - 1] - wr_qat<NB>(X, b + D);
+  }
+  const uint32_t any = __reduce_or_sync(kFull, cand);
+  uint32_t f = 0u;
+#pragma unroll
+  for (int b = 0; b < NB; ++b) {
+    if (!((any >> b) & 1u)) continue;
+    // packed sum of the window at 4b: blocks b .. b + D - 1
+    uint32_t S = 0u;
+    {
+      uint32_t own = 0u, p1 = 0u, p2 = 0u;
+#pragma unroll
+      for (int i = b; i < b + D && i < NB; ++i) own += Q[i];
+      if (b + D > NB) {
+#pragma unroll
+        for (int i = 0; i < b + D - NB && i < NB; ++i) p1 += Q[i];
+        p1 = __shfl_down_sync(kFull, p1, 1);
+      }
+      if (b + D > 2 * NB) {
+#pragma unroll
+        for (int i = 0; i < b + D - 2 * NB; ++i) p2 += Q[i];
+        p2 = __shfl_down_sync(kFull, p2, 2);
+      }
+      S = own + p1 + p2;
+    }
+    uint32_t bits = 0u;
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      bits |= ((Kp[S >> 26] - S) >> 31) << i;
+      if (i < 3) S = S - R.u[4 * b + i] + wr_uat<NPL>(R, lane, 4 * b + i + I);
+    }
+    f |= bits << (4 * b);
+  }
+  F[0] = f;
+}
+
 // Dilate the fire bits (a fired window flags its I samples), add the new
 // flags to M and store them as Z.  I is a run-time value here so that one
 // copy of this code serves every window size.
@@ -1370,19 +1453,57 @@ __device__ __forceinline__ void wr_apply(WrRow<NPL>& R, int lane, int nvalid, in
     if ((nw[j >> 5] >> (j & 31)) & 1u) R.u[j] = kZ;
 }
 
-// Loads the lane's samples (zero at or past T) as powers, flags those above
-// K1 (the I = 1 pass) and stores them as Z.
+// ---- staged segment I/O of the warp-row pass
+// Each warp owns two staging buffers in shared memory.  Lane L's NPL samples
+// of a segment fill row L of a buffer in sample order; rows are padded by 16
+// bytes so that the 16-byte shared loads of a quarter warp hit distinct
+// banks.  A segment is staged by cp.async (no registers) while the previous
+// one is computed; the build reads it from shared memory, and the output
+// zeroes its flagged samples there and stores the lane's interior samples
+// with one bulk copy.
 template <int DT, int NPL>
-__device__ __forceinline__ void wr_build(WrRow<NPL>& R, const uint8_t* grow, int xl, int T,
-                                         bool vin, uint32_t K1) {
-  const uint64_t pol = l2_policy_keep();
+struct WrStage {
+  static constexpr int kRowBytes = NPL * Traits<DT>::kBytes + 16;
+  static constexpr int kBufBytes = 32 * kRowBytes;
+};
+
+__device__ __forceinline__ void cp_async_wait_all() {
+  asm volatile("cp.async.wait_group 0;" ::: "memory");
+}
+
+// Stages the lane's samples [x, x + NPL) of a row (zeros at or past T) into
+// its buffer row srow as one cp.async group: 16-byte asynchronous copies
+// where the row is 16-byte aligned and the piece lies inside the row, plain
+// loads and shared stores elsewhere.
+template <int DT, int NPL>
+__device__ __forceinline__ void wr_stage(uint8_t* srow, const uint8_t* grow, int x, int T, bool vin,
+                                         uint64_t pol) {
+  using TR = Traits<DT>;
+  constexpr int VS = TR::kVec, NV = NPL / VS;
+  const uint32_t sa = saddr(srow);
+#pragma unroll
+  for (int q = 0; q < NV; ++q) {
+    const int xs = x + q * VS;
+    if (vin && xs + VS <= T) {
+      asm volatile("cp.async.cg.shared.global.L2::cache_hint [%0], [%1], 16, %2;" ::"r"(sa + 16 * q),
+                   "l"(grow + static_cast<size_t>(xs) * TR::kBytes), "l"(pol)
+                   : "memory");
+    } else {
+      const uint4 v = xs < T ? gload_raw<DT>(grow, xs, T, false, pol) : make_uint4(0u, 0u, 0u, 0u);
+      *reinterpret_cast<uint4*>(srow + 16 * q) = v;
+    }
+  }
+  asm volatile("cp.async.commit_group;" ::: "memory");
+}
+
+// Loads the lane's staged samples as powers, flags those above K1 (the I = 1
+// pass) and stores them as Z.
+template <int DT, int NPL>
+__device__ __forceinline__ void wr_build(WrRow<NPL>& R, const uint8_t* srow, uint32_t K1) {
   constexpr int VS = Traits<DT>::kVec, NV = NPL / VS;
   uint4 v[NV];
 #pragma unroll
-  for (int q = 0; q < NV; ++q) {
-    const int x = xl + q * VS;
-    v[q] = x < T ? gload_raw<DT>(grow, x, T, vin, pol) : make_uint4(0u, 0u, 0u, 0u);
-  }
+  for (int q = 0; q < NV; ++q) v[q] = *reinterpret_cast<const uint4*>(srow + 16 * q);
 #pragma unroll
   for (int w = 0; w < NPL / 32; ++w) R.M[w] = 0u;
 #pragma unroll
@@ -1430,12 +1551,13 @@ struct WrOut {
 };
 
 // Mask bytes and masked data of the 32 samples [x, x + 32) of one row, from
-// their flag word m (one lane; bits past T are zero).
+// their flag word m (one lane; bits past T are zero) and the lane's staged
+// samples srow.  In-place rows get no data here: their flagged samples are
+// zeroed once the whole row is final, as a later segment's halo re-reads
+// this segment's samples.
 template <int DT>
-__device__ __forceinline__ void wr_write_word(const WrOut& o, const uint8_t* grow, int x, int T,
-                                              uint32_t m) {
+__device__ __forceinline__ void wr_write_word(const WrOut& o, uint8_t* srow, int x, int T, uint32_t m) {
   using TR = Traits<DT>;
-  constexpr int VS = TR::kVec;
   const int nv = min(32, T - x);
   if (o.mask) {
     if (o.mask_vec && nv == 32) {
@@ -1450,90 +1572,96 @@ __device__ __forceinline__ void wr_write_word(const WrOut& o, const uint8_t* gro
       for (int j = 0; j < nv; ++j) o.mask[x + j] = static_cast<uint8_t>((m >> j) & 1u);
     }
   }
-  if (!o.out) return;
-  if (o.inplace) {
-    uint32_t mm = m;
-    while (mm) {
-      const int j = __ffs(mm) - 1;
-      mm &= mm - 1u;
-      TR::zero(o.out, x + j);
-    }
-    return;
+  if (!o.out || o.inplace) return;
+  uint32_t mm = m;
+  while (mm) {
+    const int j = __ffs(mm) - 1;
+    mm &= mm - 1u;
+    TR::zero(srow, j);
   }
-  if (o.vin && o.vout && nv == 32) {
-    const uint64_t pol = l2_policy_drop();
-#pragma unroll
-    for (int q = 0; q < 32 / VS; ++q) {
-      uint4 v = ldg_policy(grow + static_cast<size_t>(x + q * VS) * TR::kBytes, pol);
-      const uint32_t bits = (m >> (q * VS)) & ((1u << VS) - 1u);
-      if (bits) {
-        uint32_t wd[4] = {v.x, v.y, v.z, v.w};
-#pragma unroll
-        for (int j = 0; j < VS; ++j) {
-          if ((bits >> j) & 1u) {
-            if constexpr (VS == 4) wd[j] = 0u;
-            else wd[j >> 1] &= (j & 1) ? 0x0000FFFFu : 0xFFFF0000u;
-          }
-        }
-        v = make_uint4(wd[0], wd[1], wd[2], wd[3]);
-      }
-      __stcs(reinterpret_cast<uint4*>(o.out + static_cast<size_t>(x + q * VS) * TR::kBytes), v);
-    }
-    return;
-  }
-  for (int j = 0; j < nv; ++j) {
-    if ((m >> j) & 1u) TR::zero(o.out, x + j);
-    else TR::copy(o.out + static_cast<size_t>(x + j) * TR::kBytes, grow + static_cast<size_t>(x + j) * TR::kBytes);
+  const int bytes = nv * TR::kBytes;
+  if (o.vout && (bytes & 15) == 0) {
+    fence_async_smem();  // the staged samples and the zeroes above: generic-proxy writes
+    bulk_store(o.out + static_cast<size_t>(x) * TR::kBytes, srow, static_cast<uint32_t>(bytes));
+    bulk_commit();
+  } else {
+    for (int j = 0; j < nv; ++j)
+      TR::copy(o.out + static_cast<size_t>(x + j) * TR::kBytes, srow + j * TR::kBytes);
   }
 }
 
-// Time pass of segment sg of one row by one warp.  Writes the flag words of
-// the segment's interior to M_out (the row's words) and returns, in every
-// lane, the interior's number of flagged samples and sum of unflagged powers.
-template <int DT, int NPL>
-__device__ void wr_segment(const uint8_t* grow, int T, int sg, bool vin, int kmax,
-                           const uint32_t* s_Kp, uint32_t* M_out, const WrOut& o,
-                           int& n_flag, unsigned long long& sum_unflagged) {
-  constexpr int NW = NPL / 32, SPAN = 32 * NPL;
+// One segment of a row as seen by the lane: its span's start s0, interior
+// [oa, ob), end of valid samples vend and the lane's first sample xl.
+struct WrSeg {
+  int s0, oa, ob, vend, xl;
+};
+template <int NPL>
+__device__ __forceinline__ WrSeg wr_seg(int T, int sg) {
+  WrSeg g;
+  wr_seg_bounds<NPL>(T, sg, g.s0, g.oa, g.ob);
+  g.vend = min(T, g.s0 + 32 * NPL);
+  g.xl = g.s0 + (threadIdx.x & 31) * NPL;
+  return g;
+}
+
+// Window sizes 2^k, k0 <= k <= k1, of the time pass over a segment held in R.
+template <int NPL>
+__device__ __forceinline__ void wr_passes(WrRow<NPL>& R, const WrSeg& g, int k0, int k1,
+                                          const uint32_t* s_Kp) {
+  constexpr int NW = NPL / 32;
   const int lane = threadIdx.x & 31;
-  int s0, oa, ob;
-  wr_seg_bounds<NPL>(T, sg, s0, oa, ob);
-  const int vend = min(T, s0 + SPAN);
-  const int xl = s0 + lane * NPL;
-  WrRow<NPL> R;
-  wr_build<DT, NPL>(R, grow, xl, T, vin, s_Kp[0]);
 #pragma unroll 1
-  for (int k = 1; k <= kmax; ++k) {
+  for (int k = k0; k <= k1; ++k) {
     const int I = 1 << k;
     const uint32_t* Kp = s_Kp + koffset(k);
     uint32_t F[NW];
-    switch (k) {
-      case 1: wr_fire<NPL, 2>(R, lane, Kp, F); break;
-      case 2: wr_fire<NPL, 4>(R, lane, Kp, F); break;
-      case 3: wr_fire<NPL, 8>(R, lane, Kp, F); break;
-      case 4: wr_fire<NPL, 16>(R, lane, Kp, F); break;
-      case 5: wr_fire<NPL, 32>(R, lane, Kp, F); break;
-      default: wr_fire<NPL, 64>(R, lane, Kp, F); break;
+    if constexpr (NPL == 32) {
+      // the prefilter pays off for the largest window only (fewest candidate
+      // blocks, most shuffles in the exact loop)
+      const uint32_t c = s_Kp[kKbOff + 2 * k], Cb1 = s_Kp[kKbOff + 2 * k + 1];
+      switch (k) {
+        case 1: wr_fire<NPL, 2>(R, lane, Kp, F); break;
+        case 2: wr_fire<NPL, 4>(R, lane, Kp, F); break;
+        case 3: wr_fire<NPL, 8>(R, lane, Kp, F); break;
+        case 4: wr_fire<NPL, 16>(R, lane, Kp, F); break;
+        case 5: wr_fire<NPL, 32>(R, lane, Kp, F); break;
+        default: wr_fire_pf<NPL, 64>(R, lane, Kp, c, Cb1, F); break;
+      }
+    } else {
+      switch (k) {
+        case 1: wr_fire<NPL, 2>(R, lane, Kp, F); break;
+        case 2: wr_fire<NPL, 4>(R, lane, Kp, F); break;
+        case 3: wr_fire<NPL, 8>(R, lane, Kp, F); break;
+        case 4: wr_fire<NPL, 16>(R, lane, Kp, F); break;
+        case 5: wr_fire<NPL, 32>(R, lane, Kp, F); break;
+        default: wr_fire<NPL, 64>(R, lane, Kp, F); break;
+      }
     }
-    wr_apply<NPL>(R, lane, vend - I + 1 - xl, I, F);
+    wr_apply<NPL>(R, lane, g.vend - I + 1 - g.xl, I, F);
   }
-  // interior words [oa, ob): flag words, counts and sums of unflagged powers,
-  // and (when an output is given) the mask bytes and the masked data of the
-  // interior, written while the rows are hot in L1 (a row that the history
-  // test flags whole is rewritten afterwards)
+}
+
+// Interior words [oa, ob) of a segment: flag words to M_out (the row's
+// words), mask and masked data, and the interior's number of flagged samples
+// and sum of unflagged powers (returned in every lane).
+template <int DT, int NPL>
+__device__ __forceinline__ void wr_finish(const WrRow<NPL>& R, const WrSeg& g, int T, uint8_t* srow,
+                                          uint32_t* M_out, const WrOut& o, int& n_flag,
+                                          unsigned long long& sum_unflagged) {
+  constexpr int NW = NPL / 32;
   int nfl = 0;
   unsigned long long su = 0;
 #pragma unroll
   for (int w = 0; w < NW; ++w) {
-    const int x = xl + 32 * w;
-    if (x >= oa && x < ob) {
+    const int x = g.xl + 32 * w;
+    if (x >= g.oa && x < g.ob) {
       M_out[x >> 5] = R.M[w];
       nfl += __popc(R.M[w]);
       uint32_t s = 0u;  // packed: n * Z + sum_unflagged, n < 2^6
 #pragma unroll
       for (int b = 0; b < 32; ++b) s += R.u[32 * w + b];
       su += s - static_cast<uint32_t>(__popc(R.M[w])) * kZ;
-      if (o.enabled) wr_write_word<DT>(o, grow, x, T, R.M[w]);
+      if (o.enabled) wr_write_word<DT>(o, srow + 32 * w * Traits<DT>::kBytes, x, T, R.M[w]);
     }
   }
   n_flag = __reduce_add_sync(kFull, nfl);
@@ -2140,6 +2268,20 @@ __device__ LOFK_TASK_FN void task_flag(const KParams& kp, const DevUnit& u, Unit
       if (Kt[n] < 0 || Kt[n] >= static_cast<long long>(kZ)) bad = true;
       s_Kp[e] = static_cast<uint32_t>(n) * kZ + static_cast<uint32_t>(Kt[n]);
     }
+    // prefilter bounds of the windows I >= 8 (see wr_fire_pf): c = Kt[I - 1] + 1,
+    // Cb - 1 = min_n (Kt[n] + n * c).  The bound holds for any c >= 0; c = 0
+    // (every nonzero union a candidate) where c > 2^21 (a factor that grows
+    // with I), so that the union sums stay below 2^28.
+    if (tid >= 3 && tid <= f.kmax_t) {
+      const int k = tid, I = 1 << k;
+      const long long* Kt = f.K + koffset(k);
+      long long c = Kt[I - 1] + 1;
+      if (c > (1ll << 21)) c = 0;
+      long long m = Kt[0];
+      for (int n = 1; n <= I; ++n) m = min(m, Kt[n] + n * c);
+      s_Kp[kKbOff + 2 * k] = static_cast<uint32_t>(c);
+      s_Kp[kKbOff + 2 * k + 1] = static_cast<uint32_t>(min(max(m, 0ll), (1ll << 30)));
+    }
   }
   bad = __syncthreads_or(bad);
   if (tid == 0) f.state = bad ? 0 : 1;
@@ -2151,38 +2293,82 @@ __device__ LOFK_TASK_FN void task_flag(const KParams& kp, const DevUnit& u, Unit
     if (f.state == 1) {
       // packed values: one warp per row (its segments one after the other,
       // each in registers, mask and data written as soon as they are final),
-      // then the row's history test and, when it fires, the whole row flagged
+      // then the row's history test and, when it fires, the whole row flagged.
+      // The warp's items (row, segment) are staged one ahead in its two
+      // buffers, after the rows' flag words.
+      using ST = WrStage<DT, kWrNpl>;
       const bool vin = (u.flags & kUnitInVec) != 0;
       const int nsg = wr_seg_count<kWrNpl>(T);
-      for (int kr = warp; kr < nkeep; kr += NW) {
-        const int r = f.keep[kr];
-        const uint8_t* grow = gin + static_cast<int64_t>(row0 + r) * u.in_stride * TR::kBytes;
+      uint8_t* const stage = ws + ((4 * R * MW + 15) & ~15) + warp * 2 * ST::kBufBytes;
+      const uint64_t pol = l2_policy_drop();  // the input's last read
+      const int nrw = nkeep > warp ? (nkeep - warp + NW - 1) / NW : 0;
+      const int nit = nrw * nsg;
+      auto row_of = [&](int it) { return row0 + f.keep[warp + (it / nsg) * NW]; };
+      auto stage_item = [&](int it) {
+        const WrSeg g = wr_seg<kWrNpl>(T, it % nsg);
+        wr_stage<DT, kWrNpl>(stage + (it & 1) * ST::kBufBytes + lane * ST::kRowBytes,
+                             gin + static_cast<int64_t>(row_of(it)) * u.in_stride * TR::kBytes, g.xl, T,
+                             vin, pol);
+      };
+      if (nit > 0) stage_item(0);
+      int nfl_row = 0;
+      unsigned long long su_row = 0;
+      for (int it = 0; it < nit; ++it) {
+        const int sg = it % nsg, c = row_of(it), r = c - row0;
+        uint8_t* const srow = stage + (it & 1) * ST::kBufBytes + lane * ST::kRowBytes;
         WrOut o;
-        o.out = u.out ? static_cast<uint8_t*>(u.out) + static_cast<int64_t>(row0 + r) * u.out_stride * TR::kBytes
+        o.out = u.out ? static_cast<uint8_t*>(u.out) + static_cast<int64_t>(c) * u.out_stride * TR::kBytes
                       : nullptr;
-        o.mask = u.mask ? u.mask + static_cast<int64_t>(row0 + r) * u.mask_stride : nullptr;
+        o.mask = u.mask ? u.mask + static_cast<int64_t>(c) * u.mask_stride : nullptr;
         o.enabled = o.out != nullptr || o.mask != nullptr;
         o.inplace = (u.flags & kUnitInPlace) != 0;
         o.vout = (u.flags & kUnitOutVec) != 0;
         o.mask_vec = (u.flags & kUnitMaskVec) != 0;
         o.vin = vin;
-        int nfl_row = 0;
-        unsigned long long su_row = 0;
-        for (int sg = 0; sg < nsg; ++sg) {
-          int nfl = 0;
-          unsigned long long su = 0;
-          wr_segment<DT, kWrNpl>(grow, T, sg, vin, f.kmax_t, s_Kp, smbits + r * MW + 2, o, nfl, su);
-          nfl_row += nfl;
-          su_row += su;
+        if (sg == 0) {
+          nfl_row = 0;
+          su_row = 0;
         }
-        int fh = 0;
-        if (lane == 0) fh = history_row<NT>(kp, u, row0 + r, T, nfl_row, su_row, f);
-        fh = __shfl_sync(kFull, fh, 0);
-        if (fh) {
-          __syncwarp();
-          write_row_flagged<DT>(u, row0 + r, T);
+        const WrSeg g = wr_seg<kWrNpl>(T, sg);
+        cp_async_wait_all();  // this item's samples (the only group in flight)
+        WrRow<kWrNpl> Rw;
+        wr_build<DT, kWrNpl>(Rw, srow, s_Kp[0]);
+        if (it + 1 < nit) {
+          // the next item into the other buffer as early as possible (the
+          // input comes from DRAM), once the bulk stores of its last item
+          // have read it
+          bulk_wait_read();
+          stage_item(it + 1);
+        }
+        wr_passes<kWrNpl>(Rw, g, 1, f.kmax_t, s_Kp);
+        int nfl = 0;
+        unsigned long long su = 0;
+        wr_finish<DT, kWrNpl>(Rw, g, T, srow, smbits + r * MW + 2, o, nfl, su);
+        nfl_row += nfl;
+        su_row += su;
+        if (sg == nsg - 1) {
+          int fh = 0;
+          if (lane == 0) fh = history_row<NT>(kp, u, c, T, nfl_row, su_row, f);
+          fh = __shfl_sync(kFull, fh, 0);
+          if (fh) {
+            bulk_wait_all();  // the row's bulk stores land before the rewrite
+            __syncwarp();
+            write_row_flagged<DT>(u, c, T);
+          } else if (o.inplace && o.out) {
+            __syncwarp();  // the row's flag words, written by every lane
+            const uint32_t* mrow = smbits + r * MW + 2;
+            for (int w = lane; w < nch; w += 32) {
+              uint32_t m = mrow[w];
+              while (m) {
+                const int j = __ffs(m) - 1;
+                m &= m - 1u;
+                TR::zero(o.out, 32 * w + j);
+              }
+            }
+          }
         }
       }
+      bulk_wait_all();  // buffers free for the next task; data stored
       if (tid == 0) f.rows_done = 1;
       __syncthreads();
     } else {
@@ -2446,7 +2632,7 @@ template <int DT, int NT>
 __global__ void __launch_bounds__(NT, NT == 128 ? 4 : 2) lof_block_kernel(const KParams kp) {
   extern __shared__ __align__(128) uint8_t smem[];
   __shared__ Fixed<NT> f;
-  __shared__ uint32_t s_Kp[kKTable];
+  __shared__ uint32_t s_Kp[kKTable + 2 * 8];
   const int tid = threadIdx.x;
   if (tid == 0) {
     f.q_done = 0;

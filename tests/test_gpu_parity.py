@@ -137,6 +137,30 @@ def test_in_place_and_strided_rows():
         assert np.array_equal(ob.cpu().numpy(), want["out"])
 
 
+@pytest.mark.parametrize("np_dtype,dtype,sigma", [(np.int16, lof.LOF_CI16, 32), (np.int8, lof.LOF_CI8, 8)])
+def test_in_place_multi_segment_rows(np_dtype, dtype, sigma):
+    # rows of several time-pass segments (1024 samples each, overlapping by
+    # 120-sample halos): flagged samples inside the halos must not be seen
+    # zeroed by the next segment, so in place equals out of place
+    rng = np.random.default_rng(21)
+    T = 3072
+    d = np.clip(np.round(rng.normal(0, sigma, (24, T, 2))), -120 if np_dtype == np.int8 else -30000,
+                120 if np_dtype == np.int8 else 30000).astype(np_dtype)
+    hi = 100 if np_dtype == np.int8 else 2000
+    for r in range(24):
+        for a in (760 + 7 * r, 800 + 5 * r, 880 + 3 * r, 1660 + 4 * r, 1750 + 2 * r, 2580 + 6 * r):
+            d[r, a:a + 3 + (r % 5)] = hi
+    P = oracle_params()
+    want = oracle.flag_unit(P, d)
+    with lof.Flagger(0) as fl:
+        x = torch.as_tensor(d).to(DEV)
+        m = torch.zeros((24, T), dtype=torch.uint8, device=DEV)
+        fl.flag_block(dtype, [lof.make_unit(x, x, m)])
+        fl.status()
+        assert np.array_equal(m.cpu().numpy(), want["mask"])
+        assert np.array_equal(x.cpu().numpy(), want["out"])
+
+
 def test_host_buffer_entry_point():
     rng = np.random.default_rng(8)
     d = np.round(rng.normal(0, 8, (33, 777, 2))).astype(np.int8)
