@@ -2054,9 +2054,10 @@ __device__ LOFK_TASK_FN void task_stats(const KParams& kp, const DevUnit& u, Uni
           const uint32_t val = raw_pw<DT>(cur[q], j);
           sum += val;
           const uint32_t key = coarse_key(val);
-          atomicAdd(&hist[key], 1u);
+          // one count per sample: its value's counter inside a target bin
+          // (the bin's coarse count is rebuilt from those below), else its bin
           const uint32_t si = val + moff[key];  // spec index, or >= nsc off the targets
-          if (si < nsc) atomicAdd(&spec[si], 1u);
+          atomicAdd(si < nsc ? spec + si : hist + key, 1u);
         }
       }
     }
@@ -2097,6 +2098,14 @@ __device__ LOFK_TASK_FN void task_stats(const KParams& kp, const DevUnit& u, Uni
       f.red_b[warp] = lo;
       f.red_c[warp] = hi;
     }
+  }
+  __syncthreads();
+  // coarse counts of the target bins: the sums of their value counters
+  if (tid < nspec_t) {
+    const Target& t = f.tgt[tid];
+    uint32_t c = 0;
+    for (uint32_t i = t.base; i <= t.base + (t.hi - t.lo); ++i) c += spec[i];
+    hist[coarse_key(t.lo)] += c;
   }
   __syncthreads();
   for (int r = tid; r < R; r += NT) kp.chan_S[u.chan_off + row0 + r] = f.rowS[r];
