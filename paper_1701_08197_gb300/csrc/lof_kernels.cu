@@ -1282,13 +1282,16 @@ struct WrRow {
 };
 
 // u at lane-relative position x >= 0 (x < 3 * NPL), from the next lanes by
-// shuffle; zero past lane 31 (past the segment).
+// shuffle.  Past lane 31 (past the segment's span) the shuffle returns the
+// lane's own value: another valid packed value, read only by windows that
+// run past the span, whose fire bits wr_apply masks off.  The slide stays
+// exact for the others (every value it adds it later subtracts).
 template <int NPL>
 __device__ __forceinline__ uint32_t wr_uat(const WrRow<NPL>& R, int lane, int x) {
+  (void)lane;
   if (x < NPL) return R.u[x];
   const int q = x / NPL;
-  uint32_t v = __shfl_down_sync(kFull, R.u[x - q * NPL], q);
-  return lane + q < 32 ? v : 0u;
+  return __shfl_down_sync(kFull, R.u[x - q * NPL], q);
 }
 
 // Fire words F[w] (bit b: the window of size I at j = 32w + b fires), by a
@@ -1305,17 +1308,19 @@ __device__ __forceinline__ void wr_fire(const WrRow<NPL>& R, int lane, const uin
 #pragma unroll
     for (int k = 0; k < a; ++k) A += R.u[k];
     hs = __shfl_down_sync(kFull, A, 1);
-    if (lane + 1 >= 32) hs = 0u;
     if constexpr (m > NPL) {
       uint32_t B = 0u;
 #pragma unroll
       for (int k = 0; k < m - NPL; ++k) B += R.u[k];
       uint32_t hb = __shfl_down_sync(kFull, B, 2);
-      if (lane + 2 >= 32) hb = 0u;
       hs += hb;
     }
   }
   uint32_t S = R.u[NPL - 1] + hs;
+  // I <= 32: the table sits in registers, lane n holding Kp[n], and is read
+  // by shuffle (n = 32 wraps to Kp[0]: a window of 32 flagged samples, whose
+  // firing flags nothing new)
+  const uint32_t Kreg = I <= 32 ? Kp[lane < I ? lane : I] : 0u;
 #pragma unroll
   for (int w = NW - 1; w >= 0; --w) {
     uint32_t f = 0u;
@@ -1323,7 +1328,8 @@ __device__ __forceinline__ void wr_fire(const WrRow<NPL>& R, int lane, const uin
     for (int b = 31; b >= 0; --b) {
       const int j = 32 * w + b;
       if ((j & 15) == 15) __syncwarp();
-      f = __funnelshift_l(Kp[S >> 26] - S, f, 1);
+      const uint32_t kn = I <= 32 ? __shfl_sync(kFull, Kreg, S >> 26) : Kp[S >> 26];
+      f = __funnelshift_l(kn - S, f, 1);
       if (j > 0) S = S + R.u[j - 1] - wr_uat<NPL>(R, lane, j - 1 + I);
     }
     F[w] = f;
