@@ -978,7 +978,8 @@ __device__ void merge_fine(const KParams& kp, UnitState* slot, uint8_t* ws, Fixe
 // samples are stored as u = Z: the difference of two prefix entries is then
 // S = n_flagged * Z + sum_unflagged with both parts recoverable, and the
 // window fires exactly when S > Kp[n] = n * Z + floor((I - n) * threshold_I).
-// These rows run one warp per row with the row in registers (wr_passes).
+// These rows run one warp per row with the row in registers (wr_passes), in
+// the equivalent low-bit form (kLowShift).
 //
 // Any other unit takes the general path: rows in a shared-memory prefix
 // buffer, exact 64-bit sums of the unflagged values.  Layout of one batch of
@@ -991,8 +992,17 @@ __device__ void merge_fine(const KParams& kp, UnitState* slot, uint8_t* ws, Fixe
 // so that the prefix of u at x is Pb[x >> 5] + Pl[pidx(x)] (mod 2^32).
 
 constexpr uint32_t kZ = 1u << 26;
-// s_Kp holds the kKTable packed thresholds, then (c, Cb - 1) of each window
-// size 2^k at kKbOff + 2k (k >= 3, the prefiltered sizes).
+// The warp-row pass keeps its values in the low-bit form: unflagged
+// u = power << 6, flagged u = 1, so that the sum of a window of I <= 32
+// values is S = 64 * sum_unflagged + n_flagged (n < 64, S < 2^31 while
+// threshold_1 < 2^20) and its low five bits index the register table by
+// shuffle.  The window fires exactly when S > 64 * floor((I - n) *
+// threshold_I) + 63.  The 64-sample window works on block sums converted
+// back to n * Z + sum_unflagged.
+constexpr uint32_t kLowShift = 6;
+// s_Kp holds the kKTable thresholds (entry 0: floor(threshold_1); windows
+// 2..32 in the low-bit form above; window 64 as n * Z + Kt[n]), then (c,
+// Cb - 1) of each window size 2^k at kKbOff + 2k (k >= 3).
 constexpr int kKbOff = kKTable;
 
 struct StLayout {
@@ -1316,11 +1326,13 @@ __device__ __forceinline__ void wr_fire(const WrRow<NPL>& R, int lane, const uin
       hs += hb;
     }
   }
+  static_assert(I <= 32, "low-bit window sums");
   uint32_t S = R.u[NPL - 1] + hs;
-  // I <= 32: the table sits in registers, lane n holding Kp[n], and is read
-  // by shuffle (n = 32 wraps to Kp[0]: a window of 32 flagged samples, whose
-  // firing flags nothing new)
-  const uint32_t Kreg = I <= 32 ? Kp[lane < I ? lane : I] : 0u;
+  // the table sits in registers, lane n holding Kp[n], and is read by
+  // shuffle with the sum itself as the index (its low five bits are n; n = 32
+  // wraps to Kp[0] > S: a window of 32 flagged samples, which would flag
+  // nothing new anyway)
+  const uint32_t Kreg = Kp[lane < I ? lane : I];
 #pragma unroll
   for (int w = NW - 1; w >= 0; --w) {
     uint32_t f = 0u;
@@ -1328,8 +1340,7 @@ __device__ __forceinline__ void wr_fire(const WrRow<NPL>& R, int lane, const uin
     for (int b = 31; b >= 0; --b) {
       const int j = 32 * w + b;
       if ((j & 15) == 15) __syncwarp();
-      const uint32_t kn = I <= 32 ? __shfl_sync(kFull, Kreg, S >> 26) : Kp[S >> 26];
-      f = __funnelshift_l(kn - S, f, 1);
+      f = __funnelshift_l(__shfl_sync(kFull, Kreg, S) - S, f, 1);
       if (j > 0) S = S + R.u[j - 1] - wr_uat<NPL>(R, lane, j - 1 + I);
     }
     F[w] = f;
@@ -1363,8 +1374,9 @@ __device__ __forceinline__ void wr_fire_pf(const WrRow<NPL>& R, int lane, const 
   uint32_t Q[NB], X[NB];
 #pragma unroll
   for (int b = 0; b < NB; ++b) {
+    // low-bit block sum 64 * s + n (n <= 4), then s + n * c (< 2^24)
     Q[b] = R.u[4 * b] + R.u[4 * b + 1] + R.u[4 * b + 2] + R.u[4 * b + 3];
-    X[b] = Q[b] + (Q[b] >> 26) * (c - kZ);  // s + n * c (mod 2^32; < 2^28)
+    X[b] = (Q[b] >> kLowShift) + (Q[b] & 63u) * c;
   }
   // V = sum of X over blocks b .. b + D, descending from b = NB - 1
   uint32_t hs;
@@ -1387,29 +1399,31 @@ __device__ __forceinline__ void wr_fire_pf(const WrRow<NPL>& R, int lane, const 
 #pragma unroll
   for (int b = 0; b < NB; ++b) {
     if (!((any >> b) & 1u)) continue;
-    // packed sum of the window at 4b: blocks b .. b + D - 1
+    // window sum at 4b as n * Z + s: blocks b .. b + D - 1
     uint32_t S = 0u;
     {
+      auto zq = [](uint32_t q) { return (q >> kLowShift) + (q & 63u) * kZ; };
       uint32_t own = 0u, p1 = 0u, p2 = 0u;
 #pragma unroll
-      for (int i = b; i < b + D && i < NB; ++i) own += Q[i];
+      for (int i = b; i < b + D && i < NB; ++i) own += zq(Q[i]);
       if (b + D > NB) {
 #pragma unroll
-        for (int i = 0; i < b + D - NB && i < NB; ++i) p1 += Q[i];
+        for (int i = 0; i < b + D - NB && i < NB; ++i) p1 += zq(Q[i]);
         p1 = __shfl_down_sync(kFull, p1, 1);
       }
       if (b + D > 2 * NB) {
 #pragma unroll
-        for (int i = 0; i < b + D - 2 * NB; ++i) p2 += Q[i];
+        for (int i = 0; i < b + D - 2 * NB; ++i) p2 += zq(Q[i]);
         p2 = __shfl_down_sync(kFull, p2, 2);
       }
       S = own + p1 + p2;
     }
+    auto zu = [](uint32_t v) { return (v >> kLowShift) + (v & 1u) * kZ; };
     uint32_t bits = 0u;
 #pragma unroll
     for (int i = 0; i < 4; ++i) {
       bits |= ((Kp[S >> 26] - S) >> 31) << i;
-      if (i < 3) S = S - R.u[4 * b + i] + wr_uat<NPL>(R, lane, 4 * b + i + I);
+      if (i < 3) S = S - zu(R.u[4 * b + i]) + zu(wr_uat<NPL>(R, lane, 4 * b + i + I));
     }
     f |= bits << (4 * b);
   }
@@ -1417,8 +1431,8 @@ __device__ __forceinline__ void wr_fire_pf(const WrRow<NPL>& R, int lane, const 
 }
 
 // Dilate the fire bits (a fired window flags its I samples), add the new
-// flags to M and store them as Z.  I is a run-time value here so that one
-// copy of this code serves every window size.
+// flags to M and store them as flagged (u = 1).  I is a run-time value here
+// so that one copy of this code serves every window size.
 template <int NPL>
 __device__ __forceinline__ void wr_apply(WrRow<NPL>& R, int lane, int nvalid, int I,
                                          uint32_t (&F)[NPL / 32]) {
@@ -1456,7 +1470,7 @@ __device__ __forceinline__ void wr_apply(WrRow<NPL>& R, int lane, int nvalid, in
   if (!__any_sync(kFull, anyw != 0u)) return;
 #pragma unroll
   for (int j = 0; j < NPL; ++j)
-    if ((nw[j >> 5] >> (j & 31)) & 1u) R.u[j] = kZ;
+    if ((nw[j >> 5] >> (j & 31)) & 1u) R.u[j] = 1u;
 }
 
 // ---- staged segment I/O of the warp-row pass
@@ -1503,7 +1517,7 @@ __device__ __forceinline__ void wr_stage(uint8_t* srow, const uint8_t* grow, int
 }
 
 // Loads the lane's staged samples as powers, flags those above K1 (the I = 1
-// pass) and stores them as Z.
+// pass) and stores them as flagged (u = 1), the others as power << 6.
 template <int DT, int NPL>
 __device__ __forceinline__ void wr_build(WrRow<NPL>& R, const uint8_t* srow, uint32_t K1) {
   constexpr int VS = Traits<DT>::kVec, NV = NPL / VS;
@@ -1516,7 +1530,7 @@ __device__ __forceinline__ void wr_build(WrRow<NPL>& R, const uint8_t* srow, uin
   for (int j = 0; j < NPL; ++j) {
     const uint32_t uu = raw_pw<DT>(v[j / VS], j % VS);
     const bool fl = uu > K1;
-    R.u[j] = fl ? kZ : uu;
+    R.u[j] = fl ? 1u : (uu << kLowShift);
     if (fl) R.M[j >> 5] |= 1u << (j & 31);
   }
 }
@@ -1614,6 +1628,7 @@ __device__ __forceinline__ WrSeg wr_seg(int T, int sg) {
 template <int NPL>
 __device__ __forceinline__ void wr_passes(WrRow<NPL>& R, const WrSeg& g, int k0, int k1,
                                           const uint32_t* s_Kp) {
+  static_assert(NPL == 32, "one flag word per lane");
   constexpr int NW = NPL / 32;
   const int lane = threadIdx.x & 31;
 #pragma unroll 1
@@ -1621,27 +1636,16 @@ __device__ __forceinline__ void wr_passes(WrRow<NPL>& R, const WrSeg& g, int k0,
     const int I = 1 << k;
     const uint32_t* Kp = s_Kp + koffset(k);
     uint32_t F[NW];
-    if constexpr (NPL == 32) {
-      // the prefilter pays off for the largest window only (fewest candidate
-      // blocks, most shuffles in the exact loop)
-      const uint32_t c = s_Kp[kKbOff + 2 * k], Cb1 = s_Kp[kKbOff + 2 * k + 1];
-      switch (k) {
-        case 1: wr_fire<NPL, 2>(R, lane, Kp, F); break;
-        case 2: wr_fire<NPL, 4>(R, lane, Kp, F); break;
-        case 3: wr_fire<NPL, 8>(R, lane, Kp, F); break;
-        case 4: wr_fire<NPL, 16>(R, lane, Kp, F); break;
-        case 5: wr_fire<NPL, 32>(R, lane, Kp, F); break;
-        default: wr_fire_pf<NPL, 64>(R, lane, Kp, c, Cb1, F); break;
-      }
-    } else {
-      switch (k) {
-        case 1: wr_fire<NPL, 2>(R, lane, Kp, F); break;
-        case 2: wr_fire<NPL, 4>(R, lane, Kp, F); break;
-        case 3: wr_fire<NPL, 8>(R, lane, Kp, F); break;
-        case 4: wr_fire<NPL, 16>(R, lane, Kp, F); break;
-        case 5: wr_fire<NPL, 32>(R, lane, Kp, F); break;
-        default: wr_fire<NPL, 64>(R, lane, Kp, F); break;
-      }
+    // the prefilter pays off for the largest window only (fewest candidate
+    // blocks, most shuffles in the exact loop)
+    const uint32_t c = s_Kp[kKbOff + 2 * k], Cb1 = s_Kp[kKbOff + 2 * k + 1];
+    switch (k) {
+      case 1: wr_fire<NPL, 2>(R, lane, Kp, F); break;
+      case 2: wr_fire<NPL, 4>(R, lane, Kp, F); break;
+      case 3: wr_fire<NPL, 8>(R, lane, Kp, F); break;
+      case 4: wr_fire<NPL, 16>(R, lane, Kp, F); break;
+      case 5: wr_fire<NPL, 32>(R, lane, Kp, F); break;
+      default: wr_fire_pf<NPL, 64>(R, lane, Kp, c, Cb1, F); break;
     }
     wr_apply<NPL>(R, lane, g.vend - I + 1 - g.xl, I, F);
   }
@@ -1663,10 +1667,10 @@ __device__ __forceinline__ void wr_finish(const WrRow<NPL>& R, const WrSeg& g, i
     if (x >= g.oa && x < g.ob) {
       M_out[x >> 5] = R.M[w];
       nfl += __popc(R.M[w]);
-      uint32_t s = 0u;  // packed: n * Z + sum_unflagged, n < 2^6
+      uint32_t s = 0u;  // low-bit form: 64 * sum_unflagged + n, n <= 32
 #pragma unroll
       for (int b = 0; b < 32; ++b) s += R.u[32 * w + b];
-      su += s - static_cast<uint32_t>(__popc(R.M[w])) * kZ;
+      su += s >> kLowShift;
       if (o.enabled) wr_write_word<DT>(o, srow + 32 * w * Traits<DT>::kBytes, x, T, R.M[w]);
     }
   }
@@ -2281,7 +2285,14 @@ __device__ LOFK_TASK_FN void task_flag(const KParams& kp, const DevUnit& u, Unit
       const int n = e - koffset(k);
       const long long* Kt = f.K + koffset(k);
       if (Kt[n] < 0 || Kt[n] >= static_cast<long long>(kZ)) bad = true;
-      s_Kp[e] = static_cast<uint32_t>(n) * kZ + static_cast<uint32_t>(Kt[n]);
+      if (k == 0) {
+        s_Kp[e] = static_cast<uint32_t>(Kt[n]);
+      } else if (k <= 5) {
+        if (Kt[n] >= (1ll << 25)) bad = true;  // 64 * Kt + 63 < 2^31
+        s_Kp[e] = (static_cast<uint32_t>(Kt[n]) << kLowShift) + 63u;
+      } else {
+        s_Kp[e] = static_cast<uint32_t>(n) * kZ + static_cast<uint32_t>(Kt[n]);
+      }
     }
     // prefilter bounds of the windows I >= 8 (see wr_fire_pf): c = Kt[I - 1] + 1,
     // Cb - 1 = min_n (Kt[n] + n * c).  The bound holds for any c >= 0; c = 0
