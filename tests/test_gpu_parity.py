@@ -137,6 +137,21 @@ def test_in_place_and_strided_rows():
         assert np.array_equal(ob.cpu().numpy(), want["out"])
 
 
+@pytest.mark.parametrize("p,sigma", [(2.5, 300.0), (5.0, 34.0)])
+def test_growing_window_factors(p, sigma):
+    # p >= 2 makes threshold_I grow with I: for p = 2.5 at sigma 300 the
+    # 32-sample table leaves the register (low-bit) form and the units take the
+    # general path; for p = 5 at sigma 34 the windows up to 32 stay packed while
+    # the 64-sample prefilter bound degrades to c = 0 (every block a candidate)
+    rng = np.random.default_rng(31)
+    d = np.clip(np.round(rng.normal(0, sigma, (40, 3072, 2))), -32000, 32000).astype(np.int16)
+    d[5, 1000:1200] = np.int16(min(32000, 12 * sigma))
+    d[:, 2500:2503] = np.int16(min(32000, 20 * sigma))
+    P = oracle_params(p=p)
+    with lof.Flagger(0, n_history_slots=0, p=p) as fl:
+        _flag(fl, lof.LOF_CI16, [d], P)
+
+
 @pytest.mark.parametrize("np_dtype,dtype,sigma", [(np.int16, lof.LOF_CI16, 32), (np.int8, lof.LOF_CI8, 8)])
 def test_in_place_multi_segment_rows(np_dtype, dtype, sigma):
     # rows of several time-pass segments (1024 samples each, overlapping by
