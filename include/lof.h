@@ -183,8 +183,9 @@ typedef struct {
   int32_t ctas_per_sm;     /* resident CTAs per SM: 1 to 4 (default 2) */
   int32_t tile_bytes;      /* cap on the shared-memory bytes of a CTA */
   int32_t fine_bins;       /* counters per exact-selection refinement round */
-  int32_t flag_rows;       /* rows per time-pass task (tile height), 1..64 (default 32) */
-  int32_t stat_samples;    /* samples per statistics task, >= 1024 (default 131072) */
+  int32_t flag_rows;       /* rows per time-pass task (tile height), 1..64 (default 64) */
+  int32_t stat_samples;    /* samples per statistics task, >= 1024 (default 262144;
+                              at most 64 rows) */
 } lof_tuning;
 int lof_set_tuning(lof_ctx *ctx, const lof_tuning *t);
 int lof_get_tuning(const lof_ctx *ctx, lof_tuning *t);

@@ -46,7 +46,7 @@ struct lof_ctx {
   lof_params params{};
   int n_sm = 0;
   int smem_per_sm = 0, smem_optin = 0;
-  lof_tuning tuning{256, 2, 0, 2048, 32, 131072};
+  lof_tuning tuning{256, 2, 0, 2048, 64, 262144};
   // history
   int64_t n_slots = 0;
   int H = 0;
@@ -1232,10 +1232,12 @@ extern "C" int lof_autotune(lof_ctx* c, int dtype, const lof_unit* units, int n_
     cands.push_back(saved);  // one CTA per unit: no launch shape to choose
   } else {
     for (int threads : {128, 256})
-      for (int ctas : {1, 2, 3, 4})
-        for (int rows : {8, 16, 32})
-          for (int samples : {32768, 65536, 131072})
+      for (int ctas : {1, 2, 3, 4}) {
+        if (threads >= 256 && ctas > 2) continue;  // the launch bounds allow two
+        for (int rows : {8, 16, 32, 64})
+          for (int samples : {32768, 65536, 131072, 262144})
             cands.push_back(lof_tuning{threads, ctas, saved.tile_bytes, saved.fine_bins, rows, samples});
+      }
   }
   cudaEvent_t e0, e1;
   cudaEventCreate(&e0);

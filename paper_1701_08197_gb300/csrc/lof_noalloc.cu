@@ -98,7 +98,7 @@ extern "C" int lof_flag_block_noalloc(const lof_params* params, int dtype, const
   cudaDeviceGetAttribute(&h.n_sm, cudaDevAttrMultiProcessorCount, dev);
   cudaDeviceGetAttribute(&h.smem_per_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev);
   cudaDeviceGetAttribute(&h.smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
-  h.tuning = lof_tuning{256, 2, 0, 2048, 32, 131072};
+  h.tuning = lof_tuning{256, 2, 0, 2048, 64, 262144};
   int n_tasks = 0;
   rc = lofk::host_count_tasks(h, dtype, units, n_units, &n_tasks, why, sizeof why);
   if (rc) return fail(rc);
