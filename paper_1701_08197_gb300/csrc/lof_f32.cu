@@ -11,7 +11,8 @@
 //   a5  median and MAD of the finite samples of the kept channels: exact
 //       order statistics by three radix-select passes over monotone 32-bit
 //       keys of the floats (two ranks at once for an even count); the MAD is
-//       taken over float32 keys of |x - median| (relative error <= 2^-24)
+//       taken over float32 keys of |x - median|, formed in float32 from the
+//       median split into two floats (error about a unit in the last place)
 //   a6  SumThreshold along time, one warp per 1024-sample row segment (rows
 //       longer than 1024 overlap by a 120-sample halo, as in the integer
 //       path): flagged samples are replaced by threshold_I and the window
@@ -222,7 +223,14 @@ __device__ void select_pass(const DevUnit& u, const uint8_t* Fc, uint32_t* hist,
   const uint32_t p0 = f.prefix[0], p1 = f.prefix[1];
   const int hs = shift + nbits;  // bits above this digit are fixed
   const bool two = f.n_rank == 2;
-  const double med = f.median_t;
+  // the two ranks of an even count share their prefix until late: then one
+  // histogram serves both
+  const bool same = !two || p0 == p1;
+  // |x - median| in float32 from the median split into two floats: the
+  // error stays within a unit in the last place of the deviation (the keys
+  // are float32 anyway), with no binary64 operation per sample
+  const float med_hi = __double2float_rn(f.median_t);
+  const float med_lo = __double2float_rn(__dsub_rn(f.median_t, static_cast<double>(med_hi)));
   const bool vin = (u.flags & kUnitInVec) != 0;
   const float* gin = static_cast<const float*>(u.in);
   const int nchunk = (T + 127) / 128;  // 32 lanes x 4 samples
@@ -237,18 +245,18 @@ __device__ void select_pass(const DevUnit& u, const uint8_t* Fc, uint32_t* hist,
     for (int j = 0; j < 4; ++j) {
       const float xv = f4at(v, j);
       if (!isfinite(xv)) continue;
-      const float kv = MODE == 0 ? xv : __double2float_rn(fabs(__dsub_rn(static_cast<double>(xv), med)));
+      const float kv = MODE == 0 ? xv : fabsf(__fsub_rn(__fsub_rn(xv, med_hi), med_lo));
       const uint32_t key = fkey(kv);
       const uint32_t hi = hs >= 32 ? 0u : (key >> hs);
       const uint32_t dig = (key >> shift) & static_cast<uint32_t>(nb - 1);
       if (hi == p0) atomicAdd(&hist[dig], 1u);
-      if (two && hi == p1) atomicAdd(&hist[2048 + dig], 1u);
+      if (!same && hi == p1) atomicAdd(&hist[2048 + dig], 1u);
     }
   }
   __syncthreads();
   // pick the digit of each open rank (one warp per rank)
   if (warp < f.n_rank) {
-    const uint32_t* h = hist + 2048 * warp;
+    const uint32_t* h = hist + (same ? 0 : 2048 * warp);
     long long rk = f.rank[warp];
     long long base = 0;
     uint32_t digit = 0;
