@@ -37,6 +37,7 @@ class Params(ctypes.Structure):
         ("enable_freq", ctypes.c_int),
         ("enable_time", ctypes.c_int),
         ("enable_history", ctypes.c_int),
+        ("sir_percent", ctypes.c_int),
     ]
 
 
@@ -60,7 +61,7 @@ def default_params(**kw) -> Params:
     """Paper defaults (Section 2.1: p=1.5, sensitivity=1, 6 sigma at I=1)."""
     d = dict(p=1.5, sensitivity=1.0, start_threshold=6.0, max_window=64, history_len=60,
              history_min=8, history_k=6.0, sigma_estimator=SIGMA_MAD, enable_freq=1,
-             enable_time=1, enable_history=1)
+             enable_time=1, enable_history=1, sir_percent=0)
     d.update(kw)
     return Params(**d)
 
@@ -107,6 +108,9 @@ def lib():
         L.lof_ref_history_commit.argtypes = [P(Params), ctypes.c_int, ctypes.c_void_p,
                                              ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]
         L.lof_ref_history_commit.restype = None
+        L.lof_ref_sir.argtypes = [ctypes.c_void_p, ctypes.c_int64, ctypes.c_int64, ctypes.c_int,
+                                  ctypes.c_void_p, ctypes.c_int64]
+        L.lof_ref_sir.restype = None
         _lib = L
     return _lib
 
@@ -141,6 +145,14 @@ def sum_threshold(params: Params, v, median: float, sigma: float, entry=None) ->
     f = np.zeros(v.size, np.uint8) if entry is None else np.array(entry, dtype=np.uint8).copy()
     lib().lof_ref_sum_threshold(ctypes.byref(params), _ptr(v), v.size, median, sigma, _ptr(f))
     return f
+
+
+def sir(mask, percent: int) -> np.ndarray:
+    """Section 2.2 scale-invariant rank operator on one line of a 0/1 mask."""
+    f = np.ascontiguousarray(mask, dtype=np.uint8).ravel()
+    g = np.zeros(f.size, np.uint8)
+    lib().lof_ref_sir(_ptr(f), f.size, 1, int(percent), _ptr(g), 1)
+    return g
 
 
 def dtype_code(arr: np.ndarray) -> int:

@@ -20,7 +20,12 @@
  *    narrow-band RFI that would otherwise decrease the quality of the
  *    statistics");
  *  - the history flagger keeps one ring of per-channel means, multiplier k,
- *    ties flag (the listing's "if (currentValue < threshold)" keeps them).
+ *    ties flag (the listing's "if (currentValue < threshold)" keeps them);
+ *  - the SIR operator (Section 2.2, optional) is the scale-invariant rank
+ *    operator the section names, with eta = sir_percent / 100: a sample is
+ *    flagged when an interval around it is at least (1 - eta) flagged.  It
+ *    runs on the final mask, along time on every channel and then along
+ *    frequency on every time step, after the history values are staged.
  */
 #include "lof_ref.h"
 
@@ -140,6 +145,33 @@ void lof_ref_sum_threshold(const lof_ref_params *pr, const double *v, int64_t L,
     memcpy(flags, next, (size_t)L);
   }
   free(next);
+}
+
+/* Section 2.2: scale-invariant rank operator on one line.  With integer
+ * weights w = +percent for a flagged sample and -(100 - percent) for an
+ * unflagged one, an interval [a, b) is at least (100 - percent)% flagged
+ * exactly when its weight sum is >= 0.  With prefix sums Q[0] = 0,
+ * Q[i + 1] = Q[i] + w[i], sample x lies in such an interval exactly when
+ * max_{b > x} Q[b] >= min_{a <= x} Q[a] (the sum over [a, b) is Q[b] - Q[a]);
+ * both extremes come from one pass each, so the operator is linear in L. */
+void lof_ref_sir(const uint8_t *f, int64_t L, int64_t stride, int percent, uint8_t *g,
+                 int64_t gstride) {
+  if (L <= 0) return;
+  int64_t *Q = (int64_t *)malloc((size_t)(L + 1) * sizeof(int64_t));
+  int64_t *Qmax = (int64_t *)malloc((size_t)(L + 1) * sizeof(int64_t));
+  Q[0] = 0;
+  for (int64_t i = 0; i < L; ++i)
+    Q[i + 1] = Q[i] + (f[i * stride] ? (int64_t)percent : -(int64_t)(100 - percent));
+  /* Qmax[i] = max of Q[b] over b >= i */
+  Qmax[L] = Q[L];
+  for (int64_t i = L - 1; i >= 0; --i) Qmax[i] = Q[i] > Qmax[i + 1] ? Q[i] : Qmax[i + 1];
+  int64_t qmin = Q[0];
+  for (int64_t x = 0; x < L; ++x) {
+    if (Q[x] < qmin) qmin = Q[x];         /* min of Q[a] over a <= x */
+    g[x * gstride] = (uint8_t)(Qmax[x + 1] >= qmin);
+  }
+  free(Q);
+  free(Qmax);
 }
 
 /* Section 4: "we may have to compute amplitudes first" -- the power of one
@@ -283,16 +315,28 @@ int lof_ref_flag_unit(const lof_ref_params *pr, int dtype, const void *in, int C
     st.n_chan_hist += Fh[c];
   }
 
+  /* The final mask; Section 2.2: the optional SIR operator extends its flagged
+   * ranges, along time on every channel, then along frequency. */
+  uint8_t *Mk = (uint8_t *)malloc((size_t)(N > 0 ? N : 1));
+  for (int c = 0; c < C; ++c)
+    for (int t = 0; t < T; ++t)
+      Mk[(int64_t)c * T + t] = (uint8_t)(Fc[c] || Fh[c] || F[(int64_t)c * T + t]);
+  if (pr->sir_percent > 0) {
+    for (int c = 0; c < C; ++c) lof_ref_sir(Mk + (int64_t)c * T, T, 1, pr->sir_percent, Mk + (int64_t)c * T, 1);
+    for (int t = 0; t < T; ++t) lof_ref_sir(Mk + t, C, T, pr->sir_percent, Mk + t, T);
+  }
+
   /* Apply: flagged data is removed (zeroed) and the mask is reported. */
   for (int c = 0; c < C; ++c)
     for (int t = 0; t < T; ++t) {
-      int f = Fc[c] || Fh[c] || F[(int64_t)c * T + t];
+      int f = Mk[(int64_t)c * T + t];
       st.n_flag_total += f;
       if (mask) mask[(int64_t)c * mask_stride + t] = (uint8_t)f;
       if (out) write_out(dtype, in, (int64_t)c * in_stride + t, out, (int64_t)c * out_stride + t, f);
     }
 
   if (stats) *stats = st;
+  free(Mk);
   free(P);
   free(F);
   free(Fc);

@@ -43,6 +43,7 @@ typedef struct {
   double history_k;       /* history threshold multiplier (6) */
   int sigma_estimator;    /* LOF_REF_SIGMA_MAD or LOF_REF_SIGMA_STD */
   int enable_freq, enable_time, enable_history;
+  int sir_percent;        /* Section 2.2 SIR operator, eta in percent (0 = off) */
 } lof_ref_params;
 
 typedef struct {
@@ -69,6 +70,13 @@ double lof_ref_sigma(const lof_ref_params *pr, const double *x, int64_t n, int i
  * entry flags on input and the result on output. */
 void lof_ref_sum_threshold(const lof_ref_params *pr, const double *v, int64_t L, double median,
                            double sigma, uint8_t *flags);
+
+/* Section 2.2: the scale-invariant rank operator on one line of a mask,
+ * f[i * stride] for i < L (values 0/1).  Output g[i * gstride] = 1 exactly when
+ * some interval [a, b) holding i has at least (100 - percent)% of its samples
+ * flagged in f.  f and g may be the same array. */
+void lof_ref_sir(const uint8_t *f, int64_t L, int64_t stride, int percent, uint8_t *g,
+                 int64_t gstride);
 
 /* One unit (C channels x T samples, time fastest) through the whole hot path.
  * in/out/mask strides are in elements of the respective array.  ring holds
