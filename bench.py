@@ -88,6 +88,8 @@ def parse():
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-plain", action="store_true")
     ap.add_argument("--no-autotune", action="store_true")
+    ap.add_argument("--sir", type=int, default=0,
+                    help="SIR operator percentage (Section 2.2) on the final mask; 0 = off")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--stations", type=int, default=48,
                     help="stations per block (48 = the full configuration; fewer for profiling)")
@@ -193,12 +195,15 @@ def build_units(x, out, mask, stats, slot_base=0):
     return units
 
 
-def workload_config(stations: int) -> dict:
-    return {"workload": f"full LOFAR pre-beamformer block: {stations} st x 2 pol x 8 sb "
-                        f"= {stations * 16} units x 256 ch x 3072 t, complex int16, history 60",
-            "launch": "batched persistent (1 launch per block) + history commit",
-            "l2": "inputs > L2 (2.4 GB at 48 stations), no flush",
-            "per_rank_units": stations * 16}
+def workload_config(stations: int, sir: int = 0) -> dict:
+    c = {"workload": f"full LOFAR pre-beamformer block: {stations} st x 2 pol x 8 sb "
+                     f"= {stations * 16} units x 256 ch x 3072 t, complex int16, history 60",
+         "launch": "batched persistent (1 launch per block) + history commit",
+         "l2": "inputs > L2 (2.4 GB at 48 stations), no flush",
+         "per_rank_units": stations * 16}
+    if sir:
+        c["sir_percent"] = sir
+    return c
 
 
 def max_over_ranks(ms: float, world: int, device) -> float:
@@ -235,7 +240,7 @@ def run_gpu(args):
     out = torch.empty_like(x)
     mask = torch.empty(x.shape[:-1], dtype=torch.uint8, device=dev)
     stats = lof.stats_tensor(n_units, dev)
-    fl = lof.Flagger(local, n_history_slots=n_units * C)
+    fl = lof.Flagger(local, n_history_slots=n_units * C, sir_percent=args.sir)
     # rings pre-filled with 60 means per channel (steady state of the history flagger)
     pw = (x.to(torch.float32) ** 2).sum(-1).mean(-1).reshape(-1).double().cpu().numpy()
     rng = np.random.default_rng(7)
@@ -345,7 +350,7 @@ def run_gpu(args):
     return res
 
 
-def oracle_sample(seconds: float, seed=2):
+def oracle_sample(seconds: float, seed=2, sir=0):
     """The oracle (as it stands) on host cores: units of the same workload, one
     per thread (the paper's thread-per-subband CPU layout), bounded in time."""
     from concurrent.futures import ThreadPoolExecutor
@@ -354,7 +359,7 @@ def oracle_sample(seconds: float, seed=2):
 
     import oracle
     from paper_1701_08197_gb300 import synth
-    P = oracle.default_params()
+    P = oracle.default_params(sir_percent=sir)
     cores = os.cpu_count() or 1
     spec = synth.VoltageSpec(n_station=1, n_pol=N_POL, n_subband=N_SUBBAND, C=C, T=T,
                              sigma=32.0, tone_frac=0.02, impulse_frac=0.01)
@@ -394,7 +399,7 @@ def main():
         steps = []
         cb = None
         for i in range(args.warmup + args.steps):
-            r = oracle_sample(max(2.0, args.cpu_seconds / max(1, args.steps)))
+            r = oracle_sample(max(2.0, args.cpu_seconds / max(1, args.steps)), sir=args.sir)
             if i >= args.warmup:
                 steps.append(r)
             cb = r
@@ -406,7 +411,7 @@ def main():
                 "higher_is_better": True,
                 "scaling": "weak", "vs_baseline": None, "dtype": "int64+f64",
                 "data": "synthetic (seeded)",
-                "config": workload_config(args.stations),
+                "config": workload_config(args.stations, args.sir),
                 "cpu_baseline": {"value": v, "unit": "Msamples/s", "cores": cb["cores"],
                                  "kind": "oracle", "sample": cb["sample"]},
                 "e2e": {"value": v, "unit": "Msamples/s", "h2d_bytes_per_step": 0,
@@ -432,7 +437,7 @@ def main():
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": res["ms_per_step"],
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int32/u64",
         "data": "synthetic (seeded noise + tones + impulses)",
-        "config": dict(workload_config(args.stations), tuning=res["tuning"]),
+        "config": dict(workload_config(args.stations, args.sir), tuning=res["tuning"]),
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                      "frac": achieved / peak, "traffic": measured_traffic(args.stations * 16, res["tuning"]),
                      "kernel": "lof_block_kernel<CI16>", "bytes_per_launch": alg_bytes,
@@ -449,7 +454,7 @@ def main():
     if "e2e" in res:
         line["e2e"] = res["e2e"]
     if not args.no_cpu:
-        line["cpu_baseline"] = oracle_sample(args.cpu_seconds)
+        line["cpu_baseline"] = oracle_sample(args.cpu_seconds, sir=args.sir)
     print(json.dumps(line))
 
 

@@ -89,6 +89,13 @@ typedef struct {
   int32_t enable_freq;     /* frequency pass on (1) / off (0) */
   int32_t enable_time;     /* time pass on / off */
   int32_t enable_history;  /* history flagger on / off */
+  int32_t sir_percent;     /* Section 2.2 scale-invariant rank operator on the final mask,
+                              eta in percent (0 = off, the default; at most 99): a sample
+                              is flagged when some interval holding it, along time or
+                              then along frequency, is at least (100 - eta)% flagged.
+                              Needs the mask output of every unit; runs after the history
+                              values are staged (it changes the mask, the data and
+                              n_flag_total, not the history) */
 } lof_params;
 
 /* Per-unit results, written by lof_flag_block when lof_unit.stats != NULL

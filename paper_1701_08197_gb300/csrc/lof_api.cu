@@ -41,6 +41,11 @@ int64_t round_up64(int64_t x, int64_t m) { return (x + m - 1) / m * m; }
 
 }  // namespace
 
+// lof_sir.cu
+extern "C" int lofk_sir_max_time();
+extern "C" int lofk_launch_sir(const lofk::DevUnit* units, int n_units, int64_t n_chan, int max_chan,
+                               int percent, int es, void* stream);
+
 struct lof_ctx {
   int device = 0;
   lof_params params{};
@@ -176,6 +181,7 @@ extern "C" void lof_default_params(lof_params* p) {
   p->enable_freq = 1;
   p->enable_time = 1;
   p->enable_history = 1;
+  p->sir_percent = 0;
 }
 
 extern "C" const char* lof_last_error(const lof_ctx* c) {
@@ -199,6 +205,10 @@ static int validate_params(const lof_params* p, std::string* why) {
   }
   if (p->sigma_estimator != LOF_SIGMA_MAD && p->sigma_estimator != LOF_SIGMA_STD) {
     *why = "unknown sigma_estimator";
+    return 0;
+  }
+  if (p->sir_percent < 0 || p->sir_percent > 99) {
+    *why = "sir_percent in [0, 99] required";
     return 0;
   }
   return 1;
@@ -634,6 +644,15 @@ int host_launch_kernel(const lof_params& P, const HostCfg& h, int dtype, const P
              pr.plan.smem);
     return LOF_ERR_CUDA;
   }
+  if (P.sir_percent > 0) {
+    // Section 2.2: the SIR operator on the final mask (time, then frequency)
+    const int src = lofk_launch_sir(sc.units, n_units, pr.n_chan, kMaxChan, P.sir_percent,
+                                    esize_of(dtype), stream);
+    if (src != 0) {
+      snprintf(why, nwhy, "SIR launch failed: %d", src);
+      return LOF_ERR_CUDA;
+    }
+  }
   return LOF_OK;
 }
 
@@ -650,6 +669,19 @@ int host_launch(const lof_params& P, const HostCfg& h, int dtype, const Prep& pr
     return LOF_ERR_CUDA;
   }
   return host_launch_kernel(P, h, dtype, pr, sc, n_units, seq, stream, 1, why, nwhy);
+}
+
+// The SIR pass works on the mask output, rows up to lofk_sir_max_time() samples.
+int host_validate_sir(const lof_params& P, const lof_unit& u, int i, char* why, int nwhy) {
+  if (P.sir_percent <= 0) return LOF_OK;
+  if (!u.mask)
+    return snprintf(why, nwhy, "unit %d: the SIR operator (sir_percent > 0) needs the mask output", i),
+           LOF_ERR_INVALID;
+  if (u.n_time > lofk_sir_max_time())
+    return snprintf(why, nwhy, "unit %d: n_time %d above the SIR limit %d", i, u.n_time,
+                    lofk_sir_max_time()),
+           LOF_ERR_INVALID;
+  return LOF_OK;
 }
 
 int host_validate_unit(int dtype, const lof_unit& u, int i, int64_t n_slots, char* why, int nwhy) {
@@ -764,6 +796,8 @@ int validate_units(lof_ctx* c, int dtype, const lof_unit* units, int n_units) {
   if (n_units < 0 || (n_units > 0 && !units)) return fail(c, LOF_ERR_INVALID, "bad unit array");
   for (int i = 0; i < n_units; ++i) {
     rc = lofk::host_validate_unit(dtype, units[i], i, c->n_slots, why, sizeof why);
+    if (rc) return fail(c, rc, "%s", why);
+    rc = lofk::host_validate_sir(c->params, units[i], i, why, sizeof why);
     if (rc) return fail(c, rc, "%s", why);
   }
   return LOF_OK;

@@ -44,6 +44,7 @@ class lof_params(ctypes.Structure):
         ("enable_freq", ctypes.c_int32),
         ("enable_time", ctypes.c_int32),
         ("enable_history", ctypes.c_int32),
+        ("sir_percent", ctypes.c_int32),
     ]
 
 
