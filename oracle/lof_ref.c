@@ -21,6 +21,10 @@
  *    statistics");
  *  - the history flagger keeps one ring of per-channel means, multiplier k,
  *    ties flag (the listing's "if (currentValue < threshold)" keeps them);
+ *  - the integrated time mode (Section 3, time_mode = 1) sums the powers of the
+ *    channels kept by the frequency pass into one series G[t] (entry-flagged
+ *    samples left out), takes the statistics of its T values and runs
+ *    SumThreshold on it; a flagged time step is flagged in every kept channel;
  *  - the SIR operator (Section 2.2, optional) is the scale-invariant rank
  *    operator the section names, with eta = sir_percent / 100: a sample is
  *    flagged when an interval around it is at least (1 - eta) flagged.  It
@@ -263,28 +267,57 @@ int lof_ref_flag_unit(const lof_ref_params *pr, int dtype, const void *in, int C
   if (pr->enable_freq && C > 0) lof_ref_sum_threshold(pr, S, C, st.median_f, st.sigma_f, Fc);
   for (int c = 0; c < C; ++c) st.n_chan_freq += Fc[c];
 
-  /* Section 4 / 4.2: statistics for the time pass pool the samples of the
-   * channels left unflagged by the frequency pass. */
-  int64_t nu = 0;
-  double *U = (double *)malloc((size_t)(N > 0 ? N : 1) * sizeof(double));
-  for (int c = 0; c < C; ++c) {
-    if (Fc[c]) continue;
-    for (int t = 0; t < T; ++t)
-      if (!F[(int64_t)c * T + t]) U[nu++] = P[(int64_t)c * T + t];
-  }
-  if (nu > 0) st.sigma_t = lof_ref_sigma(pr, U, nu, is_int, &st.median_t);
-  free(U);
+  if (pr->time_mode == 1) {
+    /* Section 3: integrate the frequency direction fully for time-domain
+     * flagging, over the channels the frequency pass kept. */
+    double *G = (double *)malloc((size_t)(T > 0 ? T : 1) * sizeof(double));
+    uint8_t *Ft = (uint8_t *)calloc((size_t)(T > 0 ? T : 1), 1);
+    int nkept = 0;
+    for (int c = 0; c < C; ++c) nkept += !Fc[c];
+    for (int t = 0; t < T; ++t) {
+      double g = 0.0;
+      for (int c = 0; c < C; ++c)
+        if (!Fc[c] && !F[(int64_t)c * T + t]) g = g + P[(int64_t)c * T + t];
+      G[t] = g;
+    }
+    if (T > 0 && nkept > 0) {
+      st.sigma_t = lof_ref_sigma(pr, G, T, is_int, &st.median_t);
+      if (pr->enable_time) lof_ref_sum_threshold(pr, G, T, st.median_t, st.sigma_t, Ft);
+    }
+    for (int c = 0; c < C; ++c) {
+      if (Fc[c]) continue;
+      for (int t = 0; t < T; ++t)
+        if (Ft[t] && !F[(int64_t)c * T + t]) {
+          F[(int64_t)c * T + t] = 1;
+          st.n_flag_time++;
+        }
+    }
+    free(G);
+    free(Ft);
+  } else {
+    /* Section 4 / 4.2: statistics for the time pass pool the samples of the
+     * channels left unflagged by the frequency pass. */
+    int64_t nu = 0;
+    double *U = (double *)malloc((size_t)(N > 0 ? N : 1) * sizeof(double));
+    for (int c = 0; c < C; ++c) {
+      if (Fc[c]) continue;
+      for (int t = 0; t < T; ++t)
+        if (!F[(int64_t)c * T + t]) U[nu++] = P[(int64_t)c * T + t];
+    }
+    if (nu > 0) st.sigma_t = lof_ref_sigma(pr, U, nu, is_int, &st.median_t);
+    free(U);
 
-  /* Section 2.1 in the time direction, one channel at a time. */
-  uint8_t *entry = (uint8_t *)malloc((size_t)(T > 0 ? T : 1));
-  for (int c = 0; c < C; ++c) {
-    if (Fc[c] || !pr->enable_time || nu == 0) continue;
-    uint8_t *row = F + (int64_t)c * T;
-    memcpy(entry, row, (size_t)T);
-    lof_ref_sum_threshold(pr, P + (int64_t)c * T, T, st.median_t, st.sigma_t, row);
-    for (int t = 0; t < T; ++t) st.n_flag_time += (row[t] && !entry[t]);
+    /* Section 2.1 in the time direction, one channel at a time. */
+    uint8_t *entry = (uint8_t *)malloc((size_t)(T > 0 ? T : 1));
+    for (int c = 0; c < C; ++c) {
+      if (Fc[c] || !pr->enable_time || nu == 0) continue;
+      uint8_t *row = F + (int64_t)c * T;
+      memcpy(entry, row, (size_t)T);
+      lof_ref_sum_threshold(pr, P + (int64_t)c * T, T, st.median_t, st.sigma_t, row);
+      for (int t = 0; t < T; ++t) st.n_flag_time += (row[t] && !entry[t]);
+    }
+    free(entry);
   }
-  free(entry);
 
   /* Section 4.1: the history flagger, per channel. */
   uint8_t *Fh = (uint8_t *)calloc((size_t)(C > 0 ? C : 1), 1);

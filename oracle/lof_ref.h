@@ -44,6 +44,7 @@ typedef struct {
   int sigma_estimator;    /* LOF_REF_SIGMA_MAD or LOF_REF_SIGMA_STD */
   int enable_freq, enable_time, enable_history;
   int sir_percent;        /* Section 2.2 SIR operator, eta in percent (0 = off) */
+  int time_mode;          /* 0: time pass per channel; 1: on the frequency-integrated series */
 } lof_ref_params;
 
 typedef struct {
