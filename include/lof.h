@@ -77,6 +77,8 @@ enum { LOF_CI8 = 1, LOF_CI16 = 2, LOF_F32 = 3 };
 
 enum { LOF_SIGMA_MAD = 0, LOF_SIGMA_STD = 1 };
 
+enum { LOF_TIME_PER_CHANNEL = 0, LOF_TIME_INTEGRATED = 1 };
+
 typedef struct {
   double p;                /* Section 2.1, default 1.5 */
   double sensitivity;      /* Section 2.1, default 1.0 */
@@ -96,6 +98,13 @@ typedef struct {
                               Needs the mask output of every unit; runs after the history
                               values are staged (it changes the mask, the data and
                               n_flag_total, not the history) */
+  int32_t time_mode;       /* LOF_TIME_PER_CHANNEL (default): SumThreshold along time on
+                              every kept channel with the pooled statistics;
+                              LOF_TIME_INTEGRATED (Section 3): the frequency direction
+                              integrated fully -- one series of the summed powers of the
+                              kept channels, its own median and sigma, one SumThreshold,
+                              a flagged time step flagged in every kept channel.
+                              Integer units only, n_time <= 16384 */
 } lof_params;
 
 /* Per-unit results, written by lof_flag_block when lof_unit.stats != NULL

@@ -26,6 +26,7 @@ UNITS = [
     ("lof_kernels.cu", "lof_kernels_ci8.o", ["-DLOF_KERNEL_DT=1"]),
     ("lof_f32.cu", "lof_f32.o", []),
     ("lof_sir.cu", "lof_sir.o", []),
+    ("lof_integ.cu", "lof_integ.o", []),
     ("lof_api.cu", "lof_api.o", []),
     ("lof_noalloc.cu", "lof_noalloc.o", []),
 ]

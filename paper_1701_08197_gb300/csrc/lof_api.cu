@@ -41,8 +41,10 @@ int64_t round_up64(int64_t x, int64_t m) { return (x + m - 1) / m * m; }
 
 }  // namespace
 
-// lof_sir.cu
+// lof_sir.cu, lof_integ.cu
 extern "C" int lofk_sir_max_time();
+extern "C" int lofk_integ_max_time();
+extern "C" int lofk_launch_integ(int dtype, const lofk::KParams* kp, int n_units, int n_sm, void* stream);
 extern "C" int lofk_launch_sir(const lofk::DevUnit* units, int n_units, int64_t n_chan, int max_chan,
                                int percent, int es, void* stream);
 
@@ -182,6 +184,7 @@ extern "C" void lof_default_params(lof_params* p) {
   p->enable_time = 1;
   p->enable_history = 1;
   p->sir_percent = 0;
+  p->time_mode = LOF_TIME_PER_CHANNEL;
 }
 
 extern "C" const char* lof_last_error(const lof_ctx* c) {
@@ -209,6 +212,10 @@ static int validate_params(const lof_params* p, std::string* why) {
   }
   if (p->sir_percent < 0 || p->sir_percent > 99) {
     *why = "sir_percent in [0, 99] required";
+    return 0;
+  }
+  if (p->time_mode != LOF_TIME_PER_CHANNEL && p->time_mode != LOF_TIME_INTEGRATED) {
+    *why = "unknown time_mode";
     return 0;
   }
   return 1;
@@ -636,6 +643,8 @@ int host_launch_kernel(const lof_params& P, const HostCfg& h, int dtype, const P
   kp.gen_words = pr.gen_words;
   const int krc = dtype == LOF_F32
                       ? lofk_launch_f32(&kp, n_units, h.n_sm, pr.plan.smem, stream)
+                  : P.time_mode == LOF_TIME_INTEGRATED
+                      ? lofk_launch_integ(dtype, &kp, n_units, h.n_sm, stream)
                       : lofk_launch_block(dtype, &kp, pr.grid, pr.plan.threads, pr.plan.smem, stream,
                                           cooperative);
   if (krc != 0) {
@@ -671,8 +680,18 @@ int host_launch(const lof_params& P, const HostCfg& h, int dtype, const Prep& pr
   return host_launch_kernel(P, h, dtype, pr, sc, n_units, seq, stream, 1, why, nwhy);
 }
 
-// The SIR pass works on the mask output, rows up to lofk_sir_max_time() samples.
-int host_validate_sir(const lof_params& P, const lof_unit& u, int i, char* why, int nwhy) {
+// Options with limits of their own: the integrated time mode (integer units,
+// rows up to lofk_integ_max_time() samples) and the SIR pass (the mask output,
+// rows up to lofk_sir_max_time() samples).
+int host_validate_sir(const lof_params& P, int dtype, const lof_unit& u, int i, char* why, int nwhy) {
+  if (P.time_mode == LOF_TIME_INTEGRATED) {
+    if (dtype == LOF_F32)
+      return snprintf(why, nwhy, "the integrated time mode takes integer units only"), LOF_ERR_INVALID;
+    if (u.n_time > lofk_integ_max_time())
+      return snprintf(why, nwhy, "unit %d: n_time %d above the integrated-mode limit %d", i, u.n_time,
+                      lofk_integ_max_time()),
+             LOF_ERR_INVALID;
+  }
   if (P.sir_percent <= 0) return LOF_OK;
   if (!u.mask)
     return snprintf(why, nwhy, "unit %d: the SIR operator (sir_percent > 0) needs the mask output", i),
@@ -797,7 +816,7 @@ int validate_units(lof_ctx* c, int dtype, const lof_unit* units, int n_units) {
   for (int i = 0; i < n_units; ++i) {
     rc = lofk::host_validate_unit(dtype, units[i], i, c->n_slots, why, sizeof why);
     if (rc) return fail(c, rc, "%s", why);
-    rc = lofk::host_validate_sir(c->params, units[i], i, why, sizeof why);
+    rc = lofk::host_validate_sir(c->params, dtype, units[i], i, why, sizeof why);
     if (rc) return fail(c, rc, "%s", why);
   }
   return LOF_OK;

@@ -1,0 +1,534 @@
+// lof_integ.cu -- the integrated time mode for integer voltage units
+// (lof_params.time_mode = 1): Section 3 integrates the time direction fully for
+// frequency flagging and the frequency direction fully for time-domain
+// flagging.  One CTA flags one unit at a time:
+//   a1  powers re^2 + im^2 (exact integers)
+//   a2  row sums S[c] and the column series over all channels, one pass
+//   a3  median and sigma of S (Section 4.2; bitonic sort, exact)
+//   a4  SumThreshold over S (Section 2.1) -> channel flags
+//   a5  the series G[t] over the kept channels (flagged rows subtracted) and
+//       its median and sigma (radix selection on 64-bit keys, exact)
+//   a6  SumThreshold over G -> time flags, applied to every kept channel
+//   a7  history test per channel (Section 4.1; binary64 mean of the unflagged
+//       samples, exact integer sum)
+//   a8  mask and masked data
+// Sums of integer powers are exact in binary64 here (G <= 2048 * 2^31 and
+// window sums < 2^53), so the decisions equal those of the binary64 oracle.
+#include <cstdint>
+
+#include <cuda_runtime.h>
+
+#include "lof_internal.h"
+
+namespace lofk {
+namespace {
+
+constexpr int kNtI = 512, kNwI = kNtI / 32;
+constexpr int kIntegMaxT = 16384;
+constexpr unsigned kFullI = 0xFFFFFFFFu;
+constexpr double kMadToSigma = 1.482602218505602;
+
+// shared memory layout (bytes)
+constexpr int kOffS = 0;                                  // u64 S[kMaxChan]
+constexpr int kOffSrt = kOffS + 8 * kMaxChan;             // u64 sort buffer [kMaxChan]
+constexpr int kOffG = kOffSrt + 8 * kMaxChan;             // u64 G[kIntegMaxT]
+constexpr int kOffHist = kOffG + 8 * kIntegMaxT;          // u32 [2][2048] (two ranks)
+constexpr int kOffFc = kOffHist + 4 * 2 * 2048;           // u8 [kMaxChan]
+constexpr int kOffFcn = kOffFc + kMaxChan;                // u8 [kMaxChan]
+constexpr int kOffFt = kOffFcn + kMaxChan;                // u8 [kIntegMaxT]
+constexpr int kOffFn = kOffFt + kIntegMaxT;               // u8 [kIntegMaxT]
+constexpr int kIntegSmem = kOffFn + kIntegMaxT;
+static_assert(kIntegSmem <= 227 * 1024 - 1024, "one CTA per SM");
+
+struct IntegShared {
+  double median_f, sigma_f, median_t, sigma_t;
+  unsigned long long cnt_time, cnt_total, cnt_hist;
+  unsigned long long pref[2];
+  long long rank[2];
+  int nrank, nkept, nfc;
+  unsigned long long s1lo[kNwI], s1hi[kNwI], s2lo[kNwI], s2hi[kNwI];
+};
+
+template <int DT>
+__device__ __forceinline__ uint32_t ipow(const uint8_t* row, int t) {
+  if constexpr (DT == LOF_CI16) {
+    const uint32_t w = reinterpret_cast<const uint32_t*>(row)[t];
+    const int re = static_cast<int16_t>(w & 0xFFFFu), im = static_cast<int16_t>(w >> 16);
+    return static_cast<uint32_t>(re * re) + static_cast<uint32_t>(im * im);
+  } else {
+    const uint32_t h = reinterpret_cast<const uint16_t*>(row)[t];
+    const int re = static_cast<int8_t>(h & 0xFFu), im = static_cast<int8_t>(h >> 8);
+    return static_cast<uint32_t>(re * re + im * im);
+  }
+}
+
+// Calls fn(t, power) for every sample of a row, lanes in parallel: 16-byte
+// vector loads (four per lane issued before any is used) where the row is
+// 16-byte aligned, plain loads for the rest.
+template <int DT, class FN>
+__device__ __forceinline__ void row_powers(const uint8_t* row, int T, bool vec, FN fn) {
+  constexpr int VS = DT == LOF_CI16 ? 4 : 8, U = 4, STEP = 32 * VS * U;
+  const int lane = threadIdx.x & 31;
+  int t0 = 0;
+  if (vec) {
+    for (; t0 + STEP <= T; t0 += STEP) {
+      uint4 v[U];
+#pragma unroll
+      for (int k = 0; k < U; ++k)
+        v[k] = __ldg(reinterpret_cast<const uint4*>(row) + (t0 + k * 32 * VS) / VS + lane);
+#pragma unroll
+      for (int k = 0; k < U; ++k) {
+        const uint32_t w[4] = {v[k].x, v[k].y, v[k].z, v[k].w};
+#pragma unroll
+        for (int j = 0; j < VS; ++j) {
+          const int t = t0 + k * 32 * VS + lane * VS + j;
+          uint32_t p;
+          if constexpr (DT == LOF_CI16) {
+            const int re = static_cast<int16_t>(w[j] & 0xFFFFu), im = static_cast<int16_t>(w[j] >> 16);
+            p = static_cast<uint32_t>(re * re) + static_cast<uint32_t>(im * im);
+          } else {
+            const uint32_t h = (w[j >> 1] >> (16 * (j & 1))) & 0xFFFFu;
+            const int re = static_cast<int8_t>(h & 0xFFu), im = static_cast<int8_t>(h >> 8);
+            p = static_cast<uint32_t>(re * re + im * im);
+          }
+          fn(t, p);
+        }
+      }
+    }
+  }
+  for (int t = t0 + lane; t < T; t += 32) fn(t, ipow<DT>(row, t));
+}
+
+__device__ __forceinline__ double u128_to_double_i(unsigned __int128 m) {
+  const unsigned long long hi = static_cast<unsigned long long>(m >> 64);
+  const unsigned long long lo = static_cast<unsigned long long>(m);
+  if (hi == 0) return __ull2double_rn(lo);
+  const int s = __clzll(static_cast<long long>(hi));
+  unsigned long long top = s ? ((hi << s) | (lo >> (64 - s))) : hi;
+  const unsigned long long rest = s ? (lo << s) : lo;
+  top |= (rest != 0ull) ? 1ull : 0ull;
+  return ldexp(__ull2double_rn(top), 64 - s);
+}
+
+// Population stddev of n integers from exact moments (the oracle's integer
+// form): sqrt((n * S2 - S1^2) / n^2).  Whole CTA; v(i) gives value i.
+template <class V>
+__device__ double exact_std(long long n, V v, IntegShared& f) {
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  unsigned __int128 s1 = 0, s2 = 0;
+  for (long long i = tid; i < n; i += kNtI) {
+    const unsigned __int128 x = v(i);
+    s1 += x;
+    s2 += x * x;
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    const unsigned long long a = __shfl_xor_sync(kFullI, static_cast<unsigned long long>(s1), o);
+    const unsigned long long b = __shfl_xor_sync(kFullI, static_cast<unsigned long long>(s1 >> 64), o);
+    const unsigned long long c = __shfl_xor_sync(kFullI, static_cast<unsigned long long>(s2), o);
+    const unsigned long long d = __shfl_xor_sync(kFullI, static_cast<unsigned long long>(s2 >> 64), o);
+    s1 += (static_cast<unsigned __int128>(b) << 64) | a;
+    s2 += (static_cast<unsigned __int128>(d) << 64) | c;
+  }
+  if (lane == 0) {
+    f.s1lo[warp] = static_cast<unsigned long long>(s1);
+    f.s1hi[warp] = static_cast<unsigned long long>(s1 >> 64);
+    f.s2lo[warp] = static_cast<unsigned long long>(s2);
+    f.s2hi[warp] = static_cast<unsigned long long>(s2 >> 64);
+  }
+  __syncthreads();
+  unsigned __int128 t1 = 0, t2 = 0;
+  for (int w = 0; w < kNwI; ++w) {
+    t1 += (static_cast<unsigned __int128>(f.s1hi[w]) << 64) | f.s1lo[w];
+    t2 += (static_cast<unsigned __int128>(f.s2hi[w]) << 64) | f.s2lo[w];
+  }
+  __syncthreads();
+  if (n <= 0) return 0.0;
+  const unsigned __int128 M = static_cast<unsigned __int128>(n) * t2 - t1 * t1;
+  const double nn = __dmul_rn(static_cast<double>(n), static_cast<double>(n));
+  return __dsqrt_rn(__ddiv_rn(u128_to_double_i(M), nn));
+}
+
+// Bitonic sort of n (power of two) u64 keys, ascending (whole CTA).
+__device__ void sort_u64(unsigned long long* a, int n) {
+  for (int k = 2; k <= n; k <<= 1)
+    for (int j = k >> 1; j > 0; j >>= 1) {
+      for (int i = threadIdx.x; i < n; i += kNtI) {
+        const int l = i ^ j;
+        if (l > i) {
+          const unsigned long long x = a[i], y = a[l];
+          if (((i & k) == 0) == (x > y)) {
+            a[i] = y;
+            a[l] = x;
+          }
+        }
+      }
+      __syncthreads();
+    }
+}
+
+// Order statistics r0 <= r1 of n u64 keys key(i) (whole CTA): radix selection
+// with digits of 11 bits (the last of 9), one histogram per open rank.
+template <class K>
+__device__ void select2(long long n, long long r0, long long r1, K key, uint32_t* hist, IntegShared& f,
+                        unsigned long long* k0, unsigned long long* k1) {
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  if (tid == 0) {
+    f.pref[0] = f.pref[1] = 0ull;
+    f.rank[0] = r0;
+    f.rank[1] = r1;
+    f.nrank = r0 == r1 ? 1 : 2;
+  }
+  __syncthreads();
+  for (int pass = 0; pass < 6; ++pass) {  // bits 63..53, 52..42, 41..31, 30..20, 19..9, 8..0
+    const int nb = pass < 5 ? 11 : 9;
+    const int sh = pass < 5 ? 53 - 11 * pass : 0;
+    const int hs = sh + nb;
+    for (int i = tid; i < 2 * 2048; i += kNtI) hist[i] = 0u;
+    __syncthreads();
+    const unsigned long long p0 = f.pref[0], p1 = f.pref[1];
+    const bool two = f.nrank == 2, same = !two || p0 == p1;
+    for (long long i = tid; i < n; i += kNtI) {
+      const unsigned long long x = key(i);
+      const unsigned long long hi = hs >= 64 ? 0ull : (x >> hs);
+      const uint32_t dig = static_cast<uint32_t>((x >> sh) & ((1ull << nb) - 1ull));
+      if (hi == p0) atomicAdd(&hist[dig], 1u);
+      if (!same && hi == p1) atomicAdd(&hist[2048 + dig], 1u);
+    }
+    __syncthreads();
+    if (warp < f.nrank) {
+      const uint32_t* h = hist + (same ? 0 : 2048 * warp);
+      long long rk = f.rank[warp], base = 0;
+      uint32_t digit = 0;
+      for (int b0 = 0; b0 < (1 << nb); b0 += 32) {
+        const uint32_t cnt = h[b0 + lane];
+        uint32_t incl = cnt;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+          const uint32_t y = __shfl_up_sync(kFullI, incl, o);
+          if (lane >= o) incl += y;
+        }
+        const uint32_t tot = __shfl_sync(kFullI, incl, 31);
+        if (rk < base + tot) {
+          const unsigned hit = __ballot_sync(kFullI, rk < base + static_cast<long long>(incl));
+          const int l = __ffs(hit) - 1;
+          digit = static_cast<uint32_t>(b0 + l);
+          rk -= base + __shfl_sync(kFullI, incl - cnt, l);
+          break;
+        }
+        base += tot;
+      }
+      if (lane == 0) {
+        f.pref[warp] = (f.pref[warp] << nb) | digit;
+        f.rank[warp] = rk;
+      }
+    }
+    __syncthreads();
+    if (tid == 0 && f.nrank == 1) {
+      f.pref[1] = f.pref[0];
+      f.rank[1] = f.rank[0];
+    }
+    __syncthreads();
+  }
+  *k0 = f.pref[0];
+  *k1 = f.pref[1];
+}
+
+// Section 4.2 median and sigma of n u64 values v(i), exact: the median as
+// m2 / 2 with m2 = the sum of the two middle values (twice the middle one for
+// odd n); the MAD from the keys |2 v - m2| = 2 |v - median|.
+template <class V>
+__device__ void stats_u64(const KParams& kp, long long n, V v, uint32_t* hist, IntegShared& f,
+                          double* med, double* sig) {
+  const long long ra = (n & 1) ? n / 2 : n / 2 - 1, rb = n / 2;
+  unsigned long long a, b;
+  select2(n, ra, rb, v, hist, f, &a, &b);
+  const unsigned long long m2 = a + b;
+  *med = __dmul_rn(static_cast<double>(m2), 0.5);
+  if (kp.sigma_std) {
+    *sig = exact_std(n, v, f);
+    return;
+  }
+  auto dev = [&](long long i) {
+    const unsigned long long x2 = 2ull * v(i);
+    return x2 >= m2 ? x2 - m2 : m2 - x2;
+  };
+  unsigned long long da, db;
+  select2(n, ra, rb, dev, hist, f, &da, &db);
+  const double mad = __dmul_rn(static_cast<double>(da + db), 0.25);
+  *sig = mad > 0.0 ? __dmul_rn(kMadToSigma, mad) : exact_std(n, v, f);
+}
+
+// threshold_I = median + sigma * factor_I * sensitivity (Section 2.1)
+__device__ __forceinline__ double thr_i(const KParams& kp, double m, double s, int k) {
+  return __dadd_rn(m, __dmul_rn(__dmul_rn(s, kp.factor[k]), kp.sensitivity));
+}
+
+// Section 2.1 SumThreshold over v[0..L) (whole CTA), flags in / out in fl,
+// next as scratch: window sums of the unflagged values in binary64 (exact
+// for these integers), a window fires when the sum exceeds (I - n) * thr_I.
+template <class V>
+__device__ void st_1d(const KParams& kp, V v, int L, double med, double sig, uint8_t* fl,
+                      uint8_t* next) {
+  if (!(sig > 0.0) || L <= 0) return;
+  for (int k = 0;; ++k) {
+    const int I = 1 << k;
+    if (I > (1 << kp.max_log_window) || I > L) break;
+    const double thr = thr_i(kp, med, sig, k);
+    for (int i = threadIdx.x; i < L; i += kNtI) next[i] = fl[i];
+    __syncthreads();
+    for (int t = threadIdx.x; t + I <= L; t += kNtI) {
+      int nf = 0;
+      double su = 0.0;
+      for (int j = t; j < t + I; ++j) {
+        if (fl[j]) ++nf;
+        else su = __dadd_rn(su, static_cast<double>(v(j)));
+      }
+      if (su > __dmul_rn(static_cast<double>(I - nf), thr))
+        for (int j = t; j < t + I; ++j) next[j] = 1;
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < L; i += kNtI) fl[i] = next[i];
+    __syncthreads();
+  }
+}
+
+template <int DT>
+__device__ void integ_unit(const KParams& kp, const DevUnit& u, uint8_t* smem, IntegShared& f) {
+  constexpr int ES = DT == LOF_CI16 ? 4 : 2;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int C = u.C, T = u.T;
+  unsigned long long* S = reinterpret_cast<unsigned long long*>(smem + kOffS);
+  unsigned long long* srt = reinterpret_cast<unsigned long long*>(smem + kOffSrt);
+  unsigned long long* G = reinterpret_cast<unsigned long long*>(smem + kOffG);
+  uint32_t* hist = reinterpret_cast<uint32_t*>(smem + kOffHist);
+  uint8_t* Fc = smem + kOffFc;
+  uint8_t* Fcn = smem + kOffFcn;
+  uint8_t* Ft = smem + kOffFt;
+  uint8_t* Fn = smem + kOffFn;
+  const uint8_t* gin = static_cast<const uint8_t*>(u.in);
+  const bool vin = (u.flags & kUnitInVec) != 0;
+  for (int i = tid; i < T; i += kNtI) {
+    G[i] = 0ull;
+    Ft[i] = 0;
+  }
+  for (int i = tid; i < C; i += kNtI) Fc[i] = 0;
+  if (tid == 0) f.cnt_time = f.cnt_total = f.cnt_hist = 0ull;
+  __syncthreads();
+  // a1, a2: row sums and the column series over every channel
+  for (int c = warp; c < C; c += kNwI) {
+    const uint8_t* row = gin + static_cast<int64_t>(c) * u.in_stride * ES;
+    unsigned long long s = 0;
+    row_powers<DT>(row, T, vin, [&](int t, uint32_t p) {
+      s += p;
+      atomicAdd(&G[t], static_cast<unsigned long long>(p));
+    });
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(kFullI, s, o);
+    if (lane == 0) S[c] = s;
+  }
+  __syncthreads();
+  // a3: statistics of the spectrum (sort of the C sums)
+  {
+    int n2 = 1;
+    while (n2 < C) n2 <<= 1;
+    for (int i = tid; i < n2; i += kNtI) srt[i] = i < C ? S[i] : ~0ull;
+    __syncthreads();
+    sort_u64(srt, n2);
+    const long long ra = (C & 1) ? C / 2 : C / 2 - 1, rb = C / 2;
+    const unsigned long long m2 = srt[ra] + srt[rb];
+    const double med = __dmul_rn(static_cast<double>(m2), 0.5);
+    double sig;
+    if (kp.sigma_std) {
+      sig = exact_std(C, [&](long long i) { return S[i]; }, f);
+    } else {
+      __syncthreads();
+      for (int i = tid; i < n2; i += kNtI) {
+        if (i < C) {
+          const unsigned long long x2 = 2ull * S[i];
+          srt[i] = x2 >= m2 ? x2 - m2 : m2 - x2;
+        } else {
+          srt[i] = ~0ull;
+        }
+      }
+      __syncthreads();
+      sort_u64(srt, n2);
+      const double mad = __dmul_rn(static_cast<double>(srt[ra] + srt[rb]), 0.25);
+      sig = mad > 0.0 ? __dmul_rn(kMadToSigma, mad) : exact_std(C, [&](long long i) { return S[i]; }, f);
+    }
+    if (tid == 0) {
+      f.median_f = med;
+      f.sigma_f = sig;
+    }
+    __syncthreads();
+  }
+  // a4: frequency SumThreshold
+  if (kp.enable_freq) st_1d(kp, [&](int i) { return S[i]; }, C, f.median_f, f.sigma_f, Fc, Fcn);
+  __syncthreads();
+  // a5: the series over the kept channels and its statistics
+  for (int c = warp; c < C; c += kNwI) {
+    if (!Fc[c]) continue;
+    const uint8_t* row = gin + static_cast<int64_t>(c) * u.in_stride * ES;
+    row_powers<DT>(row, T, vin, [&](int t, uint32_t p) { atomicAdd(&G[t], 0ull - static_cast<unsigned long long>(p)); });
+  }
+  if (tid == 0) {
+    int nk = 0;
+    for (int c = 0; c < C; ++c) nk += !Fc[c];
+    f.nkept = nk;
+    f.nfc = C - nk;
+  }
+  __syncthreads();
+  double med_t = 0.0, sig_t = 0.0;
+  if (f.nkept > 0) {
+    stats_u64(kp, T, [&](long long i) { return G[i]; }, hist, f, &med_t, &sig_t);
+    // a6: SumThreshold over the series
+    if (kp.enable_time) st_1d(kp, [&](int i) { return G[i]; }, T, med_t, sig_t, Ft, Fn);
+  }
+  __syncthreads();
+  // a7, a8: per channel.  A kept row is summed for the history test while its
+  // mask and data are written as if the test keeps it (one pass over it); the
+  // rare row the test flags is then rewritten whole.
+  const bool inplace = (u.flags & kUnitInPlace) != 0;
+  const bool vout = vin && (u.flags & kUnitOutVec) && (u.flags & kUnitMaskVec) && !inplace;
+  constexpr int VS = ES == 4 ? 4 : 8;
+  for (int c = warp; c < C; c += kNwI) {
+    const uint8_t* row = gin + static_cast<int64_t>(c) * u.in_stride * ES;
+    const long long h = u.hist_slot >= 0 ? u.hist_slot + c : -1;
+    uint8_t* mr = u.mask ? u.mask + static_cast<int64_t>(c) * u.mask_stride : nullptr;
+    uint8_t* orow = u.out ? static_cast<uint8_t*>(u.out) + static_cast<int64_t>(c) * u.out_stride * ES : nullptr;
+    auto put = [&](int t, bool fl) {  // one sample's mask and data
+      if (mr) mr[t] = fl ? 1 : 0;
+      if (orow) {
+        if (ES == 4) {
+          if (fl) reinterpret_cast<uint32_t*>(orow)[t] = 0u;
+          else if (!inplace) reinterpret_cast<uint32_t*>(orow)[t] = reinterpret_cast<const uint32_t*>(row)[t];
+        } else {
+          if (fl) reinterpret_cast<uint16_t*>(orow)[t] = 0;
+          else if (!inplace) reinterpret_cast<uint16_t*>(orow)[t] = reinterpret_cast<const uint16_t*>(row)[t];
+        }
+      }
+    };
+    bool full = Fc[c] != 0;
+    if (!full) {
+      unsigned long long s = 0;
+      int n = 0;
+      int tv = 0;
+      if (vout && mr && orow) {
+        for (; tv + 32 * VS <= T; tv += 32 * VS) {
+          const int t = tv + lane * VS;
+          const uint4 v = __ldg(reinterpret_cast<const uint4*>(row + static_cast<size_t>(t) * ES));
+          uint32_t w[4] = {v.x, v.y, v.z, v.w}, mb[2] = {0u, 0u};
+#pragma unroll
+          for (int j = 0; j < VS; ++j) {
+            uint32_t pw;
+            if constexpr (DT == LOF_CI16) {
+              const int re = static_cast<int16_t>(w[j] & 0xFFFFu), im = static_cast<int16_t>(w[j] >> 16);
+              pw = static_cast<uint32_t>(re * re) + static_cast<uint32_t>(im * im);
+            } else {
+              const uint32_t hh = (w[j >> 1] >> (16 * (j & 1))) & 0xFFFFu;
+              const int re = static_cast<int8_t>(hh & 0xFFu), im = static_cast<int8_t>(hh >> 8);
+              pw = static_cast<uint32_t>(re * re + im * im);
+            }
+            if (Ft[t + j]) {
+              if (ES == 4) w[j] = 0u;
+              else w[j >> 1] &= (j & 1) ? 0x0000FFFFu : 0xFFFF0000u;
+              mb[j >> 2] |= 1u << (8 * (j & 3));
+            } else {
+              s += pw;
+              ++n;
+            }
+          }
+          *reinterpret_cast<uint4*>(orow + static_cast<size_t>(t) * ES) = make_uint4(w[0], w[1], w[2], w[3]);
+          if (VS == 4) *reinterpret_cast<uint32_t*>(mr + t) = mb[0];
+          else *reinterpret_cast<uint2*>(mr + t) = make_uint2(mb[0], mb[1]);
+        }
+      }
+      for (int t = tv + lane; t < T; t += 32) {
+        const bool fl = Ft[t] != 0;
+        if (!fl) {
+          s += ipow<DT>(row, t);
+          ++n;
+        }
+        put(t, fl);
+      }
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) {
+        s += __shfl_xor_sync(kFullI, s, o);
+        n += __shfl_xor_sync(kFullI, n, o);
+      }
+      bool fh = false;
+      if (lane == 0) {
+        if (n > 0) {
+          const double cur = __ddiv_rn(static_cast<double>(s), static_cast<double>(n));
+          double staged = cur;
+          if (kp.enable_history && h >= 0) {
+            const int cnt = kp.hist.count[h];
+            if (cnt >= kp.history_min && cnt > 0) {
+              const double thr = kp.hist.thr[h];
+              if (!(cur < thr)) {
+                fh = true;
+                staged = thr;
+              }
+            }
+          }
+          if (h >= 0) {
+            kp.hist.pend[h] = staged;
+            kp.hist.pend_flag[h] = 1;
+            kp.hist.pend_seq[h] = kp.block_seq;
+          }
+        } else if (h >= 0) {
+          kp.hist.pend_flag[h] = 0;
+        }
+        atomicAdd(&f.cnt_time, static_cast<unsigned long long>(T - n));
+        if (fh) atomicAdd(&f.cnt_hist, 1ull);
+        atomicAdd(&f.cnt_total, fh ? static_cast<unsigned long long>(T) : static_cast<unsigned long long>(T - n));
+      }
+      full = __shfl_sync(kFullI, fh ? 1 : 0, 0) != 0;
+      __syncwarp();  // the row's first writes, by every lane, before a rewrite
+    } else if (lane == 0) {
+      if (h >= 0) kp.hist.pend_flag[h] = 0;
+      atomicAdd(&f.cnt_total, static_cast<unsigned long long>(T));
+    }
+    if (full)
+      for (int t = lane; t < T; t += 32) put(t, true);
+  }
+  __syncthreads();
+  if (tid == 0 && u.stats) {
+    u.stats->median_f = f.median_f;
+    u.stats->sigma_f = f.sigma_f;
+    u.stats->median_t = med_t;
+    u.stats->sigma_t = sig_t;
+    u.stats->n_chan_freq = f.nfc;
+    u.stats->n_flag_time = static_cast<long long>(f.cnt_time);
+    u.stats->n_chan_hist = static_cast<long long>(f.cnt_hist);
+    u.stats->n_flag_total = static_cast<long long>(f.cnt_total);
+  }
+  __syncthreads();
+}
+
+template <int DT>
+__global__ void __launch_bounds__(kNtI, 1) lof_integ_kernel(const KParams kp) {
+  extern __shared__ __align__(16) uint8_t smem[];
+  __shared__ IntegShared f;
+  for (int ui = blockIdx.x; ui < kp.n_units; ui += gridDim.x) integ_unit<DT>(kp, kp.units[ui], smem, f);
+}
+
+}  // namespace
+}  // namespace lofk
+
+extern "C" int lofk_integ_max_time() { return lofk::kIntegMaxT; }
+
+// The integrated time mode over n_units integer units (one CTA per unit).
+extern "C" int lofk_launch_integ(int dtype, const lofk::KParams* kp, int n_units, int n_sm, void* stream) {
+  using namespace lofk;
+  if (n_units <= 0) return 0;
+  const void* k = dtype == LOF_CI16 ? reinterpret_cast<const void*>(&lof_integ_kernel<LOF_CI16>)
+                                    : reinterpret_cast<const void*>(&lof_integ_kernel<LOF_CI8>);
+  if (cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, kIntegSmem) != cudaSuccess)
+    return -2;
+  const int grid = n_units < n_sm ? n_units : n_sm;
+  void* args[] = {const_cast<KParams*>(kp)};
+  const cudaError_t e = cudaLaunchKernel(k, dim3(grid), dim3(kNtI), args, static_cast<size_t>(kIntegSmem),
+                                         static_cast<cudaStream_t>(stream));
+  return e == cudaSuccess ? 0 : static_cast<int>(e);
+}

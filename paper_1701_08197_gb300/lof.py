@@ -21,6 +21,7 @@ LOF_ERR_STATE = -5
 LOF_ERR_UNSUPPORTED = -6
 LOF_CI8, LOF_CI16, LOF_F32 = 1, 2, 3
 LOF_SIGMA_MAD, LOF_SIGMA_STD = 0, 1
+LOF_TIME_PER_CHANNEL, LOF_TIME_INTEGRATED = 0, 1
 
 EXPORTED = [
     "lof_default_params", "lof_create", "lof_flag_block", "lof_flag_block_host",
@@ -45,6 +46,7 @@ class lof_params(ctypes.Structure):
         ("enable_time", ctypes.c_int32),
         ("enable_history", ctypes.c_int32),
         ("sir_percent", ctypes.c_int32),
+        ("time_mode", ctypes.c_int32),
     ]
 
 
