@@ -72,8 +72,13 @@ enum {
  * (Section 4: the power is given); non-finite samples are flagged on entry.
  * F32 statistics agree with binary64 within 1e-6 relative and window sums
  * are float32 trees of at most 64 terms, so a flag can differ from binary64
- * arithmetic only where a window sum lies within ~1e-6 of its threshold. */
-enum { LOF_CI8 = 1, LOF_CI16 = 2, LOF_F32 = 3 };
+ * arithmetic only where a window sum lies within ~1e-6 of its threshold.
+ * CF32: complex float32 visibilities (interleaved re, im; the post-correlation
+ * placement of Section 3), one element = one complex sample of 8 bytes; the
+ * power re^2 + im^2 is formed in float32 and flagged like F32 (same
+ * tolerance; non-finite re or im flags the sample; a flagged sample's output
+ * is 0 + 0i). */
+enum { LOF_CI8 = 1, LOF_CI16 = 2, LOF_F32 = 3, LOF_CF32 = 4 };
 
 enum { LOF_SIGMA_MAD = 0, LOF_SIGMA_STD = 1 };
 

@@ -20,7 +20,7 @@ _LIB_PATH = os.path.join(_HERE, "_build", "liblof_ref.so")
 _lock = threading.Lock()
 _lib = None
 
-CI8, CI16, F32 = 1, 2, 3
+CI8, CI16, F32, CF32 = 1, 2, 3, 4
 SIGMA_MAD, SIGMA_STD = 0, 1
 
 
@@ -163,6 +163,8 @@ def dtype_code(arr: np.ndarray) -> int:
         return CI16
     if arr.dtype == np.float32:
         return F32
+    if arr.dtype == np.complex64:
+        return CF32
     raise TypeError(arr.dtype)
 
 
@@ -187,8 +189,8 @@ class History:
 
 def flag_unit(params: Params, data: np.ndarray, history: History | None = None, c0: int = 0,
               want_out: bool = True):
-    """Flag one unit.  data: int8/int16 array [C, T, 2] (complex voltages) or
-    float32 [C, T] (Stokes I).  Returns dict(mask, out, pending, has_pending, stats)."""
+    """Flag one unit.  data: int8/int16 array [C, T, 2] (complex voltages),
+    float32 [C, T] (Stokes I) or complex64 [C, T] (visibilities).  Returns dict(mask, out, pending, has_pending, stats)."""
     dt = dtype_code(data)
     data = np.ascontiguousarray(data)
     C, T = data.shape[0], data.shape[1]

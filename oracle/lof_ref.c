@@ -20,7 +20,8 @@
  *    narrow-band RFI that would otherwise decrease the quality of the
  *    statistics");
  *  - the history flagger keeps one ring of per-channel means, multiplier k,
- *    ties flag (the listing's "if (currentValue < threshold)" keeps them);
+ *    ties flag (a channel is kept only when its mean is strictly below the
+ *    threshold, as in the paper's code);
  *  - the integrated time mode (Section 3, time_mode = 1) sums the powers of the
  *    channels kept by the frequency pass into one series G[t] (entry-flagged
  *    samples left out), takes the statistics of its T values and runs
@@ -178,8 +179,9 @@ void lof_ref_sir(const uint8_t *f, int64_t L, int64_t stride, int percent, uint8
   free(Qmax);
 }
 
-/* Section 4: "we may have to compute amplitudes first" -- the power of one
- * sample; non-finite Stokes I values are reported through *bad. */
+/* Section 4: the power of one sample (complex input is turned into power
+ * before flagging); non-finite Stokes I values (or a non-finite part of a
+ * complex visibility) are reported through *bad. */
 static double sample_power(int dtype, const void *in, int64_t idx, int *bad) {
   *bad = 0;
   if (dtype == LOF_REF_CI8) {
@@ -189,6 +191,15 @@ static double sample_power(int dtype, const void *in, int64_t idx, int *bad) {
   }
   if (dtype == LOF_REF_CI16) {
     const int16_t *p = (const int16_t *)in + 2 * idx;
+    double re = (double)p[0], im = (double)p[1];
+    return re * re + im * im;
+  }
+  if (dtype == LOF_REF_CF32) {
+    const float *p = (const float *)in + 2 * idx;
+    if (!isfinite(p[0]) || !isfinite(p[1])) {
+      *bad = 1;
+      return 0.0;
+    }
     double re = (double)p[0], im = (double)p[1];
     return re * re + im * im;
   }
@@ -212,6 +223,11 @@ static void write_out(int dtype, const void *in, int64_t iidx, void *out, int64_
     int16_t *d = (int16_t *)out + 2 * oidx;
     d[0] = flagged ? 0 : s[0];
     d[1] = flagged ? 0 : s[1];
+  } else if (dtype == LOF_REF_CF32) {
+    const float *s = (const float *)in + 2 * iidx;
+    float *d = (float *)out + 2 * oidx;
+    d[0] = flagged ? 0.0f : s[0];
+    d[1] = flagged ? 0.0f : s[1];
   } else {
     float v = ((const float *)in)[iidx];
     ((float *)out)[oidx] = flagged ? 0.0f : v;
@@ -238,8 +254,10 @@ int lof_ref_flag_unit(const lof_ref_params *pr, int dtype, const void *in, int C
                       int64_t mask_stride, const double *ring, const int32_t *ring_count,
                       double *pending, uint8_t *has_pending, lof_ref_stats *stats) {
   if (!pr || !in || C < 0 || T < 0) return -1;
-  if (dtype != LOF_REF_CI8 && dtype != LOF_REF_CI16 && dtype != LOF_REF_F32) return -1;
-  const int is_int = dtype != LOF_REF_F32;
+  if (dtype != LOF_REF_CI8 && dtype != LOF_REF_CI16 && dtype != LOF_REF_F32 &&
+      dtype != LOF_REF_CF32)
+    return -1;
+  const int is_int = dtype == LOF_REF_CI8 || dtype == LOF_REF_CI16;
   const int64_t N = (int64_t)C * T;
   lof_ref_stats st;
   memset(&st, 0, sizeof st);

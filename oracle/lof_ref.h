@@ -30,7 +30,8 @@
 extern "C" {
 #endif
 
-enum { LOF_REF_CI8 = 1, LOF_REF_CI16 = 2, LOF_REF_F32 = 3 };
+enum { LOF_REF_CI8 = 1, LOF_REF_CI16 = 2, LOF_REF_F32 = 3,
+       LOF_REF_CF32 = 4 /* complex float32 visibilities (post-correlation) */ };
 enum { LOF_REF_SIGMA_MAD = 0, LOF_REF_SIGMA_STD = 1 };
 
 typedef struct {

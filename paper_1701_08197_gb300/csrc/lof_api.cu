@@ -34,14 +34,19 @@ int esize_of(int dtype) {
     case LOF_CI8: return 2;
     case LOF_CI16: return 4;
     case LOF_F32: return 4;
+    case LOF_CF32: return 8;
     default: return 0;
   }
 }
+// the float path (one CTA per unit): Stokes I power or complex visibilities
+bool is_float(int dtype) { return dtype == LOF_F32 || dtype == LOF_CF32; }
 int64_t round_up64(int64_t x, int64_t m) { return (x + m - 1) / m * m; }
 
 }  // namespace
 
-// lof_sir.cu, lof_integ.cu
+// lof_f32.cu, lof_sir.cu, lof_integ.cu
+extern "C" int lofk_launch_f32x(const lofk::KParams* kp, int n_units, int n_sm, int smem_bytes,
+                                void* stream, int cplx);
 extern "C" int lofk_sir_max_time();
 extern "C" int lofk_integ_max_time();
 extern "C" int lofk_launch_integ(int dtype, const lofk::KParams* kp, int n_units, int n_sm, void* stream);
@@ -414,7 +419,7 @@ namespace lofk {
 
 int host_count_tasks(const HostCfg& h, int dtype, const lof_unit* units, int n_units,
                      int* n_tasks, char* why, int nwhy) {
-  if (dtype == LOF_F32) {  // one CTA per unit, no task queue
+  if (is_float(dtype)) {  // one CTA per unit, no task queue
     for (int i = 0; i < n_units; ++i)
       if (lofk_f32_smem(units[i].n_time) > h.smem_optin) {
         snprintf(why, nwhy, "n_time %d does not fit the shared-memory budget", units[i].n_time);
@@ -484,7 +489,7 @@ int host_prepare_f32(const HostCfg& h, const lof_unit* units, int n_units, DevUn
 
 int host_prepare(const HostCfg& h, int dtype, const lof_unit* units, int n_units, DevUnit* du,
                  Task* tasks, int max_tasks, Prep* out, char* why, int nwhy) {
-  if (dtype == LOF_F32) return host_prepare_f32(h, units, n_units, du, out);
+  if (is_float(dtype)) return host_prepare_f32(h, units, n_units, du, out);
   const int es = esize_of(dtype);
   // plan over the distinct row lengths (bounded scan; units share few shapes)
   int Ts[64];
@@ -599,7 +604,7 @@ int host_launch_kernel(const lof_params& P, const HostCfg& h, int dtype, const P
                        char* why, int nwhy) {
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   cudaError_t e;
-  if (dtype != LOF_F32 &&
+  if (!is_float(dtype) &&
       ((e = cudaMemset2DAsync(sc.ustate, sizeof(UnitState), 0, kUnitStateZeroBytes, n_units, st)) !=
            cudaSuccess ||
        (e = cudaMemsetAsync(sc.ctrl, 0, sizeof(int), st)) != cudaSuccess)) {
@@ -641,8 +646,8 @@ int host_launch_kernel(const lof_params& P, const HostCfg& h, int dtype, const P
   kp.dyn_smem = pr.plan.smem;
   kp.gen_scratch = sc.gen;
   kp.gen_words = pr.gen_words;
-  const int krc = dtype == LOF_F32
-                      ? lofk_launch_f32(&kp, n_units, h.n_sm, pr.plan.smem, stream)
+  const int krc = is_float(dtype)
+                      ? lofk_launch_f32x(&kp, n_units, h.n_sm, pr.plan.smem, stream, dtype == LOF_CF32)
                   : P.time_mode == LOF_TIME_INTEGRATED
                       ? lofk_launch_integ(dtype, &kp, n_units, h.n_sm, stream)
                       : lofk_launch_block(dtype, &kp, pr.grid, pr.plan.threads, pr.plan.smem, stream,
@@ -685,7 +690,7 @@ int host_launch(const lof_params& P, const HostCfg& h, int dtype, const Prep& pr
 // rows up to lofk_sir_max_time() samples).
 int host_validate_sir(const lof_params& P, int dtype, const lof_unit& u, int i, char* why, int nwhy) {
   if (P.time_mode == LOF_TIME_INTEGRATED) {
-    if (dtype == LOF_F32)
+    if (is_float(dtype))
       return snprintf(why, nwhy, "the integrated time mode takes integer units only"), LOF_ERR_INVALID;
     if (u.n_time > lofk_integ_max_time())
       return snprintf(why, nwhy, "unit %d: n_time %d above the integrated-mode limit %d", i, u.n_time,
@@ -779,7 +784,7 @@ int flag_block_device(lof_ctx* c, int dtype, const lof_unit* units, int n_units,
   if (rc) return fail(c, rc, "lof_flag_block: %s", why);
   if ((rc = grow(c, &c->d_units, &c->cap_units, n_units, "units"))) return rc;
   if ((rc = grow(c, &c->d_tasks, &c->cap_tasks, pr.n_tasks, "tasks"))) return rc;
-  if ((rc = grow(c, &c->d_ustate, &c->cap_ustate, dtype == LOF_F32 ? 1 : n_units, "unit state")))
+  if ((rc = grow(c, &c->d_ustate, &c->cap_ustate, is_float(dtype) ? 1 : n_units, "unit state")))
     return rc;
   if ((rc = grow(c, &c->d_chanS, &c->cap_chan, static_cast<size_t>(pr.n_chan), "spectrum"))) return rc;
   if ((rc = grow(c, &c->d_chanFc, &c->cap_chanfc, static_cast<size_t>(pr.n_chan), "channel flags")))
@@ -1176,7 +1181,7 @@ extern "C" int lof_graph_create(lof_ctx* c, int dtype, const lof_unit* units, in
   g->dtype = dtype;
   g->n_units = n_units;
   cudaError_t e;
-  const size_t nus = dtype == LOF_F32 ? 1 : static_cast<size_t>(n_units);
+  const size_t nus = is_float(dtype) ? 1 : static_cast<size_t>(n_units);
   if ((e = cudaMalloc(&g->d_units, n_units * sizeof(DevUnit))) != cudaSuccess ||
       (e = cudaMalloc(&g->d_tasks, std::max(1, pr.n_tasks) * sizeof(Task))) != cudaSuccess ||
       (e = cudaMalloc(&g->d_ustate, nus * sizeof(UnitState))) != cudaSuccess ||
@@ -1281,7 +1286,7 @@ extern "C" int lof_autotune(lof_ctx* c, int dtype, const lof_unit* units, int n_
   cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
   const lof_tuning saved = c->tuning;
   std::vector<lof_tuning> cands;
-  if (dtype == LOF_F32) {
+  if (is_float(dtype)) {
     cands.push_back(saved);  // one CTA per unit: no launch shape to choose
   } else {
     for (int threads : {128, 256})

@@ -1,4 +1,6 @@
-// lof_f32.cu -- the flagger for float32 Stokes I units (power given).
+// lof_f32.cu -- the flagger for float32 units: Stokes I power (LOF_F32), or
+// complex float32 visibilities (LOF_CF32, the post-correlation placement of
+// Section 3) whose power |V|^2 = re^2 + im^2 is formed in float32 on load.
 //
 // One CTA flags one unit at a time (units are independent; a launch takes a
 // whole block of units, grid-strided).  Steps, in the order of the paper's
@@ -105,13 +107,33 @@ __device__ __forceinline__ double thr_of(const KParams& kp, double m, double s, 
   return __dadd_rn(m, __dmul_rn(__dmul_rn(s, kp.factor[k]), kp.sensitivity));
 }
 
-// 4 float samples of row r at x (x a multiple of 4); non-finite and past-T
-// samples come back as NaN.
+// Power of a complex float32 sample, in float32 (non-finite if re or im is).
+__device__ __forceinline__ float cpw(float re, float im) {
+  return __fadd_rn(__fmul_rn(re, re), __fmul_rn(im, im));
+}
+// Power of sample t of a row: IN = 0 the value itself (Stokes I), IN = 1 the
+// |V|^2 of the complex value (re, im interleaved).
+template <int IN>
+__device__ __forceinline__ float fat(const float* row, int t) {
+  if constexpr (IN == 0) return row[t];
+  else return cpw(row[2 * t], row[2 * t + 1]);
+}
+// Powers of 4 samples of a row at x (x a multiple of 4); non-finite and
+// past-T samples come back as NaN.
+template <int IN>
 __device__ __forceinline__ float4 ld4(const float* row, int x, int T, bool vec) {
-  if (vec && x + 4 <= T) return __ldg(reinterpret_cast<const float4*>(row + x));
+  if constexpr (IN == 0) {
+    if (vec && x + 4 <= T) return __ldg(reinterpret_cast<const float4*>(row + x));
+  } else {
+    if (vec && x + 4 <= T) {
+      const float4 a = __ldg(reinterpret_cast<const float4*>(row + 2 * x));
+      const float4 b = __ldg(reinterpret_cast<const float4*>(row + 2 * x + 4));
+      return make_float4(cpw(a.x, a.y), cpw(a.z, a.w), cpw(b.x, b.y), cpw(b.z, b.w));
+    }
+  }
   float a[4];
 #pragma unroll
-  for (int j = 0; j < 4; ++j) a[j] = x + j < T ? row[x + j] : __int_as_float(0x7FC00000);
+  for (int j = 0; j < 4; ++j) a[j] = x + j < T ? fat<IN>(row, x + j) : __int_as_float(0x7FC00000);
   return make_float4(a[0], a[1], a[2], a[3]);
 }
 __device__ __forceinline__ float f4at(const float4& v, int j) {
@@ -213,7 +235,7 @@ __device__ void spectrum_sum_threshold(const KParams& kp, const double* S, int C
 // One radix-select pass over the finite samples of the kept rows: histogram
 // of the 11 (or 10) key bits below those already fixed, for each open rank.
 // MODE 0: keys of x; MODE 1: keys of float(|x - median_t|).
-template <int MODE>
+template <int MODE, int IN>
 __device__ void select_pass(const DevUnit& u, const uint8_t* Fc, uint32_t* hist, int shift,
                             int nbits, F32Shared& f) {
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
@@ -237,10 +259,10 @@ __device__ void select_pass(const DevUnit& u, const uint8_t* Fc, uint32_t* hist,
   for (int item = warp; item < u.C * nchunk; item += kNwF) {
     const int c = item / nchunk, s = item - c * nchunk;
     if (Fc[c]) continue;
-    const float* row = gin + static_cast<int64_t>(c) * u.in_stride;
+    const float* row = gin + static_cast<int64_t>(c) * u.in_stride * (IN + 1);
     const int x = s * 128 + lane * 4;
     if (x >= T) continue;
-    const float4 v = ld4(row, x, T, vin);
+    const float4 v = ld4<IN>(row, x, T, vin);
 #pragma unroll
     for (int j = 0; j < 4; ++j) {
       const float xv = f4at(v, j);
@@ -295,7 +317,7 @@ __device__ void select_pass(const DevUnit& u, const uint8_t* Fc, uint32_t* hist,
   __syncthreads();
 }
 
-template <int MODE>
+template <int MODE, int IN>
 __device__ double select_median(const DevUnit& u, const uint8_t* Fc, uint32_t* hist, F32Shared& f) {
   const long long N = f.n_pool;
   if (threadIdx.x == 0) {
@@ -305,15 +327,16 @@ __device__ double select_median(const DevUnit& u, const uint8_t* Fc, uint32_t* h
     f.n_rank = (N & 1) ? 1 : 2;
   }
   __syncthreads();
-  select_pass<MODE>(u, Fc, hist, 21, 11, f);
-  select_pass<MODE>(u, Fc, hist, 10, 11, f);
-  select_pass<MODE>(u, Fc, hist, 0, 10, f);
+  select_pass<MODE, IN>(u, Fc, hist, 21, 11, f);
+  select_pass<MODE, IN>(u, Fc, hist, 10, 11, f);
+  select_pass<MODE, IN>(u, Fc, hist, 0, 10, f);
   const double a = static_cast<double>(fkey_val(f.prefix[0]));
   const double b = static_cast<double>(fkey_val(f.prefix[1]));
   return (N & 1) ? a : __dmul_rn(__dadd_rn(a, b), 0.5);
 }
 
 // population stddev of the pooled finite samples (binary64, two passes)
+template <int IN>
 __device__ double pooled_std(const DevUnit& u, const uint8_t* Fc, F32Shared& f) {
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const float* gin = static_cast<const float*>(u.in);
@@ -324,9 +347,9 @@ __device__ double pooled_std(const DevUnit& u, const uint8_t* Fc, F32Shared& f) 
     double s = 0.0;
     for (int c = warp; c < u.C; c += kNwF) {
       if (Fc[c]) continue;
-      const float* row = gin + static_cast<int64_t>(c) * u.in_stride;
+      const float* row = gin + static_cast<int64_t>(c) * u.in_stride * (IN + 1);
       for (int t = lane; t < T; t += 32) {
-        const float xv = row[t];
+        const float xv = fat<IN>(row, t);
         if (!isfinite(xv)) continue;
         const double d = pass == 0 ? static_cast<double>(xv) : __dsub_rn(static_cast<double>(xv), mu);
         s = pass == 0 ? __dadd_rn(s, d) : __dadd_rn(s, __dmul_rn(d, d));
@@ -382,6 +405,7 @@ __device__ __forceinline__ uint32_t wf_fire(const WfRow& R, int lane, float tI, 
 // Flags of segment sg of one row (rows past 1024 samples overlap by a halo of
 // 120 samples); interior flag words go to Mrow, returns the interior's number
 // of flagged samples, entry-flagged samples and unflagged sum.
+template <int IN>
 __device__ void wf_segment(const float* row, int T, int sg, bool vin, const F32Shared& f,
                            uint32_t* Mrow, int& nflag, int& nentry, double& su) {
   constexpr int SPAN = 32 * kNplF;
@@ -399,7 +423,7 @@ __device__ void wf_segment(const float* row, int T, int sg, bool vin, const F32S
 #pragma unroll
   for (int q = 0; q < kNplF / 4; ++q) {
     const int x = xl + 4 * q;
-    const float4 v = x < T ? ld4(row, x, T, vin) : make_float4(0.f, 0.f, 0.f, 0.f);
+    const float4 v = x < T ? ld4<IN>(row, x, T, vin) : make_float4(0.f, 0.f, 0.f, 0.f);
 #pragma unroll
     for (int j = 0; j < 4; ++j) {
       const float xv = f4at(v, j);
@@ -447,6 +471,7 @@ __device__ void wf_segment(const float* row, int T, int sg, bool vin, const F32S
 }
 
 // Entry flags (non-finite samples) of a row without a time pass.
+template <int IN>
 __device__ void wf_entry_only(const float* row, int T, uint32_t* Mrow, int& nflag, double& su) {
   const int lane = threadIdx.x & 31;
   int nf = 0;
@@ -454,7 +479,7 @@ __device__ void wf_entry_only(const float* row, int T, uint32_t* Mrow, int& nfla
   for (int w = lane; w < (T + 31) / 32; w += 32) {
     uint32_t m = 0u;
     for (int j = 0; j < 32 && 32 * w + j < T; ++j) {
-      const float xv = row[32 * w + j];
+      const float xv = fat<IN>(row, 32 * w + j);
       if (!isfinite(xv)) m |= 1u << j;
       else s = __dadd_rn(s, static_cast<double>(xv));
     }
@@ -466,6 +491,7 @@ __device__ void wf_entry_only(const float* row, int T, uint32_t* Mrow, int& nfla
 }
 
 // ---- one unit
+template <int IN>
 __device__ void f32_unit(const KParams& kp, const DevUnit& u, uint8_t* smem, F32Shared& f) {
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int C = u.C, T = u.T;
@@ -485,11 +511,11 @@ __device__ void f32_unit(const KParams& kp, const DevUnit& u, uint8_t* smem, F32
   }
   // a2: row sums of the finite samples (binary64)
   for (int c = warp; c < C; c += kNwF) {
-    const float* row = gin + static_cast<int64_t>(c) * u.in_stride;
+    const float* row = gin + static_cast<int64_t>(c) * u.in_stride * (IN + 1);
     double s = 0.0;
     int nfin = 0;
     for (int x = lane * 4; x < T; x += 128) {
-      const float4 v = ld4(row, x, T, vin);
+      const float4 v = ld4<IN>(row, x, T, vin);
 #pragma unroll
       for (int j = 0; j < 4; ++j) {
         const float xv = f4at(v, j);
@@ -539,13 +565,13 @@ __device__ void f32_unit(const KParams& kp, const DevUnit& u, uint8_t* smem, F32
   __syncthreads();
   double med = 0.0, sig = 0.0;
   if (f.n_pool > 0) {
-    med = select_median<0>(u, Fc, hist, f);
+    med = select_median<0, IN>(u, Fc, hist, f);
     if (tid == 0) f.median_t = med;
     __syncthreads();
     double mad = 0.0;
-    if (!kp.sigma_std) mad = select_median<1>(u, Fc, hist, f);
+    if (!kp.sigma_std) mad = select_median<1, IN>(u, Fc, hist, f);
     if (!kp.sigma_std && mad > 0.0) sig = __dmul_rn(1.482602218505602, mad);
-    else sig = pooled_std(u, Fc, f);
+    else sig = pooled_std<IN>(u, Fc, f);
   }
   if (tid == 0) {
     if (!f.ok) set_error_f(kp, kErrSelect, 700);
@@ -577,7 +603,7 @@ __device__ void f32_unit(const KParams& kp, const DevUnit& u, uint8_t* smem, F32
   const bool vout = (u.flags & kUnitOutVec) != 0;
   const bool inplace = (u.flags & kUnitInPlace) != 0;
   for (int c = warp; c < C; c += kNwF) {
-    const float* row = gin + static_cast<int64_t>(c) * u.in_stride;
+    const float* row = gin + static_cast<int64_t>(c) * u.in_stride * (IN + 1);
     const long long h = u.hist_slot >= 0 ? u.hist_slot + c : -1;
     bool full = Fc[c] != 0;
     int nflag = 0;
@@ -588,13 +614,13 @@ __device__ void f32_unit(const KParams& kp, const DevUnit& u, uint8_t* smem, F32
         for (int sg = 0; sg < nsg; ++sg) {
           int a, b;
           double s;
-          wf_segment(row, T, sg, vin, f, Mrow, a, b, s);
+          wf_segment<IN>(row, T, sg, vin, f, Mrow, a, b, s);
           nflag += a;
           nentry += b;
           su = __dadd_rn(su, s);
         }
       } else {
-        wf_entry_only(row, T, Mrow, nflag, su);
+        wf_entry_only<IN>(row, T, Mrow, nflag, su);
         nentry = nflag;
       }
       __syncwarp();
@@ -646,7 +672,29 @@ __device__ void f32_unit(const KParams& kp, const DevUnit& u, uint8_t* smem, F32
         if (mask_vec && nv == 4) *reinterpret_cast<uint32_t*>(mr + x) = (bits * 0x00204081u) & 0x01010101u;
         else for (int j = 0; j < nv; ++j) mr[x + j] = static_cast<uint8_t>((bits >> j) & 1u);
       }
-      if (u.out) {
+      if (u.out && IN == 1) {
+        // complex samples: both floats of a flagged sample zeroed
+        float* orow = static_cast<float*>(u.out) + gi * u.out_stride * 2;
+        if (inplace) {
+          for (int j = 0; j < nv; ++j)
+            if ((bits >> j) & 1u) orow[2 * (x + j)] = orow[2 * (x + j) + 1] = 0.0f;
+        } else if (vin && vout && nv == 4) {
+          float4 a = __ldg(reinterpret_cast<const float4*>(row + 2 * x));
+          float4 b = __ldg(reinterpret_cast<const float4*>(row + 2 * x + 4));
+          if (bits & 1u) a.x = a.y = 0.0f;
+          if (bits & 2u) a.z = a.w = 0.0f;
+          if (bits & 4u) b.x = b.y = 0.0f;
+          if (bits & 8u) b.z = b.w = 0.0f;
+          __stcs(reinterpret_cast<float4*>(orow + 2 * x), a);
+          __stcs(reinterpret_cast<float4*>(orow + 2 * x + 4), b);
+        } else {
+          for (int j = 0; j < nv; ++j) {
+            const bool fl = (bits >> j) & 1u;
+            orow[2 * (x + j)] = fl ? 0.0f : row[2 * (x + j)];
+            orow[2 * (x + j) + 1] = fl ? 0.0f : row[2 * (x + j) + 1];
+          }
+        }
+      } else if (u.out) {
         float* orow = static_cast<float*>(u.out) + gi * u.out_stride;
         if (inplace) {
           for (int j = 0; j < nv; ++j)
@@ -679,12 +727,13 @@ __device__ void f32_unit(const KParams& kp, const DevUnit& u, uint8_t* smem, F32
   __syncthreads();
 }
 
+template <int IN>
 __global__ void __launch_bounds__(kNtF, 2) lof_f32_kernel(const KParams kp) {
   extern __shared__ __align__(16) uint8_t smem[];
   __shared__ F32Shared f;
   for (int ui = blockIdx.x; ui < kp.n_units; ui += gridDim.x) {
     const DevUnit u = kp.units[ui];
-    f32_unit(kp, u, smem, f);
+    f32_unit<IN>(kp, u, smem, f);
   }
 }
 
@@ -696,20 +745,26 @@ extern "C" int lofk_f32_smem(int max_T) {
   return lofk::kFixedBytesF + lofk::kNwF * ((max_T + 31) / 32) * 4;
 }
 
-extern "C" int lofk_launch_f32(const lofk::KParams* kp, int n_units, int n_sm, int smem_bytes,
-                               void* stream) {
+// Float units: cplx = 0 Stokes I power, 1 complex float32 visibilities.
+extern "C" int lofk_launch_f32x(const lofk::KParams* kp, int n_units, int n_sm, int smem_bytes,
+                                void* stream, int cplx) {
   using namespace lofk;
   if (n_units <= 0) return 0;
-  if (cudaFuncSetAttribute(reinterpret_cast<const void*>(&lof_f32_kernel),
-                           cudaFuncAttributeMaxDynamicSharedMemorySize, smem_bytes) != cudaSuccess)
+  const void* k = cplx ? reinterpret_cast<const void*>(&lof_f32_kernel<1>)
+                       : reinterpret_cast<const void*>(&lof_f32_kernel<0>);
+  if (cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_bytes) != cudaSuccess)
     return -2;
   int occ = 0;
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, lof_f32_kernel, kNtF, smem_bytes) !=
-          cudaSuccess ||
-      occ < 1)
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k, kNtF, smem_bytes) != cudaSuccess || occ < 1)
     return -3;
   const int grid = n_units < n_sm * occ ? n_units : n_sm * occ;
-  lof_f32_kernel<<<grid, kNtF, smem_bytes, static_cast<cudaStream_t>(stream)>>>(*kp);
-  const cudaError_t e = cudaGetLastError();
+  void* args[] = {const_cast<KParams*>(kp)};
+  const cudaError_t e = cudaLaunchKernel(k, dim3(grid), dim3(kNtF), args, static_cast<size_t>(smem_bytes),
+                                         static_cast<cudaStream_t>(stream));
   return e == cudaSuccess ? 0 : static_cast<int>(e);
+}
+
+extern "C" int lofk_launch_f32(const lofk::KParams* kp, int n_units, int n_sm, int smem_bytes,
+                               void* stream) {
+  return lofk_launch_f32x(kp, n_units, n_sm, smem_bytes, stream, 0);
 }

@@ -130,7 +130,7 @@ extern "C" int lof_flag_block_noalloc(const lof_params* params, int dtype, const
   sc.chanFc = base + off;
   off += up256(static_cast<size_t>(pr.n_chan));
   sc.ustate = reinterpret_cast<lofk::UnitState*>(base + off);
-  off += up256(static_cast<size_t>(dtype == LOF_F32 ? 0 : n_units) * sizeof(lofk::UnitState));
+  off += up256(static_cast<size_t>((dtype == LOF_F32 || dtype == LOF_CF32) ? 0 : n_units) * sizeof(lofk::UnitState));
   sc.gen = reinterpret_cast<uint32_t*>(base + off);
   off += static_cast<size_t>(std::max(1, pr.grid)) * std::max(1, pr.gen_words) * 4;
   if (off > kScratchBytes) {

@@ -169,7 +169,8 @@ __device__ __forceinline__ int unit_of(const DevUnit* units, int n_units, int64_
 }
 
 __device__ __forceinline__ void zero_sample(void* row, int64_t t, int es) {
-  if (es == 4) reinterpret_cast<uint32_t*>(row)[t] = 0u;
+  if (es == 8) reinterpret_cast<unsigned long long*>(row)[t] = 0ull;
+  else if (es == 4) reinterpret_cast<uint32_t*>(row)[t] = 0u;
   else reinterpret_cast<uint16_t*>(row)[t] = 0;
 }
 
