@@ -457,7 +457,8 @@ def main():
         "latency_ms": {"batched_p50": pct(step_sorted, 0.5), "batched_p99": pct(step_sorted, 0.99),
                        "deadline_ms": T * 1.31072},
         "clocks": res["clocks"],
-        "gpu_launches": 2 * args.steps,
+        # per step: the flag kernel, the history commit and, with --sir, its two kernels
+        "gpu_launches": (2 + (2 if args.sir else 0)) * args.steps,
     }
     if "plain_ms" in res:
         pm = sorted(res["plain_ms"])

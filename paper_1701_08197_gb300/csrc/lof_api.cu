@@ -688,7 +688,7 @@ int host_launch(const lof_params& P, const HostCfg& h, int dtype, const Prep& pr
 // Options with limits of their own: the integrated time mode (integer units,
 // rows up to lofk_integ_max_time() samples) and the SIR pass (the mask output,
 // rows up to lofk_sir_max_time() samples).
-int host_validate_sir(const lof_params& P, int dtype, const lof_unit& u, int i, char* why, int nwhy) {
+int host_validate_options(const lof_params& P, int dtype, const lof_unit& u, int i, char* why, int nwhy) {
   if (P.time_mode == LOF_TIME_INTEGRATED) {
     if (is_float(dtype))
       return snprintf(why, nwhy, "the integrated time mode takes integer units only"), LOF_ERR_INVALID;
@@ -821,7 +821,7 @@ int validate_units(lof_ctx* c, int dtype, const lof_unit* units, int n_units) {
   for (int i = 0; i < n_units; ++i) {
     rc = lofk::host_validate_unit(dtype, units[i], i, c->n_slots, why, sizeof why);
     if (rc) return fail(c, rc, "%s", why);
-    rc = lofk::host_validate_sir(c->params, dtype, units[i], i, why, sizeof why);
+    rc = lofk::host_validate_options(c->params, dtype, units[i], i, why, sizeof why);
     if (rc) return fail(c, rc, "%s", why);
   }
   return LOF_OK;

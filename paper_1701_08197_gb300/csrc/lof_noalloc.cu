@@ -41,7 +41,7 @@ size_t up256(size_t x) { return (x + 255) & ~size_t(255); }
 
 namespace lofk {
 void host_set_error(const char* msg);
-int host_validate_sir(const lof_params& P, int dtype, const lof_unit& u, int i, char* why, int nwhy);
+int host_validate_options(const lof_params& P, int dtype, const lof_unit& u, int i, char* why, int nwhy);
 }
 
 extern "C" int lof_flag_block_noalloc(const lof_params* params, int dtype, const lof_unit* units,
@@ -69,7 +69,7 @@ extern "C" int lof_flag_block_noalloc(const lof_params* params, int dtype, const
   for (int i = 0; i < n_units; ++i) {
     rc = lofk::host_validate_unit(dtype, units[i], i, 0, why, sizeof why);
     if (rc) return fail(rc);
-    rc = lofk::host_validate_sir(P, dtype, units[i], i, why, sizeof why);
+    rc = lofk::host_validate_options(P, dtype, units[i], i, why, sizeof why);
     if (rc) return fail(rc);
     if (units[i].history_slot != -1) {
       snprintf(why, sizeof why,

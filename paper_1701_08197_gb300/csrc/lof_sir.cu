@@ -284,9 +284,9 @@ __global__ void __launch_bounds__(32 * kSirWarps) lof_sir_freq_kernel(const DevU
 }  // namespace
 }  // namespace lofk
 
-// Limits of the SIR pass: rows up to 131072 samples, up to 32768 channels.
+// Limit of the SIR pass: rows up to 131072 samples (the channel limit of a
+// unit, 2048, is far below the frequency pass's 32768).
 extern "C" int lofk_sir_max_time() { return 32 * 32 * lofk::kSirMaxTiles; }
-extern "C" int lofk_sir_max_chan() { return 32 * 8 * lofk::kSirMaxTiles; }
 
 // Both directions of the SIR operator over n_units device units (es: bytes
 // per data sample).  max_chan sizes the frequency pass's shared strip.
