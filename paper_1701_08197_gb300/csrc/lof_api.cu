@@ -1141,13 +1141,24 @@ int graph_capture(lof_graph* g, const lofk::HostCfg& h, const lofk::Prep& pr, in
   cudaGraphGetNodes(g->graph, nullptr, &n);
   std::vector<cudaGraphNode_t> nodes(n);
   cudaGraphGetNodes(g->graph, nodes.data(), &n);
-  for (size_t i = 0; i < n; ++i) {
+  // the flag kernel is the kernel node that follows no other kernel (the SIR
+  // pass's kernels, when present, follow it)
+  auto is_kernel = [](cudaGraphNode_t nd) {
     cudaGraphNodeType t;
-    if (cudaGraphNodeGetType(nodes[i], &t) == cudaSuccess && t == cudaGraphNodeTypeKernel) {
-      g->knode = nodes[i];
-      cudaGraphKernelNodeGetParams(nodes[i], &g->kparams);
-      std::memcpy(&g->kp, g->kparams.kernelParams[0], sizeof(lofk::KParams));
-    }
+    return cudaGraphNodeGetType(nd, &t) == cudaSuccess && t == cudaGraphNodeTypeKernel;
+  };
+  for (size_t i = 0; i < n && !g->knode; ++i) {
+    if (!is_kernel(nodes[i])) continue;
+    size_t nd = 0;
+    cudaGraphNodeGetDependencies(nodes[i], nullptr, nullptr, &nd);
+    std::vector<cudaGraphNode_t> deps(nd);
+    if (nd) cudaGraphNodeGetDependencies(nodes[i], deps.data(), nullptr, &nd);
+    bool after_kernel = false;
+    for (size_t j = 0; j < nd; ++j) after_kernel = after_kernel || is_kernel(deps[j]);
+    if (after_kernel) continue;
+    g->knode = nodes[i];
+    cudaGraphKernelNodeGetParams(nodes[i], &g->kparams);
+    std::memcpy(&g->kp, g->kparams.kernelParams[0], sizeof(lofk::KParams));
   }
   if (!g->knode) return snprintf(why, nwhy, "no kernel node in the captured graph"), LOF_ERR_CUDA;
   e = cudaGraphInstantiate(&g->exec, g->graph, 0);
