@@ -26,6 +26,10 @@
  *    channels kept by the frequency pass into one series G[t] (entry-flagged
  *    samples left out), takes the statistics of its T values and runs
  *    SumThreshold on it; a flagged time step is flagged in every kept channel;
+ *  - the per-channel statistics scope (stats_scope = 1, time_mode 0) gives
+ *    each kept channel's time pass the median and sigma of that channel's own
+ *    samples instead of the pooled ones (the unit's median_t and sigma_t are
+ *    then reported as 0);
  *  - the SIR operator (Section 2.2, optional) is the scale-invariant rank
  *    operator the section names, with eta = sir_percent / 100: a sample is
  *    flagged when an interval around it is at least (1 - eta) flagged.  It
@@ -325,16 +329,28 @@ int lof_ref_flag_unit(const lof_ref_params *pr, int dtype, const void *in, int C
     if (nu > 0) st.sigma_t = lof_ref_sigma(pr, U, nu, is_int, &st.median_t);
     free(U);
 
-    /* Section 2.1 in the time direction, one channel at a time. */
+    /* Section 2.1 in the time direction, one channel at a time, with the
+     * pooled statistics or (per-channel scope) the channel's own. */
     uint8_t *entry = (uint8_t *)malloc((size_t)(T > 0 ? T : 1));
+    double *V = (double *)malloc((size_t)(T > 0 ? T : 1) * sizeof(double));
     for (int c = 0; c < C; ++c) {
       if (Fc[c] || !pr->enable_time || nu == 0) continue;
       uint8_t *row = F + (int64_t)c * T;
+      double m = st.median_t, sg = st.sigma_t;
+      if (pr->stats_scope == 1) {
+        int64_t nv = 0;
+        for (int t = 0; t < T; ++t)
+          if (!row[t]) V[nv++] = P[(int64_t)c * T + t];
+        if (nv == 0) continue;
+        sg = lof_ref_sigma(pr, V, nv, is_int, &m);
+      }
       memcpy(entry, row, (size_t)T);
-      lof_ref_sum_threshold(pr, P + (int64_t)c * T, T, st.median_t, st.sigma_t, row);
+      lof_ref_sum_threshold(pr, P + (int64_t)c * T, T, m, sg, row);
       for (int t = 0; t < T; ++t) st.n_flag_time += (row[t] && !entry[t]);
     }
+    free(V);
     free(entry);
+    if (pr->stats_scope == 1) st.median_t = st.sigma_t = 0.0;
   }
 
   /* Section 4.1: the history flagger, per channel. */

@@ -46,6 +46,7 @@ typedef struct {
   int enable_freq, enable_time, enable_history;
   int sir_percent;        /* Section 2.2 SIR operator, eta in percent (0 = off) */
   int time_mode;          /* 0: time pass per channel; 1: on the frequency-integrated series */
+  int stats_scope;        /* time-pass statistics: 0 pooled over the unit; 1 per channel */
 } lof_ref_params;
 
 typedef struct {
