@@ -84,6 +84,8 @@ enum { LOF_SIGMA_MAD = 0, LOF_SIGMA_STD = 1 };
 
 enum { LOF_TIME_PER_CHANNEL = 0, LOF_TIME_INTEGRATED = 1 };
 
+enum { LOF_SCOPE_POOLED = 0, LOF_SCOPE_CHANNEL = 1 };
+
 typedef struct {
   double p;                /* Section 2.1, default 1.5 */
   double sensitivity;      /* Section 2.1, default 1.0 */
@@ -110,6 +112,13 @@ typedef struct {
                               kept channels, its own median and sigma, one SumThreshold,
                               a flagged time step flagged in every kept channel.
                               Integer units only, n_time <= 16384 */
+  int32_t stats_scope;     /* statistics of the per-channel time pass (Section 4.2 reading):
+                              LOF_SCOPE_POOLED (default) -- one median and sigma pooled over
+                              the unit's kept channels; LOF_SCOPE_CHANNEL -- each kept
+                              channel's own median and sigma over its own samples (the
+                              unit's median_t and sigma_t are then reported as 0).
+                              LOF_SCOPE_CHANNEL takes integer units, time_mode
+                              LOF_TIME_PER_CHANNEL and n_time <= 16384 */
 } lof_params;
 
 /* Per-unit results, written by lof_flag_block when lof_unit.stats != NULL

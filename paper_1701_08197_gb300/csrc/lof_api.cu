@@ -49,7 +49,8 @@ extern "C" int lofk_launch_f32x(const lofk::KParams* kp, int n_units, int n_sm, 
                                 void* stream, int cplx);
 extern "C" int lofk_sir_max_time();
 extern "C" int lofk_integ_max_time();
-extern "C" int lofk_launch_integ(int dtype, const lofk::KParams* kp, int n_units, int n_sm, void* stream);
+extern "C" int lofk_launch_integ(int dtype, const lofk::KParams* kp, int n_units, int n_sm, void* stream,
+                                 int mode);
 extern "C" int lofk_launch_sir(const lofk::DevUnit* units, int n_units, int64_t n_chan, int max_chan,
                                int percent, int es, void* stream);
 
@@ -190,6 +191,7 @@ extern "C" void lof_default_params(lof_params* p) {
   p->enable_history = 1;
   p->sir_percent = 0;
   p->time_mode = LOF_TIME_PER_CHANNEL;
+  p->stats_scope = LOF_SCOPE_POOLED;
 }
 
 extern "C" const char* lof_last_error(const lof_ctx* c) {
@@ -221,6 +223,14 @@ static int validate_params(const lof_params* p, std::string* why) {
   }
   if (p->time_mode != LOF_TIME_PER_CHANNEL && p->time_mode != LOF_TIME_INTEGRATED) {
     *why = "unknown time_mode";
+    return 0;
+  }
+  if (p->stats_scope != LOF_SCOPE_POOLED && p->stats_scope != LOF_SCOPE_CHANNEL) {
+    *why = "unknown stats_scope";
+    return 0;
+  }
+  if (p->stats_scope == LOF_SCOPE_CHANNEL && p->time_mode != LOF_TIME_PER_CHANNEL) {
+    *why = "stats_scope LOF_SCOPE_CHANNEL needs time_mode LOF_TIME_PER_CHANNEL";
     return 0;
   }
   return 1;
@@ -648,8 +658,9 @@ int host_launch_kernel(const lof_params& P, const HostCfg& h, int dtype, const P
   kp.gen_words = pr.gen_words;
   const int krc = is_float(dtype)
                       ? lofk_launch_f32x(&kp, n_units, h.n_sm, pr.plan.smem, stream, dtype == LOF_CF32)
-                  : P.time_mode == LOF_TIME_INTEGRATED
-                      ? lofk_launch_integ(dtype, &kp, n_units, h.n_sm, stream)
+                  : P.time_mode == LOF_TIME_INTEGRATED || P.stats_scope == LOF_SCOPE_CHANNEL
+                      ? lofk_launch_integ(dtype, &kp, n_units, h.n_sm, stream,
+                                          P.stats_scope == LOF_SCOPE_CHANNEL ? 1 : 0)
                       : lofk_launch_block(dtype, &kp, pr.grid, pr.plan.threads, pr.plan.smem, stream,
                                           cooperative);
   if (krc != 0) {
@@ -685,16 +696,18 @@ int host_launch(const lof_params& P, const HostCfg& h, int dtype, const Prep& pr
   return host_launch_kernel(P, h, dtype, pr, sc, n_units, seq, stream, 1, why, nwhy);
 }
 
-// Options with limits of their own: the integrated time mode (integer units,
-// rows up to lofk_integ_max_time() samples) and the SIR pass (the mask output,
-// rows up to lofk_sir_max_time() samples).
+// Options with limits of their own: the integrated time mode and the
+// per-channel statistics scope (integer units, rows up to
+// lofk_integ_max_time() samples) and the SIR pass (the mask output, rows up to
+// lofk_sir_max_time() samples).
 int host_validate_options(const lof_params& P, int dtype, const lof_unit& u, int i, char* why, int nwhy) {
-  if (P.time_mode == LOF_TIME_INTEGRATED) {
-    if (is_float(dtype))
-      return snprintf(why, nwhy, "the integrated time mode takes integer units only"), LOF_ERR_INVALID;
+  if (P.time_mode == LOF_TIME_INTEGRATED || P.stats_scope == LOF_SCOPE_CHANNEL) {
+    const char* what = P.time_mode == LOF_TIME_INTEGRATED ? "the integrated time mode"
+                                                          : "the per-channel statistics scope";
+    if (is_float(dtype)) return snprintf(why, nwhy, "%s takes integer units only", what), LOF_ERR_INVALID;
     if (u.n_time > lofk_integ_max_time())
-      return snprintf(why, nwhy, "unit %d: n_time %d above the integrated-mode limit %d", i, u.n_time,
-                      lofk_integ_max_time()),
+      return snprintf(why, nwhy, "unit %d: n_time %d above the limit %d of %s", i, u.n_time,
+                      lofk_integ_max_time(), what),
              LOF_ERR_INVALID;
   }
   if (P.sir_percent <= 0) return LOF_OK;

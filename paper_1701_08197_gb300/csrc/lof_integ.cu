@@ -47,6 +47,9 @@ struct IntegShared {
   long long rank[2];
   int nrank, nkept, nfc;
   unsigned long long s1lo[kNwI], s1hi[kNwI], s2lo[kNwI], s2hi[kNwI];
+  unsigned long long rs[kNwI];
+  int rn[kNwI];
+  int fh;
 };
 
 template <int DT>
@@ -293,42 +296,12 @@ __device__ void st_1d(const KParams& kp, V v, int L, double med, double sig, uin
   }
 }
 
-template <int DT>
-__device__ void integ_unit(const KParams& kp, const DevUnit& u, uint8_t* smem, IntegShared& f) {
-  constexpr int ES = DT == LOF_CI16 ? 4 : 2;
-  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  const int C = u.C, T = u.T;
-  unsigned long long* S = reinterpret_cast<unsigned long long*>(smem + kOffS);
-  unsigned long long* srt = reinterpret_cast<unsigned long long*>(smem + kOffSrt);
-  unsigned long long* G = reinterpret_cast<unsigned long long*>(smem + kOffG);
-  uint32_t* hist = reinterpret_cast<uint32_t*>(smem + kOffHist);
-  uint8_t* Fc = smem + kOffFc;
-  uint8_t* Fcn = smem + kOffFcn;
-  uint8_t* Ft = smem + kOffFt;
-  uint8_t* Fn = smem + kOffFn;
-  const uint8_t* gin = static_cast<const uint8_t*>(u.in);
-  const bool vin = (u.flags & kUnitInVec) != 0;
-  for (int i = tid; i < T; i += kNtI) {
-    G[i] = 0ull;
-    Ft[i] = 0;
-  }
-  for (int i = tid; i < C; i += kNtI) Fc[i] = 0;
-  if (tid == 0) f.cnt_time = f.cnt_total = f.cnt_hist = 0ull;
-  __syncthreads();
-  // a1, a2: row sums and the column series over every channel
-  for (int c = warp; c < C; c += kNwI) {
-    const uint8_t* row = gin + static_cast<int64_t>(c) * u.in_stride * ES;
-    unsigned long long s = 0;
-    row_powers<DT>(row, T, vin, [&](int t, uint32_t p) {
-      s += p;
-      atomicAdd(&G[t], static_cast<unsigned long long>(p));
-    });
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(kFullI, s, o);
-    if (lane == 0) S[c] = s;
-  }
-  __syncthreads();
-  // a3: statistics of the spectrum (sort of the C sums)
+// a3, a4 for a unit whose row sums are in S: exact median and sigma of the
+// spectrum (bitonic sort of the C sums, deviations as |2x - m2|) and the
+// frequency SumThreshold -> Fc (whole CTA).
+__device__ void freq_stage(const KParams& kp, unsigned long long* S, unsigned long long* srt, int C,
+                           uint8_t* Fc, uint8_t* Fcn, IntegShared& f) {
+  const int tid = threadIdx.x;
   {
     int n2 = 1;
     while (n2 < C) n2 <<= 1;
@@ -365,6 +338,44 @@ __device__ void integ_unit(const KParams& kp, const DevUnit& u, uint8_t* smem, I
   // a4: frequency SumThreshold
   if (kp.enable_freq) st_1d(kp, [&](int i) { return S[i]; }, C, f.median_f, f.sigma_f, Fc, Fcn);
   __syncthreads();
+}
+
+template <int DT>
+__device__ void integ_unit(const KParams& kp, const DevUnit& u, uint8_t* smem, IntegShared& f) {
+  constexpr int ES = DT == LOF_CI16 ? 4 : 2;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int C = u.C, T = u.T;
+  unsigned long long* S = reinterpret_cast<unsigned long long*>(smem + kOffS);
+  unsigned long long* srt = reinterpret_cast<unsigned long long*>(smem + kOffSrt);
+  unsigned long long* G = reinterpret_cast<unsigned long long*>(smem + kOffG);
+  uint32_t* hist = reinterpret_cast<uint32_t*>(smem + kOffHist);
+  uint8_t* Fc = smem + kOffFc;
+  uint8_t* Fcn = smem + kOffFcn;
+  uint8_t* Ft = smem + kOffFt;
+  uint8_t* Fn = smem + kOffFn;
+  const uint8_t* gin = static_cast<const uint8_t*>(u.in);
+  const bool vin = (u.flags & kUnitInVec) != 0;
+  for (int i = tid; i < T; i += kNtI) {
+    G[i] = 0ull;
+    Ft[i] = 0;
+  }
+  for (int i = tid; i < C; i += kNtI) Fc[i] = 0;
+  if (tid == 0) f.cnt_time = f.cnt_total = f.cnt_hist = 0ull;
+  __syncthreads();
+  // a1, a2: row sums and the column series over every channel
+  for (int c = warp; c < C; c += kNwI) {
+    const uint8_t* row = gin + static_cast<int64_t>(c) * u.in_stride * ES;
+    unsigned long long s = 0;
+    row_powers<DT>(row, T, vin, [&](int t, uint32_t p) {
+      s += p;
+      atomicAdd(&G[t], static_cast<unsigned long long>(p));
+    });
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(kFullI, s, o);
+    if (lane == 0) S[c] = s;
+  }
+  __syncthreads();
+  freq_stage(kp, S, srt, C, Fc, Fcn, f);
   // a5: the series over the kept channels and its statistics
   for (int c = warp; c < C; c += kNwI) {
     if (!Fc[c]) continue;
@@ -506,11 +517,152 @@ __device__ void integ_unit(const KParams& kp, const DevUnit& u, uint8_t* smem, I
   __syncthreads();
 }
 
+
+// Per-channel statistics scope (stats_scope = 1, time pass per channel): the
+// frequency stage as above, then, one kept channel at a time with the whole
+// CTA, the exact median and sigma of the channel's own powers, SumThreshold
+// along its row, the history test and the output.
 template <int DT>
+__device__ void chan_unit(const KParams& kp, const DevUnit& u, uint8_t* smem, IntegShared& f) {
+  constexpr int ES = DT == LOF_CI16 ? 4 : 2;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int C = u.C, T = u.T;
+  unsigned long long* S = reinterpret_cast<unsigned long long*>(smem + kOffS);
+  unsigned long long* srt = reinterpret_cast<unsigned long long*>(smem + kOffSrt);
+  unsigned long long* R = reinterpret_cast<unsigned long long*>(smem + kOffG);  // one row's powers
+  uint32_t* hist = reinterpret_cast<uint32_t*>(smem + kOffHist);
+  uint8_t* Fc = smem + kOffFc;
+  uint8_t* Fcn = smem + kOffFcn;
+  uint8_t* Ft = smem + kOffFt;
+  uint8_t* Fn = smem + kOffFn;
+  const uint8_t* gin = static_cast<const uint8_t*>(u.in);
+  const bool vin = (u.flags & kUnitInVec) != 0;
+  const bool inplace = (u.flags & kUnitInPlace) != 0;
+  for (int i = tid; i < C; i += kNtI) Fc[i] = 0;
+  if (tid == 0) f.cnt_time = f.cnt_total = f.cnt_hist = 0ull;
+  __syncthreads();
+  for (int c = warp; c < C; c += kNwI) {
+    const uint8_t* row = gin + static_cast<int64_t>(c) * u.in_stride * ES;
+    unsigned long long sum = 0;
+    row_powers<DT>(row, T, vin, [&](int, uint32_t p) { sum += p; });
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) sum += __shfl_xor_sync(kFullI, sum, o);
+    if (lane == 0) S[c] = sum;
+  }
+  __syncthreads();
+  freq_stage(kp, S, srt, C, Fc, Fcn, f);
+  int nfc = 0;
+  for (int c = 0; c < C; ++c) {
+    const uint8_t* row = gin + static_cast<int64_t>(c) * u.in_stride * ES;
+    const long long h = u.hist_slot >= 0 ? u.hist_slot + c : -1;
+    uint8_t* mr = u.mask ? u.mask + static_cast<int64_t>(c) * u.mask_stride : nullptr;
+    uint8_t* orow = u.out ? static_cast<uint8_t*>(u.out) + static_cast<int64_t>(c) * u.out_stride * ES : nullptr;
+    const bool kept = !Fc[c];
+    nfc += !kept;
+    if (kept) {
+      for (int t = tid; t < T; t += kNtI) {
+        R[t] = ipow<DT>(row, t);
+        Ft[t] = 0;
+      }
+      __syncthreads();
+      double med = 0.0, sig = 0.0;
+      stats_u64(kp, T, [&](long long i) { return R[i]; }, hist, f, &med, &sig);
+      if (kp.enable_time) st_1d(kp, [&](int i) { return R[i]; }, T, med, sig, Ft, Fn);
+      __syncthreads();
+      unsigned long long sum = 0;
+      int n = 0;
+      for (int t = tid; t < T; t += kNtI)
+        if (!Ft[t]) {
+          sum += R[t];
+          ++n;
+        }
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) {
+        sum += __shfl_xor_sync(kFullI, sum, o);
+        n += __shfl_xor_sync(kFullI, n, o);
+      }
+      if (lane == 0) {
+        f.rs[warp] = sum;
+        f.rn[warp] = n;
+      }
+      __syncthreads();
+      if (tid == 0) {
+        unsigned long long st = 0;
+        int nt = 0;
+        for (int w = 0; w < kNwI; ++w) {
+          st += f.rs[w];
+          nt += f.rn[w];
+        }
+        bool fh = false;
+        if (nt > 0) {
+          const double cur = __ddiv_rn(static_cast<double>(st), static_cast<double>(nt));
+          double staged = cur;
+          if (kp.enable_history && h >= 0) {
+            const int cnt = kp.hist.count[h];
+            if (cnt >= kp.history_min && cnt > 0) {
+              const double thr = kp.hist.thr[h];
+              if (!(cur < thr)) {
+                fh = true;
+                staged = thr;
+              }
+            }
+          }
+          if (h >= 0) {
+            kp.hist.pend[h] = staged;
+            kp.hist.pend_flag[h] = 1;
+            kp.hist.pend_seq[h] = kp.block_seq;
+          }
+        } else if (h >= 0) {
+          kp.hist.pend_flag[h] = 0;
+        }
+        f.cnt_time += static_cast<unsigned long long>(T - nt);
+        if (fh) f.cnt_hist += 1ull;
+        f.cnt_total += fh ? static_cast<unsigned long long>(T) : static_cast<unsigned long long>(T - nt);
+        f.fh = fh ? 1 : 0;
+      }
+      __syncthreads();
+    } else if (tid == 0) {
+      if (h >= 0) kp.hist.pend_flag[h] = 0;
+      f.cnt_total += static_cast<unsigned long long>(T);
+    }
+    const bool full = !kept || f.fh;
+    for (int t = tid; t < T; t += kNtI) {
+      const bool fl = full || Ft[t];
+      if (mr) mr[t] = fl ? 1 : 0;
+      if (orow) {
+        if (ES == 4) {
+          if (fl) reinterpret_cast<uint32_t*>(orow)[t] = 0u;
+          else if (!inplace) reinterpret_cast<uint32_t*>(orow)[t] = reinterpret_cast<const uint32_t*>(row)[t];
+        } else {
+          if (fl) reinterpret_cast<uint16_t*>(orow)[t] = 0;
+          else if (!inplace) reinterpret_cast<uint16_t*>(orow)[t] = reinterpret_cast<const uint16_t*>(row)[t];
+        }
+      }
+    }
+    __syncthreads();
+  }
+  if (tid == 0 && u.stats) {
+    u.stats->median_f = f.median_f;
+    u.stats->sigma_f = f.sigma_f;
+    u.stats->median_t = 0.0;
+    u.stats->sigma_t = 0.0;
+    u.stats->n_chan_freq = nfc;
+    u.stats->n_flag_time = static_cast<long long>(f.cnt_time);
+    u.stats->n_chan_hist = static_cast<long long>(f.cnt_hist);
+    u.stats->n_flag_total = static_cast<long long>(f.cnt_total);
+  }
+  __syncthreads();
+}
+
+// MODE 0: integrated time mode; MODE 1: per-channel statistics scope.
+template <int DT, int MODE>
 __global__ void __launch_bounds__(kNtI, 1) lof_integ_kernel(const KParams kp) {
   extern __shared__ __align__(16) uint8_t smem[];
   __shared__ IntegShared f;
-  for (int ui = blockIdx.x; ui < kp.n_units; ui += gridDim.x) integ_unit<DT>(kp, kp.units[ui], smem, f);
+  for (int ui = blockIdx.x; ui < kp.n_units; ui += gridDim.x) {
+    if constexpr (MODE == 0) integ_unit<DT>(kp, kp.units[ui], smem, f);
+    else chan_unit<DT>(kp, kp.units[ui], smem, f);
+  }
 }
 
 }  // namespace
@@ -518,12 +670,18 @@ __global__ void __launch_bounds__(kNtI, 1) lof_integ_kernel(const KParams kp) {
 
 extern "C" int lofk_integ_max_time() { return lofk::kIntegMaxT; }
 
-// The integrated time mode over n_units integer units (one CTA per unit).
-extern "C" int lofk_launch_integ(int dtype, const lofk::KParams* kp, int n_units, int n_sm, void* stream) {
+// The integrated time mode (mode 0) or the per-channel statistics scope
+// (mode 1) over n_units integer units (one CTA per unit).
+extern "C" int lofk_launch_integ(int dtype, const lofk::KParams* kp, int n_units, int n_sm, void* stream,
+                                 int mode) {
   using namespace lofk;
   if (n_units <= 0) return 0;
-  const void* k = dtype == LOF_CI16 ? reinterpret_cast<const void*>(&lof_integ_kernel<LOF_CI16>)
-                                    : reinterpret_cast<const void*>(&lof_integ_kernel<LOF_CI8>);
+  const void* k =
+      dtype == LOF_CI16
+          ? (mode ? reinterpret_cast<const void*>(&lof_integ_kernel<LOF_CI16, 1>)
+                  : reinterpret_cast<const void*>(&lof_integ_kernel<LOF_CI16, 0>))
+          : (mode ? reinterpret_cast<const void*>(&lof_integ_kernel<LOF_CI8, 1>)
+                  : reinterpret_cast<const void*>(&lof_integ_kernel<LOF_CI8, 0>));
   if (cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, kIntegSmem) != cudaSuccess)
     return -2;
   const int grid = n_units < n_sm ? n_units : n_sm;

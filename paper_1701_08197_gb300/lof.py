@@ -22,6 +22,7 @@ LOF_ERR_UNSUPPORTED = -6
 LOF_CI8, LOF_CI16, LOF_F32, LOF_CF32 = 1, 2, 3, 4
 LOF_SIGMA_MAD, LOF_SIGMA_STD = 0, 1
 LOF_TIME_PER_CHANNEL, LOF_TIME_INTEGRATED = 0, 1
+LOF_SCOPE_POOLED, LOF_SCOPE_CHANNEL = 0, 1
 
 EXPORTED = [
     "lof_default_params", "lof_create", "lof_flag_block", "lof_flag_block_host",
@@ -47,6 +48,7 @@ class lof_params(ctypes.Structure):
         ("enable_history", ctypes.c_int32),
         ("sir_percent", ctypes.c_int32),
         ("time_mode", ctypes.c_int32),
+        ("stats_scope", ctypes.c_int32),
     ]
 
 
