@@ -21,7 +21,7 @@ _lock = threading.Lock()
 _lib = None
 
 CI8, CI16, F32, CF32 = 1, 2, 3, 4
-SIGMA_MAD, SIGMA_STD = 0, 1
+SIGMA_MAD, SIGMA_STD, SIGMA_WINSOR = 0, 1, 2
 
 
 class Params(ctypes.Structure):

@@ -15,6 +15,12 @@
  *  - all windows of one size are judged against the flags of the previous
  *    sizes only (snapshot), windows lie fully inside the row;
  *  - "stddev" is the robust 1.4826*MAD (population stddev when the MAD is 0);
+ *  - the winsorized estimator (sigma_estimator = 2; Section 4.2 lists
+ *    winsorized means among the statistics) clamps the lowest and the highest
+ *    k = floor(n / 10) of the n values to the nearest kept order statistic
+ *    (10% winsorizing on each side), takes the population stddev of the
+ *    clamped values and scales it by 1/sqrt(c) so that it estimates sigma of
+ *    normal data (population stddev when the result is 0);
  *  - time-pass statistics pool every sample of the channels the frequency
  *    pass left unflagged (Section 4: frequency flagging first "removes strong
  *    narrow-band RFI that would otherwise decrease the quality of the
@@ -44,6 +50,11 @@
 
 /* 1/Phi^-1(3/4): scales the MAD of normal data to its standard deviation. */
 static const double MAD_TO_SIGMA = 1.482602218505602;
+
+/* 1/sqrt(c), c = the variance of a standard normal winsorized at its 10% and
+ * 90% quantiles +-z (z = Phi^-1(0.9) = 1.2815515655446004):
+ * c = 0.8 - 2 z phi(z) + 0.2 z^2 = 0.6786545589528744. */
+static const double WINSOR_TO_SIGMA = 1.2138796046717422;
 
 /* Section 2.1: factor_I = startThreshold * p^(log2 I) / I, I = 2^k.
  * p^k is formed by k successive multiplications. */
@@ -116,6 +127,19 @@ double lof_ref_sigma(const lof_ref_params *pr, const double *x, int64_t n, int i
   double m = lof_ref_median(x, n);
   *median = m;
   if (pr->sigma_estimator == LOF_REF_SIGMA_STD) return population_std(x, n, is_int);
+  if (pr->sigma_estimator == LOF_REF_SIGMA_WINSOR) {
+    /* winsorize: order statistics k and n-1-k bound the clamped values */
+    double *s = (double *)malloc((size_t)n * sizeof(double));
+    memcpy(s, x, (size_t)n * sizeof(double));
+    qsort(s, (size_t)n, sizeof(double), cmp_double);
+    const int64_t k = n / 10;
+    const double lo = s[k], hi = s[n - 1 - k];
+    for (int64_t i = 0; i < n; ++i) s[i] = x[i] < lo ? lo : (x[i] > hi ? hi : x[i]);
+    double sw = population_std(s, n, is_int);
+    free(s);
+    if (sw > 0.0) return WINSOR_TO_SIGMA * sw;
+    return population_std(x, n, is_int);
+  }
   double *d = (double *)malloc((size_t)n * sizeof(double));
   for (int64_t i = 0; i < n; ++i) d[i] = fabs(x[i] - m);
   double mad = lof_ref_median(d, n);

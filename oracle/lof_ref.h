@@ -32,7 +32,7 @@ extern "C" {
 
 enum { LOF_REF_CI8 = 1, LOF_REF_CI16 = 2, LOF_REF_F32 = 3,
        LOF_REF_CF32 = 4 /* complex float32 visibilities (post-correlation) */ };
-enum { LOF_REF_SIGMA_MAD = 0, LOF_REF_SIGMA_STD = 1 };
+enum { LOF_REF_SIGMA_MAD = 0, LOF_REF_SIGMA_STD = 1, LOF_REF_SIGMA_WINSOR = 2 };
 
 typedef struct {
   double p;               /* Section 2.1: 1.5 */
@@ -42,7 +42,7 @@ typedef struct {
   int history_len;        /* ring capacity H (60) */
   int history_min;        /* entries needed before the history test runs (4) */
   double history_k;       /* history threshold multiplier (6) */
-  int sigma_estimator;    /* LOF_REF_SIGMA_MAD or LOF_REF_SIGMA_STD */
+  int sigma_estimator;    /* LOF_REF_SIGMA_MAD, LOF_REF_SIGMA_STD or LOF_REF_SIGMA_WINSOR */
   int enable_freq, enable_time, enable_history;
   int sir_percent;        /* Section 2.2 SIR operator, eta in percent (0 = off) */
   int time_mode;          /* 0: time pass per channel; 1: on the frequency-integrated series */
