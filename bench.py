@@ -78,6 +78,9 @@ def measured_traffic(n_units, tuning):
         return None
 
 
+SIGMA = {"mad": 0, "std": 1, "winsor": 2}
+
+
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -87,13 +90,19 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-plain", action="store_true")
-    ap.add_argument("--no-autotune", action="store_true")
+    ap.add_argument("--autotune", action="store_true",
+                    help="time with the autotuner's launch shape instead of the library default "
+                         "(the shape the recorded DRAM counters were taken with)")
+    ap.add_argument("--no-autotune", action="store_true", help="the default; kept for old command lines")
     ap.add_argument("--integrated", action="store_true",
                     help="integrated time mode (Section 3): one SumThreshold on the frequency-"
                          "integrated series of the kept channels instead of one per channel")
     ap.add_argument("--channel-scope", action="store_true",
                     help="per-channel statistics scope: each kept channel's time pass with the "
                          "median and sigma of its own samples instead of the pooled ones")
+    ap.add_argument("--sigma", default="mad", choices=list(SIGMA),
+                    help="sigma estimator of the statistics (Section 4.2): 1.4826 * MAD, "
+                         "population stddev or winsorized stddev")
     ap.add_argument("--sir", type=int, default=0,
                     help="SIR operator percentage (Section 2.2) on the final mask; 0 = off")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
@@ -201,7 +210,8 @@ def build_units(x, out, mask, stats, slot_base=0):
     return units
 
 
-def workload_config(stations: int, sir: int = 0, integrated: bool = False, scope: bool = False) -> dict:
+def workload_config(stations: int, sir: int = 0, integrated: bool = False, scope: bool = False,
+                    sigma: str = "mad") -> dict:
     c = {"workload": f"full LOFAR pre-beamformer block: {stations} st x 2 pol x 8 sb "
                      f"= {stations * 16} units x 256 ch x 3072 t, complex int16, history 60",
          "launch": "batched persistent (1 launch per block) + history commit",
@@ -213,6 +223,8 @@ def workload_config(stations: int, sir: int = 0, integrated: bool = False, scope
         c["time_mode"] = "integrated (Section 3)"
     if scope:
         c["stats_scope"] = "per channel"
+    if sigma != "mad":
+        c["sigma_estimator"] = sigma
     return c
 
 
@@ -252,7 +264,8 @@ def run_gpu(args):
     stats = lof.stats_tensor(n_units, dev)
     fl = lof.Flagger(local, n_history_slots=n_units * C, sir_percent=args.sir,
                      time_mode=lof.LOF_TIME_INTEGRATED if args.integrated else lof.LOF_TIME_PER_CHANNEL,
-                     stats_scope=lof.LOF_SCOPE_CHANNEL if args.channel_scope else lof.LOF_SCOPE_POOLED)
+                     stats_scope=lof.LOF_SCOPE_CHANNEL if args.channel_scope else lof.LOF_SCOPE_POOLED,
+                     sigma_estimator=SIGMA[args.sigma])
     # rings pre-filled with 60 means per channel (steady state of the history flagger)
     pw = (x.to(torch.float32) ** 2).sum(-1).mean(-1).reshape(-1).double().cpu().numpy()
     rng = np.random.default_rng(7)
@@ -266,9 +279,10 @@ def run_gpu(args):
         fl.flag_block(lof.LOF_CI16, units, seq, stream)
         fl.history_update(units, stream)
 
-    # launch shape from the autotuner (untimed; results do not depend on it)
+    # launch shape: the library default, or the autotuner's pick (untimed;
+    # results do not depend on it)
     tuning = None
-    if not args.no_autotune:
+    if args.autotune and not args.no_autotune:
         tuning, _ = fl.autotune(lof.LOF_CI16, units, reps=2, stream=stream)
         torch.cuda.synchronize()
     with torch.cuda.stream(stream):
@@ -362,7 +376,7 @@ def run_gpu(args):
     return res
 
 
-def oracle_sample(seconds: float, seed=2, sir=0, integrated=False, scope=False):
+def oracle_sample(seconds: float, seed=2, sir=0, integrated=False, scope=False, sigma="mad"):
     """The oracle (as it stands) on host cores: units of the same workload, one
     per thread (the paper's thread-per-subband CPU layout), bounded in time."""
     from concurrent.futures import ThreadPoolExecutor
@@ -371,7 +385,8 @@ def oracle_sample(seconds: float, seed=2, sir=0, integrated=False, scope=False):
 
     import oracle
     from paper_1701_08197_gb300 import synth
-    P = oracle.default_params(sir_percent=sir, time_mode=1 if integrated else 0, stats_scope=1 if scope else 0)
+    P = oracle.default_params(sir_percent=sir, time_mode=1 if integrated else 0, stats_scope=1 if scope else 0,
+                              sigma_estimator=SIGMA[sigma])
     cores = os.cpu_count() or 1
     spec = synth.VoltageSpec(n_station=1, n_pol=N_POL, n_subband=N_SUBBAND, C=C, T=T,
                              sigma=32.0, tone_frac=0.02, impulse_frac=0.01)
@@ -412,7 +427,7 @@ def main():
         cb = None
         for i in range(args.warmup + args.steps):
             r = oracle_sample(max(2.0, args.cpu_seconds / max(1, args.steps)), sir=args.sir,
-                              integrated=args.integrated, scope=args.channel_scope)
+                              integrated=args.integrated, scope=args.channel_scope, sigma=args.sigma)
             if i >= args.warmup:
                 steps.append(r)
             cb = r
@@ -424,7 +439,7 @@ def main():
                 "higher_is_better": True,
                 "scaling": "weak", "vs_baseline": None, "dtype": "int64+f64",
                 "data": "synthetic (seeded)",
-                "config": workload_config(args.stations, args.sir, args.integrated, args.channel_scope),
+                "config": workload_config(args.stations, args.sir, args.integrated, args.channel_scope, args.sigma),
                 "cpu_baseline": {"value": v, "unit": "Msamples/s", "cores": cb["cores"],
                                  "kind": "oracle", "sample": cb["sample"]},
                 "e2e": {"value": v, "unit": "Msamples/s", "h2d_bytes_per_step": 0,
@@ -450,14 +465,16 @@ def main():
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": res["ms_per_step"],
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int32/u64",
         "data": "synthetic (seeded noise + tones + impulses)",
-        "config": dict(workload_config(args.stations, args.sir, args.integrated, args.channel_scope), tuning=res["tuning"]),
+        "config": dict(workload_config(args.stations, args.sir, args.integrated, args.channel_scope, args.sigma), tuning=res["tuning"]),
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                      "frac": achieved / peak,
                      # the recorded counters are those of the block kernel alone
-                     "traffic": None if (args.integrated or args.channel_scope or args.sir)
+                     "traffic": None if (args.integrated or args.channel_scope or args.sir
+                                         or args.sigma == "winsor")
                      else measured_traffic(args.stations * 16, res["tuning"]),
                      "kernel": ("lof_integ_kernel<CI16, integrated>" if args.integrated
                                 else "lof_integ_kernel<CI16, channel scope>" if args.channel_scope
+                                else "lof_integ_kernel<CI16, pooled exact>" if args.sigma == "winsor"
                                 else "lof_block_kernel<CI16>")
                                + (" + SIR" if args.sir else ""),
                      "bytes_per_launch": alg_bytes,
@@ -476,7 +493,7 @@ def main():
         line["e2e"] = res["e2e"]
     if not args.no_cpu:
         line["cpu_baseline"] = oracle_sample(args.cpu_seconds, sir=args.sir, integrated=args.integrated,
-                                             scope=args.channel_scope)
+                                             scope=args.channel_scope, sigma=args.sigma)
     print(json.dumps(line))
 
 

@@ -80,7 +80,7 @@ enum {
  * is 0 + 0i). */
 enum { LOF_CI8 = 1, LOF_CI16 = 2, LOF_F32 = 3, LOF_CF32 = 4 };
 
-enum { LOF_SIGMA_MAD = 0, LOF_SIGMA_STD = 1 };
+enum { LOF_SIGMA_MAD = 0, LOF_SIGMA_STD = 1, LOF_SIGMA_WINSOR = 2 };
 
 enum { LOF_TIME_PER_CHANNEL = 0, LOF_TIME_INTEGRATED = 1 };
 
@@ -94,7 +94,14 @@ typedef struct {
   int32_t history_len;     /* history ring capacity per channel, 1..1024; default 60 */
   int32_t history_min;     /* stored means needed before the history test; default 8 */
   double history_k;        /* history threshold = mean + k * stddev; default 6 */
-  int32_t sigma_estimator; /* LOF_SIGMA_MAD (default) or LOF_SIGMA_STD */
+  int32_t sigma_estimator; /* Section 4.2 statistics: LOF_SIGMA_MAD (default, 1.4826 * MAD),
+                              LOF_SIGMA_STD (population stddev) or LOF_SIGMA_WINSOR (the
+                              lowest and highest n / 10 values clamped to the nearest kept
+                              order statistic, population stddev of the clamped values times
+                              1.2138796046717422, which makes it estimate sigma of normal
+                              data).  Each falls back to the plain stddev when it is 0.
+                              LOF_SIGMA_WINSOR takes integer units and n_time <= 16384; it
+                              runs on the exact-statistics unit kernel (one CTA per unit) */
   int32_t enable_freq;     /* frequency pass on (1) / off (0) */
   int32_t enable_time;     /* time pass on / off */
   int32_t enable_history;  /* history flagger on / off */

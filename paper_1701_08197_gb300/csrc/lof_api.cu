@@ -213,7 +213,8 @@ static int validate_params(const lof_params* p, std::string* why) {
     *why = "history_len in [1, 1024], history_min >= 0, history_k >= 0 required";
     return 0;
   }
-  if (p->sigma_estimator != LOF_SIGMA_MAD && p->sigma_estimator != LOF_SIGMA_STD) {
+  if (p->sigma_estimator != LOF_SIGMA_MAD && p->sigma_estimator != LOF_SIGMA_STD &&
+      p->sigma_estimator != LOF_SIGMA_WINSOR) {
     *why = "unknown sigma_estimator";
     return 0;
   }
@@ -609,6 +610,17 @@ int host_prepare(const HostCfg& h, int dtype, const lof_unit* units, int n_units
 
 // Device-side steps of one block (no host memory touched): per-unit state
 // and queue reset, the kernel launch.  Stream-capturable.
+// The mode of the exact-statistics unit kernel an option set runs on (one CTA
+// per unit): 0 the integrated time mode, 1 the per-channel statistics scope, 2
+// the pooled per-channel pass with the winsorized estimator; -1 the block
+// kernel (or the float kernel) with its histogram statistics.
+int exact_stats_mode(const lof_params& P) {
+  if (P.time_mode == LOF_TIME_INTEGRATED) return 0;
+  if (P.stats_scope == LOF_SCOPE_CHANNEL) return 1;
+  if (P.sigma_estimator == LOF_SIGMA_WINSOR) return 2;
+  return -1;
+}
+
 int host_launch_kernel(const lof_params& P, const HostCfg& h, int dtype, const Prep& pr,
                        const Scratch& sc, int n_units, uint64_t seq, void* stream, int cooperative,
                        char* why, int nwhy) {
@@ -647,7 +659,9 @@ int host_launch_kernel(const lof_params& P, const HostCfg& h, int dtype, const P
   while ((2 << mlw) <= P.max_window) ++mlw;
   kp.max_log_window = mlw;
   kp.history_min = P.history_min;
-  kp.sigma_std = P.sigma_estimator == LOF_SIGMA_STD;
+  // 0 MAD, 1 stddev, 2 winsorized (the last only reaches the exact-statistics
+  // kernel: integer units, routed there below; float units reject it)
+  kp.sigma_std = P.sigma_estimator;
   kp.enable_freq = P.enable_freq;
   kp.enable_time = P.enable_time;
   kp.enable_history = P.enable_history;
@@ -658,9 +672,8 @@ int host_launch_kernel(const lof_params& P, const HostCfg& h, int dtype, const P
   kp.gen_words = pr.gen_words;
   const int krc = is_float(dtype)
                       ? lofk_launch_f32x(&kp, n_units, h.n_sm, pr.plan.smem, stream, dtype == LOF_CF32)
-                  : P.time_mode == LOF_TIME_INTEGRATED || P.stats_scope == LOF_SCOPE_CHANNEL
-                      ? lofk_launch_integ(dtype, &kp, n_units, h.n_sm, stream,
-                                          P.stats_scope == LOF_SCOPE_CHANNEL ? 1 : 0)
+                  : exact_stats_mode(P) >= 0
+                      ? lofk_launch_integ(dtype, &kp, n_units, h.n_sm, stream, exact_stats_mode(P))
                       : lofk_launch_block(dtype, &kp, pr.grid, pr.plan.threads, pr.plan.smem, stream,
                                           cooperative);
   if (krc != 0) {
@@ -696,14 +709,15 @@ int host_launch(const lof_params& P, const HostCfg& h, int dtype, const Prep& pr
   return host_launch_kernel(P, h, dtype, pr, sc, n_units, seq, stream, 1, why, nwhy);
 }
 
-// Options with limits of their own: the integrated time mode and the
-// per-channel statistics scope (integer units, rows up to
+// Options with limits of their own: the integrated time mode, the per-channel
+// statistics scope and the winsorized estimator (integer units, rows up to
 // lofk_integ_max_time() samples) and the SIR pass (the mask output, rows up to
 // lofk_sir_max_time() samples).
 int host_validate_options(const lof_params& P, int dtype, const lof_unit& u, int i, char* why, int nwhy) {
-  if (P.time_mode == LOF_TIME_INTEGRATED || P.stats_scope == LOF_SCOPE_CHANNEL) {
-    const char* what = P.time_mode == LOF_TIME_INTEGRATED ? "the integrated time mode"
-                                                          : "the per-channel statistics scope";
+  if (exact_stats_mode(P) >= 0) {
+    const char* what = P.time_mode == LOF_TIME_INTEGRATED       ? "the integrated time mode"
+                       : P.stats_scope == LOF_SCOPE_CHANNEL     ? "the per-channel statistics scope"
+                                                                : "the winsorized sigma estimator";
     if (is_float(dtype)) return snprintf(why, nwhy, "%s takes integer units only", what), LOF_ERR_INVALID;
     if (u.n_time > lofk_integ_max_time())
       return snprintf(why, nwhy, "unit %d: n_time %d above the limit %d of %s", i, u.n_time,

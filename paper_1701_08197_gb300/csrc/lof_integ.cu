@@ -1,7 +1,15 @@
-// lof_integ.cu -- the integrated time mode for integer voltage units
-// (lof_params.time_mode = 1): Section 3 integrates the time direction fully for
-// frequency flagging and the frequency direction fully for time-domain
-// flagging.  One CTA flags one unit at a time:
+// lof_integ.cu -- exact-statistics unit kernel for integer voltage units, one
+// CTA per unit, in three modes:
+//   0  the integrated time mode (lof_params.time_mode = 1): Section 3
+//      integrates the time direction fully for frequency flagging and the
+//      frequency direction fully for time-domain flagging (steps a1-a8 below);
+//   1  the per-channel statistics scope (stats_scope = 1): each kept channel's
+//      time pass with the median and sigma of its own powers;
+//   2  the pooled per-channel time pass with statistics selected exactly from
+//      the unit in global memory (the winsorized estimator, which the
+//      histogram statistics of the block kernel do not provide).
+// Every mode supports the three sigma estimators (MAD, stddev, winsorized).
+// The integrated mode, step by step:
 //   a1  powers re^2 + im^2 (exact integers)
 //   a2  row sums S[c] and the column series over all channels, one pass
 //   a3  median and sigma of S (Section 4.2; bitonic sort, exact)
@@ -27,6 +35,11 @@ constexpr int kNtI = 512, kNwI = kNtI / 32;
 constexpr int kIntegMaxT = 16384;
 constexpr unsigned kFullI = 0xFFFFFFFFu;
 constexpr double kMadToSigma = 1.482602218505602;
+// 1/sqrt(c): c = 0.8 - 2 z phi(z) + 0.2 z^2 = 0.6786545589528744 is the
+// variance of a standard normal clamped at its 10% / 90% quantiles +-z,
+// z = 1.2815515655446004, so the clamped stddev times this estimates sigma.
+constexpr double kWinsorToSigma = 1.2138796046717422;
+constexpr int kEstStd = 1, kEstWinsor = 2;  // KParams::sigma_std holds the estimator
 
 // shared memory layout (bytes)
 constexpr int kOffS = 0;                                  // u64 S[kMaxChan]
@@ -47,7 +60,7 @@ struct IntegShared {
   long long rank[2];
   int nrank, nkept, nfc;
   unsigned long long s1lo[kNwI], s1hi[kNwI], s2lo[kNwI], s2hi[kNwI];
-  unsigned long long rs[kNwI];
+  unsigned long long rs[kNwI], orw[kNwI];
   int rn[kNwI];
   int fh;
 };
@@ -171,10 +184,12 @@ __device__ void sort_u64(unsigned long long* a, int n) {
 }
 
 // Order statistics r0 <= r1 of n u64 keys key(i) (whole CTA): radix selection
-// with digits of 11 bits (the last of 9), one histogram per open rank.
+// with digits of 11 bits (the last of 9), one histogram per open rank.  Every
+// key is below 2^bits: the digits above are all zero and their passes, which
+// would leave the prefix at 0 and the ranks unchanged, are skipped.
 template <class K>
 __device__ void select2(long long n, long long r0, long long r1, K key, uint32_t* hist, IntegShared& f,
-                        unsigned long long* k0, unsigned long long* k1) {
+                        unsigned long long* k0, unsigned long long* k1, int bits = 64) {
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   if (tid == 0) {
     f.pref[0] = f.pref[1] = 0ull;
@@ -183,7 +198,9 @@ __device__ void select2(long long n, long long r0, long long r1, K key, uint32_t
     f.nrank = r0 == r1 ? 1 : 2;
   }
   __syncthreads();
-  for (int pass = 0; pass < 6; ++pass) {  // bits 63..53, 52..42, 41..31, 30..20, 19..9, 8..0
+  int first = 0;
+  while (first < 5 && 53 - 11 * first >= bits) ++first;
+  for (int pass = first; pass < 6; ++pass) {  // bits 63..53, 52..42, 41..31, 30..20, 19..9, 8..0
     const int nb = pass < 5 ? 11 : 9;
     const int sh = pass < 5 ? 53 - 11 * pass : 0;
     const int hs = sh + nb;
@@ -237,19 +254,56 @@ __device__ void select2(long long n, long long r0, long long r1, K key, uint32_t
   *k1 = f.pref[1];
 }
 
+// Bit length of the largest of n u64 values v(i) (whole CTA).
+template <class V>
+__device__ int key_bits(long long n, V v, IntegShared& f) {
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  unsigned long long o = 0;
+  for (long long i = tid; i < n; i += kNtI) o |= v(i);
+#pragma unroll
+  for (int k = 16; k > 0; k >>= 1) o |= __shfl_xor_sync(kFullI, o, k);
+  if (lane == 0) f.orw[warp] = o;
+  __syncthreads();
+  unsigned long long a = 0;
+  for (int w = 0; w < kNwI; ++w) a |= f.orw[w];
+  __syncthreads();
+  return a ? 64 - __clzll(static_cast<long long>(a)) : 0;
+}
+
+// Winsorized sigma of n u64 values v(i) given the order statistics lo = v_(k)
+// and hi = v_(n-1-k), k = n / 10: the population stddev of the values clamped
+// to [lo, hi] times kWinsorToSigma (the plain stddev when that is 0).
+template <class V>
+__device__ double winsor_sigma(long long n, V v, unsigned long long lo, unsigned long long hi, IntegShared& f) {
+  const double sw = exact_std(n, [&](long long i) {
+    const unsigned long long x = v(i);
+    return x < lo ? lo : (x > hi ? hi : x);
+  }, f);
+  return sw > 0.0 ? __dmul_rn(kWinsorToSigma, sw) : exact_std(n, v, f);
+}
+
 // Section 4.2 median and sigma of n u64 values v(i), exact: the median as
 // m2 / 2 with m2 = the sum of the two middle values (twice the middle one for
-// odd n); the MAD from the keys |2 v - m2| = 2 |v - median|.
+// odd n); the MAD from the keys |2 v - m2| = 2 |v - median|; the winsorized
+// sigma from the order statistics n / 10 and n - 1 - n / 10.
 template <class V>
 __device__ void stats_u64(const KParams& kp, long long n, V v, uint32_t* hist, IntegShared& f,
                           double* med, double* sig) {
+  const int bits = key_bits(n, v, f);
   const long long ra = (n & 1) ? n / 2 : n / 2 - 1, rb = n / 2;
   unsigned long long a, b;
-  select2(n, ra, rb, v, hist, f, &a, &b);
+  select2(n, ra, rb, v, hist, f, &a, &b, bits);
   const unsigned long long m2 = a + b;
   *med = __dmul_rn(static_cast<double>(m2), 0.5);
-  if (kp.sigma_std) {
+  if (kp.sigma_std == kEstStd) {
     *sig = exact_std(n, v, f);
+    return;
+  }
+  if (kp.sigma_std == kEstWinsor) {
+    const long long k = n / 10;
+    unsigned long long lo, hi;
+    select2(n, k, n - 1 - k, v, hist, f, &lo, &hi, bits);
+    *sig = winsor_sigma(n, v, lo, hi, f);
     return;
   }
   auto dev = [&](long long i) {
@@ -257,7 +311,7 @@ __device__ void stats_u64(const KParams& kp, long long n, V v, uint32_t* hist, I
     return x2 >= m2 ? x2 - m2 : m2 - x2;
   };
   unsigned long long da, db;
-  select2(n, ra, rb, dev, hist, f, &da, &db);
+  select2(n, ra, rb, dev, hist, f, &da, &db, bits + 1);
   const double mad = __dmul_rn(static_cast<double>(da + db), 0.25);
   *sig = mad > 0.0 ? __dmul_rn(kMadToSigma, mad) : exact_std(n, v, f);
 }
@@ -268,8 +322,12 @@ __device__ __forceinline__ double thr_i(const KParams& kp, double m, double s, i
 }
 
 // Section 2.1 SumThreshold over v[0..L) (whole CTA), flags in / out in fl,
-// next as scratch: window sums of the unflagged values in binary64 (exact
-// for these integers), a window fires when the sum exceeds (I - n) * thr_I.
+// next as scratch: a window fires when the sum of its unflagged values exceeds
+// (I - n) * thr_I.  The values are integers and every window sum is at most
+// 2^51 (64 spectrum sums of at most 2^14 powers of at most 2^31, or 64 series
+// values of at most 2^11 such powers), so the sum is accumulated in 64-bit
+// integers and converted once: the same number as a binary64 sum, whose every
+// partial sum is exact, at a fraction of the binary64 operations.
 template <class V>
 __device__ void st_1d(const KParams& kp, V v, int L, double med, double sig, uint8_t* fl,
                       uint8_t* next) {
@@ -282,12 +340,12 @@ __device__ void st_1d(const KParams& kp, V v, int L, double med, double sig, uin
     __syncthreads();
     for (int t = threadIdx.x; t + I <= L; t += kNtI) {
       int nf = 0;
-      double su = 0.0;
+      unsigned long long su = 0;
       for (int j = t; j < t + I; ++j) {
         if (fl[j]) ++nf;
-        else su = __dadd_rn(su, static_cast<double>(v(j)));
+        else su += v(j);
       }
-      if (su > __dmul_rn(static_cast<double>(I - nf), thr))
+      if (__ull2double_rn(su) > __dmul_rn(static_cast<double>(I - nf), thr))
         for (int j = t; j < t + I; ++j) next[j] = 1;
     }
     __syncthreads();
@@ -312,8 +370,11 @@ __device__ void freq_stage(const KParams& kp, unsigned long long* S, unsigned lo
     const unsigned long long m2 = srt[ra] + srt[rb];
     const double med = __dmul_rn(static_cast<double>(m2), 0.5);
     double sig;
-    if (kp.sigma_std) {
+    if (kp.sigma_std == kEstStd) {
       sig = exact_std(C, [&](long long i) { return S[i]; }, f);
+    } else if (kp.sigma_std == kEstWinsor) {
+      const unsigned long long lo = srt[C / 10], hi = srt[C - 1 - C / 10];
+      sig = winsor_sigma(C, [&](long long i) { return S[i]; }, lo, hi, f);
     } else {
       __syncthreads();
       for (int i = tid; i < n2; i += kNtI) {
@@ -518,11 +579,13 @@ __device__ void integ_unit(const KParams& kp, const DevUnit& u, uint8_t* smem, I
 }
 
 
-// Per-channel statistics scope (stats_scope = 1, time pass per channel): the
-// frequency stage as above, then, one kept channel at a time with the whole
-// CTA, the exact median and sigma of the channel's own powers, SumThreshold
-// along its row, the history test and the output.
-template <int DT>
+// The per-channel time pass (Section 2.1 along time on every kept channel):
+// the frequency stage as above; then, with POOLED, one median and sigma over
+// every power of the kept channels, selected exactly from the unit in global
+// memory, else (the per-channel statistics scope) each kept channel's own;
+// then, one kept channel at a time with the whole CTA, SumThreshold along its
+// row, the history test and the output.
+template <int DT, bool POOLED>
 __device__ void chan_unit(const KParams& kp, const DevUnit& u, uint8_t* smem, IntegShared& f) {
   constexpr int ES = DT == LOF_CI16 ? 4 : 2;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
@@ -551,6 +614,28 @@ __device__ void chan_unit(const KParams& kp, const DevUnit& u, uint8_t* smem, In
   }
   __syncthreads();
   freq_stage(kp, S, srt, C, Fc, Fcn, f);
+  double med_p = 0.0, sig_p = 0.0;
+  if constexpr (POOLED) {
+    // the kept channels' indices, in order, in the (now free) sort buffer
+    int* kidx = reinterpret_cast<int*>(srt);
+    if (tid == 0) {
+      int nk = 0;
+      for (int c = 0; c < C; ++c)
+        if (!Fc[c]) kidx[nk++] = c;
+      f.nkept = nk;
+    }
+    __syncthreads();
+    const long long nu = static_cast<long long>(f.nkept) * T;
+    if (nu > 0)
+      stats_u64(kp, nu, [&](long long i) {
+        const uint32_t ii = static_cast<uint32_t>(i);  // nu <= 2048 * 16384
+        const int r = static_cast<int>(ii / static_cast<uint32_t>(T));
+        const int t = static_cast<int>(ii - static_cast<uint32_t>(r) * static_cast<uint32_t>(T));
+        return static_cast<unsigned long long>(
+            ipow<DT>(gin + static_cast<int64_t>(kidx[r]) * u.in_stride * ES, t));
+      }, hist, f, &med_p, &sig_p);
+    __syncthreads();
+  }
   int nfc = 0;
   for (int c = 0; c < C; ++c) {
     const uint8_t* row = gin + static_cast<int64_t>(c) * u.in_stride * ES;
@@ -565,8 +650,8 @@ __device__ void chan_unit(const KParams& kp, const DevUnit& u, uint8_t* smem, In
         Ft[t] = 0;
       }
       __syncthreads();
-      double med = 0.0, sig = 0.0;
-      stats_u64(kp, T, [&](long long i) { return R[i]; }, hist, f, &med, &sig);
+      double med = med_p, sig = sig_p;
+      if constexpr (!POOLED) stats_u64(kp, T, [&](long long i) { return R[i]; }, hist, f, &med, &sig);
       if (kp.enable_time) st_1d(kp, [&](int i) { return R[i]; }, T, med, sig, Ft, Fn);
       __syncthreads();
       unsigned long long sum = 0;
@@ -644,8 +729,8 @@ __device__ void chan_unit(const KParams& kp, const DevUnit& u, uint8_t* smem, In
   if (tid == 0 && u.stats) {
     u.stats->median_f = f.median_f;
     u.stats->sigma_f = f.sigma_f;
-    u.stats->median_t = 0.0;
-    u.stats->sigma_t = 0.0;
+    u.stats->median_t = med_p;
+    u.stats->sigma_t = sig_p;
     u.stats->n_chan_freq = nfc;
     u.stats->n_flag_time = static_cast<long long>(f.cnt_time);
     u.stats->n_chan_hist = static_cast<long long>(f.cnt_hist);
@@ -654,14 +739,15 @@ __device__ void chan_unit(const KParams& kp, const DevUnit& u, uint8_t* smem, In
   __syncthreads();
 }
 
-// MODE 0: integrated time mode; MODE 1: per-channel statistics scope.
+// MODE 0: integrated time mode; MODE 1: per-channel statistics scope; MODE 2:
+// pooled per-channel time pass.
 template <int DT, int MODE>
 __global__ void __launch_bounds__(kNtI, 1) lof_integ_kernel(const KParams kp) {
   extern __shared__ __align__(16) uint8_t smem[];
   __shared__ IntegShared f;
   for (int ui = blockIdx.x; ui < kp.n_units; ui += gridDim.x) {
     if constexpr (MODE == 0) integ_unit<DT>(kp, kp.units[ui], smem, f);
-    else chan_unit<DT>(kp, kp.units[ui], smem, f);
+    else chan_unit<DT, MODE == 2>(kp, kp.units[ui], smem, f);
   }
 }
 
@@ -670,18 +756,21 @@ __global__ void __launch_bounds__(kNtI, 1) lof_integ_kernel(const KParams kp) {
 
 extern "C" int lofk_integ_max_time() { return lofk::kIntegMaxT; }
 
-// The integrated time mode (mode 0) or the per-channel statistics scope
-// (mode 1) over n_units integer units (one CTA per unit).
+// The integrated time mode (mode 0), the per-channel statistics scope (mode 1)
+// or the pooled per-channel pass with exact statistics (mode 2) over n_units
+// integer units (one CTA per unit).
 extern "C" int lofk_launch_integ(int dtype, const lofk::KParams* kp, int n_units, int n_sm, void* stream,
                                  int mode) {
   using namespace lofk;
   if (n_units <= 0) return 0;
-  const void* k =
-      dtype == LOF_CI16
-          ? (mode ? reinterpret_cast<const void*>(&lof_integ_kernel<LOF_CI16, 1>)
-                  : reinterpret_cast<const void*>(&lof_integ_kernel<LOF_CI16, 0>))
-          : (mode ? reinterpret_cast<const void*>(&lof_integ_kernel<LOF_CI8, 1>)
-                  : reinterpret_cast<const void*>(&lof_integ_kernel<LOF_CI8, 0>));
+  if (mode < 0 || mode > 2) return static_cast<int>(cudaErrorInvalidValue);
+  const void* ks[2][3] = {{reinterpret_cast<const void*>(&lof_integ_kernel<LOF_CI16, 0>),
+                           reinterpret_cast<const void*>(&lof_integ_kernel<LOF_CI16, 1>),
+                           reinterpret_cast<const void*>(&lof_integ_kernel<LOF_CI16, 2>)},
+                          {reinterpret_cast<const void*>(&lof_integ_kernel<LOF_CI8, 0>),
+                           reinterpret_cast<const void*>(&lof_integ_kernel<LOF_CI8, 1>),
+                           reinterpret_cast<const void*>(&lof_integ_kernel<LOF_CI8, 2>)}};
+  const void* k = ks[dtype == LOF_CI16 ? 0 : 1][mode];
   if (cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, kIntegSmem) != cudaSuccess)
     return -2;
   const int grid = n_units < n_sm ? n_units : n_sm;
