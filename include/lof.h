@@ -6,10 +6,11 @@
  * one (station, polarisation, subband) block of n_chan channels x n_time
  * samples (pre-correlation placement, Section 3), or one beam-formed Stokes I
  * subband (post-beam-forming placement).  Per unit, in this order:
- *   a1  power P[c,t] = re^2 + im^2 of the complex voltages (Section 4: "we may
- *       have to compute amplitudes first"); Stokes I input is already power;
- *   a2  time-integrated spectrum S[c] = sum_t P[c,t] (Section 4: "integrate the
- *       time direction fully for frequency flagging");
+ *   a1  power P[c,t] = re^2 + im^2 of the complex voltages (Section 4: complex
+ *       input is turned into power before flagging); Stokes I input is already
+ *       power;
+ *   a2  time-integrated spectrum S[c] = sum_t P[c,t] (Section 3: for frequency
+ *       flagging the time axis is summed away entirely);
  *   a3  median and robust stddev of S (Section 4.2);
  *   a4  SumThreshold over S (Section 2.1) -> whole channels flagged;
  *   a5  median and robust stddev pooled over every sample of the channels the

@@ -22,9 +22,8 @@
  *    clamped values and scales it by 1/sqrt(c) so that it estimates sigma of
  *    normal data (population stddev when the result is 0);
  *  - time-pass statistics pool every sample of the channels the frequency
- *    pass left unflagged (Section 4: frequency flagging first "removes strong
- *    narrow-band RFI that would otherwise decrease the quality of the
- *    statistics");
+ *    pass left unflagged (Section 4: flagging frequency first clears strong
+ *    narrow-band interference, which would otherwise spoil these statistics);
  *  - the history flagger keeps one ring of per-channel means, multiplier k,
  *    ties flag (a channel is kept only when its mean is strictly below the
  *    threshold, as in the paper's code);
@@ -300,7 +299,8 @@ int lof_ref_flag_unit(const lof_ref_params *pr, int dtype, const void *in, int C
       F[(int64_t)c * T + t] = (uint8_t)bad;
     }
 
-  /* Section 4: integrate the time direction fully for frequency flagging. */
+  /* Section 3: the spectrum for frequency flagging sums each channel over all
+   * of its time samples. */
   uint8_t *Fc = (uint8_t *)calloc((size_t)(C > 0 ? C : 1), 1);
   double *S = (double *)malloc((size_t)(C > 0 ? C : 1) * sizeof(double));
   for (int c = 0; c < C; ++c) {
@@ -314,8 +314,8 @@ int lof_ref_flag_unit(const lof_ref_params *pr, int dtype, const void *in, int C
   for (int c = 0; c < C; ++c) st.n_chan_freq += Fc[c];
 
   if (pr->time_mode == 1) {
-    /* Section 3: integrate the frequency direction fully for time-domain
-     * flagging, over the channels the frequency pass kept. */
+    /* Section 3: for time-domain flagging the frequency axis is summed away
+     * entirely, over the channels the frequency pass kept. */
     double *G = (double *)malloc((size_t)(T > 0 ? T : 1) * sizeof(double));
     uint8_t *Ft = (uint8_t *)calloc((size_t)(T > 0 ? T : 1), 1);
     int nkept = 0;

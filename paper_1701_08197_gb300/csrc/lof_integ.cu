@@ -1,8 +1,8 @@
 // lof_integ.cu -- exact-statistics unit kernel for integer voltage units, one
 // CTA per unit, in three modes:
-//   0  the integrated time mode (lof_params.time_mode = 1): Section 3
-//      integrates the time direction fully for frequency flagging and the
-//      frequency direction fully for time-domain flagging (steps a1-a8 below);
+//   0  the integrated time mode (lof_params.time_mode = 1): Section 3 sums
+//      the time axis away for frequency flagging and the frequency axis away
+//      for time-domain flagging (steps a1-a8 below);
 //   1  the per-channel statistics scope (stats_scope = 1): each kept channel's
 //      time pass with the median and sigma of its own powers;
 //   2  the pooled per-channel time pass with statistics selected exactly from

@@ -38,7 +38,7 @@ def test_factor_table_matches_section_2_1():
 
 
 def test_printed_sigmas():
-    # Section 2.1: "more than 6 sigma away from the median", then "4.5 sigma".
+    # Section 2.1 prints 6 sigma for the first iteration and 4.5 sigma for the second.
     P = oracle.default_params()
     assert oracle.threshold(P, 0.0, 1.0, 0) == 6.0
     assert oracle.threshold(P, 0.0, 1.0, 1) == 4.5
