@@ -40,6 +40,8 @@ class Params(ctypes.Structure):
         ("sir_percent", ctypes.c_int),
         ("time_mode", ctypes.c_int),
         ("stats_scope", ctypes.c_int),
+        ("integ_chan", ctypes.c_int),
+        ("integ_time", ctypes.c_int),
     ]
 
 
@@ -63,7 +65,8 @@ def default_params(**kw) -> Params:
     """Paper defaults (Section 2.1: p=1.5, sensitivity=1, 6 sigma at I=1)."""
     d = dict(p=1.5, sensitivity=1.0, start_threshold=6.0, max_window=64, history_len=60,
              history_min=8, history_k=6.0, sigma_estimator=SIGMA_MAD, enable_freq=1,
-             enable_time=1, enable_history=1, sir_percent=0, time_mode=0, stats_scope=0)
+             enable_time=1, enable_history=1, sir_percent=0, time_mode=0, stats_scope=0,
+             integ_chan=1, integ_time=1)
     d.update(kw)
     return Params(**d)
 

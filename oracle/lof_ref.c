@@ -35,6 +35,14 @@
  *    each kept channel's time pass the median and sigma of that channel's own
  *    samples instead of the pooled ones (the unit's median_t and sigma_t are
  *    then reported as 0);
+ *  - the two-dimensional mode (time_mode = 2; Sections 2.1 and 3 mention a 2-D
+ *    flagger that integrates partially in one or both directions) replaces
+ *    both one-dimensional passes: the powers are summed into cells of
+ *    integ_chan channels x integ_time samples, one median and sigma are taken
+ *    over the cells, and for each window size I SumThreshold runs along time
+ *    on every row of cells and then along frequency on every column; a
+ *    flagged cell flags all of its samples (enable_time / enable_freq switch
+ *    the two directions);
  *  - the SIR operator (Section 2.2, optional) is the scale-invariant rank
  *    operator the section names, with eta = sir_percent / 100: a sample is
  *    flagged when an interval around it is at least (1 - eta) flagged.  It
@@ -179,6 +187,31 @@ void lof_ref_sum_threshold(const lof_ref_params *pr, const double *v, int64_t L,
   free(next);
 }
 
+/* One window size of Section 2.1 on a line of L values v[i * stride], flags
+ * f[i * stride]: every window [t, t + I) is judged against the flags on entry
+ * and fires when the sum of its unflagged values exceeds
+ * (I - n_flagged) * thr; the fired windows are flagged afterwards. */
+static void st_one_size(const double *v, int64_t L, int64_t stride, int64_t I, double thr,
+                        uint8_t *f) {
+  uint8_t *next = (uint8_t *)malloc((size_t)(L > 0 ? L : 1));
+  for (int64_t i = 0; i < L; ++i) next[i] = f[i * stride];
+  for (int64_t t = 0; t + I <= L; ++t) {
+    int64_t nf = 0;
+    double su = 0.0;
+    for (int64_t j = t; j < t + I; ++j) {
+      if (f[j * stride])
+        nf++;
+      else
+        su = su + v[j * stride];
+    }
+    double limit = (double)(I - nf) * thr;
+    if (su > limit)
+      for (int64_t j = t; j < t + I; ++j) next[j] = 1;
+  }
+  for (int64_t i = 0; i < L; ++i) f[i * stride] = next[i];
+  free(next);
+}
+
 /* Section 2.2: scale-invariant rank operator on one line.  With integer
  * weights w = +percent for a flagged sample and -(100 - percent) for an
  * unflagged one, an interval [a, b) is at least (100 - percent)% flagged
@@ -309,11 +342,67 @@ int lof_ref_flag_unit(const lof_ref_params *pr, int dtype, const void *in, int C
       if (!F[(int64_t)c * T + t]) s = s + P[(int64_t)c * T + t];
     S[c] = s;
   }
-  if (C > 0) st.sigma_f = lof_ref_sigma(pr, S, C, is_int, &st.median_f);
-  if (pr->enable_freq && C > 0) lof_ref_sum_threshold(pr, S, C, st.median_f, st.sigma_f, Fc);
-  for (int c = 0; c < C; ++c) st.n_chan_freq += Fc[c];
+  if (pr->time_mode != 2) { /* the 2-D mode has no separate frequency pass */
+    if (C > 0) st.sigma_f = lof_ref_sigma(pr, S, C, is_int, &st.median_f);
+    if (pr->enable_freq && C > 0) lof_ref_sum_threshold(pr, S, C, st.median_f, st.sigma_f, Fc);
+    for (int c = 0; c < C; ++c) st.n_chan_freq += Fc[c];
+  }
 
-  if (pr->time_mode == 1) {
+  if (pr->time_mode == 2) {
+    /* Two-dimensional SumThreshold on integration cells. */
+    const int Fi = pr->integ_chan, Ti = pr->integ_time;
+    const int Cg = (Fi > 0 && C % Fi == 0) ? C / Fi : -1;
+    const int Tg = (Ti > 0 && T % Ti == 0) ? T / Ti : -1;
+    if (Cg < 0 || Tg < 0) {
+      free(P);
+      free(F);
+      free(Fc);
+      free(S);
+      return -1;
+    }
+    const int64_t NG = (int64_t)Cg * Tg;
+    double *V = (double *)calloc((size_t)(NG > 0 ? NG : 1), sizeof(double));
+    int64_t *cnt = (int64_t *)calloc((size_t)(NG > 0 ? NG : 1), sizeof(int64_t));
+    uint8_t *Fg = (uint8_t *)calloc((size_t)(NG > 0 ? NG : 1), 1);
+    /* a cell's value: the sum of its unflagged powers; a cell with none is flagged */
+    for (int c = 0; c < C; ++c)
+      for (int t = 0; t < T; ++t)
+        if (!F[(int64_t)c * T + t]) {
+          const int64_t g = (int64_t)(c / Fi) * Tg + t / Ti;
+          V[g] = V[g] + P[(int64_t)c * T + t];
+          cnt[g]++;
+        }
+    int64_t nu = 0;
+    double *U = (double *)malloc((size_t)(NG > 0 ? NG : 1) * sizeof(double));
+    for (int64_t g = 0; g < NG; ++g) {
+      if (cnt[g] == 0)
+        Fg[g] = 1;
+      else
+        U[nu++] = V[g];
+    }
+    if (nu > 0) st.sigma_t = lof_ref_sigma(pr, U, nu, is_int, &st.median_t);
+    if (nu > 0 && st.sigma_t > 0.0) {
+      for (int k = 0;; ++k) {
+        const int64_t I = (int64_t)1 << k;
+        if (I > pr->max_window || (I > Tg && I > Cg)) break;
+        const double thr = lof_ref_threshold(pr, st.median_t, st.sigma_t, k);
+        if (pr->enable_time && I <= Tg) /* along time, every row of cells */
+          for (int g = 0; g < Cg; ++g) st_one_size(V + (int64_t)g * Tg, Tg, 1, I, thr, Fg + (int64_t)g * Tg);
+        if (pr->enable_freq && I <= Cg) /* then along frequency, every column */
+          for (int h = 0; h < Tg; ++h) st_one_size(V + h, Cg, Tg, I, thr, Fg + h);
+      }
+    }
+    for (int c = 0; c < C; ++c)
+      for (int t = 0; t < T; ++t)
+        if (Fg[(int64_t)(c / Fi) * Tg + t / Ti] && !F[(int64_t)c * T + t]) {
+          F[(int64_t)c * T + t] = 1;
+          st.n_flag_time++;
+        }
+    free(U);
+    free(V);
+    free(cnt);
+    free(Fg);
+  } else if (pr->time_mode == 1) {
     /* Section 3: for time-domain flagging the frequency axis is summed away
      * entirely, over the channels the frequency pass kept. */
     double *G = (double *)malloc((size_t)(T > 0 ? T : 1) * sizeof(double));

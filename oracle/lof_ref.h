@@ -45,8 +45,11 @@ typedef struct {
   int sigma_estimator;    /* LOF_REF_SIGMA_MAD, LOF_REF_SIGMA_STD or LOF_REF_SIGMA_WINSOR */
   int enable_freq, enable_time, enable_history;
   int sir_percent;        /* Section 2.2 SIR operator, eta in percent (0 = off) */
-  int time_mode;          /* 0: time pass per channel; 1: on the frequency-integrated series */
+  int time_mode;          /* 0: time pass per channel; 1: on the frequency-integrated series;
+                             2: two-dimensional SumThreshold on integration cells */
   int stats_scope;        /* time-pass statistics: 0 pooled over the unit; 1 per channel */
+  int integ_chan, integ_time; /* time_mode 2: channels x samples summed into one cell (1 = none);
+                                 each divides the unit's size in its direction */
 } lof_ref_params;
 
 typedef struct {
