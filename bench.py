@@ -100,6 +100,8 @@ def parse():
     ap.add_argument("--channel-scope", action="store_true",
                     help="per-channel statistics scope: each kept channel's time pass with the "
                          "median and sigma of its own samples instead of the pooled ones")
+    ap.add_argument("--grid", default=None, metavar="FxT",
+                    help="two-dimensional mode on cells of F channels x T samples (e.g. 4x16)")
     ap.add_argument("--sigma", default="mad", choices=list(SIGMA),
                     help="sigma estimator of the statistics (Section 4.2): 1.4826 * MAD, "
                          "population stddev or winsorized stddev")
@@ -210,8 +212,16 @@ def build_units(x, out, mask, stats, slot_base=0):
     return units
 
 
+def grid_cells(grid):
+    """(channels, samples) per cell of the two-dimensional mode, or None."""
+    if not grid:
+        return None
+    f, t = grid.lower().split("x")
+    return int(f), int(t)
+
+
 def workload_config(stations: int, sir: int = 0, integrated: bool = False, scope: bool = False,
-                    sigma: str = "mad") -> dict:
+                    sigma: str = "mad", grid=None) -> dict:
     c = {"workload": f"full LOFAR pre-beamformer block: {stations} st x 2 pol x 8 sb "
                      f"= {stations * 16} units x 256 ch x 3072 t, complex int16, history 60",
          "launch": "batched persistent (1 launch per block) + history commit",
@@ -225,6 +235,8 @@ def workload_config(stations: int, sir: int = 0, integrated: bool = False, scope
         c["stats_scope"] = "per channel"
     if sigma != "mad":
         c["sigma_estimator"] = sigma
+    if grid_cells(grid):
+        c["time_mode"] = "two-dimensional on %d x %d cells" % grid_cells(grid)
     return c
 
 
@@ -263,9 +275,12 @@ def run_gpu(args):
     mask = torch.empty(x.shape[:-1], dtype=torch.uint8, device=dev)
     stats = lof.stats_tensor(n_units, dev)
     fl = lof.Flagger(local, n_history_slots=n_units * C, sir_percent=args.sir,
-                     time_mode=lof.LOF_TIME_INTEGRATED if args.integrated else lof.LOF_TIME_PER_CHANNEL,
+                     time_mode=(lof.LOF_TIME_2D if args.grid else
+                                lof.LOF_TIME_INTEGRATED if args.integrated else lof.LOF_TIME_PER_CHANNEL),
                      stats_scope=lof.LOF_SCOPE_CHANNEL if args.channel_scope else lof.LOF_SCOPE_POOLED,
-                     sigma_estimator=SIGMA[args.sigma])
+                     sigma_estimator=SIGMA[args.sigma],
+                     integ_chan=(grid_cells(args.grid) or (1, 1))[0],
+                     integ_time=(grid_cells(args.grid) or (1, 1))[1])
     # rings pre-filled with 60 means per channel (steady state of the history flagger)
     pw = (x.to(torch.float32) ** 2).sum(-1).mean(-1).reshape(-1).double().cpu().numpy()
     rng = np.random.default_rng(7)
@@ -376,7 +391,7 @@ def run_gpu(args):
     return res
 
 
-def oracle_sample(seconds: float, seed=2, sir=0, integrated=False, scope=False, sigma="mad"):
+def oracle_sample(seconds: float, seed=2, sir=0, integrated=False, scope=False, sigma="mad", grid=None):
     """The oracle (as it stands) on host cores: units of the same workload, one
     per thread (the paper's thread-per-subband CPU layout), bounded in time."""
     from concurrent.futures import ThreadPoolExecutor
@@ -385,8 +400,10 @@ def oracle_sample(seconds: float, seed=2, sir=0, integrated=False, scope=False, 
 
     import oracle
     from paper_1701_08197_gb300 import synth
-    P = oracle.default_params(sir_percent=sir, time_mode=1 if integrated else 0, stats_scope=1 if scope else 0,
-                              sigma_estimator=SIGMA[sigma])
+    cells = grid_cells(grid) or (1, 1)
+    P = oracle.default_params(sir_percent=sir, time_mode=2 if grid else 1 if integrated else 0,
+                              stats_scope=1 if scope else 0, sigma_estimator=SIGMA[sigma],
+                              integ_chan=cells[0], integ_time=cells[1])
     cores = os.cpu_count() or 1
     spec = synth.VoltageSpec(n_station=1, n_pol=N_POL, n_subband=N_SUBBAND, C=C, T=T,
                              sigma=32.0, tone_frac=0.02, impulse_frac=0.01)
@@ -427,7 +444,8 @@ def main():
         cb = None
         for i in range(args.warmup + args.steps):
             r = oracle_sample(max(2.0, args.cpu_seconds / max(1, args.steps)), sir=args.sir,
-                              integrated=args.integrated, scope=args.channel_scope, sigma=args.sigma)
+                              integrated=args.integrated, scope=args.channel_scope, sigma=args.sigma,
+                              grid=args.grid)
             if i >= args.warmup:
                 steps.append(r)
             cb = r
@@ -439,7 +457,8 @@ def main():
                 "higher_is_better": True,
                 "scaling": "weak", "vs_baseline": None, "dtype": "int64+f64",
                 "data": "synthetic (seeded)",
-                "config": workload_config(args.stations, args.sir, args.integrated, args.channel_scope, args.sigma),
+                "config": workload_config(args.stations, args.sir, args.integrated, args.channel_scope, args.sigma,
+                                    args.grid),
                 "cpu_baseline": {"value": v, "unit": "Msamples/s", "cores": cb["cores"],
                                  "kind": "oracle", "sample": cb["sample"]},
                 "e2e": {"value": v, "unit": "Msamples/s", "h2d_bytes_per_step": 0,
@@ -465,14 +484,16 @@ def main():
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": res["ms_per_step"],
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int32/u64",
         "data": "synthetic (seeded noise + tones + impulses)",
-        "config": dict(workload_config(args.stations, args.sir, args.integrated, args.channel_scope, args.sigma), tuning=res["tuning"]),
+        "config": dict(workload_config(args.stations, args.sir, args.integrated, args.channel_scope, args.sigma,
+                                    args.grid), tuning=res["tuning"]),
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                      "frac": achieved / peak,
                      # the recorded counters are those of the block kernel alone
                      "traffic": None if (args.integrated or args.channel_scope or args.sir
-                                         or args.sigma == "winsor")
+                                         or args.sigma == "winsor" or args.grid)
                      else measured_traffic(args.stations * 16, res["tuning"]),
-                     "kernel": ("lof_integ_kernel<CI16, integrated>" if args.integrated
+                     "kernel": ("lof_integ_kernel<CI16, two-dimensional>" if args.grid
+                                else "lof_integ_kernel<CI16, integrated>" if args.integrated
                                 else "lof_integ_kernel<CI16, channel scope>" if args.channel_scope
                                 else "lof_integ_kernel<CI16, pooled exact>" if args.sigma == "winsor"
                                 else "lof_block_kernel<CI16>")
@@ -493,7 +514,7 @@ def main():
         line["e2e"] = res["e2e"]
     if not args.no_cpu:
         line["cpu_baseline"] = oracle_sample(args.cpu_seconds, sir=args.sir, integrated=args.integrated,
-                                             scope=args.channel_scope, sigma=args.sigma)
+                                             scope=args.channel_scope, sigma=args.sigma, grid=args.grid)
     print(json.dumps(line))
 
 

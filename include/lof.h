@@ -83,7 +83,7 @@ enum { LOF_CI8 = 1, LOF_CI16 = 2, LOF_F32 = 3, LOF_CF32 = 4 };
 
 enum { LOF_SIGMA_MAD = 0, LOF_SIGMA_STD = 1, LOF_SIGMA_WINSOR = 2 };
 
-enum { LOF_TIME_PER_CHANNEL = 0, LOF_TIME_INTEGRATED = 1 };
+enum { LOF_TIME_PER_CHANNEL = 0, LOF_TIME_INTEGRATED = 1, LOF_TIME_2D = 2 };
 
 enum { LOF_SCOPE_POOLED = 0, LOF_SCOPE_CHANNEL = 1 };
 
@@ -119,7 +119,18 @@ typedef struct {
                               integrated fully -- one series of the summed powers of the
                               kept channels, its own median and sigma, one SumThreshold,
                               a flagged time step flagged in every kept channel.
-                              Integer units only, n_time <= 16384 */
+                              Integer units only, n_time <= 16384.
+                              LOF_TIME_2D (Sections 2.1 and 3 mention a 2-D flagger that
+                              integrates partially): replaces both passes -- the powers are
+                              summed into cells of integ_chan x integ_time samples, one
+                              median and sigma are taken over the cells, and for each window
+                              size SumThreshold runs along time on every row of cells and
+                              then along frequency on every column (enable_time /
+                              enable_freq switch the directions); a flagged cell flags all
+                              of its samples; median_f, sigma_f, n_chan_freq are reported as
+                              0 and median_t, sigma_t are the cells' statistics.  Integer
+                              units; the cell sizes divide n_chan and n_time; at most 16384
+                              cells per unit */
   int32_t stats_scope;     /* statistics of the per-channel time pass (Section 4.2 reading):
                               LOF_SCOPE_POOLED (default) -- one median and sigma pooled over
                               the unit's kept channels; LOF_SCOPE_CHANNEL -- each kept
@@ -127,6 +138,9 @@ typedef struct {
                               unit's median_t and sigma_t are then reported as 0).
                               LOF_SCOPE_CHANNEL takes integer units, time_mode
                               LOF_TIME_PER_CHANNEL and n_time <= 16384 */
+  int32_t integ_chan;      /* LOF_TIME_2D: channels per cell (default 1) */
+  int32_t integ_time;      /* LOF_TIME_2D: samples per cell (default 1); integ_chan *
+                              integ_time <= 65536 */
 } lof_params;
 
 /* Per-unit results, written by lof_flag_block when lof_unit.stats != NULL

@@ -50,7 +50,7 @@ extern "C" int lofk_launch_f32x(const lofk::KParams* kp, int n_units, int n_sm, 
 extern "C" int lofk_sir_max_time();
 extern "C" int lofk_integ_max_time();
 extern "C" int lofk_launch_integ(int dtype, const lofk::KParams* kp, int n_units, int n_sm, void* stream,
-                                 int mode);
+                                 int mode, int cell_chan, int cell_time);
 extern "C" int lofk_launch_sir(const lofk::DevUnit* units, int n_units, int64_t n_chan, int max_chan,
                                int percent, int es, void* stream);
 
@@ -192,6 +192,8 @@ extern "C" void lof_default_params(lof_params* p) {
   p->sir_percent = 0;
   p->time_mode = LOF_TIME_PER_CHANNEL;
   p->stats_scope = LOF_SCOPE_POOLED;
+  p->integ_chan = 1;
+  p->integ_time = 1;
 }
 
 extern "C" const char* lof_last_error(const lof_ctx* c) {
@@ -222,7 +224,8 @@ static int validate_params(const lof_params* p, std::string* why) {
     *why = "sir_percent in [0, 99] required";
     return 0;
   }
-  if (p->time_mode != LOF_TIME_PER_CHANNEL && p->time_mode != LOF_TIME_INTEGRATED) {
+  if (p->time_mode != LOF_TIME_PER_CHANNEL && p->time_mode != LOF_TIME_INTEGRATED &&
+      p->time_mode != LOF_TIME_2D) {
     *why = "unknown time_mode";
     return 0;
   }
@@ -232,6 +235,11 @@ static int validate_params(const lof_params* p, std::string* why) {
   }
   if (p->stats_scope == LOF_SCOPE_CHANNEL && p->time_mode != LOF_TIME_PER_CHANNEL) {
     *why = "stats_scope LOF_SCOPE_CHANNEL needs time_mode LOF_TIME_PER_CHANNEL";
+    return 0;
+  }
+  if (p->integ_chan < 1 || p->integ_time < 1 ||
+      static_cast<int64_t>(p->integ_chan) * p->integ_time > 65536) {
+    *why = "integ_chan, integ_time >= 1 with integ_chan * integ_time <= 65536 required";
     return 0;
   }
   return 1;
@@ -612,9 +620,11 @@ int host_prepare(const HostCfg& h, int dtype, const lof_unit* units, int n_units
 // and queue reset, the kernel launch.  Stream-capturable.
 // The mode of the exact-statistics unit kernel an option set runs on (one CTA
 // per unit): 0 the integrated time mode, 1 the per-channel statistics scope, 2
-// the pooled per-channel pass with the winsorized estimator; -1 the block
-// kernel (or the float kernel) with its histogram statistics.
+// the pooled per-channel pass with the winsorized estimator, 3 the
+// two-dimensional mode; -1 the block kernel (or the float kernel) with its
+// histogram statistics.
 int exact_stats_mode(const lof_params& P) {
+  if (P.time_mode == LOF_TIME_2D) return 3;
   if (P.time_mode == LOF_TIME_INTEGRATED) return 0;
   if (P.stats_scope == LOF_SCOPE_CHANNEL) return 1;
   if (P.sigma_estimator == LOF_SIGMA_WINSOR) return 2;
@@ -673,7 +683,8 @@ int host_launch_kernel(const lof_params& P, const HostCfg& h, int dtype, const P
   const int krc = is_float(dtype)
                       ? lofk_launch_f32x(&kp, n_units, h.n_sm, pr.plan.smem, stream, dtype == LOF_CF32)
                   : exact_stats_mode(P) >= 0
-                      ? lofk_launch_integ(dtype, &kp, n_units, h.n_sm, stream, exact_stats_mode(P))
+                      ? lofk_launch_integ(dtype, &kp, n_units, h.n_sm, stream, exact_stats_mode(P),
+                                          P.integ_chan, P.integ_time)
                       : lofk_launch_block(dtype, &kp, pr.grid, pr.plan.threads, pr.plan.smem, stream,
                                           cooperative);
   if (krc != 0) {
@@ -711,18 +722,31 @@ int host_launch(const lof_params& P, const HostCfg& h, int dtype, const Prep& pr
 
 // Options with limits of their own: the integrated time mode, the per-channel
 // statistics scope and the winsorized estimator (integer units, rows up to
-// lofk_integ_max_time() samples) and the SIR pass (the mask output, rows up to
-// lofk_sir_max_time() samples).
+// lofk_integ_max_time() samples), the two-dimensional mode (integer units,
+// cells that divide the unit, at most lofk_integ_max_time() cells) and the
+// SIR pass (the mask output, rows up to lofk_sir_max_time() samples).
 int host_validate_options(const lof_params& P, int dtype, const lof_unit& u, int i, char* why, int nwhy) {
-  if (exact_stats_mode(P) >= 0) {
-    const char* what = P.time_mode == LOF_TIME_INTEGRATED       ? "the integrated time mode"
-                       : P.stats_scope == LOF_SCOPE_CHANNEL     ? "the per-channel statistics scope"
-                                                                : "the winsorized sigma estimator";
-    if (is_float(dtype)) return snprintf(why, nwhy, "%s takes integer units only", what), LOF_ERR_INVALID;
-    if (u.n_time > lofk_integ_max_time())
-      return snprintf(why, nwhy, "unit %d: n_time %d above the limit %d of %s", i, u.n_time,
-                      lofk_integ_max_time(), what),
+  const int xm = exact_stats_mode(P);
+  const char* what = xm == 3   ? "the two-dimensional mode"
+                     : xm == 0 ? "the integrated time mode"
+                     : xm == 1 ? "the per-channel statistics scope"
+                               : "the winsorized sigma estimator";
+  if (xm >= 0 && is_float(dtype))
+    return snprintf(why, nwhy, "%s takes integer units only", what), LOF_ERR_INVALID;
+  if (xm == 3) {
+    if (u.n_chan % P.integ_chan || u.n_time % P.integ_time)
+      return snprintf(why, nwhy, "unit %d: %d x %d cells do not divide %d x %d samples", i, P.integ_chan,
+                      P.integ_time, u.n_chan, u.n_time),
              LOF_ERR_INVALID;
+    const int64_t cells = static_cast<int64_t>(u.n_chan / P.integ_chan) * (u.n_time / P.integ_time);
+    if (cells > lofk_integ_max_time())
+      return snprintf(why, nwhy, "unit %d: %lld cells above the two-dimensional limit %d", i,
+                      static_cast<long long>(cells), lofk_integ_max_time()),
+             LOF_ERR_INVALID;
+  } else if (xm >= 0 && u.n_time > lofk_integ_max_time()) {
+    return snprintf(why, nwhy, "unit %d: n_time %d above the limit %d of %s", i, u.n_time,
+                    lofk_integ_max_time(), what),
+           LOF_ERR_INVALID;
   }
   if (P.sir_percent <= 0) return LOF_OK;
   if (!u.mask)
@@ -1106,7 +1130,8 @@ struct lof_graph {
   cudaGraphNode_t knode = nullptr;
   cudaKernelNodeParams kparams{};
   lofk::KParams kp{};  // argument storage for parameter updates
-  void* kargs[1] = {nullptr};
+  int2 cells{1, 1};    // second argument of the exact-statistics kernel
+  void* kargs[2] = {nullptr, nullptr};
 };
 
 namespace {
@@ -1186,6 +1211,9 @@ int graph_capture(lof_graph* g, const lofk::HostCfg& h, const lofk::Prep& pr, in
     g->knode = nodes[i];
     cudaGraphKernelNodeGetParams(nodes[i], &g->kparams);
     std::memcpy(&g->kp, g->kparams.kernelParams[0], sizeof(lofk::KParams));
+    // the exact-statistics kernel takes (KParams, int2 cells); the others KParams alone
+    if (lofk::exact_stats_mode(g->ctx->params) >= 0)
+      std::memcpy(&g->cells, g->kparams.kernelParams[1], sizeof(int2));
   }
   if (!g->knode) return snprintf(why, nwhy, "no kernel node in the captured graph"), LOF_ERR_CUDA;
   e = cudaGraphInstantiate(&g->exec, g->graph, 0);
@@ -1277,6 +1305,7 @@ extern "C" int lof_graph_launch(lof_graph* g, uint64_t block_seq, void* cuda_str
   g->kp.block_seq = block_seq;
   cudaKernelNodeParams p = g->kparams;
   g->kargs[0] = &g->kp;
+  g->kargs[1] = &g->cells;  // read only by a kernel with a second parameter
   p.kernelParams = g->kargs;
   cudaError_t e = cudaGraphExecKernelNodeSetParams(g->exec, g->knode, &p);
   if (e != cudaSuccess) return cuda_fail(c, e, "lof_graph_launch: parameter update");

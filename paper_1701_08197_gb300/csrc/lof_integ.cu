@@ -7,7 +7,9 @@
 //      time pass with the median and sigma of its own powers;
 //   2  the pooled per-channel time pass with statistics selected exactly from
 //      the unit in global memory (the winsorized estimator, which the
-//      histogram statistics of the block kernel do not provide).
+//      histogram statistics of the block kernel do not provide);
+//   3  the two-dimensional mode (time_mode = 2): SumThreshold on cells of
+//      summed powers, along time and then along frequency for each window.
 // Every mode supports the three sigma estimators (MAD, stddev, winsorized).
 // The integrated mode, step by step:
 //   a1  powers re^2 + im^2 (exact integers)
@@ -739,14 +741,180 @@ __device__ void chan_unit(const KParams& kp, const DevUnit& u, uint8_t* smem, In
   __syncthreads();
 }
 
+
+// One window size of Section 2.1 along n_lines lines of L cells of the grid V
+// (line r starts at cell r * line_stride, its cells step apart), flags in fl
+// and next as scratch (whole CTA): every window is judged against the flags
+// on entry and fires when the sum of its unflagged cells exceeds
+// (I - n) * thr.  Cell sums are at most 2^16 powers of at most 2^31, so a
+// window sum is at most 2^53: exact in 64-bit integers and in binary64.
+__device__ void st_grid_lines(const unsigned long long* V, uint8_t* fl, uint8_t* next, int NG, int n_lines,
+                              int L, int step, int line_stride, int I, double thr) {
+  for (int i = threadIdx.x; i < NG; i += kNtI) next[i] = fl[i];
+  __syncthreads();
+  const int nw = L - I + 1, total = n_lines * nw;
+  for (int w = threadIdx.x; w < total; w += kNtI) {
+    const int r = w / nw, t = w - r * nw;
+    const int b = r * line_stride + t * step;
+    int nf = 0;
+    unsigned long long su = 0;
+    for (int j = 0; j < I; ++j) {
+      const int i = b + j * step;
+      if (fl[i]) ++nf;
+      else su += V[i];
+    }
+    if (__ull2double_rn(su) > __dmul_rn(static_cast<double>(I - nf), thr))
+      for (int j = 0; j < I; ++j) next[b + j * step] = 1;
+  }
+  __syncthreads();
+  for (int i = threadIdx.x; i < NG; i += kNtI) fl[i] = next[i];
+  __syncthreads();
+}
+
+// The two-dimensional mode (time_mode = 2): powers summed into cells of Fi
+// channels x Ti samples (Fi divides C, Ti divides T, at most kIntegMaxT
+// cells), one median and sigma over the cells, then for I = 1, 2, 4, ...
+// SumThreshold along time on every row of cells and then along frequency on
+// every column (enable_time / enable_freq); a flagged cell flags its samples.
+// No separate frequency pass; the history test and the output per channel as
+// in the other modes.
+template <int DT>
+__device__ void grid_unit(const KParams& kp, const DevUnit& u, uint8_t* smem, IntegShared& f, int Fi, int Ti) {
+  constexpr int ES = DT == LOF_CI16 ? 4 : 2;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int C = u.C, T = u.T;
+  // the host validates the cells; a launch with others reports an error and
+  // touches nothing
+  if (Fi < 1 || Ti < 1 || C % Fi || T % Ti || static_cast<long long>(C / Fi) * (T / Ti) > kIntegMaxT) {
+    if (tid == 0 && atomicCAS(kp.err, 0, kErrInternal) == 0) {
+      kp.err_info[0] = 800;
+      kp.err_info[1] = static_cast<int>(kp.block_seq);
+    }
+    return;
+  }
+  const int Cg = C / Fi, Tg = T / Ti, NG = Cg * Tg;
+  unsigned long long* V = reinterpret_cast<unsigned long long*>(smem + kOffG);
+  uint32_t* hist = reinterpret_cast<uint32_t*>(smem + kOffHist);
+  uint8_t* Fg = smem + kOffFt;
+  uint8_t* Fn = smem + kOffFn;
+  const uint8_t* gin = static_cast<const uint8_t*>(u.in);
+  const bool vin = (u.flags & kUnitInVec) != 0;
+  const bool inplace = (u.flags & kUnitInPlace) != 0;
+  for (int i = tid; i < NG; i += kNtI) {
+    V[i] = 0ull;
+    Fg[i] = 0;
+  }
+  if (tid == 0) f.cnt_time = f.cnt_total = f.cnt_hist = 0ull;
+  __syncthreads();
+  for (int c = warp; c < C; c += kNwI) {
+    const uint8_t* row = gin + static_cast<int64_t>(c) * u.in_stride * ES;
+    unsigned long long* vr = V + (c / Fi) * Tg;
+    row_powers<DT>(row, T, vin, [&](int t, uint32_t p) {
+      atomicAdd(&vr[t / Ti], static_cast<unsigned long long>(p));
+    });
+  }
+  __syncthreads();
+  double med = 0.0, sig = 0.0;
+  stats_u64(kp, NG, [&](long long i) { return V[i]; }, hist, f, &med, &sig);
+  if (sig > 0.0) {
+    for (int k = 0;; ++k) {
+      const int I = 1 << k;
+      if (I > (1 << kp.max_log_window) || (I > Tg && I > Cg)) break;
+      const double thr = thr_i(kp, med, sig, k);
+      if (kp.enable_time && I <= Tg) st_grid_lines(V, Fg, Fn, NG, Cg, Tg, 1, Tg, I, thr);
+      if (kp.enable_freq && I <= Cg) st_grid_lines(V, Fg, Fn, NG, Tg, Cg, Tg, 1, I, thr);
+    }
+  }
+  // per channel: the history test on the unflagged samples, mask and data
+  for (int c = warp; c < C; c += kNwI) {
+    const uint8_t* row = gin + static_cast<int64_t>(c) * u.in_stride * ES;
+    const uint8_t* fr = Fg + (c / Fi) * Tg;
+    const long long h = u.hist_slot >= 0 ? u.hist_slot + c : -1;
+    uint8_t* mr = u.mask ? u.mask + static_cast<int64_t>(c) * u.mask_stride : nullptr;
+    uint8_t* orow = u.out ? static_cast<uint8_t*>(u.out) + static_cast<int64_t>(c) * u.out_stride * ES : nullptr;
+    auto put = [&](int t, bool fl) {
+      if (mr) mr[t] = fl ? 1 : 0;
+      if (orow) {
+        if (ES == 4) {
+          if (fl) reinterpret_cast<uint32_t*>(orow)[t] = 0u;
+          else if (!inplace) reinterpret_cast<uint32_t*>(orow)[t] = reinterpret_cast<const uint32_t*>(row)[t];
+        } else {
+          if (fl) reinterpret_cast<uint16_t*>(orow)[t] = 0;
+          else if (!inplace) reinterpret_cast<uint16_t*>(orow)[t] = reinterpret_cast<const uint16_t*>(row)[t];
+        }
+      }
+    };
+    unsigned long long s = 0;
+    int n = 0;
+    for (int t = lane; t < T; t += 32) {
+      const bool fl = fr[t / Ti] != 0;
+      if (!fl) {
+        s += ipow<DT>(row, t);
+        ++n;
+      }
+      put(t, fl);
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      s += __shfl_xor_sync(kFullI, s, o);
+      n += __shfl_xor_sync(kFullI, n, o);
+    }
+    bool fh = false;
+    if (lane == 0) {
+      if (n > 0) {
+        const double cur = __ddiv_rn(static_cast<double>(s), static_cast<double>(n));
+        double staged = cur;
+        if (kp.enable_history && h >= 0) {
+          const int cnt = kp.hist.count[h];
+          if (cnt >= kp.history_min && cnt > 0) {
+            const double thr = kp.hist.thr[h];
+            if (!(cur < thr)) {
+              fh = true;
+              staged = thr;
+            }
+          }
+        }
+        if (h >= 0) {
+          kp.hist.pend[h] = staged;
+          kp.hist.pend_flag[h] = 1;
+          kp.hist.pend_seq[h] = kp.block_seq;
+        }
+      } else if (h >= 0) {
+        kp.hist.pend_flag[h] = 0;
+      }
+      atomicAdd(&f.cnt_time, static_cast<unsigned long long>(T - n));
+      if (fh) atomicAdd(&f.cnt_hist, 1ull);
+      atomicAdd(&f.cnt_total, fh ? static_cast<unsigned long long>(T) : static_cast<unsigned long long>(T - n));
+    }
+    const bool full = __shfl_sync(kFullI, fh ? 1 : 0, 0) != 0;
+    __syncwarp();  // the row's first writes, by every lane, before a rewrite
+    if (full)
+      for (int t = lane; t < T; t += 32) put(t, true);
+  }
+  __syncthreads();
+  if (tid == 0 && u.stats) {
+    u.stats->median_f = 0.0;
+    u.stats->sigma_f = 0.0;
+    u.stats->median_t = med;
+    u.stats->sigma_t = sig;
+    u.stats->n_chan_freq = 0;
+    u.stats->n_flag_time = static_cast<long long>(f.cnt_time);
+    u.stats->n_chan_hist = static_cast<long long>(f.cnt_hist);
+    u.stats->n_flag_total = static_cast<long long>(f.cnt_total);
+  }
+  __syncthreads();
+}
+
 // MODE 0: integrated time mode; MODE 1: per-channel statistics scope; MODE 2:
-// pooled per-channel time pass.
+// pooled per-channel time pass; MODE 3: two-dimensional mode on cells of
+// cells.x channels x cells.y samples (the other modes ignore cells).
 template <int DT, int MODE>
-__global__ void __launch_bounds__(kNtI, 1) lof_integ_kernel(const KParams kp) {
+__global__ void __launch_bounds__(kNtI, 1) lof_integ_kernel(const KParams kp, const int2 cells) {
   extern __shared__ __align__(16) uint8_t smem[];
   __shared__ IntegShared f;
   for (int ui = blockIdx.x; ui < kp.n_units; ui += gridDim.x) {
     if constexpr (MODE == 0) integ_unit<DT>(kp, kp.units[ui], smem, f);
+    else if constexpr (MODE == 3) grid_unit<DT>(kp, kp.units[ui], smem, f, cells.x, cells.y);
     else chan_unit<DT, MODE == 2>(kp, kp.units[ui], smem, f);
   }
 }
@@ -756,25 +924,30 @@ __global__ void __launch_bounds__(kNtI, 1) lof_integ_kernel(const KParams kp) {
 
 extern "C" int lofk_integ_max_time() { return lofk::kIntegMaxT; }
 
-// The integrated time mode (mode 0), the per-channel statistics scope (mode 1)
-// or the pooled per-channel pass with exact statistics (mode 2) over n_units
-// integer units (one CTA per unit).
+// The integrated time mode (mode 0), the per-channel statistics scope (mode 1),
+// the pooled per-channel pass with exact statistics (mode 2) or the
+// two-dimensional mode on cells of cell_chan x cell_time samples (mode 3)
+// over n_units integer units (one CTA per unit).  The kernel's arguments are
+// (KParams, int2 cells).
 extern "C" int lofk_launch_integ(int dtype, const lofk::KParams* kp, int n_units, int n_sm, void* stream,
-                                 int mode) {
+                                 int mode, int cell_chan, int cell_time) {
   using namespace lofk;
   if (n_units <= 0) return 0;
-  if (mode < 0 || mode > 2) return static_cast<int>(cudaErrorInvalidValue);
-  const void* ks[2][3] = {{reinterpret_cast<const void*>(&lof_integ_kernel<LOF_CI16, 0>),
+  if (mode < 0 || mode > 3 || cell_chan < 1 || cell_time < 1) return static_cast<int>(cudaErrorInvalidValue);
+  const void* ks[2][4] = {{reinterpret_cast<const void*>(&lof_integ_kernel<LOF_CI16, 0>),
                            reinterpret_cast<const void*>(&lof_integ_kernel<LOF_CI16, 1>),
-                           reinterpret_cast<const void*>(&lof_integ_kernel<LOF_CI16, 2>)},
+                           reinterpret_cast<const void*>(&lof_integ_kernel<LOF_CI16, 2>),
+                           reinterpret_cast<const void*>(&lof_integ_kernel<LOF_CI16, 3>)},
                           {reinterpret_cast<const void*>(&lof_integ_kernel<LOF_CI8, 0>),
                            reinterpret_cast<const void*>(&lof_integ_kernel<LOF_CI8, 1>),
-                           reinterpret_cast<const void*>(&lof_integ_kernel<LOF_CI8, 2>)}};
+                           reinterpret_cast<const void*>(&lof_integ_kernel<LOF_CI8, 2>),
+                           reinterpret_cast<const void*>(&lof_integ_kernel<LOF_CI8, 3>)}};
   const void* k = ks[dtype == LOF_CI16 ? 0 : 1][mode];
   if (cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, kIntegSmem) != cudaSuccess)
     return -2;
   const int grid = n_units < n_sm ? n_units : n_sm;
-  void* args[] = {const_cast<KParams*>(kp)};
+  int2 cells = make_int2(cell_chan, cell_time);
+  void* args[] = {const_cast<KParams*>(kp), &cells};
   const cudaError_t e = cudaLaunchKernel(k, dim3(grid), dim3(kNtI), args, static_cast<size_t>(kIntegSmem),
                                          static_cast<cudaStream_t>(stream));
   return e == cudaSuccess ? 0 : static_cast<int>(e);

@@ -21,7 +21,7 @@ LOF_ERR_STATE = -5
 LOF_ERR_UNSUPPORTED = -6
 LOF_CI8, LOF_CI16, LOF_F32, LOF_CF32 = 1, 2, 3, 4
 LOF_SIGMA_MAD, LOF_SIGMA_STD, LOF_SIGMA_WINSOR = 0, 1, 2
-LOF_TIME_PER_CHANNEL, LOF_TIME_INTEGRATED = 0, 1
+LOF_TIME_PER_CHANNEL, LOF_TIME_INTEGRATED, LOF_TIME_2D = 0, 1, 2
 LOF_SCOPE_POOLED, LOF_SCOPE_CHANNEL = 0, 1
 
 EXPORTED = [
@@ -49,6 +49,8 @@ class lof_params(ctypes.Structure):
         ("sir_percent", ctypes.c_int32),
         ("time_mode", ctypes.c_int32),
         ("stats_scope", ctypes.c_int32),
+        ("integ_chan", ctypes.c_int32),
+        ("integ_time", ctypes.c_int32),
     ]
 
 

@@ -27,11 +27,13 @@ def test_library_exports_every_declared_symbol():
 
 def test_struct_sizes_match_header_layout():
     # lof_params: 3 doubles, 3 ints (+pad), double, 4 ints
-    # ... + sir_percent, time_mode and stats_scope (int32, padded to 8)
-    assert ctypes.sizeof(lof.lof_params) == 3 * 8 + 4 * 4 + 8 + 4 * 4 + 4 + 4 + 4 + 4
+    # ... + sir_percent, time_mode, stats_scope, integ_chan, integ_time (int32, padded to 8)
+    assert ctypes.sizeof(lof.lof_params) == 3 * 8 + 4 * 4 + 8 + 4 * 4 + 5 * 4 + 4
     assert lof.lof_params.sir_percent.offset == 64
     assert lof.lof_params.time_mode.offset == 68
     assert lof.lof_params.stats_scope.offset == 72
+    assert lof.lof_params.integ_chan.offset == 76
+    assert lof.lof_params.integ_time.offset == 80
     assert ctypes.sizeof(lof.lof_unit) == 3 * 8 + 2 * 4 + 4 * 8 + 8
     assert ctypes.sizeof(lof.lof_unit_stats) == 8 * 8
 

@@ -1,6 +1,7 @@
 """The graph form (lof_graph_*) replays exactly what lof_flag_block computes,
 for every kernel family: the float path (Stokes I and visibilities), the
-integrated time mode and the SIR pass."""
+exact-statistics kernel (integrated time mode, two-dimensional mode, pooled
+winsorized statistics; it takes a second argument) and the SIR pass."""
 import numpy as np
 import pytest
 import torch
@@ -32,7 +33,7 @@ def _both(dtype, xs, **params):
     return res
 
 
-@pytest.mark.parametrize("case", ["f32", "cf32", "integrated", "sir"])
+@pytest.mark.parametrize("case", ["f32", "cf32", "integrated", "2d", "winsor", "sir"])
 def test_graph_replay_equals_flag_block(case):
     rng = np.random.default_rng(3)
     if case == "f32":
@@ -48,7 +49,10 @@ def test_graph_replay_equals_flag_block(case):
         spec = synth.VoltageSpec(C=128, T=1536, sigma=32.0, n_tones=2, n_impulses=3)
         xs = [synth.voltage_block(spec, seed=s, block=0, device=DEV)[0, 0, 0].contiguous() for s in (1, 2)]
         dtype = lof.LOF_CI16
-        params = {"time_mode": lof.LOF_TIME_INTEGRATED} if case == "integrated" else {"sir_percent": 20}
+        params = {"integrated": {"time_mode": lof.LOF_TIME_INTEGRATED},
+                  "2d": {"time_mode": lof.LOF_TIME_2D, "integ_chan": 4, "integ_time": 8},
+                  "winsor": {"sigma_estimator": lof.LOF_SIGMA_WINSOR},
+                  "sir": {"sir_percent": 20}}[case]
     (m0, o0, s0), (m1, o1, s1) = _both(dtype, xs, **params)
     for a, b in zip(m0, m1):
         assert torch.equal(a, b)
