@@ -15,6 +15,13 @@ fraction of the flag kernel, the oracle timed on the host cores
 plain form (one launch per station-subband), clocks during the timed region.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+
+Options of the method, each timed on the same block (the oracle legs take
+them too): --sir P (Section 2.2 SIR operator), --integrated (Section 3
+integrated time flagging), --channel-scope (per-channel time-pass
+statistics), --sigma {mad,std,winsor} (Section 4.2 estimators), --grid FxT
+(two-dimensional SumThreshold on F x T cells).  The launch shape is the
+library default unless --autotune.
 """
 from __future__ import annotations
 
