@@ -146,10 +146,12 @@ typedef struct {
 /* Per-unit results, written by lof_flag_block when lof_unit.stats != NULL
  * (device memory).  Medians and sigmas are the values the thresholds used. */
 typedef struct {
-  double median_f, sigma_f; /* spectrum statistics (a3) */
-  double median_t, sigma_t; /* pooled statistics of the time pass (a5) */
+  double median_f, sigma_f; /* spectrum statistics (a3); 0 in LOF_TIME_2D */
+  double median_t, sigma_t; /* pooled statistics of the time pass (a5); those of the
+                               integrated series (LOF_TIME_INTEGRATED), of the cells
+                               (LOF_TIME_2D); 0 with LOF_SCOPE_CHANNEL */
   int64_t n_chan_freq;      /* channels flagged by the frequency pass */
-  int64_t n_flag_time;      /* samples flagged by the time pass */
+  int64_t n_flag_time;      /* samples flagged by the time pass (the 2-D pass in LOF_TIME_2D) */
   int64_t n_chan_hist;      /* channels flagged by the history flagger */
   int64_t n_flag_total;     /* ones in the mask */
 } lof_unit_stats;
