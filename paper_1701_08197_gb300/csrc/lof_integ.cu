@@ -356,6 +356,37 @@ __device__ void st_1d(const KParams& kp, V v, int L, double med, double sig, uin
   }
 }
 
+// Section 4.1 history test of one channel (one thread): cur = the mean of its
+// n unflagged powers (sum s, exact); once the ring holds history_min means the
+// channel is flagged unless cur is below the cached mean + k * stddev.  The
+// value the commit will append (cur, or the threshold when flagged) is staged;
+// a channel with no unflagged sample stages nothing.  Returns the flag.
+__device__ bool stage_history(const KParams& kp, long long h, unsigned long long s, int n) {
+  bool fh = false;
+  if (n > 0) {
+    const double cur = __ddiv_rn(static_cast<double>(s), static_cast<double>(n));
+    double staged = cur;
+    if (kp.enable_history && h >= 0) {
+      const int cnt = kp.hist.count[h];
+      if (cnt >= kp.history_min && cnt > 0) {
+        const double thr = kp.hist.thr[h];
+        if (!(cur < thr)) {
+          fh = true;
+          staged = thr;
+        }
+      }
+    }
+    if (h >= 0) {
+      kp.hist.pend[h] = staged;
+      kp.hist.pend_flag[h] = 1;
+      kp.hist.pend_seq[h] = kp.block_seq;
+    }
+  } else if (h >= 0) {
+    kp.hist.pend_flag[h] = 0;
+  }
+  return fh;
+}
+
 // a3, a4 for a unit whose row sums are in S: exact median and sigma of the
 // spectrum (bitonic sort of the C sums, deviations as |2x - m2|) and the
 // frequency SumThreshold -> Fc (whole CTA).
@@ -532,27 +563,7 @@ __device__ void integ_unit(const KParams& kp, const DevUnit& u, uint8_t* smem, I
       }
       bool fh = false;
       if (lane == 0) {
-        if (n > 0) {
-          const double cur = __ddiv_rn(static_cast<double>(s), static_cast<double>(n));
-          double staged = cur;
-          if (kp.enable_history && h >= 0) {
-            const int cnt = kp.hist.count[h];
-            if (cnt >= kp.history_min && cnt > 0) {
-              const double thr = kp.hist.thr[h];
-              if (!(cur < thr)) {
-                fh = true;
-                staged = thr;
-              }
-            }
-          }
-          if (h >= 0) {
-            kp.hist.pend[h] = staged;
-            kp.hist.pend_flag[h] = 1;
-            kp.hist.pend_seq[h] = kp.block_seq;
-          }
-        } else if (h >= 0) {
-          kp.hist.pend_flag[h] = 0;
-        }
+        fh = stage_history(kp, h, s, n);
         atomicAdd(&f.cnt_time, static_cast<unsigned long long>(T - n));
         if (fh) atomicAdd(&f.cnt_hist, 1ull);
         atomicAdd(&f.cnt_total, fh ? static_cast<unsigned long long>(T) : static_cast<unsigned long long>(T - n));
@@ -680,28 +691,7 @@ __device__ void chan_unit(const KParams& kp, const DevUnit& u, uint8_t* smem, In
           st += f.rs[w];
           nt += f.rn[w];
         }
-        bool fh = false;
-        if (nt > 0) {
-          const double cur = __ddiv_rn(static_cast<double>(st), static_cast<double>(nt));
-          double staged = cur;
-          if (kp.enable_history && h >= 0) {
-            const int cnt = kp.hist.count[h];
-            if (cnt >= kp.history_min && cnt > 0) {
-              const double thr = kp.hist.thr[h];
-              if (!(cur < thr)) {
-                fh = true;
-                staged = thr;
-              }
-            }
-          }
-          if (h >= 0) {
-            kp.hist.pend[h] = staged;
-            kp.hist.pend_flag[h] = 1;
-            kp.hist.pend_seq[h] = kp.block_seq;
-          }
-        } else if (h >= 0) {
-          kp.hist.pend_flag[h] = 0;
-        }
+        const bool fh = stage_history(kp, h, st, nt);
         f.cnt_time += static_cast<unsigned long long>(T - nt);
         if (fh) f.cnt_hist += 1ull;
         f.cnt_total += fh ? static_cast<unsigned long long>(T) : static_cast<unsigned long long>(T - nt);
@@ -861,27 +851,7 @@ __device__ void grid_unit(const KParams& kp, const DevUnit& u, uint8_t* smem, In
     }
     bool fh = false;
     if (lane == 0) {
-      if (n > 0) {
-        const double cur = __ddiv_rn(static_cast<double>(s), static_cast<double>(n));
-        double staged = cur;
-        if (kp.enable_history && h >= 0) {
-          const int cnt = kp.hist.count[h];
-          if (cnt >= kp.history_min && cnt > 0) {
-            const double thr = kp.hist.thr[h];
-            if (!(cur < thr)) {
-              fh = true;
-              staged = thr;
-            }
-          }
-        }
-        if (h >= 0) {
-          kp.hist.pend[h] = staged;
-          kp.hist.pend_flag[h] = 1;
-          kp.hist.pend_seq[h] = kp.block_seq;
-        }
-      } else if (h >= 0) {
-        kp.hist.pend_flag[h] = 0;
-      }
+      fh = stage_history(kp, h, s, n);
       atomicAdd(&f.cnt_time, static_cast<unsigned long long>(T - n));
       if (fh) atomicAdd(&f.cnt_hist, 1ull);
       atomicAdd(&f.cnt_total, fh ? static_cast<unsigned long long>(T) : static_cast<unsigned long long>(T - n));
