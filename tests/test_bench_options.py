@@ -1,0 +1,54 @@
+"""The benchmark's host logic on CPU: option plumbing into the workload
+description, the two-dimensional cell parser, the traffic lookup's shape check
+and the oracle arm's JSON line with method options."""
+import json
+import os
+import subprocess
+import sys
+
+import pytest
+
+import bench
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def test_grid_cells_parse():
+    assert bench.grid_cells(None) is None
+    assert bench.grid_cells("4x16") == (4, 16)
+    assert bench.grid_cells("1X32") == (1, 32)
+
+
+def test_workload_config_names_every_option():
+    c = bench.workload_config(48)
+    assert "768 units x 256 ch x 3072 t" in c["workload"]
+    assert not {"sir_percent", "time_mode", "stats_scope", "sigma_estimator"} & set(c)
+    c = bench.workload_config(4, sir=20, scope=True, sigma="winsor")
+    assert c["sir_percent"] == 20 and c["stats_scope"] == "per channel"
+    assert c["sigma_estimator"] == "winsor" and c["per_rank_units"] == 64
+    assert "integrated" in bench.workload_config(48, integrated=True)["time_mode"]
+    assert "4 x 16" in bench.workload_config(48, grid="4x16")["time_mode"]
+
+
+def test_traffic_only_for_the_profiled_shape():
+    default = dict(threads=256, ctas_per_sm=2, tile_bytes=0, fine_bins=2048, flag_rows=64,
+                   stat_samples=262144)
+    t = bench.measured_traffic(768, default)
+    other = bench.measured_traffic(768, dict(default, flag_rows=32))
+    assert other is None
+    if t is not None:                     # the kernel sources still match the recorded hashes
+        assert t == 768 * bench.measured_traffic(1, default)
+
+
+def test_reference_arm_with_options():
+    out = subprocess.run([sys.executable, os.path.join(ROOT, "bench.py"), "--impl", "reference",
+                          "--steps", "1", "--warmup", "0", "--cpu-seconds", "0.5",
+                          "--grid", "4x16", "--sigma", "winsor"],
+                         capture_output=True, text=True, timeout=300, cwd=ROOT)
+    assert out.returncode == 0, out.stderr[-2000:]
+    line = json.loads(out.stdout.strip().splitlines()[-1])
+    assert line["impl"] == "reference" and line["value"] > 0
+    assert line["config"]["sigma_estimator"] == "winsor"
+    assert "4 x 16" in line["config"]["time_mode"]
+    assert line["cpu_baseline"]["kind"] == "oracle" and line["cpu_baseline"]["cores"] >= 1
+    assert line["e2e"]["h2d_bytes_per_step"] == 0 and line["e2e"]["value"] == line["value"]
