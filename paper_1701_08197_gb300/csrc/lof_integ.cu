@@ -1,5 +1,5 @@
 // lof_integ.cu -- exact-statistics unit kernel for integer voltage units, one
-// CTA per unit, in three modes:
+// CTA per unit, in four modes:
 //   0  the integrated time mode (lof_params.time_mode = 1): Section 3 sums
 //      the time axis away for frequency flagging and the frequency axis away
 //      for time-domain flagging (steps a1-a8 below);
@@ -23,7 +23,8 @@
 //       samples, exact integer sum)
 //   a8  mask and masked data
 // Sums of integer powers are exact in binary64 here (G <= 2048 * 2^31 and
-// window sums < 2^53), so the decisions equal those of the binary64 oracle.
+// window sums <= 2^53; the kernel adds them in 64-bit integers and converts
+// once), so the decisions equal those of the binary64 oracle.
 #include <cstdint>
 
 #include <cuda_runtime.h>
