@@ -135,6 +135,30 @@ def measured_peak_hbm():
         return 6800.0, "fallback"
 
 
+NOMINAL_HBM_GBS = 7900.0   # GB300 HBM3e, nominal
+
+
+def timed_kernel_name(args) -> str:
+    """The flag kernel a bench configuration times (plus the SIR pass)."""
+    name = ("lof_integ_kernel<CI16, two-dimensional>" if args.grid
+            else "lof_integ_kernel<CI16, integrated>" if args.integrated
+            else "lof_integ_kernel<CI16, channel scope>" if args.channel_scope
+            else "lof_integ_kernel<CI16, pooled exact>" if args.sigma == "winsor"
+            else "lof_block_kernel<CI16>")
+    return name + (" + SIR" if args.sir else "")
+
+
+def roofline_entry(alg_bytes: float, kernel_ms: float, peak: float, peak_kind: str, traffic, kernel: str):
+    """The roofline object: algorithmic bytes per launch over the kernel's
+    average CUDA-event time, against the measured copy peak (frac) and the
+    nominal HBM bandwidth (frac_nominal)."""
+    achieved = alg_bytes / (kernel_ms * 1e-3) / 1e9
+    return {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+            "frac": achieved / peak, "traffic": traffic, "kernel": kernel,
+            "bytes_per_launch": alg_bytes, "kernel_ms": kernel_ms, "peak_kind": peak_kind,
+            "nominal_peak": NOMINAL_HBM_GBS, "frac_nominal": achieved / NOMINAL_HBM_GBS}
+
+
 class ClockSampler:
     """nvidia-smi clocks and throttle reasons sampled during the timed region."""
 
@@ -480,7 +504,6 @@ def main():
     samples = res["samples"]
     kern_avg = statistics.mean(res["kern_ms"])
     alg_bytes = samples * BYTES_PER_SAMPLE
-    achieved = alg_bytes / (kern_avg * 1e-3) / 1e9
     step_sorted = sorted(res["step_ms"])
 
     def pct(a, q):
@@ -493,20 +516,12 @@ def main():
         "data": "synthetic (seeded noise + tones + impulses)",
         "config": dict(workload_config(args.stations, args.sir, args.integrated, args.channel_scope, args.sigma,
                                     args.grid), tuning=res["tuning"]),
-        "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                     "frac": achieved / peak,
-                     # the recorded counters are those of the block kernel alone
-                     "traffic": None if (args.integrated or args.channel_scope or args.sir
-                                         or args.sigma == "winsor" or args.grid)
-                     else measured_traffic(args.stations * 16, res["tuning"]),
-                     "kernel": ("lof_integ_kernel<CI16, two-dimensional>" if args.grid
-                                else "lof_integ_kernel<CI16, integrated>" if args.integrated
-                                else "lof_integ_kernel<CI16, channel scope>" if args.channel_scope
-                                else "lof_integ_kernel<CI16, pooled exact>" if args.sigma == "winsor"
-                                else "lof_block_kernel<CI16>")
-                               + (" + SIR" if args.sir else ""),
-                     "bytes_per_launch": alg_bytes,
-                     "kernel_ms": kern_avg, "peak_kind": peak_kind},
+        "roofline": roofline_entry(
+            alg_bytes, kern_avg, peak, peak_kind,
+            # the recorded counters are those of the block kernel alone
+            None if (args.integrated or args.channel_scope or args.sir or args.sigma == "winsor"
+                     or args.grid) else measured_traffic(args.stations * 16, res["tuning"]),
+            timed_kernel_name(args)),
         "latency_ms": {"batched_p50": pct(step_sorted, 0.5), "batched_p99": pct(step_sorted, 0.99),
                        "deadline_ms": T * 1.31072},
         "clocks": res["clocks"],

@@ -40,6 +40,24 @@ def test_traffic_only_for_the_profiled_shape():
         assert t == 768 * bench.measured_traffic(1, default)
 
 
+def test_roofline_entry():
+    r = bench.roofline_entry(5.4358e9, 4.4, 6775.3, "measured", 7.0e9, "lof_block_kernel<CI16>")
+    assert r["achieved"] == pytest.approx(5.4358e9 / 4.4e-3 / 1e9)
+    assert r["frac"] == pytest.approx(r["achieved"] / 6775.3)
+    assert r["frac_nominal"] == pytest.approx(r["achieved"] / 7900.0)
+    assert {"bound", "achieved", "peak", "unit", "frac", "traffic"} <= set(r)
+    assert r["bound"] == "hbm" and r["unit"] == "GB/s" and r["traffic"] == 7.0e9
+
+
+def test_timed_kernel_names():
+    import argparse
+    a = argparse.Namespace(grid=None, integrated=False, channel_scope=False, sigma="mad", sir=0)
+    assert bench.timed_kernel_name(a) == "lof_block_kernel<CI16>"
+    assert bench.timed_kernel_name(argparse.Namespace(**dict(vars(a), sir=20))).endswith("+ SIR")
+    assert "two-dimensional" in bench.timed_kernel_name(argparse.Namespace(**dict(vars(a), grid="4x16")))
+    assert "pooled exact" in bench.timed_kernel_name(argparse.Namespace(**dict(vars(a), sigma="winsor")))
+
+
 def test_reference_arm_with_options():
     out = subprocess.run([sys.executable, os.path.join(ROOT, "bench.py"), "--impl", "reference",
                           "--steps", "1", "--warmup", "0", "--cpu-seconds", "0.5",
