@@ -70,3 +70,35 @@ def test_reference_arm_with_options():
     assert "4 x 16" in line["config"]["time_mode"]
     assert line["cpu_baseline"]["kind"] == "oracle" and line["cpu_baseline"]["cores"] >= 1
     assert line["e2e"]["h2d_bytes_per_step"] == 0 and line["e2e"]["value"] == line["value"]
+
+
+def test_gpu_line_assembly_with_a_fake_run(monkeypatch, capsys):
+    # main()'s JSON line from a stand-in for run_gpu's timings: every key of
+    # the contract present, the roofline built from the kernel time
+    res = {"rank": 0, "value": 133000.0, "ms_per_step": 4.5, "step_ms": [4.5, 4.6, 4.4],
+           "kern_ms": [4.4, 4.4, 4.4], "clocks": {"sm_mhz": 2070.0, "sm_max_mhz": 2070.0, "reasons": []},
+           "samples": 768 * 256 * 3072, "plain_ms": [120.0, 119.0, 121.0],
+           "tuning": dict(threads=256, ctas_per_sm=2, tile_bytes=0, fine_bins=2048, flag_rows=64,
+                          stat_samples=262144),
+           "e2e": {"value": 16000.0, "unit": "Msamples/s", "h2d_bytes_per_step": 1,
+                   "d2h_bytes_per_step": 1}}
+    monkeypatch.setattr(bench, "run_gpu", lambda args: res)
+    for k in ("RANK", "WORLD_SIZE", "LOCAL_RANK"):
+        monkeypatch.delenv(k, raising=False)
+    for extra, kernel in (([], "lof_block_kernel<CI16>"), (["--grid", "4x16"], "two-dimensional")):
+        monkeypatch.setattr(sys, "argv", ["bench.py", "--steps", "3", "--warmup", "3", "--no-cpu"] + extra)
+        bench.main()
+        line = json.loads(capsys.readouterr().out.strip().splitlines()[-1])
+        for k in ("metric", "value", "unit", "n_gpus", "steps", "warmup", "ms_per_step", "higher_is_better",
+                  "scaling", "vs_baseline", "dtype", "data", "config", "roofline", "clocks", "e2e",
+                  "gpu_launches", "latency_ms"):
+            assert k in line, k
+        r = line["roofline"]
+        assert r["kernel_ms"] == pytest.approx(4.4) and kernel in r["kernel"]
+        assert r["achieved"] == pytest.approx(res["samples"] * 9 / 4.4e-3 / 1e9)
+        assert line["gpu_launches"] == 2 * 3
+        assert line["plain_vs_batched"] == pytest.approx(120.0 / 4.4)
+        if not extra:
+            assert r["traffic"] == bench.measured_traffic(768, res["tuning"])
+        else:
+            assert r["traffic"] is None
