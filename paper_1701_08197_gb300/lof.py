@@ -302,7 +302,16 @@ def decode_stats(row) -> dict:
 
 
 class Flagger:
-    """Owns one lof_ctx on a CUDA device."""
+    """Owns one lof_ctx on a CUDA device.
+
+    params are fields of lof_params (include/lof.h), defaults otherwise: p,
+    sensitivity, start_threshold, max_window, history_len, history_min,
+    history_k, sigma_estimator (LOF_SIGMA_MAD / _STD / _WINSOR), enable_freq,
+    enable_time, enable_history, sir_percent, time_mode
+    (LOF_TIME_PER_CHANNEL / _INTEGRATED / _2D), stats_scope
+    (LOF_SCOPE_POOLED / _CHANNEL), integ_chan, integ_time.  Invalid
+    combinations raise LofError here, at creation.
+    """
 
     def __init__(self, device: int = 0, n_history_slots: int = 0, **params):
         self.params = lof_default_params(**params)
