@@ -117,6 +117,9 @@ def parse():
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--stations", type=int, default=48,
                     help="stations per block (48 = the full configuration; fewer for profiling)")
+    ap.add_argument("--same-block", action="store_true",
+                    help="flag one block every step (the statistics hints then always hit); the "
+                         "default alternates two distinct seeded blocks, as a stream does")
     return ap.parse_args()
 
 
@@ -301,7 +304,12 @@ def run_gpu(args):
         dist.init_process_group("nccl", device_id=dev)
     n_units = args.stations * N_POL * N_SUBBAND
     samples = n_units * C * T
+    # two distinct seeded blocks (the same generator, block index 0 and 1),
+    # alternated step by step: every launch meets data it has not seen, and
+    # the statistics hints come from the other block
     x = make_block(dev, seed=2 + 1000 * rank, n_station=args.stations)
+    x1 = x if args.same_block else make_block(dev, seed=2 + 1000 * rank, block=1,
+                                               n_station=args.stations)
     out = torch.empty_like(x)
     mask = torch.empty(x.shape[:-1], dtype=torch.uint8, device=dev)
     stats = lof.stats_tensor(n_units, dev)
@@ -319,10 +327,12 @@ def run_gpu(args):
     ring = pw[:, None] * (1.0 + 0.01 * rng.standard_normal((pw.size, H)))
     fl.history_import(0, ring, np.full(pw.size, H, np.int32))
     units = build_units(x, out, mask, stats)
+    units1 = units if args.same_block else build_units(x1, out, mask, stats)
+    blocks = [units, units1]
     stream = torch.cuda.Stream(dev)
 
     def step(seq):
-        fl.flag_block(lof.LOF_CI16, units, seq, stream)
+        fl.flag_block(lof.LOF_CI16, blocks[seq % 2], seq, stream)
         fl.history_update(units, stream)
 
     # launch shape: the library default, or the autotuner's pick (untimed;
@@ -348,7 +358,7 @@ def run_gpu(args):
         ev[0].record(stream)
         for i in range(args.steps):
             kev[i][0].record(stream)
-            fl.flag_block(lof.LOF_CI16, units, 1000 + i, stream)
+            fl.flag_block(lof.LOF_CI16, blocks[i % 2], 1000 + i, stream)
             kev[i][1].record(stream)
             fl.history_update(units, stream)
             ev[i + 1].record(stream)
@@ -358,6 +368,12 @@ def run_gpu(args):
     torch.cuda.synchronize()
     if world > 1:
         dist.barrier()
+    # the exact selection's refinement work on fresh data: one more launch of
+    # each block, untimed, after the other block's (the steady state above)
+    refine = []
+    for b in (0, 1):
+        fl.flag_block(lof.LOF_CI16, blocks[b], 0, stream)
+        refine.append(fl.counters(stream))
     step_ms = [ev[i].elapsed_time(ev[i + 1]) for i in range(args.steps)]
     total_ms = ev[0].elapsed_time(ev[-1])
     kern_ms = [a.elapsed_time(b) for a, b in kev]
@@ -365,7 +381,7 @@ def run_gpu(args):
     value = job_msamples_per_s(samples, world, args.steps, t_max)
     res = {"rank": rank, "value": value, "ms_per_step": t_max / args.steps, "step_ms": step_ms,
            "kern_ms": kern_ms, "clocks": clk.summary(), "samples": samples,
-           "tuning": tuning or fl.tuning()}
+           "tuning": tuning or fl.tuning(), "refine": refine}
 
     # plain form: one launch per station-subband (its two polarisations)
     if not args.no_plain and rank == 0:
@@ -422,9 +438,11 @@ def run_gpu(args):
     return res
 
 
-def oracle_sample(seconds: float, seed=2, sir=0, integrated=False, scope=False, sigma="mad", grid=None):
+def oracle_sample(seconds: float, seed=2, sir=0, integrated=False, scope=False, sigma="mad", grid=None,
+                  threads=None):
     """The oracle (as it stands) on host cores: units of the same workload, one
-    per thread (the paper's thread-per-subband CPU layout), bounded in time."""
+    per thread (the paper's thread-per-subband CPU layout), bounded in time.
+    threads = None: every host core; 1: a single thread."""
     from concurrent.futures import ThreadPoolExecutor
 
     import torch
@@ -435,7 +453,7 @@ def oracle_sample(seconds: float, seed=2, sir=0, integrated=False, scope=False, 
     P = oracle.default_params(sir_percent=sir, time_mode=2 if grid else 1 if integrated else 0,
                               stats_scope=1 if scope else 0, sigma_estimator=SIGMA[sigma],
                               integ_chan=cells[0], integ_time=cells[1])
-    cores = os.cpu_count() or 1
+    cores = threads or os.cpu_count() or 1
     spec = synth.VoltageSpec(n_station=1, n_pol=N_POL, n_subband=N_SUBBAND, C=C, T=T,
                              sigma=32.0, tone_frac=0.02, impulse_frac=0.01)
     blk = synth.voltage_block(spec, seed=synth._mix(seed, 0), block=0, device="cpu")
@@ -485,6 +503,8 @@ def main():
         line = {"impl": "reference", "metric": METRIC, "value": v, "unit": "Msamples/s",
                 "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
                 "ms_per_step": (N_STATION * N_POL * N_SUBBAND * C * T / (v * 1e6) * 1e3) if v else None,
+                "ms_per_step_note": "extrapolated: one full block's samples at the sampled oracle rate "
+                                    "(each step times a bounded sample of the block's units)",
                 "higher_is_better": True,
                 "scaling": "weak", "vs_baseline": None, "dtype": "int64+f64",
                 "data": "synthetic (seeded)",
@@ -515,7 +535,9 @@ def main():
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int32/u64",
         "data": "synthetic (seeded noise + tones + impulses)",
         "config": dict(workload_config(args.stations, args.sir, args.integrated, args.channel_scope, args.sigma,
-                                    args.grid), tuning=res["tuning"]),
+                                    args.grid), tuning=res["tuning"],
+                       data_blocks="one block, every step" if args.same_block else
+                       "two distinct seeded blocks (block index 0, 1), alternated step by step"),
         "roofline": roofline_entry(
             alg_bytes, kern_avg, peak, peak_kind,
             # the recorded counters are those of the block kernel alone
@@ -534,9 +556,20 @@ def main():
         line["plain_vs_batched"] = pm[len(pm) // 2] / kern_avg
     if "e2e" in res:
         line["e2e"] = res["e2e"]
+    line["stats_refinement"] = {
+        "units_refined_per_launch": [r["units_refined"] for r in res["refine"]],
+        "refine_tasks_per_launch": [r["refine_tasks"] for r in res["refine"]],
+        "note": "block 0 after block 1 and block 1 after block 0: units whose pooled median/MAD "
+                "needed a refinement pass beyond the first counting pass (the previous block's "
+                "statistics as hints)" if not args.same_block else "same block every step"}
     if not args.no_cpu:
-        line["cpu_baseline"] = oracle_sample(args.cpu_seconds, sir=args.sir, integrated=args.integrated,
-                                             scope=args.channel_scope, sigma=args.sigma, grid=args.grid)
+        opts = dict(sir=args.sir, integrated=args.integrated, scope=args.channel_scope, sigma=args.sigma,
+                    grid=args.grid)
+        cb = oracle_sample(args.cpu_seconds * 0.7, **opts)
+        one = oracle_sample(max(3.0, args.cpu_seconds * 0.3), threads=1, **opts)
+        cb["single_thread"] = {"value": one["value"], "unit": one["unit"], "cores": 1,
+                               "sample": one["sample"]}
+        line["cpu_baseline"] = cb
     print(json.dumps(line))
 
 

@@ -227,6 +227,14 @@ int lof_history_import(lof_ctx *ctx, int64_t slot0, int64_t n, const double *val
  * context's kernels (LOF_ERR_TIMEOUT, ...) or LOF_OK; clears it. */
 int lof_status(lof_ctx *ctx, void *cuda_stream);
 
+/* Work counters of the last lof_flag_block on ctx (not of graph replays):
+ * counts[0] = units whose pooled time-pass statistics needed a refinement
+ * round after the first counting pass (the counts near the previous block's
+ * median and MAD did not pin them down), counts[1] = refinement tasks that
+ * read rows again.  Waits for cuda_stream.  Instrumentation of the exact
+ * selection (Section 4.2 asks for O(N) medians); results never depend on it. */
+int lof_block_counters(lof_ctx *ctx, void *cuda_stream, int64_t *counts);
+
 /* Largest n_time a unit of dtype may have with the current tuning. */
 int lof_max_time(const lof_ctx *ctx, int dtype);
 
@@ -278,8 +286,9 @@ int lof_graph_destroy(lof_graph *graph);
  * not allocate memory while they run -- real-time processing threads that
  * cannot afford cudaMalloc/cudaFree (which block and synchronise the device),
  * processes with a fixed allocation budget, or hosts without a memory pool.
- * It needs no context: params may be NULL (defaults), and the history flagger
- * is unavailable (every unit must have history_slot = -1).  Its scratch is
+ * It needs no context: params may be NULL (defaults; otherwise checked as
+ * lof_create checks them), and the history flagger is unavailable (every unit
+ * must have history_slot = -1).  Its scratch is
  * one file-scope device array of 64 MiB that every GPU which loads the
  * library holds until the process exits (about 40 KB per unit plus 9 bytes
  * per channel); host-side descriptors live in fixed static arrays (at most
@@ -288,7 +297,11 @@ int lof_graph_destroy(lof_graph *graph);
  * (lof_last_error(NULL)); nothing is launched then.
  * The first call on each device looks up the device address of the array
  * (with that device current); make that first call before any stream
- * capture.  All calls share the array and it keeps the last call's contents:
+ * capture.  The unit descriptors are uploaded from fixed host arrays that
+ * the next call reuses, so while cuda_stream is capturing the call returns
+ * LOF_ERR_INVALID and enqueues nothing; the upload copies from pageable host
+ * memory and may wait for work already queued on cuda_stream.  All calls
+ * share the array and it keeps the last call's contents:
  * each call clears what must start at zero, but calls whose work overlaps on
  * the GPU (different streams, or different host threads without ordering)
  * race on it -- serialise them.  status: optional DEVICE int that receives

@@ -59,7 +59,7 @@ struct lof_ctx {
   lof_params params{};
   int n_sm = 0;
   int smem_per_sm = 0, smem_optin = 0;
-  lof_tuning tuning{256, 2, 0, 2048, 64, 262144};
+  lof_tuning tuning = lofk::default_tuning();
   // history
   int64_t n_slots = 0;
   int H = 0;
@@ -76,7 +76,7 @@ struct lof_ctx {
   size_t cap_chan = 0, cap_chanfc = 0;
   uint32_t* d_gen = nullptr;  // general time-pass rows (per CTA)
   size_t cap_gen = 0;
-  int* d_ctrl = nullptr;  // [0] queue, [1] error, [2..3] error detail
+  int* d_ctrl = nullptr;  // [0] queue, [1] error, [2..3] error detail, [4..5] counters
   int* h_err = nullptr;   // pinned copy of d_ctrl[1..3]
   cudaEvent_t ev_err = nullptr;
   bool err_copy_pending = false;
@@ -200,50 +200,56 @@ extern "C" const char* lof_last_error(const lof_ctx* c) {
   return c ? c->last_error.c_str() : g_create_error;
 }
 
-static int validate_params(const lof_params* p, std::string* why) {
-  char b[256];
+namespace lofk {
+
+lof_tuning default_tuning() { return lof_tuning{256, 2, 0, 2048, 64, 262144}; }
+
+// Checks every field of a parameter set (shared by lof_create and the
+// allocation-free entry point); 1 = valid, else 0 with the reason in *why.
+int validate_params(const lof_params* p, char* why, int nwhy) {
   if (!(p->p > 0.0) || !(p->sensitivity > 0.0) || !(p->start_threshold > 0.0)) {
-    *why = "p, sensitivity and start_threshold must be positive";
+    snprintf(why, nwhy, "%s", "p, sensitivity and start_threshold must be positive");
     return 0;
   }
   if (p->max_window < 1 || p->max_window > 64 || (p->max_window & (p->max_window - 1))) {
-    snprintf(b, sizeof b, "max_window %d must be a power of two in [1, 64]", p->max_window);
-    *why = b;
+    snprintf(why, nwhy, "max_window %d must be a power of two in [1, 64]", p->max_window);
     return 0;
   }
   if (p->history_len < 1 || p->history_len > 1024 || p->history_min < 0 || !(p->history_k >= 0.0)) {
-    *why = "history_len in [1, 1024], history_min >= 0, history_k >= 0 required";
+    snprintf(why, nwhy, "%s", "history_len in [1, 1024], history_min >= 0, history_k >= 0 required");
     return 0;
   }
   if (p->sigma_estimator != LOF_SIGMA_MAD && p->sigma_estimator != LOF_SIGMA_STD &&
       p->sigma_estimator != LOF_SIGMA_WINSOR) {
-    *why = "unknown sigma_estimator";
+    snprintf(why, nwhy, "%s", "unknown sigma_estimator");
     return 0;
   }
   if (p->sir_percent < 0 || p->sir_percent > 99) {
-    *why = "sir_percent in [0, 99] required";
+    snprintf(why, nwhy, "%s", "sir_percent in [0, 99] required");
     return 0;
   }
   if (p->time_mode != LOF_TIME_PER_CHANNEL && p->time_mode != LOF_TIME_INTEGRATED &&
       p->time_mode != LOF_TIME_2D) {
-    *why = "unknown time_mode";
+    snprintf(why, nwhy, "%s", "unknown time_mode");
     return 0;
   }
   if (p->stats_scope != LOF_SCOPE_POOLED && p->stats_scope != LOF_SCOPE_CHANNEL) {
-    *why = "unknown stats_scope";
+    snprintf(why, nwhy, "%s", "unknown stats_scope");
     return 0;
   }
   if (p->stats_scope == LOF_SCOPE_CHANNEL && p->time_mode != LOF_TIME_PER_CHANNEL) {
-    *why = "stats_scope LOF_SCOPE_CHANNEL needs time_mode LOF_TIME_PER_CHANNEL";
+    snprintf(why, nwhy, "%s", "stats_scope LOF_SCOPE_CHANNEL needs time_mode LOF_TIME_PER_CHANNEL");
     return 0;
   }
   if (p->integ_chan < 1 || p->integ_time < 1 ||
       static_cast<int64_t>(p->integ_chan) * p->integ_time > 65536) {
-    *why = "integ_chan, integ_time >= 1 with integ_chan * integ_time <= 65536 required";
+    snprintf(why, nwhy, "%s", "integ_chan, integ_time >= 1 with integ_chan * integ_time <= 65536 required");
     return 0;
   }
   return 1;
 }
+
+}  // namespace lofk
 
 extern "C" int lof_create(const lof_params* params, int cuda_device, int64_t n_history_slots,
                           lof_ctx** out) {
@@ -252,8 +258,8 @@ extern "C" int lof_create(const lof_params* params, int cuda_device, int64_t n_h
   lof_params p;
   if (params) p = *params;
   else lof_default_params(&p);
-  std::string why;
-  if (!validate_params(&p, &why)) return fail(nullptr, LOF_ERR_INVALID, "lof_create: %s", why.c_str());
+  char why[256];
+  if (!lofk::validate_params(&p, why, sizeof why)) return fail(nullptr, LOF_ERR_INVALID, "lof_create: %s", why);
   if (n_history_slots < 0) return fail(nullptr, LOF_ERR_INVALID, "lof_create: negative history slots");
   int ndev = 0;
   cudaError_t e = cudaGetDeviceCount(&ndev);
@@ -285,7 +291,7 @@ extern "C" int lof_create(const lof_params* params, int cuda_device, int64_t n_h
   ck(cudaMalloc(&c->hist.pend_flag, ns), "history pending flag");
   ck(cudaMalloc(&c->hist.pend_seq, ns * sizeof(uint64_t)), "history pending seq");
   ck(cudaMalloc(&c->hist.hint, ns * 2 * sizeof(unsigned long long)), "statistics hints");
-  ck(cudaMalloc(&c->d_ctrl, 4 * sizeof(int)), "control words");
+  ck(cudaMalloc(&c->d_ctrl, lofk::kCtrlWords * sizeof(int)), "control words");
   ck(cudaHostAlloc(&c->h_err, 4 * sizeof(int), cudaHostAllocDefault), "pinned error word");
   ck(cudaEventCreateWithFlags(&c->ev_err, cudaEventDisableTiming), "event");
   for (int i = 0; i < kStageRing; ++i)
@@ -297,7 +303,7 @@ extern "C" int lof_create(const lof_params* params, int cuda_device, int64_t n_h
     ck(cudaMemset(c->hist.thr, 0, ns * sizeof(double)), "memset");
     ck(cudaMemset(c->hist.pend_flag, 0, ns), "memset");
     ck(cudaMemset(c->hist.hint, 0xFF, ns * 2 * sizeof(unsigned long long)), "memset");
-    ck(cudaMemset(c->d_ctrl, 0, 4 * sizeof(int)), "memset");
+    ck(cudaMemset(c->d_ctrl, 0, lofk::kCtrlWords * sizeof(int)), "memset");
     ck(cudaDeviceSynchronize(), "cudaDeviceSynchronize");
     memset(c->h_err, 0, 4 * sizeof(int));
   }
@@ -639,7 +645,8 @@ int host_launch_kernel(const lof_params& P, const HostCfg& h, int dtype, const P
   if (!is_float(dtype) &&
       ((e = cudaMemset2DAsync(sc.ustate, sizeof(UnitState), 0, kUnitStateZeroBytes, n_units, st)) !=
            cudaSuccess ||
-       (e = cudaMemsetAsync(sc.ctrl, 0, sizeof(int), st)) != cudaSuccess)) {
+       (e = cudaMemsetAsync(sc.ctrl, 0, sizeof(int), st)) != cudaSuccess ||
+       (e = cudaMemsetAsync(sc.ctrl + 4, 0, 2 * sizeof(int), st)) != cudaSuccess)) {
     snprintf(why, nwhy, "state reset: %s", cudaGetErrorString(e));
     return LOF_ERR_CUDA;
   }
@@ -652,6 +659,7 @@ int host_launch_kernel(const lof_params& P, const HostCfg& h, int dtype, const P
   kp.queue = sc.ctrl;
   kp.err = sc.ctrl + 1;
   kp.err_info = sc.ctrl + 2;
+  kp.counters = sc.ctrl + 4;
   kp.hist = sc.hist;
   kp.n_units = n_units;
   kp.n_tasks = pr.n_tasks;
@@ -1097,6 +1105,18 @@ extern "C" int lof_status(lof_ctx* c, void* cuda_stream) {
   return pending_device_error(c);
 }
 
+extern "C" int lof_block_counters(lof_ctx* c, void* cuda_stream, int64_t* counts) {
+  if (!c || !counts) return fail(c, LOF_ERR_INVALID, "lof_block_counters: NULL argument");
+  DeviceGuard g(c->device);
+  cudaError_t e = cudaStreamSynchronize(static_cast<cudaStream_t>(cuda_stream));
+  int h[2] = {0, 0};
+  if (e == cudaSuccess) e = cudaMemcpy(h, c->d_ctrl + 4, sizeof h, cudaMemcpyDeviceToHost);
+  if (e != cudaSuccess) return cuda_fail(c, e, "lof_block_counters");
+  counts[0] = h[0];
+  counts[1] = h[1];
+  return LOF_OK;
+}
+
 extern "C" int lof_max_time(const lof_ctx* c, int dtype) {
   if (!c || esize_of(dtype) == 0) return 0;
   int lo = 0, hi = 1 << 20;
@@ -1255,7 +1275,7 @@ extern "C" int lof_graph_create(lof_ctx* c, int dtype, const lof_unit* units, in
       (e = cudaMalloc(&g->d_chanFc, std::max<int64_t>(1, pr.n_chan))) != cudaSuccess ||
       (e = cudaMalloc(&g->d_gen, static_cast<size_t>(std::max(1, pr.grid)) * std::max(1, pr.gen_words) * 4)) !=
           cudaSuccess ||
-      (e = cudaMalloc(&g->d_ctrl, 4 * sizeof(int))) != cudaSuccess ||
+      (e = cudaMalloc(&g->d_ctrl, lofk::kCtrlWords * sizeof(int))) != cudaSuccess ||
       (e = cudaHostAlloc(&g->h_err, 3 * sizeof(int), cudaHostAllocDefault)) != cudaSuccess ||
       (e = cudaEventCreateWithFlags(&g->ev_err, cudaEventDisableTiming)) != cudaSuccess) {
     graph_free(g);
@@ -1265,7 +1285,7 @@ extern "C" int lof_graph_create(lof_ctx* c, int dtype, const lof_unit* units, in
           cudaSuccess ||
       (pr.n_tasks > 0 && (e = cudaMemcpy(g->d_tasks, tasks.data(), pr.n_tasks * sizeof(Task),
                                          cudaMemcpyHostToDevice)) != cudaSuccess) ||
-      (e = cudaMemset(g->d_ctrl, 0, 4 * sizeof(int))) != cudaSuccess) {
+      (e = cudaMemset(g->d_ctrl, 0, lofk::kCtrlWords * sizeof(int))) != cudaSuccess) {
     graph_free(g);
     return cuda_fail(c, e, "lof_graph_create: upload");
   }

@@ -22,6 +22,7 @@ constexpr int kMaxSpec = 1024;               // exact counters near the previous
 constexpr int kSelCap = 2048;                // bin-list capacity for exact selection
 constexpr int kMaxRounds = 12;               // refinement rounds before giving up
 constexpr int kWorkspaceBytes = 36 * 1024;   // last-arriver workspace (overlays the prefix buffer)
+constexpr int kCtrlWords = 8;               // control words of a launch (see Scratch::ctrl)
 
 // device error codes (written to the context's mapped error word)
 enum : int {
@@ -127,6 +128,8 @@ struct KParams {
   int* queue;                   // [0] next task
   int* err;                     // first device-side error (0 = none)
   int* err_info;                // detail words of that error
+  int* counters;                // [0] units whose statistics needed a refinement round,
+                                // [1] fine-count tasks that ran (zeroed per launch)
   HistoryDev hist;
   int n_units, n_tasks;
   int fine_bins;                // counters per refinement round
@@ -174,11 +177,13 @@ struct Scratch {
   UnitState* ustate;
   unsigned long long* chanS;
   uint8_t* chanFc;
-  int* ctrl;  // [0] queue, [1] error, [2..3] detail
+  int* ctrl;  // [0] queue, [1] error, [2..3] detail, [4..5] counters (kCtrlWords ints)
   HistoryDev hist;
   uint32_t* gen;  // general time-pass rows: grid x gen_words words
 };
 // lof_api.cu: heap-free steps shared by every entry point
+lof_tuning default_tuning();  // the library's launch shape before any lof_set_tuning
+int validate_params(const lof_params* p, char* why, int nwhy);  // 1 = valid
 int host_check_dtype(int dtype, char* why, int nwhy);
 int host_validate_unit(int dtype, const lof_unit& u, int i, int64_t n_slots, char* why, int nwhy);
 int host_count_tasks(const HostCfg& h, int dtype, const lof_unit* units, int n_units,

@@ -1976,8 +1976,10 @@ __device__ LOFK_TASK_FN void unit_round1(const KParams& kp, const DevUnit& u, Un
   }
   __syncthreads();
   if (tid == 0) {
+    const bool fine = __ldcg(&us->state) == kStateFine;
+    if (fine && kp.counters) atomicAdd(kp.counters, 1);
     __threadfence();
-    st_release(&us->ready, __ldcg(&us->state) == kStateFine ? 1 : 2);
+    st_release(&us->ready, fine ? 1 : 2);
   }
 }
 
@@ -2164,6 +2166,7 @@ __device__ LOFK_TASK_FN void task_fine(const KParams& kp, const DevUnit& u, Unit
   if (!f.ok || f.state == 2) return;
   count_fine_rows<DT, NT>(kp, u, us, tk.row0, tk.row0 + tk.nrows, ws, f);
   if (tid == 0) {
+    if (kp.counters) atomicAdd(kp.counters + 1, 1);
     __threadfence();
     const int old = atomicAdd(&us->done_F, 1);
     f.last = (old + 1 == u.nF) ? 1 : 0;

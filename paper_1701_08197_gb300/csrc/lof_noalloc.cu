@@ -55,6 +55,12 @@ extern "C" int lof_flag_block_noalloc(const lof_params* params, int dtype, const
   lof_params P;
   if (params) P = *params;
   else lof_default_params(&P);
+  // the same parameter checks as lof_create, before anything reads them
+  char pwhy[256];
+  if (!lofk::validate_params(&P, pwhy, sizeof pwhy)) {
+    snprintf(why, sizeof why, "lof_flag_block_noalloc: %s", pwhy);
+    return fail(LOF_ERR_INVALID);
+  }
   int rc = lofk::host_check_dtype(dtype, why, sizeof why);
   if (rc) return fail(rc);
   if (n_units < 0 || (n_units > 0 && !units)) {
@@ -79,8 +85,19 @@ extern "C" int lof_flag_block_noalloc(const lof_params* params, int dtype, const
     }
   }
   if (n_units == 0) return LOF_OK;
+  // The descriptors are uploaded from the static host arrays below, which the
+  // next call overwrites: a captured copy would replay some later call's units.
+  cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+  cudaError_t e = cudaStreamIsCapturing(static_cast<cudaStream_t>(cuda_stream), &cap);
+  if (e != cudaSuccess || cap != cudaStreamCaptureStatusNone) {
+    snprintf(why, sizeof why,
+             "lof_flag_block_noalloc: cuda_stream is capturing (or its state is unknown: %s); "
+             "nothing was enqueued",
+             cudaGetErrorString(e));
+    return fail(LOF_ERR_INVALID);
+  }
   int dev = 0;
-  cudaError_t e = cudaGetDevice(&dev);
+  e = cudaGetDevice(&dev);
   if (e != cudaSuccess || dev < 0 || dev >= kMaxDevicesNA) {
     snprintf(why, sizeof why, "lof_flag_block_noalloc: no usable current device (%s)",
              cudaGetErrorString(e));
@@ -101,7 +118,7 @@ extern "C" int lof_flag_block_noalloc(const lof_params* params, int dtype, const
   cudaDeviceGetAttribute(&h.n_sm, cudaDevAttrMultiProcessorCount, dev);
   cudaDeviceGetAttribute(&h.smem_per_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev);
   cudaDeviceGetAttribute(&h.smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
-  h.tuning = lof_tuning{256, 2, 0, 2048, 64, 262144};
+  h.tuning = lofk::default_tuning();
   int n_tasks = 0;
   rc = lofk::host_count_tasks(h, dtype, units, n_units, &n_tasks, why, sizeof why);
   if (rc) return fail(rc);
@@ -141,10 +158,10 @@ extern "C" int lof_flag_block_noalloc(const lof_params* params, int dtype, const
   }
   sc.hist = lofk::HistoryDev{};
   cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
-  // the error word and detail start at zero on every call (the queue and the
-  // per-unit counters, moments and histograms are cleared by host_launch);
-  // every other part is written before it is read
-  e = cudaMemsetAsync(sc.ctrl, 0, 4 * sizeof(int), st);
+  // the error word and detail start at zero on every call (the queue, the
+  // launch counters and the per-unit counters, moments and histograms are
+  // cleared by host_launch); every other part is written before it is read
+  e = cudaMemsetAsync(sc.ctrl, 0, lofk::kCtrlWords * sizeof(int), st);
   if (e != cudaSuccess) {
     snprintf(why, sizeof why, "lof_flag_block_noalloc: %s", cudaGetErrorString(e));
     return fail(LOF_ERR_CUDA);

@@ -29,7 +29,7 @@ EXPORTED = [
     "lof_history_update", "lof_history_export", "lof_history_import", "lof_status",
     "lof_max_time", "lof_set_tuning", "lof_get_tuning", "lof_last_error", "lof_destroy",
     "lof_flag_block_noalloc", "lof_autotune", "lof_graph_create", "lof_graph_launch",
-    "lof_graph_status", "lof_graph_destroy",
+    "lof_graph_status", "lof_graph_destroy", "lof_block_counters",
 ]
 
 
@@ -138,11 +138,12 @@ def library(build: bool = True):
     L.lof_graph_launch.argtypes = [V, ctypes.c_uint64, V]
     L.lof_graph_status.argtypes = [V, V]
     L.lof_graph_destroy.argtypes = [V]
+    L.lof_block_counters.argtypes = [V, V, P(ctypes.c_int64)]
     for name in ("lof_create", "lof_flag_block", "lof_flag_block_host", "lof_history_update",
                  "lof_history_export", "lof_history_import", "lof_status", "lof_max_time",
                  "lof_set_tuning", "lof_get_tuning", "lof_destroy", "lof_flag_block_noalloc",
                  "lof_autotune", "lof_graph_create", "lof_graph_launch", "lof_graph_status",
-                 "lof_graph_destroy"):
+                 "lof_graph_destroy", "lof_block_counters"):
         getattr(L, name).restype = ctypes.c_int
     _lib = L
     return L
@@ -354,6 +355,12 @@ class Flagger:
 
     def status(self, stream=None):
         _check(lof_status(self.ctx, self._stream(stream)), self.ctx)
+
+    def counters(self, stream=None) -> dict:
+        """Work counters of the last flag_block (lof_block_counters)."""
+        c = (ctypes.c_int64 * 2)()
+        _check(library().lof_block_counters(self.ctx, ctypes.c_void_p(self._stream(stream)), c), self.ctx)
+        return {"units_refined": int(c[0]), "refine_tasks": int(c[1])}
 
     def set_tuning(self, **kw):
         _check(lof_set_tuning(self.ctx, **kw), self.ctx)

@@ -61,3 +61,21 @@ def test_bad_parameters_are_rejected_before_touching_a_device():
     assert "max_window" in lof.lof_last_error()
     p = lof.lof_default_params(sensitivity=0.0)
     assert L.lof_create(ctypes.byref(p), 0, 0, ctypes.byref(ctx)) == lof.LOF_ERR_INVALID
+
+
+def test_noalloc_rejects_bad_parameters_before_launch():
+    """The allocation-free entry point checks its parameters as lof_create
+    does, before it reads a unit or touches a device."""
+    x = (ctypes.c_int16 * 128)()
+    u = lof.lof_unit()
+    u.in_ = ctypes.addressof(x)
+    u.n_chan, u.n_time, u.in_row_stride, u.history_slot = 1, 64, 64, -1
+    for bad, word in ((dict(max_window=128), "max_window"),
+                      (dict(time_mode=lof.LOF_TIME_2D, integ_chan=0), "integ_chan"),
+                      (dict(sensitivity=0.0), "sensitivity"),
+                      (dict(sigma_estimator=7), "sigma_estimator"),
+                      (dict(time_mode=9), "time_mode")):
+        p = lof.lof_default_params(**bad)
+        rc = lof.lof_flag_block_noalloc(p, lof.LOF_CI16, [u], 0, 0)
+        assert rc == lof.LOF_ERR_INVALID, bad
+        assert word in lof.lof_last_error(), (bad, lof.lof_last_error())

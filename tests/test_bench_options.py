@@ -81,7 +81,8 @@ def test_gpu_line_assembly_with_a_fake_run(monkeypatch, capsys):
            "tuning": dict(threads=256, ctas_per_sm=2, tile_bytes=0, fine_bins=2048, flag_rows=64,
                           stat_samples=262144),
            "e2e": {"value": 16000.0, "unit": "Msamples/s", "h2d_bytes_per_step": 1,
-                   "d2h_bytes_per_step": 1}}
+                   "d2h_bytes_per_step": 1},
+           "refine": [{"units_refined": 0, "refine_tasks": 0}, {"units_refined": 2, "refine_tasks": 6}]}
     monkeypatch.setattr(bench, "run_gpu", lambda args: res)
     for k in ("RANK", "WORLD_SIZE", "LOCAL_RANK"):
         monkeypatch.delenv(k, raising=False)
@@ -98,6 +99,7 @@ def test_gpu_line_assembly_with_a_fake_run(monkeypatch, capsys):
         assert r["achieved"] == pytest.approx(res["samples"] * 9 / 4.4e-3 / 1e9)
         assert line["gpu_launches"] == 2 * 3
         assert line["plain_vs_batched"] == pytest.approx(120.0 / 4.4)
+        assert line["stats_refinement"]["units_refined_per_launch"] == [0, 2]
         if not extra:
             assert r["traffic"] == bench.measured_traffic(768, res["tuning"])
         else:

@@ -47,7 +47,9 @@ def test_full_station_block_sampled_units_match_oracle():
         # sampled units against the oracle with the same rings
         P = oracle_params()
         xs = x.reshape(n_units, C, T, 2)
-        for ui in (0, 1, 131, 402, 767):
+        # fixed corners plus a seeded draw of 16 more units across the stations
+        draw = np.random.default_rng(20261204).choice(n_units, 16, replace=False).tolist()
+        for ui in sorted({0, 1, 131, 402, 767, *draw}):
             hist = oracle.History(C, P)
             hist.ring[:] = ring[ui * C:(ui + 1) * C]
             hist.count[:] = H
