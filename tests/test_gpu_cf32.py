@@ -1,6 +1,7 @@
 """Complex float32 visibilities (post-correlation placement): GPU path against
 the oracle under the float contract of the Stokes I path (statistics within
-1e-6 relative, masks equal away from near-threshold windows), and the
+1e-6 relative, masks equal outside the uncertain set of the binary64 replay:
+near-threshold windows and what they cascade into), and the
 complex output equal to the input with the GPU's own mask applied."""
 import numpy as np
 import pytest
@@ -9,7 +10,7 @@ import torch
 import oracle
 from paper_1701_08197_gb300 import lof
 
-from test_gpu_f32 import CASCADE, _check_unit
+from test_gpu_f32 import _check_unit
 
 pytestmark = pytest.mark.gpu
 
@@ -45,6 +46,6 @@ def test_cf32_matches_oracle_within_tolerance(shape):
         pw = (x.real.astype(np.float64) ** 2 + x.imag.astype(np.float64) ** 2)
         pw = np.where(np.isfinite(x.real) & np.isfinite(x.imag), pw, np.nan).astype(np.float32)
         ref = oracle.flag_unit(p, x)
-        nd, nn = _check_unit(p, pw, m, np.where(m.astype(bool), np.float32(0), pw),
-                             lof.decode_stats(stats.cpu()[k]), ref)
-        assert nd <= max(4 * CASCADE, nn + 2 * CASCADE)
+        nd, nn, nc = _check_unit(p, pw, m, np.where(m.astype(bool), np.float32(0), pw),
+                                 lof.decode_stats(stats.cpu()[k]), ref, tag=f"cf32 unit {k}")
+        assert nd <= nn + nc

@@ -1,11 +1,14 @@
 """Float32 Stokes I units (power given): GPU path against the oracle.
 
-Parity rule for float inputs: the spectrum and pooled statistics agree within
-1e-6 relative; masks may differ only on samples covered by a window whose
-substituted sum lies within 1e-5 relative of its threshold (I * T_I), and on
-the samples a later, larger window can reach from such a sample (cascade).
+Parity rule for float inputs (the float contract of the Stokes I path): the
+spectrum and pooled statistics agree within 1e-6 relative; a mask may differ
+only on samples the binary64 replay of tests/float_parity.py marks uncertain:
+samples of windows whose substituted sum lies within 1e-5 relative of its
+threshold I * T_I (near), and samples of later windows whose sums those
+uncertain samples can move across that band (cascade).  Any other difference
+fails.  Both counts are reported for every unit (pytest warnings summary).
 The data output must equal the input with the GPU's own mask applied."""
-import math
+import warnings
 
 import numpy as np
 import pytest
@@ -14,109 +17,44 @@ import torch
 import oracle
 from paper_1701_08197_gb300 import lof, synth
 
+from float_parity import allowed_differences
+
 pytestmark = pytest.mark.gpu
 
 DEV = "cuda:0"
 REL_STATS = 1e-6
-REL_NEAR = 1e-5
-CASCADE = 127  # reach of the later windows (1 + 2 + ... + 64)
 
 
-def _factor(p, k):
-    pk = 1.0
-    for _ in range(k):
-        pk = pk * p.p
-    return p.start_threshold * pk / float(1 << k)
+class FloatParityCounts(UserWarning):
+    """near-threshold / cascade / differing sample counts of a float unit"""
 
 
-def _thr(p, m, s, k):
-    return m + (s * _factor(p, k)) * p.sensitivity
-
-
-def _near_rows(p, P, F_entry, Fc, m, s):
-    """Replay of the time SumThreshold (binary64, same semantics as the
-    oracle) marking the samples of windows near their threshold."""
-    C, T = P.shape
-    near = np.zeros((C, T), bool)
-    if not (s > 0):
-        return near
-    for c in range(C):
-        if Fc[c]:
-            continue
-        flags = F_entry[c].copy()
-        v = np.where(F_entry[c], 0.0, P[c].astype(np.float64))
-        k = 0
-        while (1 << k) <= min(p.max_window, T):
-            I = 1 << k
-            t = _thr(p, m, s, k)
-            sub = np.where(flags, t, v)
-            cs = np.concatenate([[0.0], np.cumsum(sub)])
-            S = cs[I:] - cs[:-I]
-            lim = I * t
-            nw = np.abs(S - lim) <= REL_NEAR * abs(lim)
-            fire = S > lim
-            nxt = flags.copy()
-            for st in np.nonzero(fire)[0]:
-                nxt[st:st + I] = True
-            for st in np.nonzero(nw)[0]:
-                near[c, st:st + I] = True
-            flags = nxt
-            k += 1
-    return near
-
-
-def _near_channels(p, S, m, s):
-    """Replay of the spectrum SumThreshold: (near-threshold channels, flags)."""
-    C = len(S)
-    near = np.zeros(C, bool)
-    if not (s > 0):
-        return near, np.zeros(C, bool)
-    flags = np.zeros(C, bool)
-    k = 0
-    while (1 << k) <= min(p.max_window, C):
-        I = 1 << k
-        t = _thr(p, m, s, k)
-        sub = np.where(flags, t, S)
-        cs = np.concatenate([[0.0], np.cumsum(sub)])
-        W = cs[I:] - cs[:-I]
-        lim = I * t
-        nw = np.abs(W - lim) <= REL_NEAR * abs(lim)
-        nxt = flags.copy()
-        for st in np.nonzero(W > lim)[0]:
-            nxt[st:st + I] = True
-        for st in np.nonzero(nw)[0]:
-            near[st:st + I] = True
-        flags = nxt
-        k += 1
-    return near, flags
-
-
-def _check_unit(p, x, res_gpu_mask, res_gpu_out, gpu_stats, ref):
+def _check_unit(p, x, res_gpu_mask, res_gpu_out, gpu_stats, ref, tag=""):
+    """x: float32 powers [C, T] (non-finite = flagged on entry).  Returns
+    (differing samples, near-threshold samples, cascade samples)."""
     C, T = x.shape
     rs = ref["stats"]
-    for key in ("median_f", "sigma_f", "median_t", "sigma_t"):
-        a, b = gpu_stats[key], rs[key]
-        assert abs(a - b) <= REL_STATS * max(abs(b), 1e-30), (key, a, b)
-    P = np.where(np.isfinite(x), x, 0.0)
-    F_entry = ~np.isfinite(x)
-    S = np.array([P[c][~F_entry[c]].astype(np.float64).sum() for c in range(C)])
-    nch, Fc = _near_channels(p, S, rs["median_f"], rs["sigma_f"])
-    near = _near_rows(p, P, F_entry, Fc, rs["median_t"], rs["sigma_t"])
-    allowed = near.copy()
-    for c in range(C):
-        idx = np.nonzero(near[c])[0]
-        for t0 in idx:
-            allowed[c, max(0, t0 - CASCADE):t0 + CASCADE + 1] = True
-        if nch[c]:
-            allowed[c, :] = True
+    entry = ~np.isfinite(x)
+    P = np.where(entry, 0.0, x.astype(np.float64))
+    allowed, fc_unc, n_near, n_casc = allowed_differences(p, P, entry, rs)
+    # the statistics are compared unless a channel's frequency decision is
+    # itself uncertain and the two sides took it differently (the pooled set
+    # then differs by that channel)
+    if not (fc_unc.any() and gpu_stats["n_chan_freq"] != rs["n_chan_freq"]):
+        for key in ("median_f", "sigma_f", "median_t", "sigma_t"):
+            a, b = gpu_stats[key], rs[key]
+            assert abs(a - b) <= REL_STATS * max(abs(b), 1e-30), (tag, key, a, b)
     diff = res_gpu_mask != ref["mask"]
     bad = diff & ~allowed
-    assert not bad.any(), f"{int(bad.sum())} differing samples outside the near-threshold set " \
+    assert not bad.any(), f"{tag}: {int(bad.sum())} differing samples outside the uncertain set " \
                           f"(first at {np.argwhere(bad)[:3].tolist()})"
     # the output is the input with the GPU mask applied
     exp = np.where(res_gpu_mask.astype(bool), np.float32(0), x)
     assert np.array_equal(res_gpu_out.view(np.uint32), exp.view(np.uint32))
-    return int(diff.sum()), int(near.sum())
+    nd = int(diff.sum())
+    warnings.warn(FloatParityCounts(f"{tag} {C}x{T}: near_threshold_count={n_near} "
+                                    f"cascade_count={n_casc} differing={nd}"))
+    return nd, n_near, n_casc
 
 
 def _stokes(seed, C, T, nonfinite=0):
@@ -149,8 +87,8 @@ def test_f32_matches_oracle_within_tolerance(shape):
         masks, outs, stats = _run_gpu(fl, xs)
     for k, x in enumerate(xs):
         ref = oracle.flag_unit(p, x)
-        nd, nn = _check_unit(p, x, masks[k], outs[k], stats[k], ref)
-        assert nd <= max(4 * CASCADE, nn + 2 * CASCADE)
+        nd, nn, nc = _check_unit(p, x, masks[k], outs[k], stats[k], ref, tag=f"f32 unit {k}")
+        assert nd <= nn + nc
         if T > 1:
             assert ref["mask"].sum() > 0
 
