@@ -117,6 +117,8 @@ def parse():
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--stations", type=int, default=48,
                     help="stations per block (48 = the full configuration; fewer for profiling)")
+    ap.add_argument("--no-configs", dest="configs", action="store_false",
+                    help="skip the legs of the other configurations (batched uneven, Stokes I, serving)")
     ap.add_argument("--same-block", action="store_true",
                     help="flag one block every step (the statistics hints then always hit); the "
                          "default alternates two distinct seeded blocks, as a stream does")
@@ -433,9 +435,189 @@ def run_gpu(args):
                                                 + hst.numel() * 8),
                       "ms_per_step": e2e_ms, "wall_ms_per_step": wall * 1e3 / e2e_steps}
     fl.close()
+    # the other configurations (rank 0, one GPU): the headline's buffers go first
+    if args.configs and rank == 0 and world == 1:
+        del x, x1, out, mask, units, units1, blocks
+        torch.cuda.empty_cache()
+        legs = {}
+        for name, fn in (("config3_batched", lambda: leg_batched(dev)),
+                         ("config4_stokes", lambda: leg_stokes(dev)),
+                         ("config5_serving", lambda: leg_serving(dev))):
+            try:
+                legs[name] = fn()
+            except Exception as e:  # a leg's failure is recorded, not hidden
+                legs[name] = {"error": f"{type(e).__name__}: {e}"}
+        if isinstance(legs.get("config4_stokes"), tuple):
+            legs["config4_stokes"], res["stokes_kept"] = legs["config4_stokes"]
+        res["legs"] = legs
     if world > 1:
         dist.destroy_process_group()
     return res
+
+
+# ---------------------------------------------------------------- other configurations
+# Short legs after the headline measurement (rank 0, N = 1): the batched
+# uneven block (config 3), the Stokes I pulsar block (config 4) and the
+# serving loop (config 5), each with the sizes stated in its record.
+
+def _events_ms(fn, reps, stream):
+    import torch
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ts = []
+    for _ in range(reps):
+        e0.record(stream)
+        fn()
+        e1.record(stream)
+        e1.synchronize()
+        ts.append(e0.elapsed_time(e1))
+    return sorted(ts)[len(ts) // 2]
+
+
+def leg_batched(dev, n_subband=244, n_station=48, plain_seconds=3.0, peak=6789.0):
+    """Config 3: every station x pol x subband of a block of uneven complex
+    int8 units (C in 16/64/256, T in 768/3072/12288 drawn per subband from
+    seed 3) in ONE persistent launch captured in a CUDA graph, against one
+    launch per unit (timed on the first units for plain_seconds, scaled to all
+    units).  Units own history slots; blocks 0 and 1 alternate, so each
+    replay meets new data with the other block's statistics as hints."""
+    import torch
+    from paper_1701_08197_gb300 import batched, lof
+    stream = torch.cuda.current_stream()
+    t0 = time.perf_counter()
+    xa = batched.build(n_subband, n_station, device=dev, block=0)
+    xb = batched.build(n_subband, n_station, device=dev, block=1)
+    gen_s = time.perf_counter() - t0
+    outs = [torch.empty_like(x) for x in xa]
+    masks = [torch.empty(x.shape[:-1], dtype=torch.uint8, device=dev) for x in xa]
+    ua = batched.units_of(xa, outs, masks, history=True)
+    ub = batched.units_of(xb, outs, masks, history=True)
+    samples = sum(int(x.numel() // 2) for x in xa)
+    slots = sum(int(x.shape[0] * 2 * x.shape[2]) for x in xa)
+    res = {"workload": f"{n_subband} subbands x {n_station} stations x 2 pols = {len(ua)} uneven units, "
+                       f"C in 16/64/256, T in 768/3072/12288 (seed 3), complex int8 sigma 8, "
+                       f"{samples} samples, blocks 0/1 alternated", "samples": samples,
+           "generate_s": gen_s}
+    with lof.Flagger(dev.index or 0, n_history_slots=slots) as fl:
+        ga, gb = fl.graph(lof.LOF_CI8, ua), fl.graph(lof.LOF_CI8, ub)
+        for i in range(3):
+            (ga if i % 2 == 0 else gb).launch(i, stream)
+        ga.status(stream)
+        k = [0]
+
+        def replay():
+            (gb if k[0] % 2 == 0 else ga).launch(10 + k[0], stream)
+            k[0] += 1
+        graph_ms = _events_ms(replay, 4, stream)
+        ga.status(stream)
+        direct_ms = _events_ms(lambda: fl.flag_block(lof.LOF_CI8, ua, 0, stream), 2, stream)
+        fl.status(stream)
+        refine = fl.counters(stream)
+        ga.close()
+        gb.close()
+        # plain form: one launch per unit, as long as plain_seconds allows
+        n_plain, tp0 = 0, time.perf_counter()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        while n_plain < len(ua) and time.perf_counter() - tp0 < plain_seconds:
+            for u in ua[n_plain:n_plain + 64]:
+                fl.flag_block(lof.LOF_CI8, [u], 0, stream)
+            n_plain = min(len(ua), n_plain + 64)
+            stream.synchronize()
+        e1.record(stream)
+        e1.synchronize()
+        fl.status(stream)
+        plain_part_ms = e0.elapsed_time(e1)
+        plain_samples = sum(ua[i].n_chan * ua[i].n_time for i in range(n_plain))
+    plain_ms = plain_part_ms * samples / max(1, plain_samples)
+    res.update({"graph_ms": graph_ms, "direct_launch_ms": direct_ms,
+                "graph_Msamples_s": samples / graph_ms / 1e3,
+                "graph_GBs": 5 * samples / graph_ms / 1e6,
+                "graph_frac_of_measured_hbm": 5 * samples / graph_ms / 1e6 / peak,
+                "plain_per_unit_ms_scaled": plain_ms,
+                "plain_note": f"one launch per unit on the first {n_plain} units ({plain_part_ms:.0f} ms), "
+                              f"scaled by samples to all {len(ua)}",
+                "plain_vs_graph": plain_ms / graph_ms,
+                "units_refined_last_direct_launch": refine["units_refined"]})
+    del xa, xb, outs, masks
+    torch.cuda.empty_cache()
+    return res
+
+
+def leg_stokes(dev, n_subband=488, n_block=60, peak=6789.0, keep_units=8):
+    """Config 4: Stokes I float32, 488 subbands x 16 channels x 12288 samples
+    per block (chi-square(4) noise, a dispersed pulsar P = 0.714 s, DM 26.8,
+    narrowband and impulsive RFI): flag-kernel time of one block, and the
+    folded-profile S/N over n_block blocks for no flagging, a simple per-unit
+    5 sigma thresholder and the flagger.  Keeps block 0's first keep_units
+    subbands and their GPU masks for the float parity counts."""
+    import torch
+    from paper_1701_08197_gb300 import lof, quality, synth
+    t0 = time.perf_counter()
+    q = quality.evaluate(n_subband=n_subband, n_block=n_block, seed=4, device=str(dev))
+    tb = quality.time_block(n_subband, seed=4, reps=5, device=str(dev))
+    spec = synth.PulsarSpec(n_subband=keep_units)
+    x = synth.stokes_block(synth.PulsarSpec(n_subband=n_subband), seed=4, block=0, device=dev)[:keep_units]
+    x = x.contiguous()
+    mask = torch.empty(x.shape, dtype=torch.uint8, device=dev)
+    st = lof.stats_tensor(keep_units, dev)
+    with lof.Flagger(dev.index or 0) as fl:
+        fl.flag_block(lof.LOF_F32, [lof.make_unit(x[i], None, mask[i], -1, st[i]) for i in range(keep_units)], 0)
+        fl.status()
+    kept = {"x": x.cpu().numpy(), "mask": mask.cpu().numpy(), "stats": st.cpu().numpy()}
+    n = n_subband * spec.C * spec.T
+    res = {"workload": f"Stokes I f32 {n_subband} sb x 16 ch x 12288 t, {n_block} blocks, pulsar "
+                       f"P=0.714 s DM=26.8, seed 4",
+           "flag_kernel_ms": tb["ms"], "Msamples_s": tb["Msamples_s"], "GBs_9B_per_sample": tb["GBs_9B_per_sample"],
+           "frac_of_measured_hbm": tb["GBs_9B_per_sample"] / peak,
+           "folded_snr": {k: v["snr"] for k, v in q.items()},
+           "flagged_fraction": {k: v["flagged_fraction"] for k, v in q.items()},
+           "samples_per_block": n, "wall_s": time.perf_counter() - t0}
+    return res, kept
+
+
+def leg_serving(dev, n_streams=32, n_blocks=3, budget_gb=2.0):
+    """Config 5: 32 concurrent complex int8 streams (1-16 stations x 2 pols x
+    64-384 channels x 1024-8192 samples, seed 5) arriving every 1 s with
+    +-100 ms jitter, admitted by a device-memory budget, continuously batched;
+    p50/p99 block latency against the 1 s deadline."""
+    from paper_1701_08197_gb300 import serve
+    streams = serve.make_streams(n_streams)
+    srv, wall = serve.run(streams, n_blocks, int(budget_gb * 2 ** 30), accelerated=False,
+                          gen_device=str(dev))
+    rep = serve.report(srv, wall)
+    srv.close()
+    rep.update({"workload": f"{n_streams} streams x {n_blocks} blocks, real-time 1 s cadence +-100 ms, "
+                            f"device budget {budget_gb} GB", "wall_s": wall})
+    return rep
+
+
+def float_parity_counts(kept):
+    """Config 4 sample on the host cores: the oracle on the kept Stokes I
+    subbands against the GPU masks, with the binary64 replay's near-threshold
+    and cascade counts (the float contract)."""
+    import numpy as np
+
+    import oracle
+    sys.path.insert(0, os.path.join(ROOT, "tests"))
+    from float_parity import allowed_differences
+    from paper_1701_08197_gb300 import lof
+    P = oracle.default_params()
+    tot = {"units": 0, "samples": 0, "differing": 0, "near_threshold_count": 0, "cascade_count": 0,
+           "outside_allowed": 0}
+    for i in range(kept["x"].shape[0]):
+        x = kept["x"][i]
+        ref = oracle.flag_unit(P, x)
+        entry = ~np.isfinite(x)
+        allowed, _, nn, nc = allowed_differences(P, np.where(entry, 0.0, x.astype(np.float64)), entry,
+                                                 ref["stats"])
+        diff = kept["mask"][i] != ref["mask"]
+        tot["units"] += 1
+        tot["samples"] += int(x.size)
+        tot["differing"] += int(diff.sum())
+        tot["near_threshold_count"] += nn
+        tot["cascade_count"] += nc
+        tot["outside_allowed"] += int((diff & ~allowed).sum())
+    return tot
 
 
 def oracle_sample(seconds: float, seed=2, sir=0, integrated=False, scope=False, sigma="mad", grid=None,
@@ -562,7 +744,14 @@ def main():
         "note": "block 0 after block 1 and block 1 after block 0: units whose pooled median/MAD "
                 "needed a refinement pass beyond the first counting pass (the previous block's "
                 "statistics as hints)" if not args.same_block else "same block every step"}
+    if "legs" in res:
+        line["configs"] = res["legs"]
     if not args.no_cpu:
+        if "stokes_kept" in res:
+            try:
+                line["configs"]["config4_stokes"]["float_parity"] = float_parity_counts(res["stokes_kept"])
+            except Exception as e:
+                line["configs"]["config4_stokes"]["float_parity"] = {"error": f"{type(e).__name__}: {e}"}
         opts = dict(sir=args.sir, integrated=args.integrated, scope=args.channel_scope, sigma=args.sigma,
                     grid=args.grid)
         cb = oracle_sample(args.cpu_seconds * 0.7, **opts)

@@ -204,9 +204,15 @@ int lof_flag_block(lof_ctx *ctx, int dtype, const lof_unit *units, int n_units,
 /* Same operation with HOST buffers: in/out/mask/stats of every unit are host
  * pointers (pinned memory gives asynchronous copies).  Inputs are copied to
  * context-owned device staging memory, flagged, and out/mask/stats copied
- * back, all on cuda_stream; the call returns after enqueueing (synchronise the
- * stream before reading the results).  Host buffers must stay valid until
- * then. */
+ * back.  The units are taken in up to 8 chunks of whole units: a chunk's
+ * uploads run on an internal copy stream, its flag launch on cuda_stream
+ * (after those uploads) and its downloads on a second internal copy stream
+ * (after that launch), so the copies of neighbouring chunks overlap the
+ * kernel.  Rows that are contiguous in host memory move as one copy.  The
+ * copies start after the work already queued on cuda_stream, and cuda_stream
+ * waits for the last download: the call returns after enqueueing, and
+ * synchronising cuda_stream covers all of it.  Host buffers must stay valid
+ * until then. */
 int lof_flag_block_host(lof_ctx *ctx, int dtype, const lof_unit *units, int n_units,
                         uint64_t block_seq, void *cuda_stream);
 

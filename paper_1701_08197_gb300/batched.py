@@ -17,23 +17,29 @@ import torch
 from . import lof, synth
 
 
-def build(n_subband=61, n_station=48, seed=3, device="cuda:0"):
-    """Device tensors of the block: per subband one [S, 2, C, T, 2] int8 tensor."""
+def build(n_subband=61, n_station=48, seed=3, device="cuda:0", block=0):
+    """Device tensors of one block: per subband one [S, 2, C, T, 2] int8 tensor
+    (the shapes depend on the seed only, the samples on the block index too)."""
     shapes = synth.random_units(n_subband, (16, 64, 256), (768, 3072, 12288), seed=seed)
     xs = []
     for b, (C, T) in enumerate(shapes):
         spec = synth.VoltageSpec(n_station=n_station, n_pol=2, n_subband=1, C=C, T=T,
                                  dtype=torch.int8, sigma=8.0, tone_frac=0.02, impulse_frac=0.01)
-        xs.append(synth.voltage_block(spec, seed=synth._mix(seed, b), block=0, device=device)[:, :, 0])
+        xs.append(synth.voltage_block(spec, seed=synth._mix(seed, b), block=block, device=device)[:, :, 0])
     return xs
 
 
-def units_of(xs, outs, masks):
+def units_of(xs, outs, masks, history=False):
+    """Descriptors of every station x pol of every subband; with history,
+    each unit owns its channels' history slots (consecutive), so the
+    statistics of one block serve as hints for the next."""
     out = []
+    slot = 0
     for x, o, m in zip(xs, outs, masks):
         for s in range(x.shape[0]):
             for p in range(2):
-                out.append(lof.make_unit(x[s, p], o[s, p], m[s, p]))
+                out.append(lof.make_unit(x[s, p], o[s, p], m[s, p], slot if history else -1))
+                slot += x.shape[2]
     return out
 
 

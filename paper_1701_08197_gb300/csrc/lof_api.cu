@@ -28,6 +28,7 @@ namespace {
 thread_local char g_create_error[512];
 
 constexpr int kStageRing = 4;
+constexpr int kHostChunks = 8;  // pipeline depth of lof_flag_block_host
 
 int esize_of(int dtype) {
   switch (dtype) {
@@ -85,9 +86,13 @@ struct lof_ctx {
   size_t cap_stage[kStageRing] = {};
   cudaEvent_t ev_stage[kStageRing] = {};
   int stage_next = 0;
-  // device staging for lof_flag_block_host
+  // device staging for lof_flag_block_host, its two copy streams and the
+  // events that chain them with the caller's stream (created on first use)
   uint8_t* d_io = nullptr;
   size_t cap_io = 0;
+  cudaStream_t s_up = nullptr, s_down = nullptr;
+  cudaEvent_t ev_start = nullptr, ev_down_done = nullptr;
+  cudaEvent_t ev_in[kHostChunks] = {}, ev_flag[kHostChunks] = {};
   std::string last_error;
 };
 
@@ -337,6 +342,14 @@ extern "C" int lof_destroy(lof_ctx* c) {
   cudaFree(c->d_gen);
   cudaFree(c->d_ctrl);
   cudaFree(c->d_io);
+  if (c->s_up) cudaStreamDestroy(c->s_up);
+  if (c->s_down) cudaStreamDestroy(c->s_down);
+  if (c->ev_start) cudaEventDestroy(c->ev_start);
+  if (c->ev_down_done) cudaEventDestroy(c->ev_down_done);
+  for (int i = 0; i < kHostChunks; ++i) {
+    if (c->ev_in[i]) cudaEventDestroy(c->ev_in[i]);
+    if (c->ev_flag[i]) cudaEventDestroy(c->ev_flag[i]);
+  }
   if (c->h_err) cudaFreeHost(c->h_err);
   for (int i = 0; i < kStageRing; ++i) {
     if (c->h_stage[i]) cudaFreeHost(c->h_stage[i]);
@@ -899,6 +912,59 @@ extern "C" int lof_flag_block(lof_ctx* c, int dtype, const lof_unit* units, int 
   return flag_block_device(c, dtype, units, n_units, block_seq, cuda_stream);
 }
 
+namespace {
+
+// One host<->device copy of a run of rows: 1-D when both sides are compact
+// (consecutive units that are contiguous on both sides merge into one copy),
+// else 2-D.
+struct HostCopy {
+  void* dst;
+  const void* src;
+  size_t dpitch, spitch, width, rows;
+};
+
+void add_copy(std::vector<HostCopy>& v, void* dst, size_t dpitch, const void* src, size_t spitch,
+              size_t width, size_t rows) {
+  if (dpitch == width && spitch == width) {  // compact: one run of rows * width bytes
+    width *= rows;
+    dpitch = spitch = width;
+    rows = 1;
+  }
+  if (!v.empty() && rows == 1 && v.back().rows == 1 &&
+      static_cast<const uint8_t*>(v.back().dst) + v.back().width == dst &&
+      static_cast<const uint8_t*>(v.back().src) + v.back().width == src) {
+    v.back().width += width;  // contiguous on both sides: extend the previous copy
+    v.back().dpitch = v.back().spitch = v.back().width;
+    return;
+  }
+  v.push_back(HostCopy{dst, src, dpitch, spitch, width, rows});
+}
+
+cudaError_t run_copies(const std::vector<HostCopy>& v, cudaMemcpyKind kind, cudaStream_t st) {
+  for (const HostCopy& c : v) {
+    const cudaError_t e = c.rows == 1 ? cudaMemcpyAsync(c.dst, c.src, c.width, kind, st)
+                                      : cudaMemcpy2DAsync(c.dst, c.dpitch, c.src, c.spitch, c.width,
+                                                          c.rows, kind, st);
+    if (e != cudaSuccess) return e;
+  }
+  return cudaSuccess;
+}
+
+int host_path_streams(lof_ctx* c) {
+  if (c->s_up) return LOF_OK;
+  cudaError_t e = cudaStreamCreateWithFlags(&c->s_up, cudaStreamNonBlocking);
+  if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&c->s_down, cudaStreamNonBlocking);
+  if (e == cudaSuccess) e = cudaEventCreateWithFlags(&c->ev_start, cudaEventDisableTiming);
+  if (e == cudaSuccess) e = cudaEventCreateWithFlags(&c->ev_down_done, cudaEventDisableTiming);
+  for (int i = 0; i < kHostChunks && e == cudaSuccess; ++i) {
+    e = cudaEventCreateWithFlags(&c->ev_in[i], cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&c->ev_flag[i], cudaEventDisableTiming);
+  }
+  return e == cudaSuccess ? LOF_OK : cuda_fail(c, e, "host-path streams");
+}
+
+}  // namespace
+
 extern "C" int lof_flag_block_host(lof_ctx* c, int dtype, const lof_unit* units, int n_units,
                                    uint64_t block_seq, void* cuda_stream) {
   if (!c) return fail(nullptr, LOF_ERR_INVALID, "lof_flag_block_host: ctx is NULL");
@@ -907,6 +973,7 @@ extern "C" int lof_flag_block_host(lof_ctx* c, int dtype, const lof_unit* units,
   if (rc) return rc;
   if ((rc = validate_units(c, dtype, units, n_units))) return rc;
   if (n_units == 0) return LOF_OK;
+  if ((rc = host_path_streams(c))) return rc;
   const int es = esize_of(dtype);
   // device staging: compact [C][T] input, output and mask, plus stats
   size_t need = 0;
@@ -919,9 +986,12 @@ extern "C" int lof_flag_block_host(lof_ctx* c, int dtype, const lof_unit* units,
     if (units[i].out && units[i].out != units[i].in) need += round_up64(n * es, 256);
     off_mask[i] = need;
     if (units[i].mask) need += round_up64(n, 256);
-    off_st[i] = need;
-    if (units[i].stats) need += round_up64(sizeof(lof_unit_stats), 256);
   }
+  // statistics records of all units side by side (one download when the
+  // caller's records are contiguous too)
+  for (int i = 0; i < n_units; ++i) off_st[i] = need + static_cast<size_t>(i) * sizeof(lof_unit_stats);
+  need += round_up64(static_cast<size_t>(n_units) * sizeof(lof_unit_stats), 256);
+  cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
   if (need > c->cap_io) {
     if (c->d_io) {
       cudaError_t e = cudaDeviceSynchronize();
@@ -934,15 +1004,10 @@ extern "C" int lof_flag_block_host(lof_ctx* c, int dtype, const lof_unit* units,
     if (e != cudaSuccess) return fail(c, LOF_ERR_NOMEM, "host-path staging %zu B: %s", need, cudaGetErrorString(e));
     c->cap_io = need;
   }
-  cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
   std::vector<lof_unit> du(units, units + n_units);
   for (int i = 0; i < n_units; ++i) {
     const lof_unit& u = units[i];
-    const size_t rowb = static_cast<size_t>(u.n_time) * es;
     uint8_t* din = c->d_io + off_in[i];
-    cudaError_t e = cudaMemcpy2DAsync(din, rowb, u.in, static_cast<size_t>(u.in_row_stride) * es, rowb,
-                                      u.n_chan, cudaMemcpyHostToDevice, st);
-    if (e != cudaSuccess) return cuda_fail(c, e, "host input copy");
     du[i].in = din;
     du[i].in_row_stride = u.n_time;
     if (u.out) {
@@ -955,22 +1020,68 @@ extern "C" int lof_flag_block_host(lof_ctx* c, int dtype, const lof_unit* units,
     }
     if (u.stats) du[i].stats = reinterpret_cast<lof_unit_stats*>(c->d_io + off_st[i]);
   }
-  rc = flag_block_device(c, dtype, du.data(), n_units, block_seq, cuda_stream);
-  if (rc) return rc;
+  // Chunks of whole units by input bytes: chunk g's uploads (stream s_up),
+  // its flag launch (the caller's stream, after the uploads) and its
+  // downloads (stream s_down, after the launch) overlap with the neighbouring
+  // chunks' steps.  The copy streams first wait for the caller's earlier work
+  // (the staging may still be in use), and the caller's stream ends waiting
+  // for the last download, so synchronising it covers the whole call.
+  size_t total_in = 0;
+  for (int i = 0; i < n_units; ++i) total_in += static_cast<size_t>(units[i].n_chan) * units[i].n_time * es;
+  const size_t target = std::max<size_t>(size_t(64) << 20, (total_in + kHostChunks - 1) / kHostChunks);
+  std::vector<int> cut{0};
+  size_t acc = 0;
   for (int i = 0; i < n_units; ++i) {
-    const lof_unit& u = units[i];
-    const size_t rowb = static_cast<size_t>(u.n_time) * es;
-    cudaError_t e = cudaSuccess;
-    if (u.out)
-      e = cudaMemcpy2DAsync(u.out, static_cast<size_t>(u.out_row_stride) * es, du[i].out, rowb, rowb,
-                            u.n_chan, cudaMemcpyDeviceToHost, st);
-    if (e == cudaSuccess && u.mask)
-      e = cudaMemcpy2DAsync(u.mask, static_cast<size_t>(u.mask_row_stride), du[i].mask, u.n_time,
-                            u.n_time, u.n_chan, cudaMemcpyDeviceToHost, st);
-    if (e == cudaSuccess && u.stats)
-      e = cudaMemcpyAsync(u.stats, du[i].stats, sizeof(lof_unit_stats), cudaMemcpyDeviceToHost, st);
-    if (e != cudaSuccess) return cuda_fail(c, e, "host output copy");
+    acc += static_cast<size_t>(units[i].n_chan) * units[i].n_time * es;
+    if (acc >= target && i + 1 < n_units && static_cast<int>(cut.size()) < kHostChunks) {
+      cut.push_back(i + 1);
+      acc = 0;
+    }
   }
+  cut.push_back(n_units);
+  const int nchunk = static_cast<int>(cut.size()) - 1;
+  cudaError_t e = cudaEventRecord(c->ev_start, st);
+  if (e == cudaSuccess) e = cudaStreamWaitEvent(c->s_up, c->ev_start, 0);
+  if (e == cudaSuccess) e = cudaStreamWaitEvent(c->s_down, c->ev_start, 0);
+  if (e != cudaSuccess) return cuda_fail(c, e, "host path: stream order");
+  for (int g = 0; g < nchunk; ++g) {
+    std::vector<HostCopy> up;
+    for (int i = cut[g]; i < cut[g + 1]; ++i) {
+      const lof_unit& u = units[i];
+      const size_t rowb = static_cast<size_t>(u.n_time) * es;
+      add_copy(up, const_cast<void*>(du[i].in), rowb, u.in, static_cast<size_t>(u.in_row_stride) * es, rowb,
+               u.n_chan);
+    }
+    if ((e = run_copies(up, cudaMemcpyHostToDevice, c->s_up)) != cudaSuccess ||
+        (e = cudaEventRecord(c->ev_in[g], c->s_up)) != cudaSuccess)
+      return cuda_fail(c, e, "host input copy");
+  }
+  for (int g = 0; g < nchunk; ++g) {
+    if ((e = cudaStreamWaitEvent(st, c->ev_in[g], 0)) != cudaSuccess) return cuda_fail(c, e, "host path: stream order");
+    rc = flag_block_device(c, dtype, du.data() + cut[g], cut[g + 1] - cut[g], block_seq, cuda_stream);
+    if (rc) return rc;
+    if ((e = cudaEventRecord(c->ev_flag[g], st)) != cudaSuccess ||
+        (e = cudaStreamWaitEvent(c->s_down, c->ev_flag[g], 0)) != cudaSuccess)
+      return cuda_fail(c, e, "host path: stream order");
+    std::vector<HostCopy> down, down_mask, down_st;
+    for (int i = cut[g]; i < cut[g + 1]; ++i) {
+      const lof_unit& u = units[i];
+      const size_t rowb = static_cast<size_t>(u.n_time) * es;
+      if (u.out) add_copy(down, u.out, static_cast<size_t>(u.out_row_stride) * es, du[i].out, rowb, rowb, u.n_chan);
+      if (u.mask)
+        add_copy(down_mask, u.mask, static_cast<size_t>(u.mask_row_stride), du[i].mask, u.n_time, u.n_time,
+                 u.n_chan);
+      if (u.stats) add_copy(down_st, u.stats, sizeof(lof_unit_stats), du[i].stats, sizeof(lof_unit_stats),
+                            sizeof(lof_unit_stats), 1);
+    }
+    if ((e = run_copies(down, cudaMemcpyDeviceToHost, c->s_down)) != cudaSuccess ||
+        (e = run_copies(down_mask, cudaMemcpyDeviceToHost, c->s_down)) != cudaSuccess ||
+        (e = run_copies(down_st, cudaMemcpyDeviceToHost, c->s_down)) != cudaSuccess)
+      return cuda_fail(c, e, "host output copy");
+  }
+  if ((e = cudaEventRecord(c->ev_down_done, c->s_down)) != cudaSuccess ||
+      (e = cudaStreamWaitEvent(st, c->ev_down_done, 0)) != cudaSuccess)
+    return cuda_fail(c, e, "host path: stream order");
   return LOF_OK;
 }
 

@@ -16,12 +16,13 @@ constexpr int kMaxLogWindow = 6;             // windows 1 .. 64
 constexpr int kKTable = 134;                 // sum_{k=0..6} (2^k + 1) threshold entries
 constexpr int kMaxChan = 2048;               // channels per unit
 constexpr int kMaxRowsPerTask = 64;          // rows of one unit in one task
-constexpr int kMaxTargets = 32;              // bins refined per selection round
-constexpr int kMaxFine = 2048;               // counters per refinement round (upper bound)
-constexpr int kMaxSpec = 1024;               // exact counters near the previous block's statistics
+constexpr int kMaxTargets = 128;             // bins refined per selection round (and hinted bins)
+constexpr int kMaxFine = 4096;               // counters per refinement round (upper bound)
+constexpr int kMaxSpec = 4096;               // exact counters near the previous block's statistics
+constexpr int kSpecHalf = 682;               // largest half-width of one hinted window (3 fit kMaxSpec)
 constexpr int kSelCap = 2048;                // bin-list capacity for exact selection
 constexpr int kMaxRounds = 12;               // refinement rounds before giving up
-constexpr int kWorkspaceBytes = 36 * 1024;   // last-arriver workspace (overlays the prefix buffer)
+constexpr int kWorkspaceBytes = 56 * 1024;   // last-arriver workspace (overlays the prefix buffer)
 constexpr int kCtrlWords = 8;               // control words of a launch (see Scratch::ctrl)
 
 // device error codes (written to the context's mapped error word)

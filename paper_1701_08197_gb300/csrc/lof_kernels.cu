@@ -351,31 +351,54 @@ __device__ __forceinline__ Target ld_target(const Target* p) {
   return Target{v.x, v.y, v.z, v.w};
 }
 
-// Coarse bins around the previous block's median and MAD end points (+-1/32
-// of each value), to be counted value by value while the stats tasks run.
-// Deterministic in (m2, mad4): every task of a unit derives the same list.
-// Returns the number of targets (bins, each refined to width 1).
+// Coarse bins around the previous block's median and MAD end points, to be
+// counted value by value while the stats tasks run.  For each point p of
+// m - d, m, m + d (d = MAD) the bins overlapping [p - w, p + w] with
+// w = max(2, d / 4, p / 32), at most kSpecHalf: between blocks the pooled
+// median and MAD move by a fraction of d (a burst that covers a few percent
+// of a unit's samples shifts them by about a tenth of d), so the order
+// statistics normally land inside these bins and round 1 resolves them.
+// Bins in increasing order, none twice; the list stops where kMaxSpec
+// counters or kMaxTargets bins are used.  Deterministic in (m2, mad4): every
+// task of a unit derives the same list.  One whole warp; returns the number
+// of bins in every lane.
 __device__ int spec_targets(unsigned long long m2, unsigned long long mad4, Target* tg) {
+  const int lane = threadIdx.x & 31;
   if (m2 == ~0ull) return 0;
   const long long m = static_cast<long long>(m2 >> 1), d = static_cast<long long>(mad4 >> 2);
   const long long P[3] = {m - d, m, m + d};
   int nt = 0;
   uint32_t base = 0;
+  long long last_hi = -1;  // highest value covered so far
   for (int i = 0; i < 3; ++i) {
-    long long p = P[i] < 0 ? 0 : P[i];
+    const long long p = P[i] < 0 ? 0 : P[i];
     if (p > 0xFFFFFFFFll) break;
-    const long long del = p / 32 > 2 ? p / 32 : 2;
+    long long del = max(2ll, max(d / 4, p / 32));
+    if (del > kSpecHalf) del = kSpecHalf;
     const long long a = p - del < 0 ? 0 : p - del;
     const long long b = p + del > 0xFFFFFFFFll ? 0xFFFFFFFFll : p + del;
     const uint32_t k0 = coarse_key(static_cast<uint32_t>(a)), k1 = coarse_key(static_cast<uint32_t>(b));
-    for (uint32_t k = k0; k <= k1; ++k) {
-      uint32_t lo, hi;
-      if (!key_range(k, &lo, &hi)) continue;
-      if (nt > 0 && tg[nt - 1].lo >= lo) continue;
-      const uint32_t w = hi - lo + 1u;
-      if (base + w > static_cast<uint32_t>(kMaxSpec) || nt == kMaxTargets) return nt;
-      tg[nt++] = Target{lo, hi, 0u, base};
-      base += w;
+    for (uint32_t kb = k0; kb <= k1; kb += kWarp) {
+      const uint32_t k = kb + lane;
+      uint32_t lo = 0, hi = 0;
+      const bool ok = k <= k1 && key_range(k, &lo, &hi) && static_cast<long long>(lo) > last_hi;
+      const uint32_t w = ok ? hi - lo + 1u : 0u;
+      uint32_t tot;
+      const uint32_t ex = warp_excl_scan(w, lane, &tot);
+      const unsigned okb = __ballot_sync(0xFFFFFFFFu, ok);
+      const int rank = __popc(okb & ((1u << lane) - 1u));
+      // the ok lanes in order: a prefix of them fits (widths are positive)
+      const bool fits = ok && base + ex + w <= static_cast<uint32_t>(kMaxSpec) && nt + rank < kMaxTargets;
+      if (fits) tg[nt + rank] = Target{lo, hi, 0u, base + ex};
+      const unsigned fb = __ballot_sync(0xFFFFFFFFu, fits);
+      const int nfit = __popc(fb);
+      if (nfit > 0) {
+        const int top = 31 - __clz(static_cast<int>(fb));
+        last_hi = static_cast<long long>(__shfl_sync(0xFFFFFFFFu, hi, top));
+        base += __shfl_sync(0xFFFFFFFFu, ex + w, top);
+      }
+      nt += nfit;
+      if (nfit < __popc(okb)) return nt;  // full
     }
   }
   return nt;
@@ -1443,6 +1466,12 @@ __device__ __forceinline__ void wr_apply(WrRow<NPL>& R, int lane, int nvalid, in
     const uint32_t vm = nv >= 32 ? kFull : (nv <= 0 ? 0u : ((1u << nv) - 1u));
     F[w] &= vm;
   }
+  {
+    uint32_t anyf = 0u;
+#pragma unroll
+    for (int w = 0; w < NW; ++w) anyf |= F[w];
+    if (!__any_sync(kFull, anyf != 0u)) return;  // no window of this size fired
+  }
   // the two fire words just before the lane's first word
   uint32_t p1, p2;
   if constexpr (NW == 1) {
@@ -1682,6 +1711,295 @@ __device__ __forceinline__ void wr_finish(const WrRow<NPL>& R, const WrSeg& g, i
 // cut into overlapping segments).
 constexpr int kWrNpl = 32;
 
+// ------------------------------------------------------------------ warp-row pass, fixed encoding
+// The same pass with one flagged value for every window size: a flagged
+// sample is stored as uf = 64 c + 1 (c >= 0 an integer of the unit), an
+// unflagged one as power << 6.  The low-bit sum of a window of I <= 32
+// values is then S = 64 (s + n c) + n for n flagged samples and an
+// unflagged sum s, and the window fires (s > K[n]) exactly when
+// S > 64 (K[n] + n c) + 63, a table read with the sum's low five bits as
+// before.  With c at least every slope (K[0] - K[n]) / n of the windows of
+// 8 to 64 samples, Bt = min_n (K[n] + n c) equals K[0], and a bound needs no
+// table: s + n c grows with every sample added, so when the summed union of
+// the windows that start in a block stays at or below 64 Bt + 63 none of
+// them fires.  Only the block slots where some lane exceeds the bound run the
+// exact test.
+//
+// Table layout (uint32 s_Kp): entries koffset(k) + n as before (k = 0:
+// floor(threshold_1); k = 1..5: 64 (K[n] + n c) + 63; k = 6: n Z + K[n]),
+// then at kKbOff + 2k the bound of window size 2^k (k = 3..5: 64 Bt + 63;
+// k = 6: Bt), and c and uf at kKcOff.
+constexpr int kKcOff = kKbOff + 2 * 7;
+constexpr int kKpWords = kKcOff + 2;
+
+// The fixed-encoding tables from a unit's integer table K (kKTable
+// entries), for window sizes up to 2^kmax; whole CTA, ends with a barrier.
+// Returns true when the unit's values fit the packed form (else the general
+// path runs).
+template <int NT>
+__device__ bool fill_packed_tables(const long long* K, int kmax, uint32_t* s_Kp, int* s_c) {
+  const int tid = threadIdx.x;
+  const long long K1 = K[0];
+  if (tid < kWarp) {
+    // c = the largest slope ceil((K[0] - K[n]) / n) of the windows 8..64,
+    // at most floor(threshold_1)
+    long long c = 0;
+    for (int k = 3; k <= kmax; ++k) {
+      const int I = 1 << k;
+      const long long* Kt = K + koffset(k);
+      for (int n = 1 + tid; n <= I; n += kWarp) {
+        const long long d = Kt[0] - Kt[n];
+        c = max(c, (d + n - 1) / n);
+      }
+    }
+    for (int o = 16; o > 0; o >>= 1) c = max(c, __shfl_xor_sync(0xFFFFFFFFu, c, o));
+    if (tid == 0) *s_c = static_cast<int>(min(max(c, 0ll), max(K1, 0ll) < (1ll << 20) ? max(K1, 0ll) : 0ll));
+  }
+  __syncthreads();
+  const long long c = *s_c;
+  bool bad = K1 < 0 || K1 >= (1ll << 20);
+  const int total = koffset(kmax + 1);
+  for (int e = tid; e < total; e += NT) {
+    int k = 0;
+    while (koffset(k + 1) <= e) ++k;
+    const int n = e - koffset(k);
+    const long long* Kt = K + koffset(k);
+    if (Kt[n] < 0 || Kt[n] >= static_cast<long long>(kZ)) bad = true;
+    if (k == 0) {
+      s_Kp[e] = static_cast<uint32_t>(Kt[n]);
+    } else if (k <= 5) {
+      const long long v = Kt[n] + n * c;  // 64 v + 63 < 2^31
+      if (v >= (1ll << 25)) bad = true;
+      s_Kp[e] = (static_cast<uint32_t>(v) << kLowShift) + 63u;
+    } else {
+      s_Kp[e] = static_cast<uint32_t>(n) * kZ + static_cast<uint32_t>(Kt[n]);
+    }
+  }
+  if (tid >= 3 && tid <= kmax) {
+    const int k = tid, I = 1 << k;
+    const long long* Kt = K + koffset(k);
+    long long m = Kt[0];
+    for (int n = 1; n <= I; ++n) m = min(m, Kt[n] + n * c);
+    m = min(max(m, 0ll), (1ll << 25) - 1);
+    s_Kp[kKbOff + 2 * k] = k <= 5 ? (static_cast<uint32_t>(m) << kLowShift) + 63u : static_cast<uint32_t>(m);
+  }
+  if (tid == 0) {
+    s_Kp[kKcOff] = static_cast<uint32_t>(c);
+    s_Kp[kKcOff + 1] = (static_cast<uint32_t>(c) << kLowShift) | 1u;
+  }
+  return __syncthreads_or(bad) == 0;
+}
+
+// Loads the lane's staged samples as powers, flags those above K1 (the I = 1
+// pass) and stores them as uf, the others as power << 6.
+template <int DT, int NPL>
+__device__ __forceinline__ void wr_build_c(WrRow<NPL>& R, const uint8_t* srow, uint32_t K1, uint32_t uf) {
+  constexpr int VS = Traits<DT>::kVec, NV = NPL / VS;
+  uint4 v[NV];
+#pragma unroll
+  for (int q = 0; q < NV; ++q) v[q] = *reinterpret_cast<const uint4*>(srow + 16 * q);
+#pragma unroll
+  for (int w = 0; w < NPL / 32; ++w) R.M[w] = 0u;
+#pragma unroll
+  for (int j = 0; j < NPL; ++j) {
+    const uint32_t uu = raw_pw<DT>(v[j / VS], j % VS);
+    const bool fl = uu > K1;
+    R.u[j] = fl ? uf : (uu << kLowShift);
+    if (fl) R.M[j >> 5] |= 1u << (j & 31);
+  }
+}
+
+// Block b of the lane (sum of B consecutive values), blocks past the lane's
+// last from the next lane by shuffle.
+template <int NB>
+__device__ __forceinline__ uint32_t wr_bat(const uint32_t (&Q)[NB], int b) {
+  if (b < NB) return Q[b];
+  return __shfl_down_sync(kFull, Q[b - NB], 1);
+}
+
+// Fire words for windows of I = 8, 16, 32 samples: the block bound, then the
+// exact table test on the block slots where some lane's union exceeds it.
+template <int NPL, int I, int B>
+__device__ __forceinline__ void wr_fire_blk(const WrRow<NPL>& R, int lane, const uint32_t* Kp,
+                                            uint32_t Vthr, uint32_t (&F)[NPL / 32]) {
+  static_assert(NPL == 32 && I <= 32 && B >= 2 && I % B == 0 && I / B <= NPL / B, "block bound");
+  constexpr int NB = NPL / B, D = I / B;
+  uint32_t Q[NB];
+#pragma unroll
+  for (int b = 0; b < NB; ++b) {
+    uint32_t s = 0u;
+#pragma unroll
+    for (int i = 0; i < B; ++i) s += R.u[B * b + i];
+    Q[b] = s;
+  }
+  // V(b) = sum of blocks b .. b + D (unsigned: at most 36 values < 2^26)
+  uint32_t A = 0u;
+#pragma unroll
+  for (int k = 0; k < D; ++k) A += Q[k];
+  uint32_t V = Q[NB - 1] + __shfl_down_sync(kFull, A, 1);
+  uint32_t cand = 0u;
+#pragma unroll
+  for (int b = NB - 1; b >= 0; --b) {
+    cand |= (V > Vthr ? 1u : 0u) << b;
+    if (b > 0) V = V + Q[b - 1] - wr_bat<NB>(Q, b + D);
+  }
+  const uint32_t any = __reduce_or_sync(kFull, cand);
+  uint32_t f = 0u;
+  if (any) {
+    const uint32_t Kreg = Kp[lane < I ? lane : I];
+#pragma unroll
+    for (int b = 0; b < NB; ++b) {
+      if (!((any >> b) & 1u)) continue;
+      // window sum at B b: blocks b .. b + D - 1
+      uint32_t own = 0u, nxt = 0u;
+#pragma unroll
+      for (int k = b; k < b + D && k < NB; ++k) own += Q[k];
+      if (b + D > NB) {
+#pragma unroll
+        for (int k = 0; k < b + D - NB; ++k) nxt += Q[k];
+        nxt = __shfl_down_sync(kFull, nxt, 1);
+      }
+      uint32_t S = own + nxt, bits = 0u;
+#pragma unroll
+      for (int i = 0; i < B; ++i) {
+        bits |= ((__shfl_sync(kFull, Kreg, S) - S) >> 31) << i;
+        if (i < B - 1) S = S - R.u[B * b + i] + wr_uat<NPL>(R, lane, B * b + i + I);
+      }
+      f |= bits << (B * b);
+    }
+  }
+  F[0] = f;
+}
+
+// Windows of 64 samples under the fixed encoding: the same bound on block
+// sums of four (s + n c = q >> 6), exact test in the n Z + s form.
+template <int NPL>
+__device__ __forceinline__ void wr_fire_pf64c(const WrRow<NPL>& R, int lane, const uint32_t* Kp,
+                                              uint32_t Bt, uint32_t zc, uint32_t (&F)[NPL / 32]) {
+  static_assert(NPL == 32, "one flag word per lane");
+  constexpr int I = 64, NB = NPL / 4, D = I / 4;
+  uint32_t Q[NB], X[NB];
+#pragma unroll
+  for (int b = 0; b < NB; ++b) {
+    Q[b] = R.u[4 * b] + R.u[4 * b + 1] + R.u[4 * b + 2] + R.u[4 * b + 3];
+    X[b] = Q[b] >> kLowShift;
+  }
+  uint32_t A = 0u;
+#pragma unroll
+  for (int k = 0; k < NB; ++k) A += X[k];
+  uint32_t V = X[NB - 1] + __shfl_down_sync(kFull, A, 1) + __shfl_down_sync(kFull, A, 2);
+  uint32_t cand = 0u;
+#pragma unroll
+  for (int b = NB - 1; b >= 0; --b) {
+    cand |= (V > Bt ? 1u : 0u) << b;
+    if (b > 0) V = V + X[b - 1] - wr_qat<NB>(X, b + D);
+  }
+  const uint32_t any = __reduce_or_sync(kFull, cand);
+  uint32_t f = 0u;
+  if (any) {
+    auto zq = [zc](uint32_t q) { return (q >> kLowShift) + (q & 63u) * zc; };
+    auto zu = [zc](uint32_t v) { return (v >> kLowShift) + (v & 1u) * zc; };
+#pragma unroll
+    for (int b = 0; b < NB; ++b) {
+      if (!((any >> b) & 1u)) continue;
+      uint32_t own = 0u, p1 = 0u, p2 = 0u;
+#pragma unroll
+      for (int i = b; i < b + D && i < NB; ++i) own += zq(Q[i]);
+      if (b + D > NB) {
+#pragma unroll
+        for (int i = 0; i < b + D - NB && i < NB; ++i) p1 += zq(Q[i]);
+        p1 = __shfl_down_sync(kFull, p1, 1);
+      }
+      if (b + D > 2 * NB) {
+#pragma unroll
+        for (int i = 0; i < b + D - 2 * NB; ++i) p2 += zq(Q[i]);
+        p2 = __shfl_down_sync(kFull, p2, 2);
+      }
+      uint32_t S = own + p1 + p2, bits = 0u;
+#pragma unroll
+      for (int i = 0; i < 4; ++i) {
+        bits |= ((Kp[S >> 26] - S) >> 31) << i;
+        if (i < 3) S = S - zu(R.u[4 * b + i]) + zu(wr_uat<NPL>(R, lane, 4 * b + i + I));
+      }
+      f |= bits << (4 * b);
+    }
+  }
+  F[0] = f;
+}
+
+// Dilation and update of wr_apply, skipped when no window of the level
+// fired in the warp; new flags are stored as uf.
+template <int NPL>
+__device__ __forceinline__ void wr_apply_c(WrRow<NPL>& R, int lane, int nvalid, int I, uint32_t uf,
+                                           uint32_t (&F)[NPL / 32]) {
+  static_assert(NPL == 32, "one flag word per lane");
+  const uint32_t vm = nvalid >= 32 ? kFull : (nvalid <= 0 ? 0u : ((1u << nvalid) - 1u));
+  F[0] &= vm;
+  if (!__any_sync(kFull, F[0] != 0u)) return;
+  uint32_t p1 = __shfl_up_sync(kFull, F[0], 1);
+  uint32_t p2 = __shfl_up_sync(kFull, F[0], 2);
+  if (lane < 1) p1 = 0u;
+  if (lane < 2) p2 = 0u;
+  const uint32_t Dw = (I <= 32) ? dilate32(F[0], p1, I) : (dilate32(F[0], p1, 32) | dilate32(p1, p2, 32));
+  const uint32_t nw = Dw & ~R.M[0];
+  R.M[0] |= nw;
+  if (!__any_sync(kFull, nw != 0u)) return;
+#pragma unroll
+  for (int j = 0; j < NPL; ++j)
+    if ((nw >> j) & 1u) R.u[j] = uf;
+}
+
+// Window sizes 2^k, k0 <= k <= k1, of the fixed-encoding pass.
+template <int NPL>
+__device__ __forceinline__ void wr_passes_c(WrRow<NPL>& R, const WrSeg& g, int k0, int k1,
+                                            const uint32_t* s_Kp) {
+  static_assert(NPL == 32, "one flag word per lane");
+  const int lane = threadIdx.x & 31;
+  const uint32_t uf = s_Kp[kKcOff + 1];
+#pragma unroll 1
+  for (int k = k0; k <= k1; ++k) {
+    const int I = 1 << k;
+    const uint32_t* Kp = s_Kp + koffset(k);
+    const uint32_t bound = s_Kp[kKbOff + 2 * k];
+    uint32_t F[1];
+    switch (k) {
+      case 1: wr_fire<NPL, 2>(R, lane, Kp, F); break;
+      case 2: wr_fire<NPL, 4>(R, lane, Kp, F); break;
+      case 3: wr_fire_blk<NPL, 8, 2>(R, lane, Kp, bound, F); break;
+      case 4: wr_fire_blk<NPL, 16, 4>(R, lane, Kp, bound, F); break;
+      case 5: wr_fire_blk<NPL, 32, 4>(R, lane, Kp, bound, F); break;
+      default: wr_fire_pf64c<NPL>(R, lane, Kp, bound, kZ - s_Kp[kKcOff], F); break;
+    }
+    wr_apply_c<NPL>(R, lane, g.vend - I + 1 - g.xl, I, uf, F);
+  }
+}
+
+// wr_finish under the fixed encoding: the unflagged sum subtracts n c.
+template <int DT, int NPL>
+__device__ __forceinline__ void wr_finish_c(const WrRow<NPL>& R, const WrSeg& g, int T, uint8_t* srow,
+                                            uint32_t* M_out, const WrOut& o, uint32_t c, int& n_flag,
+                                            unsigned long long& sum_unflagged) {
+  constexpr int NW = NPL / 32;
+  int nfl = 0;
+  unsigned long long su = 0;
+#pragma unroll
+  for (int w = 0; w < NW; ++w) {
+    const int x = g.xl + 32 * w;
+    if (x >= g.oa && x < g.ob) {
+      M_out[x >> 5] = R.M[w];
+      const int nf = __popc(R.M[w]);
+      nfl += nf;
+      uint32_t s = 0u;  // 64 (sum_unflagged + nf c) + nf
+#pragma unroll
+      for (int b = 0; b < 32; ++b) s += R.u[32 * w + b];
+      su += (s >> kLowShift) - static_cast<uint32_t>(nf) * c;
+      if (o.enabled) wr_write_word<DT>(o, srow + 32 * w * Traits<DT>::kBytes, x, T, R.M[w]);
+    }
+  }
+  n_flag = __reduce_add_sync(kFull, nfl);
+  sum_unflagged = warp_sum64(su);
+}
+
 // ------------------------------------------------------------------ fine counts
 
 // Exact counts of the pooled values inside the refinement targets, for rows
@@ -1822,17 +2140,19 @@ __device__ LOFK_TASK_FN void unit_round1(const KParams& kp, const DevUnit& u, Un
   const int T = u.T;
   frequency_pass<NT>(kp, u, us, ws, f);
   if (__ldcg(&us->state) != kStateDone) {
-    // Workspace (bytes): the initial bin list lo [0, 4.2K), hi [8K, 12.2K),
-    // cum [16K, 20.2K); spec counts [24K, 28K); histogram [28K, 32.2K);
-    // Fc [34K, 36K).
+    // Workspace (bytes): the bin list lo [0, 8K), hi [8K, 16K), cum [16K,
+    // 24K) once the flagged rows are out; before that the key -> offset map
+    // [0, 4.2K) and the flagged-row list [4.5K, 6.25K); histogram [24K,
+    // 28.2K); Fc [34K, 36K) (from the frequency pass); spec counts [36K, 52K).
     const uint8_t* Fc = ws + 2 * kMaxChan * sizeof(unsigned long long) + kMaxChan;
-    uint32_t* uh = reinterpret_cast<uint32_t*>(ws + 28 * 1024);
-    uint32_t* sp = reinterpret_cast<uint32_t*>(ws + 24 * 1024);
-    if (tid == 0) {
-      f.n_tgt = 0;
+    uint32_t* uh = reinterpret_cast<uint32_t*>(ws + 24 * 1024);
+    uint32_t* sp = reinterpret_cast<uint32_t*>(ws + 36 * 1024);
+    if (tid < kWarp) {
+      int nt = 0;
       if (kp.hist.hint && u.hist_slot >= 0)
-        f.n_tgt = spec_targets(__ldcg(kp.hist.hint + 2 * u.hist_slot),
-                               __ldcg(kp.hist.hint + 2 * u.hist_slot + 1), f.tgt);
+        nt = spec_targets(__ldcg(kp.hist.hint + 2 * u.hist_slot),
+                          __ldcg(kp.hist.hint + 2 * u.hist_slot + 1), f.tgt);
+      if (tid == 0) f.n_tgt = nt;
     }
     for (int k = tid; k < kCoarseBins; k += NT) uh[k] = __ldcg(us->coarse + k);
     for (int k = tid; k < kMaxSpec; k += NT) sp[k] = __ldcg(us->spec + k);
@@ -1844,8 +2164,8 @@ __device__ LOFK_TASK_FN void unit_round1(const KParams& kp, const DevUnit& u, Un
     const int nseg = (T + SEG - 1) / SEG;
     const bool vin = (u.flags & kUnitInVec) != 0;
     const uint8_t* gin = static_cast<const uint8_t*>(u.in);
-    int* frows = reinterpret_cast<int*>(ws + 32 * 1024 + 256);  // [32.25K, 34K): up to 448 rows
-    uint32_t* moff = reinterpret_cast<uint32_t*>(ws + 12 * 1024);  // [12K, 16.2K): key -> offset
+    int* frows = reinterpret_cast<int*>(ws + 4 * 1024 + 512);  // [4.5K, 6.25K): up to 448 rows
+    uint32_t* moff = reinterpret_cast<uint32_t*>(ws);           // [0, 4.2K): key -> offset
     for (int i = tid; i < kCoarseBins; i += NT) moff[i] = kNoTarget;
     __syncthreads();
     if (tid < nspec_t) moff[coarse_key(f.tgt[tid].lo)] = f.tgt[tid].base - f.tgt[tid].lo;
@@ -2018,14 +2338,15 @@ __device__ LOFK_TASK_FN void task_stats(const KParams& kp, const DevUnit& u, Uni
   const int T = u.T, R = tk.nrows, row0 = tk.row0, nseg = (T + SEG - 1) / SEG;
   const bool vin = (u.flags & kUnitInVec) != 0;
   const uint8_t* gin = static_cast<const uint8_t*>(u.in);
-  uint32_t* hist = reinterpret_cast<uint32_t*>(ws);
-  uint32_t* moff = reinterpret_cast<uint32_t*>(ws + 10 * 1024);         // [10K, 14.2K)
-  uint32_t* spec = reinterpret_cast<uint32_t*>(ws + 6 * 1024);           // [6K, 10K)
-  if (tid == 0) {
-    f.n_tgt = 0;
+  uint32_t* hist = reinterpret_cast<uint32_t*>(ws);                     // [0, 4.2K)
+  uint32_t* spec = reinterpret_cast<uint32_t*>(ws + 6 * 1024);           // [6K, 22K)
+  uint32_t* moff = reinterpret_cast<uint32_t*>(ws + 22 * 1024);          // [22K, 26.2K)
+  if (tid < kWarp) {
+    int nt = 0;
     if (kp.hist.hint && u.hist_slot >= 0)
-      f.n_tgt = spec_targets(__ldcg(kp.hist.hint + 2 * u.hist_slot),
-                             __ldcg(kp.hist.hint + 2 * u.hist_slot + 1), f.tgt);
+      nt = spec_targets(__ldcg(kp.hist.hint + 2 * u.hist_slot),
+                        __ldcg(kp.hist.hint + 2 * u.hist_slot + 1), f.tgt);
+    if (tid == 0) f.n_tgt = nt;
   }
   for (int i = tid; i < kCoarseBins; i += NT) {
     hist[i] = 0u;
@@ -2057,20 +2378,24 @@ __device__ LOFK_TASK_FN void task_stats(const KParams& kp, const DevUnit& u, Uni
     load_seg(task + NW, nxt);
     const int r = task / nseg, s = task - r * nseg;
     unsigned long long sum = 0;
+    // one count per sample: its value's counter inside a target bin (the
+    // bin's coarse count is rebuilt from those below), else its bin
+    auto count = [&](uint32_t val) {
+      sum += val;
+      const uint32_t key = coarse_key(val);
+      const uint32_t si = val + moff[key];  // spec index, or >= nsc off the targets
+      atomicAdd(si < nsc ? spec + si : hist + key, 1u);
+    };
 #pragma unroll
     for (int q = 0; q < NQ; ++q) {
       const int x = s * SEG + q * 32 * VS + lane * VS;
+      if (x + VS <= T) {
 #pragma unroll
-      for (int j = 0; j < VS; ++j) {
-        if (x + j < T) {
-          const uint32_t val = raw_pw<DT>(cur[q], j);
-          sum += val;
-          const uint32_t key = coarse_key(val);
-          // one count per sample: its value's counter inside a target bin
-          // (the bin's coarse count is rebuilt from those below), else its bin
-          const uint32_t si = val + moff[key];  // spec index, or >= nsc off the targets
-          atomicAdd(si < nsc ? spec + si : hist + key, 1u);
-        }
+        for (int j = 0; j < VS; ++j) count(raw_pw<DT>(cur[q], j));
+      } else {
+#pragma unroll
+        for (int j = 0; j < VS; ++j)
+          if (x + j < T) count(raw_pw<DT>(cur[q], j));
       }
     }
     sum = warp_sum64(sum);
@@ -2112,12 +2437,14 @@ __device__ LOFK_TASK_FN void task_stats(const KParams& kp, const DevUnit& u, Uni
     }
   }
   __syncthreads();
-  // coarse counts of the target bins: the sums of their value counters
-  if (tid < nspec_t) {
-    const Target& t = f.tgt[tid];
+  // coarse counts of the target bins: the sums of their value counters (one
+  // warp per bin)
+  for (int t = warp; t < nspec_t; t += NW) {
+    const Target g = f.tgt[t];
     uint32_t c = 0;
-    for (uint32_t i = t.base; i <= t.base + (t.hi - t.lo); ++i) c += spec[i];
-    hist[coarse_key(t.lo)] += c;
+    for (uint32_t i = g.base + lane; i <= g.base + (g.hi - g.lo); i += kWarp) c += spec[i];
+    c = warp_sum32(c);
+    if (lane == 0) hist[coarse_key(g.lo)] += c;
   }
   __syncthreads();
   for (int r = tid; r < R; r += NT) kp.chan_S[u.chan_off + row0 + r] = f.rowS[r];

@@ -269,17 +269,19 @@ def make_streams(n_streams=32, seed=5, period_s=1.0):
     return out
 
 
-def make_block(spec: StreamSpec, block: int, seed=5):
-    """Seeded complex int8 block (sigma 8, tones and impulses) in pinned host memory."""
+def make_block(spec: StreamSpec, block: int, seed=5, device="cpu"):
+    """Seeded complex int8 block (sigma 8, tones and impulses) in pinned host
+    memory, drawn on `device` (a CUDA device draws large blocks in
+    milliseconds; the values depend on the device's generator)."""
     from . import synth
     vs = synth.VoltageSpec(n_station=spec.n_station, n_pol=2, n_subband=1, C=spec.C, T=spec.T,
                            dtype=spec.dtype, sigma=8.0, tone_frac=0.02, impulse_frac=0.01)
-    x = synth.voltage_block(vs, seed=synth._mix(seed, spec.sid), block=block, device="cpu")
-    return x[:, :, 0].contiguous().pin_memory()
+    x = synth.voltage_block(vs, seed=synth._mix(seed, spec.sid), block=block, device=device)
+    return x[:, :, 0].contiguous().cpu().pin_memory()
 
 
 def run(streams, n_blocks: int, mem_budget: int, accelerated=False, jitter_s=0.1, seed=5,
-        keep_results=False, blocks=None):
+        keep_results=False, blocks=None, gen_device="cpu"):
     """Drive the server with every stream's blocks 0..n_blocks-1 arriving on
     its cadence (jittered), or all at once when accelerated; returns the server
     (finished requests hold latencies and results) and the wall time."""
@@ -293,7 +295,7 @@ def run(streams, n_blocks: int, mem_budget: int, accelerated=False, jitter_s=0.1
     data = {} if blocks is None else blocks
     for _, sid, b in events:
         if (sid, b) not in data:
-            data[(sid, b)] = make_block(next(s for s in streams if s.sid == sid), b, seed)
+            data[(sid, b)] = make_block(next(s for s in streams if s.sid == sid), b, seed, gen_device)
     srv = Server(streams, mem_budget, keep_results=keep_results)
     by_id = {s.sid: s for s in streams}
     t0 = time.perf_counter()

@@ -197,6 +197,41 @@ def test_host_buffer_entry_point():
     assert g["median_t"] == want["stats"]["median_t"] and g["sigma_t"] == want["stats"]["sigma_t"]
 
 
+def test_host_buffer_pipeline_matches_device_path():
+    """Enough units for several upload / flag / download chunks, compact
+    (merged copies) and strided (2-D copies) host rows, two calls in a row:
+    equal to lof_flag_block on device copies, bit for bit."""
+    rng = np.random.default_rng(81)
+    C, T, n = 64, 3072, 120                     # 120 x 0.75 MiB of ci16 input, > 64 MiB
+    with lof.Flagger(0) as fl:
+        s = torch.cuda.current_stream()
+        for call in range(2):
+            blk = np.round(rng.normal(0, 32, (n, C, T, 2))).astype(np.int16)
+            blk[:, :, 1000 + 7 * call:1010 + 7 * call, 0] += 900
+            hx = torch.as_tensor(blk).pin_memory()
+            wide = torch.zeros((C, T + 8, 2), dtype=torch.int16).pin_memory()   # strided rows
+            wide[:, :T] = hx[0]
+            ho = torch.zeros_like(hx).pin_memory()
+            hm = torch.zeros((n, C, T), dtype=torch.uint8).pin_memory()
+            hs = torch.zeros((n, 8), dtype=torch.int64).pin_memory()
+            units = [lof.make_unit(wide[:, :T], ho[0], hm[0], -1, hs[0])]
+            units += [lof.make_unit(hx[i], ho[i], hm[i], -1, hs[i]) for i in range(1, n)]
+            fl.flag_block_host(lof.LOF_CI16, units, call, s)
+            s.synchronize()
+            fl.status()
+            dx = hx.to(DEV)
+            do = torch.zeros_like(dx)
+            dm = torch.zeros((n, C, T), dtype=torch.uint8, device=DEV)
+            ds = lof.stats_tensor(n, DEV)
+            fl.flag_block(lof.LOF_CI16, [lof.make_unit(dx[i], do[i], dm[i], -1, ds[i]) for i in range(n)],
+                          call, s)
+            fl.status()
+            assert torch.equal(hm, dm.cpu()), f"call {call}: masks differ"
+            assert torch.equal(ho, do.cpu()), f"call {call}: data differs"
+            assert torch.equal(hs, ds.cpu()), f"call {call}: statistics differ"
+            assert int(hm.sum()) > 0
+
+
 def test_history_export_import_roundtrip():
     P = oracle_params()
     with lof.Flagger(0, n_history_slots=40) as fl:
