@@ -75,7 +75,8 @@ def measured_traffic(n_units, tuning):
         # resident CTAs per SM are capped by the kernel's launch bounds
         cap = 4 if int(t["threads"]) == 128 else 2
         return (int(t["threads"]), min(int(t["ctas_per_sm"]), cap), int(t["tile_bytes"]),
-                int(t["fine_bins"]), int(t["flag_rows"]), int(t["stat_samples"]))
+                int(t["fine_bins"]), int(t["flag_rows"]), int(t["stat_samples"]),
+                int(t.get("schedule", -1)))
     try:
         taken = dict(f.split("=") for f in kv["tuning"].split())
         if shape(taken) != shape(tuning):

@@ -236,8 +236,8 @@ int lof_status(lof_ctx *ctx, void *cuda_stream);
 /* Work counters of the last lof_flag_block on ctx (not of graph replays):
  * counts[0] = units whose pooled time-pass statistics needed a refinement
  * round after the first counting pass (the counts near the previous block's
- * median and MAD did not pin them down), counts[1] = refinement tasks that
- * read rows again.  Waits for cuda_stream.  Instrumentation of the exact
+ * median and MAD did not pin them down), counts[1] = refinement passes that
+ * read a unit's kept rows again.  Waits for cuda_stream.  Instrumentation of the exact
  * selection (Section 4.2 asks for O(N) medians); results never depend on it. */
 int lof_block_counters(lof_ctx *ctx, void *cuda_stream, int64_t *counts);
 
@@ -254,16 +254,32 @@ typedef struct {
   int32_t flag_rows;       /* rows per time-pass task (tile height), 1..64 (default 64) */
   int32_t stat_samples;    /* samples per statistics task, >= 1024 (default 262144;
                               at most 64 rows) */
+  int32_t schedule;        /* window schedule of the time pass (Section 2.1's window sizes
+                              over a row): LOF_SCHED_SET plus any of
+                              LOF_SCHED_PACKED (rows whose values fit run in the packed
+                              low-bit form, one warp per 1024-sample segment in registers;
+                              without it every row takes the general path, exact 64-bit
+                              window sums over a shared-memory prefix), LOF_SCHED_BOUND64
+                              (the 64-sample windows are first screened by an exact bound on
+                              sums of blocks of four; without it every window is tested) and
+                              LOF_SCHED_COALESCED (the masked data of a segment leaves with
+                              coalesced 16-byte stores; without it one bulk copy per lane).
+                              Default LOF_SCHED_SET | LOF_SCHED_PACKED | LOF_SCHED_BOUND64 |
+                              LOF_SCHED_COALESCED */
 } lof_tuning;
+enum { LOF_SCHED_PACKED = 1, LOF_SCHED_BOUND64 = 2, LOF_SCHED_COALESCED = 4, LOF_SCHED_SET = 0x80 };
 int lof_set_tuning(lof_ctx *ctx, const lof_tuning *t);
 int lof_get_tuning(const lof_ctx *ctx, lof_tuning *t);
 
 /* Autotuner: times lof_flag_block on these units (reps timed launches after
  * one warm-up, median) for every candidate launch shape -- threads per CTA,
  * CTAs per SM, rows per time-pass task, samples per statistics task -- and
- * keeps the fastest in the context (*best, *best_ms if not NULL).  Results
- * never depend on the tuning.  Synchronous; stages history values like any
- * lof_flag_block call (do not commit them).  F32 units have a single shape. */
+ * then, with the fastest shape, every window schedule (the packed or the
+ * general time pass, the bound on the 64-sample windows on or off, coalesced
+ * or bulk data stores), and keeps the fastest in the context (*best, *best_ms
+ * if not NULL).  Results never depend on the tuning.  Synchronous; stages
+ * history values like any lof_flag_block call (do not commit them).  F32
+ * units have a single shape. */
 int lof_autotune(lof_ctx *ctx, int dtype, const lof_unit *units, int n_units, int reps,
                  void *cuda_stream, lof_tuning *best, float *best_ms);
 

@@ -207,7 +207,10 @@ extern "C" const char* lof_last_error(const lof_ctx* c) {
 
 namespace lofk {
 
-lof_tuning default_tuning() { return lof_tuning{256, 2, 0, 2048, 64, 262144}; }
+lof_tuning default_tuning() {
+  return lof_tuning{256, 2, 0, 2048, 64, 262144,
+                    LOF_SCHED_SET | LOF_SCHED_PACKED | LOF_SCHED_BOUND64 | LOF_SCHED_COALESCED};
+}
 
 // Checks every field of a parameter set (shared by lof_create and the
 // allocation-free entry point); 1 = valid, else 0 with the reason in *why.
@@ -385,6 +388,12 @@ extern "C" int lof_set_tuning(lof_ctx* c, const lof_tuning* t) {
     if (t->stat_samples < 1024) return fail(c, LOF_ERR_INVALID, "stat_samples >= 1024");
     n.stat_samples = t->stat_samples;
   }
+  if (t->schedule) {
+    if (!(t->schedule & LOF_SCHED_SET) ||
+        (t->schedule & ~(LOF_SCHED_SET | LOF_SCHED_PACKED | LOF_SCHED_BOUND64 | LOF_SCHED_COALESCED)))
+      return fail(c, LOF_ERR_INVALID, "schedule: LOF_SCHED_SET plus LOF_SCHED_* flags");
+    n.schedule = t->schedule;
+  }
   if (t->fine_bins) {
     if (t->fine_bins < 64 || t->fine_bins > lofk::kMaxFine)
       return fail(c, LOF_ERR_INVALID, "fine_bins in [64, %d]", lofk::kMaxFine);
@@ -477,7 +486,7 @@ int host_count_tasks(const HostCfg& h, int dtype, const lof_unit* units, int n_u
       return LOF_ERR_INVALID;
     }
     const int Rs = stat_rows(T, h.tuning.stat_samples);
-    n += 2 * ((C + Rs - 1) / Rs) + (C + Rc - 1) / Rc;
+    n += (C + Rs - 1) / Rs + (C + Rc - 1) / Rc;
   }
   if (n > (int64_t(1) << 30)) {
     snprintf(why, nwhy, "too many tasks");
@@ -589,14 +598,13 @@ int host_prepare(const HostCfg& h, int dtype, const lof_unit* units, int n_units
     d.pad = 0;
     per_step += d.nS + d.nC;
   }
-  // Queue order, software-pipelined over units: step s holds the stats tasks
-  // of unit s, the fine tasks of unit s - dF and the flag tasks of unit s - dC,
-  // so that a unit's statistics are normally final before its flag tasks
-  // are taken, while its rows are still in L2.
+  // Two queues, one per launch of the persistent kernel: the statistics
+  // launch takes every unit's stats tasks, the flag launch then every unit's
+  // flag tasks, all of whose statistics are final, so no flag task waits.
   const int grid = static_cast<int>(std::min<int64_t>(int64_t(h.n_sm) * ctas, std::max<int64_t>(1, per_step)));
   const double avg = static_cast<double>(per_step) / std::max(1, n_units);
   const int inflight = static_cast<int>(std::ceil(grid / std::max(1.0, avg)));
-  const int dF = inflight + 2, dC = dF + inflight + 2;
+  const int dF = inflight + 2;
   int n = 0;
   auto emit = [&](int ui, int kind) -> bool {
     const DevUnit& d = du[ui];
@@ -607,27 +615,30 @@ int host_prepare(const HostCfg& h, int dtype, const lof_unit* units, int n_units
     }
     return true;
   };
-  for (int step = 0; step < n_units + dC; ++step) {
-    bool ok = true;
-    if (step < n_units) ok = ok && emit(step, kTaskStats);
-    if (step - dF >= 0 && step - dF < n_units) ok = ok && emit(step - dF, kTaskFine);
-    if (step - dC >= 0 && step - dC < n_units) ok = ok && emit(step - dC, kTaskFlag);
-    if (!ok) {
-      snprintf(why, nwhy, "more than %d tasks in one block", max_tasks);
-      return LOF_ERR_INVALID;
-    }
+  // (Refinement rounds, needed when a unit's first counting pass leaves its
+  // statistics open, run in the CTA that finishes that pass; no task waits.)
+  (void)dF;
+  bool ok = true;
+  for (int ui = 0; ui < n_units && ok; ++ui) ok = emit(ui, kTaskStats);
+  const int n_stats = n;
+  for (int ui = 0; ui < n_units && ok; ++ui) ok = emit(ui, kTaskFlag);
+  if (!ok) {
+    snprintf(why, nwhy, "more than %d tasks in one block", max_tasks);
+    return LOF_ERR_INVALID;
   }
   // the row runs must match the task counts recorded per unit
   for (int i = 0; i < n_units; ++i) {
     DevUnit& d = du[i];
     const int rs = (d.C + d.nS - 1) / d.nS, rc = (d.C + d.nC - 1) / d.nC;
     d.nS = (d.C + rs - 1) / rs;
-    d.nF = d.nS;
+    d.nF = 0;
     d.nC = (d.C + rc - 1) / rc;
   }
   out->n_tasks = n;
+  out->n_tasks_stats = n_stats;
   out->n_chan = chan;
-  out->grid = std::min(grid, n);
+  out->grid = std::min(grid, n_stats);
+  out->grid_flag = std::min(grid, n - n_stats);
   // one row of the general (any-magnitude) time pass per CTA, in global scratch
   int gw = 0;
   for (int i = 0; i < nT; ++i) gw = std::max(gw, pfx_row_words(dtype, Ts[i]) + flag_words_row(Ts[i]));
@@ -659,7 +670,7 @@ int host_launch_kernel(const lof_params& P, const HostCfg& h, int dtype, const P
       ((e = cudaMemset2DAsync(sc.ustate, sizeof(UnitState), 0, kUnitStateZeroBytes, n_units, st)) !=
            cudaSuccess ||
        (e = cudaMemsetAsync(sc.ctrl, 0, sizeof(int), st)) != cudaSuccess ||
-       (e = cudaMemsetAsync(sc.ctrl + 4, 0, 2 * sizeof(int), st)) != cudaSuccess)) {
+       (e = cudaMemsetAsync(sc.ctrl + 4, 0, 3 * sizeof(int), st)) != cudaSuccess)) {
     snprintf(why, nwhy, "state reset: %s", cudaGetErrorString(e));
     return LOF_ERR_CUDA;
   }
@@ -701,13 +712,25 @@ int host_launch_kernel(const lof_params& P, const HostCfg& h, int dtype, const P
   kp.dyn_smem = pr.plan.smem;
   kp.gen_scratch = sc.gen;
   kp.gen_words = pr.gen_words;
-  const int krc = is_float(dtype)
-                      ? lofk_launch_f32x(&kp, n_units, h.n_sm, pr.plan.smem, stream, dtype == LOF_CF32)
-                  : exact_stats_mode(P) >= 0
-                      ? lofk_launch_integ(dtype, &kp, n_units, h.n_sm, stream, exact_stats_mode(P),
-                                          P.integ_chan, P.integ_time)
-                      : lofk_launch_block(dtype, &kp, pr.grid, pr.plan.threads, pr.plan.smem, stream,
-                                          cooperative);
+  kp.schedule = h.tuning.schedule;
+  int krc;
+  if (is_float(dtype)) {
+    krc = lofk_launch_f32x(&kp, n_units, h.n_sm, pr.plan.smem, stream, dtype == LOF_CF32);
+  } else if (exact_stats_mode(P) >= 0) {
+    krc = lofk_launch_integ(dtype, &kp, n_units, h.n_sm, stream, exact_stats_mode(P), P.integ_chan,
+                            P.integ_time);
+  } else {
+    // the statistics launch (stats and fine tasks), then the flag launch
+    kp.n_tasks = pr.n_tasks_stats;
+    krc = lofk_launch_block(dtype, &kp, pr.grid, pr.plan.threads, pr.plan.smem, stream, cooperative, 0);
+    if (krc == 0 && pr.n_tasks > pr.n_tasks_stats) {
+      KParams kf = kp;
+      kf.tasks = sc.tasks + pr.n_tasks_stats;
+      kf.n_tasks = pr.n_tasks - pr.n_tasks_stats;
+      kf.queue = sc.ctrl + 6;
+      krc = lofk_launch_block(dtype, &kf, pr.grid_flag, pr.plan.threads, pr.plan.smem, stream, cooperative, 1);
+    }
+  }
   if (krc != 0) {
     snprintf(why, nwhy, "kernel launch failed: %s (grid %d, %d threads, %d B)",
              cudaGetErrorString(static_cast<cudaError_t>(krc)), pr.grid, pr.plan.threads,
@@ -1260,6 +1283,10 @@ struct lof_graph {
   cudaGraphExec_t exec = nullptr;
   cudaGraphNode_t knode = nullptr;
   cudaKernelNodeParams kparams{};
+  cudaGraphNode_t knode2 = nullptr;  // the flag launch of the block kernel (its second launch)
+  cudaKernelNodeParams kparams2{};
+  lofk::KParams kp2{};
+  void* kargs2[1] = {nullptr};
   lofk::KParams kp{};  // argument storage for parameter updates
   int2 cells{1, 1};    // second argument of the exact-statistics kernel
   void* kargs[2] = {nullptr, nullptr};
@@ -1347,6 +1374,23 @@ int graph_capture(lof_graph* g, const lofk::HostCfg& h, const lofk::Prep& pr, in
       std::memcpy(&g->cells, g->kparams.kernelParams[1], sizeof(int2));
   }
   if (!g->knode) return snprintf(why, nwhy, "no kernel node in the captured graph"), LOF_ERR_CUDA;
+  // the block kernel's flag launch, right after its statistics launch
+  for (size_t i = 0; i < n && !g->knode2; ++i) {
+    if (!is_kernel(nodes[i]) || nodes[i] == g->knode) continue;
+    size_t nd = 0;
+    cudaGraphNodeGetDependencies(nodes[i], nullptr, nullptr, &nd);
+    std::vector<cudaGraphNode_t> deps(nd);
+    if (nd) cudaGraphNodeGetDependencies(nodes[i], deps.data(), nullptr, &nd);
+    bool after_first = false;
+    for (size_t j = 0; j < nd; ++j) after_first = after_first || deps[j] == g->knode;
+    cudaKernelNodeParams kp2{};
+    if (!after_first || cudaGraphKernelNodeGetParams(nodes[i], &kp2) != cudaSuccess ||
+        kp2.func != lofk_block_kernel(g->dtype, h.tuning.threads, 1))
+      continue;
+    g->knode2 = nodes[i];
+    g->kparams2 = kp2;
+    std::memcpy(&g->kp2, kp2.kernelParams[0], sizeof(lofk::KParams));
+  }
   e = cudaGraphInstantiate(&g->exec, g->graph, 0);
   if (e != cudaSuccess) return snprintf(why, nwhy, "instantiate: %s", cudaGetErrorString(e)), LOF_ERR_CUDA;
   return LOF_OK;
@@ -1407,6 +1451,7 @@ extern "C" int lof_graph_create(lof_ctx* c, int dtype, const lof_unit* units, in
   if (rc) {
     if (g->graph) cudaGraphDestroy(g->graph), g->graph = nullptr;
     g->knode = nullptr;
+    g->knode2 = nullptr;
     rc = graph_capture(g, h, pr, 0, why, sizeof why);
   }
   if (rc) {
@@ -1439,6 +1484,13 @@ extern "C" int lof_graph_launch(lof_graph* g, uint64_t block_seq, void* cuda_str
   g->kargs[1] = &g->cells;  // read only by a kernel with a second parameter
   p.kernelParams = g->kargs;
   cudaError_t e = cudaGraphExecKernelNodeSetParams(g->exec, g->knode, &p);
+  if (e == cudaSuccess && g->knode2) {
+    g->kp2.block_seq = block_seq;
+    cudaKernelNodeParams p2 = g->kparams2;
+    g->kargs2[0] = &g->kp2;
+    p2.kernelParams = g->kargs2;
+    e = cudaGraphExecKernelNodeSetParams(g->exec, g->knode2, &p2);
+  }
   if (e != cudaSuccess) return cuda_fail(c, e, "lof_graph_launch: parameter update");
   e = cudaGraphLaunch(g->exec, st);
   if (e != cudaSuccess) return cuda_fail(c, e, "lof_graph_launch");
@@ -1492,7 +1544,8 @@ extern "C" int lof_autotune(lof_ctx* c, int dtype, const lof_unit* units, int n_
         if (threads >= 256 && ctas > 2) continue;  // the launch bounds allow two
         for (int rows : {8, 16, 32, 64})
           for (int samples : {32768, 65536, 131072, 262144})
-            cands.push_back(lof_tuning{threads, ctas, saved.tile_bytes, saved.fine_bins, rows, samples});
+            cands.push_back(lof_tuning{threads, ctas, saved.tile_bytes, saved.fine_bins, rows, samples,
+                                       saved.schedule});
       }
   }
   cudaEvent_t e0, e1;
@@ -1501,7 +1554,19 @@ extern "C" int lof_autotune(lof_ctx* c, int dtype, const lof_unit* units, int n_
   float best_t = 1e30f;
   lof_tuning best_c = saved;
   std::vector<float> ts(reps);
-  for (const lof_tuning& t : cands) {
+  // stage 1: the launch shapes with the current schedule; stage 2: every
+  // window schedule with the fastest shape
+  const int n_shapes = static_cast<int>(cands.size());
+  for (int ci = 0; ci < static_cast<int>(cands.size()); ++ci) {
+    if (ci == n_shapes && !is_float(dtype)) {
+      for (int sc : {0, 1, 2, 3, 4, 5, 6, 7}) {
+        lof_tuning t = best_c;
+        t.schedule = LOF_SCHED_SET | sc;
+        if (t.schedule != best_c.schedule) cands.push_back(t);
+      }
+      if (ci == static_cast<int>(cands.size())) break;
+    }
+    const lof_tuning t = cands[ci];
     c->tuning = t;
     if (lof_flag_block(c, dtype, units, n_units, 0, st) != LOF_OK) continue;  // warm-up
     bool ok = true;

@@ -146,6 +146,7 @@ struct KParams {
   int dyn_smem;                 // dynamic shared memory of each CTA (bytes)
   uint32_t* gen_scratch;        // general time-pass rows, gen_words per CTA
   int gen_words;
+  int schedule;                 // LOF_SCHED_* bits of the time pass
 };
 
 struct CommitParams {
@@ -167,7 +168,8 @@ struct Plan {
 };
 struct Prep {
   Plan plan;
-  int n_tasks, grid;
+  int n_tasks, grid;             // all tasks; CTAs of the statistics launch
+  int n_tasks_stats, grid_flag;  // tasks of the statistics launch (the first ones); CTAs of the flag launch
   int64_t n_chan;
   int gen_words;                 // per CTA, general time-pass rows
 };
@@ -178,7 +180,8 @@ struct Scratch {
   UnitState* ustate;
   unsigned long long* chanS;
   uint8_t* chanFc;
-  int* ctrl;  // [0] queue, [1] error, [2..3] detail, [4..5] counters (kCtrlWords ints)
+  int* ctrl;  // [0] queue of the statistics launch, [1] error, [2..3] detail, [4..5] counters,
+             // [6] queue of the flag launch (kCtrlWords ints)
   HistoryDev hist;
   uint32_t* gen;  // general time-pass rows: grid x gen_words words
 };
@@ -202,7 +205,8 @@ int host_launch_kernel(const lof_params& P, const HostCfg& h, int dtype, const P
 
 // Kernel launchers (lof_kernels.cu)
 extern "C" int lofk_launch_block(int dtype, const lofk::KParams* kp, int grid, int threads,
-                                 int smem_bytes, void* stream, int cooperative);
+                                 int smem_bytes, void* stream, int cooperative, int phase);
+extern "C" void* lofk_block_kernel(int dtype, int threads, int phase);
 extern "C" int lofk_launch_commit(const lofk::CommitParams* cp, int total_channels, void* stream);
 extern "C" int lofk_launch_refresh(const lofk::CommitParams* cp, int total_channels, void* stream);
 extern "C" int lofk_max_blocks_per_sm(int dtype, int threads, int smem_bytes, int* out);

@@ -23,6 +23,7 @@ LOF_CI8, LOF_CI16, LOF_F32, LOF_CF32 = 1, 2, 3, 4
 LOF_SIGMA_MAD, LOF_SIGMA_STD, LOF_SIGMA_WINSOR = 0, 1, 2
 LOF_TIME_PER_CHANNEL, LOF_TIME_INTEGRATED, LOF_TIME_2D = 0, 1, 2
 LOF_SCOPE_POOLED, LOF_SCOPE_CHANNEL = 0, 1
+LOF_SCHED_PACKED, LOF_SCHED_BOUND64, LOF_SCHED_COALESCED, LOF_SCHED_SET = 1, 2, 4, 0x80
 
 EXPORTED = [
     "lof_default_params", "lof_create", "lof_flag_block", "lof_flag_block_host",
@@ -94,6 +95,7 @@ class lof_tuning(ctypes.Structure):
         ("fine_bins", ctypes.c_int32),
         ("flag_rows", ctypes.c_int32),
         ("stat_samples", ctypes.c_int32),
+        ("schedule", ctypes.c_int32),
     ]
 
 
@@ -223,8 +225,8 @@ def lof_max_time(ctx, dtype: int) -> int:
 
 
 def lof_set_tuning(ctx, threads=0, ctas_per_sm=0, tile_bytes=0, fine_bins=0, flag_rows=0,
-                   stat_samples=0) -> int:
-    t = lof_tuning(threads, ctas_per_sm, tile_bytes, fine_bins, flag_rows, stat_samples)
+                   stat_samples=0, schedule=0) -> int:
+    t = lof_tuning(threads, ctas_per_sm, tile_bytes, fine_bins, flag_rows, stat_samples, schedule)
     return library().lof_set_tuning(ctx, ctypes.byref(t))
 
 

@@ -110,3 +110,55 @@ def test_launch_shapes_do_not_change_results(kw):
     for i in range(len(xs)):
         assert np.array_equal(other[1][i], base[1][i])
         assert np.array_equal(other[0][i], base[0][i])
+
+
+def _ragged_ci16(seed):
+    """Ragged complex int16 units: row lengths off every segment and chunk
+    boundary, one unit with rows past the packed form's range."""
+    rng = np.random.default_rng(seed)
+    out = []
+    for C, T in [(7, 1001), (33, 3071), (5, 4097), (64, 769), (3, 37)]:
+        x = np.round(rng.normal(0, 32, (C, T, 2)))
+        x[rng.integers(0, C), :, 0] += 25 * 32
+        t0 = int(rng.integers(0, max(1, T - 70)))
+        x[:, t0:t0 + 60, 1] += 40 * 32
+        out.append(np.clip(x, -32768, 32767).astype(np.int16))
+    big = np.round(rng.normal(0, 3000, (4, 2000, 2)))           # threshold_1 above 2^20: general path
+    out.append(np.clip(big, -32768, 32767).astype(np.int16))
+    return out
+
+
+@pytest.mark.parametrize("dtype", [lof.LOF_CI8, lof.LOF_CI16])
+def test_every_window_schedule_gives_identical_results(dtype):
+    """The autotuner's window schedules (packed or general time pass, the
+    bound on the 64-sample windows on or off, coalesced or bulk data stores)
+    change the work, never the result: bit-identical masks, data and
+    statistics on ragged units, equal to the oracle."""
+    if dtype == lof.LOF_CI8:
+        xs = [x.cpu().numpy() for x in _units(36, n_units=8)]
+    else:
+        xs = _ragged_ci16(37)
+    ins = [torch.as_tensor(x).to(DEV) for x in xs]
+    outs, masks, stats, units = _bufs(ins)
+    results = {}
+    with lof.Flagger(0) as fl:
+        for sc in range(8):
+            fl.set_tuning(schedule=lof.LOF_SCHED_SET | sc)
+            assert fl.tuning()["schedule"] == lof.LOF_SCHED_SET | sc
+            for o, m in zip(outs, masks):
+                o.fill_(5)
+                m.fill_(3)
+            fl.flag_block(dtype, units, 0)
+            fl.status()
+            results[sc] = _snap(outs, masks, stats)
+    base = results[7]
+    for sc, r in results.items():
+        for i in range(len(xs)):
+            assert np.array_equal(r[1][i], base[1][i]), f"schedule {sc} unit {i}: mask"
+            assert np.array_equal(r[0][i], base[0][i]), f"schedule {sc} unit {i}: data"
+            assert r[2][i] == base[2][i], f"schedule {sc} unit {i}: statistics"
+    P = oracle.default_params()
+    for i, x in enumerate(xs):
+        want = oracle.flag_unit(P, x)
+        assert np.array_equal(base[1][i], want["mask"]), f"unit {i}: oracle mask"
+        assert np.array_equal(base[0][i], want["out"]), f"unit {i}: oracle data"
