@@ -741,7 +741,7 @@ def main():
         line["e2e"] = res["e2e"]
     line["stats_refinement"] = {
         "units_refined_per_launch": [r["units_refined"] for r in res["refine"]],
-        "refine_tasks_per_launch": [r["refine_tasks"] for r in res["refine"]],
+        "refine_passes_per_launch": [r["refine_passes"] for r in res["refine"]],
         "note": "block 0 after block 1 and block 1 after block 0: units whose pooled median/MAD "
                 "needed a refinement pass beyond the first counting pass (the previous block's "
                 "statistics as hints)" if not args.same_block else "same block every step"}

@@ -234,10 +234,11 @@ int lof_history_import(lof_ctx *ctx, int64_t slot0, int64_t n, const double *val
 int lof_status(lof_ctx *ctx, void *cuda_stream);
 
 /* Work counters of the last lof_flag_block on ctx (not of graph replays):
- * counts[0] = units whose pooled time-pass statistics needed a refinement
- * round after the first counting pass (the counts near the previous block's
- * median and MAD did not pin them down), counts[1] = refinement passes that
- * read a unit's kept rows again.  Waits for cuda_stream.  Instrumentation of the exact
+ * counts[0] = units whose pooled time-pass statistics needed another pass
+ * over their data after the first counting pass (the counts near the previous
+ * block's median and MAD did not pin them down, or the block left its value
+ * window), counts[1] = such passes that read a unit's kept rows again.
+ * Waits for cuda_stream.  Instrumentation of the exact
  * selection (Section 4.2 asks for O(N) medians); results never depend on it. */
 int lof_block_counters(lof_ctx *ctx, void *cuda_stream, int64_t *counts);
 
@@ -263,11 +264,23 @@ typedef struct {
                               (the 64-sample windows are first screened by an exact bound on
                               sums of blocks of four; without it every window is tested) and
                               LOF_SCHED_COALESCED (the masked data of a segment leaves with
-                              coalesced 16-byte stores; without it one bulk copy per lane).
+                              coalesced 16-byte stores; without it one bulk copy per lane),
+                              and for the statistics LOF_SCHED_VALUE_WINDOW (a unit whose
+                              history slot holds the previous block's median m and MAD d,
+                              with d small enough, counts its pooled powers value by value
+                              in a window of 4096 values around m plus one count below it,
+                              and resolves median and MAD from those counts; a block whose
+                              statistics leave the window is counted again in full).
                               Default LOF_SCHED_SET | LOF_SCHED_PACKED | LOF_SCHED_BOUND64 |
-                              LOF_SCHED_COALESCED */
+                              LOF_SCHED_COALESCED | LOF_SCHED_VALUE_WINDOW */
 } lof_tuning;
-enum { LOF_SCHED_PACKED = 1, LOF_SCHED_BOUND64 = 2, LOF_SCHED_COALESCED = 4, LOF_SCHED_SET = 0x80 };
+enum {
+  LOF_SCHED_PACKED = 1,
+  LOF_SCHED_BOUND64 = 2,
+  LOF_SCHED_COALESCED = 4,
+  LOF_SCHED_VALUE_WINDOW = 8,
+  LOF_SCHED_SET = 0x80
+};
 int lof_set_tuning(lof_ctx *ctx, const lof_tuning *t);
 int lof_get_tuning(const lof_ctx *ctx, lof_tuning *t);
 
@@ -276,7 +289,7 @@ int lof_get_tuning(const lof_ctx *ctx, lof_tuning *t);
  * CTAs per SM, rows per time-pass task, samples per statistics task -- and
  * then, with the fastest shape, every window schedule (the packed or the
  * general time pass, the bound on the 64-sample windows on or off, coalesced
- * or bulk data stores), and keeps the fastest in the context (*best, *best_ms
+ * or bulk data stores, value-window statistics on or off), and keeps the fastest in the context (*best, *best_ms
  * if not NULL).  Results never depend on the tuning.  Synchronous; stages
  * history values like any lof_flag_block call (do not commit them).  F32
  * units have a single shape. */

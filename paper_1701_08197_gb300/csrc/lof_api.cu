@@ -209,7 +209,8 @@ namespace lofk {
 
 lof_tuning default_tuning() {
   return lof_tuning{256, 2, 0, 2048, 64, 262144,
-                    LOF_SCHED_SET | LOF_SCHED_PACKED | LOF_SCHED_BOUND64 | LOF_SCHED_COALESCED};
+                    LOF_SCHED_SET | LOF_SCHED_PACKED | LOF_SCHED_BOUND64 | LOF_SCHED_COALESCED |
+                        LOF_SCHED_VALUE_WINDOW};
 }
 
 // Checks every field of a parameter set (shared by lof_create and the
@@ -390,7 +391,8 @@ extern "C" int lof_set_tuning(lof_ctx* c, const lof_tuning* t) {
   }
   if (t->schedule) {
     if (!(t->schedule & LOF_SCHED_SET) ||
-        (t->schedule & ~(LOF_SCHED_SET | LOF_SCHED_PACKED | LOF_SCHED_BOUND64 | LOF_SCHED_COALESCED)))
+        (t->schedule & ~(LOF_SCHED_SET | LOF_SCHED_PACKED | LOF_SCHED_BOUND64 | LOF_SCHED_COALESCED |
+                         LOF_SCHED_VALUE_WINDOW)))
       return fail(c, LOF_ERR_INVALID, "schedule: LOF_SCHED_SET plus LOF_SCHED_* flags");
     n.schedule = t->schedule;
   }
@@ -1559,7 +1561,7 @@ extern "C" int lof_autotune(lof_ctx* c, int dtype, const lof_unit* units, int n_
   const int n_shapes = static_cast<int>(cands.size());
   for (int ci = 0; ci < static_cast<int>(cands.size()); ++ci) {
     if (ci == n_shapes && !is_float(dtype)) {
-      for (int sc : {0, 1, 2, 3, 4, 5, 6, 7}) {
+      for (int sc = 0; sc < 16; ++sc) {
         lof_tuning t = best_c;
         t.schedule = LOF_SCHED_SET | sc;
         if (t.schedule != best_c.schedule) cands.push_back(t);

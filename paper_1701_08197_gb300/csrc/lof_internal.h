@@ -76,10 +76,11 @@ struct alignas(16) Target {
 struct UnitState {
   int done_S, done_F;        // completed stats / fine tasks
   int ready;                 // 0: statistics pending, 1: fine counts needed, 2: final
-  int pad_ctl;
+  int win_below;             // value-window statistics: kept samples below the window
   unsigned long long mom[4]; // sum x (lo, hi), sum x^2 (lo, hi) -- 128-bit each
   uint32_t coarse[kCoarseBins];
   uint32_t spec[kMaxSpec];   // exact counts in the bins around the previous block's statistics
+                             // (value-window statistics: one counter per value of the window)
   // ---- end of the zeroed part
   double median_f, sigma_f;
   long long n_pool;          // samples in the time-pass pool

@@ -23,6 +23,7 @@
 
 #include <algorithm>
 #include <cstdint>
+#include <type_traits>
 
 #include "lof_internal.h"
 
@@ -140,9 +141,9 @@ struct Traits<LOF_CI8> {
   static constexpr int kBytes = 2;
   static constexpr int kVec = 8;
   __device__ static __forceinline__ uint32_t pw(uint32_t h) {
-    const int re = static_cast<int>(static_cast<int8_t>(h & 0xFFu));
-    const int im = static_cast<int>(static_cast<int8_t>((h >> 8) & 0xFFu));
-    return static_cast<uint32_t>(re * re + im * im);
+    // re^2 + im^2 as one signed byte-wise dot product (upper bytes zero)
+    const int b = static_cast<int>(h & 0xFFFFu);
+    return static_cast<uint32_t>(__dp4a(b, b, 0));
   }
   __device__ static __forceinline__ uint32_t at(const uint8_t* row, int t) {
     return pw(reinterpret_cast<const uint16_t*>(row)[t]);
@@ -405,6 +406,26 @@ __device__ int spec_targets(unsigned long long m2, unsigned long long mad4, Targ
   return nt;
 }
 
+// Value window of a unit (statistics counted value by value): the kWinVals
+// values around the previous block's median m (hint 2m, 4d), starting at 1 or
+// later and ending at 2^31 or earlier, chosen when m - d and m + d lie inside
+// it with a margin of max(64, d / 2) on each side -- between blocks the
+// pooled median and MAD move by a small fraction of d.
+// Deterministic in the hint, so every task of a unit and its round 1 agree.
+constexpr uint32_t kWinVals = kMaxSpec;
+__device__ __forceinline__ bool hint_window(unsigned long long m2, unsigned long long mad4, uint32_t* lo) {
+  if (m2 == ~0ull) return false;
+  const long long m = static_cast<long long>(m2 >> 1), d = static_cast<long long>(mad4 >> 2);
+  const long long margin = d / 2 > 64 ? d / 2 : 64;
+  if (2 * (d + margin) > static_cast<long long>(kWinVals)) return false;
+  long long a = m - static_cast<long long>(kWinVals / 2);
+  const long long top = 0x80000000ll - static_cast<long long>(kWinVals);
+  if (a < 1) a = 1;  // the value 0, if any, counts as below the window
+  if (a > top) return false;
+  *lo = static_cast<uint32_t>(a);
+  return true;
+}
+
 // ------------------------------------------------------------------ shared state
 
 template <int NT>
@@ -429,6 +450,9 @@ struct Fixed {
   // last-arriver scratch
   long long m2lo, m2hi, da[2], db[2];
   int mb[2], resolved, tb[kMaxTargets], nnz[kMaxTargets];
+  int wmode;                  // value-window statistics for this unit
+  uint32_t wlo;               // first value of the window
+  long long wbelow;           // kept samples below the window
   unsigned long long sd, md4;
   double sig;
   int kmax_f;
@@ -710,6 +734,39 @@ __device__ void finalize_stats(const KParams& kp, const DevUnit& u, UnitState* s
   __syncthreads();
 }
 
+// Exact twice-median M2 and four-times-MAD mad4 of a unit's pool of N
+// values: remembered as the next block's hint, then the time-pass thresholds
+// (sigma = 1.4826 MAD, Section 2.1), or the moments for the std estimator /
+// a zero MAD.  Whole CTA.
+template <int NT>
+__device__ void finish_selected(const KParams& kp, const DevUnit& u, UnitState* slot, long long M2,
+                                long long mad4, long long N) {
+  const int tid = threadIdx.x;
+  if (tid == 0 && kp.hist.hint && u.hist_slot >= 0) {
+    kp.hist.hint[2 * u.hist_slot] = static_cast<unsigned long long>(M2);
+    kp.hist.hint[2 * u.hist_slot + 1] = static_cast<unsigned long long>(mad4);
+  }
+  const double med = __dmul_rn(static_cast<double>(M2), 0.5);
+  const double mad = __dmul_rn(static_cast<double>(mad4), 0.25);
+  if (!kp.sigma_std && mad > 0.0) {
+    finalize_stats<NT>(kp, u, slot, med, __dmul_rn(1.482602218505602, mad));
+  } else if (kp.sigma_std) {
+    // moments were accumulated with the coarse histogram
+    const unsigned __int128 s1 =
+        (static_cast<unsigned __int128>(__ldcg(slot->mom + 1)) << 64) | __ldcg(slot->mom + 0);
+    const unsigned __int128 s2 =
+        (static_cast<unsigned __int128>(__ldcg(slot->mom + 3)) << 64) | __ldcg(slot->mom + 2);
+    finalize_stats<NT>(kp, u, slot, med, moments_std(N, s1, s2));
+  } else {
+    if (tid == 0) {
+      slot->median_t = med;
+      slot->mom[0] = slot->mom[1] = slot->mom[2] = slot->mom[3] = 0;
+      slot->state = kStateMoments;
+    }
+    __syncthreads();
+  }
+}
+
 // Plan the next refinement round, or finish.  Whole CTA of the last arriver;
 // the bin list is in shared memory.
 template <int NT>
@@ -834,31 +891,7 @@ __device__ void select_plan(const KParams& kp, const DevUnit& u, UnitState* slot
     finalize_stats<NT>(kp, u, slot, 0.0, 0.0);
     return;
   }
-  const long long M2 = m2lo;
-  const long long mad4 = f.da[0] + f.da[1];  // odd N: 2 d*, even N: d*(a) + d*(b)
-  if (tid == 0 && kp.hist.hint && u.hist_slot >= 0) {
-    kp.hist.hint[2 * u.hist_slot] = static_cast<unsigned long long>(M2);
-    kp.hist.hint[2 * u.hist_slot + 1] = static_cast<unsigned long long>(mad4);
-  }
-  const double med = __dmul_rn(static_cast<double>(M2), 0.5);
-  const double mad = __dmul_rn(static_cast<double>(mad4), 0.25);
-  if (!kp.sigma_std && mad > 0.0) {
-    finalize_stats<NT>(kp, u, slot, med, __dmul_rn(1.482602218505602, mad));
-  } else if (kp.sigma_std) {
-    // moments were accumulated with the coarse histogram
-    const unsigned __int128 s1 =
-        (static_cast<unsigned __int128>(__ldcg(slot->mom + 1)) << 64) | __ldcg(slot->mom + 0);
-    const unsigned __int128 s2 =
-        (static_cast<unsigned __int128>(__ldcg(slot->mom + 3)) << 64) | __ldcg(slot->mom + 2);
-    finalize_stats<NT>(kp, u, slot, med, moments_std(N, s1, s2));
-  } else {
-    if (tid == 0) {
-      slot->median_t = med;
-      slot->mom[0] = slot->mom[1] = slot->mom[2] = slot->mom[3] = 0;
-      slot->state = kStateMoments;
-    }
-    __syncthreads();
-  }
+  finish_selected<NT>(kp, u, slot, m2lo, f.da[0] + f.da[1], N);  // odd N: 2 d*, even N: d*(a) + d*(b)
 }
 
 // Builds the initial bin list from a coarse histogram in shared memory (warp
@@ -1886,6 +1919,193 @@ __device__ void unit_moments(const KParams& kp, const DevUnit& u, UnitState* us,
   finalize_stats<NT>(kp, u, us, __ldcg(&us->median_t), f.sig);
 }
 
+// Coarse histogram uh of every kept row of a unit, by one CTA: round 1 of a
+// unit whose block left its value window starts over from it.
+template <int DT, int NT>
+__device__ void count_coarse_rows(const DevUnit& u, const uint8_t* Fc, uint32_t* uh) {
+  using TR = Traits<DT>;
+  constexpr int VS = TR::kVec, SEG = 64 * VS, NW = NT / kWarp;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int T = u.T, nseg = (T + SEG - 1) / SEG;
+  const bool vin = (u.flags & kUnitInVec) != 0;
+  const uint8_t* gin = static_cast<const uint8_t*>(u.in);
+  for (int k = tid; k < kCoarseBins; k += NT) uh[k] = 0u;
+  __syncthreads();
+  for (int task = warp; task < u.C * nseg; task += NW) {
+    const int r = task / nseg, s = task - r * nseg;
+    if (Fc[r]) continue;
+    const uint8_t* grow = gin + static_cast<int64_t>(r) * u.in_stride * TR::kBytes;
+#pragma unroll
+    for (int q = 0; q < 2; ++q) {
+      const int x = s * SEG + q * 32 * VS + lane * VS;
+      if (x < T) {
+        uint32_t v[VS];
+        gload_vec<DT>(grow, x, T, vin, v);
+#pragma unroll
+        for (int j = 0; j < VS; ++j)
+          if (x + j < T) atomicAdd(&uh[coarse_key(v[j])], 1u);
+      }
+    }
+  }
+  __syncthreads();
+}
+
+// Round 1 of a unit counted in its value window (after the frequency pass):
+// takes the rows the frequency pass flagged out of the counts, then finds the
+// exact median and MAD of the pooled powers -- the same order statistics as
+// the bin-list selection -- from the window counts, provided they and every
+// count they rest on lie inside the window.  With the cumulative counts
+// cle(y) = #{x <= y}, exact for wlo - 1 <= y < wlo + kWinVals: the r-th
+// smallest value is the least y with cle(y) >= r + 1, and the r-th smallest
+// distance |2x - M2| is the least d with c(d) = cle(endB(d)) -
+// cle(endA(d) - 1) >= r + 1 (c grows with d, and so does the range it reads,
+// so the search stops at the first d that either reaches r + 1 or reads past
+// the window).  Returns false, having written nothing, when they do not.
+template <int DT, int NT>
+__device__ bool window_resolve(const KParams& kp, const DevUnit& u, UnitState* us, uint8_t* ws,
+                               Fixed<NT>& f) {
+  using TR = Traits<DT>;
+  constexpr int NW = NT / kWarp, PER = static_cast<int>(kWinVals) / NT;
+  static_assert(PER * NT == static_cast<int>(kWinVals), "whole counters per thread");
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int T = u.T;
+  const uint32_t wlo = f.wlo;
+  // Workspace: flagged-row list [0, 8K), Fc [34K, 36K) from the frequency
+  // pass, the window counts [36K, 52K)
+  const uint8_t* Fc = ws + 2 * kMaxChan * sizeof(unsigned long long) + kMaxChan;
+  int* frows = reinterpret_cast<int*>(ws);
+  uint32_t* sp = reinterpret_cast<uint32_t*>(ws + 36 * 1024);
+  for (int k = tid; k < static_cast<int>(kWinVals); k += NT) sp[k] = __ldcg(us->spec + k);
+  if (warp == 0) {
+    int n = 0;
+    for (int base = 0; base < u.C; base += kWarp) {
+      const int c = base + lane;
+      const bool fl = c < u.C && Fc[c];
+      const unsigned bal = __ballot_sync(kFull, fl);
+      if (fl) frows[n + __popc(bal & ((1u << lane) - 1u))] = c;
+      n += __popc(bal);
+    }
+    if (lane == 0) f.n_keep = n;
+  }
+  __syncthreads();
+  // the stats tasks counted every row: take out the flagged ones
+  const int nfr = f.n_keep;
+  uint32_t nb = 0;
+  if (nfr > 0) {
+    // warps over (flagged row, segment of 32 * NQ vectors): the NQ loads of a
+    // segment are in flight together
+    constexpr int VS = TR::kVec, NQ = 32 / VS, SEG = 32 * NQ * VS;
+    const int nseg = (T + SEG - 1) / SEG;
+    const bool vin = (u.flags & kUnitInVec) != 0;
+    const uint8_t* gin = static_cast<const uint8_t*>(u.in);
+    const uint64_t pol = l2_policy_drop();
+    for (int task = warp; task < nfr * nseg; task += NW) {
+      const int i = task / nseg, s = task - i * nseg;
+      const uint8_t* grow = gin + static_cast<int64_t>(frows[i]) * u.in_stride * TR::kBytes;
+      uint4 v[NQ];
+#pragma unroll
+      for (int q = 0; q < NQ; ++q) {
+        const int x = s * SEG + q * 32 * VS + lane * VS;
+        v[q] = x < T ? gload_raw<DT>(grow, x, T, vin, pol) : make_uint4(0u, 0u, 0u, 0u);
+      }
+#pragma unroll
+      for (int q = 0; q < NQ; ++q) {
+        const int x = s * SEG + q * 32 * VS + lane * VS;
+#pragma unroll
+        for (int j = 0; j < VS; ++j) {
+          if (x + j < T) {
+            const uint32_t val = raw_pw<DT>(v[q], j), t = val - wlo;
+            if (t < kWinVals) atomicSub(&sp[t], 1u);
+            else nb += val < wlo ? 1u : 0u;
+          }
+        }
+      }
+    }
+  }
+  nb = warp_sum32(nb);
+  if (lane == 0) f.red_u32[warp] = nb;
+  __syncthreads();
+  if (tid == 0) {
+    long long b = __ldcg(&us->win_below);
+    for (int w = 0; w < NW; ++w) b -= f.red_u32[w];
+    f.wbelow = b;
+  }
+  // inclusive prefix of the window counts, PER consecutive counters a thread
+  uint32_t loc[PER];
+#pragma unroll
+  for (int k = 0; k < PER; ++k) loc[k] = sp[tid * PER + k];
+#pragma unroll
+  for (int k = 1; k < PER; ++k) loc[k] += loc[k - 1];
+  uint32_t wt;
+  const uint32_t ex = warp_excl_scan(loc[PER - 1], lane, &wt);
+  __syncthreads();
+  if (lane == 0) f.red_u32[warp] = wt;
+  __syncthreads();
+  uint32_t off = ex;
+  for (int w = 0; w < warp; ++w) off += f.red_u32[w];
+#pragma unroll
+  for (int k = 0; k < PER; ++k) sp[tid * PER + k] = off + loc[k];
+  __syncthreads();
+  if (tid == 0) {
+    const long long N = __ldcg(&us->n_pool), below = f.wbelow, inw = sp[kWinVals - 1];
+    bool ok = below >= 0 && below + inw <= N;
+    if (!ok) set_error(kp, kErrInternal, 50);
+    // the r-th smallest value (0-based)
+    auto vrank = [&](long long r, long long* y) -> bool {
+      const long long q = r + 1 - below;
+      if (q < 1 || q > inw) return false;
+      int a = 0, b = static_cast<int>(kWinVals) - 1;
+      while (a < b) {
+        const int m = (a + b) >> 1;
+        if (static_cast<long long>(sp[m]) >= q) b = m;
+        else a = m + 1;
+      }
+      *y = static_cast<long long>(wlo) + a;
+      return true;
+    };
+    auto cle = [&](long long y, bool* exact) -> long long {
+      if (y < static_cast<long long>(wlo)) {  // y = wlo - 1 (-1 when wlo = 0): the count below
+        if (y + 1 < static_cast<long long>(wlo)) *exact = false;
+        return below;
+      }
+      if (y >= static_cast<long long>(wlo) + kWinVals) {
+        *exact = false;
+        return below + inw;
+      }
+      return below + sp[y - wlo];
+    };
+    const long long r1 = (N & 1) ? (N - 1) / 2 : N / 2 - 1, r2 = (N & 1) ? r1 : N / 2;
+    long long v1 = 0, v2 = 0;
+    ok = ok && N > 0 && vrank(r1, &v1) && vrank(r2, &v2);
+    const long long M2 = v1 + v2;
+    // the r-th smallest distance: least d in [0, 2 kWinVals + 2] (beyond it
+    // endB leaves the window) with c(d) >= r + 1 or an inexact c(d)
+    auto dist = [&](long long r, long long* D) -> bool {
+      long long a = 0, b = 2ll * kWinVals + 2;
+      while (a < b) {
+        const long long m = (a + b) >> 1;
+        bool e = true;
+        const long long c = cle(endB(M2, m), &e) - cle(endA(M2, m) - 1, &e);
+        if (!e || c >= r + 1) b = m;
+        else a = m + 1;
+      }
+      bool e = true;
+      const long long c = cle(endB(M2, a), &e) - cle(endA(M2, a) - 1, &e);
+      *D = a;
+      return e && c >= r + 1;
+    };
+    long long d1 = 0, d2 = 0;
+    ok = ok && dist(r1, &d1) && ((N & 1) ? (d2 = d1, true) : dist(r2, &d2));
+    f.resolved = ok ? 1 : 0;
+    f.m2lo = M2;
+    f.da[0] = d1 + d2;
+  }
+  __syncthreads();
+  if (!f.resolved) return false;
+  finish_selected<NT>(kp, u, us, f.m2lo, f.da[0], __ldcg(&us->n_pool));
+  return true;
+}
+
 // ------------------------------------------------------------------ unit-wide steps
 
 // After the last stats task of a unit: frequency pass, pooled coarse
@@ -1899,7 +2119,19 @@ __device__ LOFK_TASK_FN void unit_round1(const KParams& kp, const DevUnit& u, Un
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int T = u.T;
   frequency_pass<NT>(kp, u, us, ws, f);
-  if (__ldcg(&us->state) != kStateDone) {
+  bool recounted = false;
+  if (__ldcg(&us->state) != kStateDone && f.wmode) {
+    if (!window_resolve<DT, NT>(kp, u, us, ws, f)) {
+      // the block left its value window: count its kept rows in full
+      if (tid == 0 && kp.counters) atomicAdd(kp.counters + 1, 1);
+      count_coarse_rows<DT, NT>(u, ws + 2 * kMaxChan * sizeof(unsigned long long) + kMaxChan,
+                                reinterpret_cast<uint32_t*>(ws + 24 * 1024));
+      recounted = true;
+    } else if (__ldcg(&us->state) == kStateMoments) {
+      unit_moments<DT, NT>(kp, u, us, ws, f);
+    }
+  }
+  if (__ldcg(&us->state) != kStateDone && (!f.wmode || recounted)) {
     // Workspace (bytes): the bin list lo [0, 8K), hi [8K, 16K), cum [16K,
     // 24K) once the flagged rows are out; before that the key -> offset map
     // [0, 4.2K) and the flagged-row list [4.5K, 6.25K); histogram [24K,
@@ -1907,6 +2139,10 @@ __device__ LOFK_TASK_FN void unit_round1(const KParams& kp, const DevUnit& u, Un
     const uint8_t* Fc = ws + 2 * kMaxChan * sizeof(unsigned long long) + kMaxChan;
     uint32_t* uh = reinterpret_cast<uint32_t*>(ws + 24 * 1024);
     uint32_t* sp = reinterpret_cast<uint32_t*>(ws + 36 * 1024);
+    if (recounted) {
+      if (tid == 0) f.n_tgt = 0;
+      __syncthreads();
+    } else {
     if (tid < kWarp) {
       int nt = 0;
       if (kp.hist.hint && u.hist_slot >= 0)
@@ -2019,6 +2255,8 @@ __device__ LOFK_TASK_FN void unit_round1(const KParams& kp, const DevUnit& u, Un
       us->mom_ready = 1;
     }
     __syncthreads();
+    }  // counts of the stats tasks
+    const int nspec_t = f.n_tgt;
     const BinList B0 = build_coarse_list<NT>(kp, us, uh, ws);
     // merge the value-by-value counts of the hinted bins (as a fine round)
     if (tid == 0) {
@@ -2057,7 +2295,7 @@ __device__ LOFK_TASK_FN void unit_round1(const KParams& kp, const DevUnit& u, Un
   __syncthreads();
   if (tid == 0) {
     const bool fine = __ldcg(&us->state) == kStateFine;
-    if (fine && kp.counters) atomicAdd(kp.counters, 1);
+    if ((fine || recounted) && kp.counters) atomicAdd(kp.counters, 1);
     // a unit that needs refinement rounds is finished by the same CTA
     // (task_stats), which releases it then
     if (!fine) {
@@ -2093,63 +2331,77 @@ __device__ LOFK_TASK_FN void unit_round2(const KParams& kp, const DevUnit& u, Un
 
 // ------------------------------------------------------------------ tasks
 
-// Stats task: row power sums (spectrum) and the coarse histogram of its rows.
-template <int DT, int NT>
-__device__ LOFK_TASK_FN void task_stats(const KParams& kp, const DevUnit& u, UnitState* us, const Task& tk,
-                           uint8_t* ws, Fixed<NT>& f) {
+// One shared-memory count, by a reduction without return value; predicated:
+// only when p holds.
+__device__ __forceinline__ void red_shared_inc(uint32_t addr) {
+  asm volatile("red.shared.add.u32 [%0], 1;" ::"r"(addr) : "memory");
+}
+__device__ __forceinline__ void red_shared_inc_if(bool p, uint32_t addr) {
+  asm volatile(
+      "{\n\t.reg .pred q;\n\tsetp.ne.u32 q, %0, 0;\n\t@q red.shared.add.u32 [%1], 1;\n\t}" ::"r"(
+          static_cast<uint32_t>(p)),
+      "r"(addr)
+      : "memory");
+}
+
+// Row power sums (spectrum) of rows [row0, row0 + R) of a unit into f.rowS,
+// and one count per sample: WIN, its value's counter in the value window
+// [wlo, wlo + kWinVals) (win), values below the window in the returned
+// per-thread total and those above it nowhere; otherwise its value's counter
+// inside a target bin (win = the spec counters, via the key -> offset map
+// moff), else its coarse bin (hist).  Warp w owns rows w, w + NW, ... and
+// walks their segments in order, the loads of its next segment in flight
+// while it counts the current one; a row's sum is reduced once, when the
+// warp leaves the row.  WIN needs
+// 1 <= wlo <= 2^31 - kWinVals, so that val - wlo is exact as a signed value
+// for every power (at most 2^31).
+template <int DT, int NT, bool WIN>
+__device__ __forceinline__ uint32_t stats_rows(const DevUnit& u, int row0, int R, uint32_t* hist,
+                                               uint32_t* win, const uint32_t* moff, uint32_t nsc,
+                                               uint32_t wlo, Fixed<NT>& f) {
   using TR = Traits<DT>;
   constexpr int VS = TR::kVec, NQ = 32 / VS, SEG = 32 * NQ * VS, NW = NT / kWarp;
-  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  const int T = u.T, R = tk.nrows, row0 = tk.row0, nseg = (T + SEG - 1) / SEG;
+  // per-lane row sums: 32 bits hold a lane's share of a ci8 row (powers at
+  // most 2^15, a lane's share at most 2^17 of them for any admissible row)
+  using Acc = std::conditional_t<DT == LOF_CI8, uint32_t, unsigned long long>;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int T = u.T, nseg = (T + SEG - 1) / SEG;
   const bool vin = (u.flags & kUnitInVec) != 0;
   const uint8_t* gin = static_cast<const uint8_t*>(u.in);
-  uint32_t* hist = reinterpret_cast<uint32_t*>(ws);                     // [0, 4.2K)
-  uint32_t* spec = reinterpret_cast<uint32_t*>(ws + 6 * 1024);           // [6K, 22K)
-  uint32_t* moff = reinterpret_cast<uint32_t*>(ws + 22 * 1024);          // [22K, 26.2K)
-  if (tid < kWarp) {
-    int nt = 0;
-    if (kp.hist.hint && u.hist_slot >= 0)
-      nt = spec_targets(__ldcg(kp.hist.hint + 2 * u.hist_slot),
-                        __ldcg(kp.hist.hint + 2 * u.hist_slot + 1), f.tgt);
-    if (tid == 0) f.n_tgt = nt;
-  }
-  for (int i = tid; i < kCoarseBins; i += NT) {
-    hist[i] = 0u;
-    moff[i] = kNoTarget;
-  }
-  for (int i = tid; i < kMaxSpec; i += NT) spec[i] = 0u;
-  for (int r = tid; r < R; r += NT) f.rowS[r] = 0;
-  __syncthreads();
-  const int nspec_t = f.n_tgt;
-  if (tid < nspec_t) moff[coarse_key(f.tgt[tid].lo)] = f.tgt[tid].base - f.tgt[tid].lo;
-  const uint32_t nsc = nspec_t ? f.tgt[nspec_t - 1].base + (f.tgt[nspec_t - 1].hi - f.tgt[nspec_t - 1].lo) + 1u : 0u;
-  __syncthreads();
-  // software-pipelined: the loads of a warp's next segment are in flight
-  // while it histograms the current one
-  const int nsegs = R * nseg;
-  const uint64_t pol = l2_policy_keep();
+  const int nk = (warp < R ? (R - warp + NW - 1) / NW : 0) * nseg;  // segments of this warp
+  const uint64_t pol = l2_policy_drop();
+  const uint32_t wsa = saddr(win), hsa = saddr(hist);
   uint4 cur[NQ], nxt[NQ];
-  auto load_seg = [&](int task, uint4 (&v)[NQ]) {
-    const int r = task / nseg, s = task - r * nseg;
-    const uint8_t* grow = gin + static_cast<int64_t>(row0 + min(r, R - 1)) * u.in_stride * TR::kBytes;
+  uint32_t below = 0;
+  // the warp's k-th segment: segment k % nseg of row warp + (k / nseg) * NW
+  auto load_seg = [&](int k, uint4 (&v)[NQ]) {
+    const int kr = k / nseg, s = k - kr * nseg;
+    const uint8_t* grow =
+        gin + static_cast<int64_t>(row0 + min(warp + kr * NW, R - 1)) * u.in_stride * TR::kBytes;
 #pragma unroll
     for (int q = 0; q < NQ; ++q) {
       const int x = s * SEG + q * 32 * VS + lane * VS;
-      v[q] = (task < nsegs && x < T) ? gload_raw<DT>(grow, x, T, vin, pol) : make_uint4(0u, 0u, 0u, 0u);
+      v[q] = (k < nk && x < T) ? gload_raw<DT>(grow, x, T, vin, pol) : make_uint4(0u, 0u, 0u, 0u);
     }
   };
-  load_seg(warp, cur);
-  for (int task = warp; task < nsegs; task += NW) {
-    load_seg(task + NW, nxt);
-    const int r = task / nseg, s = task - r * nseg;
-    unsigned long long sum = 0;
-    // one count per sample: its value's counter inside a target bin (the
-    // bin's coarse count is rebuilt from those below), else its bin
+  Acc sum = 0;
+  load_seg(0, cur);
+  for (int k = 0; k < nk; ++k) {
+    load_seg(k + 1, nxt);
+    const int kr = k / nseg, s = k - kr * nseg;
     auto count = [&](uint32_t val) {
       sum += val;
-      const uint32_t key = coarse_key(val);
-      const uint32_t si = val + moff[key];  // spec index, or >= nsc off the targets
-      atomicAdd(si < nsc ? spec + si : hist + key, 1u);
+      if constexpr (WIN) {
+        const int t = static_cast<int>(val - wlo);
+        below += static_cast<uint32_t>(t) >> 31;
+        red_shared_inc_if(static_cast<uint32_t>(t) < kWinVals, wsa + 4u * static_cast<uint32_t>(t));
+      } else {
+        // the value's counter inside a target bin (the bin's coarse count is
+        // rebuilt from those below), else its bin
+        const uint32_t key = coarse_key(val);
+        const uint32_t si = val + moff[key];  // spec index, or >= nsc off the targets
+        red_shared_inc(si < nsc ? wsa + 4u * si : hsa + 4u * key);
+      }
     };
 #pragma unroll
     for (int q = 0; q < NQ; ++q) {
@@ -2163,11 +2415,66 @@ __device__ LOFK_TASK_FN void task_stats(const KParams& kp, const DevUnit& u, Uni
           if (x + j < T) count(raw_pw<DT>(cur[q], j));
       }
     }
-    sum = warp_sum64(sum);
-    if (lane == 0) atomicAdd(&f.rowS[r], sum);
+    if (s == nseg - 1) {  // the warp leaves the row: its sum
+      const unsigned long long rs = warp_sum64(static_cast<unsigned long long>(sum));
+      if (lane == 0) f.rowS[warp + kr * NW] = rs;
+      sum = 0;
+    }
 #pragma unroll
     for (int q = 0; q < NQ; ++q) cur[q] = nxt[q];
   }
+  return below;
+}
+
+// Stats task: row power sums (spectrum) and the counts of its rows -- value
+// window counts when the unit has one, else the coarse histogram with exact
+// counts in the hinted bins.
+template <int DT, int NT>
+__device__ LOFK_TASK_FN void task_stats(const KParams& kp, const DevUnit& u, UnitState* us, const Task& tk,
+                           uint8_t* ws, Fixed<NT>& f) {
+  using TR = Traits<DT>;
+  constexpr int VS = TR::kVec, NW = NT / kWarp;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int T = u.T, R = tk.nrows, row0 = tk.row0;
+  const bool vin = (u.flags & kUnitInVec) != 0;
+  const uint8_t* gin = static_cast<const uint8_t*>(u.in);
+  uint32_t* hist = reinterpret_cast<uint32_t*>(ws);                     // [0, 4.2K)
+  uint32_t* spec = reinterpret_cast<uint32_t*>(ws + 6 * 1024);           // [6K, 22K)
+  uint32_t* moff = reinterpret_cast<uint32_t*>(ws + 22 * 1024);          // [22K, 26.2K)
+  const bool hinted = kp.hist.hint && u.hist_slot >= 0;
+  if (tid == 0) {
+    uint32_t wlo = 0;
+    f.wmode = (hinted && !kp.sigma_std && (kp.schedule & LOF_SCHED_VALUE_WINDOW) &&
+               hint_window(__ldcg(kp.hist.hint + 2 * u.hist_slot),
+                           __ldcg(kp.hist.hint + 2 * u.hist_slot + 1), &wlo))
+                  ? 1
+                  : 0;
+    f.wlo = wlo;
+  }
+  __syncthreads();
+  const bool wmode = f.wmode != 0;
+  if (tid < kWarp) {
+    int nt = 0;
+    if (hinted && !wmode)
+      nt = spec_targets(__ldcg(kp.hist.hint + 2 * u.hist_slot),
+                        __ldcg(kp.hist.hint + 2 * u.hist_slot + 1), f.tgt);
+    if (tid == 0) f.n_tgt = nt;
+  }
+  if (!wmode) {
+    for (int i = tid; i < kCoarseBins; i += NT) {
+      hist[i] = 0u;
+      moff[i] = kNoTarget;
+    }
+  }
+  for (int i = tid; i < kMaxSpec; i += NT) spec[i] = 0u;
+  for (int r = tid; r < R; r += NT) f.rowS[r] = 0;
+  __syncthreads();
+  const int nspec_t = f.n_tgt;
+  if (tid < nspec_t) moff[coarse_key(f.tgt[tid].lo)] = f.tgt[tid].base - f.tgt[tid].lo;
+  const uint32_t nsc = nspec_t ? f.tgt[nspec_t - 1].base + (f.tgt[nspec_t - 1].hi - f.tgt[nspec_t - 1].lo) + 1u : 0u;
+  __syncthreads();
+  const uint32_t below = wmode ? stats_rows<DT, NT, true>(u, row0, R, hist, spec, moff, nsc, f.wlo, f)
+                               : stats_rows<DT, NT, false>(u, row0, R, hist, spec, moff, nsc, 0u, f);
   if (kp.sigma_std) {
     // exact 128-bit moments for the std estimator, in a pass of their own
     constexpr int SEG2 = 64 * VS;
@@ -2201,6 +2508,10 @@ __device__ LOFK_TASK_FN void task_stats(const KParams& kp, const DevUnit& u, Uni
       f.red_c[warp] = hi;
     }
   }
+  if (wmode) {
+    const uint32_t b = warp_sum32(below);
+    if (lane == 0 && b) atomicAdd(&us->win_below, static_cast<int>(b));
+  }
   __syncthreads();
   // coarse counts of the target bins: the sums of their value counters (one
   // warp per bin)
@@ -2213,16 +2524,16 @@ __device__ LOFK_TASK_FN void task_stats(const KParams& kp, const DevUnit& u, Uni
   }
   __syncthreads();
   for (int r = tid; r < R; r += NT) kp.chan_S[u.chan_off + row0 + r] = f.rowS[r];
-  for (int k = tid; k < kCoarseBins; k += NT) {
-    const uint32_t h = hist[k];
-    if (h) atomicAdd(us->coarse + k, h);
-  }
-  if (nspec_t) {
-    const int nsc = static_cast<int>(f.tgt[nspec_t - 1].base + (f.tgt[nspec_t - 1].hi - f.tgt[nspec_t - 1].lo) + 1u);
-    for (int i = tid; i < nsc; i += NT) {
-      const uint32_t h = spec[i];
-      if (h) atomicAdd(us->spec + i, h);
+  if (!wmode) {
+    for (int k = tid; k < kCoarseBins; k += NT) {
+      const uint32_t h = hist[k];
+      if (h) atomicAdd(us->coarse + k, h);
     }
+  }
+  const int nflush = wmode ? static_cast<int>(kWinVals) : static_cast<int>(nsc);
+  for (int i = tid; i < nflush; i += NT) {
+    const uint32_t h = spec[i];
+    if (h) atomicAdd(us->spec + i, h);
   }
   if (tid == 0 && kp.sigma_std) {
     unsigned __int128 t1 = 0, t2 = 0;

@@ -23,7 +23,7 @@ LOF_CI8, LOF_CI16, LOF_F32, LOF_CF32 = 1, 2, 3, 4
 LOF_SIGMA_MAD, LOF_SIGMA_STD, LOF_SIGMA_WINSOR = 0, 1, 2
 LOF_TIME_PER_CHANNEL, LOF_TIME_INTEGRATED, LOF_TIME_2D = 0, 1, 2
 LOF_SCOPE_POOLED, LOF_SCOPE_CHANNEL = 0, 1
-LOF_SCHED_PACKED, LOF_SCHED_BOUND64, LOF_SCHED_COALESCED, LOF_SCHED_SET = 1, 2, 4, 0x80
+LOF_SCHED_PACKED, LOF_SCHED_BOUND64, LOF_SCHED_COALESCED, LOF_SCHED_VALUE_WINDOW, LOF_SCHED_SET = 1, 2, 4, 8, 0x80
 
 EXPORTED = [
     "lof_default_params", "lof_create", "lof_flag_block", "lof_flag_block_host",
@@ -362,7 +362,7 @@ class Flagger:
         """Work counters of the last flag_block (lof_block_counters)."""
         c = (ctypes.c_int64 * 2)()
         _check(library().lof_block_counters(self.ctx, ctypes.c_void_p(self._stream(stream)), c), self.ctx)
-        return {"units_refined": int(c[0]), "refine_tasks": int(c[1])}
+        return {"units_refined": int(c[0]), "refine_passes": int(c[1])}
 
     def set_tuning(self, **kw):
         _check(lof_set_tuning(self.ctx, **kw), self.ctx)

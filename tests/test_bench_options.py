@@ -82,7 +82,7 @@ def test_gpu_line_assembly_with_a_fake_run(monkeypatch, capsys):
                           stat_samples=262144),
            "e2e": {"value": 16000.0, "unit": "Msamples/s", "h2d_bytes_per_step": 1,
                    "d2h_bytes_per_step": 1},
-           "refine": [{"units_refined": 0, "refine_tasks": 0}, {"units_refined": 2, "refine_tasks": 6}]}
+           "refine": [{"units_refined": 0, "refine_passes": 0}, {"units_refined": 2, "refine_passes": 6}]}
     monkeypatch.setattr(bench, "run_gpu", lambda args: res)
     for k in ("RANK", "WORLD_SIZE", "LOCAL_RANK"):
         monkeypatch.delenv(k, raising=False)
