@@ -490,6 +490,9 @@ int host_count_tasks(const HostCfg& h, int dtype, const lof_unit* units, int n_u
     const int Rs = stat_rows(T, h.tuning.stat_samples);
     n += (C + Rs - 1) / Rs + (C + Rc - 1) / Rc;
   }
+  // room for the split queue tails (host_prepare): three more tasks for each
+  // of up to one task per CTA in each of the two queues
+  n += 6 * int64_t(h.n_sm) * std::max(1, h.tuning.ctas_per_sm);
   if (n > (int64_t(1) << 30)) {
     snprintf(why, nwhy, "too many tasks");
     return LOF_ERR_INVALID;
@@ -608,34 +611,51 @@ int host_prepare(const HostCfg& h, int dtype, const lof_unit* units, int n_units
   const int inflight = static_cast<int>(std::ceil(grid / std::max(1.0, avg)));
   const int dF = inflight + 2;
   int n = 0;
-  auto emit = [&](int ui, int kind) -> bool {
-    const DevUnit& d = du[ui];
-    const int rows = kind == kTaskFlag ? (d.C + d.nC - 1) / d.nC : (d.C + d.nS - 1) / d.nS;
-    for (int r0 = 0; r0 < d.C; r0 += rows) {
-      if (n >= max_tasks) return false;
-      tasks[n++] = Task{ui, kind, r0, std::min(rows, d.C - r0)};
+  // The last `grid` tasks of each queue go in quarters (rows / 4): the CTAs
+  // take tasks in queue order, so the large ones go first and the small ones
+  // even out the CTAs' finishing times (a queue of 10.1 waves of equal tasks
+  // would otherwise keep a tenth of the CTAs busy for a whole task at the
+  // end).  Only when the quarters fit the task buffer.
+  int64_t q_stats = 0, q_flag = 0;
+  for (int ui = 0; ui < n_units; ++ui) {
+    q_stats += du[ui].nS;
+    q_flag += du[ui].nC;
+  }
+  const int64_t k_stats = std::min<int64_t>(q_stats, grid), k_flag = std::min<int64_t>(q_flag, grid);
+  const bool split = q_stats + q_flag + 3 * (k_stats + k_flag) <= max_tasks;
+  auto emit_queue = [&](int kind) -> bool {
+    const int64_t q = kind == kTaskFlag ? q_flag : q_stats;
+    const int64_t first_split = split ? q - (kind == kTaskFlag ? k_flag : k_stats) : q;
+    int64_t idx = 0;
+    for (int ui = 0; ui < n_units; ++ui) {
+      DevUnit& d = du[ui];
+      const int rows = kind == kTaskFlag ? (d.C + d.nC - 1) / d.nC : (d.C + d.nS - 1) / d.nS;
+      int cnt = 0;
+      for (int r0 = 0; r0 < d.C; r0 += rows, ++idx) {
+        const int nr = std::min(rows, d.C - r0);
+        const int sub = (idx >= first_split && nr >= 4) ? (nr + 3) / 4 : nr;
+        for (int s0 = r0; s0 < r0 + nr; s0 += sub) {
+          if (n >= max_tasks) return false;
+          tasks[n++] = Task{ui, kind, s0, std::min(sub, r0 + nr - s0)};
+          ++cnt;
+        }
+      }
+      if (kind == kTaskStats) d.nS = cnt;  // the unit's stats tasks, counted on completion
+      else d.nC = cnt;
     }
     return true;
   };
   // (Refinement rounds, needed when a unit's first counting pass leaves its
   // statistics open, run in the CTA that finishes that pass; no task waits.)
   (void)dF;
-  bool ok = true;
-  for (int ui = 0; ui < n_units && ok; ++ui) ok = emit(ui, kTaskStats);
+  bool ok = emit_queue(kTaskStats);
   const int n_stats = n;
-  for (int ui = 0; ui < n_units && ok; ++ui) ok = emit(ui, kTaskFlag);
+  ok = ok && emit_queue(kTaskFlag);
   if (!ok) {
     snprintf(why, nwhy, "more than %d tasks in one block", max_tasks);
     return LOF_ERR_INVALID;
   }
-  // the row runs must match the task counts recorded per unit
-  for (int i = 0; i < n_units; ++i) {
-    DevUnit& d = du[i];
-    const int rs = (d.C + d.nS - 1) / d.nS, rc = (d.C + d.nC - 1) / d.nC;
-    d.nS = (d.C + rs - 1) / rs;
-    d.nF = 0;
-    d.nC = (d.C + rc - 1) / rc;
-  }
+  for (int i = 0; i < n_units; ++i) du[i].nF = 0;
   out->n_tasks = n;
   out->n_tasks_stats = n_stats;
   out->n_chan = chan;

@@ -442,6 +442,8 @@ struct Fixed {
   int rowNFlag[kMaxRowsPerTask];
   uint8_t rowFc[kMaxRowsPerTask];
   uint8_t rowFh[kMaxRowsPerTask];
+  uint8_t rowHon[kMaxRowsPerTask];   // the row's history threshold applies (count >= history_min)
+  double rowThr[kMaxRowsPerTask];    // that threshold (mean + k * stddev of the ring)
   int keep[kMaxRowsPerTask];
   long long K[kKTable];
   double median_t, sigma_t;
@@ -2594,7 +2596,7 @@ __device__ LOFK_TASK_FN void task_fine(const KParams& kp, const DevUnit& u, Unit
 // and adds the row to the task's counts.  One thread; returns whether the
 // whole row is flagged.
 template <int NT>
-__device__ __forceinline__ int history_row(const KParams& kp, const DevUnit& u, int c, int T,
+__device__ __forceinline__ int history_row(const KParams& kp, const DevUnit& u, int c, int r, int T,
                                            int nfl, unsigned long long su, Fixed<NT>& f) {
   const long long h = u.hist_slot >= 0 ? u.hist_slot + c : -1;
   const int n = T - nfl;
@@ -2602,14 +2604,11 @@ __device__ __forceinline__ int history_row(const KParams& kp, const DevUnit& u, 
   if (n > 0) {
     const double cur = __ddiv_rn(__ull2double_rn(su), static_cast<double>(n));
     double staged = cur;
-    if (kp.enable_history && h >= 0) {
-      const int cnt = kp.hist.count[h];
-      if (cnt >= kp.history_min && cnt > 0) {
-        const double thr = kp.hist.thr[h];
-        if (!(cur < thr)) {
-          fh = 1;
-          staged = thr;
-        }
+    if (f.rowHon[r]) {
+      const double thr = f.rowThr[r];
+      if (!(cur < thr)) {
+        fh = 1;
+        staged = thr;
       }
     }
     if (h >= 0) {
@@ -2674,6 +2673,19 @@ __device__ LOFK_TASK_FN void task_flag(const KParams& kp, const DevUnit& u, Unit
     f.rowFlagSum[r] = 0;
     f.rowNFlag[r] = 0;
     f.rowFh[r] = 0;
+    // the history thresholds of the task's rows (Section 4.1), read once here
+    const long long h = u.hist_slot >= 0 ? u.hist_slot + row0 + r : -1;
+    uint8_t on = 0;
+    double thr = 0.0;
+    if (kp.enable_history && h >= 0) {
+      const int cnt = kp.hist.count[h];
+      if (cnt >= kp.history_min && cnt > 0) {
+        on = 1;
+        thr = kp.hist.thr[h];
+      }
+    }
+    f.rowHon[r] = on;
+    f.rowThr[r] = thr;
   }
   for (int i = tid; i < R * MW; i += NT) smbits[i] = 0u;
   if (tid == 0) {
@@ -2797,7 +2809,7 @@ __device__ LOFK_TASK_FN void task_flag(const KParams& kp, const DevUnit& u, Unit
         su_row += su;
         if (sg == nsg - 1) {
           int fh = 0;
-          if (lane == 0) fh = history_row<NT>(kp, u, c, T, nfl_row, su_row, f);
+          if (lane == 0) fh = history_row<NT>(kp, u, c, r, T, nfl_row, su_row, f);
           fh = __shfl_sync(kFull, fh, 0);
           if (fh) {
             bulk_wait_all();  // the row's bulk stores land before the rewrite
@@ -2900,14 +2912,11 @@ __device__ LOFK_TASK_FN void task_flag(const KParams& kp, const DevUnit& u, Unit
         const unsigned long long su = f.rowS[r] - f.rowFlagSum[r];
         const double cur = __ddiv_rn(__ull2double_rn(su), static_cast<double>(n));
         double staged = cur;
-        if (kp.enable_history && h >= 0) {
-          const int cnt = kp.hist.count[h];
-          if (cnt >= kp.history_min && cnt > 0) {
-            const double thr = kp.hist.thr[h];
-            if (!(cur < thr)) {
-              fh = 1;
-              staged = thr;
-            }
+        if (f.rowHon[r]) {
+          const double thr = f.rowThr[r];
+          if (!(cur < thr)) {
+            fh = 1;
+            staged = thr;
           }
         }
         if (h >= 0) {
