@@ -270,7 +270,13 @@ typedef struct {
                               with d small enough, counts its pooled powers value by value
                               in a window of 4096 values around m plus one count below it,
                               and resolves median and MAD from those counts; a block whose
-                              statistics leave the window is counted again in full).
+                              statistics leave the window is counted again in full), and for
+                              Stokes I (LOF_F32) units LOF_SCHED_F32_CLUSTER (one thread-block
+                              cluster of 16, or 8, CTAs per unit holds the unit in shared
+                              memory, read from global memory once, where it fits: at most 256
+                              channels; otherwise, or without it, one CTA per unit; the input is
+                              read once, but the unit's statistics passes then wait on cluster
+                              barriers, so it is off by default).
                               Default LOF_SCHED_SET | LOF_SCHED_PACKED | LOF_SCHED_BOUND64 |
                               LOF_SCHED_COALESCED | LOF_SCHED_VALUE_WINDOW */
 } lof_tuning;
@@ -279,6 +285,7 @@ enum {
   LOF_SCHED_BOUND64 = 2,
   LOF_SCHED_COALESCED = 4,
   LOF_SCHED_VALUE_WINDOW = 8,
+  LOF_SCHED_F32_CLUSTER = 16,
   LOF_SCHED_SET = 0x80
 };
 int lof_set_tuning(lof_ctx *ctx, const lof_tuning *t);
@@ -291,8 +298,8 @@ int lof_get_tuning(const lof_ctx *ctx, lof_tuning *t);
  * general time pass, the bound on the 64-sample windows on or off, coalesced
  * or bulk data stores, value-window statistics on or off), and keeps the fastest in the context (*best, *best_ms
  * if not NULL).  Results never depend on the tuning.  Synchronous; stages
- * history values like any lof_flag_block call (do not commit them).  F32
- * units have a single shape. */
+ * history values like any lof_flag_block call (do not commit them).  Float
+ * units have no launch shape; for F32 the cluster bit is tried both ways. */
 int lof_autotune(lof_ctx *ctx, int dtype, const lof_unit *units, int n_units, int reps,
                  void *cuda_stream, lof_tuning *best, float *best_ms);
 

@@ -392,7 +392,7 @@ extern "C" int lof_set_tuning(lof_ctx* c, const lof_tuning* t) {
   if (t->schedule) {
     if (!(t->schedule & LOF_SCHED_SET) ||
         (t->schedule & ~(LOF_SCHED_SET | LOF_SCHED_PACKED | LOF_SCHED_BOUND64 | LOF_SCHED_COALESCED |
-                         LOF_SCHED_VALUE_WINDOW)))
+                         LOF_SCHED_VALUE_WINDOW | LOF_SCHED_F32_CLUSTER)))
       return fail(c, LOF_ERR_INVALID, "schedule: LOF_SCHED_SET plus LOF_SCHED_* flags");
     n.schedule = t->schedule;
   }
@@ -504,6 +504,7 @@ int host_count_tasks(const HostCfg& h, int dtype, const lof_unit* units, int n_u
 // Unit descriptors of a float32 block (one CTA per unit, no tasks).
 int host_prepare_f32(const HostCfg& h, const lof_unit* units, int n_units, DevUnit* du, Prep* out) {
   int maxT = 1;
+  out->max_C = 1;
   int64_t chan = 0;
   for (int i = 0; i < n_units; ++i) {
     const lof_unit& u = units[i];
@@ -531,7 +532,9 @@ int host_prepare_f32(const HostCfg& h, const lof_unit* units, int n_units, DevUn
       flags |= kUnitMaskVec;
     d.flags = flags;
     maxT = std::max(maxT, u.n_time);
+    out->max_C = std::max(out->max_C, u.n_chan);
   }
+  out->max_T = maxT;
   out->plan = Plan{256, 1, lofk_f32_smem(maxT)};
   out->n_tasks = 0;
   out->n_chan = chan;
@@ -737,7 +740,11 @@ int host_launch_kernel(const lof_params& P, const HostCfg& h, int dtype, const P
   kp.schedule = h.tuning.schedule;
   int krc;
   if (is_float(dtype)) {
-    krc = lofk_launch_f32x(&kp, n_units, h.n_sm, pr.plan.smem, stream, dtype == LOF_CF32);
+    // Stokes I units in clusters where they fit, else one CTA per unit
+    krc = (dtype == LOF_F32 && (h.tuning.schedule & LOF_SCHED_F32_CLUSTER))
+              ? lofk_launch_f32c(&kp, n_units, pr.max_C, pr.max_T, stream)
+              : 1;
+    if (krc == 1) krc = lofk_launch_f32x(&kp, n_units, h.n_sm, pr.plan.smem, stream, dtype == LOF_CF32);
   } else if (exact_stats_mode(P) >= 0) {
     krc = lofk_launch_integ(dtype, &kp, n_units, h.n_sm, stream, exact_stats_mode(P), P.integ_chan,
                             P.integ_time);
@@ -1559,7 +1566,11 @@ extern "C" int lof_autotune(lof_ctx* c, int dtype, const lof_unit* units, int n_
   const lof_tuning saved = c->tuning;
   std::vector<lof_tuning> cands;
   if (is_float(dtype)) {
-    cands.push_back(saved);  // one CTA per unit: no launch shape to choose
+    // no launch shape to choose: one CTA per unit, or (Stokes I) one cluster per unit
+    cands.push_back(saved);
+    lof_tuning t = saved;
+    t.schedule = saved.schedule ^ LOF_SCHED_F32_CLUSTER;
+    if (dtype == LOF_F32) cands.push_back(t);
   } else {
     for (int threads : {128, 256})
       for (int ctas : {1, 2, 3, 4}) {

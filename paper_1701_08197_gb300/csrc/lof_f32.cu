@@ -27,6 +27,7 @@
 // Float results match the binary64 oracle except for samples whose deciding
 // window sum lies within a relative 1e-5 of its threshold (and the windows a
 // changed flag touches later).
+#include <cooperative_groups.h>
 #include <cuda_runtime.h>
 
 #include <cstdint>
@@ -371,6 +372,71 @@ __device__ double pooled_std(const DevUnit& u, const uint8_t* Fc, F32Shared& f) 
   return __dsqrt_rn(__ddiv_rn(acc[1], static_cast<double>(f.n_pool)));
 }
 
+// ---- Stokes I units in a thread-block cluster (F32, Section 3's
+// beamformed placement)
+// One cluster of CL CTAs (CL = 16 where the device allows clusters that
+// large, else 8) flags one unit: CTA r holds rows [r R, r R + R) of it in
+// shared memory (R = ceil(C / CL)), read from global memory once.  The
+// steps and their arithmetic are those of f32_unit; what the CTAs share goes
+// through distributed shared memory:
+//   * the row sums S[c] and finite counts (every CTA writes its rows into
+//     every CTA), so each CTA runs the frequency pass on the whole spectrum;
+//   * each radix-select pass: every CTA histograms its rows, CTA r adds up
+//     bins [r B / CL, (r + 1) B / CL) of all CTAs and writes the sums into
+//     every CTA, each CTA then picks the same digit;
+//   * the binary64 sums of the std estimator (per CTA, added in rank order);
+//   * the flag counts, added into CTA 0, which reports the unit's statistics.
+// Row sums, window sums, order statistics and the history test are computed
+// exactly as in f32_unit (same per-row summation order), so both kernels
+// give the same flags; only the std estimator's binary64 sums may round
+// differently (their order follows the CTAs).
+namespace cg = cooperative_groups;
+
+constexpr int kCMaxCl = 256;                 // channels of a unit in the cluster path
+constexpr int kClMaxSeg = 48;                // row segments (1024-sample spans) of one row
+
+// shared-memory layout of one cluster CTA (bytes), for R rows of T samples
+constexpr int kOffClS = 0;                                // double S[256]
+constexpr int kOffClSrt = kOffClS + 8 * kCMaxCl;          // u64 sort keys [256]
+constexpr int kOffClFin = kOffClSrt + 8 * kCMaxCl;        // int finite count [256]
+constexpr int kOffClFc = kOffClFin + 4 * kCMaxCl;         // uint8 Fc [256]
+constexpr int kOffClFire = kOffClFc + kCMaxCl;            // uint8 fire [256]
+constexpr int kOffClHist = kOffClFire + kCMaxCl;          // u32 local hist[2][2048]
+constexpr int kOffClTot = kOffClHist + 2 * 2048 * 4;      // u32 cluster hist[2][2048]
+constexpr int kOffClRed = kOffClTot + 2 * 2048 * 4;       // double red[16], u64 cnt[4]
+constexpr int kOffClRows = kOffClRed + 16 * 8 + 4 * 8;    // per-row: segment sums, counts
+constexpr int kClRowBytes = kClMaxSeg * 8 + 4 * 4;        //   double su[48]; int nflag, nentry, fh, pad
+__host__ __device__ constexpr int cl_words(int T) { return (T + 31) / 32; }
+__host__ __device__ constexpr int cl_pitch(int T) { return (T + 3) & ~3; }  // floats per stored row
+__host__ __device__ inline int cl_off_mrow(int R) { return (kOffClRows + R * kClRowBytes + 15) & ~15; }
+__host__ __device__ inline int cl_off_data(int R, int T) {
+  return (cl_off_mrow(R) + R * cl_words(T) * 4 + 15) & ~15;
+}
+__host__ __device__ inline int cl_smem(int R, int T) { return cl_off_data(R, T) + R * cl_pitch(T) * 4; }
+
+// 4 samples of a stored row at x (x a multiple of 4); past T: NaN
+__device__ __forceinline__ float4 ld4s(const float* srow, int x, int T) {
+  if (x + 4 <= T) return *reinterpret_cast<const float4*>(srow + x);
+  float a[4];
+#pragma unroll
+  for (int j = 0; j < 4; ++j) a[j] = x + j < T ? srow[x + j] : __int_as_float(0x7FC00000);
+  return make_float4(a[0], a[1], a[2], a[3]);
+}
+
+// Adds the CTAs' histograms (nbins words) and leaves the sums in every CTA's
+// tot (reduce-scatter then all-gather over distributed shared memory).
+__device__ void cl_allreduce_hist(cg::cluster_group& cl, uint32_t* hist, uint32_t* tot, int nbins) {
+  const int CL = static_cast<int>(cl.num_blocks()), r = static_cast<int>(cl.block_rank());
+  cl.sync();  // every CTA's histogram complete
+  const int per = (nbins + CL - 1) / CL, b0 = r * per, b1 = min(nbins, b0 + per);
+  for (int b = b0 + static_cast<int>(threadIdx.x); b < b1; b += kNtF) {
+    uint32_t s = 0u;
+    for (int q = 0; q < CL; ++q) s += cl.map_shared_rank(hist, q)[b];
+    for (int q = 0; q < CL; ++q) cl.map_shared_rank(tot, q)[b] = s;
+  }
+  cl.sync();  // every sum in place; no CTA reads hist any more
+}
+
 // ---- time pass of one row segment by one warp (float32 window sums)
 struct WfRow {
   float v[kNplF];  // the sample (0 where non-finite)
@@ -405,7 +471,7 @@ __device__ __forceinline__ uint32_t wf_fire(const WfRow& R, int lane, float tI, 
 // Flags of segment sg of one row (rows past 1024 samples overlap by a halo of
 // 120 samples); interior flag words go to Mrow, returns the interior's number
 // of flagged samples, entry-flagged samples and unflagged sum.
-template <int IN>
+template <int IN, bool SM = false>
 __device__ void wf_segment(const float* row, int T, int sg, bool vin, const F32Shared& f,
                            uint32_t* Mrow, int& nflag, int& nentry, double& su) {
   constexpr int SPAN = 32 * kNplF;
@@ -423,7 +489,11 @@ __device__ void wf_segment(const float* row, int T, int sg, bool vin, const F32S
 #pragma unroll
   for (int q = 0; q < kNplF / 4; ++q) {
     const int x = xl + 4 * q;
-    const float4 v = x < T ? ld4<IN>(row, x, T, vin) : make_float4(0.f, 0.f, 0.f, 0.f);
+    float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+    if (x < T) {
+      if constexpr (SM) v = ld4s(row, x, T);  // a row stored in shared memory (IN = 0)
+      else v = ld4<IN>(row, x, T, vin);
+    }
 #pragma unroll
     for (int j = 0; j < 4; ++j) {
       const float xv = f4at(v, j);
@@ -737,6 +807,414 @@ __global__ void __launch_bounds__(kNtF, 2) lof_f32_kernel(const KParams kp) {
   }
 }
 
+
+// One radix-select pass of the cluster (see select_pass): histograms of the
+// CTA's own kept rows from shared memory, added over the cluster, then the
+// digit of each open rank, picked identically in every CTA.
+template <int MODE>
+__device__ void cl_select_pass(cg::cluster_group& cl, const DevUnit& u, int r0, int R, const float* data,
+                               const uint8_t* Fc, uint32_t* hist, uint32_t* tot, int shift, int nbits,
+                               F32Shared& f) {
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int T = u.T, nb = 1 << nbits, P = cl_pitch(T);
+  for (int i = tid; i < 2 * 2048; i += kNtF) hist[i] = 0u;
+  __syncthreads();
+  const uint32_t p0 = f.prefix[0], p1 = f.prefix[1];
+  const int hs = shift + nbits;
+  const bool two = f.n_rank == 2;
+  const bool same = !two || p0 == p1;
+  const float med_hi = __double2float_rn(f.median_t);
+  const float med_lo = __double2float_rn(__dsub_rn(f.median_t, static_cast<double>(med_hi)));
+  const int nchunk = (T + 127) / 128;
+  for (int item = warp; item < R * nchunk; item += kNwF) {
+    const int i = item / nchunk, s = item - i * nchunk;
+    if (r0 + i >= u.C || Fc[r0 + i]) continue;
+    const int x = s * 128 + lane * 4;
+    if (x >= T) continue;
+    const float4 v = ld4s(data + static_cast<size_t>(i) * P, x, T);
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      const float xv = f4at(v, j);
+      if (!isfinite(xv)) continue;
+      const float kv = MODE == 0 ? xv : fabsf(__fsub_rn(__fsub_rn(xv, med_hi), med_lo));
+      const uint32_t key = fkey(kv);
+      const uint32_t hi = hs >= 32 ? 0u : (key >> hs);
+      const uint32_t dig = (key >> shift) & static_cast<uint32_t>(nb - 1);
+      if (hi == p0) atomicAdd(&hist[dig], 1u);
+      if (!same && hi == p1) atomicAdd(&hist[2048 + dig], 1u);
+    }
+  }
+  __syncthreads();
+  cl_allreduce_hist(cl, hist, tot, same ? nb : 2048 + nb);
+  if (warp < f.n_rank) {
+    const uint32_t* h = tot + (same ? 0 : 2048 * warp);
+    long long rk = f.rank[warp];
+    long long base = 0;
+    uint32_t digit = 0;
+    bool found = false;
+    for (int b0 = 0; b0 < nb && !found; b0 += 32) {
+      const uint32_t cnt = h[b0 + lane];
+      uint32_t incl = cnt;
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t y = __shfl_up_sync(kFullF, incl, o);
+        if (lane >= o) incl += y;
+      }
+      const uint32_t tot_w = __shfl_sync(kFullF, incl, 31);
+      if (rk < base + tot_w) {
+        const unsigned hit = __ballot_sync(kFullF, rk < base + static_cast<long long>(incl));
+        const int l = __ffs(hit) - 1;
+        const uint32_t excl = __shfl_sync(kFullF, incl - cnt, l);
+        digit = static_cast<uint32_t>(b0 + l);
+        rk -= base + excl;
+        found = true;
+      } else {
+        base += tot_w;
+      }
+    }
+    if (lane == 0) {
+      if (!found) f.ok = 0;
+      f.prefix[warp] = (f.prefix[warp] << nbits) | digit;
+      f.rank[warp] = rk;
+    }
+  }
+  __syncthreads();
+  if (tid == 0 && f.n_rank == 1) {
+    f.prefix[1] = f.prefix[0];
+    f.rank[1] = f.rank[0];
+  }
+  __syncthreads();
+}
+
+template <int MODE>
+__device__ double cl_select_median(cg::cluster_group& cl, const DevUnit& u, int r0, int R, const float* data,
+                                   const uint8_t* Fc, uint32_t* hist, uint32_t* tot, F32Shared& f) {
+  const long long N = f.n_pool;
+  if (threadIdx.x == 0) {
+    f.prefix[0] = f.prefix[1] = 0u;
+    f.rank[0] = (N & 1) ? N / 2 : N / 2 - 1;
+    f.rank[1] = N / 2;
+    f.n_rank = (N & 1) ? 1 : 2;
+  }
+  __syncthreads();
+  cl_select_pass<MODE>(cl, u, r0, R, data, Fc, hist, tot, 21, 11, f);
+  cl_select_pass<MODE>(cl, u, r0, R, data, Fc, hist, tot, 10, 11, f);
+  cl_select_pass<MODE>(cl, u, r0, R, data, Fc, hist, tot, 0, 10, f);
+  const double a = static_cast<double>(fkey_val(f.prefix[0]));
+  const double b = static_cast<double>(fkey_val(f.prefix[1]));
+  return (N & 1) ? a : __dmul_rn(__dadd_rn(a, b), 0.5);
+}
+
+// population stddev of the pooled finite samples: per CTA binary64 sums of
+// its rows, added over the CTAs in rank order (two passes)
+__device__ double cl_pooled_std(cg::cluster_group& cl, const DevUnit& u, int r0, int R, const float* data,
+                                const uint8_t* Fc, double* red, F32Shared& f) {
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int CL = static_cast<int>(cl.num_blocks()), rank = static_cast<int>(cl.block_rank());
+  const int T = u.T, P = cl_pitch(T);
+  double acc[2] = {0.0, 0.0};
+  double mu = 0.0;
+  for (int pass = 0; pass < 2; ++pass) {
+    double s = 0.0;
+    for (int i = warp; i < R; i += kNwF) {
+      if (r0 + i >= u.C || Fc[r0 + i]) continue;
+      const float* row = data + static_cast<size_t>(i) * P;
+      for (int t = lane; t < T; t += 32) {
+        const float xv = row[t];
+        if (!isfinite(xv)) continue;
+        const double d = pass == 0 ? static_cast<double>(xv) : __dsub_rn(static_cast<double>(xv), mu);
+        s = pass == 0 ? __dadd_rn(s, d) : __dadd_rn(s, __dmul_rn(d, d));
+      }
+    }
+    s = warp_sum_d(s);
+    if (lane == 0) f.red[warp] = s;
+    __syncthreads();
+    if (tid == 0) {
+      double t = 0.0;
+      for (int w = 0; w < kNwF; ++w) t = __dadd_rn(t, f.red[w]);
+      for (int q = 0; q < CL; ++q) cl.map_shared_rank(red, q)[rank] = t;
+    }
+    cl.sync();
+    if (tid == 0) {
+      double t = 0.0;
+      for (int q = 0; q < CL; ++q) t = __dadd_rn(t, red[q]);
+      f.red[0] = t;
+    }
+    __syncthreads();
+    acc[pass] = f.red[0];
+    cl.sync();  // red is reused by the next pass
+    if (pass == 0) mu = __ddiv_rn(acc[0], static_cast<double>(f.n_pool));
+  }
+  return __dsqrt_rn(__ddiv_rn(acc[1], static_cast<double>(f.n_pool)));
+}
+
+// One unit per cluster; grid = units x CL CTAs, cluster dimension CL.
+__global__ void __launch_bounds__(kNtF, 2) lof_f32c_kernel(const KParams kp) {
+  extern __shared__ __align__(16) uint8_t smem[];
+  __shared__ F32Shared f;
+  cg::cluster_group cl = cg::this_cluster();
+  const int CL = static_cast<int>(cl.num_blocks()), rank = static_cast<int>(cl.block_rank());
+  const int ui = static_cast<int>(blockIdx.x) / CL;  // the same for every CTA of the cluster
+  if (ui >= kp.n_units) return;
+  const DevUnit u = kp.units[ui];
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int C = u.C, T = u.T, P = cl_pitch(T), nwr = cl_words(T);
+  const int R = (C + CL - 1) / CL, r0 = rank * R, nr = max(0, min(R, C - r0));
+  double* S = reinterpret_cast<double*>(smem + kOffClS);
+  unsigned long long* srt = reinterpret_cast<unsigned long long*>(smem + kOffClSrt);
+  int* fin = reinterpret_cast<int*>(smem + kOffClFin);
+  uint8_t* Fc = smem + kOffClFc;
+  uint8_t* fire = smem + kOffClFire;
+  uint32_t* hist = reinterpret_cast<uint32_t*>(smem + kOffClHist);
+  uint32_t* tot = reinterpret_cast<uint32_t*>(smem + kOffClTot);
+  double* red = reinterpret_cast<double*>(smem + kOffClRed);
+  unsigned long long* cnt = reinterpret_cast<unsigned long long*>(smem + kOffClRed + 16 * 8);
+  uint8_t* rinfo = smem + kOffClRows;
+  uint32_t* Mrows = reinterpret_cast<uint32_t*>(smem + cl_off_mrow(R));
+  float* data = reinterpret_cast<float*>(smem + cl_off_data(R, T));
+  const bool vin = (u.flags & kUnitInVec) != 0;
+  const float* gin = static_cast<const float*>(u.in);
+  auto row_su = [&](int i) { return reinterpret_cast<double*>(rinfo + i * kClRowBytes); };
+  auto row_int = [&](int i) { return reinterpret_cast<int*>(rinfo + i * kClRowBytes + kClMaxSeg * 8); };
+  if (tid == 0) {
+    f.cnt_time = f.cnt_total = f.cnt_hist = 0;
+    f.ok = 1;
+  }
+  if (tid < 4) cnt[tid] = 0ull;
+  // a1: the CTA's rows into shared memory, each sample read from global once
+  for (int i = 0; i < nr; ++i) {
+    const float* row = gin + static_cast<int64_t>(r0 + i) * u.in_stride;
+    float* srow = data + static_cast<size_t>(i) * P;
+    for (int x = tid * 4; x < T; x += kNtF * 4) {
+      const float4 v = ld4<0>(row, x, T, vin);
+      if (x + 4 <= T) {
+        *reinterpret_cast<float4*>(srow + x) = v;
+      } else {
+#pragma unroll
+        for (int j = 0; j < 4; ++j)
+          if (x + j < T) srow[x + j] = f4at(v, j);
+      }
+    }
+  }
+  for (int i = tid; i < R * 4; i += kNtF) row_int(i >> 2)[i & 3] = 0;
+  __syncthreads();
+  // a2: row sums (binary64, one warp per row in f32_unit's order), written
+  // into every CTA of the cluster
+  for (int i = warp; i < nr; i += kNwF) {
+    const float* srow = data + static_cast<size_t>(i) * P;
+    double s = 0.0;
+    int nfin = 0;
+    for (int x = lane * 4; x < T; x += 128) {
+      const float4 v = ld4s(srow, x, T);
+#pragma unroll
+      for (int j = 0; j < 4; ++j) {
+        const float xv = f4at(v, j);
+        if (x + j < T && isfinite(xv)) {
+          s = __dadd_rn(s, static_cast<double>(xv));
+          ++nfin;
+        }
+      }
+    }
+    s = warp_sum_d(s);
+    nfin = __reduce_add_sync(kFullF, nfin);
+    if (lane < CL) {
+      cl.map_shared_rank(S, lane)[r0 + i] = s;
+      cl.map_shared_rank(fin, lane)[r0 + i] = nfin;
+    }
+  }
+  for (int c = tid; c < C; c += kNtF) Fc[c] = 0;
+  cl.sync();
+  // a3, a4 on the whole spectrum, alike in every CTA
+  spectrum_stats(kp, S, C, srt, f);
+  spectrum_sum_threshold(kp, S, C, Fc, fire, f);
+  {
+    long long np = 0;
+    int nfc = 0;
+    for (int c = tid; c < C; c += kNtF) {
+      if (!Fc[c]) np += fin[c];
+      nfc += Fc[c];
+    }
+    np = warp_sum_ll(np);
+    nfc = __reduce_add_sync(kFullF, nfc);
+    if (lane == 0) {
+      srt[warp] = static_cast<unsigned long long>(np);
+      srt[kNwF + warp] = static_cast<unsigned long long>(nfc);
+    }
+    __syncthreads();
+    if (tid == 0) {
+      long long t = 0, tc = 0;
+      for (int w = 0; w < kNwF; ++w) {
+        t += static_cast<long long>(srt[w]);
+        tc += static_cast<long long>(srt[kNwF + w]);
+      }
+      f.n_pool = t;
+      f.nfc = static_cast<int>(tc);
+    }
+    __syncthreads();
+  }
+  // a5
+  double med = 0.0, sig = 0.0;
+  if (f.n_pool > 0) {
+    med = cl_select_median<0>(cl, u, r0, nr, data, Fc, hist, tot, f);
+    if (tid == 0) f.median_t = med;
+    __syncthreads();
+    double mad = 0.0;
+    if (!kp.sigma_std) mad = cl_select_median<1>(cl, u, r0, nr, data, Fc, hist, tot, f);
+    if (!kp.sigma_std && mad > 0.0) sig = __dmul_rn(1.482602218505602, mad);
+    else sig = cl_pooled_std(cl, u, r0, nr, data, Fc, red, f);
+  }
+  if (tid == 0) {
+    if (!f.ok) set_error_f(kp, kErrSelect, 701);
+    f.median_t = med;
+    f.sigma_t = sig;
+    int kmax = 0;
+    while (kmax < kp.max_log_window && (2 << kmax) <= T) ++kmax;
+    f.kmax_t = kmax;
+    f.time_on = (kp.enable_time && f.n_pool > 0 && sig > 0.0) ? 1 : 0;
+    for (int k = 0; k <= kmax; ++k) {
+      const double t = thr_of(kp, med, sig, k);
+      f.tI[k] = t;
+      f.tIf[k] = __double2float_rn(t);
+      f.limI[k] = __double2float_rn(__dmul_rn(static_cast<double>(1 << k), t));
+    }
+  }
+  __syncthreads();
+  // a6: time pass, warps over (own row, segment)
+  const int nsg = T <= 32 * kNplF ? 1 : [&] {
+    int n = 1, ob = (32 * kNplF - kHaloF) & ~31;
+    while (ob < T) {
+      const int s0 = (ob - kHaloF) & ~31;
+      ob = s0 + 32 * kNplF >= T ? T : ((s0 + 32 * kNplF - kHaloF) & ~31);
+      ++n;
+    }
+    return n;
+  }();
+  if (f.time_on) {
+    for (int item = warp; item < nr * nsg; item += kNwF) {
+      const int i = item / nsg, sg = item - i * nsg;
+      if (Fc[r0 + i]) continue;
+      int a, b;
+      double s;
+      wf_segment<0, true>(data + static_cast<size_t>(i) * P, T, sg, true, f, Mrows + i * nwr, a, b, s);
+      if (lane == 0) {
+        row_su(i)[sg] = s;
+        atomicAdd(&row_int(i)[0], a);
+        atomicAdd(&row_int(i)[1], b);
+      }
+    }
+  } else {
+    for (int i = warp; i < nr; i += kNwF) {
+      if (Fc[r0 + i]) continue;
+      int nflag;
+      double su;
+      wf_entry_only<0>(data + static_cast<size_t>(i) * P, T, Mrows + i * nwr, nflag, su);
+      if (lane == 0) {
+        row_su(i)[0] = su;
+        row_int(i)[0] = nflag;
+        row_int(i)[1] = nflag;
+      }
+    }
+  }
+  __syncthreads();
+  // a7: history (Section 4.1), one thread per own row
+  if (tid < nr) {
+    const int i = tid, c = r0 + i;
+    const long long h = u.hist_slot >= 0 ? u.hist_slot + c : -1;
+    int fh = 0;
+    if (!Fc[c]) {
+      const int nflag = row_int(i)[0], nentry = row_int(i)[1];
+      double su = 0.0;
+      for (int sg = 0; sg < (f.time_on ? nsg : 1); ++sg) su = __dadd_rn(su, row_su(i)[sg]);
+      const int n = T - nflag;
+      if (n > 0) {
+        const double cur = __ddiv_rn(su, static_cast<double>(n));
+        double staged = cur;
+        if (kp.enable_history && h >= 0) {
+          const int hc = kp.hist.count[h];
+          if (hc >= kp.history_min && hc > 0) {
+            const double thr = kp.hist.thr[h];
+            if (!(cur < thr)) {
+              fh = 1;
+              staged = thr;
+            }
+          }
+        }
+        if (h >= 0) {
+          kp.hist.pend[h] = staged;
+          kp.hist.pend_flag[h] = 1;
+          kp.hist.pend_seq[h] = kp.block_seq;
+        }
+      } else if (h >= 0) {
+        kp.hist.pend_flag[h] = 0;
+      }
+      atomicAdd(&f.cnt_time, static_cast<unsigned long long>(nflag - nentry));
+      if (fh) atomicAdd(&f.cnt_hist, 1ull);
+      atomicAdd(&f.cnt_total, fh ? static_cast<unsigned long long>(T) : static_cast<unsigned long long>(nflag));
+    } else {
+      if (h >= 0) kp.hist.pend_flag[h] = 0;
+      atomicAdd(&f.cnt_total, static_cast<unsigned long long>(T));
+      fh = 1;
+    }
+    row_int(i)[2] = fh;
+  }
+  __syncthreads();
+  // a8: mask bytes and masked data of the own rows, the data from shared memory
+  {
+    const bool mask_vec = (u.flags & kUnitMaskVec) != 0;
+    const bool vout = (u.flags & kUnitOutVec) != 0;
+    const bool inplace = (u.flags & kUnitInPlace) != 0;
+    const int nx = (T + 3) / 4;
+    for (int item = tid; item < nr * nx; item += kNtF) {
+      const int i = item / nx, x = (item - i * nx) * 4, c = r0 + i;
+      const bool full = row_int(i)[2] != 0;
+      const int nv = min(4, T - x);
+      const uint32_t valid = nv >= 4 ? 0xFu : ((1u << nv) - 1u);
+      const uint32_t bits = full ? valid : ((Mrows[i * nwr + (x >> 5)] >> (x & 31)) & valid);
+      if (u.mask) {
+        uint8_t* mr = u.mask + static_cast<int64_t>(c) * u.mask_stride;
+        if (mask_vec && nv == 4) *reinterpret_cast<uint32_t*>(mr + x) = (bits * 0x00204081u) & 0x01010101u;
+        else for (int j = 0; j < nv; ++j) mr[x + j] = static_cast<uint8_t>((bits >> j) & 1u);
+      }
+      if (u.out) {
+        float* orow = static_cast<float*>(u.out) + static_cast<int64_t>(c) * u.out_stride;
+        const float* srow = data + static_cast<size_t>(i) * P;
+        if (inplace) {
+          for (int j = 0; j < nv; ++j)
+            if ((bits >> j) & 1u) orow[x + j] = 0.0f;
+        } else if (vout && nv == 4) {
+          float4 w = *reinterpret_cast<const float4*>(srow + x);
+          if (bits & 1u) w.x = 0.0f;
+          if (bits & 2u) w.y = 0.0f;
+          if (bits & 4u) w.z = 0.0f;
+          if (bits & 8u) w.w = 0.0f;
+          __stcs(reinterpret_cast<float4*>(orow + x), w);
+        } else {
+          for (int j = 0; j < nv; ++j) orow[x + j] = ((bits >> j) & 1u) ? 0.0f : srow[x + j];
+        }
+      }
+    }
+  }
+  // the unit's counts, added into CTA 0, which reports the statistics
+  if (tid == 0) {
+    unsigned long long* c0 = cl.map_shared_rank(cnt, 0);
+    atomicAdd(c0 + 0, f.cnt_time);
+    atomicAdd(c0 + 1, f.cnt_hist);
+    atomicAdd(c0 + 2, f.cnt_total);
+  }
+  cl.sync();
+  if (rank == 0 && tid == 0 && u.stats) {
+    if (!f.ok) set_error_f(kp, kErrSelect, 702);
+    u.stats->median_f = f.median_f;
+    u.stats->sigma_f = f.sigma_f;
+    u.stats->median_t = f.median_t;
+    u.stats->sigma_t = f.sigma_t;
+    u.stats->n_chan_freq = f.nfc;
+    u.stats->n_flag_time = static_cast<long long>(cnt[0]);
+    u.stats->n_chan_hist = static_cast<long long>(cnt[1]);
+    u.stats->n_flag_total = static_cast<long long>(cnt[2]);
+  }
+}
+
 }  // namespace
 }  // namespace lofk
 
@@ -767,4 +1245,56 @@ extern "C" int lofk_launch_f32x(const lofk::KParams* kp, int n_units, int n_sm, 
 extern "C" int lofk_launch_f32(const lofk::KParams* kp, int n_units, int n_sm, int smem_bytes,
                                void* stream) {
   return lofk_launch_f32x(kp, n_units, n_sm, smem_bytes, stream, 0);
+}
+
+// Stokes I units in thread-block clusters (lof_f32c_kernel): 0 launched, 1
+// not possible for these units on this device (the caller takes the one-CTA
+// kernel), else a CUDA error code.  max_C, max_T: the largest unit.
+extern "C" int lofk_launch_f32c(const lofk::KParams* kp, int n_units, int max_C, int max_T, void* stream) {
+  using namespace lofk;
+  if (n_units <= 0) return 0;
+  if (max_C > kCMaxCl || max_C < 1) return 1;
+  {
+    int n = 1, ob = (32 * kNplF - kHaloF) & ~31;
+    while (ob < max_T) {
+      const int s0 = (ob - kHaloF) & ~31;
+      ob = s0 + 32 * kNplF >= max_T ? max_T : ((s0 + 32 * kNplF - kHaloF) & ~31);
+      ++n;
+    }
+    if (n > kClMaxSeg) return 1;
+  }
+  int dev = 0, optin = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+  const void* k = reinterpret_cast<const void*>(&lof_f32c_kernel);
+  for (int CL : {16, 8}) {
+    const int R = (max_C + CL - 1) / CL;
+    const int smem = cl_smem(R, max_T);
+    if (smem + static_cast<int>(sizeof(F32Shared)) + 1024 > optin) continue;
+    if (cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, smem) != cudaSuccess ||
+        (CL > 8 && cudaFuncSetAttribute(k, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) != cudaSuccess)) {
+      cudaGetLastError();
+      continue;
+    }
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(static_cast<unsigned>(n_units * CL));
+    cfg.blockDim = dim3(kNtF);
+    cfg.dynamicSmemBytes = static_cast<size_t>(smem);
+    cfg.stream = static_cast<cudaStream_t>(stream);
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeClusterDimension;
+    at[0].val.clusterDim.x = static_cast<unsigned>(CL);
+    at[0].val.clusterDim.y = 1;
+    at[0].val.clusterDim.z = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    int ncl = 0;
+    if (cudaOccupancyMaxActiveClusters(&ncl, k, &cfg) != cudaSuccess || ncl < 1) {
+      cudaGetLastError();
+      continue;
+    }
+    const cudaError_t e = cudaLaunchKernelEx(&cfg, lof_f32c_kernel, *kp);
+    return e == cudaSuccess ? 0 : static_cast<int>(e);
+  }
+  return 1;
 }

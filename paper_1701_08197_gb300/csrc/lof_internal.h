@@ -173,6 +173,7 @@ struct Prep {
   int n_tasks_stats, grid_flag;  // tasks of the statistics launch (the first ones); CTAs of the flag launch
   int64_t n_chan;
   int gen_words;                 // per CTA, general time-pass rows
+  int max_C, max_T;              // float units: the largest unit's channels and samples
 };
 // Device memory one launch works in.
 struct Scratch {
@@ -215,3 +216,4 @@ extern "C" int lofk_set_smem_limit(int dtype, int smem_bytes);
 extern "C" int lofk_f32_smem(int max_T);
 extern "C" int lofk_launch_f32(const lofk::KParams* kp, int n_units, int n_sm, int smem_bytes,
                                void* stream);
+extern "C" int lofk_launch_f32c(const lofk::KParams* kp, int n_units, int max_C, int max_T, void* stream);

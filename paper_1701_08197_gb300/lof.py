@@ -23,7 +23,8 @@ LOF_CI8, LOF_CI16, LOF_F32, LOF_CF32 = 1, 2, 3, 4
 LOF_SIGMA_MAD, LOF_SIGMA_STD, LOF_SIGMA_WINSOR = 0, 1, 2
 LOF_TIME_PER_CHANNEL, LOF_TIME_INTEGRATED, LOF_TIME_2D = 0, 1, 2
 LOF_SCOPE_POOLED, LOF_SCOPE_CHANNEL = 0, 1
-LOF_SCHED_PACKED, LOF_SCHED_BOUND64, LOF_SCHED_COALESCED, LOF_SCHED_VALUE_WINDOW, LOF_SCHED_SET = 1, 2, 4, 8, 0x80
+(LOF_SCHED_PACKED, LOF_SCHED_BOUND64, LOF_SCHED_COALESCED, LOF_SCHED_VALUE_WINDOW, LOF_SCHED_F32_CLUSTER,
+ LOF_SCHED_SET) = 1, 2, 4, 8, 16, 0x80
 
 EXPORTED = [
     "lof_default_params", "lof_create", "lof_flag_block", "lof_flag_block_host",

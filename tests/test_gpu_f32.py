@@ -114,3 +114,34 @@ def test_f32_pure_noise_thresholds_flag_little():
     frac = masks[0].mean()
     assert frac < 0.05, frac
     assert st[0]["n_chan_freq"] == 0
+
+
+@pytest.mark.parametrize("shape", [(16, 12288), (13, 1000), (256, 768), (1, 37), (17, 4096)])
+def test_cluster_and_single_cta_kernels_agree(shape):
+    """LOF_SCHED_F32_CLUSTER on (one thread-block cluster per unit, the unit in
+    shared memory) and off (one CTA per unit): the same row sums, order
+    statistics and window sums, so bit-identical masks, data and statistics."""
+    C, T = shape
+    xs = [_stokes(300 + i, C, T, nonfinite=2 if T > 1 else 0) for i in range(3)]
+    res = {}
+    for on in (0, lof.LOF_SCHED_F32_CLUSTER):
+        with lof.Flagger(0) as fl:
+            t = fl.tuning()
+            fl.set_tuning(schedule=(t["schedule"] & ~lof.LOF_SCHED_F32_CLUSTER) | on)
+            res[on] = _run_gpu(fl, xs)
+    (ma, oa, sa), (mb, ob, sb) = res[0], res[lof.LOF_SCHED_F32_CLUSTER]
+    for k in range(len(xs)):
+        assert np.array_equal(ma[k], mb[k]), f"unit {k}: masks differ"
+        assert np.array_equal(oa[k].view(np.uint32), ob[k].view(np.uint32)), f"unit {k}: data differ"
+        assert sa[k] == sb[k], (k, sa[k], sb[k])
+
+
+def test_cluster_kernel_std_estimator_within_tolerance():
+    """The std estimator's binary64 sums follow the cluster's CTAs: within the
+    float rule against the oracle."""
+    xs = [_stokes(400, 16, 12288)]
+    p = oracle.default_params(sigma_estimator=1)
+    with lof.Flagger(0, sigma_estimator=lof.LOF_SIGMA_STD) as fl:
+        masks, outs, stats = _run_gpu(fl, xs)
+    ref = oracle.flag_unit(p, xs[0])
+    _check_unit(p, xs[0], masks[0], outs[0], stats[0], ref, tag="f32 cluster std")
