@@ -62,7 +62,7 @@ struct F32Shared {
   unsigned long long cnt_time, cnt_total, cnt_hist;
   uint32_t prefix[2];
   long long rank[2];
-  int n_rank, kmax_t, time_on, nfc, ok;
+  int n_rank, kmax_t, time_on, nfc, ok, wmiss;
   double red[kNwF];
 };
 
@@ -233,6 +233,33 @@ __device__ void spectrum_sum_threshold(const KParams& kp, const double* S, int C
   }
 }
 
+// Calls fn(v) for each 4-sample vector of the finite-or-not samples of the
+// kept rows (Fc clear): the warps take (row, 128-sample chunk) items in turn,
+// each warp with the loads of eight items in flight before it counts them.
+template <int IN, typename Fn>
+__device__ __forceinline__ void for_kept_vectors(const DevUnit& u, const uint8_t* Fc, Fn&& fn) {
+  constexpr int NL = 8;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int T = u.T, nchunk = (T + 127) / 128, total = u.C * nchunk;
+  const bool vin = (u.flags & kUnitInVec) != 0;
+  const float* gin = static_cast<const float*>(u.in);
+  for (int i0 = warp; i0 < total; i0 += NL * kNwF) {
+    float4 v[NL];
+    bool ok[NL];
+#pragma unroll
+    for (int k = 0; k < NL; ++k) {
+      const int item = i0 + k * kNwF;
+      const int c = item / nchunk, x = (item - c * nchunk) * 128 + lane * 4;
+      ok[k] = item < total && !Fc[c] && x < T;
+      v[k] = ok[k] ? ld4<IN>(gin + static_cast<int64_t>(c) * u.in_stride * (IN + 1), x, T, vin)
+                   : make_float4(0.f, 0.f, 0.f, 0.f);
+    }
+#pragma unroll
+    for (int k = 0; k < NL; ++k)
+      if (ok[k]) fn(v[k]);
+  }
+}
+
 // One radix-select pass over the finite samples of the kept rows: histogram
 // of the 11 (or 10) key bits below those already fixed, for each open rank.
 // MODE 0: keys of x; MODE 1: keys of float(|x - median_t|).
@@ -240,7 +267,7 @@ template <int MODE, int IN>
 __device__ void select_pass(const DevUnit& u, const uint8_t* Fc, uint32_t* hist, int shift,
                             int nbits, F32Shared& f) {
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  const int T = u.T, nb = 1 << nbits;
+  const int nb = 1 << nbits;
   for (int i = tid; i < 2 * 2048; i += kNtF) hist[i] = 0u;
   __syncthreads();
   const uint32_t p0 = f.prefix[0], p1 = f.prefix[1];
@@ -254,20 +281,11 @@ __device__ void select_pass(const DevUnit& u, const uint8_t* Fc, uint32_t* hist,
   // are float32 anyway), with no binary64 operation per sample
   const float med_hi = __double2float_rn(f.median_t);
   const float med_lo = __double2float_rn(__dsub_rn(f.median_t, static_cast<double>(med_hi)));
-  const bool vin = (u.flags & kUnitInVec) != 0;
-  const float* gin = static_cast<const float*>(u.in);
-  const int nchunk = (T + 127) / 128;  // 32 lanes x 4 samples
-  for (int item = warp; item < u.C * nchunk; item += kNwF) {
-    const int c = item / nchunk, s = item - c * nchunk;
-    if (Fc[c]) continue;
-    const float* row = gin + static_cast<int64_t>(c) * u.in_stride * (IN + 1);
-    const int x = s * 128 + lane * 4;
-    if (x >= T) continue;
-    const float4 v = ld4<IN>(row, x, T, vin);
+  for_kept_vectors<IN>(u, Fc, [&](const float4& v) {
 #pragma unroll
     for (int j = 0; j < 4; ++j) {
       const float xv = f4at(v, j);
-      if (!isfinite(xv)) continue;
+      if (!isfinite(xv)) continue;  // also the NaN past T
       const float kv = MODE == 0 ? xv : fabsf(__fsub_rn(__fsub_rn(xv, med_hi), med_lo));
       const uint32_t key = fkey(kv);
       const uint32_t hi = hs >= 32 ? 0u : (key >> hs);
@@ -275,7 +293,7 @@ __device__ void select_pass(const DevUnit& u, const uint8_t* Fc, uint32_t* hist,
       if (hi == p0) atomicAdd(&hist[dig], 1u);
       if (!same && hi == p1) atomicAdd(&hist[2048 + dig], 1u);
     }
-  }
+  });
   __syncthreads();
   // pick the digit of each open rank (one warp per rank)
   if (warp < f.n_rank) {
@@ -334,6 +352,177 @@ __device__ double select_median(const DevUnit& u, const uint8_t* Fc, uint32_t* h
   const double a = static_cast<double>(fkey_val(f.prefix[0]));
   const double b = static_cast<double>(fkey_val(f.prefix[1]));
   return (N & 1) ? a : __dmul_rn(__dadd_rn(a, b), 0.5);
+}
+
+
+// ---- order statistics in a window around the previous block's value
+// With a hint h (the unit's median, or MAD, of the previous block) and a
+// half-width hw (halved up to four times until it fits), the keys of
+// [h - hw, h + hw] form an interval [klo, khi] of at most 2^22 keys (else no
+// window).  Pass 1 counts the keys below klo and
+// histograms those in the interval in 2048 bins of 2^s keys; the bin of each
+// open rank follows from the counts; pass 2 counts key by key inside those
+// bins and gives the exact keys.  The result is the same order statistic as
+// the three radix passes (select_median); false (nothing decided) when a rank
+// falls outside the interval.
+template <int MODE, int IN>
+__device__ void window_count(const DevUnit& u, const uint8_t* Fc, uint32_t* hist, uint32_t klo, int s,
+                             int fine, F32Shared& f, long long* below_out) {
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const float med_hi = __double2float_rn(f.median_t);
+  const float med_lo = __double2float_rn(__dsub_rn(f.median_t, static_cast<double>(med_hi)));
+  // fine: bins b0 = f.prefix[0], b1 = f.prefix[1] (coarse bins of the ranks)
+  const uint32_t w = 1u << s;
+  const uint32_t base0 = klo + (f.prefix[0] << s), base1 = klo + (f.prefix[1] << s);
+  const bool two = fine && f.n_rank == 2 && f.prefix[0] != f.prefix[1];
+  long long below = 0;
+  for_kept_vectors<IN>(u, Fc, [&](const float4& v) {
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      const float xv = f4at(v, j);
+      if (!isfinite(xv)) continue;
+      const float kv = MODE == 0 ? xv : fabsf(__fsub_rn(__fsub_rn(xv, med_hi), med_lo));
+      const uint32_t key = fkey(kv);
+      if (!fine) {
+        if (key < klo) {
+          ++below;
+        } else {
+          const uint32_t d = (key - klo) >> s;
+          if (d < 2048u) atomicAdd(&hist[d], 1u);
+        }
+      } else {
+        if (key - base0 < w) atomicAdd(&hist[key - base0], 1u);
+        if (two && key - base1 < w) atomicAdd(&hist[2048 + (key - base1)], 1u);
+      }
+    }
+  });
+  if (!fine) {
+    below = warp_sum_ll(below);
+    if (lane == 0) f.red[warp] = static_cast<double>(below);  // exact: counts < 2^53
+  }
+  __syncthreads();
+  if (!fine && tid == 0) {
+    long long b = 0;
+    for (int q = 0; q < kNwF; ++q) b += static_cast<long long>(f.red[q]);
+    *below_out = b;
+  }
+  __syncthreads();
+}
+
+// The bin (or key) of each open rank in hist (nb counters; rank r of rank
+// slot q, relative to the counters' start); one warp per rank.  Sets
+// f.prefix[q] to the bin and f.rank[q] to the rank inside it; f.ok = 0 if a
+// rank lies past the counted values.
+__device__ void window_pick(const uint32_t* hist, int nb, bool split, F32Shared& f) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  if (warp < f.n_rank) {
+    const uint32_t* h = hist + (split ? 2048 * warp : 0);
+    long long rk = f.rank[warp];
+    long long base = 0;
+    uint32_t digit = 0;
+    bool found = false;
+    if (rk >= 0) {
+      for (int b0 = 0; b0 < nb && !found; b0 += 32) {
+        const uint32_t cnt = b0 + lane < nb ? h[b0 + lane] : 0u;
+        uint32_t incl = cnt;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+          const uint32_t y = __shfl_up_sync(kFullF, incl, o);
+          if (lane >= o) incl += y;
+        }
+        const uint32_t tw = __shfl_sync(kFullF, incl, 31);
+        if (rk < base + tw) {
+          const unsigned hit = __ballot_sync(kFullF, rk < base + static_cast<long long>(incl));
+          const int l = __ffs(hit) - 1;
+          const uint32_t excl = __shfl_sync(kFullF, incl - cnt, l);
+          digit = static_cast<uint32_t>(b0 + l);
+          rk -= base + excl;
+          found = true;
+        } else {
+          base += tw;
+        }
+      }
+    }
+    if (lane == 0) {
+      f.prefix[warp] = digit;
+      f.rank[warp] = rk;
+      if (!found) f.wmiss = 1;
+    }
+  }
+  __syncthreads();
+}
+
+template <int MODE, int IN>
+__device__ bool window_select(const DevUnit& u, const uint8_t* Fc, uint32_t* hist, F32Shared& f, double h,
+                              double hw, double* out) {
+  const int tid = threadIdx.x;
+  const long long N = f.n_pool;
+  if (!(hw > 0.0) || N <= 0) return false;
+  // the widest of hw, hw / 2, ..., hw / 16 whose keys fit two passes (2^22)
+  uint32_t klo = 0u;
+  int s = 12;
+  for (int t = 0; t < 5 && s > 11; ++t, hw = __dmul_rn(hw, 0.5)) {
+    const float lo_v = __double2float_rd(__dsub_rn(h, hw)), hi_v = __double2float_ru(__dadd_rn(h, hw));
+    if (!isfinite(lo_v) || !isfinite(hi_v)) return false;
+    const uint32_t a = fkey(lo_v), b = fkey(hi_v);
+    if (b < a) return false;
+    const unsigned long long span = static_cast<unsigned long long>(b - a) + 1ull;
+    s = 0;
+    while ((span >> s) > 2048ull) ++s;
+    klo = a;
+  }
+  if (s > 11) return false;
+  for (int i = tid; i < 2 * 2048; i += kNtF) hist[i] = 0u;
+  if (tid == 0) {
+    f.rank[0] = (N & 1) ? N / 2 : N / 2 - 1;
+    f.rank[1] = N / 2;
+    f.n_rank = (N & 1) ? 1 : 2;
+  }
+  __shared__ long long s_below;
+  __syncthreads();
+  window_count<MODE, IN>(u, Fc, hist, klo, s, 0, f, &s_below);
+  if (tid == 0) {
+    f.rank[0] -= s_below;
+    f.rank[1] -= s_below;
+    f.wmiss = 0;
+  }
+  __syncthreads();
+  window_pick(hist, 2048, false, f);
+  const bool miss1 = f.wmiss != 0;
+  __syncthreads();
+  if (miss1) return false;
+  // pass 2: key by key inside the ranks' bins
+  for (int i = tid; i < 2 * 2048; i += kNtF) hist[i] = 0u;
+  __syncthreads();
+  const uint32_t bin0 = f.prefix[0], bin1 = f.n_rank == 2 ? f.prefix[1] : f.prefix[0];
+  if (tid == 0 && f.n_rank == 1) f.prefix[1] = f.prefix[0];
+  __syncthreads();
+  window_count<MODE, IN>(u, Fc, hist, klo, s, 1, f, &s_below);
+  const bool split = f.n_rank == 2 && bin0 != bin1;
+  window_pick(hist, 1 << s, split, f);
+  const bool miss2 = f.wmiss != 0;
+  __syncthreads();
+  if (miss2) {  // cannot happen when pass 1 placed the ranks (same counts)
+    if (tid == 0) f.ok = 0;
+    return false;
+  }
+  const uint32_t k0 = klo + (bin0 << s) + f.prefix[0];
+  const uint32_t k1 = klo + (bin1 << s) + (f.n_rank == 2 ? f.prefix[1] : f.prefix[0]);
+  const double a = static_cast<double>(fkey_val(k0)), b = static_cast<double>(fkey_val(k1));
+  *out = (N & 1) ? a : __dmul_rn(__dadd_rn(a, b), 0.5);
+  __syncthreads();
+  return true;
+}
+
+// The previous block's median and MAD of a unit with a history slot (the
+// statistics hints, stored as binary64), if any.
+__device__ __forceinline__ bool f32_hints(const KParams& kp, const DevUnit& u, double* m, double* d) {
+  if (!kp.hist.hint || u.hist_slot < 0) return false;
+  const unsigned long long a = kp.hist.hint[2 * u.hist_slot], b = kp.hist.hint[2 * u.hist_slot + 1];
+  if (a == ~0ull || b == ~0ull) return false;
+  *m = __longlong_as_double(static_cast<long long>(a));
+  *d = __longlong_as_double(static_cast<long long>(b));
+  return isfinite(*m) && isfinite(*d) && *d > 0.0;
 }
 
 // population stddev of the pooled finite samples (binary64, two passes)
@@ -584,14 +773,21 @@ __device__ void f32_unit(const KParams& kp, const DevUnit& u, uint8_t* smem, F32
     const float* row = gin + static_cast<int64_t>(c) * u.in_stride * (IN + 1);
     double s = 0.0;
     int nfin = 0;
-    for (int x = lane * 4; x < T; x += 128) {
-      const float4 v = ld4<IN>(row, x, T, vin);
+    for (int x0 = lane * 4; x0 < T; x0 += 4 * 128) {  // four loads in flight, then the sums in order
+      float4 v[4];
 #pragma unroll
-      for (int j = 0; j < 4; ++j) {
-        const float xv = f4at(v, j);
-        if (x + j < T && isfinite(xv)) {
-          s = __dadd_rn(s, static_cast<double>(xv));
-          ++nfin;
+      for (int k = 0; k < 4; ++k)
+        v[k] = x0 + 128 * k < T ? ld4<IN>(row, x0 + 128 * k, T, vin) : make_float4(0.f, 0.f, 0.f, 0.f);
+#pragma unroll
+      for (int k = 0; k < 4; ++k) {
+        const int x = x0 + 128 * k;
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+          const float xv = f4at(v[k], j);
+          if (x + j < T && isfinite(xv)) {
+            s = __dadd_rn(s, static_cast<double>(xv));
+            ++nfin;
+          }
         }
       }
     }
@@ -635,11 +831,23 @@ __device__ void f32_unit(const KParams& kp, const DevUnit& u, uint8_t* smem, F32
   __syncthreads();
   double med = 0.0, sig = 0.0;
   if (f.n_pool > 0) {
-    med = select_median<0, IN>(u, Fc, hist, f);
+    // two window passes around the previous block's median and MAD where
+    // they hold the ranks, else the three radix passes
+    double hm = 0.0, hd = 0.0;
+    const bool hinted = f32_hints(kp, u, &hm, &hd);
+    if (!(hinted && window_select<0, IN>(u, Fc, hist, f, hm, __dmul_rn(0.25, hd), &med)))
+      med = select_median<0, IN>(u, Fc, hist, f);
     if (tid == 0) f.median_t = med;
     __syncthreads();
     double mad = 0.0;
-    if (!kp.sigma_std) mad = select_median<1, IN>(u, Fc, hist, f);
+    if (!kp.sigma_std) {
+      if (!(hinted && window_select<1, IN>(u, Fc, hist, f, hd, __dmul_rn(0.25, hd), &mad)))
+        mad = select_median<1, IN>(u, Fc, hist, f);
+      if (tid == 0 && kp.hist.hint && u.hist_slot >= 0) {
+        kp.hist.hint[2 * u.hist_slot] = static_cast<unsigned long long>(__double_as_longlong(med));
+        kp.hist.hint[2 * u.hist_slot + 1] = static_cast<unsigned long long>(__double_as_longlong(mad));
+      }
+    }
     if (!kp.sigma_std && mad > 0.0) sig = __dmul_rn(1.482602218505602, mad);
     else sig = pooled_std<IN>(u, Fc, f);
   }
@@ -731,9 +939,18 @@ __device__ void f32_unit(const KParams& kp, const DevUnit& u, uint8_t* smem, F32
         atomicAdd(&f.cnt_total, static_cast<unsigned long long>(T));
       }
     }
-    // a8: mask and masked data
+    // a8: mask and masked data (the input vectors of four chunks loaded ahead)
     const int64_t gi = c;
-    for (int x = lane * 4; x < T; x += 128) {
+    const bool pf = IN == 0 && u.out && !inplace && vin && vout;
+    for (int x0 = lane * 4; x0 < T; x0 += 4 * 128) {
+    float4 pre[4];
+#pragma unroll
+    for (int k = 0; k < 4; ++k)
+      if (pf && x0 + 128 * k + 4 <= T && !full) pre[k] = __ldg(reinterpret_cast<const float4*>(row + x0 + 128 * k));
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      const int x = x0 + 128 * k;
+      if (x >= T) break;
       const int nv = min(4, T - x);
       const uint32_t valid = nv >= 4 ? 0xFu : ((1u << nv) - 1u);
       const uint32_t bits = full ? valid : ((Mrow[x >> 5] >> (x & 31)) & valid);
@@ -770,7 +987,7 @@ __device__ void f32_unit(const KParams& kp, const DevUnit& u, uint8_t* smem, F32
           for (int j = 0; j < nv; ++j)
             if ((bits >> j) & 1u) orow[x + j] = 0.0f;
         } else if (vin && vout && nv == 4) {
-          float4 w = __ldg(reinterpret_cast<const float4*>(row + x));
+          float4 w = full ? make_float4(0.f, 0.f, 0.f, 0.f) : pre[k];
           if (bits & 1u) w.x = 0.0f;
           if (bits & 2u) w.y = 0.0f;
           if (bits & 4u) w.z = 0.0f;
@@ -780,6 +997,7 @@ __device__ void f32_unit(const KParams& kp, const DevUnit& u, uint8_t* smem, F32
           for (int j = 0; j < nv; ++j) orow[x + j] = ((bits >> j) & 1u) ? 0.0f : row[x + j];
         }
       }
+    }
     }
     __syncwarp();
   }

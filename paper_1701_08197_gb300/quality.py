@@ -96,26 +96,30 @@ def evaluate(n_subband=64, n_block=4, seed=4, n_bin=256, device="cuda:0", flagge
 
 
 def time_block(n_subband=488, seed=4, reps=5, device="cuda:0"):
-    """Flag-kernel time of one full Stokes I block (CUDA events, median)."""
+    """Flag-kernel time of one full Stokes I block (CUDA events, median), as
+    in streaming: every unit has its history slots (so the previous block's
+    statistics serve as hints) and two distinct blocks alternate."""
     dev = torch.device(device)
     spec = synth.PulsarSpec(n_subband=n_subband)
-    x = synth.stokes_block(spec, seed=seed, block=0, device=dev).contiguous()
-    out = torch.empty_like(x)
-    mask = torch.empty(x.shape, dtype=torch.uint8, device=dev)
-    with lof.Flagger(dev.index or 0) as fl:
-        units = [lof.make_unit(x[s], out[s], mask[s]) for s in range(n_subband)]
+    xs = [synth.stokes_block(spec, seed=seed, block=b, device=dev).contiguous() for b in (0, 1)]
+    out = torch.empty_like(xs[0])
+    mask = torch.empty(xs[0].shape, dtype=torch.uint8, device=dev)
+    with lof.Flagger(dev.index or 0, n_history_slots=n_subband * spec.C) as fl:
+        units = [[lof.make_unit(x[s], out[s], mask[s], s * spec.C) for s in range(n_subband)] for x in xs]
         st = torch.cuda.current_stream()
-        fl.flag_block(lof.LOF_F32, units, 0)
+        for b in (0, 1):
+            fl.flag_block(lof.LOF_F32, units[b], b)
         fl.status()
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         ts = []
-        for _ in range(reps):
+        for r in range(reps):
             e0.record(st)
-            fl.flag_block(lof.LOF_F32, units, 0)
+            fl.flag_block(lof.LOF_F32, units[r % 2], 2 + r)
             e1.record(st)
             e1.synchronize()
             ts.append(e0.elapsed_time(e1))
         fl.status()
+    x = xs[0]
     ms = sorted(ts)[reps // 2]
     n = x.numel()
     return {"ms": ms, "Msamples_s": n / ms / 1e3, "GBs_9B_per_sample": 9 * n / ms / 1e6}

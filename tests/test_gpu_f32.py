@@ -145,3 +145,32 @@ def test_cluster_kernel_std_estimator_within_tolerance():
         masks, outs, stats = _run_gpu(fl, xs)
     ref = oracle.flag_unit(p, xs[0])
     _check_unit(p, xs[0], masks[0], outs[0], stats[0], ref, tag="f32 cluster std")
+
+
+def test_hinted_window_selection_equals_radix_selection():
+    """Units with history slots take the previous block's median and MAD as
+    hints (two window passes each); without slots, the three radix passes.
+    Both give the same order statistics, so identical results, on a hit
+    (block 1 after block 0), a miss (block 2 scaled by 10) and again a hit."""
+    C, T = 16, 12288
+    xs = {}
+    for b in range(4):
+        spec = synth.PulsarSpec(n_subband=3, C=C, T=T)
+        x = synth.stokes_block(spec, seed=77, block=b, device="cpu").numpy().astype(np.float32)
+        xs[b] = x * (10.0 if b == 2 else 1.0)
+    with lof.Flagger(0, n_history_slots=3 * C, enable_history=0) as fa, \
+            lof.Flagger(0, enable_history=0) as fb:
+        for b in range(4):
+            ins = [torch.as_tensor(xs[b][s]).to(DEV) for s in range(3)]
+            res = []
+            for fl, slots in ((fa, True), (fb, False)):
+                masks = [torch.empty(t.shape, dtype=torch.uint8, device=DEV) for t in ins]
+                stats = lof.stats_tensor(3, DEV)
+                units = [lof.make_unit(ins[s], None, masks[s], s * C if slots else -1, stats[s]) for s in range(3)]
+                fl.flag_block(lof.LOF_F32, units, b)
+                fl.status()
+                res.append(([m.cpu().numpy() for m in masks], [lof.decode_stats(s) for s in stats.cpu()]))
+            (ma, sa), (mb, sb) = res
+            for s in range(3):
+                assert np.array_equal(ma[s], mb[s]), f"block {b} unit {s}: masks differ"
+                assert sa[s] == sb[s], (b, s, sa[s], sb[s])
