@@ -456,11 +456,32 @@ struct Fixed {
   uint32_t wlo;               // first value of the window
   long long wbelow;           // kept samples below the window
   unsigned long long sd, md4;
+  unsigned long long sel1, sel2;  // order statistics of the spectrum (rank selection)
   double sig;
   int kmax_f;
 };
 
 // ------------------------------------------------------------------ round 1
+// Order statistics r1 <= r2 of n <= 2 NT values (whole CTA): each value's
+// rank is counted against all n (ties by index), and the values of ranks r1
+// and r2 are written to *o1, *o2.
+template <int NT>
+__device__ void rank_select2(const unsigned long long* v, int n, int r1, int r2, unsigned long long* o1,
+                             unsigned long long* o2) {
+  for (int i = threadIdx.x; i < n; i += NT) {
+    const unsigned long long x = v[i];
+    int rk = 0;
+#pragma unroll 8
+    for (int j = 0; j < n; ++j) {
+      const unsigned long long y = v[j];
+      rk += (y < x || (y == x && j < i)) ? 1 : 0;
+    }
+    if (rk == r1) *o1 = x;
+    if (rk == r2) *o2 = x;
+  }
+  __syncthreads();
+}
+
 // Frequency pass, run by the CTA that completes round 1 of a unit: median and
 // robust sigma of the spectrum and SumThreshold over it (Section 4).
 // Needs 36 KB of shared workspace.
@@ -473,8 +494,8 @@ __device__ void frequency_pass(const KParams& kp, const DevUnit& u, UnitState* s
   while (n2 < C) n2 <<= 1;
   unsigned long long* srt = reinterpret_cast<unsigned long long*>(ws);  // kMaxChan
   unsigned long long* Sv = srt + kMaxChan;                               // kMaxChan
-  uint8_t* fire = reinterpret_cast<uint8_t*>(Sv + kMaxChan);             // kMaxChan
-  uint8_t* Fc = fire + kMaxChan;                                         // kMaxChan (kept after)
+  // fire flags [32K, 34K); Fc [34K, 36K) is kept for round 1
+  uint8_t* Fc = reinterpret_cast<uint8_t*>(Sv + kMaxChan) + kMaxChan;
   const unsigned long long* gS = kp.chan_S + u.chan_off;
   for (int i = tid; i < n2; i += NT) {
     unsigned long long v = ~0ull;
@@ -486,8 +507,15 @@ __device__ void frequency_pass(const KParams& kp, const DevUnit& u, UnitState* s
     srt[i] = v;
   }
   __syncthreads();
-  block_sort64<NT>(srt, n2);
-  if (tid == 0) f.sd = (C & 1) ? 2ull * srt[C / 2] : srt[C / 2 - 1] + srt[C / 2];
+  // the middle order statistics: counted ranks for up to 2 NT channels, else a sort
+  const bool ranks = C <= 2 * NT;
+  if (ranks) {
+    rank_select2<NT>(Sv, C, (C - 1) / 2, C / 2, &f.sel1, &f.sel2);
+    if (tid == 0) f.sd = (C & 1) ? 2ull * f.sel2 : f.sel1 + f.sel2;
+  } else {
+    block_sort64<NT>(srt, n2);
+    if (tid == 0) f.sd = (C & 1) ? 2ull * srt[C / 2] : srt[C / 2 - 1] + srt[C / 2];
+  }
   __syncthreads();
   const unsigned long long M2 = f.sd;  // twice the median of S
   for (int i = tid; i < n2; i += NT) {
@@ -499,10 +527,12 @@ __device__ void frequency_pass(const KParams& kp, const DevUnit& u, UnitState* s
     srt[i] = d;
   }
   __syncthreads();
-  block_sort64<NT>(srt, n2);
+  if (ranks) rank_select2<NT>(srt, C, (C - 1) / 2, C / 2, &f.sel1, &f.sel2);
+  else block_sort64<NT>(srt, n2);
   if (tid == 0) {
     // 4 x MAD: the median of |2S - M2| counted twice
-    f.md4 = (C & 1) ? 2ull * srt[C / 2] : srt[C / 2 - 1] + srt[C / 2];
+    f.md4 = ranks ? ((C & 1) ? 2ull * f.sel2 : f.sel1 + f.sel2)
+                  : ((C & 1) ? 2ull * srt[C / 2] : srt[C / 2 - 1] + srt[C / 2]);
     const double med = __dmul_rn(__ull2double_rn(M2), 0.5);
     const double mad = __dmul_rn(__ull2double_rn(f.md4), 0.25);
     double sig;
@@ -530,6 +560,7 @@ __device__ void frequency_pass(const KParams& kp, const DevUnit& u, UnitState* s
   const int kmax = f.kmax_f;
   // Section 2.1 over the spectrum: direct window sums (C <= 2048 values)
   if (kp.enable_freq && sig > 0.0) {
+    uint8_t* fire = Fc - kMaxChan;  // [32K, 34K)
     for (int k = 0; k <= kmax; ++k) {
       const int I = 1 << k;
       const long long* Kt = f.K + koffset(k);
@@ -2048,21 +2079,34 @@ __device__ bool window_resolve(const KParams& kp, const DevUnit& u, UnitState* u
 #pragma unroll
   for (int k = 0; k < PER; ++k) sp[tid * PER + k] = off + loc[k];
   __syncthreads();
-  if (tid == 0) {
+  if (warp == 0) {
+    // warp 0: 32-ary searches (each step probes 32 points of the range)
     const long long N = __ldcg(&us->n_pool), below = f.wbelow, inw = sp[kWinVals - 1];
     bool ok = below >= 0 && below + inw <= N;
-    if (!ok) set_error(kp, kErrInternal, 50);
+    if (!ok && lane == 0) set_error(kp, kErrInternal, 50);
+    // least x in [a, b] with pred(x), pred monotone and true at b (whole warp)
+    auto first_true = [&](long long a, long long b, auto pred) -> long long {
+      while (a < b) {
+        const long long step = (b - a + 31) / 32;
+        const long long x = a + lane * step;
+        const unsigned bal = __ballot_sync(kFull, x >= b || pred(x));
+        if (bal == 0u) {  // every probe below the answer: it lies in (x_31, b]
+          a = a + 31 * step + 1;
+          continue;
+        }
+        const int fl = __ffs(bal) - 1;
+        const long long xf = a + fl * step;
+        if (xf < b) b = xf;
+        if (fl > 0) a = a + (fl - 1) * step + 1;
+      }
+      return a;
+    };
     // the r-th smallest value (0-based)
     auto vrank = [&](long long r, long long* y) -> bool {
       const long long q = r + 1 - below;
       if (q < 1 || q > inw) return false;
-      int a = 0, b = static_cast<int>(kWinVals) - 1;
-      while (a < b) {
-        const int m = (a + b) >> 1;
-        if (static_cast<long long>(sp[m]) >= q) b = m;
-        else a = m + 1;
-      }
-      *y = static_cast<long long>(wlo) + a;
+      *y = static_cast<long long>(wlo) +
+           first_true(0, kWinVals - 1, [&](long long i) { return static_cast<long long>(sp[i]) >= q; });
       return true;
     };
     auto cle = [&](long long y, bool* exact) -> long long {
@@ -2083,14 +2127,11 @@ __device__ bool window_resolve(const KParams& kp, const DevUnit& u, UnitState* u
     // the r-th smallest distance: least d in [0, 2 kWinVals + 2] (beyond it
     // endB leaves the window) with c(d) >= r + 1 or an inexact c(d)
     auto dist = [&](long long r, long long* D) -> bool {
-      long long a = 0, b = 2ll * kWinVals + 2;
-      while (a < b) {
-        const long long m = (a + b) >> 1;
+      const long long a = first_true(0, 2ll * kWinVals + 2, [&](long long m) {
         bool e = true;
         const long long c = cle(endB(M2, m), &e) - cle(endA(M2, m) - 1, &e);
-        if (!e || c >= r + 1) b = m;
-        else a = m + 1;
-      }
+        return !e || c >= r + 1;
+      });
       bool e = true;
       const long long c = cle(endB(M2, a), &e) - cle(endA(M2, a) - 1, &e);
       *D = a;
@@ -2098,9 +2139,11 @@ __device__ bool window_resolve(const KParams& kp, const DevUnit& u, UnitState* u
     };
     long long d1 = 0, d2 = 0;
     ok = ok && dist(r1, &d1) && ((N & 1) ? (d2 = d1, true) : dist(r2, &d2));
-    f.resolved = ok ? 1 : 0;
-    f.m2lo = M2;
-    f.da[0] = d1 + d2;
+    if (lane == 0) {
+      f.resolved = ok ? 1 : 0;
+      f.m2lo = M2;
+      f.da[0] = d1 + d2;
+    }
   }
   __syncthreads();
   if (!f.resolved) return false;
@@ -2380,10 +2423,16 @@ __device__ __forceinline__ uint32_t stats_rows(const DevUnit& u, int row0, int R
     const int kr = k / nseg, s = k - kr * nseg;
     const uint8_t* grow =
         gin + static_cast<int64_t>(row0 + min(warp + kr * NW, R - 1)) * u.in_stride * TR::kBytes;
+    if (k < nk && vin && s * SEG + SEG <= T) {  // a whole segment: plain vector loads
 #pragma unroll
-    for (int q = 0; q < NQ; ++q) {
-      const int x = s * SEG + q * 32 * VS + lane * VS;
-      v[q] = (k < nk && x < T) ? gload_raw<DT>(grow, x, T, vin, pol) : make_uint4(0u, 0u, 0u, 0u);
+      for (int q = 0; q < NQ; ++q)
+        v[q] = ldg_policy(grow + static_cast<size_t>(s * SEG + q * 32 * VS + lane * VS) * TR::kBytes, pol);
+    } else {
+#pragma unroll
+      for (int q = 0; q < NQ; ++q) {
+        const int x = s * SEG + q * 32 * VS + lane * VS;
+        v[q] = (k < nk && x < T) ? gload_raw<DT>(grow, x, T, vin, pol) : make_uint4(0u, 0u, 0u, 0u);
+      }
     }
   };
   Acc sum = 0;
@@ -2405,13 +2454,15 @@ __device__ __forceinline__ uint32_t stats_rows(const DevUnit& u, int row0, int R
         red_shared_inc(si < nsc ? wsa + 4u * si : hsa + 4u * key);
       }
     };
+    if (s * SEG + SEG <= T) {  // a whole segment: no bound per vector
 #pragma unroll
-    for (int q = 0; q < NQ; ++q) {
-      const int x = s * SEG + q * 32 * VS + lane * VS;
-      if (x + VS <= T) {
+      for (int q = 0; q < NQ; ++q)
 #pragma unroll
         for (int j = 0; j < VS; ++j) count(raw_pw<DT>(cur[q], j));
-      } else {
+    } else {
+#pragma unroll
+      for (int q = 0; q < NQ; ++q) {
+        const int x = s * SEG + q * 32 * VS + lane * VS;
 #pragma unroll
         for (int j = 0; j < VS; ++j)
           if (x + j < T) count(raw_pw<DT>(cur[q], j));
