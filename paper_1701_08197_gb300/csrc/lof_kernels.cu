@@ -432,6 +432,7 @@ template <int NT>
 struct Fixed {
   uint64_t mbar;
   int item, ok, last, state, n_keep, n_tgt, q_done, n_def, rows_done;
+  int row_next;  // flag task: next kept row to hand out (warps claim rows as they go)
   int def[9];  // parked tasks whose unit was not ready
   unsigned int red_u32[NT / kWarp];
   unsigned long long red_a[NT / kWarp], red_b[NT / kWarp], red_c[NT / kWarp];
@@ -2741,6 +2742,7 @@ __device__ LOFK_TASK_FN void task_flag(const KParams& kp, const DevUnit& u, Unit
   for (int i = tid; i < R * MW; i += NT) smbits[i] = 0u;
   if (tid == 0) {
     f.rows_done = 0;
+    f.row_next = NW;
     f.time_on = __ldcg(&us->time_on);
     int kmax = 0;
     while (kmax < kp.max_log_window && (2 << kmax) <= T) ++kmax;
@@ -2807,21 +2809,30 @@ __device__ LOFK_TASK_FN void task_flag(const KParams& kp, const DevUnit& u, Unit
       const int nsg = wr_seg_count<kWrNpl>(T);
       uint8_t* const stage = ws + ((4 * R * MW + 15) & ~15) + warp * 2 * ST::kBufBytes;
       const uint64_t pol = l2_policy_drop();  // the input's last read
-      const int nrw = nkeep > warp ? (nkeep - warp + NW - 1) / NW : 0;
-      const int nit = nrw * nsg;
-      auto row_of = [&](int it) { return row0 + f.keep[warp + (it / nsg) * NW]; };
-      auto stage_item = [&](int it) {
-        const WrSeg g = wr_seg<kWrNpl>(T, it % nsg);
-        wr_stage<DT, kWrNpl>(stage + (it & 1) * ST::kBufBytes + lane * ST::kRowBytes,
-                             gin + static_cast<int64_t>(row_of(it)) * u.in_stride * TR::kBytes, g.xl, T,
+      // rows are claimed one at a time (warp w starts with kept row w), so the
+      // warps of a task finish within about one row of each other
+      auto stage_item = [&](int k, int sg, int buf) {
+        const WrSeg g = wr_seg<kWrNpl>(T, sg);
+        wr_stage<DT, kWrNpl>(stage + buf * ST::kBufBytes + lane * ST::kRowBytes,
+                             gin + static_cast<int64_t>(row0 + f.keep[k]) * u.in_stride * TR::kBytes, g.xl, T,
                              vin, pol);
       };
-      if (nit > 0) stage_item(0);
+      int kc = warp < nkeep ? warp : -1, sg = 0, buf = 0;
+      if (kc >= 0) stage_item(kc, 0, 0);
       int nfl_row = 0;
       unsigned long long su_row = 0;
-      for (int it = 0; it < nit; ++it) {
-        const int sg = it % nsg, c = row_of(it), r = c - row0;
-        uint8_t* const srow = stage + (it & 1) * ST::kBufBytes + lane * ST::kRowBytes;
+      while (kc >= 0) {
+        // the next item: the next segment of this row, or the first of a claimed row
+        int kn = kc, sgn = sg + 1;
+        if (sgn == nsg) {
+          sgn = 0;
+          int claim = 0;
+          if (lane == 0) claim = atomicAdd(&f.row_next, 1);
+          claim = __shfl_sync(kFull, claim, 0);
+          kn = claim < nkeep ? claim : -1;
+        }
+        const int c = row0 + f.keep[kc], r = c - row0;
+        uint8_t* const srow = stage + buf * ST::kBufBytes + lane * ST::kRowBytes;
         WrOut o;
         o.out = u.out ? static_cast<uint8_t*>(u.out) + static_cast<int64_t>(c) * u.out_stride * TR::kBytes
                       : nullptr;
@@ -2844,18 +2855,18 @@ __device__ LOFK_TASK_FN void task_flag(const KParams& kp, const DevUnit& u, Unit
         cp_async_wait_all();  // this item's samples (the only group in flight)
         WrRow<kWrNpl> Rw;
         wr_build<DT, kWrNpl>(Rw, srow, s_Kp[0]);
-        if (it + 1 < nit) {
+        if (kn >= 0) {
           // the next item into the other buffer as early as possible (the
           // input comes from DRAM), once the bulk stores of its last item
           // have read it
           bulk_wait_read();
-          stage_item(it + 1);
+          stage_item(kn, sgn, buf ^ 1);
         }
         wr_passes<kWrNpl>(Rw, g, 1, f.kmax_t, s_Kp, (kp.schedule & LOF_SCHED_BOUND64) != 0);
         int nfl = 0;
         unsigned long long su = 0;
         wr_finish<DT, kWrNpl>(Rw, g, T, srow, smbits + r * MW + 2, o, nfl, su);
-        if (coal_row) wr_store_coalesced<DT, kWrNpl>(stage + (it & 1) * ST::kBufBytes, Rw.M[0], g, T, coal_row);
+        if (coal_row) wr_store_coalesced<DT, kWrNpl>(stage + buf * ST::kBufBytes, Rw.M[0], g, T, coal_row);
         nfl_row += nfl;
         su_row += su;
         if (sg == nsg - 1) {
@@ -2879,6 +2890,9 @@ __device__ LOFK_TASK_FN void task_flag(const KParams& kp, const DevUnit& u, Unit
             }
           }
         }
+        kc = kn;
+        sg = sgn;
+        buf ^= 1;
       }
       bulk_wait_all();  // buffers free for the next task; data stored
       if (tid == 0) f.rows_done = 1;
