@@ -204,11 +204,12 @@ int lof_flag_block(lof_ctx *ctx, int dtype, const lof_unit *units, int n_units,
 /* Same operation with HOST buffers: in/out/mask/stats of every unit are host
  * pointers (pinned memory gives asynchronous copies).  Inputs are copied to
  * context-owned device staging memory, flagged, and out/mask/stats copied
- * back.  The units are taken in up to 8 chunks of whole units: a chunk's
+ * back.  The units are taken in up to 16 chunks of whole units: a chunk's
  * uploads run on an internal copy stream, its flag launch on cuda_stream
  * (after those uploads) and its downloads on a second internal copy stream
  * (after that launch), so the copies of neighbouring chunks overlap the
- * kernel.  Rows that are contiguous in host memory move as one copy.  The
+ * kernel; each chunk's uploads are issued after the previous chunk's launch.
+ * Consecutive units whose host buffers are contiguous move as one copy.  The
  * copies start after the work already queued on cuda_stream, and cuda_stream
  * waits for the last download: the call returns after enqueueing, and
  * synchronising cuda_stream covers all of it.  Host buffers must stay valid

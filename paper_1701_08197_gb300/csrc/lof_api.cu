@@ -28,7 +28,7 @@ namespace {
 thread_local char g_create_error[512];
 
 constexpr int kStageRing = 4;
-constexpr int kHostChunks = 8;  // pipeline depth of lof_flag_block_host
+constexpr int kHostChunks = 16;  // pipeline depth of lof_flag_block_host
 
 int esize_of(int dtype) {
   switch (dtype) {
@@ -879,7 +879,7 @@ lofk::HostCfg host_cfg(const lof_ctx* c) {
 
 // Builds and launches one block for units already holding DEVICE pointers.
 int flag_block_device(lof_ctx* c, int dtype, const lof_unit* units, int n_units, uint64_t seq,
-                      void* stream) {
+                      void* stream, bool err_copy = true) {
   char why[512];
   const lofk::HostCfg h = host_cfg(c);
   int n_tasks = 0;
@@ -929,6 +929,7 @@ int flag_block_device(lof_ctx* c, int dtype, const lof_unit* units, int n_units,
   rc = lofk::host_launch(c->params, h, dtype, pr, sc, du, n_units, tasks, seq, stream, why, sizeof why);
   cudaEventRecord(c->ev_stage[si], st);
   if (rc) return fail(c, rc, "lof_flag_block: %s", why);
+  if (!err_copy) return LOF_OK;  // a later call of the same host-path block copies it
   if ((e = cudaMemcpyAsync(c->h_err, c->d_ctrl + 1, 3 * sizeof(int), cudaMemcpyDeviceToHost, st)) !=
       cudaSuccess)
     return cuda_fail(c, e, "error word copy");
@@ -1027,17 +1028,23 @@ extern "C" int lof_flag_block_host(lof_ctx* c, int dtype, const lof_unit* units,
   if (n_units == 0) return LOF_OK;
   if ((rc = host_path_streams(c))) return rc;
   const int es = esize_of(dtype);
-  // device staging: compact [C][T] input, output and mask, plus stats
+  // device staging: compact [C][T] inputs of all units, then their outputs,
+  // then their masks, then the stats (consecutive units whose host buffers
+  // are contiguous then move with one copy per chunk and direction)
   size_t need = 0;
   std::vector<size_t> off_in(n_units), off_out(n_units), off_mask(n_units), off_st(n_units);
   for (int i = 0; i < n_units; ++i) {
-    const size_t n = static_cast<size_t>(units[i].n_chan) * units[i].n_time;
     off_in[i] = need;
-    need += round_up64(n * es, 256);
+    need += round_up64(static_cast<size_t>(units[i].n_chan) * units[i].n_time * es, 256);
+  }
+  for (int i = 0; i < n_units; ++i) {
     off_out[i] = need;
-    if (units[i].out && units[i].out != units[i].in) need += round_up64(n * es, 256);
+    if (units[i].out && units[i].out != units[i].in)
+      need += round_up64(static_cast<size_t>(units[i].n_chan) * units[i].n_time * es, 256);
+  }
+  for (int i = 0; i < n_units; ++i) {
     off_mask[i] = need;
-    if (units[i].mask) need += round_up64(n, 256);
+    if (units[i].mask) need += round_up64(static_cast<size_t>(units[i].n_chan) * units[i].n_time, 256);
   }
   // statistics records of all units side by side (one download when the
   // caller's records are contiguous too)
@@ -1096,7 +1103,9 @@ extern "C" int lof_flag_block_host(lof_ctx* c, int dtype, const lof_unit* units,
   if (e == cudaSuccess) e = cudaStreamWaitEvent(c->s_up, c->ev_start, 0);
   if (e == cudaSuccess) e = cudaStreamWaitEvent(c->s_down, c->ev_start, 0);
   if (e != cudaSuccess) return cuda_fail(c, e, "host path: stream order");
-  for (int g = 0; g < nchunk; ++g) {
+  // (Issued chunk by chunk: the launch's own small descriptor copies then
+  // queue behind their chunk's upload only, not behind every chunk's.)
+  auto upload = [&](int g) -> cudaError_t {
     std::vector<HostCopy> up;
     for (int i = cut[g]; i < cut[g + 1]; ++i) {
       const lof_unit& u = units[i];
@@ -1104,14 +1113,20 @@ extern "C" int lof_flag_block_host(lof_ctx* c, int dtype, const lof_unit* units,
       add_copy(up, const_cast<void*>(du[i].in), rowb, u.in, static_cast<size_t>(u.in_row_stride) * es, rowb,
                u.n_chan);
     }
-    if ((e = run_copies(up, cudaMemcpyHostToDevice, c->s_up)) != cudaSuccess ||
-        (e = cudaEventRecord(c->ev_in[g], c->s_up)) != cudaSuccess)
-      return cuda_fail(c, e, "host input copy");
-  }
+    cudaError_t ee = run_copies(up, cudaMemcpyHostToDevice, c->s_up);
+    if (ee == cudaSuccess) ee = cudaEventRecord(c->ev_in[g], c->s_up);
+    return ee;
+  };
+  if ((e = upload(0)) != cudaSuccess) return cuda_fail(c, e, "host input copy");
   for (int g = 0; g < nchunk; ++g) {
     if ((e = cudaStreamWaitEvent(st, c->ev_in[g], 0)) != cudaSuccess) return cuda_fail(c, e, "host path: stream order");
-    rc = flag_block_device(c, dtype, du.data() + cut[g], cut[g + 1] - cut[g], block_seq, cuda_stream);
+    // the device error word is read back once, after the last chunk (a copy
+    // after every chunk would queue behind the previous chunk's downloads
+    // and hold back the next launch)
+    rc = flag_block_device(c, dtype, du.data() + cut[g], cut[g + 1] - cut[g], block_seq, cuda_stream,
+                           g + 1 == nchunk);
     if (rc) return rc;
+    if (g + 1 < nchunk && (e = upload(g + 1)) != cudaSuccess) return cuda_fail(c, e, "host input copy");
     if ((e = cudaEventRecord(c->ev_flag[g], st)) != cudaSuccess ||
         (e = cudaStreamWaitEvent(c->s_down, c->ev_flag[g], 0)) != cudaSuccess)
       return cuda_fail(c, e, "host path: stream order");
