@@ -1430,7 +1430,6 @@ __device__ __forceinline__ void wr_fire(const WrRow<NPL>& R, int lane, const uin
 #pragma unroll
     for (int b = 31; b >= 0; --b) {
       const int j = 32 * w + b;
-      if ((j & 15) == 15) __syncwarp();
       f = __funnelshift_l(__shfl_sync(kFull, Kreg, S) - S, f, 1);
       if (j > 0) S = S + R.u[j - 1] - wr_uat<NPL>(R, lane, j - 1 + I);
     }
@@ -1726,33 +1725,33 @@ __device__ __forceinline__ WrSeg wr_seg(int T, int sg) {
 // stores (whole warp): in round r lane L writes the (32 r + L)-th 16-byte
 // chunk of the span, read from the staged row of lane (32 r + L) / CPL
 // (CPL = chunks per lane) with the flagged samples zeroed from that lane's
-// flag word; a row's last chunk, when it ends inside it, sample by sample.
-// Chunks past T or outside the interior are skipped.  (Measured against one
-// bulk copy per lane from the staged rows: 0.26 against 0.42 ms for the data
-// of a full-station block.)
-// Staged rows are padded by 16 bytes, so the 16-byte shared loads of a
-// quarter warp still fall on distinct banks.
+// flag word, and, when mask_row is given, the chunk's mask bytes (four or
+// eight, one store).  Only whole chunks inside [oa, min(ob, T)) are stored
+// in the rounds; a row's last chunk, when the row ends inside it, goes
+// sample by sample from lane 0.  (Measured against one bulk copy per lane
+// from the staged rows: 0.26 against 0.42 ms for the data of a full-station
+// block.)  Staged rows are padded by 16 bytes, so the 16-byte shared loads of
+// a quarter warp still fall on distinct banks.
 template <int DT, int NPL>
 __device__ __forceinline__ void wr_store_coalesced(const uint8_t* stage, uint32_t M, const WrSeg& g, int T,
-                                                   uint8_t* out_row) {
+                                                   uint8_t* out_row, uint8_t* mask_row) {
   using TR = Traits<DT>;
-  constexpr int VS = TR::kVec, CPL = NPL / VS, RB = WrStage<DT, NPL>::kRowBytes;
+  constexpr int VS = TR::kVec, CPL = NPL / VS, LPR = 32 / CPL, RB = WrStage<DT, NPL>::kRowBytes;
+  static_assert(32 % CPL == 0, "whole staged rows per round");
   const int lane = threadIdx.x & 31;
+  const int xe = min(g.ob, T);
+  const int k_lo = (g.oa - g.s0) / VS, k_hi = (xe - g.s0) / VS;  // whole chunks [k_lo, k_hi)
+  const int q = lane % CPL, sh = VS * q;
+  const uint8_t* const sp = stage + (lane / CPL) * RB + 16 * q;
+  uint8_t* const op = out_row + static_cast<size_t>(g.s0 + lane * VS) * TR::kBytes;
+  uint8_t* const mp = mask_row ? mask_row + g.s0 + lane * VS : nullptr;
   __syncwarp();  // every lane's staged samples (its own cp.async group) visible to the warp
 #pragma unroll
   for (int r = 0; r < CPL; ++r) {
-    const int k = 32 * r + lane, src = k / CPL, q = k % CPL;
-    const uint32_t m = __shfl_sync(kFull, M, src);
-    const int x = g.s0 + k * VS;  // first sample of the chunk
-    if (x >= g.oa && x < g.ob && x < T && x + VS > T) {  // the row's last, partial chunk
-      const uint8_t* sp = stage + src * RB + 16 * q;
-      for (int j = 0; j < T - x; ++j) {
-        if ((m >> (VS * q + j)) & 1u) TR::zero(out_row, x + j);
-        else TR::copy(out_row + static_cast<size_t>(x + j) * TR::kBytes, sp + j * TR::kBytes);
-      }
-    } else if (x >= g.oa && x < g.ob && x + VS <= T) {
-      uint4 w = *reinterpret_cast<const uint4*>(stage + src * RB + 16 * q);
-      const uint32_t bits = (m >> (VS * q)) & ((1u << VS) - 1u);
+    const uint32_t m = __shfl_sync(kFull, M, r * LPR + lane / CPL);
+    if (static_cast<unsigned>(32 * r + lane - k_lo) < static_cast<unsigned>(k_hi - k_lo)) {
+      uint4 w = *reinterpret_cast<const uint4*>(sp + r * LPR * RB);
+      const uint32_t bits = (m >> sh) & ((1u << VS) - 1u);
       if (bits) {
         uint32_t wd[4] = {w.x, w.y, w.z, w.w};
 #pragma unroll
@@ -1764,7 +1763,30 @@ __device__ __forceinline__ void wr_store_coalesced(const uint8_t* stage, uint32_
         }
         w = make_uint4(wd[0], wd[1], wd[2], wd[3]);
       }
-      __stcs(reinterpret_cast<uint4*>(out_row + static_cast<size_t>(x) * TR::kBytes), w);
+      __stcs(reinterpret_cast<uint4*>(op + r * 32 * 16), w);
+      if (mp) {
+        if constexpr (VS == 4) {
+          __stcs(reinterpret_cast<unsigned int*>(mp + r * 32 * VS), (bits * 0x00204081u) & 0x01010101u);
+        } else {
+          __stcs(reinterpret_cast<uint2*>(mp + r * 32 * VS),
+                 make_uint2(((bits & 0xFu) * 0x00204081u) & 0x01010101u, ((bits >> 4) * 0x00204081u) & 0x01010101u));
+        }
+      }
+    }
+  }
+  // the row's last, partial chunk (warp-uniform condition)
+  const int xp = g.s0 + k_hi * VS;
+  if (xe == T && xp < T && xp >= g.oa) {
+    const uint32_t m = __shfl_sync(kFull, M, k_hi / CPL);
+    if (lane == 0) {
+      const uint8_t* spp = stage + (k_hi / CPL) * RB + 16 * (k_hi % CPL);
+      const int sb = VS * (k_hi % CPL);
+      for (int j = 0; j < T - xp; ++j) {
+        const uint32_t fl = (m >> (sb + j)) & 1u;
+        if (fl) TR::zero(out_row, xp + j);
+        else TR::copy(out_row + static_cast<size_t>(xp + j) * TR::kBytes, spp + j * TR::kBytes);
+        if (mask_row) mask_row[xp + j] = static_cast<uint8_t>(fl);
+      }
     }
   }
 }
@@ -2382,11 +2404,13 @@ __device__ LOFK_TASK_FN void unit_round2(const KParams& kp, const DevUnit& u, Un
 __device__ __forceinline__ void red_shared_inc(uint32_t addr) {
   asm volatile("red.shared.add.u32 [%0], 1;" ::"r"(addr) : "memory");
 }
-__device__ __forceinline__ void red_shared_inc_if(bool p, uint32_t addr) {
+// Adds 1 to the shared counter at byte address base + 4 * t when t < n
+// (unsigned): the comparison and the reduction in one predicated pair.
+__device__ __forceinline__ void red_shared_inc_below(uint32_t t, uint32_t n, uint32_t base) {
   asm volatile(
-      "{\n\t.reg .pred q;\n\tsetp.ne.u32 q, %0, 0;\n\t@q red.shared.add.u32 [%1], 1;\n\t}" ::"r"(
-          static_cast<uint32_t>(p)),
-      "r"(addr)
+      "{\n\t.reg .pred q;\n\t.reg .u32 a;\n\tsetp.lt.u32 q, %0, %1;\n\t"
+      "mad.lo.u32 a, %0, 4, %2;\n\t@q red.shared.add.u32 [a], 1;\n\t}" ::"r"(t),
+      "r"(n), "r"(base)
       : "memory");
 }
 
@@ -2446,7 +2470,7 @@ __device__ __forceinline__ uint32_t stats_rows(const DevUnit& u, int row0, int R
       if constexpr (WIN) {
         const int t = static_cast<int>(val - wlo);
         below += static_cast<uint32_t>(t) >> 31;
-        red_shared_inc_if(static_cast<uint32_t>(t) < kWinVals, wsa + 4u * static_cast<uint32_t>(t));
+        red_shared_inc_below(static_cast<uint32_t>(t), kWinVals, wsa);
       } else {
         // the value's counter inside a target bin (the bin's coarse count is
         // rebuilt from those below), else its bin
@@ -2846,7 +2870,11 @@ __device__ LOFK_TASK_FN void task_flag(const KParams& kp, const DevUnit& u, Unit
         // with coalesced stores after the pass, the mask bytes per lane
         uint8_t* const coal_row =
             ((kp.schedule & LOF_SCHED_COALESCED) && o.out && !o.inplace && o.vout) ? o.out : nullptr;
+        // with it, mask rows of 16-byte aligned rows and stride go out in the same rounds
+        uint8_t* const coal_mask = (coal_row && o.mask && o.mask_vec) ? o.mask : nullptr;
         if (coal_row) o.out = nullptr;
+        if (coal_mask) o.mask = nullptr;
+        o.enabled = o.out != nullptr || o.mask != nullptr;
         if (sg == 0) {
           nfl_row = 0;
           su_row = 0;
@@ -2866,7 +2894,8 @@ __device__ LOFK_TASK_FN void task_flag(const KParams& kp, const DevUnit& u, Unit
         int nfl = 0;
         unsigned long long su = 0;
         wr_finish<DT, kWrNpl>(Rw, g, T, srow, smbits + r * MW + 2, o, nfl, su);
-        if (coal_row) wr_store_coalesced<DT, kWrNpl>(stage + buf * ST::kBufBytes, Rw.M[0], g, T, coal_row);
+        if (coal_row)
+          wr_store_coalesced<DT, kWrNpl>(stage + buf * ST::kBufBytes, Rw.M[0], g, T, coal_row, coal_mask);
         nfl_row += nfl;
         su_row += su;
         if (sg == nsg - 1) {
