@@ -53,7 +53,7 @@ extern "C" int lofk_integ_max_time();
 extern "C" int lofk_launch_integ(int dtype, const lofk::KParams* kp, int n_units, int n_sm, void* stream,
                                  int mode, int cell_chan, int cell_time);
 extern "C" int lofk_launch_sir(const lofk::DevUnit* units, int n_units, int64_t n_chan, int max_chan,
-                               int percent, int es, void* stream);
+                               int max_time, int percent, int es, void* stream);
 
 struct lof_ctx {
   int device = 0;
@@ -573,9 +573,13 @@ int host_prepare(const HostCfg& h, int dtype, const lof_unit* units, int n_units
   int budget = dyn_budget(h, dtype, pl.threads, pl.ctas);
   if (h.tuning.tile_bytes) budget = std::min(budget, h.tuning.tile_bytes);
   int64_t chan = 0, per_step = 0;
+  out->max_C = 1;
+  out->max_T = 1;
   for (int i = 0; i < n_units; ++i) {
     const lof_unit& u = units[i];
     DevUnit& d = du[i];
+    out->max_C = std::max(out->max_C, u.n_chan);
+    out->max_T = std::max(out->max_T, u.n_time);
     d.in = u.in;
     d.out = u.out;
     d.mask = u.mask;
@@ -768,7 +772,7 @@ int host_launch_kernel(const lof_params& P, const HostCfg& h, int dtype, const P
   }
   if (P.sir_percent > 0) {
     // Section 2.2: the SIR operator on the final mask (time, then frequency)
-    const int src = lofk_launch_sir(sc.units, n_units, pr.n_chan, kMaxChan, P.sir_percent,
+    const int src = lofk_launch_sir(sc.units, n_units, pr.n_chan, pr.max_C, pr.max_T, P.sir_percent,
                                     esize_of(dtype), stream);
     if (src != 0) {
       snprintf(why, nwhy, "SIR launch failed: %d", src);

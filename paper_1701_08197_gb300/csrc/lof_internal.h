@@ -173,7 +173,7 @@ struct Prep {
   int n_tasks_stats, grid_flag;  // tasks of the statistics launch (the first ones); CTAs of the flag launch
   int64_t n_chan;
   int gen_words;                 // per CTA, general time-pass rows
-  int max_C, max_T;              // float units: the largest unit's channels and samples
+  int max_C, max_T;              // the largest unit's channels and samples
 };
 // Device memory one launch works in.
 struct Scratch {

@@ -16,7 +16,9 @@
 // before it and the suffix maximum after it, from which its NPT decisions
 // follow in registers.  Newly flagged samples get mask 1 and zero data, and
 // are added to the unit's flag count.
+#include <algorithm>
 #include <cstdint>
+#include <type_traits>
 
 #include <cuda_runtime.h>
 
@@ -225,12 +227,12 @@ __global__ void __launch_bounds__(32 * kSirWarps) lof_sir_time_kernel(const DevU
 // the operator down the channels, then the strip is written back.  Marks:
 // bit 0 = flagged, bit 1 = newly flagged here.
 __global__ void __launch_bounds__(32 * kSirWarps) lof_sir_freq_kernel(const DevUnit* units, int percent,
-                                                                      int es) {
+                                                                      int es, int skip_upto) {
   extern __shared__ uint8_t strip[];
   __shared__ SirTiles tiles[kSirWarps];
   __shared__ int s_added;
   const DevUnit& u = units[blockIdx.y];
-  if (!u.mask || u.C > 32 * 8 * kSirMaxTiles) return;
+  if (!u.mask || u.C > 32 * 8 * kSirMaxTiles || u.C <= skip_upto) return;
   const int C = u.C, T = u.T, warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   constexpr int RS = kSirStrip + 1;
   for (int t0 = blockIdx.x * kSirStrip; t0 < T; t0 += gridDim.x * kSirStrip) {
@@ -281,6 +283,105 @@ __global__ void __launch_bounds__(32 * kSirWarps) lof_sir_freq_kernel(const DevU
   }
 }
 
+// Frequency direction for units of at most 32 * NW channels: one thread per
+// time step (a column of the unit), its flags held as bits in registers, so
+// the columns run independently with no shuffles and no barriers.  A forward
+// pass over the column loads its flags and gives, per block of 32 channels,
+// the prefix sum at the block's start and the least prefix sum over the
+// block's starts a.  A backward pass over the blocks then recomputes each
+// block's prefix minima min_{a <= x} Q[a] in registers (from the least prefix
+// sum over the blocks before it) and decides the block's channels from the
+// last one down against the running maximum max_{b > x} Q[b].  The same
+// integer prefix sums as the line form above, so the same decisions.
+constexpr int kSirColThreads = 128;
+constexpr int kSirColWords = 8;  // channels up to 256
+
+template <int NW>
+__global__ void __launch_bounds__(kSirColThreads) lof_sir_freq_cols_kernel(const DevUnit* units, int percent,
+                                                                          int es) {
+  const DevUnit& u = units[blockIdx.y];
+  const int C = u.C, T = u.T;
+  if (!u.mask || C > 32 * NW) return;  // the line form takes the unit
+  const int t = blockIdx.x * kSirColThreads + threadIdx.x;
+  const bool on = t < T;
+  const int wp = percent, wn = percent - 100;
+  const int64_t ms = u.mask_stride;
+  uint8_t* const mcol = u.mask + (on ? t : 0);
+  uint32_t bits[NW];
+  int qs[NW], lmin[NW];
+  int q = 0;
+#pragma unroll
+  for (int w = 0; w < NW; ++w) {
+    const int n = on ? min(32, C - 32 * w) : 0;
+    uint32_t b = 0u;
+    int mn = INT32_MAX;
+    qs[w] = q;
+#pragma unroll 8
+    for (int i = 0; i < n; ++i) {
+      const uint32_t fl = mcol[static_cast<int64_t>(32 * w + i) * ms] != 0 ? 1u : 0u;
+      b = __funnelshift_r(b, fl, 1);  // bit 31 <- this flag; bit i after the shift below
+      mn = min(mn, q);
+      q += fl ? wp : wn;
+    }
+    bits[w] = n > 0 ? b >> (32 - n) : 0u;
+    lmin[w] = mn;
+  }
+  int pl[NW];  // least prefix sum over the starts of the blocks before w
+  {
+    int m = INT32_MAX;
+#pragma unroll
+    for (int w = 0; w < NW; ++w) {
+      pl[w] = m;
+      m = min(m, lmin[w]);
+    }
+  }
+  uint8_t* const orow = static_cast<uint8_t*>(u.out);
+  int added = 0, R = INT32_MIN;
+  // the block's decisions: FULL blocks hold 32 channels, the last may hold fewer
+  auto block = [&](int w, int n, auto full) {
+    constexpr bool FULL = decltype(full)::value;
+    const uint32_t bw = bits[w];
+    int L[32];
+    int l = pl[w], qq = qs[w], qe = 0;
+#pragma unroll
+    for (int i = 0; i < 32; ++i) {
+      l = min(l, qq);  // a = 32 w + i
+      L[i] = l;
+      qq += ((bw >> i) & 1u) ? wp : wn;
+      if (!FULL && i + 1 == n) qe = qq;
+    }
+    if (FULL) qe = qq;  // Q at the block's end
+    uint32_t nb = 0u;
+#pragma unroll
+    for (int i = 31; i >= 0; --i) {
+      if (FULL || i < n) {
+        R = max(R, qe);  // b = 32 w + i + 1
+        nb |= (R >= L[i] ? 1u : 0u) << i;
+        qe -= ((bw >> i) & 1u) ? wp : wn;
+      }
+    }
+    nb &= ~bw;
+    while (nb) {
+      const int i = __ffs(nb) - 1;
+      nb &= nb - 1u;
+      const int64_t c = 32 * w + i;
+      mcol[c * ms] = 1;
+      if (orow) zero_sample(orow + c * u.out_stride * es, t, es);
+      ++added;
+    }
+  };
+#pragma unroll
+  for (int w = NW - 1; w >= 0; --w) {
+    const int n = on ? min(32, C - 32 * w) : 0;
+    if (n == 32) block(w, 32, std::true_type{});
+    else if (n > 0) block(w, n, std::false_type{});
+  }
+  added = __reduce_add_sync(kFullS, added);
+  if ((threadIdx.x & 31) == 0 && added && u.stats)
+    atomicAdd(reinterpret_cast<unsigned long long*>(&u.stats->n_flag_total),
+              static_cast<unsigned long long>(added));
+}
+
 }  // namespace
 }  // namespace lofk
 
@@ -291,7 +392,7 @@ extern "C" int lofk_sir_max_time() { return 32 * 32 * lofk::kSirMaxTiles; }
 // Both directions of the SIR operator over n_units device units (es: bytes
 // per data sample).  max_chan sizes the frequency pass's shared strip.
 extern "C" int lofk_launch_sir(const lofk::DevUnit* units, int n_units, int64_t n_chan, int max_chan,
-                               int percent, int es, void* stream) {
+                               int max_time, int percent, int es, void* stream) {
   using namespace lofk;
   if (n_units <= 0 || percent <= 0) return 0;
   cudaStream_t st = static_cast<cudaStream_t>(stream);
@@ -300,12 +401,20 @@ extern "C" int lofk_launch_sir(const lofk::DevUnit* units, int n_units, int64_t 
                                                                           percent, es);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return static_cast<int>(e);
+  // frequency: units of up to 256 channels one thread per time step, larger
+  // ones by the line form (which skips the others)
+  const unsigned gx = static_cast<unsigned>((std::max(1, max_time) + kSirColThreads - 1) / kSirColThreads);
+  lof_sir_freq_cols_kernel<kSirColWords><<<dim3(gx, static_cast<unsigned>(n_units)), kSirColThreads, 0, st>>>(
+      units, percent, es);
+  e = cudaGetLastError();
+  if (e != cudaSuccess) return static_cast<int>(e);
+  if (max_chan <= 32 * kSirColWords) return 0;
   const int smem = max_chan * (kSirStrip + 1);
   if (cudaFuncSetAttribute(reinterpret_cast<const void*>(&lof_sir_freq_kernel),
                            cudaFuncAttributeMaxDynamicSharedMemorySize, smem) != cudaSuccess)
     return -2;
-  lof_sir_freq_kernel<<<dim3(16, static_cast<unsigned>(n_units)), 32 * kSirWarps, smem, st>>>(units, percent,
-                                                                                            es);
+  lof_sir_freq_kernel<<<dim3(16, static_cast<unsigned>(n_units)), 32 * kSirWarps, smem, st>>>(
+      units, percent, es, 32 * kSirColWords);
   e = cudaGetLastError();
   return e == cudaSuccess ? 0 : static_cast<int>(e);
 }

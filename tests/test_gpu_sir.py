@@ -44,6 +44,25 @@ def test_sir_units_match_oracle(percent):
                 compare_unit(d, oracle.flag_unit(P, d), outs[i], masks[i], stats[i], tag=f"unit {i}")
 
 
+@pytest.mark.parametrize("shape", [(1, 100), (33, 129), (255, 7), (32, 1000), (64, 130), (257, 64)])
+def test_sir_edge_shapes_match_oracle(shape):
+    """Channel counts around the 32-channel blocks of the frequency pass (one
+    thread per time step up to 256 channels, the line form above), time
+    steps around its 128-thread CTAs."""
+    C, T = shape
+    rng = np.random.default_rng(C * 1000 + T)
+    d = np.round(rng.normal(0, 32, (C, T, 2))).astype(np.int16)
+    d[:, T // 3:T // 3 + 3] += 400
+    d[C // 2] += 100
+    d[:, :: 7] += 60
+    P = oracle_params(sir_percent=30)
+    with lof.Flagger(0, n_history_slots=0, sir_percent=30) as fl:
+        ins, outs, masks, stats, units = gpu_units([d], DEV)
+        fl.flag_block(lof.LOF_CI16, units, 0)
+        fl.status()
+        compare_unit(d, oracle.flag_unit(P, d), outs[0], masks[0], stats[0], tag=str(shape))
+
+
 def test_sir_full_station_block_against_mask_without_sir():
     dev = torch.device(DEV)
     x = bench.make_block(dev, seed=2, n_station=4)
