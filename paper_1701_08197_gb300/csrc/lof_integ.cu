@@ -81,6 +81,30 @@ __device__ __forceinline__ uint32_t ipow(const uint8_t* row, int t) {
   }
 }
 
+// Sum of the powers of the samples of one 16-byte vector (4 ci16 or 8 ci8).
+template <int DT>
+__device__ __forceinline__ unsigned long long vec_power_sum(const uint4& v) {
+  const uint32_t w[4] = {v.x, v.y, v.z, v.w};
+  unsigned long long s = 0ull;
+#pragma unroll
+  for (int j = 0; j < 4; ++j) {
+    if constexpr (DT == LOF_CI16) {
+      const int re = static_cast<int16_t>(w[j] & 0xFFFFu), im = static_cast<int16_t>(w[j] >> 16);
+      s += static_cast<unsigned long long>(static_cast<uint32_t>(re * re) + static_cast<uint32_t>(im * im));
+    } else {
+      uint32_t p = 0u;
+#pragma unroll
+      for (int h = 0; h < 2; ++h) {
+        const uint32_t x = (w[j] >> (16 * h)) & 0xFFFFu;
+        const int re = static_cast<int8_t>(x & 0xFFu), im = static_cast<int8_t>(x >> 8);
+        p += static_cast<uint32_t>(re * re + im * im);
+      }
+      s += p;
+    }
+  }
+  return s;
+}
+
 // Calls fn(t, power) for every sample of a row, lanes in parallel: 16-byte
 // vector loads (four per lane issued before any is used) where the row is
 // 16-byte aligned, plain loads for the rest.
@@ -738,24 +762,42 @@ __device__ void chan_unit(const KParams& kp, const DevUnit& u, uint8_t* smem, In
 // and next as scratch (whole CTA): every window is judged against the flags
 // on entry and fires when the sum of its unflagged cells exceeds
 // (I - n) * thr.  Cell sums are at most 2^16 powers of at most 2^31, so a
-// window sum is at most 2^53: exact in 64-bit integers and in binary64.
+// window sum is at most 2^53: exact in 64-bit integers and in binary64, and
+// the test is the integer one su > Kw[n], Kw[n] = floor((I - n) * thr) (the
+// binary64 product), -1 where that is negative.  One thread per line slides
+// the unflagged sum and the flagged count along it (each cell enters and
+// leaves once); a fired window at t flags cells t .. t + I - 1, which the
+// slide marks as it passes them.
 __device__ void st_grid_lines(const unsigned long long* V, uint8_t* fl, uint8_t* next, int NG, int n_lines,
-                              int L, int step, int line_stride, int I, double thr) {
+                              int L, int step, int line_stride, int I, double thr, long long* Kw) {
   for (int i = threadIdx.x; i < NG; i += kNtI) next[i] = fl[i];
+  for (int n = threadIdx.x; n <= I; n += kNtI) {
+    const double P = __dmul_rn(static_cast<double>(I - n), thr);
+    Kw[n] = P < 0.0 ? -1ll : (P >= 9.0e18 ? 0x7FFFFFFFFFFFFFFFll : __double2ll_rd(P));
+  }
   __syncthreads();
-  const int nw = L - I + 1, total = n_lines * nw;
-  for (int w = threadIdx.x; w < total; w += kNtI) {
-    const int r = w / nw, t = w - r * nw;
-    const int b = r * line_stride + t * step;
+  for (int r = threadIdx.x; r < n_lines; r += kNtI) {
+    const int b = r * line_stride;
+    unsigned long long su = 0ull;
     int nf = 0;
-    unsigned long long su = 0;
-    for (int j = 0; j < I; ++j) {
+    for (int j = 0; j < I - 1; ++j) {
       const int i = b + j * step;
       if (fl[i]) ++nf;
       else su += V[i];
     }
-    if (__ull2double_rn(su) > __dmul_rn(static_cast<double>(I - nf), thr))
-      for (int j = 0; j < I; ++j) next[b + j * step] = 1;
+    int until = 0;  // cells below it lie in a fired window
+    for (int t = 0; t < L; ++t) {
+      if (t + I - 1 < L) {
+        const int ie = b + (t + I - 1) * step;  // the window at t: cells t .. t + I - 1
+        if (fl[ie]) ++nf;
+        else su += V[ie];
+        if (static_cast<long long>(su) > Kw[nf]) until = t + I;
+        const int il = b + t * step;
+        if (fl[il]) --nf;
+        else su -= V[il];
+      }
+      if (t < until) next[b + t * step] = 1;
+    }
   }
   __syncthreads();
   for (int i = threadIdx.x; i < NG; i += kNtI) fl[i] = next[i];
@@ -797,12 +839,52 @@ __device__ void grid_unit(const KParams& kp, const DevUnit& u, uint8_t* smem, In
   }
   if (tid == 0) f.cnt_time = f.cnt_total = f.cnt_hist = 0ull;
   __syncthreads();
+  // Rows of at least 32 cells: each lane sums whole cells of the row (cells
+  // [lane * gpl, lane * gpl + gpl)) in registers and adds each cell once;
+  // rows of fewer cells sample by sample.
+  constexpr int VS = DT == LOF_CI16 ? 4 : 8;
+  const int gpl = (Tg + 31) / 32;
+  const bool chunked = Tg >= 32;
+  const bool vcell = vin && Ti % VS == 0;  // 16-byte vectors within every cell
+  const int g0 = lane * gpl, g1 = min(Tg, g0 + gpl);
   for (int c = warp; c < C; c += kNwI) {
     const uint8_t* row = gin + static_cast<int64_t>(c) * u.in_stride * ES;
     unsigned long long* vr = V + (c / Fi) * Tg;
-    row_powers<DT>(row, T, vin, [&](int t, uint32_t p) {
-      atomicAdd(&vr[t / Ti], static_cast<unsigned long long>(p));
-    });
+    if (chunked && vcell) {
+      // the lane's cells are one run of 16-byte vectors: eight loads in flight
+      const int vpc = Ti / VS, nvec = (g1 - g0) * vpc;
+      const uint4* vb = reinterpret_cast<const uint4*>(row + static_cast<size_t>(g0) * Ti * ES);
+      unsigned long long sc = 0ull;
+      int kc = 0, g = g0;
+      for (int k0 = 0; k0 < nvec; k0 += 8) {
+        uint4 v[8];
+#pragma unroll
+        for (int j = 0; j < 8; ++j)
+          if (k0 + j < nvec) v[j] = __ldg(vb + k0 + j);
+#pragma unroll
+        for (int j = 0; j < 8; ++j) {
+          if (k0 + j < nvec) {
+            sc += vec_power_sum<DT>(v[j]);
+            if (++kc == vpc) {
+              atomicAdd(&vr[g], sc);
+              sc = 0ull;
+              kc = 0;
+              ++g;
+            }
+          }
+        }
+      }
+    } else if (chunked) {
+      for (int g = g0; g < g1; ++g) {
+        unsigned long long sc = 0ull;
+        for (int t = g * Ti; t < g * Ti + Ti; ++t) sc += ipow<DT>(row, t);
+        atomicAdd(&vr[g], sc);
+      }
+    } else {
+      row_powers<DT>(row, T, vin, [&](int t, uint32_t p) {
+        atomicAdd(&vr[t / Ti], static_cast<unsigned long long>(p));
+      });
+    }
   }
   __syncthreads();
   double med = 0.0, sig = 0.0;
@@ -812,11 +894,14 @@ __device__ void grid_unit(const KParams& kp, const DevUnit& u, uint8_t* smem, In
       const int I = 1 << k;
       if (I > (1 << kp.max_log_window) || (I > Tg && I > Cg)) break;
       const double thr = thr_i(kp, med, sig, k);
-      if (kp.enable_time && I <= Tg) st_grid_lines(V, Fg, Fn, NG, Cg, Tg, 1, Tg, I, thr);
-      if (kp.enable_freq && I <= Cg) st_grid_lines(V, Fg, Fn, NG, Tg, Cg, Tg, 1, I, thr);
+      long long* Kw = reinterpret_cast<long long*>(hist);  // the selection's histogram is free here
+      if (kp.enable_time && I <= Tg) st_grid_lines(V, Fg, Fn, NG, Cg, Tg, 1, Tg, I, thr, Kw);
+      if (kp.enable_freq && I <= Cg) st_grid_lines(V, Fg, Fn, NG, Tg, Cg, Tg, 1, I, thr, Kw);
     }
   }
   // per channel: the history test on the unflagged samples, mask and data
+  const bool vout_cell = vcell && (!u.mask || (u.flags & kUnitMaskVec)) &&
+                         (!u.out || inplace || (u.flags & kUnitOutVec));
   for (int c = warp; c < C; c += kNwI) {
     const uint8_t* row = gin + static_cast<int64_t>(c) * u.in_stride * ES;
     const uint8_t* fr = Fg + (c / Fi) * Tg;
@@ -837,13 +922,62 @@ __device__ void grid_unit(const KParams& kp, const DevUnit& u, uint8_t* smem, In
     };
     unsigned long long s = 0;
     int n = 0;
-    for (int t = lane; t < T; t += 32) {
-      const bool fl = fr[t / Ti] != 0;
-      if (!fl) {
-        s += ipow<DT>(row, t);
-        ++n;
+    if (chunked && vout_cell) {
+      // the lane's whole cells with 16-byte vectors: the mask VS bytes and the
+      // data 16 bytes at a time, the power sum of the unflagged cells
+      // eight vectors of the lane's run of cells loaded before any is stored
+      const int vpc = Ti / VS, nvec = (g1 - g0) * vpc;
+      int kc = 0, g = g0;
+      bool fl = g < g1 && fr[g] != 0;
+      for (int k0 = 0; k0 < nvec; k0 += 8) {
+        uint4 v[8];
+#pragma unroll
+        for (int j = 0; j < 8; ++j)
+          if (k0 + j < nvec)
+            v[j] = __ldg(reinterpret_cast<const uint4*>(row + (static_cast<size_t>(g0) * Ti + (k0 + j) * VS) * ES));
+#pragma unroll
+        for (int j = 0; j < 8; ++j) {
+          if (k0 + j < nvec) {
+            const int t = g0 * Ti + (k0 + j) * VS;
+            if (mr) {
+              if constexpr (VS == 4) *reinterpret_cast<uint32_t*>(mr + t) = fl ? 0x01010101u : 0u;
+              else *reinterpret_cast<uint2*>(mr + t) = fl ? make_uint2(0x01010101u, 0x01010101u) : make_uint2(0u, 0u);
+            }
+            if (fl) {
+              if (orow) *reinterpret_cast<uint4*>(orow + t * ES) = make_uint4(0u, 0u, 0u, 0u);
+            } else {
+              s += vec_power_sum<DT>(v[j]);
+              n += VS;
+              if (orow && !inplace) *reinterpret_cast<uint4*>(orow + t * ES) = v[j];
+            }
+            if (++kc == vpc) {
+              kc = 0;
+              ++g;
+              fl = g < g1 && fr[g] != 0;
+            }
+          }
+        }
       }
-      put(t, fl);
+    } else if (chunked) {
+      for (int g = g0; g < g1; ++g) {
+        const bool fl = fr[g] != 0;
+        for (int t = g * Ti; t < g * Ti + Ti; ++t) {
+          if (!fl) {
+            s += ipow<DT>(row, t);
+            ++n;
+          }
+          put(t, fl);
+        }
+      }
+    } else {
+      for (int t = lane; t < T; t += 32) {
+        const bool fl = fr[t / Ti] != 0;
+        if (!fl) {
+          s += ipow<DT>(row, t);
+          ++n;
+        }
+        put(t, fl);
+      }
     }
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
