@@ -432,14 +432,14 @@ template <int NT>
 struct Fixed {
   uint64_t mbar;
   int item, ok, last, state, n_keep, n_tgt, q_done, n_def, rows_done;
-  int row_next;  // flag task: next kept row to hand out (warps claim rows as they go)
+  int row_next;  // flag task: next (kept row, segment) item to hand out (warps claim items as they go)
   int def[9];  // parked tasks whose unit was not ready
   unsigned int red_u32[NT / kWarp];
   unsigned long long red_a[NT / kWarp], red_b[NT / kWarp], red_c[NT / kWarp];
   unsigned long long cnt_time, cnt_total, cnt_hist;
   unsigned long long mo1, mo2lo, mo2hi;  // moments of this CTA's rows
   unsigned long long rowS[kMaxRowsPerTask];
-  unsigned long long rowFlagSum[kMaxRowsPerTask];
+  unsigned long long rowFlagSum[kMaxRowsPerTask];  // flagged sum (general path), unflagged (packed)
   int rowNFlag[kMaxRowsPerTask];
   uint8_t rowFc[kMaxRowsPerTask];
   uint8_t rowFh[kMaxRowsPerTask];
@@ -2667,40 +2667,6 @@ __device__ LOFK_TASK_FN void task_fine(const KParams& kp, const DevUnit& u, Unit
   if (f.last) unit_round2<DT, NT>(kp, u, us, ws, f);
 }
 
-// History test of one row (Section 4.1): the mean of its unflagged powers
-// against the cached threshold of its ring; stages the value for the commit
-// and adds the row to the task's counts.  One thread; returns whether the
-// whole row is flagged.
-template <int NT>
-__device__ __forceinline__ int history_row(const KParams& kp, const DevUnit& u, int c, int r, int T,
-                                           int nfl, unsigned long long su, Fixed<NT>& f) {
-  const long long h = u.hist_slot >= 0 ? u.hist_slot + c : -1;
-  const int n = T - nfl;
-  int fh = 0;
-  if (n > 0) {
-    const double cur = __ddiv_rn(__ull2double_rn(su), static_cast<double>(n));
-    double staged = cur;
-    if (f.rowHon[r]) {
-      const double thr = f.rowThr[r];
-      if (!(cur < thr)) {
-        fh = 1;
-        staged = thr;
-      }
-    }
-    if (h >= 0) {
-      kp.hist.pend[h] = staged;
-      kp.hist.pend_flag[h] = 1;
-      kp.hist.pend_seq[h] = kp.block_seq;
-    }
-  } else if (h >= 0) {
-    kp.hist.pend_flag[h] = 0;
-  }
-  atomicAdd(&f.cnt_time, static_cast<unsigned long long>(nfl));
-  if (fh) atomicAdd(&f.cnt_hist, 1ull);
-  atomicAdd(&f.cnt_total, fh ? static_cast<unsigned long long>(T) : static_cast<unsigned long long>(nfl));
-  return fh;
-}
-
 // A row flagged whole: mask all ones, data all zero.  One warp.
 template <int DT>
 __device__ void write_row_flagged(const DevUnit& u, int c, int T) {
@@ -2833,62 +2799,58 @@ __device__ LOFK_TASK_FN void task_flag(const KParams& kp, const DevUnit& u, Unit
       const int nsg = wr_seg_count<kWrNpl>(T);
       uint8_t* const stage = ws + ((4 * R * MW + 15) & ~15) + warp * 2 * ST::kBufBytes;
       const uint64_t pol = l2_policy_drop();  // the input's last read
-      // rows are claimed one at a time (warp w starts with kept row w), so the
-      // warps of a task finish within about one row of each other
-      auto stage_item = [&](int k, int sg, int buf) {
-        const WrSeg g = wr_seg<kWrNpl>(T, sg);
+      // items (kept row k, segment) are claimed one at a time, item i being
+      // segment i % nsg of kept row i / nsg (warp w starts with item w), so the
+      // warps of a task finish within about one segment of each other.  The
+      // segments of a row add their flagged counts and unflagged sums into
+      // the row's accumulators (rowNFlag, rowFlagSum); the rows' history tests,
+      // the rows it flags whole and the zeroes of in-place rows follow the
+      // task's barrier below.
+      auto stage_item = [&](int it, int buf) {
+        const int k = it / nsg;
+        const WrSeg g = wr_seg<kWrNpl>(T, it - k * nsg);
         wr_stage<DT, kWrNpl>(stage + buf * ST::kBufBytes + lane * ST::kRowBytes,
                              gin + static_cast<int64_t>(row0 + f.keep[k]) * u.in_stride * TR::kBytes, g.xl, T,
                              vin, pol);
       };
-      int kc = warp < nkeep ? warp : -1, sg = 0, buf = 0;
-      if (kc >= 0) stage_item(kc, 0, 0);
-      int nfl_row = 0;
-      unsigned long long su_row = 0;
-      while (kc >= 0) {
-        // the next item: the next segment of this row, or the first of a claimed row
-        int kn = kc, sgn = sg + 1;
-        if (sgn == nsg) {
-          sgn = 0;
-          int claim = 0;
-          if (lane == 0) claim = atomicAdd(&f.row_next, 1);
-          claim = __shfl_sync(kFull, claim, 0);
-          kn = claim < nkeep ? claim : -1;
-        }
+      const int n_items = nkeep * nsg;
+      int it = warp < n_items ? warp : -1, buf = 0;
+      if (it >= 0) stage_item(it, 0);
+      while (it >= 0) {
+        int claim = 0;
+        if (lane == 0) claim = atomicAdd(&f.row_next, 1);
+        claim = __shfl_sync(kFull, claim, 0);
+        const int in = claim < n_items ? claim : -1;
+        const int kc = it / nsg, sg = it - kc * nsg;
         const int c = row0 + f.keep[kc], r = c - row0;
         uint8_t* const srow = stage + buf * ST::kBufBytes + lane * ST::kRowBytes;
         WrOut o;
         o.out = u.out ? static_cast<uint8_t*>(u.out) + static_cast<int64_t>(c) * u.out_stride * TR::kBytes
                       : nullptr;
         o.mask = u.mask ? u.mask + static_cast<int64_t>(c) * u.mask_stride : nullptr;
-        o.enabled = o.out != nullptr || o.mask != nullptr;
         o.inplace = (u.flags & kUnitInPlace) != 0;
         o.vout = (u.flags & kUnitOutVec) != 0;
         o.mask_vec = (u.flags & kUnitMaskVec) != 0;
         o.vin = vin;
         // out-of-place rows with 16-byte aligned output: the data goes out
-        // with coalesced stores after the pass, the mask bytes per lane
+        // with coalesced stores after the pass, and with it the mask bytes of
+        // 16-byte aligned mask rows
         uint8_t* const coal_row =
             ((kp.schedule & LOF_SCHED_COALESCED) && o.out && !o.inplace && o.vout) ? o.out : nullptr;
-        // with it, mask rows of 16-byte aligned rows and stride go out in the same rounds
         uint8_t* const coal_mask = (coal_row && o.mask && o.mask_vec) ? o.mask : nullptr;
         if (coal_row) o.out = nullptr;
         if (coal_mask) o.mask = nullptr;
         o.enabled = o.out != nullptr || o.mask != nullptr;
-        if (sg == 0) {
-          nfl_row = 0;
-          su_row = 0;
-        }
         const WrSeg g = wr_seg<kWrNpl>(T, sg);
         cp_async_wait_all();  // this item's samples (the only group in flight)
         WrRow<kWrNpl> Rw;
         wr_build<DT, kWrNpl>(Rw, srow, s_Kp[0]);
-        if (kn >= 0) {
+        if (in >= 0) {
           // the next item into the other buffer as early as possible (the
           // input comes from DRAM), once the bulk stores of its last item
           // have read it
           bulk_wait_read();
-          stage_item(kn, sgn, buf ^ 1);
+          stage_item(in, buf ^ 1);
         }
         wr_passes<kWrNpl>(Rw, g, 1, f.kmax_t, s_Kp, (kp.schedule & LOF_SCHED_BOUND64) != 0);
         int nfl = 0;
@@ -2896,31 +2858,13 @@ __device__ LOFK_TASK_FN void task_flag(const KParams& kp, const DevUnit& u, Unit
         wr_finish<DT, kWrNpl>(Rw, g, T, srow, smbits + r * MW + 2, o, nfl, su);
         if (coal_row)
           wr_store_coalesced<DT, kWrNpl>(stage + buf * ST::kBufBytes, Rw.M[0], g, T, coal_row, coal_mask);
-        nfl_row += nfl;
-        su_row += su;
-        if (sg == nsg - 1) {
-          int fh = 0;
-          if (lane == 0) fh = history_row<NT>(kp, u, c, r, T, nfl_row, su_row, f);
-          fh = __shfl_sync(kFull, fh, 0);
-          if (fh) {
-            bulk_wait_all();  // the row's bulk stores land before the rewrite
-            __syncwarp();
-            write_row_flagged<DT>(u, c, T);
-          } else if (o.inplace && o.out) {
-            __syncwarp();  // the row's flag words, written by every lane
-            const uint32_t* mrow = smbits + r * MW + 2;
-            for (int w = lane; w < nch; w += 32) {
-              uint32_t m = mrow[w];
-              while (m) {
-                const int j = __ffs(m) - 1;
-                m &= m - 1u;
-                TR::zero(o.out, 32 * w + j);
-              }
-            }
-          }
+        // the row's counts: its history test and any whole-row flagging
+        // follow the task's barrier, once every segment of the row is written
+        if (lane == 0) {
+          atomicAdd(&f.rowNFlag[r], nfl);
+          atomicAdd(&f.rowFlagSum[r], su);
         }
-        kc = kn;
-        sg = sgn;
+        it = in;
         buf ^= 1;
       }
       bulk_wait_all();  // buffers free for the next task; data stored
@@ -2992,7 +2936,6 @@ __device__ LOFK_TASK_FN void task_flag(const KParams& kp, const DevUnit& u, Unit
   // time pass has not finished)
   const bool rows_done = f.rows_done != 0;
   for (int r = tid; r < R; r += NT) {
-    if (rows_done && !f.rowFc[r]) continue;
     const long long h = u.hist_slot >= 0 ? u.hist_slot + row0 + r : -1;
     unsigned long long add_total;
     if (f.rowFc[r]) {
@@ -3003,7 +2946,8 @@ __device__ LOFK_TASK_FN void task_flag(const KParams& kp, const DevUnit& u, Unit
       const int n = T - nfl;
       uint8_t fh = 0;
       if (n > 0) {
-        const unsigned long long su = f.rowS[r] - f.rowFlagSum[r];
+        // the packed pass accumulates the unflagged sum, the general path the flagged one
+        const unsigned long long su = rows_done ? f.rowFlagSum[r] : f.rowS[r] - f.rowFlagSum[r];
         const double cur = __ddiv_rn(__ull2double_rn(su), static_cast<double>(n));
         double staged = cur;
         if (f.rowHon[r]) {
@@ -3041,12 +2985,13 @@ __device__ LOFK_TASK_FN void task_flag(const KParams& kp, const DevUnit& u, Unit
     const int nsego = (T + SEGO - 1) / SEGO;
     const uint64_t pol_drop = l2_policy_drop();
     // rows of the packed time pass were written by the warps that flagged
-    // them; only rows flagged whole (frequency pass, history test) remain
+    // them; only rows flagged whole (frequency pass, history test) and the
+    // zeroes of in-place rows remain
     const bool fused = rows_done;
     for (int task = warp; task < R * nsego; task += NW) {
       const int r = task / nsego, s = task - r * nsego;
       const bool full = f.rowFc[r] || f.rowFh[r];
-      if (fused && !full) continue;
+      if (fused && !full && !(inplace && u.out)) continue;
       const uint32_t* M = smbits + r * MW + 2;
       const int64_t grow_idx = static_cast<int64_t>(row0 + r);
       uint4 win[NQO];
