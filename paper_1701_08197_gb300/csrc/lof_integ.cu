@@ -57,6 +57,8 @@ constexpr int kIntegSmem = kOffFn + kIntegMaxT;
 static_assert(kIntegSmem <= 227 * 1024 - 1024, "one CTA per SM");
 
 struct IntegShared {
+  long long kw[65];      // integer window thresholds of one window size (I <= 64)
+  uint32_t ctot[128];    // chunk totals of the selection histograms (32 bins a chunk)
   double median_f, sigma_f, median_t, sigma_t;
   unsigned long long cnt_time, cnt_total, cnt_hist;
   unsigned long long pref[2];
@@ -243,28 +245,45 @@ __device__ void select2(long long n, long long r0, long long r1, K key, uint32_t
       if (!same && hi == p1) atomicAdd(&hist[2048 + dig], 1u);
     }
     __syncthreads();
+    // the histograms' chunk totals (32 bins a chunk), one warp a chunk
+    const int nch = (1 << nb) / 32, nh = same ? 1 : 2;
+    for (int c = warp; c < nh * nch; c += kNwI) {
+      uint32_t x = hist[(c / nch) * 2048 + (c % nch) * 32 + lane];
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(kFullI, x, o);
+      if (lane == 0) f.ctot[c] = x;
+    }
+    __syncthreads();
     if (warp < f.nrank) {
       const uint32_t* h = hist + (same ? 0 : 2048 * warp);
+      const uint32_t* ct = f.ctot + (same ? 0 : nch * warp);
       long long rk = f.rank[warp], base = 0;
       uint32_t digit = 0;
-      for (int b0 = 0; b0 < (1 << nb); b0 += 32) {
-        const uint32_t cnt = h[b0 + lane];
-        uint32_t incl = cnt;
+      // the rank's chunk from the chunk totals, then its bin inside the chunk
+      auto find = [&](const uint32_t* cnts, int n, int& at) {
+        for (int b0 = 0; b0 < n; b0 += 32) {
+          const uint32_t cnt = b0 + lane < n ? cnts[b0 + lane] : 0u;
+          uint32_t incl = cnt;
 #pragma unroll
-        for (int o = 1; o < 32; o <<= 1) {
-          const uint32_t y = __shfl_up_sync(kFullI, incl, o);
-          if (lane >= o) incl += y;
+          for (int o = 1; o < 32; o <<= 1) {
+            const uint32_t y = __shfl_up_sync(kFullI, incl, o);
+            if (lane >= o) incl += y;
+          }
+          const uint32_t tot = __shfl_sync(kFullI, incl, 31);
+          if (rk < base + tot) {
+            const unsigned hit = __ballot_sync(kFullI, rk < base + static_cast<long long>(incl));
+            const int l = __ffs(hit) - 1;
+            at = b0 + l;
+            rk -= base + __shfl_sync(kFullI, incl - cnt, l);
+            base = 0;
+            return true;
+          }
+          base += tot;
         }
-        const uint32_t tot = __shfl_sync(kFullI, incl, 31);
-        if (rk < base + tot) {
-          const unsigned hit = __ballot_sync(kFullI, rk < base + static_cast<long long>(incl));
-          const int l = __ffs(hit) - 1;
-          digit = static_cast<uint32_t>(b0 + l);
-          rk -= base + __shfl_sync(kFullI, incl - cnt, l);
-          break;
-        }
-        base += tot;
-      }
+        return false;
+      };
+      int chunk = 0, bin = 0;
+      if (find(ct, nch, chunk) && find(h + 32 * chunk, 32, bin)) digit = static_cast<uint32_t>(32 * chunk + bin);
       if (lane == 0) {
         f.pref[warp] = (f.pref[warp] << nb) | digit;
         f.rank[warp] = rk;
@@ -357,23 +376,42 @@ __device__ __forceinline__ double thr_i(const KParams& kp, double m, double s, i
 // partial sum is exact, at a fraction of the binary64 operations.
 template <class V>
 __device__ void st_1d(const KParams& kp, V v, int L, double med, double sig, uint8_t* fl,
-                      uint8_t* next) {
+                      uint8_t* next, long long* Kw) {
   if (!(sig > 0.0) || L <= 0) return;
   for (int k = 0;; ++k) {
     const int I = 1 << k;
     if (I > (1 << kp.max_log_window) || I > L) break;
     const double thr = thr_i(kp, med, sig, k);
     for (int i = threadIdx.x; i < L; i += kNtI) next[i] = fl[i];
+    // the binary64 test su > (I - n) * thr as the integer one su > Kw[n]
+    // (su is exact and at most 2^51; Kw[n] = floor of the product, -1 below 0)
+    for (int n = threadIdx.x; n <= I; n += kNtI) {
+      const double P = __dmul_rn(static_cast<double>(I - n), thr);
+      Kw[n] = P < 0.0 ? -1ll : (P >= 9.0e18 ? 0x7FFFFFFFFFFFFFFFll : __double2ll_rd(P));
+    }
     __syncthreads();
-    for (int t = threadIdx.x; t + I <= L; t += kNtI) {
-      int nf = 0;
-      unsigned long long su = 0;
-      for (int j = t; j < t + I; ++j) {
+    // each thread slides over its run of window starts (each value enters and
+    // leaves its window sum once) against the flags on entry
+    const int nw = L - I + 1, per = (nw + kNtI - 1) / kNtI;
+    const int t0 = threadIdx.x * per, t1 = min(nw, t0 + per);
+    if (t0 < t1) {
+      unsigned long long su = 0ull;
+      int nf = 0, done = 0;
+      for (int j = t0; j < t0 + I - 1; ++j) {
         if (fl[j]) ++nf;
         else su += v(j);
       }
-      if (__ull2double_rn(su) > __dmul_rn(static_cast<double>(I - nf), thr))
-        for (int j = t; j < t + I; ++j) next[j] = 1;
+      for (int t = t0; t < t1; ++t) {
+        const int e = t + I - 1;
+        if (fl[e]) ++nf;
+        else su += v(e);
+        if (static_cast<long long>(su) > Kw[nf]) {
+          for (int j = max(t, done); j < t + I; ++j) next[j] = 1;
+          done = t + I;
+        }
+        if (fl[t]) --nf;
+        else su -= v(t);
+      }
     }
     __syncthreads();
     for (int i = threadIdx.x; i < L; i += kNtI) fl[i] = next[i];
@@ -455,7 +493,7 @@ __device__ void freq_stage(const KParams& kp, unsigned long long* S, unsigned lo
     __syncthreads();
   }
   // a4: frequency SumThreshold
-  if (kp.enable_freq) st_1d(kp, [&](int i) { return S[i]; }, C, f.median_f, f.sigma_f, Fc, Fcn);
+  if (kp.enable_freq) st_1d(kp, [&](int i) { return S[i]; }, C, f.median_f, f.sigma_f, Fc, Fcn, f.kw);
   __syncthreads();
 }
 
@@ -512,7 +550,7 @@ __device__ void integ_unit(const KParams& kp, const DevUnit& u, uint8_t* smem, I
   if (f.nkept > 0) {
     stats_u64(kp, T, [&](long long i) { return G[i]; }, hist, f, &med_t, &sig_t);
     // a6: SumThreshold over the series
-    if (kp.enable_time) st_1d(kp, [&](int i) { return G[i]; }, T, med_t, sig_t, Ft, Fn);
+    if (kp.enable_time) st_1d(kp, [&](int i) { return G[i]; }, T, med_t, sig_t, Ft, Fn, f.kw);
   }
   __syncthreads();
   // a7, a8: per channel.  A kept row is summed for the history test while its
@@ -690,7 +728,7 @@ __device__ void chan_unit(const KParams& kp, const DevUnit& u, uint8_t* smem, In
       __syncthreads();
       double med = med_p, sig = sig_p;
       if constexpr (!POOLED) stats_u64(kp, T, [&](long long i) { return R[i]; }, hist, f, &med, &sig);
-      if (kp.enable_time) st_1d(kp, [&](int i) { return R[i]; }, T, med, sig, Ft, Fn);
+      if (kp.enable_time) st_1d(kp, [&](int i) { return R[i]; }, T, med, sig, Ft, Fn, f.kw);
       __syncthreads();
       unsigned long long sum = 0;
       int n = 0;
