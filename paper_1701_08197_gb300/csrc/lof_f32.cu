@@ -71,6 +71,20 @@ __device__ __forceinline__ double warp_sum_d(double v) {
   for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(kFullF, v, o);
   return v;
 }
+// Compensated float32 accumulation (Knuth's TwoSum): hi + lo carries the
+// sum of the added values to about 2^-48 relative per lane, in float32
+// arithmetic (GB300's binary64 rate is a small fraction of its float32 one).
+// The caller checks that hi and lo stay finite (a sum beyond the float32
+// range) and then sums in binary64 instead.
+__device__ __forceinline__ void df_add(float& hi, float& lo, float x) {
+  const float t = __fadd_rn(hi, x);
+  const float bp = __fsub_rn(t, hi);
+  const float e = __fadd_rn(__fsub_rn(hi, __fsub_rn(t, bp)), __fsub_rn(x, bp));
+  hi = t;
+  lo = __fadd_rn(lo, e);
+}
+__device__ __forceinline__ bool df_ok(float hi, float lo) { return isfinite(hi) && isfinite(lo); }
+
 __device__ __forceinline__ long long warp_sum_ll(long long v) {
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(kFullF, v, o);
@@ -720,9 +734,17 @@ __device__ void wf_segment(const float* row, int T, int sg, bool vin, const F32S
     Mrow[xl >> 5] = R.M;
     nf = __popc(R.M);
     ne = __popc(entry);
+    float hi = 0.f, lo = 0.f;
 #pragma unroll
     for (int j = 0; j < kNplF; ++j)
-      if (!((R.M >> j) & 1u)) s = __dadd_rn(s, static_cast<double>(R.v[j]));
+      if (!((R.M >> j) & 1u)) df_add(hi, lo, R.v[j]);
+    s = __dadd_rn(static_cast<double>(hi), static_cast<double>(lo));
+    if (!df_ok(hi, lo)) {  // beyond the float32 range
+      s = 0.0;
+#pragma unroll
+      for (int j = 0; j < kNplF; ++j)
+        if (!((R.M >> j) & 1u)) s = __dadd_rn(s, static_cast<double>(R.v[j]));
+    }
   }
   nflag = __reduce_add_sync(kFullF, nf);
   nentry = __reduce_add_sync(kFullF, ne);
@@ -771,7 +793,7 @@ __device__ void f32_unit(const KParams& kp, const DevUnit& u, uint8_t* smem, F32
   // a2: row sums of the finite samples (binary64)
   for (int c = warp; c < C; c += kNwF) {
     const float* row = gin + static_cast<int64_t>(c) * u.in_stride * (IN + 1);
-    double s = 0.0;
+    float hi = 0.f, lo = 0.f;
     int nfin = 0;
     for (int x0 = lane * 4; x0 < T; x0 += 4 * 128) {  // four loads in flight, then the sums in order
       float4 v[4];
@@ -785,9 +807,21 @@ __device__ void f32_unit(const KParams& kp, const DevUnit& u, uint8_t* smem, F32
         for (int j = 0; j < 4; ++j) {
           const float xv = f4at(v[k], j);
           if (x + j < T && isfinite(xv)) {
-            s = __dadd_rn(s, static_cast<double>(xv));
+            df_add(hi, lo, xv);
             ++nfin;
           }
+        }
+      }
+    }
+    double s = __dadd_rn(static_cast<double>(hi), static_cast<double>(lo));
+    if (__any_sync(kFullF, !df_ok(hi, lo))) {  // beyond the float32 range: binary64, same lanes and order
+      s = 0.0;
+      for (int x = lane * 4; x < T; x += 128) {
+        const float4 v = ld4<IN>(row, x, T, vin);
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+          const float xv = f4at(v, j);
+          if (x + j < T && isfinite(xv)) s = __dadd_rn(s, static_cast<double>(xv));
         }
       }
     }
@@ -1220,7 +1254,7 @@ __global__ void __launch_bounds__(kNtF, 2) lof_f32c_kernel(const KParams kp) {
   // into every CTA of the cluster
   for (int i = warp; i < nr; i += kNwF) {
     const float* srow = data + static_cast<size_t>(i) * P;
-    double s = 0.0;
+    float hi = 0.f, lo = 0.f;
     int nfin = 0;
     for (int x = lane * 4; x < T; x += 128) {
       const float4 v = ld4s(srow, x, T);
@@ -1228,8 +1262,20 @@ __global__ void __launch_bounds__(kNtF, 2) lof_f32c_kernel(const KParams kp) {
       for (int j = 0; j < 4; ++j) {
         const float xv = f4at(v, j);
         if (x + j < T && isfinite(xv)) {
-          s = __dadd_rn(s, static_cast<double>(xv));
+          df_add(hi, lo, xv);
           ++nfin;
+        }
+      }
+    }
+    double s = __dadd_rn(static_cast<double>(hi), static_cast<double>(lo));
+    if (__any_sync(kFullF, !df_ok(hi, lo))) {  // beyond the float32 range: binary64, same lanes and order
+      s = 0.0;
+      for (int x = lane * 4; x < T; x += 128) {
+        const float4 v = ld4s(srow, x, T);
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+          const float xv = f4at(v, j);
+          if (x + j < T && isfinite(xv)) s = __dadd_rn(s, static_cast<double>(xv));
         }
       }
     }
