@@ -85,6 +85,19 @@ __device__ __forceinline__ void df_add(float& hi, float& lo, float x) {
 }
 __device__ __forceinline__ bool df_ok(float hi, float lo) { return isfinite(hi) && isfinite(lo); }
 
+__device__ __forceinline__ uint32_t saddr_f(const void* p) {
+  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+// Adds 1 to the shared counter at byte address base + 4 * t when t < n
+// (unsigned), as one predicated reduction.
+__device__ __forceinline__ void red_shared_inc_f(uint32_t t, uint32_t n, uint32_t base) {
+  asm volatile(
+      "{\n\t.reg .pred q;\n\t.reg .u32 a;\n\tsetp.lt.u32 q, %0, %1;\n\t"
+      "mad.lo.u32 a, %0, 4, %2;\n\t@q red.shared.add.u32 [a], 1;\n\t}" ::"r"(t),
+      "r"(n), "r"(base)
+      : "memory");
+}
+
 __device__ __forceinline__ long long warp_sum_ll(long long v) {
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(kFullF, v, o);
@@ -389,29 +402,40 @@ __device__ void window_count(const DevUnit& u, const uint8_t* Fc, uint32_t* hist
   const uint32_t w = 1u << s;
   const uint32_t base0 = klo + (f.prefix[0] << s), base1 = klo + (f.prefix[1] << s);
   const bool two = fine && f.n_rank == 2 && f.prefix[0] != f.prefix[1];
-  long long below = 0;
-  for_kept_vectors<IN>(u, Fc, [&](const float4& v) {
-#pragma unroll
-    for (int j = 0; j < 4; ++j) {
-      const float xv = f4at(v, j);
-      if (!isfinite(xv)) continue;
-      const float kv = MODE == 0 ? xv : fabsf(__fsub_rn(__fsub_rn(xv, med_hi), med_lo));
-      const uint32_t key = fkey(kv);
-      if (!fine) {
-        if (key < klo) {
-          ++below;
-        } else {
-          const uint32_t d = (key - klo) >> s;
-          if (d < 2048u) atomicAdd(&hist[d], 1u);
-        }
-      } else {
-        if (key - base0 < w) atomicAdd(&hist[key - base0], 1u);
-        if (two && key - base1 < w) atomicAdd(&hist[2048 + (key - base1)], 1u);
-      }
-    }
-  });
+  // Predicated counts, no branch per sample.  A key below klo wraps:
+  // key - klo >= 2^32 - klo > 2^23, as klo is the key of a finite value
+  // (at most that of FLT_MAX, 0xFF7FFFFF), so (key - klo) >> s >= 4096 for
+  // s <= 11 and the bin test alone keeps it out of the counters.
+  const uint32_t hsa = saddr_f(hist), hsa1 = hsa + 4u * 2048u;
+  const uint32_t wlim = two ? w : 0u;
+  uint32_t below = 0u;  // a lane's share: below 2^31 samples
   if (!fine) {
-    below = warp_sum_ll(below);
+    for_kept_vectors<IN>(u, Fc, [&](const float4& v) {
+#pragma unroll
+      for (int j = 0; j < 4; ++j) {
+        const float xv = f4at(v, j);
+        const float kv = MODE == 0 ? xv : fabsf(__fsub_rn(__fsub_rn(xv, med_hi), med_lo));
+        const uint32_t key = fkey(kv);
+        const uint32_t fin = isfinite(xv) ? 1u : 0u;
+        below += fin & (key < klo ? 1u : 0u);
+        red_shared_inc_f(fin ? (key - klo) >> s : 0xFFFFFFFFu, 2048u, hsa);
+      }
+    });
+  } else {
+    for_kept_vectors<IN>(u, Fc, [&](const float4& v) {
+#pragma unroll
+      for (int j = 0; j < 4; ++j) {
+        const float xv = f4at(v, j);
+        const float kv = MODE == 0 ? xv : fabsf(__fsub_rn(__fsub_rn(xv, med_hi), med_lo));
+        const uint32_t key = fkey(kv);
+        const bool fin = isfinite(xv);
+        red_shared_inc_f(fin ? key - base0 : 0xFFFFFFFFu, w, hsa);
+        red_shared_inc_f(fin ? key - base1 : 0xFFFFFFFFu, wlim, hsa1);
+      }
+    });
+  }
+  if (!fine) {
+    below = static_cast<uint32_t>(warp_sum_ll(static_cast<long long>(below)));
     if (lane == 0) f.red[warp] = static_cast<double>(below);  // exact: counts < 2^53
   }
   __syncthreads();
