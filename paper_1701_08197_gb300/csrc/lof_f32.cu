@@ -270,16 +270,24 @@ __device__ __forceinline__ void for_kept_vectors(const DevUnit& u, const uint8_t
   const int T = u.T, nchunk = (T + 127) / 128, total = u.C * nchunk;
   const bool vin = (u.flags & kUnitInVec) != 0;
   const float* gin = static_cast<const float*>(u.in);
+  // item i = row c, 128-sample chunk q: (c, q) advance by kNwF items a step
+  // (chunks < nchunk, kNwF <= nchunk or several wraps), no division per item
+  int c = warp / nchunk, q = warp - c * nchunk;
   for (int i0 = warp; i0 < total; i0 += NL * kNwF) {
     float4 v[NL];
     bool ok[NL];
 #pragma unroll
     for (int k = 0; k < NL; ++k) {
       const int item = i0 + k * kNwF;
-      const int c = item / nchunk, x = (item - c * nchunk) * 128 + lane * 4;
+      const int x = q * 128 + lane * 4;
       ok[k] = item < total && !Fc[c] && x < T;
       v[k] = ok[k] ? ld4<IN>(gin + static_cast<int64_t>(c) * u.in_stride * (IN + 1), x, T, vin)
                    : make_float4(0.f, 0.f, 0.f, 0.f);
+      q += kNwF;
+      while (q >= nchunk) {
+        q -= nchunk;
+        ++c;
+      }
     }
 #pragma unroll
     for (int k = 0; k < NL; ++k)
@@ -727,6 +735,17 @@ __device__ void wf_segment(const float* row, int T, int sg, bool vin, const F32S
       const bool bad = x + j < T && !isfinite(xv);
       R.v[4 * q + j] = (x + j < T && !bad) ? xv : 0.0f;
       if (bad) R.M |= 1u << (4 * q + j);
+    }
+  }
+  if constexpr (!SM) {
+    // the next segment's samples toward L2 while this one is computed
+    if (ob < T) {
+      const int s0n = (ob - kHaloF) & ~31;
+      const float* pn = row + static_cast<int64_t>(s0n + lane * kNplF) * (IN + 1);
+      if (s0n + lane * kNplF < T) {
+#pragma unroll
+        for (int q = 0; q <= IN; ++q) asm volatile("prefetch.global.L2 [%0];" ::"l"(pn + 32 * q));
+      }
     }
   }
   const uint32_t entry = R.M;
