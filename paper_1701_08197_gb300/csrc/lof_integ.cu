@@ -842,6 +842,47 @@ __device__ void st_grid_lines(const unsigned long long* V, uint8_t* fl, uint8_t*
   __syncthreads();
 }
 
+// The same test along the rows of cells (the time direction: lines of L
+// contiguous cells): one warp per line, each lane sliding over its run of
+// window starts, the window sum at its first start summed directly, so the
+// lanes of a warp read cells of one row (few shared-memory bank conflicts)
+// and all warps of the CTA take lines.
+__device__ void st_grid_rows(const unsigned long long* V, uint8_t* fl, uint8_t* next, int NG, int n_lines,
+                             int L, int I, double thr, long long* Kw) {
+  for (int i = threadIdx.x; i < NG; i += kNtI) next[i] = fl[i];
+  for (int n = threadIdx.x; n <= I; n += kNtI) {
+    const double P = __dmul_rn(static_cast<double>(I - n), thr);
+    Kw[n] = P < 0.0 ? -1ll : (P >= 9.0e18 ? 0x7FFFFFFFFFFFFFFFll : __double2ll_rd(P));
+  }
+  __syncthreads();
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int nw = L - I + 1, per = (nw + 31) / 32;
+  for (int r = warp; r < n_lines; r += kNwI) {
+    const int b = r * L, t0 = lane * per, t1 = min(nw, t0 + per);
+    if (t0 >= t1) continue;
+    unsigned long long su = 0ull;
+    int nf = 0, done = 0;
+    for (int j = t0; j < t0 + I - 1; ++j) {
+      if (fl[b + j]) ++nf;
+      else su += V[b + j];
+    }
+    for (int t = t0; t < t1; ++t) {
+      const int e = b + t + I - 1;
+      if (fl[e]) ++nf;
+      else su += V[e];
+      if (static_cast<long long>(su) > Kw[nf]) {
+        for (int j = max(t, done); j < t + I; ++j) next[b + j] = 1;
+        done = t + I;
+      }
+      if (fl[b + t]) --nf;
+      else su -= V[b + t];
+    }
+  }
+  __syncthreads();
+  for (int i = threadIdx.x; i < NG; i += kNtI) fl[i] = next[i];
+  __syncthreads();
+}
+
 // The two-dimensional mode (time_mode = 2): powers summed into cells of Fi
 // channels x Ti samples (Fi divides C, Ti divides T, at most kIntegMaxT
 // cells), one median and sigma over the cells, then for I = 1, 2, 4, ...
@@ -933,7 +974,7 @@ __device__ void grid_unit(const KParams& kp, const DevUnit& u, uint8_t* smem, In
       if (I > (1 << kp.max_log_window) || (I > Tg && I > Cg)) break;
       const double thr = thr_i(kp, med, sig, k);
       long long* Kw = reinterpret_cast<long long*>(hist);  // the selection's histogram is free here
-      if (kp.enable_time && I <= Tg) st_grid_lines(V, Fg, Fn, NG, Cg, Tg, 1, Tg, I, thr, Kw);
+      if (kp.enable_time && I <= Tg) st_grid_rows(V, Fg, Fn, NG, Cg, Tg, I, thr, Kw);
       if (kp.enable_freq && I <= Cg) st_grid_lines(V, Fg, Fn, NG, Tg, Cg, Tg, 1, I, thr, Kw);
     }
   }
@@ -960,23 +1001,25 @@ __device__ void grid_unit(const KParams& kp, const DevUnit& u, uint8_t* smem, In
     };
     unsigned long long s = 0;
     int n = 0;
-    if (chunked && vout_cell) {
-      // the lane's whole cells with 16-byte vectors: the mask VS bytes and the
-      // data 16 bytes at a time, the power sum of the unflagged cells
-      // eight vectors of the lane's run of cells loaded before any is stored
-      const int vpc = Ti / VS, nvec = (g1 - g0) * vpc;
-      int kc = 0, g = g0;
-      bool fl = g < g1 && fr[g] != 0;
-      for (int k0 = 0; k0 < nvec; k0 += 8) {
+    if (vout_cell) {
+      // the row's 16-byte vectors, lane L taking vectors L, L + 32, ... (coalesced
+      // loads and stores), eight in flight; the cell of vector k is k / vpc,
+      // tracked from one step to the next without a division
+      const int vpc = Ti / VS, nv = T / VS, qd = 32 / vpc, rd = 32 % vpc;
+      int g = lane / vpc, kc = lane - (lane / vpc) * vpc;
+      for (int k0 = 0; k0 < nv; k0 += 8 * 32) {
         uint4 v[8];
 #pragma unroll
-        for (int j = 0; j < 8; ++j)
-          if (k0 + j < nvec)
-            v[j] = __ldg(reinterpret_cast<const uint4*>(row + (static_cast<size_t>(g0) * Ti + (k0 + j) * VS) * ES));
+        for (int j = 0; j < 8; ++j) {
+          const int k = k0 + 32 * j + lane;
+          if (k < nv) v[j] = __ldg(reinterpret_cast<const uint4*>(row) + k);
+        }
 #pragma unroll
         for (int j = 0; j < 8; ++j) {
-          if (k0 + j < nvec) {
-            const int t = g0 * Ti + (k0 + j) * VS;
+          const int k = k0 + 32 * j + lane;
+          if (k < nv) {
+            const bool fl = fr[g] != 0;
+            const int t = k * VS;
             if (mr) {
               if constexpr (VS == 4) *reinterpret_cast<uint32_t*>(mr + t) = fl ? 0x01010101u : 0u;
               else *reinterpret_cast<uint2*>(mr + t) = fl ? make_uint2(0x01010101u, 0x01010101u) : make_uint2(0u, 0u);
@@ -988,11 +1031,12 @@ __device__ void grid_unit(const KParams& kp, const DevUnit& u, uint8_t* smem, In
               n += VS;
               if (orow && !inplace) *reinterpret_cast<uint4*>(orow + t * ES) = v[j];
             }
-            if (++kc == vpc) {
-              kc = 0;
-              ++g;
-              fl = g < g1 && fr[g] != 0;
-            }
+          }
+          g += qd;
+          kc += rd;
+          if (kc >= vpc) {
+            kc -= vpc;
+            ++g;
           }
         }
       }
