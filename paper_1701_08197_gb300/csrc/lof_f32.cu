@@ -703,6 +703,14 @@ __device__ __forceinline__ uint32_t wf_fire(const WfRow& R, int lane, float tI, 
   return f;
 }
 
+// Segments of a row of T samples: a segment that does not reach T ends its
+// interior D = (SPAN - halo) & ~31 after its start (a multiple of 32), and
+// the next starts STEP = (D - halo) & ~31 later.
+__device__ __forceinline__ int wf_seg_count(int T) {
+  constexpr int SPAN = 32 * kNplF, D = (SPAN - kHaloF) & ~31, STEP = (D - kHaloF) & ~31;
+  return T <= SPAN ? 1 : (T - SPAN + STEP - 1) / STEP + 1;
+}
+
 // Flags of segment sg of one row (rows past 1024 samples overlap by a halo of
 // 120 samples); interior flag words go to Mrow, returns the interior's number
 // of flagged samples, entry-flagged samples and unflagged sum.
@@ -711,12 +719,9 @@ __device__ void wf_segment(const float* row, int T, int sg, bool vin, const F32S
                            uint32_t* Mrow, int& nflag, int& nentry, double& su) {
   constexpr int SPAN = 32 * kNplF;
   const int lane = threadIdx.x & 31;
-  int oa = 0, s0 = 0, ob = SPAN >= T ? T : ((SPAN - kHaloF) & ~31);
-  for (int i = 0; i < sg; ++i) {
-    oa = ob;
-    s0 = (oa - kHaloF) & ~31;
-    ob = s0 + SPAN >= T ? T : ((s0 + SPAN - kHaloF) & ~31);
-  }
+  // starts are multiples of 32, so the steps are constant (wf_seg_count)
+  constexpr int D = (SPAN - kHaloF) & ~31, STEP = (D - kHaloF) & ~31;
+  const int s0 = sg * STEP, oa = sg == 0 ? 0 : s0 - STEP + D, ob = s0 + SPAN >= T ? T : s0 + D;
   const int vend = min(T, s0 + SPAN);
   const int xl = s0 + lane * kNplF;
   WfRow R;
@@ -945,15 +950,7 @@ __device__ void f32_unit(const KParams& kp, const DevUnit& u, uint8_t* smem, F32
   }
   __syncthreads();
   // a6 - a8, one warp per row
-  const int nsg = T <= 32 * kNplF ? 1 : [&] {
-    int n = 1, ob = (32 * kNplF - kHaloF) & ~31;
-    while (ob < T) {
-      const int s0 = (ob - kHaloF) & ~31;
-      ob = s0 + 32 * kNplF >= T ? T : ((s0 + 32 * kNplF - kHaloF) & ~31);
-      ++n;
-    }
-    return n;
-  }();
+  const int nsg = wf_seg_count(T);
   const bool mask_vec = (u.flags & kUnitMaskVec) != 0;
   const bool vout = (u.flags & kUnitOutVec) != 0;
   const bool inplace = (u.flags & kUnitInPlace) != 0;
@@ -1387,15 +1384,7 @@ __global__ void __launch_bounds__(kNtF, 2) lof_f32c_kernel(const KParams kp) {
   }
   __syncthreads();
   // a6: time pass, warps over (own row, segment)
-  const int nsg = T <= 32 * kNplF ? 1 : [&] {
-    int n = 1, ob = (32 * kNplF - kHaloF) & ~31;
-    while (ob < T) {
-      const int s0 = (ob - kHaloF) & ~31;
-      ob = s0 + 32 * kNplF >= T ? T : ((s0 + 32 * kNplF - kHaloF) & ~31);
-      ++n;
-    }
-    return n;
-  }();
+  const int nsg = wf_seg_count(T);
   if (f.time_on) {
     for (int item = warp; item < nr * nsg; item += kNwF) {
       const int i = item / nsg, sg = item - i * nsg;

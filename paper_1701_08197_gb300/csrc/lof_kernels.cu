@@ -1636,28 +1636,22 @@ __device__ __forceinline__ void wr_build(WrRow<NPL>& R, const uint8_t* srow, uin
 // kWrHalo samples (rounded to whole 32-sample words) before the end of the
 // previous interior; a segment's interior ends kWrHalo samples (rounded down
 // to a word) before its span, except at the end of the row.
+// With every start a multiple of 32, the steps are constant: a segment that
+// does not reach T ends its interior D = (SPAN - halo) & ~31 after its start,
+// and the next one starts STEP = (D - halo) & ~31 later, so segment sg spans
+// [sg * STEP, sg * STEP + SPAN) with interior [(sg - 1) * STEP + D, sg * STEP + D)
+// (from 0 for the first, to T for the last).
 template <int NPL>
 __device__ __forceinline__ void wr_seg_bounds(int T, int sg, int& s0, int& oa, int& ob) {
-  constexpr int SPAN = 32 * NPL;
-  oa = 0;
-  s0 = 0;
-  ob = SPAN >= T ? T : ((SPAN - kWrHalo) & ~31);
-  for (int i = 0; i < sg; ++i) {
-    oa = ob;
-    s0 = (oa - kWrHalo) & ~31;
-    ob = s0 + SPAN >= T ? T : ((s0 + SPAN - kWrHalo) & ~31);
-  }
+  constexpr int SPAN = 32 * NPL, D = (SPAN - kWrHalo) & ~31, STEP = (D - kWrHalo) & ~31;
+  s0 = sg * STEP;
+  oa = sg == 0 ? 0 : s0 - STEP + D;
+  ob = s0 + SPAN >= T ? T : s0 + D;
 }
 template <int NPL>
 __device__ __forceinline__ int wr_seg_count(int T) {
-  constexpr int SPAN = 32 * NPL;
-  int n = 1, ob = SPAN >= T ? T : ((SPAN - kWrHalo) & ~31);
-  while (ob < T) {
-    const int s0 = (ob - kWrHalo) & ~31;
-    ob = s0 + SPAN >= T ? T : ((s0 + SPAN - kWrHalo) & ~31);
-    ++n;
-  }
-  return n;
+  constexpr int SPAN = 32 * NPL, D = (SPAN - kWrHalo) & ~31, STEP = (D - kWrHalo) & ~31;
+  return T <= SPAN ? 1 : (T - SPAN + STEP - 1) / STEP + 1;
 }
 
 // Output of one row for the fused writer of the warp-row pass.
@@ -2443,9 +2437,9 @@ __device__ __forceinline__ uint32_t stats_rows(const DevUnit& u, int row0, int R
   const uint32_t wsa = saddr(win), hsa = saddr(hist);
   uint4 cur[NQ], nxt[NQ];
   uint32_t below = 0;
-  // the warp's k-th segment: segment k % nseg of row warp + (k / nseg) * NW
-  auto load_seg = [&](int k, uint4 (&v)[NQ]) {
-    const int kr = k / nseg, s = k - kr * nseg;
+  // the warp's k-th segment: segment s = k % nseg of row warp + kr * NW,
+  // kr = k / nseg (the pair advanced step by step, no division)
+  auto load_seg = [&](int k, int kr, int s, uint4 (&v)[NQ]) {
     const uint8_t* grow =
         gin + static_cast<int64_t>(row0 + min(warp + kr * NW, R - 1)) * u.in_stride * TR::kBytes;
     if (k < nk && vin && s * SEG + SEG <= T) {  // a whole segment: plain vector loads
@@ -2461,10 +2455,11 @@ __device__ __forceinline__ uint32_t stats_rows(const DevUnit& u, int row0, int R
     }
   };
   Acc sum = 0;
-  load_seg(0, cur);
+  load_seg(0, 0, 0, cur);
+  int kr = 0, s = 0;
   for (int k = 0; k < nk; ++k) {
-    load_seg(k + 1, nxt);
-    const int kr = k / nseg, s = k - kr * nseg;
+    const int sn = s + 1 == nseg ? 0 : s + 1, krn = s + 1 == nseg ? kr + 1 : kr;
+    load_seg(k + 1, krn, sn, nxt);
     auto count = [&](uint32_t val) {
       sum += val;
       if constexpr (WIN) {
@@ -2500,6 +2495,8 @@ __device__ __forceinline__ uint32_t stats_rows(const DevUnit& u, int row0, int R
     }
 #pragma unroll
     for (int q = 0; q < NQ; ++q) cur[q] = nxt[q];
+    kr = krn;
+    s = sn;
   }
   return below;
 }
@@ -2806,8 +2803,14 @@ __device__ LOFK_TASK_FN void task_flag(const KParams& kp, const DevUnit& u, Unit
       // the row's accumulators (rowNFlag, rowFlagSum); the rows' history tests,
       // the rows it flags whole and the zeroes of in-place rows follow the
       // task's barrier below.
+      // item / nsg as a multiply-high: m = ceil(2^32 / nsg) gives the exact
+      // quotient for items below 2^32 / nsg (here below 64 * nsg)
+      const uint32_t mq = nsg > 1 ? static_cast<uint32_t>((0x100000000ull + nsg - 1) / nsg) : 0u;
+      auto item_row = [&](int it) {
+        return nsg > 1 ? static_cast<int>(__umulhi(static_cast<uint32_t>(it), mq)) : it;
+      };
       auto stage_item = [&](int it, int buf) {
-        const int k = it / nsg;
+        const int k = item_row(it);
         const WrSeg g = wr_seg<kWrNpl>(T, it - k * nsg);
         wr_stage<DT, kWrNpl>(stage + buf * ST::kBufBytes + lane * ST::kRowBytes,
                              gin + static_cast<int64_t>(row0 + f.keep[k]) * u.in_stride * TR::kBytes, g.xl, T,
@@ -2821,7 +2824,7 @@ __device__ LOFK_TASK_FN void task_flag(const KParams& kp, const DevUnit& u, Unit
         if (lane == 0) claim = atomicAdd(&f.row_next, 1);
         claim = __shfl_sync(kFull, claim, 0);
         const int in = claim < n_items ? claim : -1;
-        const int kc = it / nsg, sg = it - kc * nsg;
+        const int kc = item_row(it), sg = it - kc * nsg;
         const int c = row0 + f.keep[kc], r = c - row0;
         uint8_t* const srow = stage + buf * ST::kBufBytes + lane * ST::kRowBytes;
         WrOut o;
