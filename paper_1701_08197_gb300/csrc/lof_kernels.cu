@@ -2991,75 +2991,78 @@ __device__ LOFK_TASK_FN void task_flag(const KParams& kp, const DevUnit& u, Unit
     // them; only rows flagged whole (frequency pass, history test) and the
     // zeroes of in-place rows remain
     const bool fused = rows_done;
-    for (int task = warp; task < R * nsego; task += NW) {
-      const int r = task / nsego, s = task - r * nsego;
+    // rows first (each warp reads the rows' flags; rows with nothing left
+    // are skipped whole), their segments striped over the warps
+    for (int r = 0; r < R; ++r) {
       const bool full = f.rowFc[r] || f.rowFh[r];
       if (fused && !full && !(inplace && u.out)) continue;
-      const uint32_t* M = smbits + r * MW + 2;
-      const int64_t grow_idx = static_cast<int64_t>(row0 + r);
-      uint4 win[NQO];
-      if (u.out && !inplace && vin && vout && !full) {
+      for (int s = warp; s < nsego; s += NW) {
+        const uint32_t* M = smbits + r * MW + 2;
+        const int64_t grow_idx = static_cast<int64_t>(row0 + r);
+        uint4 win[NQO];
+        if (u.out && !inplace && vin && vout && !full) {
+#pragma unroll
+          for (int q = 0; q < NQO; ++q) {
+            const int x = s * SEGO + q * 32 * VS + lane * VS;
+            if (x + VS <= T)
+              win[q] = ldg_policy(gin + grow_idx * u.in_stride * TR::kBytes +
+                                      static_cast<size_t>(x) * TR::kBytes, pol_drop);
+          }
+        }
 #pragma unroll
         for (int q = 0; q < NQO; ++q) {
           const int x = s * SEGO + q * 32 * VS + lane * VS;
-          if (x + VS <= T)
-            win[q] = ldg_policy(gin + grow_idx * u.in_stride * TR::kBytes +
-                                    static_cast<size_t>(x) * TR::kBytes, pol_drop);
-        }
-      }
-#pragma unroll
-      for (int q = 0; q < NQO; ++q) {
-        const int x = s * SEGO + q * 32 * VS + lane * VS;
-        if (x >= T) continue;
-        const int nv = min(VS, T - x);
-        const uint32_t valid = nv >= VS ? kVm : ((1u << nv) - 1u);
-        const uint32_t bits = full ? valid : ((M[x >> 5] >> (x & 31)) & valid);
-        if (u.mask) {
-          uint8_t* mrow = u.mask + grow_idx * u.mask_stride;
-          if (mask_vec && nv == VS) {
-            if constexpr (VS == 4) {
-              st_stream_u32(mrow + x, (bits * 0x00204081u) & 0x01010101u);
-            } else {
-              const uint32_t lo = ((bits & 0xFu) * 0x00204081u) & 0x01010101u;
-              const uint32_t hi = (((bits >> 4) & 0xFu) * 0x00204081u) & 0x01010101u;
-              st_stream_u64(mrow + x, lo, hi);
-            }
-          } else {
-            for (int j = 0; j < nv; ++j) mrow[x + j] = static_cast<uint8_t>((bits >> j) & 1u);
-          }
-        }
-        if (u.out) {
-          uint8_t* orow = static_cast<uint8_t*>(u.out) + grow_idx * u.out_stride * TR::kBytes;
-          if (inplace) {
-            uint32_t m = bits;
-            while (m) {
-              const int j = __ffs(m) - 1;
-              m &= m - 1u;
-              TR::zero(orow, x + j);
-            }
-          } else if (vin && vout && nv == VS) {
-            uint4 w = make_uint4(0u, 0u, 0u, 0u);
-            if (bits != kVm) {
-              w = win[q];
-              if (bits) {
-                uint32_t wd[4] = {w.x, w.y, w.z, w.w};
-#pragma unroll
-                for (int j = 0; j < VS; ++j) {
-                  if ((bits >> j) & 1u) {
-                    if constexpr (VS == 4) wd[j] = 0u;
-                    else wd[j >> 1] &= (j & 1) ? 0x0000FFFFu : 0xFFFF0000u;
-                  }
-                }
-                w = make_uint4(wd[0], wd[1], wd[2], wd[3]);
+          if (x >= T) continue;
+          const int nv = min(VS, T - x);
+          const uint32_t valid = nv >= VS ? kVm : ((1u << nv) - 1u);
+          const uint32_t bits = full ? valid : ((M[x >> 5] >> (x & 31)) & valid);
+          if (u.mask) {
+            uint8_t* mrow = u.mask + grow_idx * u.mask_stride;
+            if (mask_vec && nv == VS) {
+              if constexpr (VS == 4) {
+                st_stream_u32(mrow + x, (bits * 0x00204081u) & 0x01010101u);
+              } else {
+                const uint32_t lo = ((bits & 0xFu) * 0x00204081u) & 0x01010101u;
+                const uint32_t hi = (((bits >> 4) & 0xFu) * 0x00204081u) & 0x01010101u;
+                st_stream_u64(mrow + x, lo, hi);
               }
+            } else {
+              for (int j = 0; j < nv; ++j) mrow[x + j] = static_cast<uint8_t>((bits >> j) & 1u);
             }
-            __stcs(reinterpret_cast<uint4*>(orow + static_cast<size_t>(x) * TR::kBytes), w);
-          } else {
-            const uint8_t* irow = gin + grow_idx * u.in_stride * TR::kBytes;
-            for (int j = 0; j < nv; ++j) {
-              if ((bits >> j) & 1u) TR::zero(orow, x + j);
-              else TR::copy(orow + static_cast<size_t>(x + j) * TR::kBytes,
-                            irow + static_cast<size_t>(x + j) * TR::kBytes);
+          }
+          if (u.out) {
+            uint8_t* orow = static_cast<uint8_t*>(u.out) + grow_idx * u.out_stride * TR::kBytes;
+            if (inplace) {
+              uint32_t m = bits;
+              while (m) {
+                const int j = __ffs(m) - 1;
+                m &= m - 1u;
+                TR::zero(orow, x + j);
+              }
+            } else if (vin && vout && nv == VS) {
+              uint4 w = make_uint4(0u, 0u, 0u, 0u);
+              if (bits != kVm) {
+                w = win[q];
+                if (bits) {
+                  uint32_t wd[4] = {w.x, w.y, w.z, w.w};
+#pragma unroll
+                  for (int j = 0; j < VS; ++j) {
+                    if ((bits >> j) & 1u) {
+                      if constexpr (VS == 4) wd[j] = 0u;
+                      else wd[j >> 1] &= (j & 1) ? 0x0000FFFFu : 0xFFFF0000u;
+                    }
+                  }
+                  w = make_uint4(wd[0], wd[1], wd[2], wd[3]);
+                }
+              }
+              __stcs(reinterpret_cast<uint4*>(orow + static_cast<size_t>(x) * TR::kBytes), w);
+            } else {
+              const uint8_t* irow = gin + grow_idx * u.in_stride * TR::kBytes;
+              for (int j = 0; j < nv; ++j) {
+                if ((bits >> j) & 1u) TR::zero(orow, x + j);
+                else TR::copy(orow + static_cast<size_t>(x + j) * TR::kBytes,
+                              irow + static_cast<size_t>(x + j) * TR::kBytes);
+              }
             }
           }
         }
