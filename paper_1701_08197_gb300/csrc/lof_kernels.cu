@@ -2460,6 +2460,15 @@ __device__ __forceinline__ uint32_t stats_rows(const DevUnit& u, int row0, int R
   for (int k = 0; k < nk; ++k) {
     const int sn = s + 1 == nseg ? 0 : s + 1, krn = s + 1 == nseg ? kr + 1 : kr;
     load_seg(k + 1, krn, sn, nxt);
+    {  // the segment after that toward L2, one 128-byte line a lane
+      const int s2 = sn + 1 == nseg ? 0 : sn + 1, kr2 = sn + 1 == nseg ? krn + 1 : krn;
+      constexpr int LINES = SEG * TR::kBytes / 128;
+      if (k + 2 < nk && s2 * SEG + SEG <= T && lane < LINES) {
+        const uint8_t* g2 = gin + static_cast<int64_t>(row0 + warp + kr2 * NW) * u.in_stride * TR::kBytes +
+                            static_cast<size_t>(s2) * SEG * TR::kBytes + lane * 128;
+        asm volatile("prefetch.global.L2 [%0];" ::"l"(g2));
+      }
+    }
     auto count = [&](uint32_t val) {
       sum += val;
       if constexpr (WIN) {
