@@ -179,7 +179,7 @@ __device__ __forceinline__ void zero_sample(void* row, int64_t t, int es) {
 // Time direction: one warp per channel row.
 __global__ void __launch_bounds__(32 * kSirWarps) lof_sir_time_kernel(const DevUnit* units, int n_units,
                                                                       int64_t n_chan, int percent,
-                                                                      int es) {
+                                                                      int es, int skip_upto) {
   __shared__ SirTiles tiles[kSirWarps];
   const int warp = threadIdx.x >> 5;
   const int64_t g = static_cast<int64_t>(blockIdx.x) * kSirWarps + warp;
@@ -187,7 +187,7 @@ __global__ void __launch_bounds__(32 * kSirWarps) lof_sir_time_kernel(const DevU
   const int ui = unit_of(units, n_units, g);
   const DevUnit& u = units[ui];
   const int c = static_cast<int>(g - u.chan_off);
-  if (c < 0 || c >= u.C || !u.mask || u.T > 32 * 32 * kSirMaxTiles) return;
+  if (c < 0 || c >= u.C || !u.mask || u.T > 32 * 32 * kSirMaxTiles || u.T <= skip_upto) return;
   uint8_t* mrow = u.mask + static_cast<int64_t>(c) * u.mask_stride;
   uint8_t* orow = u.out ? static_cast<uint8_t*>(u.out) + static_cast<int64_t>(c) * u.out_stride * es
                         : nullptr;
@@ -220,6 +220,95 @@ __global__ void __launch_bounds__(32 * kSirWarps) lof_sir_time_kernel(const DevU
   if ((threadIdx.x & 31) == 0 && added && u.stats)
     atomicAdd(reinterpret_cast<unsigned long long*>(&u.stats->n_flag_total),
               static_cast<unsigned long long>(added));
+}
+
+// Time direction for rows of up to 32 * kSirRowBlocks samples: one thread per
+// row (a channel), the row taken in blocks of 32 samples.  A forward pass over
+// the blocks keeps, per block, the prefix sum at its start and the least
+// prefix sum over the starts of the blocks before it (in shared memory,
+// [block][thread]); a backward pass then reloads each block's flags,
+// recomputes its prefix minima in registers and decides its samples from
+// the last one down against the running maximum of the prefix sums after
+// them -- the same integer prefix sums as the line form, no shuffles and no
+// barriers.
+constexpr int kSirRowThreads = 64;
+constexpr int kSirRowBlocks = 96;  // rows up to 3072 samples
+
+// Flag bits of samples [x, x + 32) of a mask row (0 past T), as a word.
+__device__ __forceinline__ uint32_t mask_bits32(const uint8_t* mrow, int x, int T, bool vec) {
+  uint32_t b = 0u;
+  if (vec && x + 32 <= T) {
+    const uint4 p = *reinterpret_cast<const uint4*>(mrow + x);
+    const uint4 q = *reinterpret_cast<const uint4*>(mrow + x + 16);
+    const uint32_t w[8] = {p.x, p.y, p.z, p.w, q.x, q.y, q.z, q.w};
+#pragma unroll
+    for (int i = 0; i < 32; ++i) b |= (((w[i >> 2] >> (8 * (i & 3))) & 0xFFu) != 0u ? 1u : 0u) << i;
+  } else {
+    for (int i = 0; i < 32 && x + i < T; ++i) b |= (mrow[x + i] != 0 ? 1u : 0u) << i;
+  }
+  return b;
+}
+
+__global__ void __launch_bounds__(kSirRowThreads) lof_sir_time_rows_kernel(const DevUnit* units, int n_units,
+                                                                          int64_t n_chan, int percent, int es) {
+  __shared__ int s_qs[kSirRowBlocks][kSirRowThreads], s_pl[kSirRowBlocks][kSirRowThreads];
+  const int tid = threadIdx.x;
+  const int64_t g = static_cast<int64_t>(blockIdx.x) * kSirRowThreads + tid;
+  if (g >= n_chan) return;  // no warp-wide step follows
+  const DevUnit& u = units[unit_of(units, n_units, g)];
+  const int c = static_cast<int>(g - u.chan_off);
+  const int T = u.T;
+  if (c < 0 || c >= u.C || !u.mask || T > 32 * kSirRowBlocks) return;
+  uint8_t* const mrow = u.mask + static_cast<int64_t>(c) * u.mask_stride;
+  uint8_t* const orow =
+      u.out ? static_cast<uint8_t*>(u.out) + static_cast<int64_t>(c) * u.out_stride * es : nullptr;
+  const bool vec = (u.flags & kUnitMaskVec) != 0;
+  const int wp = percent, wn = percent - 100;
+  const int nb = (T + 31) / 32;
+  int q = 0, m = INT32_MAX;
+  for (int b = 0; b < nb; ++b) {
+    const uint32_t bits = mask_bits32(mrow, 32 * b, T, vec);
+    const int n = min(32, T - 32 * b);
+    s_qs[b][tid] = q;
+    s_pl[b][tid] = m;
+    for (int i = 0; i < n; ++i) {
+      m = min(m, q);
+      q += ((bits >> i) & 1u) ? wp : wn;
+    }
+  }
+  int R = INT32_MIN, added = 0;
+  for (int b = nb - 1; b >= 0; --b) {
+    const uint32_t bits = mask_bits32(mrow, 32 * b, T, vec);
+    const int n = min(32, T - 32 * b);
+    int L[32];
+    int l = s_pl[b][tid], qq = s_qs[b][tid], qe = 0;
+#pragma unroll
+    for (int i = 0; i < 32; ++i) {
+      l = min(l, qq);  // a = 32 b + i
+      L[i] = l;
+      qq += ((bits >> i) & 1u) ? wp : wn;
+      if (i + 1 == n) qe = qq;  // Q at the block's last sample + 1
+    }
+    uint32_t nw = 0u;
+#pragma unroll
+    for (int i = 31; i >= 0; --i) {
+      if (i < n) {
+        R = max(R, qe);
+        nw |= (R >= L[i] ? 1u : 0u) << i;
+        qe -= ((bits >> i) & 1u) ? wp : wn;
+      }
+    }
+    nw &= ~bits;
+    while (nw) {
+      const int i = __ffs(nw) - 1;
+      nw &= nw - 1u;
+      mrow[32 * b + i] = 1;
+      if (orow) zero_sample(orow, 32 * b + i, es);
+      ++added;
+    }
+  }
+  if (added && u.stats)
+    atomicAdd(reinterpret_cast<unsigned long long*>(&u.stats->n_flag_total), static_cast<unsigned long long>(added));
 }
 
 // Frequency direction: a CTA stages a strip of 32 time steps of every
@@ -396,11 +485,20 @@ extern "C" int lofk_launch_sir(const lofk::DevUnit* units, int n_units, int64_t 
   using namespace lofk;
   if (n_units <= 0 || percent <= 0) return 0;
   cudaStream_t st = static_cast<cudaStream_t>(stream);
-  const int64_t nb = (n_chan + kSirWarps - 1) / kSirWarps;
-  lof_sir_time_kernel<<<static_cast<unsigned>(nb), 32 * kSirWarps, 0, st>>>(units, n_units, n_chan,
-                                                                          percent, es);
+  // time: rows of up to 3072 samples one thread per row, longer ones by the
+  // line form (which skips the others)
+  const int64_t nr = (n_chan + kSirRowThreads - 1) / kSirRowThreads;
+  lof_sir_time_rows_kernel<<<static_cast<unsigned>(nr), kSirRowThreads, 0, st>>>(units, n_units, n_chan, percent,
+                                                                               es);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return static_cast<int>(e);
+  if (max_time > 32 * kSirRowBlocks) {
+    const int64_t nb = (n_chan + kSirWarps - 1) / kSirWarps;
+    lof_sir_time_kernel<<<static_cast<unsigned>(nb), 32 * kSirWarps, 0, st>>>(units, n_units, n_chan, percent,
+                                                                            es, 32 * kSirRowBlocks);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return static_cast<int>(e);
+  }
   // frequency: units of up to 256 channels one thread per time step, larger
   // ones by the line form (which skips the others)
   const unsigned gx = static_cast<unsigned>((std::max(1, max_time) + kSirColThreads - 1) / kSirColThreads);
