@@ -409,6 +409,18 @@ def run_gpu(args):
 
     # end to end through the host-buffer entry point
     if not args.no_e2e and rank == 0:
+        # the host buffers on the GPU's own NUMA node: allocated (first touch)
+        # from the CPUs local to the GPU, the process's affinity restored after
+        saved_cpus = None
+        local = gpu_local_cpus(dev)
+        if local:
+            try:
+                saved_cpus = os.sched_getaffinity(0)
+                os.sched_setaffinity(0, local)
+            except OSError:
+                saved_cpus = None
+        res["e2e_host_cpus"] = (f"{len(local)} CPUs local to the GPU" if saved_cpus is not None
+                                else "unchanged (the GPU's local CPUs not found)")
         hx = x.cpu().pin_memory()
         hout = torch.empty_like(hx).pin_memory()
         hmask = torch.empty(hx.shape[:-1], dtype=torch.uint8).pin_memory()
@@ -430,11 +442,14 @@ def run_gpu(args):
         wall = time.perf_counter() - t0
         fl.status(stream)
         e2e_ms = e0.elapsed_time(e1) / e2e_steps
+        if saved_cpus is not None:
+            os.sched_setaffinity(0, saved_cpus)
         res["e2e"] = {"value": samples / (e2e_ms * 1e-3) / 1e6, "unit": "Msamples/s",
                       "h2d_bytes_per_step": int(hx.numel() * hx.element_size()),
                       "d2h_bytes_per_step": int(hout.numel() * hout.element_size() + hmask.numel()
                                                 + hst.numel() * 8),
-                      "ms_per_step": e2e_ms, "wall_ms_per_step": wall * 1e3 / e2e_steps}
+                      "ms_per_step": e2e_ms, "wall_ms_per_step": wall * 1e3 / e2e_steps,
+                      "host_buffers": res.pop("e2e_host_cpus")}
     fl.close()
     # the other configurations (rank 0, one GPU): the headline's buffers go first
     if args.configs and rank == 0 and world == 1:
@@ -454,6 +469,31 @@ def run_gpu(args):
     if world > 1:
         dist.destroy_process_group()
     return res
+
+
+def gpu_local_cpus(dev):
+    """The CPUs (of those this process may use) that Linux lists as local to
+    the GPU `dev` (sysfs local_cpulist of its PCI device), or an empty set."""
+    import torch
+    try:
+        pr = torch.cuda.get_device_properties(dev)
+        dom, bus, devn = (getattr(pr, "pci_domain_id", None), getattr(pr, "pci_bus_id", None),
+                          getattr(pr, "pci_device_id", None))
+        if bus is None:
+            return set()
+        path = f"/sys/bus/pci/devices/{dom or 0:04x}:{bus:02x}:{devn or 0:02x}.0/local_cpulist"
+        with open(path) as fh:
+            text = fh.read().strip()
+        cpus = set()
+        for part in text.split(","):
+            if "-" in part:
+                lo, hi = part.split("-")
+                cpus.update(range(int(lo), int(hi) + 1))
+            elif part:
+                cpus.add(int(part))
+        return cpus & os.sched_getaffinity(0)
+    except (OSError, ValueError, RuntimeError, AttributeError):
+        return set()
 
 
 # ---------------------------------------------------------------- other configurations
