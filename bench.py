@@ -471,6 +471,19 @@ def run_gpu(args):
     return res
 
 
+def parse_cpulist(text):
+    """CPU ids of a Linux cpulist string ("0-3,8,10-11")."""
+    cpus = set()
+    for part in text.strip().split(","):
+        part = part.strip()
+        if "-" in part:
+            lo, hi = part.split("-")
+            cpus.update(range(int(lo), int(hi) + 1))
+        elif part:
+            cpus.add(int(part))
+    return cpus
+
+
 def gpu_local_cpus(dev):
     """The CPUs (of those this process may use) that Linux lists as local to
     the GPU `dev` (sysfs local_cpulist of its PCI device), or an empty set."""
@@ -483,16 +496,8 @@ def gpu_local_cpus(dev):
             return set()
         path = f"/sys/bus/pci/devices/{dom or 0:04x}:{bus:02x}:{devn or 0:02x}.0/local_cpulist"
         with open(path) as fh:
-            text = fh.read().strip()
-        cpus = set()
-        for part in text.split(","):
-            if "-" in part:
-                lo, hi = part.split("-")
-                cpus.update(range(int(lo), int(hi) + 1))
-            elif part:
-                cpus.add(int(part))
-        return cpus & os.sched_getaffinity(0)
-    except (OSError, ValueError, RuntimeError, AttributeError):
+            return parse_cpulist(fh.read()) & os.sched_getaffinity(0)
+    except Exception:  # no GPU, no such sysfs entry, no affinity interface: leave things as they are
         return set()
 
 

@@ -1,6 +1,7 @@
 """The benchmark's host logic on CPU: option plumbing into the workload
-description, the two-dimensional cell parser, the traffic lookup's shape check
-and the oracle arm's JSON line with method options."""
+description, the two-dimensional cell parser, the cpulist parser of the e2e
+leg's host-buffer placement, the traffic lookup's shape check and the oracle
+arm's JSON line with method options."""
 import json
 import os
 import subprocess
@@ -17,6 +18,16 @@ def test_grid_cells_parse():
     assert bench.grid_cells(None) is None
     assert bench.grid_cells("4x16") == (4, 16)
     assert bench.grid_cells("1X32") == (1, 32)
+
+
+def test_cpulist_parse_and_no_gpu_means_no_affinity_change():
+    assert bench.parse_cpulist("0-3,8,10-11\n") == {0, 1, 2, 3, 8, 10, 11}
+    assert bench.parse_cpulist("5") == {5}
+    assert bench.parse_cpulist("") == set()
+    # without a GPU (or its sysfs entry) the e2e leg leaves the affinity alone
+    import torch
+    if not torch.cuda.is_available():
+        assert bench.gpu_local_cpus(0) == set()
 
 
 def test_workload_config_names_every_option():
